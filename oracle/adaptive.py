@@ -1,0 +1,74 @@
+"""Global adaptive sketching loop (oracle; test infrastructure only).
+
+Follows Algorithm 1 (HSSCompressAdaptive) restricted to the global sketch of A,
+which is this project's reading of the stopping test's scope (the paper applies
+it per HSS node, with eps / level(tau)):
+
+1. R <- JL-Operator(d0 + Delta-d, n); S <- A R (and S' <- A^T R).
+2. Q <- orthonormal basis of S(:, 1:d)   (QR of the first d columns).
+3. S~ <- S(:, d+1 : d+Delta-d)             (the last Delta-d columns).
+4. S^ <- (I - Q Q^T)^2 S~                  (two steps of block Gram-Schmidt,
+   the remark after Eq. stopping_criteria-1).
+5. stop when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F
+   (Eq. stopping_criteria-1; no 1/sqrt(d) factor, the remark before it).
+6. otherwise R <- [R  R_bar], d <- d + Delta-d, S <- A R, and repeat, while the
+   grown R keeps at most d_max columns.
+
+S is recomputed from the grown R at every step (the plain definition), so the
+CUDA path's incremental update (rescale old columns, sketch only the new ones)
+is checked against it.  QR is numpy's (LAPACK Householder), a library step.
+When both S and S' are tested, the loop stops when both tests pass.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .operators import Operator
+from .sketch import apply
+
+
+def project_twice(Q: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """(I - Q Q^T)^2 B, two block Gram-Schmidt passes."""
+    B = B - Q @ (Q.T @ B)
+    return B - Q @ (Q.T @ B)
+
+
+def norm_test(S: np.ndarray, d: int, dd: int, eps_rel: float, eps_abs: float):
+    """One stopping test on the columns of S: returns (stop, ||S^||_F, ||S~||_F)."""
+    Q = np.linalg.qr(S[:, :d])[0]
+    St = S[:, d:d + dd]
+    Sh = project_twice(Q, St)
+    nh = float(np.linalg.norm(Sh))
+    nt = float(np.linalg.norm(St))
+    stop = (nh < eps_abs) or (nh < eps_rel * nt)
+    return stop, nh, nt
+
+
+def adaptive(A: np.ndarray, kind: str, d0: int, dd: int, alpha: int, seed: int,
+             d_max: int, eps_rel: float, eps_abs: float, which: str = "both"):
+    """Run the loop; returns a dict with the operator, final S, S', the
+    per-test history [(d, stop, nh_S, nt_S, nh_St, nt_St)], and 'converged'."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    if A.shape[1] != n:
+        raise ValueError("square A expected")
+    if d0 + dd > d_max:
+        raise ValueError("d0 + Delta-d exceeds d_max")
+    op = Operator(kind, n, d0 + dd, alpha, seed)
+    d = d0
+    history = []
+    while True:
+        S, St = apply(A, op.dense())
+        stop_s, nh_s, nt_s = norm_test(S, d, dd, eps_rel, eps_abs)
+        if which == "S":
+            stop_t, nh_t, nt_t = True, 0.0, 0.0
+        else:
+            stop_t, nh_t, nt_t = norm_test(St, d, dd, eps_rel, eps_abs)
+        stop = stop_s and stop_t
+        history.append((d, stop, nh_s, nt_s, nh_t, nt_t))
+        if stop:
+            return dict(op=op, S=S, St=St, history=history, converged=True)
+        if op.d_total + dd > d_max:
+            return dict(op=op, S=S, St=St, history=history, converged=False)
+        op.increment(dd)
+        d += dd

@@ -1,0 +1,69 @@
+"""Pins for the oracle's adaptive loop (CPU only).
+
+* An exactly rank-r matrix with r < d0 has no range left for the new columns:
+  the first test must stop with ||S^|| ~ 0 (Sec. 4, Eq. stopping_criteria-1).
+* A matrix with a prescribed geometric singular spectrum reaches a larger d for
+  a smaller eps_rel (the test is monotone in its tolerance).
+* The two-pass projection leaves a block orthogonal to Q.
+* A full-rank matrix with a flat spectrum never passes a tight test and stops
+  at d_max without converging.
+"""
+import numpy as np
+import pytest
+
+from oracle import adaptive as ad
+from paper_2302_01977_gb300 import inputs
+
+KINDS = [("sjlt_block", 4), ("sjlt_graph", 4), ("srht", 1), ("gauss", 1)]
+
+
+@pytest.mark.parametrize("kind,alpha", KINDS)
+def test_low_rank_stops_first_test(kind, alpha):
+    n, r = 128, 12
+    A = inputs.low_rank_matrix(n, r, seed=1)
+    res = ad.adaptive(A, kind, d0=32, dd=16, alpha=alpha, seed=2, d_max=96,
+                      eps_rel=1e-8, eps_abs=1e-30)
+    assert res["converged"] and len(res["history"]) == 1
+    d, stop, nh, nt, nh_t, nt_t = res["history"][0]
+    assert nh < 1e-12 * nt and nh_t < 1e-12 * nt_t
+
+
+@pytest.mark.parametrize("kind,alpha", KINDS)
+def test_d_reached_monotone_in_eps(kind, alpha):
+    n = 128
+    sigma = 0.7 ** np.arange(n)
+    A = inputs.spectrum_matrix(n, sigma, seed=3)
+    reached = []
+    for eps in (1e-1, 1e-3, 1e-6):
+        res = ad.adaptive(A, kind, d0=8, dd=8, alpha=alpha, seed=4, d_max=128,
+                          eps_rel=eps, eps_abs=1e-300, which="S")
+        reached.append(res["op"].d_total)
+    assert reached[0] <= reached[1] <= reached[2]
+    assert reached[0] < reached[2]
+
+
+def test_projection_orthogonal():
+    Q, _ = np.linalg.qr(inputs.dense_matrix(200, 30, seed=5))
+    B = inputs.dense_matrix(200, 7, seed=6)
+    P = ad.project_twice(Q, B)
+    assert np.abs(Q.T @ P).max() < 1e-13 * np.abs(B).max()
+    # projecting a block already in range(Q) gives zero
+    assert np.abs(ad.project_twice(Q, Q @ B[:30])).max() < 1e-13
+
+
+def test_flat_spectrum_hits_d_max():
+    n = 96
+    A = inputs.spectrum_matrix(n, np.ones(n), seed=7)
+    res = ad.adaptive(A, "gauss", d0=16, dd=16, alpha=1, seed=8, d_max=64,
+                      eps_rel=1e-6, eps_abs=1e-300)
+    assert not res["converged"]
+    assert res["op"].d_total == 64
+    assert [h[0] for h in res["history"]] == [16, 32, 48]
+
+
+def test_absolute_tolerance_stops():
+    n = 64
+    A = 1e-12 * inputs.dense_matrix(n, n, seed=9)
+    res = ad.adaptive(A, "sjlt_block", d0=16, dd=8, alpha=4, seed=1, d_max=64,
+                      eps_rel=1e-12, eps_abs=1e-6)
+    assert res["converged"] and len(res["history"]) == 1

@@ -1,0 +1,274 @@
+"""Pins for the oracle's JL operators and sketch products (CPU only).
+
+Each check is a fact the paper or the mathematics fixes, not a retyped formula:
+nonzero counts and values (Sec. 3.2.3), the Sec. 6.1 worked example, the
+Sylvester recursion and H H^T = nu I (Sec. 3.2.2), R^T R = (n/d) I for an SRHT
+of power-of-two order, the FWHT route agreeing with the element formula,
+E||x^T R||^2 = ||x||^2 (Definition 3.2), A = I giving R back, and brute-force
+triple loops at n <= 64.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import operators as ops
+from oracle import sketch as sk
+from paper_2302_01977_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- SJLT ----------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,alpha", [(64, 16, 4), (100, 24, 3), (257, 128, 4), (33, 8, 8), (50, 5, 1)])
+def test_sjlt_block_structure(n, d, alpha):
+    op = ops.Operator("sjlt_block", n, d, alpha, seed=11)
+    R = op.dense()
+    nz = R != 0
+    assert (nz.sum(axis=1) == alpha).all()
+    assert np.allclose(np.abs(R[nz]), 1.0 / math.sqrt(alpha), rtol=0, atol=0)
+    chunk = d // alpha
+    for k in range(alpha):  # exactly one nonzero per chunk
+        assert (nz[:, k * chunk:(k + 1) * chunk].sum(axis=1) == 1).all()
+    assert abs((R ** 2).sum() - n) < 1e-9
+    cols, signs = op.sjlt_entries()
+    assert set(np.unique(signs).tolist()) <= {-1, 1}
+
+
+@pytest.mark.parametrize("n,d,alpha", [(64, 16, 4), (200, 128, 4), (40, 7, 7), (31, 9, 2)])
+def test_sjlt_graph_structure(n, d, alpha):
+    op = ops.Operator("sjlt_graph", n, d, alpha, seed=5)
+    cols, signs = op.sjlt_entries()
+    assert (np.diff(cols, axis=1) > 0).all()  # distinct and ascending
+    assert cols.min() >= 0 and cols.max() < d
+    R = op.dense()
+    assert ((R != 0).sum(axis=1) == alpha).all()
+    assert abs((R ** 2).sum() - n) < 1e-9
+
+
+def test_sjlt_positions_uniform_and_signs_balanced():
+    n, d, alpha = 20000, 64, 4
+    cols, signs = ops.Operator("sjlt_block", n, d, alpha, seed=3).sjlt_entries()
+    rel = cols - (np.arange(alpha) * (d // alpha))[None, :]
+    counts = np.bincount(rel.ravel(), minlength=d // alpha)
+    expect = n * alpha / (d // alpha)
+    chi2 = ((counts - expect) ** 2 / expect).sum()
+    assert chi2 < 60  # 15 dof: P(chi2 > 60) ~ 1e-7
+    assert abs((signs == 1).mean() - 0.5) < 0.01
+
+
+def test_sjlt_worked_example_crs_ccs():
+    ex = json.load(open(os.path.join(GOLDEN, "sjlt_worked_example.json")))
+    R = np.array(ex["R_times_sqrt_alpha"])
+    rows, colsk = np.nonzero(R)
+    n, d = R.shape
+    alpha = ex["alpha"]
+    cols = colsk.reshape(n, alpha)
+    signs = np.sign(R[rows, colsk]).astype(np.int8).reshape(n, alpha)
+    st = ops.crs_ccs(cols, signs, d)
+    for name, key in (("plus", "B_plus"), ("minus", "B_minus")):
+        B = np.zeros((n, d), dtype=int)
+        crs = st[name]
+        for i in range(n):
+            B[i, crs["col_idx"][crs["row_ptr"][i]:crs["row_ptr"][i + 1]]] = 1
+        assert (B == np.array(ex[key])).all()
+        B2 = np.zeros((n, d), dtype=int)
+        for c in range(d):
+            B2[crs["row_idx"][crs["col_ptr"][c]:crs["col_ptr"][c + 1]], c] = 1
+        assert (B2 == np.array(ex[key])).all()
+    # R = (B+ - B-)/sqrt(alpha)
+    Rs = (np.array(ex["B_plus"]) - np.array(ex["B_minus"])) / math.sqrt(alpha)
+    assert np.array_equal(Rs, R / math.sqrt(alpha))
+
+
+@pytest.mark.parametrize("kind", ["sjlt_block", "sjlt_graph"])
+def test_sjlt_outer_and_inner_forms_brute_force(kind):
+    n, d, alpha = 48, 16, 4
+    A = inputs.dense_matrix(n, n, seed=1)
+    op = ops.Operator(kind, n, d, alpha, seed=9)
+    cols, signs = op.sjlt_entries()
+    S_outer = sk.apply_sjlt_outer(A, cols, signs, op.scale(), d)
+    St_inner = sk.apply_sjlt_inner(A, ops.crs_ccs(cols, signs, d), op.scale(), d)
+    R = op.dense()
+    S_bf = np.zeros((n, d))
+    St_bf = np.zeros((n, d))
+    for i in range(n):
+        for c in range(d):
+            S_bf[i, c] = sum(A[i, j] * R[j, c] for j in range(n))
+            St_bf[i, c] = sum(A[j, i] * R[j, c] for j in range(n))
+    S, St = sk.apply(A, R)
+    for X in (S_outer, S):
+        assert np.allclose(X, S_bf, rtol=1e-13, atol=1e-13)
+    for X in (St_inner, St):
+        assert np.allclose(X, St_bf, rtol=1e-13, atol=1e-13)
+
+
+# --- SRHT ----------------------------------------------------------------
+
+@pytest.mark.parametrize("nu", [1, 2, 4, 16, 64])
+def test_hadamard_recursion_orthogonality(nu):
+    H = sk.hadamard(nu)
+    assert np.array_equal(H @ H.T, nu * np.eye(nu))
+    i = np.arange(nu)[:, None]
+    j = np.arange(nu)[None, :]
+    assert np.array_equal(H, np.where(ops.popcount_parity(i & j) == 1, -1.0, 1.0))
+
+
+def test_fwht_is_hadamard_product():
+    x = inputs.dense_matrix(5, 64, seed=2)
+    assert np.allclose(sk.fwht(x), x @ sk.hadamard(64).T, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,d", [(64, 16), (128, 128), (32, 5)])
+def test_srht_orthogonal_columns_power_of_two(n, d):
+    op = ops.Operator("srht", n, d, seed=4)
+    R = op.dense()
+    assert np.allclose(R.T @ R, (n / d) * np.eye(d), rtol=0, atol=1e-12)
+    mu = op.srht_samples()
+    assert len(set(mu.tolist())) == d and mu.min() >= 0 and mu.max() < n
+    assert abs((R ** 2).sum() - n) < 1e-9
+
+
+@pytest.mark.parametrize("n,d", [(64, 16), (50, 12), (37, 32)])
+def test_srht_fwht_route_equals_element_formula(n, d):
+    A = inputs.dense_matrix(9, n, seed=8)
+    op = ops.Operator("srht", n, d, seed=21)
+    S_def = A @ op.dense()
+    S_fwht = sk.srht_by_fwht(A, op.srht_diag(), op.srht_samples(), op.d_total)
+    assert np.allclose(S_def, S_fwht, rtol=1e-12, atol=1e-12)
+
+
+def test_srht_nu_too_small_rejected():
+    with pytest.raises(ValueError):
+        ops.Operator("srht", 8, 9)
+    op = ops.Operator("srht", 8, 6)
+    with pytest.raises(ValueError):
+        op.increment(3)
+
+
+# --- Gaussian ------------------------------------------------------------
+
+def test_gaussian_distribution():
+    from scipy import stats
+    z = ops.gaussian_z(4000, 0, 64, seed=12).ravel()
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # even/odd columns (cos and sin halves of one Box-Muller pair) uncorrelated
+    zz = ops.gaussian_z(20000, 0, 2, seed=13)
+    assert abs(np.corrcoef(zz[:, 0], zz[:, 1])[0, 1]) < 5 / math.sqrt(20000)
+
+
+def test_gaussian_columns_independent_of_width():
+    a = ops.gaussian_z(30, 0, 10, seed=1)
+    b = ops.gaussian_z(30, 3, 7, seed=1)
+    assert np.array_equal(a[:, 3:7], b)
+
+
+# --- all operators -------------------------------------------------------
+
+KIND_ARGS = [("sjlt_block", 4), ("sjlt_graph", 4), ("srht", 1), ("gauss", 1)]
+
+
+@pytest.mark.parametrize("kind,alpha", KIND_ARGS)
+def test_identity_returns_R(kind, alpha):
+    n, d = 64, 16
+    op = ops.Operator(kind, n, d, alpha, seed=77)
+    R = op.dense()
+    S, St = sk.apply(np.eye(n), R)
+    assert np.array_equal(S, R) and np.array_equal(St, R)
+
+
+@pytest.mark.parametrize("kind,alpha", KIND_ARGS)
+def test_unit_matrix_picks_row(kind, alpha):
+    n, d = 40, 8
+    op = ops.Operator(kind, n, d, alpha, seed=78)
+    R = op.dense()
+    E = np.zeros((n, n))
+    E[3, 17] = 1.0
+    S, St = sk.apply(E, R)
+    expect = np.zeros((n, d))
+    expect[3] = R[17]
+    assert np.array_equal(S, expect)
+    expect_t = np.zeros((n, d))
+    expect_t[17] = R[3]
+    assert np.array_equal(St, expect_t)
+
+
+@pytest.mark.parametrize("kind,alpha", KIND_ARGS)
+def test_symmetric_A_gives_equal_sketches(kind, alpha):
+    n, d = 64, 16
+    X = inputs.dense_matrix(n, n, seed=5)
+    A = X + X.T
+    S, St = sk.apply(A, ops.Operator(kind, n, d, alpha, seed=3).dense())
+    assert np.allclose(S, St, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind,alpha", KIND_ARGS)
+def test_jl_norm_expectation_monte_carlo(kind, alpha):
+    """E ||x^T R||^2 = ||x||^2 (Definition 3.2 with eps -> expectation)."""
+    n, d, T = 64, 16, 400
+    x = inputs.dense_matrix(1, n, seed=6)[0]
+    vals = np.array([((x @ ops.Operator(kind, n, d, alpha, seed=s).dense()) ** 2).sum() for s in range(T)])
+    mean, sd = vals.mean(), vals.std(ddof=1)
+    nx = (x ** 2).sum()
+    assert abs(mean - nx) < 5 * sd / math.sqrt(T)
+
+
+@pytest.mark.parametrize("kind,alpha", KIND_ARGS)
+def test_increment_rescales_and_appends(kind, alpha):
+    n, d0, dd = 64, 16, 8
+    base = ops.Operator(kind, n, d0, alpha, seed=31)
+    grown = ops.Operator(kind, n, d0, alpha, seed=31)
+    grown.increment(dd)
+    R0, R1 = base.dense(), grown.dense()
+    assert R1.shape == (n, d0 + dd)
+    ratio = grown.scale() / base.scale()
+    assert np.allclose(R1[:, :d0], R0 * ratio, rtol=1e-15, atol=0)
+    # the grown operator is again a JL operator of the new width
+    if kind.startswith("sjlt"):
+        assert ((R1[:, d0:] != 0).sum(axis=1) == alpha).all()
+        assert abs((R1 ** 2).sum() - n) < 1e-9
+    if kind == "srht":
+        assert np.allclose(R1.T @ R1, (n / (d0 + dd)) * np.eye(d0 + dd), atol=1e-12)
+
+
+def test_invalid_operator_arguments():
+    with pytest.raises(ValueError):
+        ops.Operator("sjlt_block", 10, 10, 3)
+    with pytest.raises(ValueError):
+        ops.Operator("sjlt_graph", 10, 3, 4)
+    with pytest.raises(ValueError):
+        ops.Operator("nope", 10, 3, 1)
+    with pytest.raises(ValueError):
+        ops.Operator("gauss", 0, 3, 1)
+
+
+# --- kernel matrix and input ordering -------------------------------------
+
+def test_kernel_matrix_brute_force_and_symmetry():
+    X = inputs.points(20, seed=1, dtype=np.float64)
+    Y = inputs.points(15, seed=2, dtype=np.float64)
+    A = sk.kernel_matrix(X, Y, 0.3, 0.0)
+    for i in range(20):
+        for j in range(15):
+            r2 = sum((X[i, k] - Y[j, k]) ** 2 for k in range(3))
+            assert abs(A[i, j] - math.exp(-r2 / (2 * 0.09))) < 1e-15
+    As = sk.kernel_matrix(X, X, 0.2, 1e-2)
+    assert np.array_equal(As, As.T)
+    assert np.allclose(np.diag(As), 1.0 + 1e-2, rtol=0, atol=1e-15)
+    rows = np.array([0, 7, 19])
+    assert np.array_equal(sk.kernel_rows(X, X, rows, 0.2, 1e-2), As[rows])
+
+
+def test_bisection_order_is_a_valid_median_split():
+    P = inputs.points(1000, seed=3, dtype=np.float64)
+    perm = inputs.bisection_order(P, leaf=64)
+    assert np.array_equal(np.sort(perm), np.arange(1000))
+    # top-level split: on the widest axis, left half <= right half
+    Q = P[perm]
+    axis = int(np.argmax(P.max(0) - P.min(0)))
+    assert Q[:500, axis].max() <= Q[500:, axis].min()
