@@ -1,0 +1,203 @@
+/*
+ * jlsketch.h -- C ABI of libjlsketch, Johnson-Lindenstrauss sketching of dense
+ * matrices on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the random samples of adaptive randomized HSS
+ * construction (Yaniv, Ghysels, Malik, Boateng, Li, "Construction of HSS matrix
+ * representation using adaptive Johnson-Lindenstrauss sketching"):
+ *
+ *     S  = A R        (sketch of the rows of A,    Sec. 6.3 "A R")
+ *     S' = A^T R      (sketch of the columns of A, Sec. 6.3 "A* R"; real A)
+ *
+ * for three JL operators R (n x d): the SJLT (Sec. 3.2.3, data structure
+ * Sec. 6.1), the SRHT R = D H P (Sec. 3.2.2, element formula Eq. RsrHt) and the
+ * Gaussian operator N(0, 1/d) (Sec. 3.2.1); R grows by Delta-d columns
+ * (Sec. 6.2, Algorithm 1: R <- [R R_bar], S <- [S A R_bar]) until the Frobenius
+ * stopping test of Eq. stopping_criteria-1 passes.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  A is rows x cols with leading dimension ld
+ *    (elements); S and S' are n x d_total with leading dimensions ldS, ldSt.
+ *  - Pointers named "device" must be CUDA device (or managed) memory of the
+ *    current device; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls that only launch work are asynchronous on that stream; calls that
+ *    return data to the host synchronize it and say so.
+ *  - Every call returns SK_OK (0) or a negative SK_ERR_* code and never throws.
+ *    A handle whose device work reported an error (an internal bound or wait
+ *    limit, see sketch_device_status) refuses further work with SK_ERR_DEVICE.
+ *  - The caller owns A, X, Y, S, S' and the stream.  A handle owns its
+ *    operator arrays, its orthonormal bases for the stopping test and its
+ *    scratch, all in device memory, and frees them in sketch_destroy.
+ *  - There is no CPU fallback: without a usable GPU, calls fail with
+ *    SK_ERR_DEVICE.
+ */
+#ifndef JLSKETCH_H
+#define JLSKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SK_OK                 0
+#define SK_ERR_INVALID_ARG   -1  /* bad size, kind, alpha, which, null pointer */
+#define SK_ERR_ALIGN         -2  /* pointer or leading dimension not aligned as required */
+#define SK_ERR_DTYPE         -3  /* unsupported element type / precision combination */
+#define SK_ERR_NOMEM         -4  /* device allocation failed */
+#define SK_ERR_D_MAX         -5  /* an increment would exceed the d_max given at creation */
+#define SK_ERR_STATE         -6  /* call out of order (e.g. increment apply before increment) */
+#define SK_ERR_TIMEOUT       -7  /* a bounded device-side wait gave up */
+#define SK_ERR_DEVICE        -8  /* CUDA error or device-side error flag */
+#define SK_ERR_UNSUPPORTED   -9  /* valid request this build does not implement */
+
+/* ---- operator kinds (Sec. 3.2) ------------------------------------------ */
+#define SK_SJLT_GRAPH 1  /* alpha distinct positions uniform in each row's block  */
+#define SK_SJLT_BLOCK 2  /* one position in each of alpha chunks of width/alpha    */
+#define SK_SRHT       3  /* R = D H P, nu = 2^ceil(log2 n), columns w/o replacement */
+#define SK_GAUSS      4  /* i.i.d. N(0, 1/d)                                      */
+
+/* ---- element types ------------------------------------------------------ */
+#define SK_F64 1
+#define SK_F32 2
+
+/* ---- arithmetic of an apply -------------------------------------------- */
+#define SK_PREC_NATIVE 0  /* F64 data: FP64; F32 data: FP32 on CUDA cores          */
+#define SK_PREC_BF16X2 3  /* F32 data: A = A_hi + A_lo (bf16), R likewise (Gaussian)
+                             or exact (+-1, SRHT); tcgen05 tensor cores, FP32
+                             accumulation; SRHT and Gaussian only                  */
+
+/* ---- which sketch ------------------------------------------------------- */
+#define SK_S    1  /* S  = A R   */
+#define SK_ST   2  /* S' = A^T R */
+#define SK_BOTH 3
+
+typedef struct sk_op* sk_handle;
+
+/* An input matrix: explicit, or generated from points (a Gaussian kernel). */
+typedef struct sk_matrix {
+  int32_t dtype;       /* SK_F32 or SK_F64 (also the type of X, Y)                 */
+  int32_t generator;   /* 0: explicit A; 1: A_ij = exp(-|x_i-y_j|^2/(2h^2)) + shift*[i==j] */
+  int64_t rows, cols;  /* A is rows x cols                                          */
+  const void* A;       /* explicit: device, row-major, 16-byte aligned               */
+  int64_t ld;          /* explicit: leading dimension >= cols; ld*elem_size % 16 == 0 */
+  const void* X;       /* generator: device, rows x 3, row-major                     */
+  const void* Y;       /* generator: device, cols x 3, row-major                     */
+  double h;            /* generator: kernel width h > 0                              */
+  double shift;        /* generator: diagonal shift                                  */
+} sk_matrix;
+
+/*
+ * sketch_create -- draw a JL operator R of size n x d on the device.
+ *   kind   SK_SJLT_GRAPH | SK_SJLT_BLOCK | SK_SRHT | SK_GAUSS (Sec. 3.2).
+ *   n      rows of R (= cols of A for S, rows of A for S'), 1 <= n < 2^31.
+ *   d      initial columns (Algorithm 1 starts with d0 + Delta-d), 1 <= d <= d_max.
+ *   alpha  SJLT nonzeros per row and block, 1 <= alpha <= min(d, 32); block
+ *          construction needs alpha | d (Sec. 3.2.3).  Ignored otherwise.
+ *   seed   64-bit seed; R is a pure function of (kind, n, d, alpha, seed) and
+ *          the increments applied (Philox4x64-10 streams).
+ *   d_max  capacity in columns, d <= d_max <= 8192; SRHT needs d_max <= nu.
+ *   stream where the generation kernels run (asynchronous).
+ * Out: *out receives the handle.  Errors: INVALID_ARG, NOMEM, DEVICE.
+ */
+int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t alpha,
+                  uint64_t seed, int32_t d_max, void* stream);
+
+/*
+ * sketch_increment -- append Delta-d columns to R (Algorithm 1, R <- [R R_bar]).
+ *   SJLT: a new block of alpha nonzeros per row in the new columns; the scale
+ *   becomes 1/sqrt(alpha * blocks) ("adjusting the scaling factor", Sec. 6.2).
+ *   SRHT: the next delta_d distinct sampled columns of the same D H.
+ *   Gaussian: delta_d new N(0,1) columns; all columns scale as 1/sqrt(d_total).
+ *   Block SJLT needs alpha | delta_d; SRHT needs d_total <= nu.
+ * Errors: INVALID_ARG, D_MAX, NOMEM, DEVICE.
+ */
+int sketch_increment(sk_handle h, int32_t delta_d, void* stream);
+
+/*
+ * sketch_apply -- S = A R and/or S' = A^T R for the current R (Sec. 6.3).
+ *   A      explicit (generator == 0) or kernel generator; rows x cols with
+ *          cols == n for S and rows == n for S'.
+ *   which  SK_S, SK_ST or SK_BOTH.
+ *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 (F32, SRHT/Gaussian).
+ *   S      device, rows x d_total (ldS >= d_total) of A's dtype; used if which & SK_S.
+ *   St     device, cols x d_total (ldSt >= d_total);             used if which & SK_ST.
+ * Asynchronous.  Errors: INVALID_ARG, ALIGN, DTYPE, UNSUPPORTED, DEVICE.
+ */
+int sketch_apply(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec,
+                 void* S, int64_t ldS, void* St, int64_t ldSt, void* stream);
+
+/*
+ * sketch_apply_increment -- after sketch_increment, bring S (S') from the
+ * operator before the last increment to the grown one without recomputing
+ * the old columns: the d_old existing columns are rescaled to the new scale
+ * and only the delta_d new columns A R_bar are computed (Algorithm 1,
+ * S <- [S A R_bar]).  S must hold the sketch of the previous operator (same
+ * A); call it once per sketch buffer and increment.
+ * Errors: as sketch_apply, plus STATE when no increment has been made.
+ */
+int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec,
+                           void* S, int64_t ldS, void* St, int64_t ldSt, void* stream);
+
+/*
+ * adaptive_norm_test -- the Frobenius stopping test (Eq. stopping_criteria-1)
+ * on the global sketch held in S (rows x d_total, device, dtype, row-major):
+ *   S~ = the last delta_d columns of S (Algorithm 1's "last Delta-d columns"),
+ *   S^ = (I - Q Q^T)^2 S~ with Q an orthonormal basis of the first
+ *        d_total - delta_d columns (two block Gram-Schmidt passes, the remark
+ *        after the equation), and
+ *   stop = ||S^||_F < eps_abs  or  ||S^||_F < eps_rel ||S~||_F.
+ *   slot   0 or 1: which basis Q the handle keeps (use 0 for S, 1 for S').
+ * Q is kept in the handle and only the columns not yet in it are
+ * orthonormalised (block Gram-Schmidt twice + Cholesky QR twice, 64 columns at
+ * a time), so successive calls cost one projection each; Q is rebuilt from
+ * scratch when the split point moves backwards or `rows` changes.  Norms and
+ * Gram matrices accumulate in FP64.  Synchronizes `stream`; writes *stop and,
+ * if not NULL, *norm_hat = ||S^||_F and *norm_tilde = ||S~||_F (host).
+ * Errors: INVALID_ARG, STATE (delta_d < 1 or >= d_total), ALIGN, DEVICE.
+ */
+int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, int64_t ldS,
+                       int32_t dtype, int32_t delta_d, double eps_rel, double eps_abs,
+                       int32_t* stop, double* norm_hat, double* norm_tilde, void* stream);
+
+/*
+ * kernel_matrix -- write the explicit matrix of a generator descriptor:
+ * A_ij = exp(-||x_i - y_j||^2 / (2 h^2)) + shift * [i == j]  (device, row-major,
+ * ld >= cols, dtype of the descriptor).  Asynchronous.
+ */
+int kernel_matrix(const sk_matrix* gen, void* A, int64_t ld, void* stream);
+
+/* sketch_dims -- shape of the current operator (host outputs; any may be NULL). */
+int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha,
+                int32_t* blocks);
+
+/*
+ * sketch_export -- host copies of the operator for checking (synchronizes):
+ *   cols, signs  SJLT: n x (alpha*blocks) int32 global column / int8 +-1, block
+ *                by block, each block's entries in chunk order (block) or
+ *                ascending column order (graph); the Sec. 6.1 structure.
+ *   diag, mu     SRHT: n int8 signs d_i and d_total int32 sampled columns.
+ *   R, R_dtype   dense R (n x d_total, row-major, host) of SK_F32/SK_F64, the
+ *                values the apply kernels use (scale included).
+ * Pointers that do not apply to the kind, or are NULL, are skipped.
+ */
+int sketch_export(sk_handle h, int32_t* cols, int8_t* signs, int8_t* diag, int32_t* mu,
+                  void* R, int32_t R_dtype);
+
+/* sketch_device_status -- synchronize `stream` and report (and clear) the
+ * handle's device-side error flag: SK_OK, SK_ERR_TIMEOUT or SK_ERR_DEVICE. */
+int sketch_device_status(sk_handle h, void* stream);
+
+/* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */
+void sketch_destroy(sk_handle h);
+
+/* sketch_strerror -- static text for a status code. */
+const char* sketch_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JLSKETCH_H */

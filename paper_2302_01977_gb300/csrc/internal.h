@@ -1,0 +1,135 @@
+// internal.h -- host-side declarations shared by the libjlsketch translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/jlsketch.h"
+
+namespace jls {
+
+// Tile sizes (rows of R per tile) of the tiled compressed-column structure,
+// per element size: the S and S' SJLT kernels stage TILE x 32 elements of A.
+constexpr int SJLT_TILE_F32 = 512;
+constexpr int SJLT_TILE_F64 = 256;
+constexpr int SJLT_MAX_ALPHA = 32;
+constexpr int MAX_D = 8192;
+
+// Tiled CCS of R (Sec. 6.1's compressed column storage, cut into tiles of
+// `tile` rows): for tile t, entries[t*e_stride + p] = row_in_tile | sign<<15
+// sorted by column (rows ascending inside a column), and
+// offs[t*o_stride + c] = first entry of column c (offs[.. + d_total] = count).
+struct TiledCcs {
+  int tile = 0;
+  int built_d = -1;           // d_total it was built for
+  int ntiles = 0;
+  int64_t e_stride = 0;       // uint16 entries per tile (multiple of 8)
+  int64_t o_stride = 0;       // uint32 offsets per tile (multiple of 4)
+  uint16_t* ents = nullptr;
+  uint32_t* offs = nullptr;
+  size_t ents_cap = 0, offs_cap = 0;  // bytes
+};
+
+struct Basis {                // orthonormal basis Q of earlier sketch columns
+  void* Q = nullptr;          // rows x d_max, row-major (ld = d_max), dtype
+  int dtype = 0;
+  int64_t rows = 0;
+  int cols = 0;               // columns of Q so far
+  int covered = 0;            // sketch columns already absorbed into Q
+};
+
+}  // namespace jls
+
+struct sk_op {
+  int kind = 0;
+  int64_t n = 0;
+  int alpha = 1;
+  int d_total = 0;
+  int d_max = 0;
+  int64_t nu = 1;
+  uint64_t seed = 0;
+  int device = 0;
+  std::vector<int> blocks;     // block widths (first = initial d, then increments)
+  int pending_old_d = -1;      // d_total before the last increment not yet applied
+  int* d_err = nullptr;        // device error flag
+
+  // SJLT: packed entries [block][n][alpha] = column | (sign < 0) << 31
+  int32_t* sjlt_ents = nullptr;
+  int sjlt_blocks_cap = 0;
+  jls::TiledCcs ccs[2];        // [0] tile for F32, [1] tile for F64
+
+  // SRHT: D signs, sampled columns, sampling state (next counter)
+  int8_t* srht_diag = nullptr;
+  int32_t* srht_mu = nullptr;
+  unsigned long long* srht_state = nullptr;
+
+  // Gaussian: unscaled z, transposed (column c of R contiguous over rows)
+  float* z32 = nullptr;
+  double* z64 = nullptr;
+  uint16_t* zhi = nullptr;     // bf16 bits
+  uint16_t* zlo = nullptr;
+  int z32_cols = 0, z64_cols = 0, zbf_cols = 0;
+
+  // SRHT +-1 plane for the tensor-core path (bf16 bits, d_max x n)
+  uint16_t* srht_pm1 = nullptr;
+  int pm1_cols = 0;
+
+  jls::Basis basis[2];
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+namespace jls {
+
+// --- operators.cu ---
+int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s);
+int build_ccs(sk_op* h, int which_tile, cudaStream_t s);
+int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s);
+int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s);  // plane: 0 f32, 1 f64, 2 bf16x2
+int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s);
+int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s);
+
+// --- sjlt_apply.cu ---
+// S = A R (rows kernel) and S' = A^T R (cols kernel) for output columns
+// [c_lo, c_hi) of R, writing scale * (signed sums).
+int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
+               void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+
+// --- dense_simt.cu ---  SRHT / Gaussian on CUDA cores (FP32 or FP64)
+int dense_apply_simt(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
+                     void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+
+// --- gemm_tc.cu ---  SRHT / Gaussian on tcgen05 tensor cores, bf16 hi+lo split
+int dense_apply_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
+                   void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+
+// --- kernel_matrix.cu ---
+int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s);
+
+// --- adaptive.cu ---
+int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, double factor,
+                  cudaStream_t s);
+int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
+              int c_end, double eps_rel, double eps_abs, int* stop, double* nh, double* nt,
+              cudaStream_t s);
+
+// --- jlsketch.cu helpers ---
+int cuda_status(cudaError_t e);
+size_t elem_size(int dtype);
+
+}  // namespace jls
+
+#define JLS_CHECK_CUDA(expr)                                   \
+  do {                                                         \
+    cudaError_t e__ = (expr);                                  \
+    if (e__ != cudaSuccess) return ::jls::cuda_status(e__);    \
+  } while (0)
+
+#define JLS_CHECK(expr)                \
+  do {                                 \
+    int r__ = (expr);                  \
+    if (r__ != SK_OK) return r__;      \
+  } while (0)

@@ -1,0 +1,262 @@
+// jlsketch.cu -- the C ABI of libjlsketch: argument checks, handle state and
+// dispatch to the kernels.  Every function returns a status and never throws.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace jls {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SK_OK;
+  cudaGetLastError();  // clear non-sticky errors
+  return e == cudaErrorMemoryAllocation ? SK_ERR_NOMEM : SK_ERR_DEVICE;
+}
+
+size_t elem_size(int dtype) { return dtype == SK_F64 ? 8 : 4; }
+
+double op_scale(const sk_op* h) {
+  if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
+    return 1.0 / std::sqrt((double)h->alpha * (double)h->blocks.size());
+  return 1.0 / std::sqrt((double)h->d_total);
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static int check_device() {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    return SK_ERR_DEVICE;
+  }
+  return SK_OK;
+}
+
+// Validate an explicit-matrix apply request against the operator.
+static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, const void* S, int64_t ldS,
+                       const void* St, int64_t ldSt) {
+  if (!A || which < SK_S || which > SK_BOTH) return SK_ERR_INVALID_ARG;
+  if (A->dtype != SK_F32 && A->dtype != SK_F64) return SK_ERR_DTYPE;
+  if (A->generator) return SK_ERR_UNSUPPORTED;
+  if (A->rows < 1 || A->cols < 1 || !A->A || A->ld < A->cols) return SK_ERR_INVALID_ARG;
+  if (!aligned16(A->A) || (A->ld * (int64_t)elem_size(A->dtype)) % 16 != 0) return SK_ERR_ALIGN;
+  if ((which & SK_S) && (A->cols != h->n || !S || ldS < h->d_total)) return SK_ERR_INVALID_ARG;
+  if ((which & SK_ST) && (A->rows != h->n || !St || ldSt < h->d_total)) return SK_ERR_INVALID_ARG;
+  if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2) return SK_ERR_DTYPE;
+  if (prec == SK_PREC_BF16X2 && (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
+    return SK_ERR_DTYPE;
+  return SK_OK;
+}
+
+static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, void* S, int64_t ldS,
+                    void* St, int64_t ldSt, cudaStream_t s) {
+  const double scale = op_scale(h);
+  if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
+    return sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+  if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+  return dense_apply_simt(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+}
+
+static void free_handle(sk_op* h) {
+  if (!h) return;
+  void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
+                  h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
+                  h->basis[0].Q, h->basis[1].Q, h->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+}  // namespace jls
+
+using namespace jls;
+
+extern "C" {
+
+const char* sketch_strerror(int status) {
+  switch (status) {
+    case SK_OK: return "ok";
+    case SK_ERR_INVALID_ARG: return "invalid argument";
+    case SK_ERR_ALIGN: return "pointer or leading dimension not 16-byte aligned";
+    case SK_ERR_DTYPE: return "unsupported element type or precision";
+    case SK_ERR_NOMEM: return "device allocation failed";
+    case SK_ERR_D_MAX: return "increment exceeds d_max";
+    case SK_ERR_STATE: return "call out of order";
+    case SK_ERR_TIMEOUT: return "device-side wait timed out";
+    case SK_ERR_DEVICE: return "CUDA or device-side error";
+    case SK_ERR_UNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t alpha, uint64_t seed,
+                  int32_t d_max, void* stream) {
+  if (!out) return SK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (kind < SK_SJLT_GRAPH || kind > SK_GAUSS) return SK_ERR_INVALID_ARG;
+  if (n < 1 || n >= (1ll << 31) || d < 1 || d_max < d || d_max > MAX_D) return SK_ERR_INVALID_ARG;
+  const bool sjlt = kind == SK_SJLT_BLOCK || kind == SK_SJLT_GRAPH;
+  if (sjlt && (alpha < 1 || alpha > d || alpha > SJLT_MAX_ALPHA)) return SK_ERR_INVALID_ARG;
+  if (kind == SK_SJLT_BLOCK && d % alpha) return SK_ERR_INVALID_ARG;
+  int64_t nu = 1;
+  while (nu < n) nu <<= 1;
+  if (kind == SK_SRHT && d_max > nu) return SK_ERR_INVALID_ARG;
+  JLS_CHECK(check_device());
+  sk_op* h = new (std::nothrow) sk_op();
+  if (!h) return SK_ERR_NOMEM;
+  h->kind = kind;
+  h->n = n;
+  h->alpha = sjlt ? alpha : 1;
+  h->d_total = d;
+  h->d_max = d_max;
+  h->nu = nu;
+  h->seed = seed;
+  h->blocks.push_back(d);
+  cudaGetDevice(&h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = cuda_status(cudaMalloc(&h->d_err, sizeof(int)));
+  if (rc == SK_OK) rc = cuda_status(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  if (rc == SK_OK && sjlt) rc = gen_sjlt_block(h, 0, 0, d, s);
+  if (rc == SK_OK && kind == SK_SRHT) rc = gen_srht(h, 0, d, s);
+  if (rc != SK_OK) {
+    free_handle(h);
+    return rc;
+  }
+  *out = h;
+  return SK_OK;
+}
+
+int sketch_increment(sk_handle h, int32_t delta_d, void* stream) {
+  if (!h || delta_d < 1) return SK_ERR_INVALID_ARG;
+  if (h->d_total + (int64_t)delta_d > h->d_max) return SK_ERR_D_MAX;
+  const bool sjlt = h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH;
+  if (h->kind == SK_SJLT_BLOCK && delta_d % h->alpha) return SK_ERR_INVALID_ARG;
+  if (sjlt && delta_d < h->alpha) return SK_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d_old = h->d_total;
+  if (sjlt) JLS_CHECK(gen_sjlt_block(h, (int)h->blocks.size(), d_old, delta_d, s));
+  if (h->kind == SK_SRHT) JLS_CHECK(gen_srht(h, d_old, d_old + delta_d, s));
+  h->blocks.push_back(delta_d);
+  h->d_total = d_old + delta_d;
+  h->pending_old_d = d_old;
+  return SK_OK;
+}
+
+int sketch_apply(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec, void* S, int64_t ldS, void* St,
+                 int64_t ldSt, void* stream) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  JLS_CHECK(check_apply(h, A, which, prec, S, ldS, St, ldSt));
+  return dispatch(h, A, which, prec, 0, h->d_total, S, ldS, St, ldSt, static_cast<cudaStream_t>(stream));
+}
+
+int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec, void* S, int64_t ldS,
+                           void* St, int64_t ldSt, void* stream) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  if (h->pending_old_d < 0) return SK_ERR_STATE;
+  JLS_CHECK(check_apply(h, A, which, prec, S, ldS, St, ldSt));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d_old = h->pending_old_d;
+  // scale of the operator before the last increment, and now
+  double old_scale;
+  if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
+    old_scale = 1.0 / std::sqrt((double)h->alpha * (double)(h->blocks.size() - 1));
+  else
+    old_scale = 1.0 / std::sqrt((double)d_old);
+  const double factor = op_scale(h) / old_scale;
+  if (which & SK_S) JLS_CHECK(scale_columns(S, A->dtype, A->rows, ldS, 0, d_old, factor, s));
+  if (which & SK_ST) JLS_CHECK(scale_columns(St, A->dtype, A->cols, ldSt, 0, d_old, factor, s));
+  return dispatch(h, A, which, prec, d_old, h->d_total, S, ldS, St, ldSt, s);
+}
+
+int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, int64_t ldS, int32_t dtype,
+                       int32_t delta_d, double eps_rel, double eps_abs, int32_t* stop, double* norm_hat,
+                       double* norm_tilde, void* stream) {
+  if (!h || !S || !stop || slot < 0 || slot > 1 || rows < 1 || ldS < h->d_total) return SK_ERR_INVALID_ARG;
+  if (dtype != SK_F32 && dtype != SK_F64) return SK_ERR_DTYPE;
+  if (delta_d < 1 || delta_d >= h->d_total) return SK_ERR_STATE;
+  if (!aligned16(S) || (ldS * (int64_t)elem_size(dtype)) % 16) return SK_ERR_ALIGN;
+  int st = 0;
+  double nh = 0, nt = 0;
+  JLS_CHECK(norm_test(h, slot, S, rows, ldS, dtype, h->d_total - delta_d, h->d_total, eps_rel, eps_abs, &st, &nh,
+                      &nt, static_cast<cudaStream_t>(stream)));
+  *stop = st;
+  if (norm_hat) *norm_hat = nh;
+  if (norm_tilde) *norm_tilde = nt;
+  return SK_OK;
+}
+
+int kernel_matrix(const sk_matrix* gen, void* A, int64_t ld, void* stream) {
+  if (!gen || !A || !gen->X || !gen->Y || gen->rows < 1 || gen->cols < 1 || ld < gen->cols || !(gen->h > 0))
+    return SK_ERR_INVALID_ARG;
+  if (gen->dtype != SK_F32 && gen->dtype != SK_F64) return SK_ERR_DTYPE;
+  JLS_CHECK(check_device());
+  return launch_kernel_matrix(gen, A, ld, static_cast<cudaStream_t>(stream));
+}
+
+int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha, int32_t* blocks) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  if (kind) *kind = h->kind;
+  if (n) *n = h->n;
+  if (d_total) *d_total = h->d_total;
+  if (alpha) *alpha = h->alpha;
+  if (blocks) *blocks = (int32_t)h->blocks.size();
+  return SK_OK;
+}
+
+int sketch_export(sk_handle h, int32_t* cols, int8_t* signs, int8_t* diag, int32_t* mu, void* R,
+                  int32_t R_dtype) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  JLS_CHECK_CUDA(cudaDeviceSynchronize());
+  const bool sjlt = h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH;
+  const int B = (int)h->blocks.size();
+  if (sjlt && (cols || signs)) {
+    std::vector<int32_t> e((size_t)B * h->n * h->alpha);
+    JLS_CHECK_CUDA(cudaMemcpy(e.data(), h->sjlt_ents, e.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int w = h->alpha * B;
+    for (int b = 0; b < B; ++b)
+      for (int64_t i = 0; i < h->n; ++i)
+        for (int k = 0; k < h->alpha; ++k) {
+          const int32_t v = e[((size_t)b * h->n + i) * h->alpha + k];
+          const size_t o = (size_t)i * w + (size_t)b * h->alpha + k;
+          if (cols) cols[o] = v & 0x7fffffff;
+          if (signs) signs[o] = v < 0 ? -1 : 1;
+        }
+  }
+  if (h->kind == SK_SRHT) {
+    if (diag) JLS_CHECK_CUDA(cudaMemcpy(diag, h->srht_diag, h->n, cudaMemcpyDeviceToHost));
+    if (mu) JLS_CHECK_CUDA(cudaMemcpy(mu, h->srht_mu, sizeof(int32_t) * h->d_total, cudaMemcpyDeviceToHost));
+  }
+  if (R) {
+    if (R_dtype != SK_F32 && R_dtype != SK_F64) return SK_ERR_DTYPE;
+    const size_t bytes = (size_t)h->n * h->d_total * elem_size(R_dtype);
+    void* dR = nullptr;
+    JLS_CHECK_CUDA(cudaMalloc(&dR, bytes));
+    int rc = export_dense_R(h, dR, R_dtype, 0);
+    if (rc == SK_OK) rc = cuda_status(cudaMemcpy(R, dR, bytes, cudaMemcpyDeviceToHost));
+    cudaFree(dR);
+    JLS_CHECK(rc);
+  }
+  return SK_OK;
+}
+
+int sketch_device_status(sk_handle h, void* stream) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  JLS_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int flag = 0;
+  JLS_CHECK_CUDA(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) JLS_CHECK_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+  if (flag & ERRF_TIMEOUT) return SK_ERR_TIMEOUT;
+  if (flag) return SK_ERR_DEVICE;
+  return SK_OK;
+}
+
+void sketch_destroy(sk_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_handle(h);
+}
+
+}  // extern "C"

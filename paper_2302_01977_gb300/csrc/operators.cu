@@ -1,0 +1,385 @@
+// operators.cu -- drawing the JL operators on the device (Sec. 3.2, Sec. 6.1-6.2).
+//
+// Stream layout (identical to the host oracle's, which is written independently):
+//  * SJLT row i, block b: draws t = 0, 1, ... at Philox counter (i, t, 0, 0),
+//    key (seed, TAG_SJLT | b); slot k takes the next accepted draw,
+//    position = lemire(word0, span) (span = width/alpha for the block
+//    construction, width for the graph construction, Sec. 3.2.3); a draw is
+//    skipped on Lemire rejection or, in the graph construction, on a repeated
+//    column; sign = top bit of word1 (set means -1).
+//  * SRHT: d_i = top bit of word0 at counter (i, 0, 0, 0), key (seed, TAG_SRHT_D);
+//    sampled columns = first distinct lemire(word0, nu) over counters
+//    (t, 0, 0, 0), key (seed, TAG_SRHT_MU) (Sec. 3.2.2, without replacement).
+//  * Gaussian column c: counter (i, c >> 1, 0, 0), key (seed, TAG_GAUSS),
+//    Box-Muller on u1 in (0,1], u2 in [0,1): cos half for even c, sin for odd.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace jls {
+
+// ---------------------------------------------------------------------------
+// SJLT: one thread per row, alpha slots, packed entry = col | (neg << 31).
+__global__ void sjlt_draw_kernel(int64_t n, int alpha, int width, int block_construction,
+                                 uint64_t seed, int block, int col_off, int32_t* __restrict__ out,
+                                 int* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t key1 = TAG_SJLT | (uint64_t)block;
+  const uint64_t span = block_construction ? (uint64_t)(width / alpha) : (uint64_t)width;
+  int cols[SJLT_MAX_ALPHA];
+  int neg[SJLT_MAX_ALPHA];
+  uint64_t t = 0;
+  for (int k = 0; k < alpha; ++k) {
+    int tries = 0;
+    while (true) {
+      if (++tries > (1 << 20)) {  // practically unreachable; never spin forever
+        set_err(err, ERRF_RNG);
+        return;
+      }
+      const u64x4 w = philox4x64_10((uint64_t)i, t, 0, 0, seed, key1);
+      ++t;
+      uint64_t v;
+      if (!lemire(w.x0, span, &v)) continue;
+      int c = block_construction ? (int)(k * span + v) : (int)v;
+      bool dup = false;
+      if (!block_construction)
+        for (int q = 0; q < k; ++q) dup |= (cols[q] == c);
+      if (dup) continue;
+      cols[k] = c;
+      neg[k] = (int)(w.x1 >> 63);
+      break;
+    }
+  }
+  if (!block_construction) {  // ascending columns, signs travel with them
+    for (int a = 1; a < alpha; ++a) {
+      const int c = cols[a], s = neg[a];
+      int b = a - 1;
+      while (b >= 0 && cols[b] > c) {
+        cols[b + 1] = cols[b];
+        neg[b + 1] = neg[b];
+        --b;
+      }
+      cols[b + 1] = c;
+      neg[b + 1] = s;
+    }
+  }
+  int32_t* o = out + i * alpha;
+  for (int k = 0; k < alpha; ++k)
+    o[k] = (int32_t)((uint32_t)(cols[k] + col_off) | ((uint32_t)neg[k] << 31));
+}
+
+int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s) {
+  if (block >= h->sjlt_blocks_cap) {
+    const int new_cap = std::max(4, 2 * h->sjlt_blocks_cap);
+    int32_t* p = nullptr;
+    const size_t per = (size_t)h->n * h->alpha * sizeof(int32_t);
+    JLS_CHECK_CUDA(cudaMalloc(&p, per * new_cap));
+    if (h->sjlt_ents) {
+      JLS_CHECK_CUDA(cudaMemcpyAsync(p, h->sjlt_ents, per * h->sjlt_blocks_cap,
+                                     cudaMemcpyDeviceToDevice, s));
+      JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+      cudaFree(h->sjlt_ents);
+    }
+    h->sjlt_ents = p;
+    h->sjlt_blocks_cap = new_cap;
+  }
+  const int threads = 256;
+  const int64_t grid = (h->n + threads - 1) / threads;
+  sjlt_draw_kernel<<<(unsigned)grid, threads, 0, s>>>(
+      h->n, h->alpha, width, h->kind == SK_SJLT_BLOCK, h->seed, block, col_off,
+      h->sjlt_ents + (size_t)block * h->n * h->alpha, h->d_err);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tiled CCS build: one CTA per tile of `tile` rows of R.  Each thread owns
+// columns c = tid, tid + blockDim, ...; blocks occupy disjoint column ranges,
+// so column c is only looked up in its own block's alpha slots.  Pass 1
+// counts, a CTA scan turns counts into offsets, pass 2 writes the entries of
+// each column in ascending row order (deterministic).
+__global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha,
+                                 const int* __restrict__ blk_of_col, const int* __restrict__ blk_off,
+                                 int d_total, int tile, int64_t e_stride, int64_t o_stride,
+                                 uint16_t* __restrict__ out_e, uint32_t* __restrict__ out_o) {
+  extern __shared__ uint32_t sh_cnt[];  // d_total + 1
+  const int t = blockIdx.x;
+  const int64_t r0 = (int64_t)t * tile;
+  const int rows = (int)min64(tile, n - r0);
+  for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
+    const int b = blk_of_col[c];
+    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    uint32_t cnt = 0;
+    for (int r = 0; r < rows; ++r)
+      for (int k = 0; k < alpha; ++k)
+        cnt += ((base[(int64_t)r * alpha + k] & 0x7fffffff) == c);
+    sh_cnt[c] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // small serial scan (d_total <= 8192)
+    uint32_t acc = 0;
+    for (int c = 0; c < d_total; ++c) {
+      const uint32_t v = sh_cnt[c];
+      sh_cnt[c] = acc;
+      acc += v;
+    }
+    sh_cnt[d_total] = acc;
+  }
+  __syncthreads();
+  uint32_t* oo = out_o + (int64_t)t * o_stride;
+  uint16_t* oe = out_e + (int64_t)t * e_stride;
+  for (int c = threadIdx.x; c <= d_total; c += blockDim.x) oo[c] = sh_cnt[c];
+  for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
+    const int b = blk_of_col[c];
+    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    uint32_t pos = sh_cnt[c];
+    for (int r = 0; r < rows; ++r)
+      for (int k = 0; k < alpha; ++k) {
+        const int32_t e = base[(int64_t)r * alpha + k];
+        if ((e & 0x7fffffff) == c) oe[pos++] = (uint16_t)(r | ((e < 0) ? 0x8000 : 0));
+      }
+  }
+  (void)blk_off;
+}
+
+int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
+  TiledCcs& C = h->ccs[which_tile];
+  const int tile = which_tile == 0 ? SJLT_TILE_F32 : SJLT_TILE_F64;
+  if (C.built_d == h->d_total && C.tile == tile) return SK_OK;
+  const int B = (int)h->blocks.size();
+  C.tile = tile;
+  C.ntiles = (int)((h->n + tile - 1) / tile);
+  C.e_stride = ((int64_t)h->alpha * B * tile + 7) / 8 * 8;
+  C.o_stride = ((int64_t)h->d_total + 1 + 3) / 4 * 4;
+  const size_t eb = (size_t)C.e_stride * C.ntiles * sizeof(uint16_t);
+  const size_t ob = (size_t)C.o_stride * C.ntiles * sizeof(uint32_t);
+  if (eb > C.ents_cap) {
+    if (C.ents) cudaFree(C.ents);
+    C.ents = nullptr;
+    JLS_CHECK_CUDA(cudaMalloc(&C.ents, eb));
+    C.ents_cap = eb;
+  }
+  if (ob > C.offs_cap) {
+    if (C.offs) cudaFree(C.offs);
+    C.offs = nullptr;
+    JLS_CHECK_CUDA(cudaMalloc(&C.offs, ob));
+    C.offs_cap = ob;
+  }
+  // column -> block map (host-built, tiny)
+  std::vector<int> boc(h->d_total), boff(B);
+  int off = 0;
+  for (int b = 0; b < B; ++b) {
+    boff[b] = off;
+    for (int c = 0; c < h->blocks[b]; ++c) boc[off + c] = b;
+    off += h->blocks[b];
+  }
+  int* d_boc = nullptr;
+  int* d_boff = nullptr;
+  JLS_CHECK_CUDA(cudaMalloc(&d_boc, sizeof(int) * (h->d_total + B)));
+  d_boff = d_boc + h->d_total;
+  JLS_CHECK_CUDA(cudaMemcpyAsync(d_boc, boc.data(), sizeof(int) * h->d_total, cudaMemcpyHostToDevice, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(d_boff, boff.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  const size_t shm = sizeof(uint32_t) * (h->d_total + 1);
+  if (shm > 48 * 1024)
+    JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)shm));
+  ccs_build_kernel<<<C.ntiles, 512, shm, s>>>(h->sjlt_ents, h->n, h->alpha, d_boc, d_boff,
+                                              h->d_total, tile, C.e_stride, C.o_stride, C.ents,
+                                              C.offs);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));  // the pageable host vectors above die here
+  cudaFree(d_boc);
+  C.built_d = h->d_total;
+  return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SRHT
+__global__ void srht_diag_kernel(int64_t n, uint64_t seed, int8_t* __restrict__ diag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u64x4 w = philox4x64_10((uint64_t)i, 0, 0, 0, seed, TAG_SRHT_D);
+  diag[i] = (w.x0 >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
+// One thread: continue the sequence of candidate columns from the saved
+// counter until d_new distinct columns exist.  Membership uses an
+// open-addressing table in shared memory (capacity `cap`, a power of two).
+__global__ void srht_mu_kernel(int64_t nu, uint64_t seed, int d_old, int d_new, int cap,
+                               int32_t* __restrict__ mu, unsigned long long* __restrict__ state,
+                               int* err) {
+  extern __shared__ int32_t table[];
+  if (threadIdx.x != 0) return;
+  for (int q = 0; q < cap; ++q) table[q] = -1;
+  auto insert = [&](int32_t v) -> bool {  // true if newly inserted
+    uint32_t hsh = ((uint32_t)v * 2654435761u) & (cap - 1);
+    while (true) {
+      if (table[hsh] == v) return false;
+      if (table[hsh] < 0) {
+        table[hsh] = v;
+        return true;
+      }
+      hsh = (hsh + 1) & (cap - 1);
+    }
+  };
+  for (int q = 0; q < d_old; ++q) insert(mu[q]);
+  unsigned long long t = state[0];
+  int have = d_old;
+  uint64_t guard = 0;
+  while (have < d_new) {
+    if (++guard > (1ull << 32)) {
+      set_err(err, ERRF_RNG);
+      return;
+    }
+    const u64x4 w = philox4x64_10((uint64_t)t, 0, 0, 0, seed, TAG_SRHT_MU);
+    ++t;
+    uint64_t v;
+    if (!lemire(w.x0, (uint64_t)nu, &v)) continue;
+    if (insert((int32_t)v)) mu[have++] = (int32_t)v;
+  }
+  state[0] = t;
+}
+
+int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s) {
+  if (!h->srht_diag) {
+    JLS_CHECK_CUDA(cudaMalloc(&h->srht_diag, h->n));
+    JLS_CHECK_CUDA(cudaMalloc(&h->srht_mu, sizeof(int32_t) * h->d_max));
+    JLS_CHECK_CUDA(cudaMalloc(&h->srht_state, sizeof(unsigned long long)));
+    JLS_CHECK_CUDA(cudaMemsetAsync(h->srht_state, 0, sizeof(unsigned long long), s));
+    const int threads = 256;
+    srht_diag_kernel<<<(unsigned)((h->n + threads - 1) / threads), threads, 0, s>>>(h->n, h->seed,
+                                                                                    h->srht_diag);
+    JLS_CHECK_CUDA(cudaGetLastError());
+  }
+  int cap = 1;
+  while (cap < 2 * d_new) cap <<= 1;
+  const size_t shm = sizeof(int32_t) * cap;
+  if (shm > 48 * 1024)
+    JLS_CHECK_CUDA(
+        cudaFuncSetAttribute(srht_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  srht_mu_kernel<<<1, 32, shm, s>>>(h->nu, h->seed, d_old, d_new, cap, h->srht_mu, h->srht_state,
+                                    h->d_err);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian z (unscaled N(0,1)), stored transposed: plane[c * n + i].
+__device__ __forceinline__ double gauss_z(int64_t i, int c, uint64_t seed) {
+  const u64x4 w = philox4x64_10((uint64_t)i, (uint64_t)(c >> 1), 0, 0, seed, TAG_GAUSS);
+  const double u1 = u53_open0(w.x0);
+  const double u2 = u53(w.x1);
+  const double rad = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return (c & 1) ? rad * sn : rad * cs;
+}
+
+__global__ void gauss_gen_kernel(int64_t n, int c0, int c1, uint64_t seed, float* __restrict__ z32,
+                                 double* __restrict__ z64, __nv_bfloat16* __restrict__ zhi,
+                                 __nv_bfloat16* __restrict__ zlo) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int c = c0 + blockIdx.y;
+  if (i >= n || c >= c1) return;
+  const double z = gauss_z(i, c, seed);
+  const int64_t o = (int64_t)c * n + i;
+  if (z32) z32[o] = (float)z;
+  if (z64) z64[o] = z;
+  if (zhi) {
+    const float zf = (float)z;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(zf);
+    zhi[o] = hi;
+    zlo[o] = __float2bfloat16_rn(zf - __bfloat162float(hi));
+  }
+}
+
+int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s) {
+  const size_t cells = (size_t)h->d_max * h->n;
+  int* have = plane == 0 ? &h->z32_cols : plane == 1 ? &h->z64_cols : &h->zbf_cols;
+  if (plane == 0 && !h->z32) JLS_CHECK_CUDA(cudaMalloc(&h->z32, cells * sizeof(float)));
+  if (plane == 1 && !h->z64) JLS_CHECK_CUDA(cudaMalloc(&h->z64, cells * sizeof(double)));
+  if (plane == 2 && !h->zhi) {
+    JLS_CHECK_CUDA(cudaMalloc(&h->zhi, cells * sizeof(uint16_t)));
+    JLS_CHECK_CUDA(cudaMalloc(&h->zlo, cells * sizeof(uint16_t)));
+  }
+  if (*have >= c_end) return SK_OK;
+  const int c0 = *have;
+  dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)(c_end - c0));
+  gauss_gen_kernel<<<grid, 256, 0, s>>>(h->n, c0, c_end, h->seed, plane == 0 ? h->z32 : nullptr,
+                                        plane == 1 ? h->z64 : nullptr,
+                                        plane == 2 ? reinterpret_cast<__nv_bfloat16*>(h->zhi) : nullptr,
+                                        plane == 2 ? reinterpret_cast<__nv_bfloat16*>(h->zlo) : nullptr);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  *have = c_end;
+  return SK_OK;
+}
+
+// SRHT +-1 plane (bf16 bits, exact), transposed: pm1[c * n + i] = d_i (-1)^popc(i & mu_c).
+__global__ void srht_pm1_kernel(int64_t n, int c0, int c1, const int8_t* __restrict__ diag,
+                                const int32_t* __restrict__ mu, uint16_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int c = c0 + blockIdx.y;
+  if (i >= n || c >= c1) return;
+  const int neg = (__popcll((unsigned long long)i & (unsigned long long)(uint32_t)mu[c]) & 1) ^ (diag[i] < 0);
+  out[(int64_t)c * n + i] = neg ? (uint16_t)0xBF80 : (uint16_t)0x3F80;  // bf16 -1 / +1
+}
+
+int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s) {
+  if (!h->srht_pm1) JLS_CHECK_CUDA(cudaMalloc(&h->srht_pm1, (size_t)h->d_max * h->n * sizeof(uint16_t)));
+  if (h->pm1_cols >= c_end) return SK_OK;
+  dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)(c_end - h->pm1_cols));
+  srht_pm1_kernel<<<grid, 256, 0, s>>>(h->n, h->pm1_cols, c_end, h->srht_diag, h->srht_mu, h->srht_pm1);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  h->pm1_cols = c_end;
+  return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dense R for export (scale included), row-major n x d_total.
+template <typename T>
+__global__ void dense_R_kernel(int kind, int64_t n, int d_total, int alpha, int nblocks, double scale,
+                               const int32_t* __restrict__ ents, const int8_t* __restrict__ diag,
+                               const int32_t* __restrict__ mu, uint64_t seed, T* __restrict__ R) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T* row = R + i * d_total;
+  if (kind == SK_SJLT_BLOCK || kind == SK_SJLT_GRAPH) {
+    for (int c = 0; c < d_total; ++c) row[c] = T(0);
+    for (int b = 0; b < nblocks; ++b)
+      for (int k = 0; k < alpha; ++k) {
+        const int32_t e = ents[((int64_t)b * n + i) * alpha + k];
+        row[e & 0x7fffffff] = (T)((e < 0) ? -scale : scale);
+      }
+  } else if (kind == SK_SRHT) {
+    for (int c = 0; c < d_total; ++c) {
+      const int neg = (__popcll((unsigned long long)i & (unsigned long long)(uint32_t)mu[c]) & 1) ^ (diag[i] < 0);
+      row[c] = (T)(neg ? -scale : scale);
+    }
+  } else {
+    for (int c = 0; c < d_total; ++c) row[c] = (T)(gauss_z(i, c, seed) * scale);
+  }
+}
+
+double op_scale(const sk_op* h);
+
+int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s) {
+  const int threads = 128;
+  const unsigned grid = (unsigned)((h->n + threads - 1) / threads);
+  const double sc = op_scale(h);
+  if (dtype == SK_F64)
+    dense_R_kernel<double><<<grid, threads, 0, s>>>(h->kind, h->n, h->d_total, h->alpha,
+                                                    (int)h->blocks.size(), sc, h->sjlt_ents, h->srht_diag,
+                                                    h->srht_mu, h->seed, (double*)R_dev);
+  else
+    dense_R_kernel<float><<<grid, threads, 0, s>>>(h->kind, h->n, h->d_total, h->alpha,
+                                                   (int)h->blocks.size(), sc, h->sjlt_ents, h->srht_diag,
+                                                   h->srht_mu, h->seed, (float*)R_dev);
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+}  // namespace jls

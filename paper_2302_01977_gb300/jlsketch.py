@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libjlsketch (include/jlsketch.h).
+
+Argument marshalling only: every step of the sketching path runs in the CUDA
+library.  Functions carry the C names; tensors are torch CUDA tensors (row-major
+2-D, unit column stride) whose ``data_ptr()`` is passed through, and streams
+default to torch's current stream.  A non-zero status raises ``JLSketchError``.
+If the shared library has not been built the first call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjlsketch.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "jlsketch.h")
+
+# constants (mirrors include/jlsketch.h; tests check the two agree)
+SK_OK = 0
+SK_ERR_INVALID_ARG = -1
+SK_ERR_ALIGN = -2
+SK_ERR_DTYPE = -3
+SK_ERR_NOMEM = -4
+SK_ERR_D_MAX = -5
+SK_ERR_STATE = -6
+SK_ERR_TIMEOUT = -7
+SK_ERR_DEVICE = -8
+SK_ERR_UNSUPPORTED = -9
+SK_SJLT_GRAPH = 1
+SK_SJLT_BLOCK = 2
+SK_SRHT = 3
+SK_GAUSS = 4
+SK_F64 = 1
+SK_F32 = 2
+SK_PREC_NATIVE = 0
+SK_PREC_BF16X2 = 3
+SK_S = 1
+SK_ST = 2
+SK_BOTH = 3
+
+KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
+
+EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
+           "adaptive_norm_test", "kernel_matrix", "sketch_dims", "sketch_export",
+           "sketch_device_status", "sketch_destroy", "sketch_strerror"]
+
+
+class JLSketchError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {sketch_strerror(status)} (status {status})")
+
+
+class SkMatrix(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("generator", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("ld", ctypes.c_int64),
+                ("X", ctypes.c_void_p), ("Y", ctypes.c_void_p),
+                ("h", ctypes.c_double), ("shift", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libjlsketch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the sketching path has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "sketch_create": (i32, [P(vp), i32, i64, i32, i32, u64, i32, vp]),
+        "sketch_increment": (i32, [vp, i32, vp]),
+        "sketch_apply": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
+        "sketch_apply_increment": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
+        "adaptive_norm_test": (i32, [vp, i32, vp, i64, i64, i32, i32, dbl, dbl, P(i32), P(dbl), P(dbl), vp]),
+        "kernel_matrix": (i32, [P(SkMatrix), vp, i64, vp]),
+        "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
+        "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
+        "sketch_device_status": (i32, [vp, vp]),
+        "sketch_destroy": (None, [vp]),
+        "sketch_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_constants() -> dict:
+    """#define SK_* values parsed from include/jlsketch.h."""
+    out = {}
+    for line in open(HEADER):
+        m = re.match(r"#define\s+(SK_\w+)\s+(-?\d+)", line)
+        if m:
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def sketch_strerror(status: int) -> str:
+    try:
+        return lib().sketch_strerror(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SK_OK:
+        raise JLSketchError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return SK_F32
+    if t.dtype == torch.float64:
+        return SK_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _check_2d(t, name):
+    if t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+        raise ValueError(f"{name} must be a 2-D CUDA tensor with unit column stride")
+
+
+def matrix(A) -> SkMatrix:
+    """Descriptor of an explicit row-major matrix held in a CUDA tensor."""
+    if isinstance(A, SkMatrix):
+        return A
+    _check_2d(A, "A")
+    return SkMatrix(dtype=_dtype_code(A), generator=0, rows=A.shape[0], cols=A.shape[1],
+                    A=A.data_ptr(), ld=A.stride(0), X=None, Y=None, h=0.0, shift=0.0)
+
+
+def generator(X, Y, h: float, shift: float = 0.0) -> SkMatrix:
+    """Descriptor of A_ij = exp(-||x_i - y_j||^2/(2h^2)) + shift [i == j]."""
+    for t, nm in ((X, "X"), (Y, "Y")):
+        if t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor of shape (m, 3)")
+    return SkMatrix(dtype=_dtype_code(X), generator=1, rows=X.shape[0], cols=Y.shape[0], A=None, ld=0,
+                    X=X.data_ptr(), Y=Y.data_ptr(), h=float(h), shift=float(shift))
+
+
+def sketch_create(kind, n: int, d: int, alpha: int = 1, seed: int = 0, d_max: int | None = None,
+                  stream=None) -> ctypes.c_void_p:
+    k = KIND_NAMES.get(kind, kind) if isinstance(kind, str) else int(kind)
+    h = ctypes.c_void_p()
+    rc = lib().sketch_create(ctypes.byref(h), k, int(n), int(d), int(alpha), int(seed) & (2**64 - 1),
+                             int(d if d_max is None else d_max), _stream(stream))
+    _check(rc, "sketch_create")
+    return h
+
+
+def sketch_increment(h, delta_d: int, stream=None) -> None:
+    _check(lib().sketch_increment(h, int(delta_d), _stream(stream)), "sketch_increment")
+
+
+def _apply(fn, name, h, A, which, prec, S, St, stream):
+    desc = matrix(A)
+    sp, lds, stp, ldst = None, 0, None, 0
+    if S is not None:
+        _check_2d(S, "S")
+        sp, lds = S.data_ptr(), S.stride(0)
+    if St is not None:
+        _check_2d(St, "St")
+        stp, ldst = St.data_ptr(), St.stride(0)
+    _check(fn(h, ctypes.byref(desc), int(which), int(prec), sp, lds, stp, ldst, _stream(stream)), name)
+
+
+def sketch_apply(h, A, which: int = SK_BOTH, prec: int = SK_PREC_NATIVE, S=None, St=None, stream=None) -> None:
+    _apply(lib().sketch_apply, "sketch_apply", h, A, which, prec, S, St, stream)
+
+
+def sketch_apply_increment(h, A, which: int = SK_BOTH, prec: int = SK_PREC_NATIVE, S=None, St=None,
+                           stream=None) -> None:
+    _apply(lib().sketch_apply_increment, "sketch_apply_increment", h, A, which, prec, S, St, stream)
+
+
+def adaptive_norm_test(h, slot: int, S, delta_d: int, eps_rel: float, eps_abs: float, stream=None):
+    """Returns (stop, ||S^||_F, ||S~||_F)."""
+    _check_2d(S, "S")
+    stop = ctypes.c_int32()
+    nh = ctypes.c_double()
+    nt = ctypes.c_double()
+    rc = lib().adaptive_norm_test(h, int(slot), S.data_ptr(), S.shape[0], S.stride(0), _dtype_code(S),
+                                  int(delta_d), float(eps_rel), float(eps_abs), ctypes.byref(stop),
+                                  ctypes.byref(nh), ctypes.byref(nt), _stream(stream))
+    _check(rc, "adaptive_norm_test")
+    return bool(stop.value), nh.value, nt.value
+
+
+def kernel_matrix(gen: SkMatrix, A, stream=None) -> None:
+    _check_2d(A, "A")
+    _check(lib().kernel_matrix(ctypes.byref(gen), A.data_ptr(), A.stride(0), _stream(stream)), "kernel_matrix")
+
+
+def sketch_dims(h) -> dict:
+    kind, d, alpha, blocks = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    n = ctypes.c_int64()
+    _check(lib().sketch_dims(h, ctypes.byref(kind), ctypes.byref(n), ctypes.byref(d), ctypes.byref(alpha),
+                             ctypes.byref(blocks)), "sketch_dims")
+    return dict(kind=kind.value, n=n.value, d_total=d.value, alpha=alpha.value, blocks=blocks.value)
+
+
+def sketch_export(h, dense: bool = False, dense_dtype: int = SK_F64) -> dict:
+    """Host copies: SJLT cols/signs, SRHT diag/mu, and optionally dense R."""
+    dims = sketch_dims(h)
+    n, d, a, B, kind = dims["n"], dims["d_total"], dims["alpha"], dims["blocks"], dims["kind"]
+    out = {}
+    cols = signs = diag = mu = R = None
+    if kind in (SK_SJLT_GRAPH, SK_SJLT_BLOCK):
+        cols = np.zeros((n, a * B), dtype=np.int32)
+        signs = np.zeros((n, a * B), dtype=np.int8)
+        out.update(cols=cols, signs=signs)
+    if kind == SK_SRHT:
+        diag = np.zeros(n, dtype=np.int8)
+        mu = np.zeros(d, dtype=np.int32)
+        out.update(diag=diag, mu=mu)
+    if dense:
+        R = np.zeros((n, d), dtype=np.float64 if dense_dtype == SK_F64 else np.float32)
+        out["R"] = R
+    ptr = lambda x: None if x is None else x.ctypes.data  # noqa: E731
+    _check(lib().sketch_export(h, ptr(cols), ptr(signs), ptr(diag), ptr(mu), ptr(R), int(dense_dtype)),
+           "sketch_export")
+    return out
+
+
+def sketch_device_status(h, stream=None) -> None:
+    _check(lib().sketch_device_status(h, _stream(stream)), "sketch_device_status")
+
+
+def sketch_destroy(h) -> None:
+    if h:
+        lib().sketch_destroy(h)
+
+
+class Sketch:
+    """Owning wrapper of a handle (closes it on exit / garbage collection)."""
+
+    def __init__(self, kind, n, d, alpha=1, seed=0, d_max=None, stream=None):
+        self.h = sketch_create(kind, n, d, alpha, seed, d_max, stream)
+
+    def close(self):
+        if self.h:
+            sketch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

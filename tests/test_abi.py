@@ -1,0 +1,99 @@
+"""The C ABI library loads and exports every entry point include/jlsketch.h
+declares; constants agree; host-side argument checks and the no-GPU path
+return the documented status codes (no compute call is made here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2302_01977_gb300 import jlsketch as jl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(jl.LIB_PATH):
+        from paper_2302_01977_gb300 import build
+        build.build()
+    return jl.lib()
+
+
+def declared_functions():
+    text = open(jl.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(jl.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", jl.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(L, name)
+
+
+def test_constants_match_header():
+    hc = jl.header_constants()
+    for name, val in hc.items():
+        assert getattr(jl, name) == val, name
+    assert len(hc) >= 20
+
+
+def test_strerror_covers_codes(L):
+    for code in range(0, -10, -1):
+        s = jl.sketch_strerror(code)
+        assert s and s != "unknown status"
+    assert jl.sketch_strerror(-99) == "unknown status"
+
+
+def test_create_argument_checks(L):
+    h = ctypes.c_void_p()
+    bad = [
+        (0, 64, 16, 4, 16),            # kind
+        (jl.SK_SJLT_BLOCK, 0, 16, 4, 16),   # n
+        (jl.SK_SJLT_BLOCK, 64, 0, 4, 16),   # d
+        (jl.SK_SJLT_BLOCK, 64, 16, 3, 16),  # alpha does not divide d
+        (jl.SK_SJLT_GRAPH, 64, 4, 8, 16),   # alpha > d
+        (jl.SK_SJLT_GRAPH, 64, 64, 33, 64),  # alpha > 32
+        (jl.SK_GAUSS, 64, 16, 1, 8),        # d_max < d
+        (jl.SK_SRHT, 64, 16, 1, 128),       # d_max > nu
+        (jl.SK_GAUSS, 64, 16, 1, 9000),     # d_max > 8192
+    ]
+    for kind, n, d, a, dmax in bad:
+        assert L.sketch_create(ctypes.byref(h), kind, n, d, a, 1, dmax, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_create(None, jl.SK_GAUSS, 64, 16, 1, 1, 16, None) == jl.SK_ERR_INVALID_ARG
+
+
+def test_null_handle_calls(L):
+    assert L.sketch_increment(None, 4, None) == jl.SK_ERR_INVALID_ARG
+    m = jl.SkMatrix()
+    assert L.sketch_apply(None, ctypes.byref(m), 1, 0, None, 0, None, 0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_dims(None, None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_device_status(None, None) == jl.SK_ERR_INVALID_ARG
+    L.sketch_destroy(None)  # no-op
+    assert L.kernel_matrix(None, None, 0, None) == jl.SK_ERR_INVALID_ARG
+
+
+def test_no_gpu_fails_loudly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert L.sketch_create(ctypes.byref(h), jl.SK_GAUSS, 64, 16, 1, 1, 16, None) == jl.SK_ERR_DEVICE
+    with pytest.raises(jl.JLSketchError):
+        jl.sketch_create("gauss", 64, 16, stream=0)
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(jl, "_lib", None)
+    monkeypatch.setattr(jl, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        jl.lib()
