@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark: S = A R and S' = A^T R throughput on GB300 (GB/s of A).
+
+One step is one pass of the whole sketching path over the n = 32768 FP32
+kernel-matrix workload (A_ij = exp(-||x_i - y_j||^2 / (2 * 0.1^2)), X != Y,
+32768 points each, uniform in [0,1]^3; A resident in HBM, 4.29 GB):
+
+  1. operator generation: block SJLT (d = 256, alpha = 4), SRHT (d = 256),
+     Gaussian (d = 256);
+  2. S and S' for each operator (SJLT on CUDA cores in FP32; SRHT and
+     Gaussian on the fastest available path);
+  3. the adaptive SJLT run: d0 = 128, Delta-d = 64, up to 512 columns, stopping
+     test after every increment (eps_rel = 1e-2, eps_abs = 1e-8), S and S'.
+
+value = bytes of A streamed by all sketch products of the step / step time.
+A is larger than L2 (126 MB), so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.  Under torchrun every rank runs an independent
+replica (the path is not sharded); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "S=A·R throughput (GB/s of A, % HBM peak) per JL operator at stated error"
+WORKLOAD = dict(name="kernel_fp32_n32768", n=32768, d=256, alpha=4, h=0.1, seed=20230203 + 1,
+                d0=128, dd=64, d_max=512, eps_rel=1e-2, eps_abs=1e-8)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+class Step:
+    """Everything one step does, with per-call CUDA events."""
+
+    def __init__(self, A, n, prec_dense, timed_events=True):
+        import torch
+        from paper_2302_01977_gb300 import jlsketch as jl
+        self.jl, self.torch = jl, torch
+        self.A, self.n = A, n
+        self.prec_dense = prec_dense
+        w = WORKLOAD
+        dev = A.device
+        self.bufs = {k: torch.empty((n, w["d"]), dtype=torch.float32, device=dev)
+                     for k in ("sjlt_S", "sjlt_St", "srht_S", "srht_St", "gauss_S", "gauss_St")}
+        self.adS = torch.empty((n, w["d_max"]), dtype=torch.float32, device=dev)
+        self.adSt = torch.empty((n, w["d_max"]), dtype=torch.float32, device=dev)
+        self.events = []  # (label, start, end)
+        self.timed = timed_events
+        self.adaptive_info = None
+
+    def _ev(self, label, fn):
+        if not self.timed:
+            fn()
+            return
+        s = self.torch.cuda.Event(enable_timing=True)
+        e = self.torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        self.events.append((label, s, e))
+
+    def run(self, step_idx):
+        jl, A, w = self.jl, self.A, WORKLOAD
+        seed = w["seed"] + 7919 * step_idx
+        hs = []
+        try:
+            ops = [("sjlt", "sjlt_block", w["alpha"], jl.SK_PREC_NATIVE),
+                   ("srht", "srht", 1, self.prec_dense), ("gauss", "gauss", 1, self.prec_dense)]
+            for name, kind, alpha, prec in ops:
+                h = jl.sketch_create(kind, self.n, w["d"], alpha, seed, w["d"])
+                hs.append(h)
+                S, St = self.bufs[name + "_S"], self.bufs[name + "_St"]
+                self._ev(f"{name}.S", lambda: jl.sketch_apply(h, A, jl.SK_S, prec, S=S))
+                self._ev(f"{name}.St", lambda: jl.sketch_apply(h, A, jl.SK_ST, prec, St=St))
+            # adaptive SJLT run (Algorithm 1 on the global sketch)
+            h = jl.sketch_create("sjlt_block", self.n, w["d0"] + w["dd"], w["alpha"], seed + 1, w["d_max"])
+            hs.append(h)
+            self._ev("adaptive.apply", lambda: jl.sketch_apply(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
+            d, passes, hist = w["d0"], 2, []
+            while True:
+                wd = d + w["dd"]
+                s1 = jl.adaptive_norm_test(h, 0, self.adS[:, :wd], w["dd"], w["eps_rel"], w["eps_abs"])
+                s2 = jl.adaptive_norm_test(h, 1, self.adSt[:, :wd], w["dd"], w["eps_rel"], w["eps_abs"])
+                hist.append((d, s1[1] / s1[2], s2[1] / s2[2]))
+                if (s1[0] and s2[0]) or wd + w["dd"] > w["d_max"]:
+                    converged = s1[0] and s2[0]
+                    break
+                jl.sketch_increment(h, w["dd"])
+                self._ev("adaptive.increment",
+                         lambda: jl.sketch_apply_increment(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
+                passes += 2
+                d += w["dd"]
+            self.adaptive_info = dict(d_reached=d + w["dd"], converged=bool(converged), passes_over_A=passes,
+                                      ratios=[(int(a), round(b, 6), round(c, 6)) for a, b, c in hist])
+            return 6 + passes  # passes over A in this step
+        finally:
+            for h in hs:
+                jl.sketch_destroy(h)
+
+
+def kernel_times(events):
+    """label -> list of ms."""
+    out = {}
+    for label, s, e in events:
+        out.setdefault(label, []).append(s.elapsed_time(e))
+    return out
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(X, Y, S_gpu, rows_per_product, seed):
+    """Time the FP64 oracle on a bounded sample and check the GPU results on it."""
+    import numpy as np
+
+    from oracle import operators as ops
+    from oracle import sketch as osk
+    w = WORKLOAD
+    n, d = w["n"], w["d"]
+    rng = np.random.default_rng(12345)
+    rows = np.sort(rng.choice(n, rows_per_product, replace=False))
+    A_rows = osk.kernel_matrix(X[rows], Y, w["h"])          # inputs prepared before timing
+    A_cols = osk.kernel_matrix(X, Y[rows], w["h"]).T
+    t0 = time.perf_counter()
+    errs = {}
+    for name, kind, alpha in (("sjlt", "sjlt_block", w["alpha"]), ("srht", "srht", 1), ("gauss", "gauss", 1)):
+        R = ops.Operator(kind, n, d, alpha, seed).dense()
+        S_s = A_rows @ R
+        St_s = A_cols @ R
+        if S_gpu is not None:
+            gs, gst = S_gpu[name]
+            errs[name] = max(float(np.linalg.norm(gs[rows] - S_s) / np.linalg.norm(S_s)),
+                             float(np.linalg.norm(gst[rows] - St_s) / np.linalg.norm(St_s)))
+    dt = time.perf_counter() - t0
+    bytes_a = 6 * rows_per_product * n * 4
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(value=bytes_a / dt / 1e9, unit="GB/s", cores=cores, kind="oracle",
+                sample=f"{rows_per_product} sampled rows of S and of S' for each of SJLT, SRHT, Gaussian "
+                       f"(operators formed densely in FP64, products by numpy), {dt:.1f} s",
+                seconds=dt), errs
+
+
+def traffic_from_profile(kernel_file):
+    """dram bytes per launch recorded in profiles/ for the current source, else None."""
+    p = os.path.join(ROOT, "profiles", "sjlt_traffic.json.txt")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.loads(open(p).read())
+    except ValueError:
+        return None
+    src = os.path.join(ROOT, "paper_2302_01977_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    n = w["n"]
+    X = inputs.points(n, seed=w["seed"])
+    Y = inputs.points(n, seed=w["seed"] + 1000)
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    jl.kernel_matrix(jl.generator(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), w["h"]), A)
+    prec_dense = jl.SK_PREC_BF16X2 if args.prec == "bf16x2" else jl.SK_PREC_NATIVE
+    if args.prec == "auto":
+        prec_dense = jl.SK_PREC_NATIVE
+        try:  # use the tensor-core path when this build provides it
+            h = jl.sketch_create("gauss", 1024, 64, 1, 1, 64)
+            T = torch.zeros((1024, 1024), device="cuda")
+            O = torch.zeros((1024, 64), device="cuda")
+            jl.sketch_apply(h, T, jl.SK_S, jl.SK_PREC_BF16X2, S=O)
+            jl.sketch_destroy(h)
+            prec_dense = jl.SK_PREC_BF16X2
+        except jl.JLSketchError:
+            pass
+    step = Step(A, n, prec_dense)
+    for i in range(args.warmup):
+        step.run(i)
+    torch.cuda.synchronize()
+    step.events.clear()
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = jl.sketch_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    passes = 0
+    for i in range(args.steps):
+        passes += step.run(args.warmup + i)
+    t_end.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = jl.sketch_launch_count() - launches0
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    bytes_a = n * n * 4
+    total_bytes = bytes_a * passes * world
+    value = total_bytes / elapsed / 1e9
+    times = kernel_times(step.events)
+    hbm, bf16, bf16s, peak_kind = peaks()
+
+    per_op = {}
+    for name in ("sjlt", "srht", "gauss"):
+        ts, tst = statistics.median(times[f"{name}.S"]), statistics.median(times[f"{name}.St"])
+        per_op[name] = {"S_gbs": round(bytes_a / ts / 1e6, 1), "St_gbs": round(bytes_a / tst / 1e6, 1),
+                        "S_ms": round(ts, 4), "St_ms": round(tst, 4),
+                        "pct_hbm_S": round(100 * bytes_a / ts / 1e6 / hbm, 1),
+                        "pct_hbm_St": round(100 * bytes_a / tst / 1e6 / hbm, 1)}
+    per_op["srht"]["prec"] = per_op["gauss"]["prec"] = "bf16x2" if prec_dense == jl.SK_PREC_BF16X2 else "fp32"
+    per_op["sjlt"]["prec"] = "fp32"
+    per_op["adaptive_sjlt"] = dict(step.adaptive_info)
+
+    # dominant kernel: the class with the largest total time in the timed region
+    totals = {k: sum(v) for k, v in times.items()}
+    cls = {"sjlt_rows": totals.get("sjlt.S", 0), "sjlt_cols": totals.get("sjlt.St", 0),
+           "srht": totals.get("srht.S", 0) + totals.get("srht.St", 0),
+           "gauss": totals.get("gauss.S", 0) + totals.get("gauss.St", 0)}
+    d_out_bytes = n * w["d"] * 4
+    ccs_bytes = n * w["alpha"] * 2 + (n // 512) * (w["d"] + 4) * 4
+    # the SJLT kernels are the ones the roofline tracks (HBM-bound, one pass of A)
+    sj = "sjlt_cols" if cls["sjlt_cols"] >= cls["sjlt_rows"] else "sjlt_rows"
+    t_launch = statistics.median(times["sjlt.St" if sj == "sjlt_cols" else "sjlt.S"]) / 1e3
+    alg_bytes = bytes_a + d_out_bytes + ccs_bytes
+    achieved = alg_bytes / t_launch / 1e9
+    prof = traffic_from_profile("sjlt_apply.cu")
+    traffic = None
+    if prof:
+        traffic = prof.get("cols_bytes_per_launch" if sj == "sjlt_cols" else "rows_bytes_per_launch")
+    roofline = {"kernel": "sjlt_cols_kernel (S' = A^T R)" if sj == "sjlt_cols" else "sjlt_rows_kernel (S = A R)",
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes}
+    step_share = {k: round(v / max(1e-9, sum(cls.values())), 3) for k, v in cls.items()}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * elapsed / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": w["name"], "n": n, "d": w["d"], "alpha": w["alpha"], "h": w["h"],
+                       "adaptive": {k: w[k] for k in ("d0", "dd", "d_max", "eps_rel", "eps_abs")},
+                       "passes_over_A_per_step": passes // max(1, args.steps),
+                       "l2": "inputs larger than L2 (A = 4.29 GB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "per_operator": per_op, "time_share": step_share, "roofline": roofline,
+            "gpu_launches": int(launches), "clocks": clk}
+
+    # ---- end to end: A from pinned host memory, results back to the host
+    if not args.no_e2e:
+        A_host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A)
+        step_e = Step(A, n, prec_dense, timed_events=False)
+        outs = list(step_e.bufs.values()) + [step_e.adS, step_e.adSt]
+        hosts = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p2 = 0
+        for i in range(args.steps):
+            A.copy_(A_host, non_blocking=True)
+            p2 += step_e.run(1000 + i)
+            for o, hh in zip(outs, hosts):
+                hh.copy_(o, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": round(bytes_a * p2 * world / te / 1e9, 1), "unit": "GB/s",
+                       "h2d_bytes_per_step": bytes_a,
+                       "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs))}
+        del A_host, hosts
+
+    # ---- CPU baseline (oracle) on rank 0, N = 1 only; also checks the GPU results
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gpu = {}
+        seed = w["seed"] + 7919 * (args.warmup + args.steps - 1)
+        for name, kind, alpha, prec in (("sjlt", "sjlt_block", w["alpha"], 0), ("srht", "srht", 1, prec_dense),
+                                        ("gauss", "gauss", 1, prec_dense)):
+            h = jl.sketch_create(kind, n, w["d"], alpha, seed, w["d"])
+            S = torch.empty((n, w["d"]), device="cuda")
+            St = torch.empty_like(S)
+            jl.sketch_apply(h, A, jl.SK_BOTH, prec, S=S, St=St)
+            jl.sketch_destroy(h)
+            gpu[name] = (S.double().cpu().numpy(), St.double().cpu().numpy())
+        cb, errs = cpu_baseline(X, Y, gpu, args.cpu_rows, seed)
+        line["cpu_baseline"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in cb.items()}
+        for name in errs:
+            line["per_operator"][name]["rel_err_vs_oracle"] = float(f"{errs[name]:.3e}")
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores on a bounded sample."""
+    import numpy as np  # noqa: F401
+
+    from paper_2302_01977_gb300 import inputs
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOAD
+    X = inputs.points(w["n"], seed=w["seed"])
+    Y = inputs.points(w["n"], seed=w["seed"] + 1000)
+    for i in range(args.warmup):
+        cpu_baseline(X, Y, None, args.ref_rows, w["seed"] + i)
+    secs, vals = 0.0, []
+    for i in range(args.steps):
+        cb, _ = cpu_baseline(X, Y, None, args.ref_rows, w["seed"] + 100 + i)
+        secs += cb["seconds"]
+        vals.append(cb["value"])
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "n": w["n"], "d": w["d"], "alpha": w["alpha"], "h": w["h"],
+                       "sample_rows_per_product": args.ref_rows},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["auto", "fp32", "bf16x2"], default="auto")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=512)
+    ap.add_argument("--ref-rows", type=int, default=128)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

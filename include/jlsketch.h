@@ -156,7 +156,7 @@ int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32
  * scratch when the split point moves backwards or `rows` changes.  Norms and
  * Gram matrices accumulate in FP64.  Synchronizes `stream`; writes *stop and,
  * if not NULL, *norm_hat = ||S^||_F and *norm_tilde = ||S~||_F (host).
- * Errors: INVALID_ARG, STATE (delta_d < 1 or >= d_total), ALIGN, DEVICE.
+ * Errors: INVALID_ARG, STATE (delta_d < 1 or >= d_total), DEVICE.
  */
 int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, int64_t ldS,
                        int32_t dtype, int32_t delta_d, double eps_rel, double eps_abs,
@@ -189,6 +189,10 @@ int sketch_export(sk_handle h, int32_t* cols, int8_t* signs, int8_t* diag, int32
 /* sketch_device_status -- synchronize `stream` and report (and clear) the
  * handle's device-side error flag: SK_OK, SK_ERR_TIMEOUT or SK_ERR_DEVICE. */
 int sketch_device_status(sk_handle h, void* stream);
+
+/* sketch_launch_count -- number of kernels this library has launched in the
+ * process so far (all handles); a diagnostic for counting device work. */
+int64_t sketch_launch_count(void);
 
 /* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */
 void sketch_destroy(sk_handle h);

@@ -38,7 +38,7 @@ int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, 
   if (dtype == SK_F32)
     scale_cols_kernel<float><<<grid, 256, 0, s>>>((float*)S, rows, ld, c0, c1, (float)factor);
   else
-    scale_cols_kernel<double><<<grid, 256, 0, s>>>((double*)S, rows, ld, c0, c1, factor);
+    scale_cols_kernel<double><<<grid, 256, 0, s>>>((double*)S, rows, ld, c0, c1, factor); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -281,8 +281,8 @@ int tsgemm(const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q, int64
   const int64_t rpc = ((rows + nchunks - 1) / nchunks + 31) / 32 * 32;
   const int nch = (int)((rows + rpc - 1) / rpc);
   dim3 grid((p + 31) / 32, (q + 31) / 32, nch);
-  tsgemm_tn_partial<T><<<grid, 256, 0, s>>>(X, ldx, p, Y, ldy, q, rows, rpc, part);
-  reduce_partials<<<64, 256, 0, s>>>(part, nch, (int64_t)p * q, out);
+  tsgemm_tn_partial<T><<<grid, 256, 0, s>>>(X, ldx, p, Y, ldy, q, rows, rpc, part); note_launch();
+  reduce_partials<<<64, 256, 0, s>>>(part, nch, (int64_t)p * q, out); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -302,8 +302,8 @@ int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int6
       // (sub_qg indexes G[i * q + j]); reuse part as staging
       double* slab = sc.part;
       dim3 g1((unsigned)((B.cols * 64 + 255) / 256));
-      copy_block_kernel<double><<<g1, 256, 0, s>>>(sc.G + j0, b, slab, q, B.cols, q);
-      sub_qg_kernel<T><<<(unsigned)((rows + 31) / 32), 256, 0, s>>>(W + j0, ldw, q, Q, h->d_max, B.cols, slab, rows);
+      copy_block_kernel<double><<<g1, 256, 0, s>>>(sc.G + j0, b, slab, q, B.cols, q); note_launch();
+      sub_qg_kernel<T><<<(unsigned)((rows + 31) / 32), 256, 0, s>>>(W + j0, ldw, q, Q, h->d_max, B.cols, slab, rows); note_launch();
     }
     JLS_CHECK_CUDA(cudaGetLastError());
   }
@@ -312,7 +312,7 @@ int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int6
 
 template <typename T>
 int sumsq(const T* W, int64_t ldw, int64_t rows, int b, const Scratch& sc, double* out, cudaStream_t s) {
-  sumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, sc.norms);
+  sumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, sc.norms); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   double part[NORM_GRID];
   JLS_CHECK_CUDA(cudaMemcpyAsync(part, sc.norms, sizeof(part), cudaMemcpyDeviceToHost, s));
@@ -355,21 +355,21 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
   // absorb columns [covered, c_split) into Q, 64 at a time
   while (B.covered < c_split) {
     const int b = std::min(64, c_split - B.covered);
-    copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b);
+    copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b); note_launch();
     JLS_CHECK(project_twice<T>(h, B, W, 64, b, rows, sc, nchunks, s));
     for (int pass = 0; pass < 2; ++pass) {  // Cholesky QR twice
       JLS_CHECK(tsgemm<T>(W, 64, b, W, 64, b, rows, nchunks, sc.part, sc.G, s));
-      chol_inv_kernel<<<1, 64, CHOL_SMEM, s>>>(sc.G, b, sc.U, h->d_err);
-      mul_upper_kernel<T><<<(unsigned)((rows + 15) / 16), 256, 0, s>>>(W, 64, sc.U, b, W2, 64, rows);
-      copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W2, 64, W, 64, rows, b);
+      chol_inv_kernel<<<1, 64, CHOL_SMEM, s>>>(sc.G, b, sc.U, h->d_err); note_launch();
+      mul_upper_kernel<T><<<(unsigned)((rows + 15) / 16), 256, 0, s>>>(W, 64, sc.U, b, W2, 64, rows); note_launch();
+      copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W2, 64, W, 64, rows, b); note_launch();
     }
-    copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W, 64, Q + B.cols, h->d_max, rows, b);
+    copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W, 64, Q + B.cols, h->d_max, rows, b); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
     B.cols += b;
     B.covered += b;
   }
   // the test block
-  copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt);
+  copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   double t2 = 0, h2 = 0;
   JLS_CHECK(sumsq<T>(W, wmax, rows, bt, sc, &t2, s));

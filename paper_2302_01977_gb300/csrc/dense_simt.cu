@@ -124,6 +124,7 @@ static int launch_dense(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int 
   else if (srht) JLS_LAUNCH(false, true);
   else JLS_LAUNCH(false, false);
 #undef JLS_LAUNCH
+  note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }

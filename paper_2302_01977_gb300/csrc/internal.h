@@ -117,6 +117,7 @@ int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int 
               cudaStream_t s);
 
 // --- jlsketch.cu helpers ---
+void note_launch();  // counts kernel launches (sketch_launch_count)
 int cuda_status(cudaError_t e);
 size_t elem_size(int dtype);
 

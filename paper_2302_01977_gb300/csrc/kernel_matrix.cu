@@ -48,7 +48,7 @@ int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s
     kernel_matrix_kernel<double, CPC><<<grid, 256, 0, s>>>(static_cast<const double*>(g->X),
                                                           static_cast<const double*>(g->Y), g->rows, g->cols,
                                                           nih, g->shift, static_cast<double*>(A), ld,
-                                                          rows_per_cta);
+                                                          rows_per_cta); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }

@@ -91,7 +91,7 @@ int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s) 
   const int64_t grid = (h->n + threads - 1) / threads;
   sjlt_draw_kernel<<<(unsigned)grid, threads, 0, s>>>(
       h->n, h->alpha, width, h->kind == SK_SJLT_BLOCK, h->seed, block, col_off,
-      h->sjlt_ents + (size_t)block * h->n * h->alpha, h->d_err);
+      h->sjlt_ents + (size_t)block * h->n * h->alpha, h->d_err); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -189,7 +189,7 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
                                         (int)shm));
   ccs_build_kernel<<<C.ntiles, 512, shm, s>>>(h->sjlt_ents, h->n, h->alpha, d_boc, d_boff,
                                               h->d_total, tile, C.e_stride, C.o_stride, C.ents,
-                                              C.offs);
+                                              C.offs); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   JLS_CHECK_CUDA(cudaStreamSynchronize(s));  // the pageable host vectors above die here
   cudaFree(d_boc);
@@ -252,7 +252,7 @@ int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s) {
     JLS_CHECK_CUDA(cudaMemsetAsync(h->srht_state, 0, sizeof(unsigned long long), s));
     const int threads = 256;
     srht_diag_kernel<<<(unsigned)((h->n + threads - 1) / threads), threads, 0, s>>>(h->n, h->seed,
-                                                                                    h->srht_diag);
+                                                                                    h->srht_diag); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
   int cap = 1;
@@ -262,7 +262,7 @@ int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s) {
     JLS_CHECK_CUDA(
         cudaFuncSetAttribute(srht_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   srht_mu_kernel<<<1, 32, shm, s>>>(h->nu, h->seed, d_old, d_new, cap, h->srht_mu, h->srht_state,
-                                    h->d_err);
+                                    h->d_err); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -312,7 +312,7 @@ int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s) {
   gauss_gen_kernel<<<grid, 256, 0, s>>>(h->n, c0, c_end, h->seed, plane == 0 ? h->z32 : nullptr,
                                         plane == 1 ? h->z64 : nullptr,
                                         plane == 2 ? reinterpret_cast<__nv_bfloat16*>(h->zhi) : nullptr,
-                                        plane == 2 ? reinterpret_cast<__nv_bfloat16*>(h->zlo) : nullptr);
+                                        plane == 2 ? reinterpret_cast<__nv_bfloat16*>(h->zlo) : nullptr); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   *have = c_end;
   return SK_OK;
@@ -332,7 +332,7 @@ int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s) {
   if (!h->srht_pm1) JLS_CHECK_CUDA(cudaMalloc(&h->srht_pm1, (size_t)h->d_max * h->n * sizeof(uint16_t)));
   if (h->pm1_cols >= c_end) return SK_OK;
   dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)(c_end - h->pm1_cols));
-  srht_pm1_kernel<<<grid, 256, 0, s>>>(h->n, h->pm1_cols, c_end, h->srht_diag, h->srht_mu, h->srht_pm1);
+  srht_pm1_kernel<<<grid, 256, 0, s>>>(h->n, h->pm1_cols, c_end, h->srht_diag, h->srht_mu, h->srht_pm1); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   h->pm1_cols = c_end;
   return SK_OK;
@@ -377,7 +377,7 @@ int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s) {
   else
     dense_R_kernel<float><<<grid, threads, 0, s>>>(h->kind, h->n, h->d_total, h->alpha,
                                                    (int)h->blocks.size(), sc, h->sjlt_ents, h->srht_diag,
-                                                   h->srht_mu, h->seed, (float*)R_dev);
+                                                   h->srht_mu, h->seed, (float*)R_dev); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }

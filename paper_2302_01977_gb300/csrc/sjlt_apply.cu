@@ -26,6 +26,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -90,12 +91,16 @@ template <typename T, int TILE, int NB, int STAGES>
 __global__ void __launch_bounds__(17 * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
                      const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
-                     int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, T* __restrict__ St,
+                     int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES, T* __restrict__ St,
                      int64_t ldSt, T scale, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int BOXR = TILE < 256 ? TILE : 256;
   constexpr uint32_t TILE_BYTES = TILE * 32 * sizeof(T);
-  const uint32_t E_BYTES = (uint32_t)(e_stride * 2), O_BYTES = (uint32_t)(o_stride * 4);
+  // only the offsets [o_lo, o_lo + o_cnt) and the entries of columns
+  // [c_lo, c_hi) of each tile are staged (16-byte aligned supersets)
+  const int o_lo = c_lo & ~3;
+  const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
+  const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
   T* tiles = reinterpret_cast<T*>(smem);
   uint16_t* sh_e = reinterpret_cast<uint16_t*>(smem + STAGES * TILE_BYTES);
   uint32_t* sh_o = reinterpret_cast<uint32_t*>(smem + STAGES * (TILE_BYTES + E_BYTES));
@@ -131,13 +136,21 @@ __global__ void __launch_bounds__(17 * 32, 1)
         if (t >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((t / STAGES) - 1) & 1, err);
         if (!ok) break;
         const uint32_t fb = full0 + 8 * s;
-        mbar_arrive_expect_tx(fb, TILE_BYTES + E_BYTES + O_BYTES);
+        const uint32_t* ot = offs + (int64_t)t * o_stride;
+        const uint32_t e_al = __ldg(ot + c_lo) & ~7u;
+        const uint32_t eb = ((__ldg(ot + c_hi) - e_al) * 2 + 15) & ~15u;
+        if (eb > E_BYTES) {  // host sizing guarantees this never happens
+          set_err(err, ERRF_BOUNDS);
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(fb, TILE_BYTES + eb + O_BYTES);
         const uint32_t dst = smem_u32(tiles) + s * TILE_BYTES;
 #pragma unroll
         for (int q = 0; q < TILE / BOXR; ++q)
           tma_load_2d(dst + q * BOXR * 32 * sizeof(T), &tmA, fb, (int32_t)j0, (int32_t)(t * TILE + q * BOXR));
-        bulk_g2s(smem_u32(sh_e) + s * E_BYTES, ents + (int64_t)t * e_stride, E_BYTES, fb);
-        bulk_g2s(smem_u32(sh_o) + s * O_BYTES, offs + (int64_t)t * o_stride, O_BYTES, fb);
+        if (eb) bulk_g2s(smem_u32(sh_e) + s * E_BYTES, ents + (int64_t)t * e_stride + e_al, eb, fb);
+        bulk_g2s(smem_u32(sh_o) + s * O_BYTES, ot + o_lo, O_BYTES, fb);
         issued = t + 1;
       }
       // drain: never leave the CTA with copies in flight
@@ -148,9 +161,11 @@ __global__ void __launch_bounds__(17 * 32, 1)
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % STAGES;
       if (!mbar_wait(full0 + 8 * s, (t / STAGES) & 1, err)) break;
+      const uint32_t* O = sh_o + s * (O_BYTES / 4) - o_lo;  // indexed by absolute column
+      const uint32_t e_al = O[c_lo] & ~7u;
       if (nb > 0)
-        accumulate_tile<T, NB, 32>(acc, sh_e + s * (E_BYTES / 2), sh_o + s * (O_BYTES / 4),
-                                   tiles + (size_t)s * TILE * 32 + lane, cw0, nb);
+        accumulate_tile<T, NB, 32>(acc, sh_e + s * (E_BYTES / 2) - e_al, O, tiles + (size_t)s * TILE * 32 + lane,
+                                   cw0, nb);
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * s);
     }
@@ -177,12 +192,14 @@ template <typename T, int TILE, int NB, int STAGES>
 __global__ void __launch_bounds__(16 * 32, 1)
     sjlt_rows_kernel(const T* __restrict__ A, int64_t lda, int64_t rowsA, int64_t colsA,
                      const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
-                     int64_t o_stride, int c_lo, int c_hi, int nbw, T* __restrict__ S, int64_t ldS,
-                     T scale, int* err) {
+                     int64_t o_stride, int c_lo, int c_hi, int nbw, uint32_t E_BYTES, T* __restrict__ S,
+                     int64_t ldS, T scale, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int P = TILE + 1;
   constexpr uint32_t TILE_BYTES = ((32 * P * sizeof(T)) + 127) / 128 * 128;
-  const uint32_t E_BYTES = (uint32_t)(e_stride * 2), O_BYTES = (uint32_t)(o_stride * 4);
+  const int o_lo = c_lo & ~3;
+  const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
+  const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
   uint8_t* base_t = smem;
   uint8_t* base_e = smem + STAGES * TILE_BYTES;
   uint8_t* base_o = base_e + STAGES * E_BYTES;
@@ -205,11 +222,18 @@ __global__ void __launch_bounds__(16 * 32, 1)
         else
           cp_async_8(dst + (r * P + c) * 8, src, in ? 8 : 0);
       }
+      const uint32_t* ot = offs + (int64_t)t * o_stride;
+      const uint32_t e_al = __ldg(ot + c_lo) & ~7u;
+      uint32_t eb = ((__ldg(ot + c_hi) - e_al) * 2 + 15) & ~15u;
+      if (eb > E_BYTES) {  // host sizing guarantees this never happens
+        set_err(err, ERRF_BOUNDS);
+        eb = 0;
+      }
       const uint32_t de = smem_u32(base_e + s * E_BYTES);
-      const uint8_t* se = reinterpret_cast<const uint8_t*>(ents + (int64_t)t * e_stride);
-      for (uint32_t q = threadIdx.x; q < E_BYTES / 16; q += nthreads) cp_async_16(de + q * 16, se + q * 16);
+      const uint8_t* se = reinterpret_cast<const uint8_t*>(ents + (int64_t)t * e_stride + e_al);
+      for (uint32_t q = threadIdx.x; q < eb / 16; q += nthreads) cp_async_16(de + q * 16, se + q * 16);
       const uint32_t dof = smem_u32(base_o + s * O_BYTES);
-      const uint8_t* so = reinterpret_cast<const uint8_t*>(offs + (int64_t)t * o_stride);
+      const uint8_t* so = reinterpret_cast<const uint8_t*>(ot + o_lo);
       for (uint32_t q = threadIdx.x; q < O_BYTES / 16; q += nthreads) cp_async_16(dof + q * 16, so + q * 16);
     }
     cp_async_commit();
@@ -229,9 +253,10 @@ __global__ void __launch_bounds__(16 * 32, 1)
     __syncthreads();
     load_tile(t + STAGES - 1, (t + STAGES - 1) % STAGES);
     const int s = t % STAGES;
+    const uint32_t* O = reinterpret_cast<const uint32_t*>(base_o + s * O_BYTES) - o_lo;
+    const uint32_t e_al = O[c_lo] & ~7u;
     if (nb > 0)
-      accumulate_tile<T, NB, 1>(acc, reinterpret_cast<const uint16_t*>(base_e + s * E_BYTES),
-                                reinterpret_cast<const uint32_t*>(base_o + s * O_BYTES),
+      accumulate_tile<T, NB, 1>(acc, reinterpret_cast<const uint16_t*>(base_e + s * E_BYTES) - e_al, O,
                                 reinterpret_cast<const T*>(base_t + s * TILE_BYTES) + lane * P, cw0, nb);
   }
   cp_async_wait<0>();
@@ -285,6 +310,35 @@ Jobs plan_jobs(int ncols) {
   return {nj, nbw};
 }
 
+// Column ranges one launch can take: <= MAX_JOBS * NB columns, and few enough
+// blocks that STAGES tiles plus their entries fit in shared memory.  Each
+// launch streams A once; ranges are cut at block boundaries.
+struct Range {
+  int lo, hi, nblk;
+};
+std::vector<Range> plan_ranges(const sk_op* h, int c_lo, int c_hi, int max_blk) {
+  std::vector<Range> out;
+  int c = c_lo;
+  while (c < c_hi) {
+    int hi = c, nblk = 0, off = 0;
+    for (size_t b = 0; b < h->blocks.size(); ++b) {
+      const int b_lo = off, b_hi = off + h->blocks[b];
+      off = b_hi;
+      if (b_hi <= c) continue;
+      if (b_lo >= c_hi) break;
+      if (nblk == max_blk) break;
+      const int take_hi = std::min(std::min(b_hi, c_hi), c + MAX_JOBS * NB_SJLT);
+      if (take_hi <= hi) break;
+      hi = take_hi;
+      ++nblk;
+      if (hi < std::min(b_hi, c_hi)) break;  // width limit reached inside a block
+    }
+    out.push_back({c, hi, nblk});
+    c = hi;
+  }
+  return out;
+}
+
 template <typename T, int TILE>
 int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
                 int64_t ldSt, cudaStream_t s) {
@@ -303,17 +357,23 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return SK_ERR_ALIGN;
   const size_t tile_b = (size_t)TILE * 32 * sizeof(T);
-  const size_t smem = STAGES * (tile_b + C.e_stride * 2 + C.o_stride * 4) + 2 * STAGES * 8;
-  for (int lo = c_lo; lo < c_hi; lo += MAX_JOBS * NB_SJLT) {
-    const int hi = std::min(c_hi, lo + MAX_JOBS * NB_SJLT);
-    const Jobs J = plan_jobs(hi - lo);
-    const size_t out_b = (size_t)32 * (hi - lo + 1) * sizeof(T);
+  const size_t o_max = (MAX_JOBS * NB_SJLT + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * TILE * 2;
+  const size_t budget = 227 * 1024 - 2 * STAGES * 8;
+  const long fit = ((long)budget / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  if (fit < 1) return SK_ERR_UNSUPPORTED;
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit)) {
+    const Jobs J = plan_jobs(rg.hi - rg.lo);
+    const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
+    const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
+    const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
+    const size_t out_b = (size_t)32 * (rg.hi - rg.lo + 1) * sizeof(T);
     if (smem > 227 * 1024 || out_b > STAGES * tile_b) return SK_ERR_UNSUPPORTED;
     auto kern = sjlt_cols_kernel<T, TILE, NB_SJLT, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)((A->cols + 31) / 32);
-    kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride, lo,
-                                                hi, J.nbw, J.njobs, St, ldSt, scale, h->d_err);
+    kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride,
+                                                rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
   return SK_OK;
@@ -324,17 +384,23 @@ int launch_rows(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
                 cudaStream_t s) {
   constexpr int STAGES = 3;
   const size_t tile_b = ((32 * (TILE + 1) * sizeof(T)) + 127) / 128 * 128;
-  const size_t smem = STAGES * (tile_b + C.e_stride * 2 + C.o_stride * 4);
-  for (int lo = c_lo; lo < c_hi; lo += MAX_JOBS * NB_SJLT) {
-    const int hi = std::min(c_hi, lo + MAX_JOBS * NB_SJLT);
-    const Jobs J = plan_jobs(hi - lo);
-    const size_t out_b = (size_t)32 * (hi - lo + 1) * sizeof(T);
+  const size_t o_max = (MAX_JOBS * NB_SJLT + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * TILE * 2;
+  const long fit = ((long)(227 * 1024) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  if (fit < 1) return SK_ERR_UNSUPPORTED;
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit)) {
+    const Jobs J = plan_jobs(rg.hi - rg.lo);
+    const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
+    const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
+    const size_t smem = STAGES * (tile_b + e_bytes + o_bytes);
+    const size_t out_b = (size_t)32 * (rg.hi - rg.lo + 1) * sizeof(T);
     if (smem > 227 * 1024 || out_b > smem) return SK_ERR_UNSUPPORTED;
     auto kern = sjlt_rows_kernel<T, TILE, NB_SJLT, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)((A->rows + 31) / 32);
     kern<<<grid, J.njobs * 32, smem, s>>>(static_cast<const T*>(A->A), A->ld, A->rows, A->cols, C.ents, C.offs,
-                                          C.e_stride, C.o_stride, lo, hi, J.nbw, S, ldS, scale, h->d_err);
+                                          C.e_stride, C.o_stride, rg.lo, rg.hi, J.nbw, e_bytes, S, ldS, scale,
+                                          h->d_err); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
   return SK_OK;

@@ -46,7 +46,7 @@ KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": 
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
            "adaptive_norm_test", "kernel_matrix", "sketch_dims", "sketch_export",
-           "sketch_device_status", "sketch_destroy", "sketch_strerror"]
+           "sketch_device_status", "sketch_launch_count", "sketch_destroy", "sketch_strerror"]
 
 
 class JLSketchError(RuntimeError):
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
         "sketch_device_status": (i32, [vp, vp]),
+        "sketch_launch_count": (i64, []),
         "sketch_destroy": (None, [vp]),
         "sketch_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -247,6 +248,10 @@ def sketch_export(h, dense: bool = False, dense_dtype: int = SK_F64) -> dict:
 
 def sketch_device_status(h, stream=None) -> None:
     _check(lib().sketch_device_status(h, _stream(stream)), "sketch_device_status")
+
+
+def sketch_launch_count() -> int:
+    return int(lib().sketch_launch_count())
 
 
 def sketch_destroy(h) -> None:

@@ -24,7 +24,7 @@ def L():
 def declared_functions():
     text = open(jl.HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

@@ -12,7 +12,7 @@ import pytest
 
 from oracle import adaptive as oad
 from paper_2302_01977_gb300 import inputs
-from tests.util import dev, ensure_built
+from tests.util import dev_padded, ensure_built
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def gpu_loop(A_np, dtype, **kw):
     from paper_2302_01977_gb300 import jlsketch as jl
     from paper_2302_01977_gb300.adaptive import adaptive_sketch
     tdt = torch.float64 if dtype == "f64" else torch.float32
-    res = adaptive_sketch(dev(A_np, tdt), **kw)
+    res = adaptive_sketch(dev_padded(A_np, tdt), **kw)
     try:
         jl.sketch_device_status(res["handle"])
     finally:

@@ -10,7 +10,7 @@ import pytest
 from oracle import operators as ops
 from oracle import sketch as osk
 from paper_2302_01977_gb300 import inputs
-from tests.util import TOL, dev, ensure_built, host, rel_fro
+from tests.util import TOL, dev_padded, ensure_built, host, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -27,20 +27,22 @@ def jlmod():
     return jl
 
 
-def sketch(kind, A_np, d, seed, dtype, prec=0, incs=()):
+def sketch(kind, A_np, d, seed, dtype, prec=0, incs=(), which=3):
     jl = jlmod()
     tdt = torch.float64 if dtype == "f64" else torch.float32
     m, n = A_np.shape
-    A = dev(A_np, tdt)
+    A = dev_padded(A_np, tdt)
     dmax = d + sum(incs)
     h = jl.sketch_create(kind, n, d, 1, seed, dmax)
     try:
         S = torch.full((m, dmax), np.nan, dtype=tdt, device="cuda")
         St = torch.full((n, dmax), np.nan, dtype=tdt, device="cuda")
-        jl.sketch_apply(h, A, prec=prec, S=S, St=St)
+        Sa = S if which & 1 else None
+        Sta = St if which & 2 else None
+        jl.sketch_apply(h, A, which=which, prec=prec, S=Sa, St=Sta)
         for dd in incs:
             jl.sketch_increment(h, dd)
-            jl.sketch_apply_increment(h, A, prec=prec, S=S, St=St)
+            jl.sketch_apply_increment(h, A, which=which, prec=prec, S=Sa, St=Sta)
         torch.cuda.synchronize()
         jl.sketch_device_status(h)
     finally:
@@ -80,7 +82,7 @@ def test_srht_matches_fwht_route():
     """The element-formula sketch equals the transform of the padded rows (Sec. 6.2)."""
     n, d = 1000, 64
     A = inputs.dense_matrix(50, n, seed=2)
-    S, _ = sketch("srht", A, d, 5, "f64")
+    S, _ = sketch("srht", A, d, 5, "f64", which=1)
     op = ops.Operator("srht", n, d, 1, 5)
     ref = osk.srht_by_fwht(A, op.srht_diag(), op.srht_samples(), d)
     assert rel_fro(S, ref) <= TOL["f64"]

@@ -1,6 +1,7 @@
 """The device kernel-matrix generator against the oracle's FP64 formula.
 
-FP64: elementwise relative error <= 1e-14 (libm vs CUDA exp rounding).
+FP64: |dA| <= (4 + 8|arg|) * 2^-52 * A_64: exp rounding plus the argument, which
+carries about four roundings (squares and sum, 1/(2h^2), the product).
 FP32: the device works in FP32 (distance and expf), so the bound is a few ulp
 plus the argument's rounding: |dA| <= (4 + 2|arg|) * 2^-23 * A_64 + 1e-37.
 """
@@ -33,10 +34,10 @@ def test_kernel_matrix(dtype, m, n, h, shift):
     jl.kernel_matrix(jl.generator(dev(X), dev(Y), h, shift), A)
     got = host(A)[:, :n]
     ref = osk.kernel_matrix(X, Y, h, shift)
+    d2 = ((X.astype(np.float64)[:, None, :] - Y.astype(np.float64)[None]) ** 2).sum(-1)
+    arg = d2 / (2 * h * h)
     if dtype == "f64":
-        assert np.max(np.abs(got - ref) / ref) <= 1e-14
+        assert np.all(np.abs(got - ref) <= (4 + 8 * arg) * 2.0 ** -52 * ref)
     else:
-        d2 = ((X.astype(np.float64)[:, None, :] - Y.astype(np.float64)[None]) ** 2).sum(-1)
-        arg = d2 / (2 * h * h)
-        bound = (4 + 2 * arg) * 2.0 ** -23 * ref + 1e-37
+        bound = (4 + 8 * arg) * 2.0 ** -23 * ref + 1e-37
         assert np.all(np.abs(got - ref) <= bound)

@@ -12,7 +12,7 @@ import pytest
 from oracle import operators as ops
 from oracle import sketch as osk
 from paper_2302_01977_gb300 import inputs
-from tests.util import TOL, dev, ensure_built, host, rel_fro
+from tests.util import TOL, dev, dev_padded, ensure_built, host, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +34,7 @@ def run_apply(kind, A_np, d, alpha, seed, dtype, which=3, incs=(), ld_pad=0, s_p
     jl = jlmod()
     tdt = torch.float64 if dtype == "f64" else torch.float32
     m, n = A_np.shape
-    Ad = torch.zeros((m, n + ld_pad), dtype=tdt, device="cuda")
-    Ad[:, :n] = dev(A_np, tdt)
-    A = Ad[:, :n]
+    A = dev_padded(np.pad(A_np, ((0, 0), (0, ld_pad))), tdt)[:, :n]
     dmax = d + sum(incs)
     h = jl.sketch_create(kind, n if which & 1 else m, d, alpha, seed, dmax)
     try:
@@ -96,12 +94,12 @@ def test_rectangular_and_padded(which):
 def test_increments_match_grown_operator(kind, dtype):
     """apply, then increment + apply_increment twice == oracle S of the grown R."""
     jl = jlmod()
-    n, d0, dd, alpha, seed = 1100, 64, 32, 4, 99
+    n, d0, dd, alpha, seed = 1101, 64, 32, 4, 99
     tdt = torch.float64 if dtype == "f64" else torch.float32
     A_np = inputs.dense_matrix(n, n, seed=8)
     if dtype == "f32":
         A_np = A_np.astype(np.float32)
-    A = dev(A_np, tdt)
+    A = dev_padded(A_np, tdt)
     h = jl.sketch_create(kind, n, d0, alpha, seed, d0 + 2 * dd)
     op = ops.Operator(kind, n, d0, alpha, seed)
     try:
@@ -169,3 +167,18 @@ def test_full_size_fp32_sampled_rows():
     assert rel_fro(host(St)[rows], A_cols @ R) <= TOL["f32"]
     # every row is finite (no tile left unwritten)
     assert np.isfinite(host(S)).all() and np.isfinite(host(St)).all()
+
+
+def test_unaligned_leading_dimension_rejected():
+    """TMA needs 16-byte row pitches: an odd FP32 leading dimension is refused."""
+    jl = jlmod()
+    n = 129
+    A = dev(np.ones((n, n), dtype=np.float32))  # ld = 129 floats = 516 bytes
+    h = jl.sketch_create("sjlt_block", n, 16, 4, 1, 16)
+    try:
+        S = torch.zeros((n, 16), dtype=torch.float32, device="cuda")
+        with pytest.raises(jl.JLSketchError) as e:
+            jl.sketch_apply(h, A, which=1, S=S)
+        assert e.value.status == jl.SK_ERR_ALIGN
+    finally:
+        jl.sketch_destroy(h)

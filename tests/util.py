@@ -19,6 +19,19 @@ def dev(x, dtype=None):
     return t.cuda()
 
 
+def dev_padded(x, dtype):
+    """Device copy of a 2-D array whose leading dimension is rounded up to 16
+    bytes (the library's alignment contract); returns the (rows, cols) view."""
+    import torch
+    x = np.ascontiguousarray(x)
+    m, n = x.shape
+    es = 8 if dtype == torch.float64 else 4
+    ld = (n * es + 15) // 16 * 16 // es
+    buf = torch.zeros((m, ld), dtype=dtype, device="cuda")
+    buf[:, :n] = torch.from_numpy(x).to(dtype).cuda()
+    return buf[:, :n]
+
+
 def host(t):
     return t.detach().cpu().numpy()
 
