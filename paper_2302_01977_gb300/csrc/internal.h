@@ -12,9 +12,9 @@
 namespace jls {
 
 // Tile sizes (rows of R per tile) of the tiled compressed-column structure,
-// per element size: the S and S' SJLT kernels stage TILE x 32 elements of A.
-constexpr int SJLT_TILE_F32 = 512;
-constexpr int SJLT_TILE_F64 = 256;
+// per element size (the S and S' SJLT kernels stage TILE rows or columns of A).
+constexpr int SJLT_TILE_F32 = 128;
+constexpr int SJLT_TILE_F64 = 64;
 constexpr int SJLT_MAX_ALPHA = 32;
 constexpr int MAX_D = 8192;
 

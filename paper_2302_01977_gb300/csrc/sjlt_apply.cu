@@ -2,27 +2,31 @@
 //
 // R is held as a tiled compressed-column structure (Sec. 6.1's CCS of B+ and
 // B-, merged with a sign bit and cut into tiles of TILE rows of R): for each
-// tile, the entries (row-in-tile, sign) sorted by column.  No multiplications:
-// every entry adds or subtracts one element of A, and the scale 1/sqrt(alpha *
-// blocks) is applied once at the end, as in the paper's binary-matrix design.
+// tile, the entries (row-in-tile, sign) sorted by column.  No products with
+// the values of R: every entry adds or subtracts elements of A, and the scale
+// 1/sqrt(alpha * blocks) is applied once when results are written, as in the
+// paper's binary-matrix design.
 //
-// GB300 mapping.  Both kernels stream A exactly once from HBM and stage each
-// tile in shared memory; a warp owns a range of <= NB output columns of R and
-// keeps their sums in registers for the whole stream.  Because the entries of
-// a tile are grouped by column, the warp walks them column by column with
-// compile-time accumulator indices (no dynamic register indexing), and the
-// tile element an entry names is at the same place for every lane:
-//
-//  * S' (cols kernel): lanes own 32 consecutive columns of A.  Tiles of TILE
-//    rows x 32 columns arrive by TMA (cp.async.bulk.tensor) into a dense
-//    layout; an entry (row r) makes every lane read tile[r][lane]
-//    (conflict-free).  A producer warp runs a STAGES-deep mbarrier ring.
-//  * S  (rows kernel): lanes own 32 consecutive rows of A.  Tiles of 32 rows x
-//    TILE columns (= TILE rows of R) are copied with 4/8-byte cp.async into a
-//    row pitch of TILE+1 elements, so that lanes reading tile[lane][j] hit 32
-//    different banks.
-//
-// Results are staged in shared memory and written with coalesced stores.
+// GB300 mapping (both kernels stream A exactly once from HBM):
+//  * Persistent stream-K grid, one CTA per SM: the (block of A, tile of R)
+//    units are cut into equal contiguous ranges, so every SM streams the same
+//    number of bytes; a block split between two CTAs gets two contributions,
+//    added with red.global.add into a zeroed output (two terms onto zero:
+//    order-independent, so results are deterministic).
+//  * A warp owns <= NB output columns of R and keeps their sums in registers
+//    for the whole block; because a tile's entries are grouped by column, the
+//    warp walks them column by column with compile-time accumulator indices.
+//  * S' (cols kernel): lanes own VEC consecutive columns of A (one 16-byte
+//    vector).  Tiles of TILE rows x 32*VEC columns arrive by TMA into a dense
+//    layout; an entry (row r) makes each lane read one 16-byte vector of row
+//    r (conflict-free LDS.128).  One producer warp runs a STAGES-deep
+//    mbarrier ring; the tile's entries and column offsets ride along as bulk
+//    copies on the same barrier.
+//  * S (rows kernel): lanes own RPL = 4 rows of A (lane + 32 q).  Tiles of 128
+//    rows x TILE columns of A (= TILE rows of R) are copied by two producer
+//    warps with 4/8-byte cp.async into a row pitch of TILE + 1 elements, so
+//    that 32 lanes reading tile[row][j] hit 32 banks; completion is tracked
+//    with cp.async.mbarrier.arrive on the same ring.
 #include <cuda.h>
 
 #include <algorithm>
@@ -34,16 +38,37 @@
 namespace jls {
 
 template <typename T>
-__device__ __forceinline__ T flip(T v, uint32_t neg);
+struct V16;  // one 16-byte vector of T
 template <>
-__device__ __forceinline__ float flip<float>(float v, uint32_t neg) {
-  return __int_as_float(__float_as_int(v) ^ (int)(neg << 16));  // neg = 0 or 0x8000
-}
+struct V16<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
 template <>
-__device__ __forceinline__ double flip<double>(double v, uint32_t neg) {
-  const long long b = __double_as_longlong(v) ^ ((long long)neg << 48);
-  return __longlong_as_double(b);
+struct V16<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+
+__device__ __forceinline__ float lane_get(const float4& v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
+__device__ __forceinline__ double lane_get(const double2& v, int q) { return q == 0 ? v.x : v.y; }
+__device__ __forceinline__ void fma_into(float4& a, const float4& v, float s) {
+  a.x = fmaf(v.x, s, a.x);
+  a.y = fmaf(v.y, s, a.y);
+  a.z = fmaf(v.z, s, a.z);
+  a.w = fmaf(v.w, s, a.w);
+}
+__device__ __forceinline__ void fma_into(double2& a, const double2& v, double s) {
+  a.x = fma(v.x, s, a.x);
+  a.y = fma(v.y, s, a.y);
+}
+// +1 or -1 from the sign bit (0x8000) of an entry
+__device__ __forceinline__ float sgn_of(uint32_t en, float) {
+  return __int_as_float(0x3f800000 | ((en & 0x8000u) << 16));
+}
+__device__ __forceinline__ double sgn_of(uint32_t en, double) { return (en & 0x8000u) ? -1.0 : 1.0; }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
@@ -54,62 +79,72 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 __device__ __forceinline__ void cp_async_16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 
-// Walk the entries of columns [cw0, cw0 + nb) of one tile and accumulate.
-// LD is the element distance between consecutive entries' rows (cols kernel:
-// 32, lanes add `lane`), or 1 for the rows kernel (lane rows at lane*pitch).
-template <typename T, int NB, int ROWSTRIDE>
-__device__ __forceinline__ void accumulate_tile(T (&acc)[NB], const uint16_t* __restrict__ E,
-                                                const uint32_t* __restrict__ O, const T* __restrict__ X,
-                                                int cw0, int nb) {
-  uint32_t p = O[cw0];
+// accumulate a contribution into the zeroed output (<= 2 contributors per cell)
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+__device__ __forceinline__ void red_add1(float* p, float a) { atomicAdd(p, a); }
+__device__ __forceinline__ void red_add1(double* p, double a) { atomicAdd(p, a); }
+
+// Add scale * v[b] (b < nb) to output row `out_row` (columns cw0 + b).
+template <int NB>
+__device__ __forceinline__ void flush_row(float* out_row, const float (&v)[NB], int nb, float scale, bool vec_ok) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    if (b < nb) {
-      const uint32_t e = O[cw0 + b + 1];
-      T a0 = acc[b], a1 = T(0);
-      for (; p + 1 < e; p += 2) {
-        const uint32_t en0 = E[p], en1 = E[p + 1];
-        const T v0 = X[(en0 & 0x7fff) * ROWSTRIDE];
-        const T v1 = X[(en1 & 0x7fff) * ROWSTRIDE];
-        a0 += flip(v0, en0 & 0x8000);
-        a1 += flip(v1, en1 & 0x8000);
-      }
-      if (p < e) {
-        const uint32_t en0 = E[p];
-        a0 += flip(X[(en0 & 0x7fff) * ROWSTRIDE], en0 & 0x8000);
-        ++p;
-      }
-      acc[b] = a0 + a1;
+  for (int b = 0; b < NB; b += 4) {
+    if (b + 3 < nb && vec_ok) {
+      red_add4(out_row + b, v[b] * scale, v[b + 1] * scale, v[b + 2] * scale, v[b + 3] * scale);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (b + u < nb) red_add1(out_row + b + u, v[b + u] * scale);
     }
   }
+}
+template <int NB>
+__device__ __forceinline__ void flush_row(double* out_row, const double (&v)[NB], int nb, double scale, bool) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (b < nb) red_add1(out_row + b, v[b] * scale);
+}
+
+struct SplitK {  // stream-K range of this CTA
+  int64_t u0, u1;
+};
+__device__ __forceinline__ SplitK cta_range(int64_t units) {
+  const int64_t g = gridDim.x, b = blockIdx.x;
+  return {units * b / g, units * (b + 1) / g};
 }
 
 // ---------------------------------------------------------------------------
 // S' = A^T R : lanes over columns of A, TMA-fed.
 template <typename T, int TILE, int NB, int STAGES>
-__global__ void __launch_bounds__(17 * 32, 1)
+__global__ void __launch_bounds__(16 * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
                      const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
-                     int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES, T* __restrict__ St,
-                     int64_t ldSt, T scale, int* err) {
+                     int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
+                     T* __restrict__ St, int64_t ldSt, T scale, int* err) {
+  using VT = typename V16<T>::type;
+  constexpr int VEC = V16<T>::N;
+  constexpr int BW = 32 * VEC;  // columns of A per block
+  constexpr uint32_t TILE_BYTES = TILE * BW * sizeof(T);
   extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int BOXR = TILE < 256 ? TILE : 256;
-  constexpr uint32_t TILE_BYTES = TILE * 32 * sizeof(T);
-  // only the offsets [o_lo, o_lo + o_cnt) and the entries of columns
-  // [c_lo, c_hi) of each tile are staged (16-byte aligned supersets)
   const int o_lo = c_lo & ~3;
   const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
   const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
-  T* tiles = reinterpret_cast<T*>(smem);
-  uint16_t* sh_e = reinterpret_cast<uint16_t*>(smem + STAGES * TILE_BYTES);
-  uint32_t* sh_o = reinterpret_cast<uint32_t*>(smem + STAGES * (TILE_BYTES + E_BYTES));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * (TILE_BYTES + E_BYTES + O_BYTES));
+  uint8_t* tiles = smem;
+  uint8_t* sh_e = smem + STAGES * TILE_BYTES;
+  uint8_t* sh_o = sh_e + STAGES * E_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh_o + STAGES * O_BYTES);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j0 = (int64_t)blockIdx.x * 32;
   const int ntiles = (int)((rowsA + TILE - 1) / TILE);
+  const int64_t nblk = (colsA + BW - 1) / BW;
+  const SplitK rg = cta_range(nblk * ntiles);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -120,103 +155,153 @@ __global__ void __launch_bounds__(17 * 32, 1)
   }
   __syncthreads();
 
-  T acc[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) acc[b] = T(0);
-  const int cw0 = c_lo + warp * nbw;
-  const int nb = min(nbw, c_hi - cw0);
-
   if (warp == njobs) {  // ---- producer
     if (lane == 0) {
       tma_prefetch_desc(&tmA);
-      bool ok = true;
-      int issued = 0;
-      for (int t = 0; t < ntiles && ok; ++t) {
-        const int s = t % STAGES;
-        if (t >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((t / STAGES) - 1) & 1, err);
-        if (!ok) break;
+      int k = 0;
+      for (int64_t u = rg.u0; u < rg.u1; ++u, ++k) {
+        const int s = k % STAGES;
+        if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
+        const int64_t blk = u / ntiles;
+        const int t = (int)(u % ntiles);
         const uint32_t fb = full0 + 8 * s;
         const uint32_t* ot = offs + (int64_t)t * o_stride;
         const uint32_t e_al = __ldg(ot + c_lo) & ~7u;
         const uint32_t eb = ((__ldg(ot + c_hi) - e_al) * 2 + 15) & ~15u;
         if (eb > E_BYTES) {  // host sizing guarantees this never happens
           set_err(err, ERRF_BOUNDS);
-          ok = false;
           break;
         }
         mbar_arrive_expect_tx(fb, TILE_BYTES + eb + O_BYTES);
-        const uint32_t dst = smem_u32(tiles) + s * TILE_BYTES;
-#pragma unroll
-        for (int q = 0; q < TILE / BOXR; ++q)
-          tma_load_2d(dst + q * BOXR * 32 * sizeof(T), &tmA, fb, (int32_t)j0, (int32_t)(t * TILE + q * BOXR));
+        tma_load_2d(smem_u32(tiles) + s * TILE_BYTES, &tmA, fb, (int32_t)(blk * BW), t * TILE);
         if (eb) bulk_g2s(smem_u32(sh_e) + s * E_BYTES, ents + (int64_t)t * e_stride + e_al, eb, fb);
         bulk_g2s(smem_u32(sh_o) + s * O_BYTES, ot + o_lo, O_BYTES, fb);
-        issued = t + 1;
       }
-      // drain: never leave the CTA with copies in flight
-      for (int t = max(0, issued - STAGES); t < issued; ++t)
-        mbar_wait(full0 + 8 * (t % STAGES), (t / STAGES) & 1, err);
     }
   } else {  // ---- consumers
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = t % STAGES;
-      if (!mbar_wait(full0 + 8 * s, (t / STAGES) & 1, err)) break;
-      const uint32_t* O = sh_o + s * (O_BYTES / 4) - o_lo;  // indexed by absolute column
-      const uint32_t e_al = O[c_lo] & ~7u;
-      if (nb > 0)
-        accumulate_tile<T, NB, 32>(acc, sh_e + s * (E_BYTES / 2) - e_al, O, tiles + (size_t)s * TILE * 32 + lane,
-                                   cw0, nb);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty0 + 8 * s);
+    VT acc[NB];
+    const VT zero = {};
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[b] = zero;
+    const int cw0 = c_lo + warp * nbw;
+    const int nb = max(0, min(nbw, c_hi - cw0));
+    const bool vec_ok = ((ldSt | cw0) & 3) == 0;
+    int k = 0;
+    auto flush = [&](int64_t blk) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        const int64_t j = blk * BW + lane * VEC + q;
+        if (j < colsA) {
+          T v[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) v[b] = lane_get(acc[b], q);
+          flush_row<NB>(St + j * ldSt + cw0, v, nb, scale, vec_ok);
+        }
+      }
+    };
+    bool ok = true;
+    for (int64_t u = rg.u0; u < rg.u1 && ok;) {  // one block of A per outer iteration
+      const int64_t blk = u / ntiles;
+      const int64_t u_end = min64(rg.u1, (blk + 1) * ntiles);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) acc[b] = zero;
+      for (; u < u_end; ++u, ++k) {
+        const int s = k % STAGES;
+        if (!mbar_wait(full0 + 8 * s, (k / STAGES) & 1, err)) {
+          ok = false;
+          break;
+        }
+        if (nb > 0) {
+          const uint32_t* O = reinterpret_cast<const uint32_t*>(sh_o + s * O_BYTES) - o_lo;
+          const uint16_t* E = reinterpret_cast<const uint16_t*>(sh_e + s * E_BYTES) - (O[c_lo] & ~7u);
+          const T* X = reinterpret_cast<const T*>(tiles + s * TILE_BYTES) + lane * VEC;
+          uint32_t p = O[cw0];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            if (b < nb) {
+              const uint32_t e = O[cw0 + b + 1];
+              VT a2 = zero;
+              for (; p + 1 < e; p += 2) {
+                const uint32_t en0 = E[p], en1 = E[p + 1];
+                const VT v0 = *reinterpret_cast<const VT*>(X + (en0 & 0x7fffu) * BW);
+                const VT v1 = *reinterpret_cast<const VT*>(X + (en1 & 0x7fffu) * BW);
+                fma_into(acc[b], v0, sgn_of(en0, T()));
+                fma_into(a2, v1, sgn_of(en1, T()));
+              }
+              if (p < e) {
+                const uint32_t en0 = E[p];
+                fma_into(acc[b], *reinterpret_cast<const VT*>(X + (en0 & 0x7fffu) * BW), sgn_of(en0, T()));
+                ++p;
+              }
+              fma_into(acc[b], a2, T(1));
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+      }
+      if (ok && nb > 0) flush(blk);
     }
   }
-  __syncthreads();
-  // stage results: out[lane][col], pitch ncols + 1, then coalesced stores
-  const int ncols = c_hi - c_lo, pitch = ncols + 1;
-  T* out = tiles;
-  if (warp < njobs) {
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (b < nb) out[lane * pitch + warp * nbw + b] = acc[b] * scale;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 32 * ncols; q += blockDim.x) {
-    const int r = q / ncols, c = q % ncols;
-    if (j0 + r < colsA) St[(j0 + r) * ldSt + c_lo + c] = out[r * pitch + c];
-  }
+  __syncthreads();  // no CTA exits while its copies may still land in shared memory
 }
 
 // ---------------------------------------------------------------------------
-// S = A R : lanes over rows of A, cp.async-fed, padded pitch TILE + 1.
+// S = A R : lanes over rows of A (RPL rows each), cp.async-fed, pitch TILE + 1.
+constexpr int RPL = 4;  // rows per lane
+constexpr int ROWS_BLK = 32 * RPL;
+constexpr int NPROD = 2;  // producer warps
+
 template <typename T, int TILE, int NB, int STAGES>
 __global__ void __launch_bounds__(16 * 32, 1)
     sjlt_rows_kernel(const T* __restrict__ A, int64_t lda, int64_t rowsA, int64_t colsA,
                      const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
-                     int64_t o_stride, int c_lo, int c_hi, int nbw, uint32_t E_BYTES, T* __restrict__ S,
-                     int64_t ldS, T scale, int* err) {
-  extern __shared__ __align__(1024) uint8_t smem[];
+                     int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
+                     T* __restrict__ S, int64_t ldS, T scale, int* err) {
   constexpr int P = TILE + 1;
-  constexpr uint32_t TILE_BYTES = ((32 * P * sizeof(T)) + 127) / 128 * 128;
+  constexpr uint32_t TILE_BYTES = ((ROWS_BLK * P * sizeof(T)) + 127) / 128 * 128;
+  extern __shared__ __align__(1024) uint8_t smem[];
   const int o_lo = c_lo & ~3;
   const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
   const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
-  uint8_t* base_t = smem;
-  uint8_t* base_e = smem + STAGES * TILE_BYTES;
-  uint8_t* base_o = base_e + STAGES * E_BYTES;
+  uint8_t* tiles = smem;
+  uint8_t* sh_e = smem + STAGES * TILE_BYTES;
+  uint8_t* sh_o = sh_e + STAGES * E_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sh_o + STAGES * O_BYTES);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nthreads = blockDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
   const int ntiles = (int)((colsA + TILE - 1) / TILE);
+  const int64_t nblk = (rowsA + ROWS_BLK - 1) / ROWS_BLK;
+  const SplitK rg = cta_range(nblk * ntiles);
 
-  auto load_tile = [&](int t, int s) {
-    if (t < ntiles) {
-      const uint32_t dst = smem_u32(base_t + s * TILE_BYTES);
-      const int64_t jb = (int64_t)t * TILE;
-      for (int q = threadIdx.x; q < 32 * TILE; q += nthreads) {
-        const int r = q / TILE, c = q % TILE;
-        const bool in = (i0 + r < rowsA) && (jb + c < colsA);
-        const T* src = in ? A + (i0 + r) * lda + jb + c : A;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, NPROD * 32);
+      mbar_init(empty0 + 8 * s, njobs);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp >= njobs) {  // ---- producers: NPROD warps of cp.async
+    const int pt = threadIdx.x - njobs * 32;  // 0 .. NPROD*32-1
+    const int pw = pt >> 5;
+    int k = 0;
+    for (int64_t u = rg.u0; u < rg.u1; ++u, ++k) {
+      const int s = k % STAGES;
+      if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
+      const int64_t blk = u / ntiles;
+      const int t = (int)(u % ntiles);
+      const int64_t i0 = blk * ROWS_BLK, j0 = (int64_t)t * TILE;
+      const uint32_t dst = smem_u32(tiles) + s * TILE_BYTES;
+      // warp-chunks of 32 consecutive columns of one row: coalesced reads,
+      // consecutive banks on the shared-memory side
+      constexpr int CHUNKS = ROWS_BLK * (TILE / 32);
+      for (int g = pw; g < CHUNKS; g += NPROD) {
+        const int r = g / (TILE / 32), c = (g % (TILE / 32)) * 32 + lane;
+        const bool in = (i0 + r < rowsA) && (j0 + c < colsA);
+        const T* src = in ? A + (i0 + r) * lda + j0 + c : A;
         if (sizeof(T) == 4)
           cp_async_4(dst + (r * P + c) * 4, src, in ? 4 : 0);
         else
@@ -229,49 +314,72 @@ __global__ void __launch_bounds__(16 * 32, 1)
         set_err(err, ERRF_BOUNDS);
         eb = 0;
       }
-      const uint32_t de = smem_u32(base_e + s * E_BYTES);
+      const uint32_t de = smem_u32(sh_e) + s * E_BYTES;
       const uint8_t* se = reinterpret_cast<const uint8_t*>(ents + (int64_t)t * e_stride + e_al);
-      for (uint32_t q = threadIdx.x; q < eb / 16; q += nthreads) cp_async_16(de + q * 16, se + q * 16);
-      const uint32_t dof = smem_u32(base_o + s * O_BYTES);
+      for (uint32_t q = pt; q < eb / 16; q += NPROD * 32) cp_async_16(de + q * 16, se + q * 16);
+      const uint32_t dof = smem_u32(sh_o) + s * O_BYTES;
       const uint8_t* so = reinterpret_cast<const uint8_t*>(ot + o_lo);
-      for (uint32_t q = threadIdx.x; q < O_BYTES / 16; q += nthreads) cp_async_16(dof + q * 16, so + q * 16);
+      for (uint32_t q = pt; q < O_BYTES / 16; q += NPROD * 32) cp_async_16(dof + q * 16, so + q * 16);
+      cp_async_mbar_arrive(full0 + 8 * s);
     }
-    cp_async_commit();
-  };
-
+    cp_async_wait<0>();
+  } else {  // ---- consumers
+    T acc[RPL][NB];
 #pragma unroll
-  for (int s = 0; s < STAGES - 1; ++s) load_tile(s, s);
-
-  T acc[NB];
+    for (int q = 0; q < RPL; ++q)
 #pragma unroll
-  for (int b = 0; b < NB; ++b) acc[b] = T(0);
-  const int cw0 = c_lo + warp * nbw;
-  const int nb = min(nbw, c_hi - cw0);
-
-  for (int t = 0; t < ntiles; ++t) {
-    cp_async_wait<STAGES - 2>();
-    __syncthreads();
-    load_tile(t + STAGES - 1, (t + STAGES - 1) % STAGES);
-    const int s = t % STAGES;
-    const uint32_t* O = reinterpret_cast<const uint32_t*>(base_o + s * O_BYTES) - o_lo;
-    const uint32_t e_al = O[c_lo] & ~7u;
-    if (nb > 0)
-      accumulate_tile<T, NB, 1>(acc, reinterpret_cast<const uint16_t*>(base_e + s * E_BYTES) - e_al, O,
-                                reinterpret_cast<const T*>(base_t + s * TILE_BYTES) + lane * P, cw0, nb);
+      for (int b = 0; b < NB; ++b) acc[q][b] = T(0);
+    const int cw0 = c_lo + warp * nbw;
+    const int nb = max(0, min(nbw, c_hi - cw0));
+    const bool vec_ok = ((ldS | cw0) & 3) == 0;
+    int k = 0;
+    auto flush = [&](int64_t blk) {
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int64_t i = blk * ROWS_BLK + lane + 32 * q;
+        if (i < rowsA) flush_row<NB>(S + i * ldS + cw0, acc[q], nb, scale, vec_ok);
+      }
+    };
+    bool ok = true;
+    for (int64_t u = rg.u0; u < rg.u1 && ok;) {  // one block of A per outer iteration
+      const int64_t blk = u / ntiles;
+      const int64_t u_end = min64(rg.u1, (blk + 1) * ntiles);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[q][b] = T(0);
+      for (; u < u_end; ++u, ++k) {
+        const int s = k % STAGES;
+        if (!mbar_wait(full0 + 8 * s, (k / STAGES) & 1, err)) {
+          ok = false;
+          break;
+        }
+        if (nb > 0) {
+          const uint32_t* O = reinterpret_cast<const uint32_t*>(sh_o + s * O_BYTES) - o_lo;
+          const uint16_t* E = reinterpret_cast<const uint16_t*>(sh_e + s * E_BYTES) - (O[c_lo] & ~7u);
+          const T* X = reinterpret_cast<const T*>(tiles + s * TILE_BYTES) + lane * P;
+          uint32_t p = O[cw0];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            if (b < nb) {
+              const uint32_t e = O[cw0 + b + 1];
+              for (; p < e; ++p) {
+                const uint32_t en = E[p];
+                const T sg = sgn_of(en, T());
+                const T* x = X + (en & 0x7fffu);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) acc[q][b] = fma(x[q * 32 * P], sg, acc[q][b]);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+      }
+      if (ok && nb > 0) flush(blk);
+    }
   }
-  cp_async_wait<0>();
   __syncthreads();
-  const int ncols = c_hi - c_lo, pitch = ncols + 1;
-  T* out = reinterpret_cast<T*>(smem);
-#pragma unroll
-  for (int b = 0; b < NB; ++b)
-    if (b < nb) out[lane * pitch + warp * nbw + b] = acc[b] * scale;
-  __syncthreads();
-  for (int q = threadIdx.x; q < 32 * ncols; q += nthreads) {
-    const int r = q / ncols, c = q % ncols;
-    if (i0 + r < rowsA) S[(i0 + r) * ldS + c_lo + c] = out[r * pitch + c];
-  }
-  (void)err;
 }
 
 // ---------------------------------------------------------------------------
@@ -293,30 +401,46 @@ PFN_encodeTiled get_encode_tiled() {
   return fn;
 }
 
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  return sms;
+}
+
 namespace {
 
-constexpr int NB_SJLT = 32;
-constexpr int MAX_JOBS = 16;
+// 16 warps per CTA (4 per SM sub-partition, 128 registers each): the cols
+// kernel runs 15 consumer warps + 1 TMA producer, the rows kernel 14 consumer
+// warps + NPROD = 2 cp.async producers.  A consumer warp owns <= NB columns.
+constexpr int COLS_JOBS = 15;
+constexpr int ROWS_JOBS = 16 - NPROD;
+constexpr int NB_COLS = 20;
+template <typename T>
+constexpr int nb_rows() { return sizeof(T) == 4 ? 20 : 10; }
+constexpr int STAGES = 3;
 
 struct Jobs {
   int njobs, nbw;
 };
-Jobs plan_jobs(int ncols) {
-  int nj = (ncols + NB_SJLT - 1) / NB_SJLT;
-  nj = std::max(nj, std::min(4, ncols));
-  nj = std::min(nj, MAX_JOBS);
+Jobs plan_jobs(int ncols, int max_jobs) {
+  // spread the columns over as many warps as allowed (more warps hide more latency)
+  int nj = std::min(max_jobs, ncols);
   int nbw = (ncols + nj - 1) / nj;
   nj = (ncols + nbw - 1) / nbw;
   return {nj, nbw};
 }
 
-// Column ranges one launch can take: <= MAX_JOBS * NB columns, and few enough
-// blocks that STAGES tiles plus their entries fit in shared memory.  Each
-// launch streams A once; ranges are cut at block boundaries.
+// Column ranges one launch can take: <= jobs * NB columns and few enough
+// blocks that the staged entries fit.  Each launch streams A once; ranges are
+// cut at block boundaries.
 struct Range {
   int lo, hi, nblk;
 };
-std::vector<Range> plan_ranges(const sk_op* h, int c_lo, int c_hi, int max_blk) {
+std::vector<Range> plan_ranges(const sk_op* h, int c_lo, int c_hi, int max_blk, int max_cols) {
   std::vector<Range> out;
   int c = c_lo;
   while (c < c_hi) {
@@ -327,7 +451,7 @@ std::vector<Range> plan_ranges(const sk_op* h, int c_lo, int c_hi, int max_blk) 
       if (b_hi <= c) continue;
       if (b_lo >= c_hi) break;
       if (nblk == max_blk) break;
-      const int take_hi = std::min(std::min(b_hi, c_hi), c + MAX_JOBS * NB_SJLT);
+      const int take_hi = std::min(std::min(b_hi, c_hi), c + max_cols);
       if (take_hi <= hi) break;
       hi = take_hi;
       ++nblk;
@@ -339,41 +463,49 @@ std::vector<Range> plan_ranges(const sk_op* h, int c_lo, int c_hi, int max_blk) 
   return out;
 }
 
+template <typename T>
+int zero_columns(T* out, int64_t ld, int64_t rows, int c_lo, int c_hi, cudaStream_t s) {
+  JLS_CHECK_CUDA(cudaMemset2DAsync(out + c_lo, ld * sizeof(T), 0, (size_t)(c_hi - c_lo) * sizeof(T), rows, s));
+  return SK_OK;
+}
+
 template <typename T, int TILE>
 int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
                 int64_t ldSt, cudaStream_t s) {
-  constexpr int STAGES = 3;
+  constexpr int VEC = V16<T>::N, BW = 32 * VEC;
   PFN_encodeTiled enc = get_encode_tiled();
   if (!enc) return SK_ERR_DEVICE;
   CUtensorMap tm;
   const cuuint64_t gdim[2] = {(cuuint64_t)A->cols, (cuuint64_t)A->rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)(A->ld * sizeof(T))};
-  constexpr int BOXR = TILE < 256 ? TILE : 256;
-  const cuuint32_t box[2] = {32, (cuuint32_t)BOXR};
+  const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)TILE};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(&tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
                    const_cast<void*>(A->A), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return SK_ERR_ALIGN;
-  const size_t tile_b = (size_t)TILE * 32 * sizeof(T);
-  const size_t o_max = (MAX_JOBS * NB_SJLT + 8) * 4;
+  JLS_CHECK(zero_columns(St, ldSt, A->cols, c_lo, c_hi, s));
+  const size_t tile_b = (size_t)TILE * BW * sizeof(T);
+  const size_t o_max = (COLS_JOBS * NB_COLS + 8) * 4;
   const size_t e_blk = (size_t)h->alpha * TILE * 2;
-  const size_t budget = 227 * 1024 - 2 * STAGES * 8;
-  const long fit = ((long)budget / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  const long fit = ((long)(227 * 1024 - 2 * STAGES * 8) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
   if (fit < 1) return SK_ERR_UNSUPPORTED;
-  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit)) {
-    const Jobs J = plan_jobs(rg.hi - rg.lo);
+  // at most one CTA per block of A keeps every block within two contiguous
+  // CTA ranges, i.e. at most two contributions per output cell
+  const int64_t nblk = (A->cols + BW - 1) / BW;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, COLS_JOBS * NB_COLS)) {
+    const Jobs J = plan_jobs(rg.hi - rg.lo, COLS_JOBS);
     const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
     const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
-    const size_t out_b = (size_t)32 * (rg.hi - rg.lo + 1) * sizeof(T);
-    if (smem > 227 * 1024 || out_b > STAGES * tile_b) return SK_ERR_UNSUPPORTED;
-    auto kern = sjlt_cols_kernel<T, TILE, NB_SJLT, STAGES>;
+    if (smem > 227 * 1024) return SK_ERR_UNSUPPORTED;
+    auto kern = sjlt_cols_kernel<T, TILE, NB_COLS, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = (unsigned)((A->cols + 31) / 32);
     kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride,
-                                                rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err); note_launch();
+                                                rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err);
+    note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
   return SK_OK;
@@ -382,25 +514,27 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
 template <typename T, int TILE>
 int launch_rows(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* S, int64_t ldS,
                 cudaStream_t s) {
-  constexpr int STAGES = 3;
-  const size_t tile_b = ((32 * (TILE + 1) * sizeof(T)) + 127) / 128 * 128;
-  const size_t o_max = (MAX_JOBS * NB_SJLT + 8) * 4;
+  JLS_CHECK(zero_columns(S, ldS, A->rows, c_lo, c_hi, s));
+  constexpr int NB = nb_rows<T>();
+  const size_t tile_b = ((ROWS_BLK * (TILE + 1) * sizeof(T)) + 127) / 128 * 128;
+  const size_t o_max = (ROWS_JOBS * NB + 8) * 4;
   const size_t e_blk = (size_t)h->alpha * TILE * 2;
-  const long fit = ((long)(227 * 1024) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  const long fit = ((long)(227 * 1024 - 2 * STAGES * 8) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
   if (fit < 1) return SK_ERR_UNSUPPORTED;
-  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit)) {
-    const Jobs J = plan_jobs(rg.hi - rg.lo);
+  const int64_t nblk = (A->rows + ROWS_BLK - 1) / ROWS_BLK;  // see launch_cols
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, ROWS_JOBS * NB)) {
+    const Jobs J = plan_jobs(rg.hi - rg.lo, ROWS_JOBS);
     const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
-    const size_t smem = STAGES * (tile_b + e_bytes + o_bytes);
-    const size_t out_b = (size_t)32 * (rg.hi - rg.lo + 1) * sizeof(T);
-    if (smem > 227 * 1024 || out_b > smem) return SK_ERR_UNSUPPORTED;
-    auto kern = sjlt_rows_kernel<T, TILE, NB_SJLT, STAGES>;
+    const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
+    if (smem > 227 * 1024) return SK_ERR_UNSUPPORTED;
+    auto kern = sjlt_rows_kernel<T, TILE, NB, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = (unsigned)((A->rows + 31) / 32);
-    kern<<<grid, J.njobs * 32, smem, s>>>(static_cast<const T*>(A->A), A->ld, A->rows, A->cols, C.ents, C.offs,
-                                          C.e_stride, C.o_stride, rg.lo, rg.hi, J.nbw, e_bytes, S, ldS, scale,
-                                          h->d_err); note_launch();
+    kern<<<grid, (J.njobs + NPROD) * 32, smem, s>>>(static_cast<const T*>(A->A), A->ld, A->rows, A->cols, C.ents,
+                                                    C.offs, C.e_stride, C.o_stride, rg.lo, rg.hi, J.nbw, J.njobs,
+                                                    e_bytes, S, ldS, scale, h->d_err);
+    note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
   return SK_OK;
