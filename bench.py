@@ -93,7 +93,7 @@ class Clocks:
 class Step:
     """Everything one step does, with per-call CUDA events."""
 
-    def __init__(self, A, n, prec_dense, timed_events=True):
+    def __init__(self, A, n, prec_dense, timed_events=True, only="all"):
         import torch
         from paper_2302_01977_gb300 import jlsketch as jl
         self.jl, self.torch = jl, torch
@@ -107,6 +107,7 @@ class Step:
         self.adSt = torch.empty((n, w["d_max"]), dtype=torch.float32, device=dev)
         self.events = []  # (label, start, end)
         self.timed = timed_events
+        self.only = only
         self.adaptive_info = None
 
     def _ev(self, label, fn):
@@ -127,17 +128,25 @@ class Step:
         try:
             ops = [("sjlt", "sjlt_block", w["alpha"], jl.SK_PREC_NATIVE),
                    ("srht", "srht", 1, self.prec_dense), ("gauss", "gauss", 1, self.prec_dense)]
+            passes = 0
             for name, kind, alpha, prec in ops:
+                if self.only not in ("all", name):
+                    continue
+                passes += 2
                 h = jl.sketch_create(kind, self.n, w["d"], alpha, seed, w["d"])
                 hs.append(h)
                 S, St = self.bufs[name + "_S"], self.bufs[name + "_St"]
                 self._ev(f"{name}.S", lambda: jl.sketch_apply(h, A, jl.SK_S, prec, S=S))
                 self._ev(f"{name}.St", lambda: jl.sketch_apply(h, A, jl.SK_ST, prec, St=St))
+            if self.only not in ("all", "adaptive"):
+                return passes
             # adaptive SJLT run (Algorithm 1 on the global sketch)
             h = jl.sketch_create("sjlt_block", self.n, w["d0"] + w["dd"], w["alpha"], seed + 1, w["d_max"])
             hs.append(h)
             self._ev("adaptive.apply", lambda: jl.sketch_apply(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
-            d, passes, hist = w["d0"], 2, []
+            d, hist = w["d0"], []
+            passes += 2
+            ad_passes = 2
             while True:
                 wd = d + w["dd"]
                 s1 = jl.adaptive_norm_test(h, 0, self.adS[:, :wd], w["dd"], w["eps_rel"], w["eps_abs"])
@@ -150,10 +159,11 @@ class Step:
                 self._ev("adaptive.increment",
                          lambda: jl.sketch_apply_increment(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
                 passes += 2
+                ad_passes += 2
                 d += w["dd"]
-            self.adaptive_info = dict(d_reached=d + w["dd"], converged=bool(converged), passes_over_A=passes,
+            self.adaptive_info = dict(d_reached=d + w["dd"], converged=bool(converged), passes_over_A=ad_passes,
                                       ratios=[(int(a), round(b, 6), round(c, 6)) for a, b, c in hist])
-            return 6 + passes  # passes over A in this step
+            return passes  # passes over A in this step
         finally:
             for h in hs:
                 jl.sketch_destroy(h)
@@ -231,7 +241,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     w = WORKLOAD
-    n = w["n"]
+    n = w["n"] = args.n
+    w["name"] = f"kernel_fp32_n{n}"
     X = inputs.points(n, seed=w["seed"])
     Y = inputs.points(n, seed=w["seed"] + 1000)
     A = torch.empty((n, n), dtype=torch.float32, device="cuda")
@@ -248,7 +259,7 @@ def run_ours(args):
             prec_dense = jl.SK_PREC_BF16X2
         except jl.JLSketchError:
             pass
-    step = Step(A, n, prec_dense)
+    step = Step(A, n, prec_dense, only=args.only)
     for i in range(args.warmup):
         step.run(i)
     torch.cuda.synchronize()
@@ -284,14 +295,20 @@ def run_ours(args):
 
     per_op = {}
     for name in ("sjlt", "srht", "gauss"):
+        if f"{name}.S" not in times:
+            continue
         ts, tst = statistics.median(times[f"{name}.S"]), statistics.median(times[f"{name}.St"])
         per_op[name] = {"S_gbs": round(bytes_a / ts / 1e6, 1), "St_gbs": round(bytes_a / tst / 1e6, 1),
                         "S_ms": round(ts, 4), "St_ms": round(tst, 4),
                         "pct_hbm_S": round(100 * bytes_a / ts / 1e6 / hbm, 1),
                         "pct_hbm_St": round(100 * bytes_a / tst / 1e6 / hbm, 1)}
-    per_op["srht"]["prec"] = per_op["gauss"]["prec"] = "bf16x2" if prec_dense == jl.SK_PREC_BF16X2 else "fp32"
-    per_op["sjlt"]["prec"] = "fp32"
-    per_op["adaptive_sjlt"] = dict(step.adaptive_info)
+    for name in ("srht", "gauss"):
+        if name in per_op:
+            per_op[name]["prec"] = "bf16x2" if prec_dense == jl.SK_PREC_BF16X2 else "fp32"
+    if "sjlt" in per_op:
+        per_op["sjlt"]["prec"] = "fp32"
+    if step.adaptive_info:
+        per_op["adaptive_sjlt"] = dict(step.adaptive_info)
 
     # dominant kernel: the class with the largest total time in the timed region
     totals = {k: sum(v) for k, v in times.items()}
@@ -302,7 +319,8 @@ def run_ours(args):
     ccs_bytes = n * w["alpha"] * 2 + (n // 512) * (w["d"] + 4) * 4
     # the SJLT kernels are the ones the roofline tracks (HBM-bound, one pass of A)
     sj = "sjlt_cols" if cls["sjlt_cols"] >= cls["sjlt_rows"] else "sjlt_rows"
-    t_launch = statistics.median(times["sjlt.St" if sj == "sjlt_cols" else "sjlt.S"]) / 1e3
+    key = "sjlt.St" if sj == "sjlt_cols" else "sjlt.S"
+    t_launch = statistics.median(times[key]) / 1e3 if key in times else float("inf")
     alg_bytes = bytes_a + d_out_bytes + ccs_bytes
     achieved = alg_bytes / t_launch / 1e9
     prof = traffic_from_profile("sjlt_apply.cu")
@@ -331,7 +349,7 @@ def run_ours(args):
     if not args.no_e2e:
         A_host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
         A_host.copy_(A)
-        step_e = Step(A, n, prec_dense, timed_events=False)
+        step_e = Step(A, n, prec_dense, timed_events=False, only=args.only)
         outs = list(step_e.bufs.values()) + [step_e.adS, step_e.adSt]
         hosts = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
         torch.cuda.synchronize()
@@ -357,7 +375,7 @@ def run_ours(args):
         del A_host, hosts
 
     # ---- CPU baseline (oracle) on rank 0, N = 1 only; also checks the GPU results
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.only == "all":
         gpu = {}
         seed = w["seed"] + 7919 * (args.warmup + args.steps - 1)
         for name, kind, alpha, prec in (("sjlt", "sjlt_block", w["alpha"], 0), ("srht", "srht", 1, prec_dense),
@@ -421,6 +439,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-rows", type=int, default=128)
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"],
+                    help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
+    ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",
+                    help="restrict the step (profiling captures); the benchmark runs all")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

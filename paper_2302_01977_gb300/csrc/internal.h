@@ -17,6 +17,7 @@ constexpr int SJLT_TILE_F32 = 128;
 constexpr int SJLT_TILE_F64 = 64;
 constexpr int SJLT_MAX_ALPHA = 32;
 constexpr int MAX_D = 8192;
+constexpr int MAX_BLOCKS = 256;  // SJLT blocks (initial + increments) a handle can hold
 
 // Tiled CCS of R (Sec. 6.1's compressed column storage, cut into tiles of
 // `tile` rows): for tile t, entries[t*e_stride + p] = row_in_tile | sign<<15

@@ -124,6 +124,7 @@ int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t al
   int rc = cuda_status(cudaMalloc(&h->d_err, sizeof(int)));
   if (rc == SK_OK) rc = cuda_status(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   if (rc == SK_OK && sjlt) rc = gen_sjlt_block(h, 0, 0, d, s);
+  if (rc == SK_OK && sjlt) rc = build_ccs(h, 0, s);  // tiled CCS for FP32 tiles
   if (rc == SK_OK && kind == SK_SRHT) rc = gen_srht(h, 0, d, s);
   if (rc != SK_OK) {
     free_handle(h);
@@ -141,11 +142,13 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream) {
   if (sjlt && delta_d < h->alpha) return SK_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int d_old = h->d_total;
+  if (sjlt && (int)h->blocks.size() >= MAX_BLOCKS) return SK_ERR_UNSUPPORTED;
   if (sjlt) JLS_CHECK(gen_sjlt_block(h, (int)h->blocks.size(), d_old, delta_d, s));
   if (h->kind == SK_SRHT) JLS_CHECK(gen_srht(h, d_old, d_old + delta_d, s));
   h->blocks.push_back(delta_d);
   h->d_total = d_old + delta_d;
   h->pending_old_d = d_old;
+  if (sjlt) JLS_CHECK(build_ccs(h, 0, s));
   return SK_OK;
 }
 

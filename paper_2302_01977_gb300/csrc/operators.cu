@@ -74,7 +74,7 @@ __global__ void sjlt_draw_kernel(int64_t n, int alpha, int width, int block_cons
 
 int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s) {
   if (block >= h->sjlt_blocks_cap) {
-    const int new_cap = std::max(4, 2 * h->sjlt_blocks_cap);
+    const int new_cap = std::max(8, 2 * h->sjlt_blocks_cap);
     int32_t* p = nullptr;
     const size_t per = (size_t)h->n * h->alpha * sizeof(int32_t);
     JLS_CHECK_CUDA(cudaMalloc(&p, per * new_cap));
@@ -98,25 +98,33 @@ int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s) 
 
 // ---------------------------------------------------------------------------
 // Tiled CCS build: one CTA per tile of `tile` rows of R.  Each thread owns
-// columns c = tid, tid + blockDim, ...; blocks occupy disjoint column ranges,
-// so column c is only looked up in its own block's alpha slots.  Pass 1
-// counts, a CTA scan turns counts into offsets, pass 2 writes the entries of
-// each column in ascending row order (deterministic).
+// columns c = tid, tid + blockDim, ...; blocks occupy disjoint column ranges
+// (offsets boff[0..nblocks]), so column c is only looked up in its own
+// block's alpha slots.  Pass 1 counts, a CTA scan turns counts into offsets,
+// pass 2 writes the entries of each column in ascending row order
+// (deterministic).
+struct BlockOffsets {
+  int n;
+  int off[MAX_BLOCKS + 1];
+};
+
 __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha,
-                                 const int* __restrict__ blk_of_col, const int* __restrict__ blk_off,
-                                 int d_total, int tile, int64_t e_stride, int64_t o_stride,
-                                 uint16_t* __restrict__ out_e, uint32_t* __restrict__ out_o) {
+                                 const __grid_constant__ BlockOffsets bo, int d_total, int tile, int64_t e_stride,
+                                 int64_t o_stride, uint16_t* __restrict__ out_e, uint32_t* __restrict__ out_o) {
   extern __shared__ uint32_t sh_cnt[];  // d_total + 1
   const int t = blockIdx.x;
   const int64_t r0 = (int64_t)t * tile;
   const int rows = (int)min64(tile, n - r0);
+  auto block_of = [&](int c) {
+    int b = 0;
+    while (b + 1 < bo.n && bo.off[b + 1] <= c) ++b;
+    return b;
+  };
   for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
-    const int b = blk_of_col[c];
-    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    const int32_t* base = ents + ((int64_t)block_of(c) * n + r0) * alpha;
     uint32_t cnt = 0;
     for (int r = 0; r < rows; ++r)
-      for (int k = 0; k < alpha; ++k)
-        cnt += ((base[(int64_t)r * alpha + k] & 0x7fffffff) == c);
+      for (int k = 0; k < alpha; ++k) cnt += ((base[(int64_t)r * alpha + k] & 0x7fffffff) == c);
     sh_cnt[c] = cnt;
   }
   __syncthreads();
@@ -134,8 +142,7 @@ __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, in
   uint16_t* oe = out_e + (int64_t)t * e_stride;
   for (int c = threadIdx.x; c <= d_total; c += blockDim.x) oo[c] = sh_cnt[c];
   for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
-    const int b = blk_of_col[c];
-    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    const int32_t* base = ents + ((int64_t)block_of(c) * n + r0) * alpha;
     uint32_t pos = sh_cnt[c];
     for (int r = 0; r < rows; ++r)
       for (int k = 0; k < alpha; ++k) {
@@ -143,7 +150,6 @@ __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, in
         if ((e & 0x7fffffff) == c) oe[pos++] = (uint16_t)(r | ((e < 0) ? 0x8000 : 0));
       }
   }
-  (void)blk_off;
 }
 
 int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
@@ -151,6 +157,7 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   const int tile = which_tile == 0 ? SJLT_TILE_F32 : SJLT_TILE_F64;
   if (C.built_d == h->d_total && C.tile == tile) return SK_OK;
   const int B = (int)h->blocks.size();
+  if (B > MAX_BLOCKS) return SK_ERR_UNSUPPORTED;
   C.tile = tile;
   C.ntiles = (int)((h->n + tile - 1) / tile);
   C.e_stride = ((int64_t)h->alpha * B * tile + 7) / 8 * 8;
@@ -160,39 +167,32 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   if (eb > C.ents_cap) {
     if (C.ents) cudaFree(C.ents);
     C.ents = nullptr;
+    C.ents_cap = 0;
     JLS_CHECK_CUDA(cudaMalloc(&C.ents, eb));
     C.ents_cap = eb;
   }
   if (ob > C.offs_cap) {
     if (C.offs) cudaFree(C.offs);
     C.offs = nullptr;
+    C.offs_cap = 0;
     JLS_CHECK_CUDA(cudaMalloc(&C.offs, ob));
     C.offs_cap = ob;
   }
-  // column -> block map (host-built, tiny)
-  std::vector<int> boc(h->d_total), boff(B);
+  BlockOffsets bo;
+  bo.n = B;
   int off = 0;
   for (int b = 0; b < B; ++b) {
-    boff[b] = off;
-    for (int c = 0; c < h->blocks[b]; ++c) boc[off + c] = b;
+    bo.off[b] = off;
     off += h->blocks[b];
   }
-  int* d_boc = nullptr;
-  int* d_boff = nullptr;
-  JLS_CHECK_CUDA(cudaMalloc(&d_boc, sizeof(int) * (h->d_total + B)));
-  d_boff = d_boc + h->d_total;
-  JLS_CHECK_CUDA(cudaMemcpyAsync(d_boc, boc.data(), sizeof(int) * h->d_total, cudaMemcpyHostToDevice, s));
-  JLS_CHECK_CUDA(cudaMemcpyAsync(d_boff, boff.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  bo.off[B] = off;
   const size_t shm = sizeof(uint32_t) * (h->d_total + 1);
   if (shm > 48 * 1024)
     JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)shm));
-  ccs_build_kernel<<<C.ntiles, 512, shm, s>>>(h->sjlt_ents, h->n, h->alpha, d_boc, d_boff,
-                                              h->d_total, tile, C.e_stride, C.o_stride, C.ents,
-                                              C.offs); note_launch();
+  ccs_build_kernel<<<C.ntiles, 256, shm, s>>>(h->sjlt_ents, h->n, h->alpha, bo, h->d_total, tile, C.e_stride,
+                                              C.o_stride, C.ents, C.offs); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
-  JLS_CHECK_CUDA(cudaStreamSynchronize(s));  // the pageable host vectors above die here
-  cudaFree(d_boc);
   C.built_d = h->d_total;
   return SK_OK;
 }
