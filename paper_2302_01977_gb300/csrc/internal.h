@@ -20,16 +20,22 @@ constexpr int MAX_D = 8192;
 constexpr int MAX_BLOCKS = 256;  // SJLT blocks (initial + increments) a handle can hold
 
 // Tiled CCS of R (Sec. 6.1's compressed column storage, cut into tiles of
-// `tile` rows): for tile t, entries[t*e_stride + p] = row_in_tile | sign<<15
-// sorted by column (rows ascending inside a column), and
-// offs[t*o_stride + c] = first entry of column c (offs[.. + d_total] = count).
+// `tile` rows): for tile t, entries[t*e_stride + p] sorted by column (rows
+// ascending inside a column), and offs[t*o_stride + c] = first entry of
+// column c (offs[.. + d_total] = count).  An entry for row r of the tile is a
+// 16-byte record read with one shared-memory load by the apply kernels:
+//   x = r * CCS_ROW_BYTES   (byte offset of row r in an S' kernel tile)
+//   y, z = the sign as +-1.0 (FP32 tiles: the float twice; FP64 tiles: the
+//          double's low and high words)
+//   w = r * element size    (byte offset of column r in an S kernel tile row)
+constexpr int CCS_ROW_BYTES = 512;  // S' tiles: 128 FP32 or 64 FP64 columns per row
 struct TiledCcs {
   int tile = 0;
   int built_d = -1;           // d_total it was built for
   int ntiles = 0;
-  int64_t e_stride = 0;       // uint16 entries per tile (multiple of 8)
+  int64_t e_stride = 0;       // entries per tile
   int64_t o_stride = 0;       // uint32 offsets per tile (multiple of 4)
-  uint16_t* ents = nullptr;
+  uint4* ents = nullptr;
   uint32_t* offs = nullptr;
   size_t ents_cap = 0, offs_cap = 0;  // bytes
 };

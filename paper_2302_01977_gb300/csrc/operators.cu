@@ -109,8 +109,9 @@ struct BlockOffsets {
 };
 
 __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha,
-                                 const __grid_constant__ BlockOffsets bo, int d_total, int tile, int64_t e_stride,
-                                 int64_t o_stride, uint16_t* __restrict__ out_e, uint32_t* __restrict__ out_o) {
+                                 const __grid_constant__ BlockOffsets bo, int d_total, int tile, int esize,
+                                 int64_t e_stride, int64_t o_stride, uint4* __restrict__ out_e,
+                                 uint32_t* __restrict__ out_o) {
   extern __shared__ uint32_t sh_cnt[];  // d_total + 1
   const int t = blockIdx.x;
   const int64_t r0 = (int64_t)t * tile;
@@ -139,7 +140,7 @@ __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, in
   }
   __syncthreads();
   uint32_t* oo = out_o + (int64_t)t * o_stride;
-  uint16_t* oe = out_e + (int64_t)t * e_stride;
+  uint4* oe = out_e + (int64_t)t * e_stride;
   for (int c = threadIdx.x; c <= d_total; c += blockDim.x) oo[c] = sh_cnt[c];
   for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
     const int32_t* base = ents + ((int64_t)block_of(c) * n + r0) * alpha;
@@ -147,7 +148,19 @@ __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, in
     for (int r = 0; r < rows; ++r)
       for (int k = 0; k < alpha; ++k) {
         const int32_t e = base[(int64_t)r * alpha + k];
-        if ((e & 0x7fffffff) == c) oe[pos++] = (uint16_t)(r | ((e < 0) ? 0x8000 : 0));
+        if ((e & 0x7fffffff) == c) {
+          // {S' offset of row r, sign, sign, S offset of row r}, see TiledCcs
+          uint4 rec;
+          rec.x = (uint32_t)r * CCS_ROW_BYTES;
+          rec.w = (uint32_t)(r * esize);
+          if (esize == 4) {
+            rec.y = rec.z = (e < 0) ? 0xbf800000u : 0x3f800000u;
+          } else {
+            rec.y = 0u;
+            rec.z = (e < 0) ? 0xbff00000u : 0x3ff00000u;
+          }
+          oe[pos++] = rec;
+        }
       }
   }
 }
@@ -160,9 +173,9 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   if (B > MAX_BLOCKS) return SK_ERR_UNSUPPORTED;
   C.tile = tile;
   C.ntiles = (int)((h->n + tile - 1) / tile);
-  C.e_stride = ((int64_t)h->alpha * B * tile + 7) / 8 * 8;
+  C.e_stride = (int64_t)h->alpha * B * tile;
   C.o_stride = ((int64_t)h->d_total + 1 + 3) / 4 * 4;
-  const size_t eb = (size_t)C.e_stride * C.ntiles * sizeof(uint16_t);
+  const size_t eb = (size_t)C.e_stride * C.ntiles * sizeof(uint4);
   const size_t ob = (size_t)C.o_stride * C.ntiles * sizeof(uint32_t);
   if (eb > C.ents_cap) {
     if (C.ents) cudaFree(C.ents);
@@ -190,8 +203,9 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   if (shm > 48 * 1024)
     JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)shm));
-  ccs_build_kernel<<<C.ntiles, 256, shm, s>>>(h->sjlt_ents, h->n, h->alpha, bo, h->d_total, tile, C.e_stride,
-                                              C.o_stride, C.ents, C.offs); note_launch();
+  ccs_build_kernel<<<C.ntiles, 256, shm, s>>>(h->sjlt_ents, h->n, h->alpha, bo, h->d_total, tile,
+                                              which_tile == 0 ? 4 : 8, C.e_stride, C.o_stride, C.ents, C.offs);
+  note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   C.built_d = h->d_total;
   return SK_OK;

@@ -1,29 +1,34 @@
 // sjlt_apply.cu -- S = A R and S' = A^T R for an SJLT R (Sec. 6.3), sm_103a.
 //
 // R is held as a tiled compressed-column structure (Sec. 6.1's CCS of B+ and
-// B-, merged with a sign bit and cut into tiles of TILE rows of R): for each
-// tile, the entries (row-in-tile, sign) sorted by column.  No products with
-// the values of R: every entry adds or subtracts elements of A, and the scale
-// 1/sqrt(alpha * blocks) is applied once when results are written, as in the
-// paper's binary-matrix design.
+// B-, merged with the sign and cut into tiles of TILE rows of R; see
+// TiledCcs): for each tile, the entries of each column of R in row order.
+// Every entry adds or subtracts elements of A (the +-1 is applied by a fused
+// multiply-add with the entry's sign), and the scale 1/sqrt(alpha * blocks) is
+// applied once when results are written, as in the paper's binary-matrix
+// design.
 //
 // GB300 mapping (both kernels stream A exactly once from HBM):
-//  * Persistent stream-K grid, one CTA per SM: the (block of A, tile of R)
-//    units are cut into equal contiguous ranges, so every SM streams the same
-//    number of bytes; a block split between two CTAs gets two contributions,
-//    added with red.global.add into a zeroed output (two terms onto zero:
-//    order-independent, so results are deterministic).
-//  * A warp owns <= NB output columns of R and keeps their sums in registers
-//    for the whole block; because a tile's entries are grouped by column, the
-//    warp walks them column by column with compile-time accumulator indices.
+//  * Persistent stream-K grid, at most one CTA per SM: the (block of A, tile
+//    of R) units are cut into equal contiguous ranges, so every SM streams the
+//    same number of bytes; a block split between two CTAs gets two
+//    contributions, added with red.global.add into a zeroed output (two terms
+//    onto zero: order-independent, so results are deterministic).
+//  * A consumer warp owns <= NB output columns of R and keeps their sums in
+//    registers for the whole block; because a tile's entries are grouped by
+//    column, the warp walks them column by column with compile-time
+//    accumulator indices.  Each entry is one broadcast 16-byte shared load
+//    (byte offset + sign), one 32-bit add for the address, one data load and
+//    two paired FP32 FMAs (FFMA2).  Each CTA has 16 warps (4 per SM
+//    sub-partition) so that every thread can hold 128 registers.
 //  * S' (cols kernel): lanes own VEC consecutive columns of A (one 16-byte
 //    vector).  Tiles of TILE rows x 32*VEC columns arrive by TMA into a dense
-//    layout; an entry (row r) makes each lane read one 16-byte vector of row
-//    r (conflict-free LDS.128).  One producer warp runs a STAGES-deep
-//    mbarrier ring; the tile's entries and column offsets ride along as bulk
-//    copies on the same barrier.
+//    layout; an entry makes each lane read one 16-byte vector of row r
+//    (conflict-free).  One producer warp runs a STAGES-deep mbarrier ring; the
+//    tile's entries and column offsets ride along as bulk copies on the same
+//    barrier.
 //  * S (rows kernel): lanes own RPL = 4 rows of A (lane + 32 q).  Tiles of 128
-//    rows x TILE columns of A (= TILE rows of R) are copied by two producer
+//    rows x TILE columns of A (= TILE rows of R) are copied by NPROD producer
 //    warps with 4/8-byte cp.async into a row pitch of TILE + 1 elements, so
 //    that 32 lanes reading tile[row][j] hit 32 banks; completion is tracked
 //    with cp.async.mbarrier.arrive on the same ring.
@@ -36,39 +41,6 @@
 #include "internal.h"
 
 namespace jls {
-
-template <typename T>
-struct V16;  // one 16-byte vector of T
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int N = 4;
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int N = 2;
-};
-
-__device__ __forceinline__ float lane_get(const float4& v, int q) {
-  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ double lane_get(const double2& v, int q) { return q == 0 ? v.x : v.y; }
-__device__ __forceinline__ void fma_into(float4& a, const float4& v, float s) {
-  a.x = fmaf(v.x, s, a.x);
-  a.y = fmaf(v.y, s, a.y);
-  a.z = fmaf(v.z, s, a.z);
-  a.w = fmaf(v.w, s, a.w);
-}
-__device__ __forceinline__ void fma_into(double2& a, const double2& v, double s) {
-  a.x = fma(v.x, s, a.x);
-  a.y = fma(v.y, s, a.y);
-}
-// +1 or -1 from the sign bit (0x8000) of an entry
-__device__ __forceinline__ float sgn_of(uint32_t en, float) {
-  return __int_as_float(0x3f800000 | ((en & 0x8000u) << 16));
-}
-__device__ __forceinline__ double sgn_of(uint32_t en, double) { return (en & 0x8000u) ? -1.0 : 1.0; }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
@@ -119,25 +91,57 @@ __device__ __forceinline__ SplitK cta_range(int64_t units) {
   return {units * b / g, units * (b + 1) / g};
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double sign_d(const uint4& r) { return __hiloint2double((int)r.z, (int)r.y); }
+
 // ---------------------------------------------------------------------------
 // S' = A^T R : lanes over columns of A, TMA-fed.
+// Accumulators per bucket: FP32 -> 2 float2 (the lane's 4 columns),
+//                          FP64 -> 2 doubles (the lane's 2 columns).
+template <typename T>
+struct ColsAcc;
+template <>
+struct ColsAcc<float> {
+  float2 a, b;
+  __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
+  __device__ __forceinline__ void add(uint32_t xaddr, const uint4& r) {
+    const float4 v = lds_f4(xaddr + r.x);
+    const float2 s = f2(__uint_as_float(r.y), __uint_as_float(r.z));
+    a = __ffma2_rn(f2(v.x, v.y), s, a);
+    b = __ffma2_rn(f2(v.z, v.w), s, b);
+  }
+  __device__ __forceinline__ float get(int q) const { return q == 0 ? a.x : q == 1 ? a.y : q == 2 ? b.x : b.y; }
+};
+template <>
+struct ColsAcc<double> {
+  double a, b;
+  __device__ __forceinline__ void zero() { a = b = 0.0; }
+  __device__ __forceinline__ void add(uint32_t xaddr, const uint4& r) {
+    const double2 v = lds_d2(xaddr + r.x);
+    const double s = sign_d(r);
+    a = fma(v.x, s, a);
+    b = fma(v.y, s, b);
+  }
+  __device__ __forceinline__ double get(int q) const { return q == 0 ? a : b; }
+};
+
 template <typename T, int TILE, int NB, int STAGES>
 __global__ void __launch_bounds__(16 * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
-                     const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
+                     const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
                      int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
                      T* __restrict__ St, int64_t ldSt, T scale, int* err) {
-  using VT = typename V16<T>::type;
-  constexpr int VEC = V16<T>::N;
+  constexpr int VEC = 16 / sizeof(T);
   constexpr int BW = 32 * VEC;  // columns of A per block
   constexpr uint32_t TILE_BYTES = TILE * BW * sizeof(T);
+  static_assert(BW * sizeof(T) == CCS_ROW_BYTES, "entry offsets assume 512-byte tile rows");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int o_lo = c_lo & ~3;
   const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
   const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
-  uint8_t* tiles = smem;
-  uint8_t* sh_e = smem + STAGES * TILE_BYTES;
-  uint8_t* sh_o = sh_e + STAGES * E_BYTES;
+  const uint32_t tiles_sa = smem_u32(smem);
+  const uint32_t ents_sa = tiles_sa + STAGES * TILE_BYTES;
+  uint8_t* sh_o = smem + STAGES * (TILE_BYTES + E_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sh_o + STAGES * O_BYTES);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
 
@@ -156,36 +160,41 @@ __global__ void __launch_bounds__(16 * 32, 1)
   __syncthreads();
 
   if (warp == njobs) {  // ---- producer
-    if (lane == 0) {
+    if (lane == 0 && rg.u1 > rg.u0) {
       tma_prefetch_desc(&tmA);
       int k = 0;
+      // entry range of the next tile, loaded one tile ahead
+      int t = (int)(rg.u0 % ntiles);
+      uint32_t e_lo = __ldg(offs + (int64_t)t * o_stride + c_lo), e_hi = __ldg(offs + (int64_t)t * o_stride + c_hi);
       for (int64_t u = rg.u0; u < rg.u1; ++u, ++k) {
         const int s = k % STAGES;
-        if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
         const int64_t blk = u / ntiles;
-        const int t = (int)(u % ntiles);
-        const uint32_t fb = full0 + 8 * s;
-        const uint32_t* ot = offs + (int64_t)t * o_stride;
-        const uint32_t e_al = __ldg(ot + c_lo) & ~7u;
-        const uint32_t eb = ((__ldg(ot + c_hi) - e_al) * 2 + 15) & ~15u;
+        t = (int)(u % ntiles);
+        const uint32_t lo = e_lo, hi = e_hi;
+        if (u + 1 < rg.u1) {
+          const int tn = (int)((u + 1) % ntiles);
+          e_lo = __ldg(offs + (int64_t)tn * o_stride + c_lo);
+          e_hi = __ldg(offs + (int64_t)tn * o_stride + c_hi);
+        }
+        const uint32_t eb = (hi - lo) * 16;
         if (eb > E_BYTES) {  // host sizing guarantees this never happens
           set_err(err, ERRF_BOUNDS);
           break;
         }
+        if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
+        const uint32_t fb = full0 + 8 * s;
         mbar_arrive_expect_tx(fb, TILE_BYTES + eb + O_BYTES);
-        tma_load_2d(smem_u32(tiles) + s * TILE_BYTES, &tmA, fb, (int32_t)(blk * BW), t * TILE);
-        if (eb) bulk_g2s(smem_u32(sh_e) + s * E_BYTES, ents + (int64_t)t * e_stride + e_al, eb, fb);
-        bulk_g2s(smem_u32(sh_o) + s * O_BYTES, ot + o_lo, O_BYTES, fb);
+        tma_load_2d(tiles_sa + s * TILE_BYTES, &tmA, fb, (int32_t)(blk * BW), t * TILE);
+        if (eb) bulk_g2s(ents_sa + s * E_BYTES, ents + (int64_t)t * e_stride + lo, eb, fb);
+        bulk_g2s(smem_u32(sh_o) + s * O_BYTES, offs + (int64_t)t * o_stride + o_lo, O_BYTES, fb);
       }
     }
   } else {  // ---- consumers
-    VT acc[NB];
-    const VT zero = {};
-#pragma unroll
-    for (int b = 0; b < NB; ++b) acc[b] = zero;
+    ColsAcc<T> acc[NB];
     const int cw0 = c_lo + warp * nbw;
     const int nb = max(0, min(nbw, c_hi - cw0));
     const bool vec_ok = ((ldSt | cw0) & 3) == 0;
+    const uint32_t lane_off = lane * 16;
     int k = 0;
     auto flush = [&](int64_t blk) {
 #pragma unroll
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(16 * 32, 1)
         if (j < colsA) {
           T v[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) v[b] = lane_get(acc[b], q);
+          for (int b = 0; b < NB; ++b) v[b] = acc[b].get(q);
           flush_row<NB>(St + j * ldSt + cw0, v, nb, scale, vec_ok);
         }
       }
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(16 * 32, 1)
       const int64_t blk = u / ntiles;
       const int64_t u_end = min64(rg.u1, (blk + 1) * ntiles);
 #pragma unroll
-      for (int b = 0; b < NB; ++b) acc[b] = zero;
+      for (int b = 0; b < NB; ++b) acc[b].zero();
       for (; u < u_end; ++u, ++k) {
         const int s = k % STAGES;
         if (!mbar_wait(full0 + 8 * s, (k / STAGES) & 1, err)) {
@@ -213,27 +222,24 @@ __global__ void __launch_bounds__(16 * 32, 1)
         }
         if (nb > 0) {
           const uint32_t* O = reinterpret_cast<const uint32_t*>(sh_o + s * O_BYTES) - o_lo;
-          const uint16_t* E = reinterpret_cast<const uint16_t*>(sh_e + s * E_BYTES) - (O[c_lo] & ~7u);
-          const T* X = reinterpret_cast<const T*>(tiles + s * TILE_BYTES) + lane * VEC;
+          // shared address of entry index p is ebase + 16 p
+          const uint32_t ebase = ents_sa + s * E_BYTES - O[c_lo] * 16;
+          const uint32_t xaddr = tiles_sa + s * TILE_BYTES + lane_off;
           uint32_t p = O[cw0];
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             if (b < nb) {
               const uint32_t e = O[cw0 + b + 1];
-              VT a2 = zero;
-              for (; p + 1 < e; p += 2) {
-                const uint32_t en0 = E[p], en1 = E[p + 1];
-                const VT v0 = *reinterpret_cast<const VT*>(X + (en0 & 0x7fffu) * BW);
-                const VT v1 = *reinterpret_cast<const VT*>(X + (en1 & 0x7fffu) * BW);
-                fma_into(acc[b], v0, sgn_of(en0, T()));
-                fma_into(a2, v1, sgn_of(en1, T()));
+              uint32_t ea = ebase + p * 16;
+              for (; p + 1 < e; p += 2, ea += 32) {
+                const uint4 r0 = lds_u4(ea), r1 = lds_u4(ea + 16);
+                acc[b].add(xaddr, r0);
+                acc[b].add(xaddr, r1);
               }
               if (p < e) {
-                const uint32_t en0 = E[p];
-                fma_into(acc[b], *reinterpret_cast<const VT*>(X + (en0 & 0x7fffu) * BW), sgn_of(en0, T()));
+                acc[b].add(xaddr, lds_u4(ea));
                 ++p;
               }
-              fma_into(acc[b], a2, T(1));
             }
           }
         }
@@ -252,21 +258,52 @@ constexpr int RPL = 4;  // rows per lane
 constexpr int ROWS_BLK = 32 * RPL;
 constexpr int NPROD = 2;  // producer warps
 
+template <typename T>
+struct RowsAcc;
+template <>
+struct RowsAcc<float> {
+  float2 a, b;  // rows (q0, q1), (q2, q3)
+  __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
+  template <uint32_t STEP>
+  __device__ __forceinline__ void add(uint32_t raddr, const uint4& r) {
+    const uint32_t x = raddr + r.w;
+    const float v0 = lds_f1(x), v1 = lds_f1(x + STEP), v2 = lds_f1(x + 2 * STEP), v3 = lds_f1(x + 3 * STEP);
+    const float2 s = f2(__uint_as_float(r.y), __uint_as_float(r.z));
+    a = __ffma2_rn(f2(v0, v1), s, a);
+    b = __ffma2_rn(f2(v2, v3), s, b);
+  }
+  __device__ __forceinline__ float get(int q) const { return q == 0 ? a.x : q == 1 ? a.y : q == 2 ? b.x : b.y; }
+};
+template <>
+struct RowsAcc<double> {
+  double v[4];
+  __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
+  template <uint32_t STEP>
+  __device__ __forceinline__ void add(uint32_t raddr, const uint4& r) {
+    const uint32_t x = raddr + r.w;
+    const double s = sign_d(r);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = fma(lds_d1(x + q * STEP), s, v[q]);
+  }
+  __device__ __forceinline__ double get(int q) const { return v[q]; }
+};
+
 template <typename T, int TILE, int NB, int STAGES>
 __global__ void __launch_bounds__(16 * 32, 1)
     sjlt_rows_kernel(const T* __restrict__ A, int64_t lda, int64_t rowsA, int64_t colsA,
-                     const uint16_t* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
+                     const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
                      int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
                      T* __restrict__ S, int64_t ldS, T scale, int* err) {
   constexpr int P = TILE + 1;
   constexpr uint32_t TILE_BYTES = ((ROWS_BLK * P * sizeof(T)) + 127) / 128 * 128;
+  constexpr uint32_t ROW_STEP = 32 * P * sizeof(T);  // bytes between a lane's rows q and q + 1
   extern __shared__ __align__(1024) uint8_t smem[];
   const int o_lo = c_lo & ~3;
   const int o_cnt = ((c_hi + 1 + 3) & ~3) - o_lo;
   const uint32_t O_BYTES = (uint32_t)o_cnt * 4;
-  uint8_t* tiles = smem;
-  uint8_t* sh_e = smem + STAGES * TILE_BYTES;
-  uint8_t* sh_o = sh_e + STAGES * E_BYTES;
+  const uint32_t tiles_sa = smem_u32(smem);
+  const uint32_t ents_sa = tiles_sa + STAGES * TILE_BYTES;
+  uint8_t* sh_o = smem + STAGES * (TILE_BYTES + E_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sh_o + STAGES * O_BYTES);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
 
@@ -288,56 +325,83 @@ __global__ void __launch_bounds__(16 * 32, 1)
     const int pt = threadIdx.x - njobs * 32;  // 0 .. NPROD*32-1
     const int pw = pt >> 5;
     int k = 0;
+    int t = rg.u1 > rg.u0 ? (int)(rg.u0 % ntiles) : 0;
+    uint32_t e_lo = 0, e_hi = 0;
+    if (rg.u1 > rg.u0) {
+      e_lo = __ldg(offs + (int64_t)t * o_stride + c_lo);
+      e_hi = __ldg(offs + (int64_t)t * o_stride + c_hi);
+    }
     for (int64_t u = rg.u0; u < rg.u1; ++u, ++k) {
       const int s = k % STAGES;
-      if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
       const int64_t blk = u / ntiles;
-      const int t = (int)(u % ntiles);
-      const int64_t i0 = blk * ROWS_BLK, j0 = (int64_t)t * TILE;
-      const uint32_t dst = smem_u32(tiles) + s * TILE_BYTES;
-      // warp-chunks of 32 consecutive columns of one row: coalesced reads,
-      // consecutive banks on the shared-memory side
-      constexpr int CHUNKS = ROWS_BLK * (TILE / 32);
-      for (int g = pw; g < CHUNKS; g += NPROD) {
-        const int r = g / (TILE / 32), c = (g % (TILE / 32)) * 32 + lane;
-        const bool in = (i0 + r < rowsA) && (j0 + c < colsA);
-        const T* src = in ? A + (i0 + r) * lda + j0 + c : A;
-        if (sizeof(T) == 4)
-          cp_async_4(dst + (r * P + c) * 4, src, in ? 4 : 0);
-        else
-          cp_async_8(dst + (r * P + c) * 8, src, in ? 8 : 0);
+      t = (int)(u % ntiles);
+      const uint32_t lo = e_lo, hi = e_hi;
+      if (u + 1 < rg.u1) {  // next tile's entry range, one tile ahead
+        const int tn = (int)((u + 1) % ntiles);
+        e_lo = __ldg(offs + (int64_t)tn * o_stride + c_lo);
+        e_hi = __ldg(offs + (int64_t)tn * o_stride + c_hi);
       }
-      const uint32_t* ot = offs + (int64_t)t * o_stride;
-      const uint32_t e_al = __ldg(ot + c_lo) & ~7u;
-      uint32_t eb = ((__ldg(ot + c_hi) - e_al) * 2 + 15) & ~15u;
+      if (k >= STAGES && !mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err)) break;
+      const int64_t i0 = blk * ROWS_BLK, j0 = (int64_t)t * TILE;
+      const uint32_t dst = tiles_sa + s * TILE_BYTES;
+      if (i0 + ROWS_BLK <= rowsA && j0 + TILE <= colsA) {
+        // full tile: each warp copies every NPROD-th row, 32 consecutive
+        // columns per instruction (coalesced; consecutive banks)
+        const T* src = A + (i0 + pw) * lda + j0 + lane;
+        uint32_t d = dst + (pw * P + lane) * (uint32_t)sizeof(T);
+        for (int r = pw; r < ROWS_BLK; r += NPROD, src += NPROD * lda, d += NPROD * P * (uint32_t)sizeof(T)) {
+#pragma unroll
+          for (int q = 0; q < TILE / 32; ++q) {
+            if (sizeof(T) == 4)
+              cp_async_4(d + q * 32 * 4, src + q * 32, 4);
+            else
+              cp_async_8(d + q * 32 * 8, src + q * 32, 8);
+          }
+        }
+      } else {  // ragged tile: per-element bounds, zero fill outside A
+        for (int r = pw; r < ROWS_BLK; r += NPROD) {
+#pragma unroll
+          for (int q = 0; q < TILE / 32; ++q) {
+            const int c = q * 32 + lane;
+            const bool in = (i0 + r < rowsA) && (j0 + c < colsA);
+            const T* src = in ? A + (i0 + r) * lda + j0 + c : A;
+            if (sizeof(T) == 4)
+              cp_async_4(dst + (r * P + c) * 4, src, in ? 4 : 0);
+            else
+              cp_async_8(dst + (r * P + c) * 8, src, in ? 8 : 0);
+          }
+        }
+      }
+      uint32_t eb = (hi - lo) * 16;
       if (eb > E_BYTES) {  // host sizing guarantees this never happens
         set_err(err, ERRF_BOUNDS);
         eb = 0;
       }
-      const uint32_t de = smem_u32(sh_e) + s * E_BYTES;
-      const uint8_t* se = reinterpret_cast<const uint8_t*>(ents + (int64_t)t * e_stride + e_al);
-      for (uint32_t q = pt; q < eb / 16; q += NPROD * 32) cp_async_16(de + q * 16, se + q * 16);
-      const uint32_t dof = smem_u32(sh_o) + s * O_BYTES;
-      const uint8_t* so = reinterpret_cast<const uint8_t*>(ot + o_lo);
-      for (uint32_t q = pt; q < O_BYTES / 16; q += NPROD * 32) cp_async_16(dof + q * 16, so + q * 16);
+      const uint8_t* se = reinterpret_cast<const uint8_t*>(ents + (int64_t)t * e_stride + lo);
+      for (uint32_t q = pt; q < eb / 16; q += NPROD * 32) cp_async_16(ents_sa + s * E_BYTES + q * 16, se + q * 16);
+      const uint8_t* so = reinterpret_cast<const uint8_t*>(offs + (int64_t)t * o_stride + o_lo);
+      for (uint32_t q = pt; q < O_BYTES / 16; q += NPROD * 32)
+        cp_async_16(smem_u32(sh_o) + s * O_BYTES + q * 16, so + q * 16);
       cp_async_mbar_arrive(full0 + 8 * s);
     }
     cp_async_wait<0>();
   } else {  // ---- consumers
-    T acc[RPL][NB];
-#pragma unroll
-    for (int q = 0; q < RPL; ++q)
-#pragma unroll
-      for (int b = 0; b < NB; ++b) acc[q][b] = T(0);
+    RowsAcc<T> acc[NB];
     const int cw0 = c_lo + warp * nbw;
     const int nb = max(0, min(nbw, c_hi - cw0));
     const bool vec_ok = ((ldS | cw0) & 3) == 0;
+    const uint32_t lane_off = lane * P * (uint32_t)sizeof(T);
     int k = 0;
     auto flush = [&](int64_t blk) {
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         const int64_t i = blk * ROWS_BLK + lane + 32 * q;
-        if (i < rowsA) flush_row<NB>(S + i * ldS + cw0, acc[q], nb, scale, vec_ok);
+        if (i < rowsA) {
+          T v[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) v[b] = acc[b].get(q);
+          flush_row<NB>(S + i * ldS + cw0, v, nb, scale, vec_ok);
+        }
       }
     };
     bool ok = true;
@@ -345,9 +409,7 @@ __global__ void __launch_bounds__(16 * 32, 1)
       const int64_t blk = u / ntiles;
       const int64_t u_end = min64(rg.u1, (blk + 1) * ntiles);
 #pragma unroll
-      for (int q = 0; q < RPL; ++q)
-#pragma unroll
-        for (int b = 0; b < NB; ++b) acc[q][b] = T(0);
+      for (int b = 0; b < NB; ++b) acc[b].zero();
       for (; u < u_end; ++u, ++k) {
         const int s = k % STAGES;
         if (!mbar_wait(full0 + 8 * s, (k / STAGES) & 1, err)) {
@@ -356,19 +418,22 @@ __global__ void __launch_bounds__(16 * 32, 1)
         }
         if (nb > 0) {
           const uint32_t* O = reinterpret_cast<const uint32_t*>(sh_o + s * O_BYTES) - o_lo;
-          const uint16_t* E = reinterpret_cast<const uint16_t*>(sh_e + s * E_BYTES) - (O[c_lo] & ~7u);
-          const T* X = reinterpret_cast<const T*>(tiles + s * TILE_BYTES) + lane * P;
+          const uint32_t ebase = ents_sa + s * E_BYTES - O[c_lo] * 16;
+          const uint32_t raddr = tiles_sa + s * TILE_BYTES + lane_off;
           uint32_t p = O[cw0];
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             if (b < nb) {
               const uint32_t e = O[cw0 + b + 1];
-              for (; p < e; ++p) {
-                const uint32_t en = E[p];
-                const T sg = sgn_of(en, T());
-                const T* x = X + (en & 0x7fffu);
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) acc[q][b] = fma(x[q * 32 * P], sg, acc[q][b]);
+              uint32_t ea = ebase + p * 16;
+              for (; p + 1 < e; p += 2, ea += 32) {
+                const uint4 r0 = lds_u4(ea), r1 = lds_u4(ea + 16);
+                acc[b].template add<ROW_STEP>(raddr, r0);
+                acc[b].template add<ROW_STEP>(raddr, r1);
+              }
+              if (p < e) {
+                acc[b].template add<ROW_STEP>(raddr, lds_u4(ea));
+                ++p;
               }
             }
           }
@@ -420,8 +485,17 @@ constexpr int COLS_JOBS = 15;
 constexpr int ROWS_JOBS = 16 - NPROD;
 constexpr int NB_COLS = 20;
 template <typename T>
-constexpr int nb_rows() { return sizeof(T) == 4 ? 20 : 10; }
-constexpr int STAGES = 3;
+constexpr int nb_rows() {
+  return sizeof(T) == 4 ? 20 : 10;
+}
+constexpr size_t ENTRY_BYTES = sizeof(uint4);
+constexpr long SMEM_MAX = 227 * 1024;
+
+// blocks of R whose entries fit next to STAGES tiles
+template <int STAGES>
+long blocks_that_fit(size_t tile_b, size_t o_max, size_t e_blk) {
+  return ((SMEM_MAX - 2 * STAGES * 8) / STAGES - (long)tile_b - (long)o_max) / (long)e_blk;
+}
 
 struct Jobs {
   int njobs, nbw;
@@ -469,10 +543,10 @@ int zero_columns(T* out, int64_t ld, int64_t rows, int c_lo, int c_hi, cudaStrea
   return SK_OK;
 }
 
-template <typename T, int TILE>
+template <typename T, int TILE, int STAGES>
 int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
                 int64_t ldSt, cudaStream_t s) {
-  constexpr int VEC = V16<T>::N, BW = 32 * VEC;
+  constexpr int VEC = 16 / sizeof(T), BW = 32 * VEC;
   PFN_encodeTiled enc = get_encode_tiled();
   if (!enc) return SK_ERR_DEVICE;
   CUtensorMap tm;
@@ -488,8 +562,8 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
   JLS_CHECK(zero_columns(St, ldSt, A->cols, c_lo, c_hi, s));
   const size_t tile_b = (size_t)TILE * BW * sizeof(T);
   const size_t o_max = (COLS_JOBS * NB_COLS + 8) * 4;
-  const size_t e_blk = (size_t)h->alpha * TILE * 2;
-  const long fit = ((long)(227 * 1024 - 2 * STAGES * 8) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
+  const long fit = blocks_that_fit<STAGES>(tile_b, o_max, e_blk);
   if (fit < 1) return SK_ERR_UNSUPPORTED;
   // at most one CTA per block of A keeps every block within two contiguous
   // CTA ranges, i.e. at most two contributions per output cell
@@ -497,10 +571,10 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
   for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, COLS_JOBS * NB_COLS)) {
     const Jobs J = plan_jobs(rg.hi - rg.lo, COLS_JOBS);
-    const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
+    const uint32_t e_bytes = (uint32_t)(e_blk * rg.nblk);
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
     const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
-    if (smem > 227 * 1024) return SK_ERR_UNSUPPORTED;
+    if ((long)smem > SMEM_MAX) return SK_ERR_UNSUPPORTED;
     auto kern = sjlt_cols_kernel<T, TILE, NB_COLS, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride,
@@ -511,24 +585,24 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
   return SK_OK;
 }
 
-template <typename T, int TILE>
+template <typename T, int TILE, int STAGES>
 int launch_rows(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* S, int64_t ldS,
                 cudaStream_t s) {
   JLS_CHECK(zero_columns(S, ldS, A->rows, c_lo, c_hi, s));
   constexpr int NB = nb_rows<T>();
   const size_t tile_b = ((ROWS_BLK * (TILE + 1) * sizeof(T)) + 127) / 128 * 128;
   const size_t o_max = (ROWS_JOBS * NB + 8) * 4;
-  const size_t e_blk = (size_t)h->alpha * TILE * 2;
-  const long fit = ((long)(227 * 1024 - 2 * STAGES * 8) / STAGES - (long)tile_b - (long)o_max - 16) / (long)e_blk;
+  const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
+  const long fit = blocks_that_fit<STAGES>(tile_b, o_max, e_blk);
   if (fit < 1) return SK_ERR_UNSUPPORTED;
   const int64_t nblk = (A->rows + ROWS_BLK - 1) / ROWS_BLK;  // see launch_cols
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
   for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, ROWS_JOBS * NB)) {
     const Jobs J = plan_jobs(rg.hi - rg.lo, ROWS_JOBS);
-    const uint32_t e_bytes = (uint32_t)((e_blk * rg.nblk + 16 + 15) & ~(size_t)15);
+    const uint32_t e_bytes = (uint32_t)(e_blk * rg.nblk);
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
     const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
-    if (smem > 227 * 1024) return SK_ERR_UNSUPPORTED;
+    if ((long)smem > SMEM_MAX) return SK_ERR_UNSUPPORTED;
     auto kern = sjlt_rows_kernel<T, TILE, NB, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, (J.njobs + NPROD) * 32, smem, s>>>(static_cast<const T*>(A->A), A->ld, A->rows, A->cols, C.ents,
@@ -540,6 +614,27 @@ int launch_rows(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
   return SK_OK;
 }
 
+// Three stages when one block's entries fit beside them, else two.
+template <typename T, int TILE>
+int launch_cols_any(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
+                    int64_t ldSt, cudaStream_t s) {
+  const size_t tile_b = (size_t)TILE * 512, o_max = (COLS_JOBS * NB_COLS + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
+  if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
+    return launch_cols<T, TILE, 3>(h, A, C, c_lo, c_hi, scale, St, ldSt, s);
+  return launch_cols<T, TILE, 2>(h, A, C, c_lo, c_hi, scale, St, ldSt, s);
+}
+template <typename T, int TILE>
+int launch_rows_any(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* S,
+                    int64_t ldS, cudaStream_t s) {
+  const size_t tile_b = ((ROWS_BLK * (TILE + 1) * sizeof(T)) + 127) / 128 * 128;
+  const size_t o_max = (ROWS_JOBS * nb_rows<T>() + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
+  if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
+    return launch_rows<T, TILE, 3>(h, A, C, c_lo, c_hi, scale, S, ldS, s);
+  return launch_rows<T, TILE, 2>(h, A, C, c_lo, c_hi, scale, S, ldS, s);
+}
+
 }  // namespace
 
 int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
@@ -549,15 +644,15 @@ int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, doub
   const TiledCcs& C = h->ccs[tsel];
   if (which & SK_S) {
     if (A->dtype == SK_F32)
-      JLS_CHECK((launch_rows<float, SJLT_TILE_F32>(h, A, C, c_lo, c_hi, (float)scale, (float*)S, ldS, s)));
+      JLS_CHECK((launch_rows_any<float, SJLT_TILE_F32>(h, A, C, c_lo, c_hi, (float)scale, (float*)S, ldS, s)));
     else
-      JLS_CHECK((launch_rows<double, SJLT_TILE_F64>(h, A, C, c_lo, c_hi, scale, (double*)S, ldS, s)));
+      JLS_CHECK((launch_rows_any<double, SJLT_TILE_F64>(h, A, C, c_lo, c_hi, scale, (double*)S, ldS, s)));
   }
   if (which & SK_ST) {
     if (A->dtype == SK_F32)
-      JLS_CHECK((launch_cols<float, SJLT_TILE_F32>(h, A, C, c_lo, c_hi, (float)scale, (float*)St, ldSt, s)));
+      JLS_CHECK((launch_cols_any<float, SJLT_TILE_F32>(h, A, C, c_lo, c_hi, (float)scale, (float*)St, ldSt, s)));
     else
-      JLS_CHECK((launch_cols<double, SJLT_TILE_F64>(h, A, C, c_lo, c_hi, scale, (double*)St, ldSt, s)));
+      JLS_CHECK((launch_cols_any<double, SJLT_TILE_F64>(h, A, C, c_lo, c_hi, scale, (double*)St, ldSt, s)));
   }
   return SK_OK;
 }
