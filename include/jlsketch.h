@@ -9,11 +9,11 @@
  *     S  = A R        (sketch of the rows of A,    Sec. 6.3 "A R")
  *     S' = A^T R      (sketch of the columns of A, Sec. 6.3 "A* R"; real A)
  *
- * for three JL operators R (n x d): the SJLT (Sec. 3.2.3, data structure
- * Sec. 6.1), the SRHT R = D H P (Sec. 3.2.2, element formula Eq. RsrHt) and the
- * Gaussian operator N(0, 1/d) (Sec. 3.2.1); R grows by Delta-d columns
+ * for three JL operators R (n x d): the SJLT (Sec. 2.4.3, data structure
+ * Sec. 6.1), the SRHT R = D H P (Sec. 2.4.2, element formula the element formula of Sec. 7.2) and the
+ * Gaussian operator N(0, 1/d) (Sec. 2.4.1); R grows by Delta-d columns
  * (Sec. 6.2, Algorithm 1: R <- [R R_bar], S <- [S A R_bar]) until the Frobenius
- * stopping test of Eq. stopping_criteria-1 passes.
+ * stopping test of Eq. (3.1) passes.
  *
  * Conventions for every entry point:
  *  - Matrices are row-major.  A is rows x cols with leading dimension ld
@@ -53,7 +53,7 @@ extern "C" {
 #define SK_ERR_DEVICE        -8  /* CUDA error or device-side error flag */
 #define SK_ERR_UNSUPPORTED   -9  /* valid request this build does not implement */
 
-/* ---- operator kinds (Sec. 3.2) ------------------------------------------ */
+/* ---- operator kinds (Sec. 2.4) ------------------------------------------ */
 #define SK_SJLT_GRAPH 1  /* alpha distinct positions uniform in each row's block  */
 #define SK_SJLT_BLOCK 2  /* one position in each of alpha chunks of width/alpha    */
 #define SK_SRHT       3  /* R = D H P, nu = 2^ceil(log2 n), columns w/o replacement */
@@ -91,11 +91,11 @@ typedef struct sk_matrix {
 
 /*
  * sketch_create -- draw a JL operator R of size n x d on the device.
- *   kind   SK_SJLT_GRAPH | SK_SJLT_BLOCK | SK_SRHT | SK_GAUSS (Sec. 3.2).
+ *   kind   SK_SJLT_GRAPH | SK_SJLT_BLOCK | SK_SRHT | SK_GAUSS (Sec. 2.4).
  *   n      rows of R (= cols of A for S, rows of A for S'), 1 <= n < 2^31.
  *   d      initial columns (Algorithm 1 starts with d0 + Delta-d), 1 <= d <= d_max.
  *   alpha  SJLT nonzeros per row and block, 1 <= alpha <= min(d, 32); block
- *          construction needs alpha | d (Sec. 3.2.3).  Ignored otherwise.
+ *          construction needs alpha | d (Sec. 2.4.3).  Ignored otherwise.
  *   seed   64-bit seed; R is a pure function of (kind, n, d, alpha, seed) and
  *          the increments applied (Philox4x64-10 streams).
  *   d_max  capacity in columns, d <= d_max <= 8192; SRHT needs d_max <= nu.
@@ -142,7 +142,7 @@ int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32
                            void* S, int64_t ldS, void* St, int64_t ldSt, void* stream);
 
 /*
- * adaptive_norm_test -- the Frobenius stopping test (Eq. stopping_criteria-1)
+ * adaptive_norm_test -- the Frobenius stopping test (Eq. (3.1))
  * on the global sketch held in S (rows x d_total, device, dtype, row-major):
  *   S~ = the last delta_d columns of S (Algorithm 1's "last Delta-d columns"),
  *   S^ = (I - Q Q^T)^2 S~ with Q an orthonormal basis of the first

@@ -8,9 +8,9 @@ it per HSS node, with eps / level(tau)):
 2. Q <- orthonormal basis of S(:, 1:d)   (QR of the first d columns).
 3. S~ <- S(:, d+1 : d+Delta-d)             (the last Delta-d columns).
 4. S^ <- (I - Q Q^T)^2 S~                  (two steps of block Gram-Schmidt,
-   the remark after Eq. stopping_criteria-1).
+   the remark after Eq. (3.1)).
 5. stop when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F
-   (Eq. stopping_criteria-1; no 1/sqrt(d) factor, the remark before it).
+   (Eq. (3.1); no 1/sqrt(d) factor, the remark before it).
 6. otherwise R <- [R  R_bar], d <- d + Delta-d, S <- A R, and repeat, while the
    grown R keeps at most d_max columns.
 

@@ -2,14 +2,14 @@
 
 Operators and the sections they follow:
 
-* Gaussian (Sec. 3.2.1): R in R^{n x d}, i.i.d. N(0, 1/d).
-* SRHT (Sec. 3.2.2 and Sec. 6.2 "Sketching diagonal blocks"): R = D H P with
+* Gaussian (Sec. 2.4.1): R in R^{n x d}, i.i.d. N(0, 1/d).
+* SRHT (Sec. 2.4.2 and Sec. 7.2): R = D H P with
   D a Rademacher diagonal, H the normalized Sylvester-Hadamard matrix of order
   nu = 2^ceil(log2 n) (zero padding of A to nu columns), and P selecting d
   columns with scale sqrt(nu/d); element-wise R_ij = d_i (-1)^(i . mu_j)/sqrt(d)
-  (Eq. RsrHt), i . mu the dot product of the base-2 digits of the 0-based
+  (the element formula of Sec. 7.2), i . mu the dot product of the base-2 digits of the 0-based
   indices.
-* SJLT (Sec. 3.2.3): alpha nonzeros of value +-1/sqrt(alpha) per row; graph
+* SJLT (Sec. 2.4.3): alpha nonzeros of value +-1/sqrt(alpha) per row; graph
   construction = alpha distinct positions uniform in [d]; block construction =
   one position uniform in each of the alpha chunks of d/alpha columns.  The
   data structure R = (B+ - B-)/sqrt(alpha) with B+ and B- kept in CRS and CCS
@@ -52,7 +52,7 @@ KINDS = ("sjlt_graph", "sjlt_block", "srht", "gauss")
 
 def popcount_parity(x: np.ndarray) -> np.ndarray:
     """Parity (0/1) of the number of set bits of non-negative int64 ``x``:
-    (-1)^(i . mu) with i . mu the base-2 digit dot product (Eq. RsrHt)."""
+    (-1)^(i . mu) with i . mu the base-2 digit dot product (the element formula of Sec. 7.2)."""
     x = np.asarray(x, dtype=np.int64)
     if hasattr(np, "bitwise_count"):
         return (np.bitwise_count(x) & 1).astype(np.int64)

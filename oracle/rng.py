@@ -1,6 +1,6 @@
 """Counter-based random numbers for the oracle (test infrastructure only).
 
-The paper draws its operators with ``std::minstd_rand`` (Sec. 7.2) and does not
+The paper draws its operators with ``std::minstd_rand`` (Sec. 8.3.1) and does not
 say how streams are laid out.  This project's reading: every random quantity is
 a pure function of (seed, tag, counter) through Philox4x64-10 (Salmon, Moraes,
 Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11), so that the

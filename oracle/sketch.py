@@ -11,13 +11,13 @@
   for A^T R through the compressed column storage of B+ and B-.
 * ``kernel_matrix(X, Y, h, shift)``: A_ij = exp(-||x_i - y_j||^2 / (2 h^2)) +
   shift * delta_ij in FP64 (a Gaussian kernel; the paper's covariance problem
-  uses an exponential kernel, Sec. 7.1, the workloads here use the Gaussian one).
+  uses an exponential kernel, Sec. 8.1, the workloads here use the Gaussian one).
 * ``hadamard(nu)``: unnormalised Sylvester matrix, H_1 = [1],
-  H_2m = [[H_m, H_m], [H_m, -H_m]] (Sec. 3.2.2).
+  H_2m = [[H_m, H_m], [H_m, -H_m]] (Sec. 2.4.2).
 * ``fwht(x)``: unnormalised fast Walsh-Hadamard transform along the last axis,
-  log2(nu) butterfly stages (the O(n log n) transform of Sec. 6.2).
+  log2(nu) butterfly stages (the O(n log n) transform of Sec. 7.1).
 * ``srht_by_fwht(A, D, mu, d_total)``: S = A D H P sqrt(nu/d) computed through
-  the transform of the zero-padded rows (Sec. 6.2, A padded to nu columns).
+  the transform of the zero-padded rows (Sec. 7.1, A padded to nu columns).
 """
 from __future__ import annotations
 

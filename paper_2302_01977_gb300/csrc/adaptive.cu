@@ -1,6 +1,6 @@
 // adaptive.cu -- increment rescale and the Frobenius stopping test.
 //
-// Stopping test (Eq. stopping_criteria-1 with the two-pass projection of the
+// Stopping test (Eq. (3.1) with the two-pass projection of the
 // remark after it; Algorithm 1's S~ = last Delta-d columns):
 //   S^ = (I - Q Q^T)^2 S~,  stop = ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
 // Q is an orthonormal basis of the earlier sketch columns kept per handle and
@@ -393,3 +393,4 @@ int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int 
 }
 
 }  // namespace jls
+

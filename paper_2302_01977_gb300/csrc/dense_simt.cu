@@ -2,8 +2,8 @@
 //
 //   S  = scale * A   * B     (Sec. 6.3 "A R")
 //   S' = scale * A^T * B     (Sec. 6.3 "A* R", real A)
-// with B the unscaled operator: Gaussian z (N(0,1), Sec. 3.2.1) read from the
-// stored plane, or the SRHT sign pattern d_k (-1)^popc(k & mu_c) (Eq. RsrHt)
+// with B the unscaled operator: Gaussian z (N(0,1), Sec. 2.4.1) read from the
+// stored plane, or the SRHT sign pattern d_k (-1)^popc(k & mu_c) (the element formula of Sec. 7.2)
 // generated while the B tile is staged.  This is the plain path the tensor-core
 // split path is measured against, and the FP64 path.  Tiles of 128 x 64
 // outputs over K steps of 16, 256 threads with 8 x 4 outputs each; FP32 sums

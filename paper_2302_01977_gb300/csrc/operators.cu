@@ -1,15 +1,15 @@
-// operators.cu -- drawing the JL operators on the device (Sec. 3.2, Sec. 6.1-6.2).
+// operators.cu -- drawing the JL operators on the device (Sec. 2.4, Sec. 6.1-6.2, Sec. 7.2).
 //
 // Stream layout (identical to the host oracle's, which is written independently):
 //  * SJLT row i, block b: draws t = 0, 1, ... at Philox counter (i, t, 0, 0),
 //    key (seed, TAG_SJLT | b); slot k takes the next accepted draw,
 //    position = lemire(word0, span) (span = width/alpha for the block
-//    construction, width for the graph construction, Sec. 3.2.3); a draw is
+//    construction, width for the graph construction, Sec. 2.4.3); a draw is
 //    skipped on Lemire rejection or, in the graph construction, on a repeated
 //    column; sign = top bit of word1 (set means -1).
 //  * SRHT: d_i = top bit of word0 at counter (i, 0, 0, 0), key (seed, TAG_SRHT_D);
 //    sampled columns = first distinct lemire(word0, nu) over counters
-//    (t, 0, 0, 0), key (seed, TAG_SRHT_MU) (Sec. 3.2.2, without replacement).
+//    (t, 0, 0, 0), key (seed, TAG_SRHT_MU) (Sec. 2.4.2, without replacement).
 //  * Gaussian column c: counter (i, c >> 1, 0, 0), key (seed, TAG_GAUSS),
 //    Box-Muller on u1 in (0,1], u2 in [0,1): cos half for even c, sin for odd.
 #include <cuda_bf16.h>

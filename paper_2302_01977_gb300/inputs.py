@@ -3,13 +3,13 @@
 This module holds no sketching arithmetic: it only draws points, orders them and
 draws dense test matrices.  Everything here is host-side numpy.
 
-Workloads (shapes follow the paper's test problems, Sec. 7.1, and the kernel
+Workloads (shapes follow the paper's test problems, Sec. 8.1, and the kernel
 matrices used to exercise the sketch):
 
 * points uniform in [0,1]^3, drawn from numpy's Philox bit generator with a
   fixed seed (seed = 20230203 + workload index unless a test picks its own);
 * an optional recursive median bisection ordering of the points (the paper
-  orders its covariance test problem by recursive bisection, Sec. 7.1): split
+  orders its covariance test problem by recursive bisection, Sec. 8.1): split
   on the coordinate of largest extent (lowest axis index on ties), stable sort by
   (coordinate, original index), left child gets floor(m/2) points, stop at a
   leaf of <= ``leaf`` points;

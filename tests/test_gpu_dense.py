@@ -79,7 +79,7 @@ def test_dense_increments(kind):
 
 
 def test_srht_matches_fwht_route():
-    """The element-formula sketch equals the transform of the padded rows (Sec. 6.2)."""
+    """The element-formula sketch equals the transform of the padded rows (Sec. 7.1)."""
     n, d = 1000, 64
     A = inputs.dense_matrix(50, n, seed=2)
     S, _ = sketch("srht", A, d, 5, "f64", which=1)

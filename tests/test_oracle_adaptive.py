@@ -1,7 +1,7 @@
 """Pins for the oracle's adaptive loop (CPU only).
 
 * An exactly rank-r matrix with r < d0 has no range left for the new columns:
-  the first test must stop with ||S^|| ~ 0 (Sec. 4, Eq. stopping_criteria-1).
+  the first test must stop with ||S^|| ~ 0 (Sec. 3, Eq. (3.1)).
 * A matrix with a prescribed geometric singular spectrum reaches a larger d for
   a smaller eps_rel (the test is monotone in its tolerance).
 * The two-pass projection leaves a block orthogonal to Q.

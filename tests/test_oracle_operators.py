@@ -1,10 +1,10 @@
 """Pins for the oracle's JL operators and sketch products (CPU only).
 
 Each check is a fact the paper or the mathematics fixes, not a retyped formula:
-nonzero counts and values (Sec. 3.2.3), the Sec. 6.1 worked example, the
-Sylvester recursion and H H^T = nu I (Sec. 3.2.2), R^T R = (n/d) I for an SRHT
+nonzero counts and values (Sec. 2.4.3), the Sec. 6.1 worked example, the
+Sylvester recursion and H H^T = nu I (Sec. 2.4.2), R^T R = (n/d) I for an SRHT
 of power-of-two order, the FWHT route agreeing with the element formula,
-E||x^T R||^2 = ||x||^2 (Definition 3.2), A = I giving R back, and brute-force
+E||x^T R||^2 = ||x||^2 (Definition 2.2), A = I giving R back, and brute-force
 triple loops at n <= 64.
 """
 import json
@@ -209,7 +209,7 @@ def test_symmetric_A_gives_equal_sketches(kind, alpha):
 
 @pytest.mark.parametrize("kind,alpha", KIND_ARGS)
 def test_jl_norm_expectation_monte_carlo(kind, alpha):
-    """E ||x^T R||^2 = ||x||^2 (Definition 3.2 with eps -> expectation)."""
+    """E ||x^T R||^2 = ||x||^2 (Definition 2.2 with eps -> expectation)."""
     n, d, T = 64, 16, 400
     x = inputs.dense_matrix(1, n, seed=6)[0]
     vals = np.array([((x @ ops.Operator(kind, n, d, alpha, seed=s).dense()) ** 2).sum() for s in range(T)])
