@@ -163,6 +163,40 @@ int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, i
                        int32_t* stop, double* norm_hat, double* norm_tilde, void* stream);
 
 /*
+ * sketch_project_norms_noalloc -- the projection and norms of the stopping
+ * test, for callers that cannot allocate device memory.  (The paper has no
+ * counterpart: this is an interface variant of adaptive_norm_test's arithmetic.)
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph (an allocation there breaks the capture), processes whose device memory
+ * is owned by another allocator or a fixed pool, and callers that must not take
+ * the device-wide synchronization that cudaMalloc/cudaFree can imply.  This call
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ * Its scratch is a file-scope device array of 4.5 MiB inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   Q        device, rows x q_cols, row-major (ldQ >= q_cols): an orthonormal
+ *            basis supplied by the caller (may be NULL when q_cols == 0).
+ *   S_tilde  device, rows x b (ldS >= b): the block to test.
+ *   S_hat    device, rows x b (ldH >= b): receives (I - Q Q^T)^2 S_tilde.
+ *   Writes *stop = ||S_hat||_F < eps_abs or ||S_hat||_F < eps_rel ||S_tilde||_F
+ *   and, if not NULL, *norm_hat and *norm_tilde (host; FP64 sums).
+ * Limits: q_cols <= 1024 and b <= 64 (larger requests return
+ * SK_ERR_INVALID_ARG without touching the device).  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and nothing in it needs to start at zero (each call
+ * writes every element it reads), but calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it: serialize them.
+ * Synchronizes `stream`.  Errors: INVALID_ARG, DTYPE, UNSUPPORTED, DEVICE.
+ */
+int sketch_project_norms_noalloc(const void* Q, int64_t ldQ, int32_t q_cols,
+                                 const void* S_tilde, int64_t ldS, int64_t rows, int32_t b,
+                                 int32_t dtype, void* S_hat, int64_t ldH,
+                                 double eps_rel, double eps_abs, int32_t* stop,
+                                 double* norm_hat, double* norm_tilde, void* stream);
+
+/*
  * kernel_matrix -- write the explicit matrix of a generator descriptor:
  * A_ij = exp(-||x_i - y_j||^2 / (2 h^2)) + shift * [i == j]  (device, row-major,
  * ld >= cols, dtype of the descriptor).  Asynchronous.

@@ -14,6 +14,7 @@
 // summed in FP64 by a second kernel.  Frobenius norms are FP64 sums of squares.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -394,3 +395,115 @@ int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int 
 
 }  // namespace jls
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the stopping test's projection and norms.
+//
+// Some callers cannot allocate device memory: code running inside CUDA stream
+// capture (where cudaMalloc would break the capture), processes whose device
+// memory is fully owned by another allocator or pool, and callers that must
+// not block on the synchronization cudaMalloc/cudaFree imply.  For them,
+// sketch_project_norms_noalloc takes its scratch (the tall-skinny product's
+// partial sums, the reduced product Q^T S and the norm partials) from the
+// file-scope array below instead of a handle.  Every GPU that loads the library
+// holds this array until the process exits.
+namespace jls {
+namespace {
+
+constexpr int NOALLOC_MAX_Q = 1024;  // columns of Q
+constexpr int NOALLOC_MAX_B = 64;    // columns of S~
+constexpr int NOALLOC_CHUNKS = 8;    // row chunks of the partial products
+constexpr size_t NOALLOC_PART = (size_t)NOALLOC_CHUNKS * NOALLOC_MAX_Q * NOALLOC_MAX_B;
+constexpr size_t NOALLOC_G = (size_t)NOALLOC_MAX_Q * NOALLOC_MAX_B;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_PART + NOALLOC_G + NORM_GRID;  // 4.5 MiB
+
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  JLS_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SK_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    JLS_CHECK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SK_OK;
+}
+
+template <typename T>
+int sumsq_noalloc(const T* W, int64_t ldw, int64_t rows, int b, double* partials, double* out, cudaStream_t s) {
+  sumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, partials); note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  double part[NORM_GRID];
+  JLS_CHECK_CUDA(cudaMemcpyAsync(part, partials, sizeof(part), cudaMemcpyDeviceToHost, s));
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  double acc = 0;
+  for (int i = 0; i < NORM_GRID; ++i) acc += part[i];  // fixed order: deterministic
+  *out = acc;
+  return SK_OK;
+}
+
+template <typename T>
+int project_norms_noalloc_t(const T* Q, int64_t ldQ, int q_cols, const T* St, int64_t ldS, int64_t rows, int b,
+                            T* Sh, int64_t ldH, double* nh, double* nt, cudaStream_t s) {
+  double* scratch = nullptr;
+  JLS_CHECK(noalloc_scratch(&scratch));
+  double* part = scratch;
+  double* G = scratch + NOALLOC_PART;
+  double* norms = G + NOALLOC_G;
+  copy_block_kernel<T><<<152 * 4, 256, 0, s>>>(St, ldS, Sh, ldH, rows, b); note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  double t2 = 0, h2 = 0;
+  JLS_CHECK(sumsq_noalloc<T>(Sh, ldH, rows, b, norms, &t2, s));
+  for (int pass = 0; pass < 2 && q_cols > 0; ++pass) {  // S^ <- (I - Q Q^T) S^, twice
+    JLS_CHECK(tsgemm<T>(Q, ldQ, q_cols, Sh, ldH, b, rows, NOALLOC_CHUNKS, part, G, s));
+    sub_qg_kernel<T><<<(unsigned)((rows + 31) / 32), 256, 0, s>>>(Sh, ldH, b, Q, ldQ, q_cols, G, rows); note_launch();
+    JLS_CHECK_CUDA(cudaGetLastError());
+  }
+  JLS_CHECK(sumsq_noalloc<T>(Sh, ldH, rows, b, norms, &h2, s));
+  *nt = std::sqrt(t2);
+  *nh = std::sqrt(h2);
+  return SK_OK;
+}
+
+}  // namespace
+
+}  // namespace jls
+
+extern "C" int sketch_project_norms_noalloc(const void* Q, int64_t ldQ, int32_t q_cols, const void* S_tilde,
+                                            int64_t ldS, int64_t rows, int32_t b, int32_t dtype, void* S_hat,
+                                            int64_t ldH, double eps_rel, double eps_abs, int32_t* stop,
+                                            double* norm_hat, double* norm_tilde, void* stream) {
+  using namespace jls;
+  if (!S_tilde || !S_hat || !stop || rows < 1 || b < 1 || q_cols < 0 || ldS < b || ldH < b) return SK_ERR_INVALID_ARG;
+  if (b > NOALLOC_MAX_B || q_cols > NOALLOC_MAX_Q) return SK_ERR_INVALID_ARG;  // beyond the static scratch
+  if (q_cols > 0 && (!Q || ldQ < q_cols)) return SK_ERR_INVALID_ARG;
+  if (dtype != SK_F32 && dtype != SK_F64) return SK_ERR_DTYPE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double nh = 0, nt = 0;
+  if (dtype == SK_F32)
+    JLS_CHECK(project_norms_noalloc_t<float>(static_cast<const float*>(Q), ldQ, q_cols,
+                                             static_cast<const float*>(S_tilde), ldS, rows, b,
+                                             static_cast<float*>(S_hat), ldH, &nh, &nt, s));
+  else
+    JLS_CHECK(project_norms_noalloc_t<double>(static_cast<const double*>(Q), ldQ, q_cols,
+                                              static_cast<const double*>(S_tilde), ldS, rows, b,
+                                              static_cast<double*>(S_hat), ldH, &nh, &nt, s));
+  *stop = (nh < eps_abs) || (nh < eps_rel * nt);
+  if (norm_hat) *norm_hat = nh;
+  if (norm_tilde) *norm_tilde = nt;
+  return SK_OK;
+}

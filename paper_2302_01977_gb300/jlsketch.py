@@ -45,7 +45,7 @@ SK_BOTH = 3
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
-           "adaptive_norm_test", "kernel_matrix", "sketch_dims", "sketch_export",
+           "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_launch_count", "sketch_destroy", "sketch_strerror"]
 
 
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
         "sketch_apply": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
         "sketch_apply_increment": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
         "adaptive_norm_test": (i32, [vp, i32, vp, i64, i64, i32, i32, dbl, dbl, P(i32), P(dbl), P(dbl), vp]),
+        "sketch_project_norms_noalloc": (i32, [vp, i64, i32, vp, i64, i64, i32, i32, vp, i64, dbl, dbl, P(i32),
+                                               P(dbl), P(dbl), vp]),
         "kernel_matrix": (i32, [P(SkMatrix), vp, i64, vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
@@ -207,6 +209,26 @@ def adaptive_norm_test(h, slot: int, S, delta_d: int, eps_rel: float, eps_abs: f
                                   int(delta_d), float(eps_rel), float(eps_abs), ctypes.byref(stop),
                                   ctypes.byref(nh), ctypes.byref(nt), _stream(stream))
     _check(rc, "adaptive_norm_test")
+    return bool(stop.value), nh.value, nt.value
+
+
+def sketch_project_norms_noalloc(Q, S_tilde, S_hat, eps_rel: float, eps_abs: float, stream=None):
+    """(I - Q Q^T)^2 S_tilde into S_hat without device allocation; returns
+    (stop, ||S_hat||_F, ||S_tilde||_F).  Q may be None for an empty basis."""
+    _check_2d(S_tilde, "S_tilde")
+    _check_2d(S_hat, "S_hat")
+    q_ptr, ldq, qc = None, 0, 0
+    if Q is not None:
+        _check_2d(Q, "Q")
+        q_ptr, ldq, qc = Q.data_ptr(), Q.stride(0), Q.shape[1]
+    stop = ctypes.c_int32()
+    nh = ctypes.c_double()
+    nt = ctypes.c_double()
+    rc = lib().sketch_project_norms_noalloc(q_ptr, ldq, qc, S_tilde.data_ptr(), S_tilde.stride(0),
+                                            S_tilde.shape[0], S_tilde.shape[1], _dtype_code(S_tilde),
+                                            S_hat.data_ptr(), S_hat.stride(0), float(eps_rel), float(eps_abs),
+                                            ctypes.byref(stop), ctypes.byref(nh), ctypes.byref(nt), _stream(stream))
+    _check(rc, "sketch_project_norms_noalloc")
     return bool(stop.value), nh.value, nt.value
 
 
