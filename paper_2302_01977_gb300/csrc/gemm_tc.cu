@@ -1,14 +1,571 @@
-// gemm_tc.cu -- SRHT / Gaussian sketches on tcgen05 tensor cores (bf16 split).
+// gemm_tc.cu -- SRHT and Gaussian sketches on tcgen05 tensor cores, with the
+// FP32 input split into two bf16 terms.
+//
+//   S  = scale * A   * B     (Sec. 6.3 "A R")
+//   S' = scale * A^T * B     (Sec. 6.3 "A* R", real A)
+//
+// B is the unscaled operator, held as bf16 planes [c][k] (row c of a plane is
+// column c of R, rows of bf_pitch(n) elements):
+//   SRHT   one plane, the sign pattern d_k (-1)^popc(k & mu_c) of the element
+//          formula of Sec. 7.2 -- exact in bf16;
+//   Gauss  two planes z_hi = bf16(z), z_lo = bf16(z - z_hi) of the FP32 draw z
+//          (Sec. 2.4.1).
+// Each FP32 value a of A is split the same way while it is staged:
+// a = a_hi + a_lo + r with |r| <= 2^-16 |a|.  The kernel sums the products
+//   SRHT   a_hi b + a_lo b
+//   Gauss  a_hi z_hi + a_hi z_lo + a_lo z_hi       (a_lo z_lo ~ 2^-16 |a z| dropped)
+// on the tensor cores with FP32 accumulation in tensor memory.
+//
+// Tiles: 128 output rows (TMEM lanes) x NT output columns (TMEM columns,
+// NT <= 256, a multiple of 16) over K stages of 64.  Operand tiles are
+// K-major with the 128-byte swizzle: row r of a tile is 128 bytes (64 bf16 of
+// K), rows 8 apart are 1024 bytes apart, and 16-byte chunk j of row r sits at
+// chunk j ^ (r & 7).  B tiles arrive by TMA in that layout; A tiles are written
+// in it by the converter warps.
+//
+// Work: units are (N tile, M tile, K stage) in that order; a persistent grid
+// of at most one CTA per SM takes a contiguous range of units (stream-K), so
+// a tile is finished by at most two CTAs whose partial sums are added with
+// red.global.add into the zeroed output -- two terms added to zero give the
+// same result in either order.  Inside a CTA the MMA chain for one tile part
+// is cut every FOLD stages: the epilogue warps add each chain's sum into a
+// running total in a second TMEM region, so no single tensor-core
+// accumulation chain covers more than FOLD * 64 values of K.
+//
+// Warp roles (14 warps, one CTA per SM):
+//   warp 0       TMA producer for the B planes (one elected lane)
+//   warp 1       TMEM allocation; one lane issues tcgen05.mma and commits
+//   warps 2..9   converters: load FP32 A (coalesced), split, write bf16 tiles
+//   warps 10..13 epilogue: tcgen05.ld, fold or scale + red.global.add
+// Every wait is bounded: on a timeout the waiting role sets the error flag
+// and an abort flag in shared memory, the other roles stop at their next
+// unit, in-flight copies and MMAs are waited for (bounded) and TMEM is freed.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
+#ifndef JLS_TC_FOLD_STAGES
+#define JLS_TC_FOLD_STAGES 16
+#endif
+
 namespace jls {
+
+namespace {
+
+constexpr int TC_BM = 128;                 // output rows per tile (UMMA M)
+constexpr int TC_BK = 64;                  // K per stage (one 128-byte swizzle row of bf16)
+constexpr int TC_NMAX = 256;               // output columns per tile (UMMA N limit)
+constexpr int TC_CONV_WARPS = 8;
+constexpr int TC_EPI_WARPS = 4;
+constexpr int TC_THREADS = 32 * (2 + TC_CONV_WARPS + TC_EPI_WARPS);
+constexpr int TC_FOLD = JLS_TC_FOLD_STAGES;  // K stages per accumulation chain (0: no cut)
+constexpr uint32_t TC_A_PLANE = TC_BM * TC_BK * 2;  // 16 KB: one bf16 term of an A tile
+constexpr int TC_MAX_STAGES = 4;
+constexpr long TC_SMEM_MAX = 227 * 1024;
+constexpr uint32_t TC_BAR_BYTES = 256;
+
+// ---- tcgen05 wrappers ----------------------------------------------------------
+// Shared-memory matrix descriptor for a K-major operand tile with the 128-byte
+// swizzle: start address >> 4 in bits 0-13, leading offset (unused by this
+// layout) 16 bytes, stride offset 1024 bytes (8 rows x 128 bytes) in bits
+// 32-45, descriptor version 1 in bits 46-47, layout 2 (128-byte swizzle) in
+// bits 61-63.  Tiles are 1024-byte aligned, so the base offset field is 0.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), bf16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns (lane = TMEM lane of this warp's quarter)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void sts_v2(uint32_t a, uint32_t x, uint32_t y) {
+  asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(a), "r"(x), "r"(y) : "memory");
+}
+__device__ __forceinline__ void sts_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+__device__ __forceinline__ void red_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// bf16 pair (x at the lower address) and the bf16 pair of the residuals.
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+struct TcWork {
+  int64_t m_rows, k_len;     // output rows M, reduction length K (= n)
+  int64_t mtiles;
+  int kst;                   // K stages per tile
+  int nt;                    // output columns per tile
+  int c_lo, c_hi;
+  int stages;
+  uint32_t stage_bytes;
+  uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ void decode(const TcWork& w, int64_t u, int& ntile, int64_t& mt, int& ks) {
+  const int64_t per_n = w.mtiles * w.kst;
+  ntile = (int)(u / per_n);
+  const int64_t r = u - (int64_t)ntile * per_n;
+  mt = r / w.kst;
+  ks = (int)(r - mt * w.kst);
+}
+__device__ __forceinline__ bool chain_begins(int64_t u, int64_t u0, int ks) {
+  return u == u0 || ks == 0 || (TC_FOLD > 0 && ks % (TC_FOLD > 0 ? TC_FOLD : 1) == 0);
+}
+__device__ __forceinline__ bool chain_ends(int64_t u, int64_t u1, int ks, int kst) {
+  return u + 1 == u1 || ks + 1 == kst || (TC_FOLD > 0 && (ks + 1) % (TC_FOLD > 0 ? TC_FOLD : 1) == 0);
+}
+
+// Lane 0 waits, the warp learns the outcome.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int* err) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// ---- converters: FP32 A -> bf16 (hi, lo) tiles -------------------------------------
+// S  (TRANS = false): A is M x K row-major.  Converter thread t takes float4
+//    j*256 + t of the 128 x 64 stage: row (j*256 + t) / 16, K quad t % 16, so
+//    16 lanes read one row's 256 contiguous bytes and write its 128-byte
+//    swizzled bf16 row without bank conflicts.
+// S' (TRANS = true): A is K x M row-major (the tile's rows are A's columns).
+//    Thread t takes tile row r = t % 128 and K half t / 128: 32 loads of
+//    A[k][m0 + r], each a 128-byte coalesced warp access; it then owns four
+//    whole 16-byte chunks of row r per plane, stored conflict-free.
+template <bool TRANS>
+__device__ __forceinline__ void conv_load(const float* __restrict__ A, int64_t lda, const TcWork& w, int64_t mt,
+                                          int ks, int ct, float (&v)[32]) {
+  const int64_t m0 = mt * TC_BM;
+  const int64_t k0 = (int64_t)ks * TC_BK;
+  if (!TRANS) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = j * 256 + ct;
+      const int64_t m = m0 + (idx >> 4);
+      const int64_t k = k0 + (idx & 15) * 4;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < w.m_rows) {
+        const float* p = A + m * lda + k;
+        if (k + 3 < w.k_len) {
+          x = __ldg(reinterpret_cast<const float4*>(p));
+        } else {
+          if (k < w.k_len) x.x = __ldg(p);
+          if (k + 1 < w.k_len) x.y = __ldg(p + 1);
+          if (k + 2 < w.k_len) x.z = __ldg(p + 2);
+        }
+      }
+      v[4 * j] = x.x;
+      v[4 * j + 1] = x.y;
+      v[4 * j + 2] = x.z;
+      v[4 * j + 3] = x.w;
+    }
+  } else {
+    const int64_t m = m0 + (ct & 127);
+    const int64_t kb = k0 + (ct >> 7) * 32;
+    const bool mok = m < w.m_rows;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int64_t k = kb + e;
+      v[e] = (mok && k < w.k_len) ? __ldg(A + k * lda + m) : 0.f;
+    }
+  }
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void conv_store(uint32_t a_hi, int ct, const float (&v)[32]) {
+  const uint32_t a_lo = a_hi + TC_A_PLANE;
+  if (!TRANS) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = j * 256 + ct;
+      const uint32_t r = (uint32_t)(idx >> 4), kq = (uint32_t)(idx & 15);
+      const uint32_t off = r * 128 + ((((kq >> 1) ^ (r & 7)) << 4) | ((kq & 1) << 3));
+      uint32_t h0, l0, h1, l1;
+      split2(v[4 * j], v[4 * j + 1], h0, l0);
+      split2(v[4 * j + 2], v[4 * j + 3], h1, l1);
+      sts_v2(a_hi + off, h0, h1);
+      sts_v2(a_lo + off, l0, l1);
+    }
+  } else {
+    const uint32_t r = (uint32_t)(ct & 127), half = (uint32_t)(ct >> 7);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t off = r * 128 + (((half * 4 + c) ^ (r & 7)) << 4);
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) split2(v[8 * c + 2 * q], v[8 * c + 2 * q + 1], h[q], l[q]);
+      sts_v4(a_hi + off, h[0], h[1], h[2], h[3]);
+      sts_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+}  // namespace
+
+template <bool TRANS, int PLANES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_sketch_kernel(const float* __restrict__ A, int64_t lda, const __grid_constant__ CUtensorMap tmB0,
+                     const __grid_constant__ CUtensorMap tmB1, const TcWork w, float scale, float* __restrict__ out,
+                     int64_t ldo, int vec_ok, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  const uint32_t bars = base + (uint32_t)w.stages * w.stage_bytes;
+  // barrier block: full_b[S], full_a[S], empty[S], tmem_full, tmem_empty, done; tmem slot; abort flag
+  auto full_b = [&](int s) { return bars + 8u * s; };
+  auto full_a = [&](int s) { return bars + 8u * (TC_MAX_STAGES + s); };
+  auto empty = [&](int s) { return bars + 8u * (2 * TC_MAX_STAGES + s); };
+  const uint32_t tmem_full = bars + 8u * (3 * TC_MAX_STAGES);
+  const uint32_t tmem_empty = tmem_full + 8u;
+  const uint32_t done_bar = tmem_full + 16u;
+  const uint32_t tmem_slot = tmem_full + 24u;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem_raw + (bars - raw) + 8u * (3 * TC_MAX_STAGES) + 28u);
+  volatile uint32_t* tmem_slot_p = reinterpret_cast<volatile uint32_t*>(smem_raw + (tmem_slot - raw));
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t units = (int64_t)((w.c_hi - w.c_lo + w.nt - 1) / w.nt) * w.mtiles * w.kst;
+  const int64_t u0 = units * blockIdx.x / gridDim.x;
+  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < w.stages; ++s) {
+      mbar_init(full_b(s), 1);
+      mbar_init(full_a(s), TC_CONV_WARPS);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(tmem_full, 1);
+    mbar_init(tmem_empty, TC_EPI_WARPS);
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, w.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot_p;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: B planes ----------------
+    if (lane == 0) {
+      tma_prefetch_desc(&tmB0);
+      if (PLANES == 2) tma_prefetch_desc(&tmB1);
+      const uint32_t b_bytes = (uint32_t)PLANES * (uint32_t)w.nt * 128u;
+      int64_t issued = 0;
+      for (int64_t u = u0; u < u1; ++u) {
+        if (*abort_flag) break;
+        const int64_t i = u - u0;
+        const int s = (int)(i % w.stages);
+        if (!mbar_wait(empty(s), (uint32_t)(((i / w.stages) & 1) ^ 1), err)) {
+          *abort_flag = 1;
+          break;
+        }
+        int ntile, ks;
+        int64_t mt;
+        decode(w, u, ntile, mt, ks);
+        const uint32_t dst = base + (uint32_t)s * w.stage_bytes + 2 * TC_A_PLANE;
+        mbar_arrive_expect_tx(full_b(s), b_bytes);
+        tma_load_2d(dst, &tmB0, full_b(s), ks * TC_BK, w.c_lo + ntile * w.nt);
+        if (PLANES == 2) tma_load_2d(dst + (uint32_t)w.nt * 128u, &tmB1, full_b(s), ks * TC_BK, w.c_lo + ntile * w.nt);
+        issued = i + 1;
+      }
+      // wait for every copy still in flight (the last one issued into each slot)
+      for (int64_t i = std::max<int64_t>(0, issued - w.stages); i < issued; ++i)
+        mbar_wait(full_b((int)(i % w.stages)), (uint32_t)((i / w.stages) & 1), err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(TC_BM, w.nt);
+      uint32_t chain = 0;
+      bool first = true;
+      for (int64_t u = u0; u < u1; ++u) {
+        if (*abort_flag) break;
+        const int64_t i = u - u0;
+        const int s = (int)(i % w.stages);
+        const uint32_t par = (uint32_t)((i / w.stages) & 1);
+        int ntile, ks;
+        int64_t mt;
+        decode(w, u, ntile, mt, ks);
+        if (chain_begins(u, u0, ks)) {
+          if (!mbar_wait(tmem_empty, (chain & 1) ^ 1, err)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          first = true;
+        }
+        if (!mbar_wait(full_b(s), par, err) || !mbar_wait(full_a(s), par, err)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + (uint32_t)s * w.stage_bytes;
+        const uint32_t b0 = st + 2 * TC_A_PLANE, b1 = b0 + (uint32_t)w.nt * 128u;
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const uint32_t ko = (uint32_t)kk * 32u;  // 16 bf16 along K inside the swizzled row
+          const uint64_t dah = sw128_desc(st + ko), dal = sw128_desc(st + TC_A_PLANE + ko);
+          const uint64_t db0 = sw128_desc(b0 + ko);
+          umma_bf16(tmem, dah, db0, idesc, first ? 0u : 1u);
+          umma_bf16(tmem, dal, db0, idesc, 1u);
+          if (PLANES == 2) umma_bf16(tmem, dah, sw128_desc(b1 + ko), idesc, 1u);
+          first = false;
+        }
+        umma_commit(empty(s));
+        if (chain_ends(u, u1, ks, w.kst)) {
+          umma_commit(tmem_full);
+          ++chain;
+        }
+      }
+      // all MMAs issued by this thread have completed once done_bar flips
+      umma_commit(done_bar);
+      mbar_wait(done_bar, 0, err);
+    }
+  } else if (warp < 2 + TC_CONV_WARPS) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 64;
+    float va[32], vb[32];
+    int64_t u = u0;
+    auto put = [&](const float (&v)[32], int64_t uu) -> bool {
+      const int64_t i = uu - u0;
+      const int s = (int)(i % w.stages);
+      if (*abort_flag) return false;
+      if (!warp_wait(empty(s), (uint32_t)(((i / w.stages) & 1) ^ 1), err)) {
+        *abort_flag = 1;
+        return false;
+      }
+      conv_store<TRANS>(base + (uint32_t)s * w.stage_bytes, ct, v);
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full_a(s));
+      return true;
+    };
+    if (u < u1) {
+      int ntile, ks;
+      int64_t mt;
+      decode(w, u, ntile, mt, ks);
+      conv_load<TRANS>(A, lda, w, mt, ks, ct, va);
+    }
+    while (u < u1) {
+      int ntile, ks;
+      int64_t mt;
+      if (u + 1 < u1) {
+        decode(w, u + 1, ntile, mt, ks);
+        conv_load<TRANS>(A, lda, w, mt, ks, ct, vb);
+      }
+      if (!put(va, u)) break;
+      if (++u >= u1) break;
+      if (u + 1 < u1) {
+        decode(w, u + 1, ntile, mt, ks);
+        conv_load<TRANS>(A, lda, w, mt, ks, ct, va);
+      }
+      if (!put(vb, u)) break;
+      ++u;
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    uint32_t chain = 0;
+    bool has_total = false;
+    for (int64_t u = u0; u < u1; ++u) {
+      int ntile, ks;
+      int64_t mt;
+      decode(w, u, ntile, mt, ks);
+      if (chain_begins(u, u0, ks)) has_total = !(u == u0 || ks == 0);
+      if (!chain_ends(u, u1, ks, w.kst)) continue;
+      if (*abort_flag) break;
+      if (!warp_wait(tmem_full, chain & 1, err)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const bool emit = (u + 1 == u1) || (ks + 1 == w.kst);
+      const int64_t row = mt * TC_BM + q * 32 + lane;
+      for (int cc = 0; cc < w.nt; cc += 16) {
+        uint32_t v[16], t[16];
+        tmem_ld16(trow + (uint32_t)cc, v);
+        if (has_total) tmem_ld16(trow + (uint32_t)(w.nt + cc), t);
+        tmem_wait_ld();
+        if (has_total) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(t[j]));
+        }
+        if (!emit) {
+          tmem_st16(trow + (uint32_t)(w.nt + cc), v);
+          continue;
+        }
+        const int c0 = w.c_lo + ntile * w.nt + cc;
+        if (row < w.m_rows && c0 < w.c_hi) {
+          float* p = out + row * ldo + c0;
+          if (vec_ok && c0 + 16 <= w.c_hi) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              red_v4(p + j, scale * __uint_as_float(v[j]), scale * __uint_as_float(v[j + 1]),
+                     scale * __uint_as_float(v[j + 2]), scale * __uint_as_float(v[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < w.c_hi) atomicAdd(p + j, scale * __uint_as_float(v[j]));
+          }
+        }
+      }
+      if (!emit) tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);
+      ++chain;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, w.tmem_cols);
+}
+
+namespace {
+
+int encode_plane(CUtensorMap* tm, const uint16_t* plane, int64_t n, int rows, int nt) {
+  PFN_encodeTiled enc = get_encode_tiled();
+  if (!enc) return SK_ERR_DEVICE;
+  const cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(bf_pitch(n) * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)nt};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(plane), gdim, gstride, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_ALIGN;
+}
+
+uint32_t tmem_cols_for(int cols) {
+  uint32_t c = 32;
+  while ((int)c < cols) c <<= 1;
+  return c;
+}
+
+int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, float scale, float* out, int64_t ldo,
+              cudaStream_t s) {
+  const int planes = h->kind == SK_GAUSS ? 2 : 1;
+  const uint16_t* p0 = h->kind == SK_GAUSS ? h->zhi : h->srht_pm1;
+  const uint16_t* p1 = h->kind == SK_GAUSS ? h->zlo : h->srht_pm1;
+  TcWork w{};
+  w.m_rows = trans ? A->cols : A->rows;
+  w.k_len = h->n;
+  w.mtiles = (w.m_rows + TC_BM - 1) / TC_BM;
+  w.kst = (int)((h->n + TC_BK - 1) / TC_BK);
+  const int ncols = c_hi - c_lo;
+  const int ntiles = (ncols + TC_NMAX - 1) / TC_NMAX;
+  w.nt = ((ncols + ntiles - 1) / ntiles + 15) / 16 * 16;
+  w.c_lo = c_lo;
+  w.c_hi = c_hi;
+  w.stage_bytes = 2 * TC_A_PLANE + (uint32_t)planes * (uint32_t)w.nt * 128u;
+  const long avail = TC_SMEM_MAX - 1024 - (long)TC_BAR_BYTES;
+  w.stages = (int)std::min<long>(TC_MAX_STAGES, avail / (long)w.stage_bytes);
+  if (w.stages < 2) return SK_ERR_UNSUPPORTED;
+  w.tmem_cols = tmem_cols_for(TC_FOLD > 0 ? 2 * w.nt : w.nt);
+  if (w.tmem_cols > 512) return SK_ERR_UNSUPPORTED;
+
+  CUtensorMap t0, t1;
+  JLS_CHECK(encode_plane(&t0, p0, h->n, c_hi, w.nt));
+  JLS_CHECK(encode_plane(&t1, p1, h->n, c_hi, w.nt));
+  JLS_CHECK_CUDA(cudaMemset2DAsync(out + c_lo, ldo * sizeof(float), 0, (size_t)ncols * sizeof(float),
+                                   (size_t)w.m_rows, s));
+  const int64_t tiles = (int64_t)ntiles * w.mtiles;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), tiles));
+  const size_t smem = 1024 + (size_t)w.stages * w.stage_bytes + TC_BAR_BYTES;
+  const int vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0 && ldo % 4 == 0 && c_lo % 4 == 0) ? 1 : 0;
+  const float* a = static_cast<const float*>(A->A);
+#define JLS_TC_LAUNCH(TR, PL)                                                                                \
+  do {                                                                                                       \
+    auto kern = tc_sketch_kernel<TR, PL>;                                                                   \
+    JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
+    kern<<<grid, TC_THREADS, smem, s>>>(a, A->ld, t0, t1, w, scale, out, ldo, vec_ok, h->d_err);            \
+  } while (0)
+  if (trans && planes == 2) JLS_TC_LAUNCH(true, 2);
+  else if (trans) JLS_TC_LAUNCH(true, 1);
+  else if (planes == 2) JLS_TC_LAUNCH(false, 2);
+  else JLS_TC_LAUNCH(false, 1);
+#undef JLS_TC_LAUNCH
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+}  // namespace
 
 int dense_apply_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
                    void* St, int64_t ldSt, cudaStream_t s) {
-  (void)h; (void)A; (void)which; (void)c_lo; (void)c_hi; (void)scale; (void)S; (void)ldS; (void)St; (void)ldSt;
-  (void)s;
-  return SK_ERR_UNSUPPORTED;
+  if (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)) return SK_ERR_DTYPE;
+  if (c_hi <= c_lo) return SK_OK;
+  if (h->kind == SK_GAUSS) JLS_CHECK(gen_gauss(h, 2, h->d_total, s));
+  else JLS_CHECK(gen_srht_pm1(h, h->d_total, s));
+  if (which & SK_S) JLS_CHECK(launch_tc(h, A, false, c_lo, c_hi, (float)scale, (float*)S, ldS, s));
+  if (which & SK_ST) JLS_CHECK(launch_tc(h, A, true, c_lo, c_hi, (float)scale, (float*)St, ldSt, s));
+  return SK_OK;
 }
 
 }  // namespace jls

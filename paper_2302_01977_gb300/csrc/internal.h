@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/jlsketch.h"
@@ -18,6 +19,10 @@ constexpr int SJLT_TILE_F64 = 64;
 constexpr int SJLT_MAX_ALPHA = 32;
 constexpr int MAX_D = 8192;
 constexpr int MAX_BLOCKS = 256;  // SJLT blocks (initial + increments) a handle can hold
+
+// Row pitch (elements) of the bf16 operator planes [c][k] read by the
+// tensor-core path: rows start on 128-byte boundaries, as TMA wants.
+__host__ __device__ inline int64_t bf_pitch(int64_t n) { return (n + 63) / 64 * 64; }
 
 // Tiled CCS of R (Sec. 6.1's compressed column storage, cut into tiles of
 // `tile` rows): for tile t, entries[t*e_stride + p] sorted by column (rows
@@ -76,11 +81,11 @@ struct sk_op {
   // Gaussian: unscaled z, transposed (column c of R contiguous over rows)
   float* z32 = nullptr;
   double* z64 = nullptr;
-  uint16_t* zhi = nullptr;     // bf16 bits
+  uint16_t* zhi = nullptr;     // bf16 bits, rows of bf_pitch(n)
   uint16_t* zlo = nullptr;
   int z32_cols = 0, z64_cols = 0, zbf_cols = 0;
 
-  // SRHT +-1 plane for the tensor-core path (bf16 bits, d_max x n)
+  // SRHT +-1 plane for the tensor-core path (bf16 bits, d_max rows of bf_pitch(n))
   uint16_t* srht_pm1 = nullptr;
   int pm1_cols = 0;
 
@@ -122,6 +127,13 @@ int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, 
 int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
               int c_end, double eps_rel, double eps_abs, int* stop, double* nh, double* nt,
               cudaStream_t s);
+
+// --- sjlt_apply.cu host helpers (also used by gemm_tc.cu) ---
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+PFN_encodeTiled get_encode_tiled();  // cuTensorMapEncodeTiled from the driver, or null
+int num_sms();
 
 // --- jlsketch.cu helpers ---
 void note_launch();  // counts kernel launches (sketch_launch_count)

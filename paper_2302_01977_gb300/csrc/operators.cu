@@ -303,22 +303,24 @@ __global__ void gauss_gen_kernel(int64_t n, int c0, int c1, uint64_t seed, float
   const int64_t o = (int64_t)c * n + i;
   if (z32) z32[o] = (float)z;
   if (z64) z64[o] = z;
-  if (zhi) {
+  if (zhi) {  // z = z_hi + z_lo + O(2^-16 |z|): the two bf16 terms of (float)z
+    const int64_t ob = (int64_t)c * bf_pitch(n) + i;
     const float zf = (float)z;
     const __nv_bfloat16 hi = __float2bfloat16_rn(zf);
-    zhi[o] = hi;
-    zlo[o] = __float2bfloat16_rn(zf - __bfloat162float(hi));
+    zhi[ob] = hi;
+    zlo[ob] = __float2bfloat16_rn(zf - __bfloat162float(hi));
   }
 }
 
 int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s) {
   const size_t cells = (size_t)h->d_max * h->n;
+  const size_t bf_cells = (size_t)h->d_max * bf_pitch(h->n);
   int* have = plane == 0 ? &h->z32_cols : plane == 1 ? &h->z64_cols : &h->zbf_cols;
   if (plane == 0 && !h->z32) JLS_CHECK_CUDA(cudaMalloc(&h->z32, cells * sizeof(float)));
   if (plane == 1 && !h->z64) JLS_CHECK_CUDA(cudaMalloc(&h->z64, cells * sizeof(double)));
   if (plane == 2 && !h->zhi) {
-    JLS_CHECK_CUDA(cudaMalloc(&h->zhi, cells * sizeof(uint16_t)));
-    JLS_CHECK_CUDA(cudaMalloc(&h->zlo, cells * sizeof(uint16_t)));
+    JLS_CHECK_CUDA(cudaMalloc(&h->zhi, bf_cells * sizeof(uint16_t)));
+    JLS_CHECK_CUDA(cudaMalloc(&h->zlo, bf_cells * sizeof(uint16_t)));
   }
   if (*have >= c_end) return SK_OK;
   const int c0 = *have;
@@ -332,18 +334,19 @@ int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s) {
   return SK_OK;
 }
 
-// SRHT +-1 plane (bf16 bits, exact), transposed: pm1[c * n + i] = d_i (-1)^popc(i & mu_c).
+// SRHT +-1 plane (bf16 bits, exact), transposed: pm1[c * bf_pitch(n) + i] = d_i (-1)^popc(i & mu_c).
 __global__ void srht_pm1_kernel(int64_t n, int c0, int c1, const int8_t* __restrict__ diag,
                                 const int32_t* __restrict__ mu, uint16_t* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int c = c0 + blockIdx.y;
   if (i >= n || c >= c1) return;
   const int neg = (__popcll((unsigned long long)i & (unsigned long long)(uint32_t)mu[c]) & 1) ^ (diag[i] < 0);
-  out[(int64_t)c * n + i] = neg ? (uint16_t)0xBF80 : (uint16_t)0x3F80;  // bf16 -1 / +1
+  out[(int64_t)c * bf_pitch(n) + i] = neg ? (uint16_t)0xBF80 : (uint16_t)0x3F80;  // bf16 -1 / +1
 }
 
 int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s) {
-  if (!h->srht_pm1) JLS_CHECK_CUDA(cudaMalloc(&h->srht_pm1, (size_t)h->d_max * h->n * sizeof(uint16_t)));
+  if (!h->srht_pm1)
+    JLS_CHECK_CUDA(cudaMalloc(&h->srht_pm1, (size_t)h->d_max * bf_pitch(h->n) * sizeof(uint16_t)));
   if (h->pm1_cols >= c_end) return SK_OK;
   dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)(c_end - h->pm1_cols));
   srht_pm1_kernel<<<grid, 256, 0, s>>>(h->n, h->pm1_cols, c_end, h->srht_diag, h->srht_mu, h->srht_pm1); note_launch();

@@ -449,10 +449,6 @@ __global__ void __launch_bounds__(16 * 32, 1)
 
 // ---------------------------------------------------------------------------
 // host side
-typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 PFN_encodeTiled get_encode_tiled() {
   static PFN_encodeTiled fn = nullptr;
   if (!fn) {
