@@ -10,8 +10,9 @@
 // block adds zero columns to Q, which do not change Q Q^T).
 //
 // Tall-skinny products X^T Y (rows ~ n, widths <= 512) run on CUDA cores: each
-// CTA reduces a chunk of rows into a 32 x 32 tile of partial sums, chunks are
-// summed in FP64 by a second kernel.  Frobenius norms are FP64 sums of squares.
+// CTA reduces a chunk of rows into a 64 x 64 tile of partial sums, chunks are
+// summed in FP64 by a second kernel.  Frobenius norms are FP64 sums of squares,
+// and the test synchronizes with the host once, to read them.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -46,37 +47,68 @@ int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, 
 
 // ---------------------------------------------------------------------------
 // partial[chunk][i][j] = sum_{r in chunk} X[r][i] * Y[r][j]   (i < p, j < q)
+// One CTA: a 64 x 64 block of (i, j) over one chunk of rows; 256 threads with
+// 4 x 4 outputs each, rows staged 32 at a time (coalesced 256-byte row reads)
+// and the next 32 rows loaded into registers while the current ones are used.
 template <typename T>
 __global__ void __launch_bounds__(256)
     tsgemm_tn_partial(const T* __restrict__ X, int64_t ldx, int p, const T* __restrict__ Y, int64_t ldy, int q,
                       int64_t rows, int64_t rows_per_chunk, double* __restrict__ part) {
-  __shared__ T xs[32][33];
-  __shared__ T ys[32][33];
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  __shared__ __align__(16) T xs[32][68];
+  __shared__ __align__(16) T ys[32][68];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
   const int64_t r_begin = (int64_t)blockIdx.z * rows_per_chunk;
   const int64_t r_end = min64(rows, r_begin + rows_per_chunk);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty in 0..7
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  // this thread stages elements e = threadIdx.x + 256 u of each 32 x 64 tile: row e / 64, column e % 64
+  const int c = threadIdx.x & 63, rb = threadIdx.x >> 6;
+  const bool xin = i0 + c < p, yin = j0 + c < q;
+  T xr[8], yr[8];
+  auto fetch = [&](int64_t r0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t r = r0 + rb + 4 * u;
+      xr[u] = (r < r_end && xin) ? X[r * ldx + i0 + c] : T(0);
+      yr[u] = (r < r_end && yin) ? Y[r * ldy + j0 + c] : T(0);
+    }
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) acc[a][cc] = T(0);
+  if (r_begin < r_end) fetch(r_begin);
   for (int64_t r0 = r_begin; r0 < r_end; r0 += 32) {
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int64_t r = r0 + rr;
-      xs[rr][tx] = (r < r_end && i0 + tx < p) ? X[r * ldx + i0 + tx] : T(0);
-      ys[rr][tx] = (r < r_end && j0 + tx < q) ? Y[r * ldy + j0 + tx] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      xs[rb + 4 * u][c] = xr[u];
+      ys[rb + 4 * u][c] = yr[u];
     }
     __syncthreads();
+    if (r0 + 32 < r_end) fetch(r0 + 32);
 #pragma unroll 8
     for (int rr = 0; rr < 32; ++rr) {
-      const T yv = ys[rr][tx];
+      T xv[4], yv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(xs[rr][ty + 8 * u], yv, acc[u]);
+      for (int a = 0; a < 4; ++a) xv[a] = xs[rr][ty * 4 + a];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) yv[cc] = ys[rr][tx * 4 + cc];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc[a][cc] = fma(xv[a], yv[cc], acc[a][cc]);
     }
     __syncthreads();
   }
   double* out = part + (int64_t)blockIdx.z * p * q;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = i0 + ty + 8 * u, j = j0 + tx;
-    if (i < p && j < q) out[(int64_t)i * q + j] = (double)acc[u];
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int j = j0 + tx * 4 + cc;
+      if (i < p && j < q) out[(int64_t)i * q + j] = (double)acc[a][cc];
+    }
   }
 }
 
@@ -88,116 +120,201 @@ __global__ void reduce_partials(const double* __restrict__ part, int nchunks, in
   }
 }
 
-// W[r][j] -= sum_i Q[r][i] * G[i][j]   (G is p x q in FP64, q <= 64)
-template <typename T>
+// Y[r][j] = sum_{i < p} X[r][i] M[i][j]     (SUB = false)
+// Y[r][j] -= sum_{i < p} X[r][i] M[i][j]    (SUB = true)
+// for j < q <= 64; M is FP64, row-major with leading dimension ldm.  One CTA
+// owns 64 rows and reads all of them before it writes, so Y may alias X.
+// The next 32-wide slice of X and M is loaded into registers while the
+// current one is used.
+template <typename T, bool SUB>
 __global__ void __launch_bounds__(256)
-    sub_qg_kernel(T* __restrict__ W, int64_t ldw, int q, const T* __restrict__ Q, int64_t ldq, int p,
-                  const double* __restrict__ G, int64_t rows) {
-  __shared__ T gs[32][64];
-  __shared__ T qs[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  const int j = threadIdx.x & 63, rg = threadIdx.x >> 6;  // rg 0..3 -> 8 rows each
-  T acc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = T(0);
-  for (int i0 = 0; i0 < p; i0 += 32) {
-    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
-      const int ii = e / 64, jj = e % 64;
-      gs[ii][jj] = (i0 + ii < p && jj < q) ? (T)G[(int64_t)(i0 + ii) * q + jj] : T(0);
-    }
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-      const int rr = e / 32, ii = e % 32;
-      const int64_t r = r0 + rr;
-      qs[rr][ii] = (r < rows && i0 + ii < p) ? Q[r * ldq + i0 + ii] : T(0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int ii = 0; ii < 32; ++ii) {
-      const T g = gs[ii][j];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] = fma(qs[rg * 8 + u][ii], g, acc[u]);
-    }
-    __syncthreads();
-  }
-  if (j < q)
+    rows_small_gemm(const T* X, int64_t ldx, int p, const double* __restrict__ M, int64_t ldm, int q, T* Y,
+                    int64_t ldy, int64_t rows) {
+  __shared__ __align__(16) T xs[32][68];  // [i][row]
+  __shared__ __align__(16) T ms[32][68];  // [i][col]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  // staging: X element (row e / 32, i e % 32), M element (i e / 64, col e % 64) for e = threadIdx.x + 256 u
+  const int xi = threadIdx.x & 31, xr0 = threadIdx.x >> 5;
+  const int mc = threadIdx.x & 63, mi0 = threadIdx.x >> 6;
+  T xv_n[8], mv_n[8];
+  auto fetch = [&](int i0) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int64_t r = r0 + rg * 8 + u;
-      if (r < rows) W[r * ldw + j] -= acc[u];
+      const int64_t r = r0 + xr0 + 8 * u;
+      xv_n[u] = (r < rows && i0 + xi < p) ? X[r * ldx + i0 + xi] : T(0);
+      const int i = i0 + mi0 + 4 * u;
+      mv_n[u] = (i < p && mc < q) ? (T)M[(int64_t)i * ldm + mc] : T(0);
     }
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+  fetch(0);
+  for (int i0 = 0; i0 < p; i0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      xs[xi][xr0 + 8 * u] = xv_n[u];
+      ms[mi0 + 4 * u][mc] = mv_n[u];
+    }
+    __syncthreads();
+    if (i0 + 32 < p) fetch(i0 + 32);
+#pragma unroll 8
+    for (int ii = 0; ii < 32; ++ii) {
+      T xv[4], mv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xv[a] = xs[ii][ty * 4 + a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mv[c] = ms[ii][tx * 4 + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(xv[a], mv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = r0 + ty * 4 + a;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = tx * 4 + c;
+      if (j < q) Y[r * ldy + j] = SUB ? Y[r * ldy + j] - acc[a][c] : acc[a][c];
+    }
+  }
 }
 
-// Cholesky of the b x b (b <= 64) FP64 Gram matrix with column dropping, then
-// U = L^{-T} (upper triangular, dropped columns zero).  One CTA of 64 threads.
-__global__ void chol_inv_kernel(const double* __restrict__ Gm, int b, double* __restrict__ U, int* err) {
-  extern __shared__ double chol_sh[];
-  double (*L)[65] = reinterpret_cast<double (*)[65]>(chol_sh);
-  double (*Li)[65] = reinterpret_cast<double (*)[65]>(chol_sh + 64 * 65);
-  __shared__ int drop[64];
-  const int t = threadIdx.x;
-  for (int i = 0; i < b; ++i)
-    if (t < b) L[i][t] = Gm[i * b + t];
+// 1 / sqrt(x) for x > 0.  In FP64: Newton-Raphson steps y <- y (3 - x y^2) / 2
+// from the FP32 hardware estimate (relative error <= 2^-21; one step leaves
+// <= 1.5 (2^-21)^2 < 1e-12, two steps reach FP64 rounding).  GB300's FP64
+// square root and division each take several hundred cycles of latency, a
+// Newton step four dependent FP64 operations.  Outside FP32's exponent range
+// the plain FP64 sqrt and division are used.
+template <int STEPS>
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+#pragma unroll
+  for (int s = 0; s < STEPS; ++s) y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
+}
+
+// Cholesky G = L L^T of the b x b (b <= 64) FP64 Gram matrix, right-looking,
+// in arithmetic type A, with column dropping: a pivot <= 1e-26 of the largest
+// diagonal (or a zero Gram matrix) zeroes that column of L.  Writes L (lower,
+// b x b row-major, type T, zeros above the diagonal) and rinv[j] = 1 / L[j][j]
+// (0 for a dropped column).  One CTA of 256 threads; the pivot of step k + 1
+// is taken by thread 0 while warps 1..7 finish step k's trailing update.
+template <typename A, typename T, int NR>
+__global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restrict__ Gm, int b, T* __restrict__ Lo,
+                                                          T* __restrict__ rinv_out) {
+  __shared__ A L[64][65];
+  __shared__ A rinv[64];
+  __shared__ A s_sq[2], s_iv[2];
+  __shared__ A s_dmax;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < b * b; e += 256) L[e / b][e % b] = (A)Gm[e];
   __syncthreads();
-  double dmax = 0;
-  for (int i = 0; i < b; ++i) dmax = fmax(dmax, L[i][i]);
-  for (int k = 0; k < b; ++k) {
-    __syncthreads();
-    const double pk = L[k][k];
-    const bool dk = !(pk > 1e-26 * dmax) || !(dmax > 0);
-    if (t == 0) drop[k] = dk;
-    __syncthreads();
-    const double sq = dk ? 0.0 : sqrt(pk);
-    if (t >= k && t < b) L[t][k] = dk ? 0.0 : L[t][k] / sq;  // column k of L (L[k][k] = sqrt)
-    __syncthreads();
-    if (t > k && t < b)
-      for (int j = k + 1; j <= t; ++j) L[t][j] -= L[t][k] * L[j][k];
+  if (tid < 32) {
+    A m = 0;
+    for (int i = tid; i < b; i += 32) m = fmax(m, L[i][i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) s_dmax = m;
   }
   __syncthreads();
-  // Li = L^{-1} (lower), column by column: thread t solves column t
-  if (t < b) {
-    for (int i = 0; i < b; ++i) Li[i][t] = 0.0;
-    if (!drop[t]) {
-      Li[t][t] = 1.0 / L[t][t];
-      for (int i = t + 1; i < b; ++i) {
-        if (drop[i]) continue;
-        double sacc = 0;
-        for (int k = t; k < i; ++k) sacc += L[i][k] * Li[k][t];
-        Li[i][t] = -sacc / L[i][i];
+  auto pivot = [&](int k) {  // thread 0 only
+    const A dmax = s_dmax, pk = L[k][k];
+    const bool dk = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
+    A iv = A(0);
+    if (!dk) {
+      if constexpr (sizeof(A) == 8) iv = rsqrt_nr<NR>(pk);
+      else iv = 1.0f / sqrtf(pk);
+    }
+    s_iv[k & 1] = iv;
+    s_sq[k & 1] = dk ? A(0) : pk * iv;
+    rinv[k] = iv;
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  const int w = tid >> 5;
+  const int ut = tid - 32, ti = ut / 14, tj = ut % 14;  // warps 1..7: 16 x 14 update grid
+  for (int k = 0; k < b; ++k) {
+    const A iv = s_iv[k & 1];
+    if (tid > k && tid < b) L[tid][k] *= iv;
+    if (tid == k) L[k][k] = s_sq[k & 1];
+    __syncthreads();
+    if (k + 1 < b && tid > k && tid < b) L[tid][k + 1] -= L[tid][k] * L[k + 1][k];  // column k + 1 first
+    __syncthreads();
+    if (k + 1 < b) {
+      if (tid == 0) {
+        pivot(k + 1);
+      } else if (w > 0 && ti < 16) {
+        for (int i = k + 2 + ti; i < b; i += 16) {
+          const A lik = L[i][k];
+          for (int j = k + 2 + tj; j <= i; j += 14) L[i][j] -= lik * L[j][k];
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // U = Li^T : U[i][j] = Li[j][i]
-  if (t < b)
-    for (int i = 0; i < b; ++i) U[i * b + t] = Li[t][i];
-  (void)err;
+  for (int e = tid; e < b * b; e += 256) {
+    const int i = e / b, j = e % b;
+    Lo[e] = j <= i ? (T)L[i][j] : T(0);
+  }
+  if (tid < b) rinv_out[tid] = (T)rinv[tid];
 }
 
-// Wout[r][j] = sum_{i <= j} W[r][i] * U[i][j]  (b <= 64), U FP64; 16 rows per CTA
+// W[r][:] <- W[r][:] L^{-T} (b <= 64 columns) in place, by forward
+// substitution x_j = (w_j - sum_{i<j} x_i L[j][i]) / L[j][j], one thread per
+// row, with rinv[j] = 1 / L[j][j] (0 for a dropped column, whose x_j is then 0).
+// trsm_rows<T>() rows per CTA, staged through shared memory with coalesced accesses.
 template <typename T>
-__global__ void __launch_bounds__(256)
-    mul_upper_kernel(const T* __restrict__ W, int64_t ldw, const double* __restrict__ U, int b, T* __restrict__ Wo,
-                     int64_t ldo, int64_t rows) {
-  __shared__ T us[64][64];
-  __shared__ T ws[16][65];
-  for (int e = threadIdx.x; e < 64 * 64; e += 256) {
-    const int i = e / 64, j = e % 64;
-    us[i][j] = (i < b && j < b) ? (T)U[i * b + j] : T(0);
+constexpr int trsm_rows() {
+  return sizeof(T) == 4 ? 64 : 16;
+}
+template <typename T>
+__global__ void __launch_bounds__(trsm_rows<T>()) rows_trsm_kernel(T* W, int64_t ldw, int b, const T* __restrict__ Lo,
+                                                                   const T* __restrict__ rinv, int64_t rows) {
+  constexpr int RT = trsm_rows<T>();
+  __shared__ __align__(16) T ls[64][64];
+  __shared__ T rv[64];
+  __shared__ T ws[RT][65];
+  const int64_t r0 = (int64_t)blockIdx.x * RT;
+  for (int e = threadIdx.x; e < 64 * 64; e += RT) {
+    const int j = e >> 6, i = e & 63;
+    ls[j][i] = (j < b && i < b) ? Lo[j * b + i] : T(0);
   }
-  const int64_t r0 = (int64_t)blockIdx.x * 16;
-  for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-    const int rr = e / 64, i = e % 64;
+  for (int j = threadIdx.x; j < 64; j += RT) rv[j] = j < b ? rinv[j] : T(0);
+  for (int e = threadIdx.x; e < RT * 64; e += RT) {
+    const int rr = e >> 6, j = e & 63;
     const int64_t r = r0 + rr;
-    ws[rr][i] = (r < rows && i < b) ? W[r * ldw + i] : T(0);
+    ws[rr][j] = (r < rows && j < b) ? W[r * ldw + j] : T(0);
   }
   __syncthreads();
-  const int j = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  for (int u = 0; u < 4; ++u) {
-    const int rr = rg * 4 + u;
+  T x[64];
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    T a0 = ws[t][j], a1 = T(0);
+#pragma unroll
+    for (int i = 0; i + 1 < j; i += 2) {
+      a0 = fma(-x[i], ls[j][i], a0);
+      a1 = fma(-x[i + 1], ls[j][i + 1], a1);
+    }
+    if (j & 1) a0 = fma(-x[j - 1], ls[j][j - 1], a0);
+    x[j] = (a0 + a1) * rv[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 64; ++j) ws[t][j] = x[j];
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * 64; e += RT) {
+    const int rr = e >> 6, j = e & 63;
     const int64_t r = r0 + rr;
-    T acc = T(0);
-    for (int i = 0; i <= j && i < b; ++i) acc = fma(ws[rr][i], us[i][j], acc);
-    if (r < rows && j < b) Wo[r * ldo + j] = acc;
+    if (r < rows && j < b) W[r * ldw + j] = ws[rr][j];
   }
 }
 
@@ -234,25 +351,22 @@ __global__ void sumsq_partial(const T* __restrict__ W, int64_t ldw, int64_t rows
 namespace {
 
 constexpr int NORM_GRID = 256;
-constexpr int CHOL_SMEM = 2 * 64 * 65 * sizeof(double);
 
 struct Scratch {
   void* W;        // rows x wmax (T)
-  void* W2;       // rows x 64 (T)
   double* part;   // partial products
   double* G;      // up to d_max x wmax
-  double* U;      // 64 x 64
-  double* norms;  // NORM_GRID partials
+  double* U;      // Cholesky factor (64 x 64) and reciprocal pivots (64), type T
+  double* norms;  // 2 x NORM_GRID partials (||S~||^2, ||S^||^2)
   size_t part_elems;
 };
 
 int ensure_scratch(sk_op* h, int64_t rows, int dtype, int wmax, Scratch* sc, int nchunks) {
   const size_t es = elem_size(dtype);
   const size_t wb = ((size_t)rows * wmax * es + 255) / 256 * 256;
-  const size_t w2b = ((size_t)rows * 64 * es + 255) / 256 * 256;
   const size_t part_elems = (size_t)nchunks * h->d_max * wmax;
   const size_t gb = (size_t)h->d_max * wmax * sizeof(double);
-  const size_t need = wb + w2b + part_elems * sizeof(double) + gb + 64 * 64 * sizeof(double) + NORM_GRID * sizeof(double);
+  const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 2 * NORM_GRID * sizeof(double);
   if (h->scratch_bytes < need) {
     if (h->scratch) cudaFree(h->scratch);
     h->scratch = nullptr;
@@ -263,14 +377,12 @@ int ensure_scratch(sk_op* h, int64_t rows, int dtype, int wmax, Scratch* sc, int
   uint8_t* p = static_cast<uint8_t*>(h->scratch);
   sc->W = p;
   p += wb;
-  sc->W2 = p;
-  p += w2b;
   sc->part = reinterpret_cast<double*>(p);
   p += part_elems * sizeof(double);
   sc->G = reinterpret_cast<double*>(p);
   p += gb;
   sc->U = reinterpret_cast<double*>(p);
-  p += 64 * 64 * sizeof(double);
+  p += 64 * 65 * sizeof(double);
   sc->norms = reinterpret_cast<double*>(p);
   sc->part_elems = part_elems;
   return SK_OK;
@@ -279,11 +391,26 @@ int ensure_scratch(sk_op* h, int64_t rows, int dtype, int wmax, Scratch* sc, int
 template <typename T>
 int tsgemm(const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q, int64_t rows, int nchunks, double* part,
            double* out, cudaStream_t s) {
-  const int64_t rpc = ((rows + nchunks - 1) / nchunks + 31) / 32 * 32;
+  // about two CTAs per SM; nchunks bounds the partial-sum buffer
+  const int blocks = ((p + 63) / 64) * ((q + 63) / 64);
+  const int want = std::max(1, std::min(nchunks, (2 * num_sms() + blocks - 1) / blocks));
+  const int64_t rpc = ((rows + want - 1) / want + 31) / 32 * 32;
   const int nch = (int)((rows + rpc - 1) / rpc);
-  dim3 grid((p + 31) / 32, (q + 31) / 32, nch);
+  dim3 grid((p + 63) / 64, (q + 63) / 64, nch);
   tsgemm_tn_partial<T><<<grid, 256, 0, s>>>(X, ldx, p, Y, ldy, q, rows, rpc, part); note_launch();
   reduce_partials<<<64, 256, 0, s>>>(part, nch, (int64_t)p * q, out); note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// W (rows x b, ld ldw) <- W - Q G for G = Q^T W (p x b, FP64, ld b), 64 columns at a time
+template <typename T>
+int sub_qg(T* W, int64_t ldw, int b, const T* Q, int64_t ldq, int p, const double* G, int64_t rows, cudaStream_t s) {
+  for (int j0 = 0; j0 < b; j0 += 64) {
+    const int q = std::min(64, b - j0);
+    rows_small_gemm<T, true><<<(unsigned)((rows + 63) / 64), 256, 0, s>>>(Q, ldq, p, G + j0, b, q, W + j0, ldw,
+                                                                            rows); note_launch();
+  }
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -296,31 +423,16 @@ int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int6
   const T* Q = static_cast<const T*>(B.Q);
   for (int pass = 0; pass < 2; ++pass) {
     JLS_CHECK(tsgemm<T>(Q, h->d_max, B.cols, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
-    for (int j0 = 0; j0 < b; j0 += 64) {
-      // G is B.cols x b row-major; sub_qg reads a 64-column slab via a shifted base
-      const int q = std::min(64, b - j0);
-      // copy the slab into contiguous form expected by sub_qg (ld = q)
-      // (sub_qg indexes G[i * q + j]); reuse part as staging
-      double* slab = sc.part;
-      dim3 g1((unsigned)((B.cols * 64 + 255) / 256));
-      copy_block_kernel<double><<<g1, 256, 0, s>>>(sc.G + j0, b, slab, q, B.cols, q); note_launch();
-      sub_qg_kernel<T><<<(unsigned)((rows + 31) / 32), 256, 0, s>>>(W + j0, ldw, q, Q, h->d_max, B.cols, slab, rows); note_launch();
-    }
-    JLS_CHECK_CUDA(cudaGetLastError());
+    JLS_CHECK(sub_qg<T>(W, ldw, b, Q, h->d_max, B.cols, sc.G, rows, s));
   }
   return SK_OK;
 }
 
+// NORM_GRID partial sums of squares of W into `part` (no synchronization)
 template <typename T>
-int sumsq(const T* W, int64_t ldw, int64_t rows, int b, const Scratch& sc, double* out, cudaStream_t s) {
-  sumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, sc.norms); note_launch();
+int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cudaStream_t s) {
+  sumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, part); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
-  double part[NORM_GRID];
-  JLS_CHECK_CUDA(cudaMemcpyAsync(part, sc.norms, sizeof(part), cudaMemcpyDeviceToHost, s));
-  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
-  double acc = 0;
-  for (int i = 0; i < NORM_GRID; ++i) acc += part[i];  // fixed order: deterministic
-  *out = acc;
   return SK_OK;
 }
 
@@ -344,13 +456,7 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
   const int nchunks = (int)std::min<int64_t>(64, (rows + 511) / 512);
   Scratch sc;
   JLS_CHECK(ensure_scratch(h, rows, dtype, wmax, &sc, nchunks));
-  static bool chol_attr = false;
-  if (!chol_attr) {
-    JLS_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CHOL_SMEM));
-    chol_attr = true;
-  }
   T* W = static_cast<T*>(sc.W);
-  T* W2 = static_cast<T*>(sc.W2);
   T* Q = static_cast<T*>(B.Q);
   const unsigned cgrid = 152 * 4;
   // absorb columns [covered, c_split) into Q, 64 at a time
@@ -358,24 +464,43 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
     const int b = std::min(64, c_split - B.covered);
     copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b); note_launch();
     JLS_CHECK(project_twice<T>(h, B, W, 64, b, rows, sc, nchunks, s));
-    for (int pass = 0; pass < 2; ++pass) {  // Cholesky QR twice
+    // Cholesky QR twice.  The first factorization is in FP64 (the Gram matrix
+    // squares W's condition number); the second Gram matrix is the identity up
+    // to the first pass's rounding, so with FP32 data it is factored in FP32.
+    T* Lf = reinterpret_cast<T*>(sc.U);
+    T* rinv = Lf + 64 * 64;
+    constexpr int RT = trsm_rows<T>();
+    const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
+    for (int pass = 0; pass < 2; ++pass) {
       JLS_CHECK(tsgemm<T>(W, 64, b, W, 64, b, rows, nchunks, sc.part, sc.G, s));
-      chol_inv_kernel<<<1, 64, CHOL_SMEM, s>>>(sc.G, b, sc.U, h->d_err); note_launch();
-      mul_upper_kernel<T><<<(unsigned)((rows + 15) / 16), 256, 0, s>>>(W, 64, sc.U, b, W2, 64, rows); note_launch();
-      copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W2, 64, W, 64, rows, b); note_launch();
+      if (sizeof(T) == 8)
+        chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      else if (pass == 0)
+        chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      else
+        chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      note_launch();
+      rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, 64, b, Lf, rinv, rows); note_launch();
     }
     copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W, 64, Q + B.cols, h->d_max, rows, b); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
     B.cols += b;
     B.covered += b;
   }
-  // the test block
+  // the test block: both norms summed on the device, one synchronization
   copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
-  double t2 = 0, h2 = 0;
-  JLS_CHECK(sumsq<T>(W, wmax, rows, bt, sc, &t2, s));
+  JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
   JLS_CHECK(project_twice<T>(h, B, W, wmax, bt, rows, sc, nchunks, s));
-  JLS_CHECK(sumsq<T>(W, wmax, rows, bt, sc, &h2, s));
+  JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms + NORM_GRID, s));
+  double part[2 * NORM_GRID];
+  JLS_CHECK_CUDA(cudaMemcpyAsync(part, sc.norms, sizeof(part), cudaMemcpyDeviceToHost, s));
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  double t2 = 0, h2 = 0;
+  for (int i = 0; i < NORM_GRID; ++i) {  // fixed order: deterministic
+    t2 += part[i];
+    h2 += part[NORM_GRID + i];
+  }
   *nt = std::sqrt(t2);
   *nh = std::sqrt(h2);
   *stop = (*nh < eps_abs) || (*nh < eps_rel * *nt);
@@ -470,8 +595,7 @@ int project_norms_noalloc_t(const T* Q, int64_t ldQ, int q_cols, const T* St, in
   JLS_CHECK(sumsq_noalloc<T>(Sh, ldH, rows, b, norms, &t2, s));
   for (int pass = 0; pass < 2 && q_cols > 0; ++pass) {  // S^ <- (I - Q Q^T) S^, twice
     JLS_CHECK(tsgemm<T>(Q, ldQ, q_cols, Sh, ldH, b, rows, NOALLOC_CHUNKS, part, G, s));
-    sub_qg_kernel<T><<<(unsigned)((rows + 31) / 32), 256, 0, s>>>(Sh, ldH, b, Q, ldQ, q_cols, G, rows); note_launch();
-    JLS_CHECK_CUDA(cudaGetLastError());
+    JLS_CHECK(sub_qg<T>(Sh, ldH, b, Q, ldQ, q_cols, G, rows, s));
   }
   JLS_CHECK(sumsq_noalloc<T>(Sh, ldH, rows, b, norms, &h2, s));
   *nt = std::sqrt(t2);

@@ -293,19 +293,36 @@ __device__ __forceinline__ double gauss_z(int64_t i, int c, uint64_t seed) {
   return (c & 1) ? rad * sn : rad * cs;
 }
 
+// The same draw with the transcendental steps in FP32, for the FP32 and bf16
+// planes (GB300 runs FP64 at a small fraction of its FP32 rate): the uniforms
+// are the same 53-bit values; -2 ln u1 takes logf(u1) below 1/2 and
+// log1pf(-(1 - u1)) above it (1 - u1 is exact in FP64), so both tails keep
+// FP32 relative accuracy; the angle is sincospif(2 u2).  The result differs
+// from the FP64 draw by a few FP32 ulps.
+__device__ __forceinline__ float gauss_z32(int64_t i, int c, uint64_t seed) {
+  const u64x4 w = philox4x64_10((uint64_t)i, (uint64_t)(c >> 1), 0, 0, seed, TAG_GAUSS);
+  const double u1 = u53_open0(w.x0);
+  const double u2 = u53(w.x1);
+  const float l = u1 < 0.5 ? logf((float)u1) : log1pf(-(float)(1.0 - u1));
+  const float rad = sqrtf(-2.0f * l);
+  float sn, cs;
+  sincospif(2.0f * (float)u2, &sn, &cs);
+  return (c & 1) ? rad * sn : rad * cs;
+}
+
 __global__ void gauss_gen_kernel(int64_t n, int c0, int c1, uint64_t seed, float* __restrict__ z32,
                                  double* __restrict__ z64, __nv_bfloat16* __restrict__ zhi,
                                  __nv_bfloat16* __restrict__ zlo) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int c = c0 + blockIdx.y;
   if (i >= n || c >= c1) return;
-  const double z = gauss_z(i, c, seed);
   const int64_t o = (int64_t)c * n + i;
-  if (z32) z32[o] = (float)z;
-  if (z64) z64[o] = z;
-  if (zhi) {  // z = z_hi + z_lo + O(2^-16 |z|): the two bf16 terms of (float)z
+  if (z64) z64[o] = gauss_z(i, c, seed);
+  if (!z32 && !zhi) return;
+  const float zf = gauss_z32(i, c, seed);
+  if (z32) z32[o] = zf;
+  if (zhi) {  // z = z_hi + z_lo + O(2^-16 |z|): the two bf16 terms of the FP32 draw
     const int64_t ob = (int64_t)c * bf_pitch(n) + i;
-    const float zf = (float)z;
     const __nv_bfloat16 hi = __float2bfloat16_rn(zf);
     zhi[ob] = hi;
     zlo[ob] = __float2bfloat16_rn(zf - __bfloat162float(hi));

@@ -86,3 +86,13 @@ def test_srht_matches_fwht_route():
     op = ops.Operator("srht", n, d, 1, 5)
     ref = osk.srht_by_fwht(A, op.srht_diag(), op.srht_samples(), d)
     assert rel_fro(S, ref) <= TOL["f64"]
+
+
+def test_gauss_fp32_plane_values():
+    """A = I gives S = R: the FP32 Gaussian plane (Box-Muller with FP32
+    transcendentals) matches the FP64 draw of the oracle to a few FP32 ulps."""
+    n, d = 4096, 64
+    A = np.eye(n, dtype=np.float32)
+    S, _ = sketch("gauss", A, d, 77, "f32", which=1)
+    R = ops.Operator("gauss", n, d, 1, 77).dense()
+    assert np.max(np.abs(S[:, :d] - R)) <= 1e-6 * np.max(np.abs(R))
