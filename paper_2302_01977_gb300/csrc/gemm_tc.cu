@@ -32,11 +32,12 @@
 // running total in a second TMEM region, so no single tensor-core
 // accumulation chain covers more than FOLD * 64 values of K.
 //
-// Warp roles (14 warps, one CTA per SM):
+// Warp roles (22 warps, one CTA per SM):
 //   warp 0       TMA producer for the B planes (one elected lane)
 //   warp 1       TMEM allocation; one lane issues tcgen05.mma and commits
-//   warps 2..9   converters: load FP32 A (coalesced), split, write bf16 tiles
-//   warps 10..13 epilogue: tcgen05.ld, fold or scale + red.global.add
+//   warps 2..17  converters: load FP32 A (coalesced, two K stages ahead in a
+//                ring of three register buffers), split, write bf16 tiles
+//   warps 18..21 epilogue: tcgen05.ld, fold or scale + red.global.add
 // Every wait is bounded: on a timeout the waiting role sets the error flag
 // and an abort flag in shared memory, the other roles stop at their next
 // unit, in-flight copies and MMAs are waited for (bounded) and TMEM is freed.
@@ -58,7 +59,9 @@ namespace {
 constexpr int TC_BM = 128;                 // output rows per tile (UMMA M)
 constexpr int TC_BK = 64;                  // K per stage (one 128-byte swizzle row of bf16)
 constexpr int TC_NMAX = 256;               // output columns per tile (UMMA N limit)
-constexpr int TC_CONV_WARPS = 8;
+constexpr int TC_CONV_WARPS = 16;
+constexpr int TC_CONV_THREADS = 32 * TC_CONV_WARPS;
+constexpr int TC_CV = TC_BM * TC_BK / TC_CONV_THREADS;  // FP32 values a converter thread stages per K stage
 constexpr int TC_EPI_WARPS = 4;
 constexpr int TC_THREADS = 32 * (2 + TC_CONV_WARPS + TC_EPI_WARPS);
 constexpr int TC_FOLD = JLS_TC_FOLD_STAGES;  // K stages per accumulation chain (0: no cut)
@@ -143,15 +146,6 @@ __device__ __forceinline__ void red_v4(float* p, float a, float b, float c, floa
   asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-// bf16 pair (x at the lower address) and the bf16 pair of the residuals.
-__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-
 struct TcWork {
   int64_t m_rows, k_len;     // output rows M, reduction length K (= n)
   int64_t mtiles;
@@ -163,19 +157,43 @@ struct TcWork {
   uint32_t tmem_cols;
 };
 
-__device__ __forceinline__ void decode(const TcWork& w, int64_t u, int& ntile, int64_t& mt, int& ks) {
-  const int64_t per_n = w.mtiles * w.kst;
-  ntile = (int)(u / per_n);
-  const int64_t r = u - (int64_t)ntile * per_n;
-  mt = r / w.kst;
-  ks = (int)(r - mt * w.kst);
-}
-__device__ __forceinline__ bool chain_begins(int64_t u, int64_t u0, int ks) {
-  return u == u0 || ks == 0 || (TC_FOLD > 0 && ks % (TC_FOLD > 0 ? TC_FOLD : 1) == 0);
-}
-__device__ __forceinline__ bool chain_ends(int64_t u, int64_t u1, int ks, int kst) {
-  return u + 1 == u1 || ks + 1 == kst || (TC_FOLD > 0 && (ks + 1) % (TC_FOLD > 0 ? TC_FOLD : 1) == 0);
-}
+// Position of a unit (N tile, M tile, K stage), advanced one unit at a time
+// (units are ordered N tile, then M tile, then K stage).
+struct Cursor {
+  int nt;
+  int64_t mt;
+  int ks;
+  __device__ __forceinline__ void init(const TcWork& w, int64_t u) {
+    const int64_t per_n = w.mtiles * w.kst;
+    nt = (int)(u / per_n);
+    const int64_t r = u - (int64_t)nt * per_n;
+    mt = r / w.kst;
+    ks = (int)(r - mt * w.kst);
+  }
+  __device__ __forceinline__ void next(const TcWork& w) {
+    if (++ks == w.kst) {
+      ks = 0;
+      if (++mt == w.mtiles) {
+        mt = 0;
+        ++nt;
+      }
+    }
+  }
+};
+// Slot and phase parity of the shared-memory ring for consecutive units.
+struct Ring {
+  int s = 0;
+  uint32_t ph = 0;
+  __device__ __forceinline__ void next(int stages) {
+    if (++s == stages) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+__device__ __forceinline__ bool fold_point(int ks) { return TC_FOLD > 0 && (ks & (TC_FOLD - 1)) == 0; }
+static_assert(TC_FOLD == 0 || (TC_FOLD & (TC_FOLD - 1)) == 0, "the fold interval is a power of two");
 
 // Lane 0 waits, the warp learns the outcome.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int* err) {
@@ -184,82 +202,129 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int* er
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// ---- converters: FP32 A -> bf16 (hi, lo) tiles -------------------------------------
-// S  (TRANS = false): A is M x K row-major.  Converter thread t takes float4
-//    j*256 + t of the 128 x 64 stage: row (j*256 + t) / 16, K quad t % 16, so
-//    16 lanes read one row's 256 contiguous bytes and write its 128-byte
-//    swizzled bf16 row without bank conflicts.
-// S' (TRANS = true): A is K x M row-major (the tile's rows are A's columns).
-//    Thread t takes tile row r = t % 128 and K half t / 128: 32 loads of
-//    A[k][m0 + r], each a 128-byte coalesced warp access; it then owns four
-//    whole 16-byte chunks of row r per plane, stored conflict-free.
-template <bool TRANS>
-__device__ __forceinline__ void conv_load(const float* __restrict__ A, int64_t lda, const TcWork& w, int64_t mt,
-                                          int ks, int ct, float (&v)[32]) {
-  const int64_t m0 = mt * TC_BM;
-  const int64_t k0 = (int64_t)ks * TC_BK;
-  if (!TRANS) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int idx = j * 256 + ct;
-      const int64_t m = m0 + (idx >> 4);
-      const int64_t k = k0 + (idx & 15) * 4;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < w.m_rows) {
-        const float* p = A + m * lda + k;
-        if (k + 3 < w.k_len) {
-          x = __ldg(reinterpret_cast<const float4*>(p));
-        } else {
-          if (k < w.k_len) x.x = __ldg(p);
-          if (k + 1 < w.k_len) x.y = __ldg(p + 1);
-          if (k + 2 < w.k_len) x.z = __ldg(p + 2);
-        }
-      }
-      v[4 * j] = x.x;
-      v[4 * j + 1] = x.y;
-      v[4 * j + 2] = x.z;
-      v[4 * j + 3] = x.w;
-    }
-  } else {
-    const int64_t m = m0 + (ct & 127);
-    const int64_t kb = k0 + (ct >> 7) * 32;
-    const bool mok = m < w.m_rows;
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      const int64_t k = kb + e;
-      v[e] = (mok && k < w.k_len) ? __ldg(A + k * lda + m) : 0.f;
-    }
-  }
+// bf16x2 of (lo, hi): `lo` lands in the lower 16 bits (the lower address).
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// Split four consecutive values: hi = bf16(x), lo = bf16(x - hi) (the
+// subtraction is exact), as two bf16x2 words each.
+__device__ __forceinline__ void split4(float4 x, uint32_t& h01, uint32_t& h23, uint32_t& l01, uint32_t& l23) {
+  h01 = bf16x2(x.x, x.y);
+  h23 = bf16x2(x.z, x.w);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 r01 = __ffma2_rn(make_float2(__uint_as_float(h01 << 16), __uint_as_float(h01 & 0xffff0000u)), m1,
+                                make_float2(x.x, x.y));
+  const float2 r23 = __ffma2_rn(make_float2(__uint_as_float(h23 << 16), __uint_as_float(h23 & 0xffff0000u)), m1,
+                                make_float2(x.z, x.w));
+  l01 = bf16x2(r01.x, r01.y);
+  l23 = bf16x2(r23.x, r23.y);
 }
 
+// ---- converters: FP32 A -> bf16 (hi, lo) tiles -------------------------------------
+// 512 converter threads, TC_CV = 16 values each per 128 x 64 stage.
+// S  (TRANS = false): A is M x K row-major.  Thread t takes float4 j*512 + t
+//    (j < 4) of the stage: row j*32 + t/16, K quad t % 16, so 16 lanes read one
+//    row's 256 contiguous bytes and write its 128-byte swizzled bf16 row
+//    without bank conflicts.
+// S' (TRANS = true): A is K x M row-major (the tile's rows are A's columns).
+//    Thread t takes tile row r = t % 128 and K quarter t / 128: 16 loads of
+//    A[k][m0 + r], each a 128-byte coalesced warp access; it then owns two
+//    whole 16-byte chunks of row r per plane, stored conflict-free.
+// Shared-memory offsets within a tile are fixed per thread; tiles wholly
+// inside A take an unchecked path.
 template <bool TRANS>
-__device__ __forceinline__ void conv_store(uint32_t a_hi, int ct, const float (&v)[32]) {
-  const uint32_t a_lo = a_hi + TC_A_PLANE;
-  if (!TRANS) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int idx = j * 256 + ct;
-      const uint32_t r = (uint32_t)(idx >> 4), kq = (uint32_t)(idx & 15);
-      const uint32_t off = r * 128 + ((((kq >> 1) ^ (r & 7)) << 4) | ((kq & 1) << 3));
-      uint32_t h0, l0, h1, l1;
-      split2(v[4 * j], v[4 * j + 1], h0, l0);
-      split2(v[4 * j + 2], v[4 * j + 3], h1, l1);
-      sts_v2(a_hi + off, h0, h1);
-      sts_v2(a_lo + off, l0, l1);
-    }
-  } else {
-    const uint32_t r = (uint32_t)(ct & 127), half = (uint32_t)(ct >> 7);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t off = r * 128 + (((half * 4 + c) ^ (r & 7)) << 4);
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) split2(v[8 * c + 2 * q], v[8 * c + 2 * q + 1], h[q], l[q]);
-      sts_v4(a_hi + off, h[0], h[1], h[2], h[3]);
-      sts_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+struct Converter {
+  const float* A;
+  int64_t lda;
+  int64_t m_rows, k_len;
+  int ct;
+  uint32_t off0;  // S: offset of row t/16 (j = 0); S': offset of row t % 128, first chunk
+
+  __device__ __forceinline__ void setup(const float* A_, int64_t lda_, const TcWork& w, int ct_) {
+    A = A_;
+    lda = lda_;
+    m_rows = w.m_rows;
+    k_len = w.k_len;
+    ct = ct_;
+    if (!TRANS) {
+      const uint32_t r = (uint32_t)(ct >> 4), kq = (uint32_t)(ct & 15);
+      off0 = r * 128 + ((((kq >> 1) ^ (r & 7)) << 4) | ((kq & 1) << 3));
+    } else {
+      const uint32_t r = (uint32_t)(ct & 127);
+      off0 = r * 128;
     }
   }
-}
+
+  __device__ __forceinline__ void load(int64_t mt, int ks, float (&v)[TC_CV]) const {
+    const int64_t m0 = mt * TC_BM, k0 = (int64_t)ks * TC_BK;
+    const bool full = m0 + TC_BM <= m_rows && k0 + TC_BK <= k_len;
+    if (!TRANS) {
+      const int64_t m = m0 + (ct >> 4);
+      const int64_t k = k0 + (ct & 15) * 4;
+      const float* p = A + m * lda + k;
+      const int64_t step = 32 * lda;
+#pragma unroll
+      for (int j = 0; j < TC_CV / 4; ++j) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (full) {
+          x = __ldg(reinterpret_cast<const float4*>(p + j * step));
+        } else if (m + 32 * j < m_rows) {
+          const float* q = p + j * step;
+          if (k + 3 < k_len) {
+            x = __ldg(reinterpret_cast<const float4*>(q));
+          } else {
+            if (k < k_len) x.x = __ldg(q);
+            if (k + 1 < k_len) x.y = __ldg(q + 1);
+            if (k + 2 < k_len) x.z = __ldg(q + 2);
+          }
+        }
+        v[4 * j] = x.x;
+        v[4 * j + 1] = x.y;
+        v[4 * j + 2] = x.z;
+        v[4 * j + 3] = x.w;
+      }
+    } else {
+      const int64_t m = m0 + (ct & 127);
+      const int64_t kb = k0 + (ct >> 7) * TC_CV;
+      const float* p = A + kb * lda + m;
+      if (full) {
+#pragma unroll
+        for (int e = 0; e < TC_CV; ++e) v[e] = __ldg(p + e * lda);
+      } else {
+        const bool mok = m < m_rows;
+#pragma unroll
+        for (int e = 0; e < TC_CV; ++e) v[e] = (mok && kb + e < k_len) ? __ldg(p + e * lda) : 0.f;
+      }
+    }
+  }
+
+  __device__ __forceinline__ void store(uint32_t a_hi, const float (&v)[TC_CV]) const {
+    const uint32_t a_lo = a_hi + TC_A_PLANE;
+    if (!TRANS) {
+#pragma unroll
+      for (int j = 0; j < TC_CV / 4; ++j) {
+        uint32_t h01, h23, l01, l23;
+        split4(make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]), h01, h23, l01, l23);
+        const uint32_t off = off0 + (uint32_t)j * (32 * 128);  // 32 rows on: same swizzle phase
+        sts_v2(a_hi + off, h01, h23);
+        sts_v2(a_lo + off, l01, l23);
+      }
+    } else {
+      const uint32_t r7 = (uint32_t)(ct & 7), quarter = (uint32_t)(ct >> 7);
+#pragma unroll
+      for (int c = 0; c < TC_CV / 8; ++c) {
+        const uint32_t off = off0 + (((quarter * (TC_CV / 8) + c) ^ r7) << 4);
+        uint32_t h[4], l[4];
+        split4(make_float4(v[8 * c], v[8 * c + 1], v[8 * c + 2], v[8 * c + 3]), h[0], h[1], l[0], l[1]);
+        split4(make_float4(v[8 * c + 4], v[8 * c + 5], v[8 * c + 6], v[8 * c + 7]), h[2], h[3], l[2], l[3]);
+        sts_v4(a_hi + off, h[0], h[1], h[2], h[3]);
+        sts_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+      }
+    }
+  }
+};
 
 }  // namespace
 
@@ -286,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t units = (int64_t)((w.c_hi - w.c_lo + w.nt - 1) / w.nt) * w.mtiles * w.kst;
   const int64_t u0 = units * blockIdx.x / gridDim.x;
-  const int64_t u1 = units * (blockIdx.x + 1) / gridDim.x;
+  const int cnt = (int)(units * (blockIdx.x + 1) / gridDim.x - u0);  // units of this CTA
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < w.stages; ++s) {
@@ -312,27 +377,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tma_prefetch_desc(&tmB0);
       if (PLANES == 2) tma_prefetch_desc(&tmB1);
       const uint32_t b_bytes = (uint32_t)PLANES * (uint32_t)w.nt * 128u;
-      int64_t issued = 0;
-      for (int64_t u = u0; u < u1; ++u) {
+      Cursor c;
+      c.init(w, u0);
+      Ring rg;
+      int issued = 0;
+      for (int i = 0; i < cnt; ++i, c.next(w), rg.next(w.stages)) {
         if (*abort_flag) break;
-        const int64_t i = u - u0;
-        const int s = (int)(i % w.stages);
-        if (!mbar_wait(empty(s), (uint32_t)(((i / w.stages) & 1) ^ 1), err)) {
+        if (!mbar_wait(empty(rg.s), rg.ph ^ 1u, err)) {
           *abort_flag = 1;
           break;
         }
-        int ntile, ks;
-        int64_t mt;
-        decode(w, u, ntile, mt, ks);
-        const uint32_t dst = base + (uint32_t)s * w.stage_bytes + 2 * TC_A_PLANE;
-        mbar_arrive_expect_tx(full_b(s), b_bytes);
-        tma_load_2d(dst, &tmB0, full_b(s), ks * TC_BK, w.c_lo + ntile * w.nt);
-        if (PLANES == 2) tma_load_2d(dst + (uint32_t)w.nt * 128u, &tmB1, full_b(s), ks * TC_BK, w.c_lo + ntile * w.nt);
+        const uint32_t dst = base + (uint32_t)rg.s * w.stage_bytes + 2 * TC_A_PLANE;
+        const int row = w.c_lo + c.nt * w.nt;
+        mbar_arrive_expect_tx(full_b(rg.s), b_bytes);
+        tma_load_2d(dst, &tmB0, full_b(rg.s), c.ks * TC_BK, row);
+        if (PLANES == 2) tma_load_2d(dst + (uint32_t)w.nt * 128u, &tmB1, full_b(rg.s), c.ks * TC_BK, row);
         issued = i + 1;
       }
       // wait for every copy still in flight (the last one issued into each slot)
-      for (int64_t i = std::max<int64_t>(0, issued - w.stages); i < issued; ++i)
-        mbar_wait(full_b((int)(i % w.stages)), (uint32_t)((i / w.stages) & 1), err);
+      for (int i = max(0, issued - w.stages); i < issued; ++i)
+        mbar_wait(full_b(i % w.stages), (uint32_t)((i / w.stages) & 1), err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -340,15 +404,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t idesc = idesc_bf16(TC_BM, w.nt);
       uint32_t chain = 0;
       bool first = true;
-      for (int64_t u = u0; u < u1; ++u) {
+      Cursor c;
+      c.init(w, u0);
+      Ring rg;
+      for (int i = 0; i < cnt; ++i, c.next(w), rg.next(w.stages)) {
         if (*abort_flag) break;
-        const int64_t i = u - u0;
-        const int s = (int)(i % w.stages);
-        const uint32_t par = (uint32_t)((i / w.stages) & 1);
-        int ntile, ks;
-        int64_t mt;
-        decode(w, u, ntile, mt, ks);
-        if (chain_begins(u, u0, ks)) {
+        if (i == 0 || c.ks == 0 || fold_point(c.ks)) {  // a chain begins: the accumulator must be free
           if (!mbar_wait(tmem_empty, (chain & 1) ^ 1, err)) {
             *abort_flag = 1;
             break;
@@ -356,12 +417,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           first = true;
         }
-        if (!mbar_wait(full_b(s), par, err) || !mbar_wait(full_a(s), par, err)) {
+        if (!mbar_wait(full_b(rg.s), rg.ph, err) || !mbar_wait(full_a(rg.s), rg.ph, err)) {
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t st = base + (uint32_t)s * w.stage_bytes;
+        const uint32_t st = base + (uint32_t)rg.s * w.stage_bytes;
         const uint32_t b0 = st + 2 * TC_A_PLANE, b1 = b0 + (uint32_t)w.nt * 128u;
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
@@ -373,8 +434,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (PLANES == 2) umma_bf16(tmem, dah, sw128_desc(b1 + ko), idesc, 1u);
           first = false;
         }
-        umma_commit(empty(s));
-        if (chain_ends(u, u1, ks, w.kst)) {
+        umma_commit(empty(rg.s));
+        if (i + 1 == cnt || c.ks + 1 == w.kst || fold_point(c.ks + 1)) {  // the chain ends
           umma_commit(tmem_full);
           ++chain;
         }
@@ -385,44 +446,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp < 2 + TC_CONV_WARPS) {
     // ---------------- converters ----------------
-    const int ct = threadIdx.x - 64;
-    float va[32], vb[32];
-    int64_t u = u0;
-    auto put = [&](const float (&v)[32], int64_t uu) -> bool {
-      const int64_t i = uu - u0;
-      const int s = (int)(i % w.stages);
+    // three register buffers: the loads of the next two stages are in flight
+    // while one stage is split and stored
+    Converter<TRANS> cv;
+    cv.setup(A, lda, w, threadIdx.x - 64);
+    float va[TC_CV], vb[TC_CV], vc[TC_CV];
+    Cursor lc;  // next unit to load
+    lc.init(w, u0);
+    int loaded = 0;
+    auto load = [&](float (&v)[TC_CV]) {
+      if (loaded < cnt) {
+        cv.load(lc.mt, lc.ks, v);
+        lc.next(w);
+        ++loaded;
+      }
+    };
+    Ring rg;
+    auto put = [&](const float (&v)[TC_CV]) -> bool {
       if (*abort_flag) return false;
-      if (!warp_wait(empty(s), (uint32_t)(((i / w.stages) & 1) ^ 1), err)) {
+      if (!warp_wait(empty(rg.s), rg.ph ^ 1u, err)) {
         *abort_flag = 1;
         return false;
       }
-      conv_store<TRANS>(base + (uint32_t)s * w.stage_bytes, ct, v);
+      cv.store(base + (uint32_t)rg.s * w.stage_bytes, v);
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(full_a(s));
+      if (lane == 0) mbar_arrive(full_a(rg.s));
+      rg.next(w.stages);
       return true;
     };
-    if (u < u1) {
-      int ntile, ks;
-      int64_t mt;
-      decode(w, u, ntile, mt, ks);
-      conv_load<TRANS>(A, lda, w, mt, ks, ct, va);
-    }
-    while (u < u1) {
-      int ntile, ks;
-      int64_t mt;
-      if (u + 1 < u1) {
-        decode(w, u + 1, ntile, mt, ks);
-        conv_load<TRANS>(A, lda, w, mt, ks, ct, vb);
-      }
-      if (!put(va, u)) break;
-      if (++u >= u1) break;
-      if (u + 1 < u1) {
-        decode(w, u + 1, ntile, mt, ks);
-        conv_load<TRANS>(A, lda, w, mt, ks, ct, va);
-      }
-      if (!put(vb, u)) break;
-      ++u;
+    load(va);
+    load(vb);
+    for (int i = 0; i < cnt; i += 3) {
+      load(vc);
+      if (!put(va) || i + 1 >= cnt) break;
+      load(va);
+      if (!put(vb) || i + 2 >= cnt) break;
+      load(vb);
+      if (!put(vc)) break;
     }
   } else {
     // ---------------- epilogue ----------------
@@ -430,20 +491,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t chain = 0;
     bool has_total = false;
-    for (int64_t u = u0; u < u1; ++u) {
-      int ntile, ks;
-      int64_t mt;
-      decode(w, u, ntile, mt, ks);
-      if (chain_begins(u, u0, ks)) has_total = !(u == u0 || ks == 0);
-      if (!chain_ends(u, u1, ks, w.kst)) continue;
+    Cursor c;
+    c.init(w, u0);
+    for (int i = 0; i < cnt; ++i, c.next(w)) {
+      if (i == 0 || c.ks == 0 || fold_point(c.ks)) has_total = !(i == 0 || c.ks == 0);
+      const bool emit = (i + 1 == cnt) || (c.ks + 1 == w.kst);
+      if (!emit && !fold_point(c.ks + 1)) continue;  // the chain goes on
       if (*abort_flag) break;
       if (!warp_wait(tmem_full, chain & 1, err)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      const bool emit = (u + 1 == u1) || (ks + 1 == w.kst);
-      const int64_t row = mt * TC_BM + q * 32 + lane;
+      const int64_t row = c.mt * TC_BM + q * 32 + lane;
       for (int cc = 0; cc < w.nt; cc += 16) {
         uint32_t v[16], t[16];
         tmem_ld16(trow + (uint32_t)cc, v);
@@ -457,7 +517,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_st16(trow + (uint32_t)(w.nt + cc), v);
           continue;
         }
-        const int c0 = w.c_lo + ntile * w.nt + cc;
+        const int c0 = w.c_lo + c.nt * w.nt + cc;
         if (row < w.m_rows && c0 < w.c_hi) {
           float* p = out + row * ldo + c0;
           if (vec_ok && c0 + 16 <= w.c_hi) {
