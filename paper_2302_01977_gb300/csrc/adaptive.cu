@@ -436,6 +436,44 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
   return SK_OK;
 }
 
+// Orthonormalize the b <= 64 columns of W (ld ldw) by Cholesky QR twice and
+// append them to Q.  With `project`, W is first made orthogonal to Q by two
+// block Gram-Schmidt passes.  The first factorization is in FP64 (the Gram
+// matrix squares W's condition number); the second Gram matrix is the
+// identity up to the first pass's rounding, so with FP32 data it is factored
+// in FP32.
+template <typename T>
+int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
+                 bool project, cudaStream_t s) {
+  if (project) JLS_CHECK(project_twice<T>(h, B, W, ldw, b, rows, sc, nchunks, s));
+  T* Lf = reinterpret_cast<T*>(sc.U);
+  T* rinv = Lf + 64 * 64;
+  constexpr int RT = trsm_rows<T>();
+  const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
+  for (int pass = 0; pass < 2; ++pass) {
+    JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
+    if (sizeof(T) == 8)
+      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+    else if (pass == 0)
+      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+    else
+      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+    note_launch();
+    rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, ldw, b, Lf, rinv, rows); note_launch();
+  }
+  copy_block_kernel<T><<<152 * 4, 256, 0, s>>>(W, ldw, static_cast<T*>(B.Q) + B.cols, h->d_max, rows, b);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  B.cols += b;
+  return SK_OK;
+}
+
+// The test of Eq. (3.1) on S~ = S[:, c_split:c_end], then Algorithm 1's
+// extension of Q by the QR of S^ (made at once, so that the next test, on the
+// next Delta-d columns, starts from the basis of every earlier column).
+// Columns of S before c_split that Q does not cover yet (the first d0, or
+// after a restart) are absorbed first.  The two norms are copied to pinned
+// host memory and read after an event, while the extension of Q runs on.
 template <typename T>
 int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
                 double eps_rel, double eps_abs, int* stop, double* nh, double* nt, cudaStream_t s) {
@@ -450,6 +488,8 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
     B.cols = 0;
     B.covered = 0;
   }
+  if (!h->host_norms) JLS_CHECK_CUDA(cudaMallocHost(&h->host_norms, 2 * NORM_GRID * sizeof(double)));
+  if (!h->norms_ready) JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->norms_ready, cudaEventDisableTiming));
   const int bt = c_end - c_split;
   const int wmax = std::max(64, bt);
   if (bt > 512) return SK_ERR_UNSUPPORTED;
@@ -457,49 +497,34 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
   Scratch sc;
   JLS_CHECK(ensure_scratch(h, rows, dtype, wmax, &sc, nchunks));
   T* W = static_cast<T*>(sc.W);
-  T* Q = static_cast<T*>(B.Q);
   const unsigned cgrid = 152 * 4;
-  // absorb columns [covered, c_split) into Q, 64 at a time
+  // columns [covered, c_split) not in Q yet, 64 at a time
   while (B.covered < c_split) {
     const int b = std::min(64, c_split - B.covered);
     copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b); note_launch();
-    JLS_CHECK(project_twice<T>(h, B, W, 64, b, rows, sc, nchunks, s));
-    // Cholesky QR twice.  The first factorization is in FP64 (the Gram matrix
-    // squares W's condition number); the second Gram matrix is the identity up
-    // to the first pass's rounding, so with FP32 data it is factored in FP32.
-    T* Lf = reinterpret_cast<T*>(sc.U);
-    T* rinv = Lf + 64 * 64;
-    constexpr int RT = trsm_rows<T>();
-    const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
-    for (int pass = 0; pass < 2; ++pass) {
-      JLS_CHECK(tsgemm<T>(W, 64, b, W, 64, b, rows, nchunks, sc.part, sc.G, s));
-      if (sizeof(T) == 8)
-        chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
-      else if (pass == 0)
-        chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
-      else
-        chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
-      note_launch();
-      rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, 64, b, Lf, rinv, rows); note_launch();
-    }
-    copy_block_kernel<T><<<cgrid, 256, 0, s>>>(W, 64, Q + B.cols, h->d_max, rows, b); note_launch();
-    JLS_CHECK_CUDA(cudaGetLastError());
-    B.cols += b;
+    JLS_CHECK(absorb_block<T>(h, B, W, 64, b, rows, sc, nchunks, true, s));
     B.covered += b;
   }
-  // the test block: both norms summed on the device, one synchronization
+  // the test block: both norms summed on the device
   copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
   JLS_CHECK(project_twice<T>(h, B, W, wmax, bt, rows, sc, nchunks, s));
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms + NORM_GRID, s));
-  double part[2 * NORM_GRID];
-  JLS_CHECK_CUDA(cudaMemcpyAsync(part, sc.norms, sizeof(part), cudaMemcpyDeviceToHost, s));
-  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(h->host_norms, sc.norms, 2 * NORM_GRID * sizeof(double), cudaMemcpyDeviceToHost, s));
+  JLS_CHECK_CUDA(cudaEventRecord(h->norms_ready, s));
+  // extend Q by S^ (64 columns at a time; later chunks are first made
+  // orthogonal to the chunks just added)
+  for (int j0 = 0; j0 < bt; j0 += 64) {
+    const int b = std::min(64, bt - j0);
+    JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, s));
+  }
+  B.covered = c_end;
+  JLS_CHECK_CUDA(cudaEventSynchronize(h->norms_ready));
   double t2 = 0, h2 = 0;
   for (int i = 0; i < NORM_GRID; ++i) {  // fixed order: deterministic
-    t2 += part[i];
-    h2 += part[NORM_GRID + i];
+    t2 += h->host_norms[i];
+    h2 += h->host_norms[NORM_GRID + i];
   }
   *nt = std::sqrt(t2);
   *nh = std::sqrt(h2);

@@ -92,6 +92,8 @@ struct sk_op {
   jls::Basis basis[2];
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  double* host_norms = nullptr;       // pinned: the stopping test's norm partials
+  cudaEvent_t norms_ready = nullptr;  // recorded after their copy
 };
 
 namespace jls {

@@ -71,6 +71,8 @@ static void free_handle(sk_op* h) {
                   h->basis[0].Q, h->basis[1].Q, h->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (h->host_norms) cudaFreeHost(h->host_norms);
+  if (h->norms_ready) cudaEventDestroy(h->norms_ready);
   delete h;
 }
 
