@@ -68,6 +68,11 @@ extern "C" {
 #define SK_PREC_BF16X2 3  /* F32 data: A = A_hi + A_lo (bf16), R likewise (Gaussian)
                              or exact (+-1, SRHT); tcgen05 tensor cores, FP32
                              accumulation; SRHT and Gaussian only                  */
+#define SK_PREC_FP8    4  /* F32 data: e4m3 hi + lo terms of A per 128 x 128 tile
+                             scale and of z per (128 x 1) scale, SRHT signs exact;
+                             tcgen05 tensor cores, FP32 accumulation, scales
+                             applied per 128-value K tile; SRHT and Gaussian only;
+                             relative error of order 1e-3 (tolerance 2e-2)         */
 
 /* ---- which sketch ------------------------------------------------------- */
 #define SK_S    1  /* S  = A R   */
@@ -121,7 +126,7 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream);
  *   A      explicit (generator == 0) or kernel generator; rows x cols with
  *          cols == n for S and rows == n for S'.
  *   which  SK_S, SK_ST or SK_BOTH.
- *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 (F32, SRHT/Gaussian).
+ *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 / SK_PREC_FP8 (F32, SRHT/Gaussian).
  *   S      device, rows x d_total (ldS >= d_total) of A's dtype; used if which & SK_S.
  *   St     device, cols x d_total (ldSt >= d_total);             used if which & SK_ST.
  * Asynchronous.  Errors: INVALID_ARG, ALIGN, DTYPE, UNSUPPORTED, DEVICE.

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace jls {
@@ -193,6 +194,21 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// ---- e4m3 (FP8) conversions ---------------------------------------------------------
+// e4m3x2 of (lo, hi): `lo` in the lower byte (the lower address), round to
+// nearest, saturating at +-448.
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+  unsigned short d;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// The two values of an e4m3x2 pair, exactly, as FP32.
+__device__ __forceinline__ float2 e4m3x2_to_f2(uint32_t q) {
+  uint32_t h2;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((unsigned short)q));
+  const __half2 h = *reinterpret_cast<const __half2*>(&h2);
+  return __half22float2(h);
+}
 __device__ __forceinline__ bool elect_lane0() { return (threadIdx.x & 31) == 0; }
 
 }  // namespace jls

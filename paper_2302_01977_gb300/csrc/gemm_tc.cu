@@ -47,6 +47,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 #ifndef JLS_TC_FOLD_STAGES
 #define JLS_TC_FOLD_STAGES 16
@@ -55,6 +56,8 @@
 namespace jls {
 
 namespace {
+
+using namespace tcx;
 
 constexpr int TC_BM = 128;                 // output rows per tile (UMMA M)
 constexpr int TC_BK = 64;                  // K per stage (one 128-byte swizzle row of bf16)
@@ -70,137 +73,8 @@ constexpr int TC_MAX_STAGES = 4;
 constexpr long TC_SMEM_MAX = 227 * 1024;
 constexpr uint32_t TC_BAR_BYTES = 256;
 
-// ---- tcgen05 wrappers ----------------------------------------------------------
-// Shared-memory matrix descriptor for a K-major operand tile with the 128-byte
-// swizzle: start address >> 4 in bits 0-13, leading offset (unused by this
-// layout) 16 bytes, stride offset 1024 bytes (8 rows x 128 bytes) in bits
-// 32-45, descriptor version 1 in bits 46-47, layout 2 (128-byte swizzle) in
-// bits 61-63.  Tiles are 1024-byte aligned, so the base offset field is 0.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), bf16 A
-// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
-// 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-// 32 lanes x 16 consecutive 32-bit columns (lane = TMEM lane of this warp's quarter)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void sts_v2(uint32_t a, uint32_t x, uint32_t y) {
-  asm volatile("st.shared.v2.b32 [%0], {%1,%2};" ::"r"(a), "r"(x), "r"(y) : "memory");
-}
-__device__ __forceinline__ void sts_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
-  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
-}
-__device__ __forceinline__ void red_v4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
-}
-
-struct TcWork {
-  int64_t m_rows, k_len;     // output rows M, reduction length K (= n)
-  int64_t mtiles;
-  int kst;                   // K stages per tile
-  int nt;                    // output columns per tile
-  int c_lo, c_hi;
-  int stages;
-  uint32_t stage_bytes;
-  uint32_t tmem_cols;
-};
-
-// Position of a unit (N tile, M tile, K stage), advanced one unit at a time
-// (units are ordered N tile, then M tile, then K stage).
-struct Cursor {
-  int nt;
-  int64_t mt;
-  int ks;
-  __device__ __forceinline__ void init(const TcWork& w, int64_t u) {
-    const int64_t per_n = w.mtiles * w.kst;
-    nt = (int)(u / per_n);
-    const int64_t r = u - (int64_t)nt * per_n;
-    mt = r / w.kst;
-    ks = (int)(r - mt * w.kst);
-  }
-  __device__ __forceinline__ void next(const TcWork& w) {
-    if (++ks == w.kst) {
-      ks = 0;
-      if (++mt == w.mtiles) {
-        mt = 0;
-        ++nt;
-      }
-    }
-  }
-};
-// Slot and phase parity of the shared-memory ring for consecutive units.
-struct Ring {
-  int s = 0;
-  uint32_t ph = 0;
-  __device__ __forceinline__ void next(int stages) {
-    if (++s == stages) {
-      s = 0;
-      ph ^= 1u;
-    }
-  }
-};
-
 __device__ __forceinline__ bool fold_point(int ks) { return TC_FOLD > 0 && (ks & (TC_FOLD - 1)) == 0; }
 static_assert(TC_FOLD == 0 || (TC_FOLD & (TC_FOLD - 1)) == 0, "the fold interval is a power of two");
-
-// Lane 0 waits, the warp learns the outcome.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int* err) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
 
 // bf16x2 of (lo, hi): `lo` lands in the lower 16 bits (the lower address).
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
@@ -559,12 +433,6 @@ int encode_plane(CUtensorMap* tm, const uint16_t* plane, int64_t n, int rows, in
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SK_OK : SK_ERR_ALIGN;
-}
-
-uint32_t tmem_cols_for(int cols) {
-  uint32_t c = 32;
-  while ((int)c < cols) c <<= 1;
-  return c;
 }
 
 int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, float scale, float* out, int64_t ldo,

@@ -23,6 +23,9 @@ constexpr int MAX_BLOCKS = 256;  // SJLT blocks (initial + increments) a handle 
 // Row pitch (elements) of the bf16 operator planes [c][k] read by the
 // tensor-core path: rows start on 128-byte boundaries, as TMA wants.
 __host__ __device__ inline int64_t bf_pitch(int64_t n) { return (n + 63) / 64 * 64; }
+// Row pitch (bytes) of the e4m3 operator planes of the FP8 path.
+__host__ __device__ inline int64_t f8_pitch(int64_t n) { return (n + 127) / 128 * 128; }
+constexpr int F8_KTILE = 128;  // values of K per FP8 scale tile
 
 // Tiled CCS of R (Sec. 6.1's compressed column storage, cut into tiles of
 // `tile` rows): for tile t, entries[t*e_stride + p] sorted by column (rows
@@ -89,6 +92,16 @@ struct sk_op {
   uint16_t* srht_pm1 = nullptr;
   int pm1_cols = 0;
 
+  // FP8 path: e4m3 planes (d_max rows of f8_pitch(n) bytes).  Gaussian: z_hi,
+  // z_lo in units of the scale of each (128-value K tile, column), scales
+  // [ceil(n/128)][d_max]; SRHT: the exact +-1 plane.
+  uint8_t* z8_hi = nullptr;
+  uint8_t* z8_lo = nullptr;
+  float* z8_scale = nullptr;
+  int z8_cols = 0;
+  uint8_t* srht_q8 = nullptr;
+  int q8_cols = 0;
+
   jls::Basis basis[2];
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -104,6 +117,8 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s);
 int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s);
 int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s);  // plane: 0 f32, 1 f64, 2 bf16x2
 int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s);
+int gen_gauss_fp8(sk_op* h, int c_end, cudaStream_t s);
+int gen_srht_fp8(sk_op* h, int c_end, cudaStream_t s);
 int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s);
 
 // --- sjlt_apply.cu ---
@@ -119,6 +134,10 @@ int dense_apply_simt(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi
 // --- gemm_tc.cu ---  SRHT / Gaussian on tcgen05 tensor cores, bf16 hi+lo split
 int dense_apply_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
                    void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+
+// --- gemm_fp8.cu ---  SRHT / Gaussian on tcgen05 tensor cores, e4m3 split with tile scales
+int dense_apply_fp8(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S,
+                    int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
 
 // --- kernel_matrix.cu ---
 int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s);

@@ -49,8 +49,8 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
   if (!aligned16(A->A) || (A->ld * (int64_t)elem_size(A->dtype)) % 16 != 0) return SK_ERR_ALIGN;
   if ((which & SK_S) && (A->cols != h->n || !S || ldS < h->d_total)) return SK_ERR_INVALID_ARG;
   if ((which & SK_ST) && (A->rows != h->n || !St || ldSt < h->d_total)) return SK_ERR_INVALID_ARG;
-  if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2) return SK_ERR_DTYPE;
-  if (prec == SK_PREC_BF16X2 && (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
+  if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2 && prec != SK_PREC_FP8) return SK_ERR_DTYPE;
+  if (prec != SK_PREC_NATIVE && (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
     return SK_ERR_DTYPE;
   return SK_OK;
 }
@@ -61,6 +61,7 @@ static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo,
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
     return sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+  if (prec == SK_PREC_FP8) return dense_apply_fp8(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   return dense_apply_simt(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
 }
 
@@ -68,6 +69,7 @@ static void free_handle(sk_op* h) {
   if (!h) return;
   void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
+                  h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
                   h->basis[0].Q, h->basis[1].Q, h->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);

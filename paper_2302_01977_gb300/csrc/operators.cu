@@ -373,6 +373,74 @@ int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// FP8 planes.  Gaussian: one CTA of 128 threads per (K tile of 128, column c)
+// draws the tile's FP32 z (as for the FP32 plane), takes its amax, and writes
+// w_hi = e4m3(z / s), w_lo = e4m3(z / s - w_hi) with s = amax / 448, and s.
+// Columns are quantized independently, so an increment never changes the
+// planes of earlier columns.
+__global__ void gauss_fp8_kernel(int64_t n, int c0, uint64_t seed, int64_t pitch, int64_t sld, uint8_t* __restrict__ zh,
+                                 uint8_t* __restrict__ zl, float* __restrict__ zs) {
+  __shared__ float wmax[4];
+  const int kt = blockIdx.x, c = c0 + blockIdx.y;
+  const int64_t k = (int64_t)kt * F8_KTILE + threadIdx.x;
+  const float z = k < n ? gauss_z32(k, c, seed) : 0.f;
+  float m = fabsf(z);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  const float amax = fmaxf(fmaxf(wmax[0], wmax[1]), fmaxf(wmax[2], wmax[3]));
+  const float inv = amax > 0.f ? 448.f / amax : 0.f;
+  const float y = z * inv;
+  const uint32_t h = e4m3x2(y, 0.f) & 0xffu;
+  const float r = y - e4m3x2_to_f2(h).x;
+  const uint32_t l = e4m3x2(r, 0.f) & 0xffu;
+  if (k < n) {
+    zh[(int64_t)c * pitch + k] = (uint8_t)h;
+    zl[(int64_t)c * pitch + k] = (uint8_t)l;
+  }
+  if (threadIdx.x == 0) zs[(int64_t)kt * sld + c] = amax / 448.f;
+}
+
+int gen_gauss_fp8(sk_op* h, int c_end, cudaStream_t s) {
+  const int64_t kts = (h->n + F8_KTILE - 1) / F8_KTILE;
+  if (!h->z8_hi) {
+    const size_t bytes = (size_t)h->d_max * f8_pitch(h->n);
+    JLS_CHECK_CUDA(cudaMalloc(&h->z8_hi, bytes));
+    JLS_CHECK_CUDA(cudaMalloc(&h->z8_lo, bytes));
+    JLS_CHECK_CUDA(cudaMalloc(&h->z8_scale, (size_t)kts * h->d_max * sizeof(float)));
+  }
+  if (h->z8_cols >= c_end) return SK_OK;
+  dim3 grid((unsigned)kts, (unsigned)(c_end - h->z8_cols));
+  gauss_fp8_kernel<<<grid, F8_KTILE, 0, s>>>(h->n, h->z8_cols, h->seed, f8_pitch(h->n), h->d_max, h->z8_hi, h->z8_lo,
+                                             h->z8_scale); note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  h->z8_cols = c_end;
+  return SK_OK;
+}
+
+// SRHT sign plane in e4m3 (exact): 0x38 = +1.0, 0xB8 = -1.0.
+__global__ void srht_q8_kernel(int64_t n, int c0, int c1, const int8_t* __restrict__ diag,
+                               const int32_t* __restrict__ mu, int64_t pitch, uint8_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int c = c0 + blockIdx.y;
+  if (i >= n || c >= c1) return;
+  const int neg = (__popcll((unsigned long long)i & (unsigned long long)(uint32_t)mu[c]) & 1) ^ (diag[i] < 0);
+  out[(int64_t)c * pitch + i] = neg ? (uint8_t)0xB8 : (uint8_t)0x38;
+}
+
+int gen_srht_fp8(sk_op* h, int c_end, cudaStream_t s) {
+  if (!h->srht_q8) JLS_CHECK_CUDA(cudaMalloc(&h->srht_q8, (size_t)h->d_max * f8_pitch(h->n)));
+  if (h->q8_cols >= c_end) return SK_OK;
+  dim3 grid((unsigned)((h->n + 255) / 256), (unsigned)(c_end - h->q8_cols));
+  srht_q8_kernel<<<grid, 256, 0, s>>>(h->n, h->q8_cols, c_end, h->srht_diag, h->srht_mu, f8_pitch(h->n), h->srht_q8);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  h->q8_cols = c_end;
+  return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Dense R for export (scale included), row-major n x d_total.
 template <typename T>
 __global__ void dense_R_kernel(int kind, int64_t n, int d_total, int alpha, int nblocks, double scale,

@@ -38,6 +38,7 @@ SK_F64 = 1
 SK_F32 = 2
 SK_PREC_NATIVE = 0
 SK_PREC_BF16X2 = 3
+SK_PREC_FP8 = 4
 SK_S = 1
 SK_ST = 2
 SK_BOTH = 3
