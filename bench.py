@@ -428,6 +428,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+PRECISION = dict(name="precision_fp32_n65536", n=65536, d=512, h=0.05, seed=20230203 + 2, sample_rows=4096)
+
+
+def run_precision(args):
+    """The Gaussian sketch S = A R of the 65536 x 65536 FP32 kernel matrix
+    (h = 0.05, A = 17.2 GB) at d = 512 in each arithmetic: FP32 CUDA cores,
+    the bf16 split and scaled FP8 on the tensor cores.  Each result's error is
+    measured against the FP64 oracle on sampled rows, with A's FP32 values read
+    back from the device (so the error is the sketch's, not the kernel's exp)."""
+    import numpy as np
+    import torch
+
+    from oracle import operators as ops
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = PRECISION
+    n, d = w["n"], w["d"]
+    torch.cuda.set_device(0)
+    X = torch.from_numpy(inputs.points(n, seed=w["seed"])).cuda()
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    jl.kernel_matrix(jl.generator(X, X, w["h"], 0.0), A)
+    h = jl.sketch_create("gauss", n, d, 1, w["seed"], d)
+    rng = np.random.default_rng(w["seed"])
+    rows = np.sort(rng.choice(n, w["sample_rows"], replace=False))
+    rows_t = torch.from_numpy(rows).cuda()
+    hbm, bf16, _, peak_kind = peaks()
+    results = {}
+    clocks = Clocks(0)
+    clocks.start()
+    try:
+        for name, prec in (("fp32", jl.SK_PREC_NATIVE), ("bf16x2", jl.SK_PREC_BF16X2), ("fp8", jl.SK_PREC_FP8)):
+            S = torch.empty((n, d), dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup if name != "fp32" else 1):
+                jl.sketch_apply(h, A, jl.SK_S, prec, S=S)
+            reps = args.steps if name != "fp32" else 1
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                jl.sketch_apply(h, A, jl.SK_S, prec, S=S)
+            e1.record()
+            torch.cuda.synchronize()
+            jl.sketch_device_status(h)
+            ms = e0.elapsed_time(e1) / reps
+            results[name] = {"ms": round(ms, 3), "gbs_of_A": round(4.0 * n * n / ms / 1e6, 1),
+                             "useful_tflops": round(2.0 * n * n * d / ms / 1e9, 1),
+                             "S_rows": S.index_select(0, rows_t).cpu().numpy().astype(np.float64)}
+            del S
+    finally:
+        ck = clocks.stop()
+    A_rows = A.index_select(0, rows_t).cpu().numpy().astype(np.float64)
+    jl.sketch_destroy(h)
+    t0 = time.perf_counter()
+    ref = A_rows @ ops.Operator("gauss", n, d, 1, w["seed"]).dense()
+    t_oracle = time.perf_counter() - t0
+    den = float(np.linalg.norm(ref))
+    for r in results.values():
+        r["rel_err_vs_oracle"] = float(f"{float(np.linalg.norm(r.pop('S_rows') - ref)) / den:.3e}")
+    tol = {"fp32": 1e-5, "bf16x2": 1e-5, "fp8": 2e-2}
+    for name, r in results.items():
+        r["tolerance"] = tol[name]
+        r["pct_of_bf16_peak"] = round(100 * r["useful_tflops"] / bf16, 1)
+    best = results["bf16x2"]
+    line = {"metric": METRIC, "value": best["gbs_of_A"], "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 data; bf16 split", "data": "synthetic", "impl": "ours",
+            "config": {"workload": w["name"], "n": n, "d": d, "h": w["h"], "operator": "gaussian", "which": "S",
+                       "error_sample_rows": w["sample_rows"], "l2": "inputs larger than L2 (A = 17.2 GB)"},
+            "per_precision": results, "peak_bf16_tflops": bf16, "peak_source": peak_kind,
+            "oracle_seconds_on_sample": round(t_oracle, 1), "clocks": ck}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,6 +517,9 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
+    ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536"],
+                    default="kernel_fp32_n32768",
+                    help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",
                     help="restrict the step (profiling captures); the benchmark runs all")
     args = ap.parse_args()
@@ -448,6 +527,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "precision_fp32_n65536":
+        run_precision(args)
     else:
         run_ours(args)
 
