@@ -233,6 +233,15 @@ int sketch_device_status(sk_handle h, void* stream);
  * process so far (all handles); a diagnostic for counting device work. */
 int64_t sketch_launch_count(void);
 
+/* sketch_srht_route -- which route the SRHT S = A R product takes for a shape
+ * (nu = 2^ceil(log2 n), A's rows and cols, the number of columns applied, and
+ * prec): 1 the row FWHT of Sec. 7.1, 0 the +-1 product of the element formula
+ * of Sec. 7.2, -1 not measured yet.  The first apply of a shape times both
+ * routes on its stream (one synchronization) and keeps the faster; only FP32
+ * data with nu in [2^14, 2^16] and SK_PREC_NATIVE or SK_PREC_BF16X2 has both
+ * routes.  A diagnostic query; the paper has no counterpart. */
+int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int32_t prec);
+
 /* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */
 void sketch_destroy(sk_handle h);
 

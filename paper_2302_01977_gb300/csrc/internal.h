@@ -135,6 +135,11 @@ int dense_apply_simt(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi
 int dense_apply_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
                    void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
 
+// --- srht_fwht.cu ---  SRHT S = A D H P / sqrt(d) by row transforms (FP32, nu in [2^14, 2^16])
+int fwht_segments(int64_t nu);  // 0 if the FWHT path does not apply
+int srht_apply_fwht(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double scale, float* S, int64_t ldS,
+                    cudaStream_t s);
+
 // --- gemm_fp8.cu ---  SRHT / Gaussian on tcgen05 tensor cores, e4m3 split with tile scales
 int dense_apply_fp8(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S,
                     int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);

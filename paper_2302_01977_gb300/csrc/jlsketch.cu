@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -55,9 +56,74 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
   return SK_OK;
 }
 
+// SRHT S = A R has two FP32-accurate routes: the row FWHT (srht_fwht.cu) and
+// the +-1 product (tensor-core bf16 split for SK_PREC_BF16X2, CUDA cores for
+// SK_PREC_NATIVE).  The first apply of a shape times both on the caller's
+// stream (one synchronization) and the faster is kept for that shape.
+struct SrhtPick {
+  int64_t nu, rows, cols;
+  int width, prec;
+  bool fwht;
+};
+static std::mutex g_pick_mu;
+static std::vector<SrhtPick> g_picks;
+
+static int srht_s_gemm(sk_op* h, const sk_matrix* A, int prec, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
+                       cudaStream_t s) {
+  if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, SK_S, c_lo, c_hi, scale, S, ldS, nullptr, 0, s);
+  return dense_apply_simt(h, A, SK_S, c_lo, c_hi, scale, S, ldS, nullptr, 0, s);
+}
+
+static int srht_pick_fwht(sk_op* h, const sk_matrix* A, int prec, int c_lo, int c_hi, double scale, void* S,
+                          int64_t ldS, cudaStream_t s, bool* fwht) {
+  const SrhtPick key{h->nu, A->rows, A->cols, c_hi - c_lo, prec, false};
+  {
+    std::lock_guard<std::mutex> lock(g_pick_mu);
+    for (const SrhtPick& p : g_picks)
+      if (p.nu == key.nu && p.rows == key.rows && p.cols == key.cols && p.width == key.width && p.prec == key.prec) {
+        *fwht = p.fwht;
+        return SK_OK;
+      }
+  }
+  cudaEvent_t ev[4];
+  for (auto& e : ev) JLS_CHECK_CUDA(cudaEventCreate(&e));
+  int rc = SK_OK;
+  float t_f = 0.f, t_g = 0.f;
+  // warm both once (operator planes, attributes), then time one call of each
+  if ((rc = srht_apply_fwht(h, A, c_lo, c_hi, scale, (float*)S, ldS, s)) == SK_OK &&
+      (rc = srht_s_gemm(h, A, prec, c_lo, c_hi, scale, S, ldS, s)) == SK_OK) {
+    cudaEventRecord(ev[0], s);
+    rc = srht_apply_fwht(h, A, c_lo, c_hi, scale, (float*)S, ldS, s);
+    cudaEventRecord(ev[1], s);
+    if (rc == SK_OK) rc = srht_s_gemm(h, A, prec, c_lo, c_hi, scale, S, ldS, s);
+    cudaEventRecord(ev[2], s);
+    if (rc == SK_OK && cudaEventSynchronize(ev[2]) == cudaSuccess) {
+      cudaEventElapsedTime(&t_f, ev[0], ev[1]);
+      cudaEventElapsedTime(&t_g, ev[1], ev[2]);
+    } else if (rc == SK_OK) {
+      rc = cuda_status(cudaGetLastError());
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc != SK_OK) return rc;
+  *fwht = t_f <= t_g;
+  std::lock_guard<std::mutex> lock(g_pick_mu);
+  g_picks.push_back({key.nu, key.rows, key.cols, key.width, key.prec, *fwht});
+  return SK_OK;
+}
+
 static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, void* S, int64_t ldS,
                     void* St, int64_t ldSt, cudaStream_t s) {
   const double scale = op_scale(h);
+  if (h->kind == SK_SRHT && (which & SK_S) && A->dtype == SK_F32 &&
+      (prec == SK_PREC_NATIVE || prec == SK_PREC_BF16X2) && fwht_segments(h->nu) && c_hi > c_lo) {
+    bool fwht = false;
+    JLS_CHECK(srht_pick_fwht(h, A, prec, c_lo, c_hi, scale, S, ldS, s, &fwht));
+    JLS_CHECK(fwht ? srht_apply_fwht(h, A, c_lo, c_hi, scale, (float*)S, ldS, s)
+                   : srht_s_gemm(h, A, prec, c_lo, c_hi, scale, S, ldS, s));
+    which &= ~SK_S;
+    if (!which) return SK_OK;
+  }
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
     return sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
@@ -264,6 +330,13 @@ int sketch_device_status(sk_handle h, void* stream) {
 }
 
 int64_t sketch_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int32_t prec) {
+  std::lock_guard<std::mutex> lock(g_pick_mu);
+  for (const SrhtPick& p : g_picks)
+    if (p.nu == nu && p.rows == rows && p.cols == cols && p.width == width && p.prec == prec) return p.fwht ? 1 : 0;
+  return -1;
+}
 
 void sketch_destroy(sk_handle h) {
   if (!h) return;

@@ -1,0 +1,212 @@
+// srht_fwht.cu -- S = A D H P / sqrt(d) for the SRHT by a fast Walsh-Hadamard
+// transform of each row of A (Sec. 7.1), FP32, GB300.
+//
+// Row i of A (zero-padded to nu = 2^ceil(log2 n)) is sign-flipped by D,
+// transformed by the unnormalized Sylvester H (y_o = sum_k x_k (-1)^popc(k & o))
+// and the d sampled outputs y_{mu_c} are kept, scaled by 1 / sqrt(d) -- the
+// element formula of Sec. 7.2 evaluated through the transform.
+//
+// GB300 mapping.  A 32768-value row is 128 KB, half the register file, so a
+// row is cut into nu / L sub-transforms of L = 16384 values: the butterflies of
+// the top log2(nu / L) bits are applied while loading (unit (i, p) loads every
+// L-segment q of the row and sums (-1)^popc(p & q) x_q), and each unit is an
+// independent transform of length L whose outputs are y_{p L + o}.  A unit is
+// one CTA of 128 threads x 128 values in registers (three CTAs per SM, so
+// some load while others compute; the segments' second readers hit L2): seven
+// butterfly stages in registers, one transpose through shared memory, seven
+// more stages.  The transformed unit is written back to the buffer and the
+// sampled columns whose output index falls in segment p are gathered and
+// stored (plain stores: every column belongs to one unit).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace jls {
+
+namespace {
+
+constexpr int FW_THREADS = 128;
+constexpr int FW_E = 128;                   // values per thread
+constexpr int FW_L = FW_THREADS * FW_E;     // 16384: length of a unit's transform
+constexpr int FW_LOG_L = 14;
+constexpr int FW_MAX_SEG = 4;               // nu <= 65536
+constexpr int FW_BUF = FW_L + FW_L / 128;   // exchange buffer, one pad word every 128
+constexpr int FW_DWORDS = FW_MAX_SEG * 4 * FW_THREADS;  // D sign bits, per thread and segment
+
+__device__ __forceinline__ int pad(int k) { return k + (k >> 7); }
+
+// butterfly stage on register index bit `s` of an array of N values, two
+// butterflies per FFMA2 pair (x + y and x - y as fma(y, +-1, x), exact)
+template <int N>
+__device__ __forceinline__ void stage(float (&x)[N], int s) {
+  const float2 p1 = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
+  const int d = 1 << s;
+  if (d == 1) {  // partners are neighbours: pair butterflies j = 4r, 4r + 2
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      const float2 a = make_float2(x[j], x[j + 2]), b = make_float2(x[j + 1], x[j + 3]);
+      const float2 sum = __ffma2_rn(b, p1, a), dif = __ffma2_rn(b, m1, a);
+      x[j] = sum.x;
+      x[j + 2] = sum.y;
+      x[j + 1] = dif.x;
+      x[j + 3] = dif.y;
+    }
+  } else {  // pair butterflies j, j + 1 (both with bit s clear)
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      if ((j >> s) & 1) continue;
+      const float2 a = make_float2(x[j], x[j + 1]), b = make_float2(x[j + d], x[j + d + 1]);
+      const float2 sum = __ffma2_rn(b, p1, a), dif = __ffma2_rn(b, m1, a);
+      x[j] = sum.x;
+      x[j + 1] = sum.y;
+      x[j + d] = dif.x;
+      x[j + d + 1] = dif.y;
+    }
+  }
+}
+
+}  // namespace
+
+// One CTA of 128 threads per unit at a time (three CTAs per SM).  Thread t
+// holds k = t + 128 j (j < 128): round A transforms bits 7..13 in registers,
+// one transpose through the padded buffer (pad(k) = k + k/128, so both the
+// write k = t + 128 j and the read k = j + 128 t are conflict-free) gives
+// k = j + 128 t, and round B transforms bits 0..6.
+__global__ void __launch_bounds__(FW_THREADS, 3)
+    srht_fwht_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t n, int nseg,
+                          const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, int c_lo, int c_hi,
+                          float scale, float* __restrict__ S, int64_t ldS) {
+  extern __shared__ float buf[];                                        // FW_BUF floats
+  uint32_t* dbits = reinterpret_cast<uint32_t*>(buf + FW_BUF);          // [seg][word][thread]
+  const int t = threadIdx.x;
+
+  // D sign bits re-laid out per thread: bit (j % 32) of dbits[(q*4 + j/32)*128 + t] is d_{qL + t + 128 j} < 0
+  for (int e = t; e < nseg * 4 * FW_THREADS; e += FW_THREADS) {
+    const int tt = e % FW_THREADS, wq = e / FW_THREADS, q = wq >> 2, wj = wq & 3;
+    uint32_t m = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int64_t k = (int64_t)q * FW_L + tt + FW_THREADS * (32 * wj + b);
+      if (k < n && diag[k] < 0) m |= 1u << b;
+    }
+    dbits[e] = m;
+  }
+  __syncthreads();
+
+  const int64_t units = rows * nseg;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t i = u / nseg;
+    const int p = (int)(u - i * nseg);
+    const float* a = A + i * lda;
+    const bool whole = (int64_t)nseg * FW_L <= n;  // no zero padding in this row
+    float x[FW_E];
+    // segment 1 (if any) by cp.async into this thread's round-A slots of the
+    // buffer, segment 0 into registers: all loads of both are in flight at once
+    const uint32_t sb = smem_u32(buf) + 4u * (uint32_t)t;  // slot of k = t + 128 j is t + 129 j
+    if (nseg > 1) {
+      const float* a1 = a + FW_L + t;
+#pragma unroll 8
+      for (int j = 0; j < FW_E; ++j) {
+        const bool in = whole || FW_L + t + FW_THREADS * j < n;
+        cp_async_4(sb + 4u * 129u * (uint32_t)j, in ? a1 + FW_THREADS * j : a, in ? 4u : 0u);
+      }
+      cp_async_commit();
+    }
+#pragma unroll
+    for (int j = 0; j < FW_E; ++j) x[j] = (whole || t + FW_THREADS * j < n) ? __ldg(a + t + FW_THREADS * j) : 0.f;
+#pragma unroll
+    for (int wj = 0; wj < 4; ++wj) {
+      const uint32_t m = dbits[wj * FW_THREADS + t];
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        const int j = 32 * wj + b;
+        x[j] = __uint_as_float(__float_as_uint(x[j]) ^ ((m << (31 - b)) & 0x80000000u));
+      }
+    }
+    if (nseg > 1) {  // the top-bit butterfly with segment 1: sign (-1)^popc(p & 1)
+      cp_async_wait<0>();
+      const uint32_t flip = (uint32_t)(p & 1) << 31;
+#pragma unroll
+      for (int wj = 0; wj < 4; ++wj) {
+        const uint32_t m = dbits[(4 + wj) * FW_THREADS + t];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+          const int j = 32 * wj + b;
+          x[j] += __uint_as_float(__float_as_uint(buf[t + 129 * j]) ^ ((m << (31 - b)) & 0x80000000u) ^ flip);
+        }
+      }
+    }
+    // segments 2 and 3 (nu = 65536): register loads, 16 at a time
+    for (int q = 2; q < nseg; ++q) {
+      const uint32_t flip = (uint32_t)(__popc(p & q) & 1) << 31;
+      const float* aq = a + q * FW_L + t;
+      const int kq = q * FW_L + t;
+#pragma unroll
+      for (int wj = 0; wj < 4; ++wj) {
+        const uint32_t m = dbits[(q * 4 + wj) * FW_THREADS + t];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[16];
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            const int j = 32 * wj + 16 * h + b;
+            v[b] = (whole || kq + FW_THREADS * j < n) ? __ldg(aq + FW_THREADS * j) : 0.f;
+          }
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            const int j = 32 * wj + 16 * h + b;
+            x[j] += __uint_as_float(__float_as_uint(v[b]) ^ ((m << (31 - (16 * h + b))) & 0x80000000u) ^ flip);
+          }
+        }
+      }
+    }
+    // round A: bits 7..13 (register index j); k = t + 128 j at pad(k) = t + 129 j
+#pragma unroll
+    for (int s = 0; s < 7; ++s) stage<FW_E>(x, s);
+#pragma unroll
+    for (int j = 0; j < FW_E; ++j) buf[t + 129 * j] = x[j];
+    __syncthreads();
+    // round B: bits 0..6; k = j + 128 t at pad(k) = j + 129 t (this thread's own slots from here on)
+#pragma unroll
+    for (int j = 0; j < FW_E; ++j) x[j] = buf[j + 129 * t];
+#pragma unroll
+    for (int s = 0; s < 7; ++s) stage<FW_E>(x, s);
+#pragma unroll
+    for (int j = 0; j < FW_E; ++j) buf[j + 129 * t] = x[j];
+    __syncthreads();
+    // sampled columns whose output index is in segment p
+    for (int c = c_lo + t; c < c_hi; c += FW_THREADS) {
+      const int o = mu[c];
+      if ((o >> FW_LOG_L) == p) S[i * ldS + c] = scale * buf[pad(o & (FW_L - 1))];
+    }
+    __syncthreads();
+  }
+}
+
+// Unit length and segment count for nu; 0 if the FWHT path does not apply.
+int fwht_segments(int64_t nu) {
+  if (nu < FW_L || nu > (int64_t)FW_L * FW_MAX_SEG) return 0;
+  return (int)(nu / FW_L);
+}
+
+int srht_apply_fwht(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double scale, float* S, int64_t ldS,
+                    cudaStream_t s) {
+  const int nseg = fwht_segments(h->nu);
+  if (!nseg || A->dtype != SK_F32) return SK_ERR_UNSUPPORTED;
+  if (c_hi <= c_lo) return SK_OK;
+  const size_t smem = FW_BUF * sizeof(float) + FW_DWORDS * sizeof(uint32_t);
+  static bool attr = false;
+  if (!attr) {
+    JLS_CHECK_CUDA(cudaFuncSetAttribute(srht_fwht_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const int64_t units = A->rows * nseg;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(3 * num_sms(), units));
+  srht_fwht_rows_kernel<<<grid, FW_THREADS, smem, s>>>(static_cast<const float*>(A->A), A->ld, A->rows, h->n, nseg,
+                                                        h->srht_diag, h->srht_mu, c_lo, c_hi, (float)scale, S, ldS);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+}  // namespace jls

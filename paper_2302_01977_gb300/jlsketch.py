@@ -47,7 +47,8 @@ KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": 
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
            "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_dims", "sketch_export",
-           "sketch_device_status", "sketch_launch_count", "sketch_destroy", "sketch_strerror"]
+           "sketch_device_status", "sketch_launch_count", "sketch_srht_route", "sketch_destroy",
+           "sketch_strerror"]
 
 
 class JLSketchError(RuntimeError):
@@ -91,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
         "sketch_device_status": (i32, [vp, vp]),
         "sketch_launch_count": (i64, []),
+        "sketch_srht_route": (i32, [i64, i64, i64, i32, i32]),
         "sketch_destroy": (None, [vp]),
         "sketch_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -275,6 +277,11 @@ def sketch_device_status(h, stream=None) -> None:
 
 def sketch_launch_count() -> int:
     return int(lib().sketch_launch_count())
+
+
+def sketch_srht_route(nu: int, rows: int, cols: int, width: int, prec: int) -> int:
+    """1: row FWHT, 0: +-1 product, -1: shape not measured yet (SRHT S = A R)."""
+    return int(lib().sketch_srht_route(int(nu), int(rows), int(cols), int(width), int(prec)))
 
 
 def sketch_destroy(h) -> None:
