@@ -124,12 +124,15 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream);
 /*
  * sketch_apply -- S = A R and/or S' = A^T R for the current R (Sec. 6.3).
  *   A      explicit (generator == 0) or kernel generator; rows x cols with
- *          cols == n for S and rows == n for S'.
+ *          cols == n for S and rows == n for S'.  A generated K(X, Y) is
+ *          written in blocks of rows (at least 20480, or 2 GiB) to scratch the
+ *          handle owns and each block is sketched; S' is computed as the S
+ *          product of K(Y, X), which equals K^T.
  *   which  SK_S, SK_ST or SK_BOTH.
  *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 / SK_PREC_FP8 (F32, SRHT/Gaussian).
  *   S      device, rows x d_total (ldS >= d_total) of A's dtype; used if which & SK_S.
  *   St     device, cols x d_total (ldSt >= d_total);             used if which & SK_ST.
- * Asynchronous.  Errors: INVALID_ARG, ALIGN, DTYPE, UNSUPPORTED, DEVICE.
+ * Asynchronous.  Errors: INVALID_ARG, ALIGN, DTYPE, UNSUPPORTED, NOMEM, DEVICE.
  */
 int sketch_apply(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec,
                  void* S, int64_t ldS, void* St, int64_t ldSt, void* stream);

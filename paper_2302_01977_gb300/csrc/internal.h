@@ -105,6 +105,8 @@ struct sk_op {
   jls::Basis basis[2];
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* gen_scratch = nullptr;        // row blocks of a generated kernel matrix
+  size_t gen_scratch_bytes = 0;
   double* host_norms = nullptr;       // pinned: the stopping test's norm partials
   cudaEvent_t norms_ready = nullptr;  // recorded after their copy
 };
@@ -145,7 +147,8 @@ int dense_apply_fp8(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi,
                     int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
 
 // --- kernel_matrix.cu ---
-int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s);
+// A_ij = K(x_i, y_j) + shift [i + diag_off == j] for the generator's X, Y
+int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s, int64_t diag_off = 0);
 
 // --- adaptive.cu ---
 int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, double factor,

@@ -1,5 +1,6 @@
 // jlsketch.cu -- the C ABI of libjlsketch: argument checks, handle state and
 // dispatch to the kernels.  Every function returns a status and never throws.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -45,9 +46,12 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
                        const void* St, int64_t ldSt) {
   if (!A || which < SK_S || which > SK_BOTH) return SK_ERR_INVALID_ARG;
   if (A->dtype != SK_F32 && A->dtype != SK_F64) return SK_ERR_DTYPE;
-  if (A->generator) return SK_ERR_UNSUPPORTED;
-  if (A->rows < 1 || A->cols < 1 || !A->A || A->ld < A->cols) return SK_ERR_INVALID_ARG;
-  if (!aligned16(A->A) || (A->ld * (int64_t)elem_size(A->dtype)) % 16 != 0) return SK_ERR_ALIGN;
+  if (A->generator) {
+    if (A->generator != 1 || A->rows < 1 || A->cols < 1 || !A->X || !A->Y || !(A->h > 0)) return SK_ERR_INVALID_ARG;
+  } else {
+    if (A->rows < 1 || A->cols < 1 || !A->A || A->ld < A->cols) return SK_ERR_INVALID_ARG;
+    if (!aligned16(A->A) || (A->ld * (int64_t)elem_size(A->dtype)) % 16 != 0) return SK_ERR_ALIGN;
+  }
   if ((which & SK_S) && (A->cols != h->n || !S || ldS < h->d_total)) return SK_ERR_INVALID_ARG;
   if ((which & SK_ST) && (A->rows != h->n || !St || ldSt < h->d_total)) return SK_ERR_INVALID_ARG;
   if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2 && prec != SK_PREC_FP8) return SK_ERR_DTYPE;
@@ -136,7 +140,7 @@ static void free_handle(sk_op* h) {
   void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
                   h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
-                  h->basis[0].Q, h->basis[1].Q, h->scratch};
+                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_norms) cudaFreeHost(h->host_norms);
@@ -222,11 +226,64 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream) {
   return SK_OK;
 }
 
+// A generated kernel matrix K(X, Y) is sketched in blocks of rows written to
+// handle-owned scratch (at least 20480 rows -- 160 M-tiles, more than the SMs
+// -- or 2 GiB): S = K R block by block, and S' = K^T R as the S product of
+// K(Y, X), which is K^T (the kernel and the diagonal shift are symmetric), so
+// every block is an ordinary S product over all of R.
+static int apply_generator(sk_op* h, const sk_matrix* g, int which, int prec, int c_lo, int c_hi, void* S,
+                           int64_t ldS, void* St, int64_t ldSt, cudaStream_t s) {
+  const size_t es = elem_size(g->dtype);
+  for (int part = 0; part < 2; ++part) {
+    if (!(which & (part == 0 ? SK_S : SK_ST))) continue;
+    const int64_t rows = part == 0 ? g->rows : g->cols, n = part == 0 ? g->cols : g->rows;
+    const uint8_t* P = static_cast<const uint8_t*>(part == 0 ? g->X : g->Y);
+    const void* Q = part == 0 ? g->Y : g->X;
+    uint8_t* out = static_cast<uint8_t*>(part == 0 ? S : St);
+    const int64_t ldo = part == 0 ? ldS : ldSt;
+    const int64_t ld = (n * (int64_t)es + 15) / 16 * 16 / (int64_t)es;
+    const int64_t row_bytes = ld * (int64_t)es;
+    int64_t blk = std::max<int64_t>(20480, ((int64_t)1 << 31) / row_bytes);
+    blk = std::min(rows, (blk + 127) / 128 * 128);
+    const size_t need = (size_t)(blk * row_bytes);
+    if (h->gen_scratch_bytes < need) {
+      if (h->gen_scratch) cudaFree(h->gen_scratch);
+      h->gen_scratch = nullptr;
+      h->gen_scratch_bytes = 0;
+      JLS_CHECK_CUDA(cudaMalloc(&h->gen_scratch, need));
+      h->gen_scratch_bytes = need;
+    }
+    for (int64_t r0 = 0; r0 < rows; r0 += blk) {
+      const int64_t rb = std::min(blk, rows - r0);
+      sk_matrix gb = *g;
+      gb.rows = rb;
+      gb.cols = n;
+      gb.X = P + (size_t)(3 * r0) * es;
+      gb.Y = Q;
+      JLS_CHECK(launch_kernel_matrix(&gb, h->gen_scratch, ld, s, r0));
+      sk_matrix eb{};
+      eb.dtype = g->dtype;
+      eb.rows = rb;
+      eb.cols = n;
+      eb.A = h->gen_scratch;
+      eb.ld = ld;
+      JLS_CHECK(dispatch(h, &eb, SK_S, prec, c_lo, c_hi, out + (size_t)(r0 * ldo) * es, ldo, nullptr, 0, s));
+    }
+  }
+  return SK_OK;
+}
+
+static int run_apply(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, void* S, int64_t ldS,
+                     void* St, int64_t ldSt, cudaStream_t s) {
+  if (A->generator) return apply_generator(h, A, which, prec, c_lo, c_hi, S, ldS, St, ldSt, s);
+  return dispatch(h, A, which, prec, c_lo, c_hi, S, ldS, St, ldSt, s);
+}
+
 int sketch_apply(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec, void* S, int64_t ldS, void* St,
                  int64_t ldSt, void* stream) {
   if (!h) return SK_ERR_INVALID_ARG;
   JLS_CHECK(check_apply(h, A, which, prec, S, ldS, St, ldSt));
-  return dispatch(h, A, which, prec, 0, h->d_total, S, ldS, St, ldSt, static_cast<cudaStream_t>(stream));
+  return run_apply(h, A, which, prec, 0, h->d_total, S, ldS, St, ldSt, static_cast<cudaStream_t>(stream));
 }
 
 int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec, void* S, int64_t ldS,
@@ -245,7 +302,7 @@ int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32
   const double factor = op_scale(h) / old_scale;
   if (which & SK_S) JLS_CHECK(scale_columns(S, A->dtype, A->rows, ldS, 0, d_old, factor, s));
   if (which & SK_ST) JLS_CHECK(scale_columns(St, A->dtype, A->cols, ldSt, 0, d_old, factor, s));
-  return dispatch(h, A, which, prec, d_old, h->d_total, S, ldS, St, ldSt, s);
+  return run_apply(h, A, which, prec, d_old, h->d_total, S, ldS, St, ldSt, s);
 }
 
 int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, int64_t ldS, int32_t dtype,

@@ -1,6 +1,6 @@
 // kernel_matrix.cu -- explicit Gaussian kernel matrix
-//   A_ij = exp(-||x_i - y_j||^2 / (2 h^2)) + shift * [i == j]
-// written row-major.  Store-bound: one coalesced pass over A; the y points of
+//   A_ij = exp(-||x_i - y_j||^2 / (2 h^2)) + shift * [i + diag_off == j]
+// written row-major (diag_off places a block of rows inside a larger matrix).  Store-bound: one coalesced pass over A; the y points of
 // a column block are staged in shared memory once per CTA.
 #include "common.cuh"
 #include "internal.h"
@@ -13,7 +13,8 @@ __device__ __forceinline__ double kexp(double x) { return exp(x); }
 template <typename T, int COLS_PER_CTA>
 __global__ void __launch_bounds__(256)
     kernel_matrix_kernel(const T* __restrict__ X, const T* __restrict__ Y, int64_t rows, int64_t cols,
-                         T neg_inv_2h2, T shift, T* __restrict__ A, int64_t ld, int rows_per_cta) {
+                         T neg_inv_2h2, T shift, int64_t diag_off, T* __restrict__ A, int64_t ld,
+                         int rows_per_cta) {
   __shared__ T ys[3 * COLS_PER_CTA];
   const int64_t c0 = (int64_t)blockIdx.x * COLS_PER_CTA;
   const int ncols = (int)min64(COLS_PER_CTA, cols - c0);
@@ -27,13 +28,13 @@ __global__ void __launch_bounds__(256)
     for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
       const T d0 = x0 - ys[3 * j], d1 = x1 - ys[3 * j + 1], d2 = x2 - ys[3 * j + 2];
       T a = kexp((d0 * d0 + d1 * d1 + d2 * d2) * neg_inv_2h2);
-      if (i == c0 + j) a += shift;
+      if (i + diag_off == c0 + j) a += shift;
       arow[j] = a;
     }
   }
 }
 
-int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s) {
+int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s, int64_t diag_off) {
   constexpr int CPC = 1024;
   const int rows_per_cta = 64;
   dim3 grid((unsigned)((g->cols + CPC - 1) / CPC), (unsigned)((g->rows + rows_per_cta - 1) / rows_per_cta));
@@ -42,12 +43,12 @@ int launch_kernel_matrix(const sk_matrix* g, void* A, int64_t ld, cudaStream_t s
   if (g->dtype == SK_F32)
     kernel_matrix_kernel<float, CPC><<<grid, 256, 0, s>>>(static_cast<const float*>(g->X),
                                                          static_cast<const float*>(g->Y), g->rows, g->cols,
-                                                         (float)nih, (float)g->shift, static_cast<float*>(A),
-                                                         ld, rows_per_cta);
+                                                         (float)nih, (float)g->shift, diag_off,
+                                                         static_cast<float*>(A), ld, rows_per_cta);
   else
     kernel_matrix_kernel<double, CPC><<<grid, 256, 0, s>>>(static_cast<const double*>(g->X),
                                                           static_cast<const double*>(g->Y), g->rows, g->cols,
-                                                          nih, g->shift, static_cast<double*>(A), ld,
+                                                          nih, g->shift, diag_off, static_cast<double*>(A), ld,
                                                           rows_per_cta); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
