@@ -26,12 +26,10 @@ namespace jls {
 template <typename T>
 __global__ void scale_cols_kernel(T* S, int64_t rows, int64_t ld, int c0, int c1, T f) {
   const int w = c1 - c0;
-  const int64_t total = rows * w;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = q / w;
-    const int c = (int)(q % w);
-    S[r * ld + c0 + c] *= f;
-  }
+  const int64_t rpb = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r_beg = (int64_t)blockIdx.x * rpb, r_end = min64(rows, r_beg + rpb);
+  for (int64_t r = r_beg; r < r_end; ++r)
+    for (int c = threadIdx.x; c < w; c += blockDim.x) S[r * ld + c0 + c] *= f;
 }
 
 int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, double factor, cudaStream_t s) {
@@ -318,27 +316,46 @@ __global__ void __launch_bounds__(trsm_rows<T>()) rows_trsm_kernel(T* W, int64_t
   }
 }
 
-template <typename T>
-__global__ void copy_block_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd,
-                                  int64_t rows, int b) {
-  const int64_t total = rows * b;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / b;
-    const int c = (int)(e % b);
-    dst[r * ldd + c] = src[r * lds + c];
+// Walk the b columns of rows [r_begin, r_end) with blockDim.x = 256 threads and
+// no per-element division: for b <= 256, 256/b rows at a time (thread t takes
+// column t % b of row t / b); for wider blocks, each row in steps of 256.
+template <typename F>
+__device__ __forceinline__ void for_block(int64_t r_begin, int64_t r_end, int b, F f) {
+  const int t = threadIdx.x;
+  if (b <= 256) {
+    const int per = 256 / b;
+    if (t >= per * b) return;
+    const int c = t % b, ro = t / b;
+    for (int64_t r = r_begin + ro; r < r_end; r += per) f(r, c);
+  } else {
+    for (int64_t r = r_begin; r < r_end; ++r)
+      for (int c = t; c < b; c += 256) f(r, c);
   }
 }
 
 template <typename T>
-__global__ void sumsq_partial(const T* __restrict__ W, int64_t ldw, int64_t rows, int b, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) copy_block_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
+                                                         int64_t ldd, int64_t rows, int b) {
+  const int64_t rpb = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min64(rows, r0 + rpb);
+  for_block(r0, r1, b, [&](int64_t r, int c) { dst[r * ldd + c] = src[r * lds + c]; });
+}
+
+// Sum of squares of a rows x b block, one FP64 partial per CTA.  A thread
+// sums its own values in T (at most rows / gridDim of them, a few hundred
+// here), the CTA adds the thread sums in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) sumsq_partial(const T* __restrict__ W, int64_t ldw, int64_t rows, int b,
+                                                     double* __restrict__ part) {
   __shared__ double red[256];
-  double s = 0;
-  const int64_t total = rows * b;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)W[(e / b) * ldw + (e % b)];
-    s += v * v;
-  }
-  red[threadIdx.x] = s;
+  const int64_t rpb = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min64(rows, r0 + rpb);
+  T s = T(0);
+  for_block(r0, r1, b, [&](int64_t r, int c) {
+    const T v = W[r * ldw + c];
+    s = fma(v, v, s);
+  });
+  red[threadIdx.x] = (double)s;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];

@@ -108,47 +108,71 @@ struct BlockOffsets {
   int off[MAX_BLOCKS + 1];
 };
 
-__global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha,
-                                 const __grid_constant__ BlockOffsets bo, int d_total, int tile, int esize,
-                                 int64_t e_stride, int64_t o_stride, uint4* __restrict__ out_e,
-                                 uint32_t* __restrict__ out_o) {
-  extern __shared__ uint32_t sh_cnt[];  // d_total + 1
-  const int t = blockIdx.x;
+// One CTA (256 threads) per tile of `tile` rows of R: a counting sort of the
+// tile's entries by column.  (1) count per column with shared atomics; (2)
+// exclusive scan; (3) place, one block of R at a time: the block's entries are
+// staged in shared memory and warp 0 walks the rows in order, so rows stay
+// ascending inside a column (a row has at most one entry per column within a
+// block, and blocks own disjoint columns, so the running cursors never clash).
+constexpr int CCS_THREADS = 256;
+constexpr int CCS_STAGE = SJLT_TILE_F32 * SJLT_MAX_ALPHA;  // staged entries of one block
+
+__global__ void __launch_bounds__(CCS_THREADS)
+    ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha, const __grid_constant__ BlockOffsets bo,
+                     int d_total, int tile, int esize, int64_t e_stride, int64_t o_stride, uint4* __restrict__ out_e,
+                     uint32_t* __restrict__ out_o) {
+  extern __shared__ uint32_t sh_cnt[];  // d_total + 1 counters / cursors
+  __shared__ uint32_t th_sum[CCS_THREADS];
+  __shared__ int32_t stage[CCS_STAGE];
+  const int t = blockIdx.x, tid = threadIdx.x;
   const int64_t r0 = (int64_t)t * tile;
   const int rows = (int)min64(tile, n - r0);
-  auto block_of = [&](int c) {
-    int b = 0;
-    while (b + 1 < bo.n && bo.off[b + 1] <= c) ++b;
-    return b;
-  };
-  for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
-    const int32_t* base = ents + ((int64_t)block_of(c) * n + r0) * alpha;
-    uint32_t cnt = 0;
-    for (int r = 0; r < rows; ++r)
-      for (int k = 0; k < alpha; ++k) cnt += ((base[(int64_t)r * alpha + k] & 0x7fffffff) == c);
-    sh_cnt[c] = cnt;
+  const int B = bo.n;
+  for (int c = tid; c <= d_total; c += CCS_THREADS) sh_cnt[c] = 0;
+  __syncthreads();
+  const int per_blk = rows * alpha;
+  for (int b = 0; b < B; ++b) {
+    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    for (int q = tid; q < per_blk; q += CCS_THREADS) atomicAdd(&sh_cnt[base[q] & 0x7fffffff], 1u);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {  // small serial scan (d_total <= 8192)
+  // exclusive scan: each thread owns a contiguous chunk of counters
+  const int chunk = (d_total + CCS_THREADS - 1) / CCS_THREADS;
+  const int c_beg = min(d_total, tid * chunk), c_end = min(d_total, c_beg + chunk);
+  uint32_t local = 0;
+  for (int c = c_beg; c < c_end; ++c) local += sh_cnt[c];
+  th_sum[tid] = local;
+  __syncthreads();
+  if (tid == 0) {
     uint32_t acc = 0;
-    for (int c = 0; c < d_total; ++c) {
-      const uint32_t v = sh_cnt[c];
-      sh_cnt[c] = acc;
+    for (int q = 0; q < CCS_THREADS; ++q) {
+      const uint32_t v = th_sum[q];
+      th_sum[q] = acc;
       acc += v;
     }
     sh_cnt[d_total] = acc;
   }
   __syncthreads();
+  uint32_t acc = th_sum[tid];
+  for (int c = c_beg; c < c_end; ++c) {
+    const uint32_t v = sh_cnt[c];
+    sh_cnt[c] = acc;
+    acc += v;
+  }
+  __syncthreads();
   uint32_t* oo = out_o + (int64_t)t * o_stride;
   uint4* oe = out_e + (int64_t)t * e_stride;
-  for (int c = threadIdx.x; c <= d_total; c += blockDim.x) oo[c] = sh_cnt[c];
-  for (int c = threadIdx.x; c < d_total; c += blockDim.x) {
-    const int32_t* base = ents + ((int64_t)block_of(c) * n + r0) * alpha;
-    uint32_t pos = sh_cnt[c];
-    for (int r = 0; r < rows; ++r)
-      for (int k = 0; k < alpha; ++k) {
-        const int32_t e = base[(int64_t)r * alpha + k];
-        if ((e & 0x7fffffff) == c) {
+  for (int c = tid; c <= d_total; c += CCS_THREADS) oo[c] = sh_cnt[c];
+  __syncthreads();
+  for (int b = 0; b < B; ++b) {
+    const int32_t* base = ents + ((int64_t)b * n + r0) * alpha;
+    for (int q = tid; q < per_blk; q += CCS_THREADS) stage[q] = base[q];
+    __syncthreads();
+    if (tid < 32) {
+      for (int r = 0; r < rows; ++r) {
+        for (int k = tid; k < alpha; k += 32) {
+          const int32_t e = stage[r * alpha + k];
+          const uint32_t pos = sh_cnt[e & 0x7fffffff]++;
           // {S' offset of row r, sign, sign, S offset of row r}, see TiledCcs
           uint4 rec;
           rec.x = (uint32_t)r * CCS_ROW_BYTES;
@@ -159,9 +183,12 @@ __global__ void ccs_build_kernel(const int32_t* __restrict__ ents, int64_t n, in
             rec.y = 0u;
             rec.z = (e < 0) ? 0xbff00000u : 0x3ff00000u;
           }
-          oe[pos++] = rec;
+          oe[pos] = rec;
         }
+        __syncwarp();
       }
+    }
+    __syncthreads();
   }
 }
 
@@ -200,10 +227,8 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   }
   bo.off[B] = off;
   const size_t shm = sizeof(uint32_t) * (h->d_total + 1);
-  if (shm > 48 * 1024)
-    JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)shm));
-  ccs_build_kernel<<<C.ntiles, 256, shm, s>>>(h->sjlt_ents, h->n, h->alpha, bo, h->d_total, tile,
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  ccs_build_kernel<<<C.ntiles, CCS_THREADS, shm, s>>>(h->sjlt_ents, h->n, h->alpha, bo, h->d_total, tile,
                                               which_tile == 0 ? 4 : 8, C.e_stride, C.o_stride, C.ents, C.offs);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
