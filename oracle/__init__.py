@@ -20,6 +20,9 @@ operators  SJLT (graph and block construction, Sec. 2.4.3; data structure
            Algorithm 1).
 sketch     S = A R and S' = A^T R by dense FP64 products (Sec. 6.3), the
            kernel-matrix generator, a textbook fast Walsh-Hadamard transform.
+kernel_grad the matrix-free kernel sketch S = K(X, X; h) R and the gradient
+           of <dS, S> with respect to X and h (chain rule of the definition;
+           the paper does not differentiate the sketch).
 adaptive   the global adaptive loop: first sketch with d0 + Delta-d columns,
            two-pass block Gram-Schmidt projection and the Frobenius stopping
            test (Eq. (3.1) and the remark after it; Algorithm 1).
