@@ -504,6 +504,72 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+DIFF = dict(name="kernel_sketch_grad_n262144", n=262144, d=256, alpha=4, h=0.05, seed=20230203 + 4)
+
+
+def run_differentiation(args):
+    """Matrix-free S = K(X, X; h) R (K never formed) and its adjoint (dX, dh)
+    for 262144 points uniform in [0,1]^3, h = 0.05, block SJLT d = 256,
+    alpha = 4, upstream dS ~ N(0, 1); against the explicit-K plain path (the
+    generator mode of sketch_apply: K written block by block, 20480 rows at a
+    time, then the SJLT S = A R product of each block)."""
+    import torch
+
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = DIFF
+    n, d = w["n"], w["d"]
+    torch.cuda.set_device(0)
+    X = torch.from_numpy(inputs.points(n, seed=w["seed"]).astype("float32")).cuda()
+    op = jl.Sketch("sjlt_block", n, d, w["alpha"], w["seed"] + 3)
+    S = torch.empty((n, d), device="cuda")
+    S2 = torch.empty((n, d), device="cuda")
+    dS = torch.randn((n, d), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    dX = torch.empty_like(X)
+    dh = torch.empty(1, dtype=torch.float64, device="cuda")
+    gen = jl.generator(X, X, w["h"])
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    clocks = Clocks(0)
+    clocks.start()
+    l0 = jl.sketch_launch_count()
+    t_fwd = timed(lambda: jl.sketch_kernel_apply(op.h, X, X, w["h"], S), args.steps)
+    t_adj = timed(lambda: jl.sketch_kernel_adjoint(op.h, X, w["h"], dS, dX, dh), args.steps)
+    launches = jl.sketch_launch_count() - l0
+    t_exp = timed(lambda: jl.sketch_apply(op.h, gen, jl.SK_S, 0, S=S2), 1)
+    ck = clocks.stop()
+    jl.sketch_device_status(op.h)
+    fwd_err = float((torch.linalg.norm(S - S2) / torch.linalg.norm(S2)).item())
+    pairs = float(n) * n
+    line = {"metric": METRIC, "value": round(pairs / (t_fwd + t_adj) / 1e6, 1), "unit": "G kernel pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_fwd + t_adj, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "ours",
+            "config": {"workload": w["name"], "n": n, "d": d, "alpha": w["alpha"], "h": w["h"],
+                       "upstream": "dS ~ N(0,1)", "l2": "A never formed; X (3 MB) and dS (268 MB)"},
+            "forward_ms": round(t_fwd, 3), "adjoint_ms": round(t_adj, 3),
+            "explicit_k_forward_ms": round(t_exp, 3), "forward_speedup_vs_explicit": round(t_exp / t_fwd, 2),
+            "forward_rel_diff_vs_explicit": float(f"{fwd_err:.3e}"),
+            "forward_gpairs_per_s": round(pairs / t_fwd / 1e6, 1), "adjoint_gpairs_per_s": round(pairs / t_adj / 1e6, 1),
+            "gpu_launches": int(launches), "clocks": ck}
+    op.close()
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,7 +583,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
-    ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536"],
+    ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536",
+                                           "kernel_sketch_grad_n262144"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",
@@ -529,6 +596,8 @@ def main():
         run_reference(args)
     elif args.workload == "precision_fp32_n65536":
         run_precision(args)
+    elif args.workload == "kernel_sketch_grad_n262144":
+        run_differentiation(args)
     else:
         run_ours(args)
 

@@ -211,6 +211,45 @@ int sketch_project_norms_noalloc(const void* Q, int64_t ldQ, int32_t q_cols,
  */
 int kernel_matrix(const sk_matrix* gen, void* A, int64_t ld, void* stream);
 
+/*
+ * sketch_kernel_apply -- matrix-free sketch of a Gaussian kernel matrix that is
+ * never formed (the matrix-free setting of Sec. 1.1, kernel matrices of points
+ * as in Sec. 8.1):
+ *     S = K(X, Y; h) R,  K_ij = exp(-||x_i - y_j||^2 / (2 h^2)) + shift [i == j],
+ * for an SJLT operator R (Sec. 2.4.3, n = the handle's n).  Tiles of K are
+ * computed in shared memory next to the SJLT product of Sec. 6.3 and
+ * discarded; K is never written to device memory.
+ *   X      device FP32, m x 3, row-major: points of the rows of S, m >= 1.
+ *   Y      device FP32, n x 3: points of the rows of R (X == Y is allowed).
+ *   h_bw   kernel width h > 0;  shift  added where i == j (0 for a pure kernel).
+ *   S      device FP32, m x d_total (ldS >= d_total), overwritten.
+ * Asynchronous on `stream`.  FP32 arithmetic (exp2 of FP32 squared distances),
+ * relative error of order 1e-6 against the FP64 definition.
+ * Errors: INVALID_ARG, UNSUPPORTED (not an SJLT handle), NOMEM, DEVICE.
+ */
+int sketch_kernel_apply(sk_handle h, const float* X, int64_t m, const float* Y, double h_bw,
+                        double shift, float* S, int64_t ldS, void* stream);
+
+/*
+ * sketch_kernel_adjoint -- gradient of L = <dS, K(X, X; h) R> (shift 0) with
+ * respect to the points X and the width h, for an SJLT R (the adjoint of
+ * sketch_kernel_apply with X == Y; the paper does not differentiate the
+ * sketch, this is the chain rule of its definition):
+ *     G = dS R^T,
+ *     dX_i = (1/h^2) sum_j (G_ij + G_ji) K_ij (x_j - x_i),
+ *     dh   = (1/h^3) sum_ij G_ij K_ij ||x_i - x_j||^2.
+ * K is recomputed tile by tile, never stored.
+ *   X    device FP32, n x 3 (n = the handle's n).
+ *   dS   device FP32, n x d_total (ldS >= d_total): the upstream gradient.
+ *   dX   device FP32, n x 3, overwritten (must not alias X).
+ *   dh   device FP64, one value, overwritten.
+ * Needs d_total <= 384 and alpha * blocks <= 32 (else UNSUPPORTED).  The handle
+ * keeps an n x 4 FP32 scratch buffer for the sums over the second index.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, NOMEM, DEVICE.
+ */
+int sketch_kernel_adjoint(sk_handle h, const float* X, double h_bw, const float* dS, int64_t ldS,
+                          float* dX, double* dh, void* stream);
+
 /* sketch_dims -- shape of the current operator (host outputs; any may be NULL). */
 int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha,
                 int32_t* blocks);

@@ -48,6 +48,18 @@ struct TiledCcs {
   size_t ents_cap = 0, offs_cap = 0;  // bytes
 };
 
+// Matrix-free S' tiles (sjlt_cols_kernel<..., GEN = true>): A_ij = K(p_i, q_j) =
+// exp2(-c2 |p_i - q_j|^2) + shift [i == j], c2 = log2(e) / (2 h^2); P holds the
+// points of the rows of R, Q the points of the output rows (FP32, 3 per point).
+struct KGen {
+  const float* P = nullptr;
+  const float* Q = nullptr;
+  float c2 = 0.f;
+  float shift = 0.f;
+};
+constexpr int GEN_WARPS = 3;   // tile-computing warps per CTA
+constexpr int GEN_JOBS = 13;   // consumer warps per CTA beside them (16 warps in all)
+
 struct Basis {                // orthonormal basis Q of earlier sketch columns
   void* Q = nullptr;          // rows x d_max, row-major (ld = d_max), dtype
   int dtype = 0;
@@ -106,6 +118,8 @@ struct sk_op {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   void* gen_scratch = nullptr;        // row blocks of a generated kernel matrix
+  float* ksk_u = nullptr;             // kernel-sketch adjoint: second sums, n x 4
+  size_t ksk_u_bytes = 0;
   size_t gen_scratch_bytes = 0;
   double* host_norms = nullptr;       // pinned: the stopping test's norm partials
   cudaEvent_t norms_ready = nullptr;  // recorded after their copy
@@ -128,6 +142,15 @@ int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s);
 // [c_lo, c_hi) of R, writing scale * (signed sums).
 int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
                void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+
+// Matrix-free S = K(Q, P; h) R (+ shift on the diagonal) for an SJLT R with n
+// rows (P: n points) and m output rows (Q: m points), FP32, never forming K.
+int sjlt_kernel_apply(sk_op* h, const float* P, int64_t n, const float* Q, int64_t m, double hbw,
+                      double shift, double scale, float* S, int64_t ldS, cudaStream_t s);
+
+// --- kernel_sketch.cu ---  gradient of <dS, K(X, X; h) R> in X and h (SJLT R)
+int kernel_sketch_adjoint(sk_op* h, const float* X, double hbw, double scale, const float* dS, int64_t ldS,
+                          float* dX, double* dh, cudaStream_t s);
 
 // --- dense_simt.cu ---  SRHT / Gaussian on CUDA cores (FP32 or FP64)
 int dense_apply_simt(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,

@@ -140,7 +140,7 @@ static void free_handle(sk_op* h) {
   void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
                   h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
-                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch};
+                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch, h->ksk_u};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_norms) cudaFreeHost(h->host_norms);
@@ -327,6 +327,24 @@ int kernel_matrix(const sk_matrix* gen, void* A, int64_t ld, void* stream) {
   if (gen->dtype != SK_F32 && gen->dtype != SK_F64) return SK_ERR_DTYPE;
   JLS_CHECK(check_device());
   return launch_kernel_matrix(gen, A, ld, static_cast<cudaStream_t>(stream));
+}
+
+static bool is_sjlt(const sk_op* h) { return h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH; }
+
+int sketch_kernel_apply(sk_handle h, const float* X, int64_t m, const float* Y, double h_bw, double shift, float* S,
+                        int64_t ldS, void* stream) {
+  if (!h || !X || !Y || !S || m < 1 || !(h_bw > 0) || ldS < h->d_total) return SK_ERR_INVALID_ARG;
+  if (!is_sjlt(h)) return SK_ERR_UNSUPPORTED;
+  JLS_CHECK(check_device());
+  return sjlt_kernel_apply(h, Y, h->n, X, m, h_bw, shift, op_scale(h), S, ldS, static_cast<cudaStream_t>(stream));
+}
+
+int sketch_kernel_adjoint(sk_handle h, const float* X, double h_bw, const float* dS, int64_t ldS, float* dX,
+                          double* dh, void* stream) {
+  if (!h || !X || !dS || !dX || !dh || !(h_bw > 0) || ldS < h->d_total) return SK_ERR_INVALID_ARG;
+  if (!is_sjlt(h)) return SK_ERR_UNSUPPORTED;
+  JLS_CHECK(check_device());
+  return kernel_sketch_adjoint(h, X, h_bw, op_scale(h), dS, ldS, dX, dh, static_cast<cudaStream_t>(stream));
 }
 
 int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha, int32_t* blocks) {

@@ -125,12 +125,147 @@ struct ColsAcc<double> {
   __device__ __forceinline__ double get(int q) const { return q == 0 ? a : b; }
 };
 
-template <typename T, int TILE, int NB, int STAGES>
+// ---------------------------------------------------------------------------
+// Matrix-free tiles: GEN_WARPS warps compute the S' tile A_ij = K(p_i, q_j) =
+// 2^(-c2 |p_i - q_j|^2) (+ shift where i == j) in shared memory instead of
+// loading it, so the kernel sketches a Gaussian kernel matrix that is never
+// written to HBM.  Lane l owns the 4 columns of its 16-byte slot (their points
+// stay in registers for the whole block of A) and computes them for rows pw,
+// pw + GEN_WARPS, ... of the tile; the rows' points are loaded one tile ahead,
+// two per lane, and broadcast by shuffles.  Arithmetic runs on pairs of
+// columns (FADD2 / FFMA2), the exponential is the MUFU ex2 instruction.  Warp 0
+// lane 0 also brings the tile's entry records and column offsets by bulk copy.
+// Rows and columns outside the matrix hold 0.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int TILE, int STAGES>
+__device__ __forceinline__ void gen_producer(const KGen& g, int64_t rowsA, int64_t colsA, const uint4* ents,
+                                             const uint32_t* offs, int64_t e_stride, int64_t o_stride, int c_lo,
+                                             int c_hi, uint32_t E_BYTES, uint32_t O_BYTES, uint32_t tiles_sa,
+                                             uint32_t ents_sa, uint32_t offs_sa, uint32_t full0, uint32_t empty0,
+                                             int o_lo, int pw, int lane, int64_t u0, int64_t u1, int* err) {
+  constexpr int BW = 128;
+  constexpr uint32_t TILE_BYTES = TILE * BW * 4;
+  constexpr int ROWS = (TILE + GEN_WARPS - 1) / GEN_WARPS;  // rows per warp (<= 64: two per lane)
+  static_assert(ROWS <= 64, "two row points per lane");
+  const int ntiles = (int)((rowsA + TILE - 1) / TILE);
+  const float2 nc2 = make_float2(-g.c2, -g.c2);
+  float2 nqx0, nqx1, nqy0, nqy1, nqz0, nqz1;  // minus this lane's column points, as pairs (0,1), (2,3)
+  bool cin[4];
+  int64_t cur_blk = -1;
+  // points of rows pw + GEN_WARPS * lane and pw + GEN_WARPS * (lane + 32) of a tile
+  auto load_rows = [&](int t, float (&pa)[3], float (&pb)[3]) {
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int r = pw + GEN_WARPS * (lane + 32 * h2);
+      const int64_t i = (int64_t)t * TILE + r;
+      const bool in = r < TILE && i < rowsA;
+      float* dst = h2 ? pb : pa;
+      dst[0] = in ? __ldg(g.P + 3 * i) : 0.f;
+      dst[1] = in ? __ldg(g.P + 3 * i + 1) : 0.f;
+      dst[2] = in ? __ldg(g.P + 3 * i + 2) : 0.f;
+    }
+  };
+  float pa[3], pb[3];
+  if (u1 > u0) load_rows((int)(u0 % ntiles), pa, pb);
+  int k = 0;
+  for (int64_t u = u0; u < u1; ++u, ++k) {
+    const int s = k % STAGES;
+    const int64_t blk = u / ntiles;
+    const int t = (int)(u % ntiles);
+    float na[3], nb[3];  // next tile's row points, in flight while this tile is computed
+    if (u + 1 < u1) load_rows((int)((u + 1) % ntiles), na, nb);
+    if (k >= STAGES) {
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(empty0 + 8 * s, ((k / STAGES) - 1) & 1, err) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+    }
+    const uint32_t fb = full0 + 8 * s;
+    if (pw == 0 && lane == 0) {
+      const uint32_t lo = __ldg(offs + (int64_t)t * o_stride + c_lo), hi = __ldg(offs + (int64_t)t * o_stride + c_hi);
+      uint32_t eb = (hi - lo) * 16;
+      if (eb > E_BYTES) {  // host sizing guarantees this never happens
+        set_err(err, ERRF_BOUNDS);
+        eb = 0;
+      }
+      mbar_arrive_expect_tx(fb, eb + O_BYTES);
+      if (eb) bulk_g2s(ents_sa + s * E_BYTES, ents + (int64_t)t * e_stride + lo, eb, fb);
+      bulk_g2s(offs_sa + s * O_BYTES, offs + (int64_t)t * o_stride + o_lo, O_BYTES, fb);
+    }
+    if (blk != cur_blk) {
+      cur_blk = blk;
+      float q[4][3];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t j = blk * BW + lane * 4 + c;
+        cin[c] = j < colsA;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[c][a] = cin[c] ? -__ldg(g.Q + 3 * j + a) : 0.f;
+      }
+      nqx0 = make_float2(q[0][0], q[1][0]);
+      nqx1 = make_float2(q[2][0], q[3][0]);
+      nqy0 = make_float2(q[0][1], q[1][1]);
+      nqy1 = make_float2(q[2][1], q[3][1]);
+      nqz0 = make_float2(q[0][2], q[1][2]);
+      nqz1 = make_float2(q[2][2], q[3][2]);
+    }
+    const int64_t j0 = blk * BW + lane * 4;
+    const uint32_t dst = tiles_sa + s * TILE_BYTES + lane * 16;
+    const int64_t i0 = (int64_t)t * TILE;
+#pragma unroll 2
+    for (int uu = 0; uu < ROWS; ++uu) {
+      const int r = pw + GEN_WARPS * uu;
+      if (r >= TILE) break;  // uniform
+      const int src = uu & 31;
+      const float px = __shfl_sync(0xffffffffu, uu < 32 ? pa[0] : pb[0], src);
+      const float py = __shfl_sync(0xffffffffu, uu < 32 ? pa[1] : pb[1], src);
+      const float pz = __shfl_sync(0xffffffffu, uu < 32 ? pa[2] : pb[2], src);
+      const float2 px2 = make_float2(px, px), py2 = make_float2(py, py), pz2 = make_float2(pz, pz);
+      const float2 dx0 = __fadd2_rn(px2, nqx0), dx1 = __fadd2_rn(px2, nqx1);
+      const float2 dy0 = __fadd2_rn(py2, nqy0), dy1 = __fadd2_rn(py2, nqy1);
+      const float2 dz0 = __fadd2_rn(pz2, nqz0), dz1 = __fadd2_rn(pz2, nqz1);
+      float2 a0 = __ffma2_rn(dx0, dx0, __ffma2_rn(dy0, dy0, __fmul2_rn(dz0, dz0)));
+      float2 a1 = __ffma2_rn(dx1, dx1, __ffma2_rn(dy1, dy1, __fmul2_rn(dz1, dz1)));
+      a0 = __fmul2_rn(a0, nc2);
+      a1 = __fmul2_rn(a1, nc2);
+      const int64_t i = i0 + r;
+      const bool rin = i < rowsA;
+      float v0 = (rin && cin[0]) ? ex2_approx(a0.x) : 0.f;
+      float v1 = (rin && cin[1]) ? ex2_approx(a0.y) : 0.f;
+      float v2 = (rin && cin[2]) ? ex2_approx(a1.x) : 0.f;
+      float v3 = (rin && cin[3]) ? ex2_approx(a1.y) : 0.f;
+      if (g.shift != 0.f && i >= j0 && i < j0 + 4) {  // the diagonal crosses this slot
+        if (i == j0 && cin[0]) v0 += g.shift;
+        if (i == j0 + 1 && cin[1]) v1 += g.shift;
+        if (i == j0 + 2 && cin[2]) v2 += g.shift;
+        if (i == j0 + 3 && cin[3]) v3 += g.shift;
+      }
+      asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};" ::"r"(dst + r * (uint32_t)(BW * 4)), "f"(v0), "f"(v1),
+                   "f"(v2), "f"(v3)
+                   : "memory");
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(fb);
+    if (u + 1 < u1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        pa[a] = na[a];
+        pb[a] = nb[a];
+      }
+    }
+  }
+}
+
+template <typename T, int TILE, int NB, int STAGES, bool GEN = false>
 __global__ void __launch_bounds__(16 * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
                      const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
                      int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
-                     T* __restrict__ St, int64_t ldSt, T scale, int* err) {
+                     T* __restrict__ St, int64_t ldSt, T scale, int* err, KGen gen) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int BW = 32 * VEC;  // columns of A per block
   constexpr uint32_t TILE_BYTES = TILE * BW * sizeof(T);
@@ -152,14 +287,18 @@ __global__ void __launch_bounds__(16 * 32, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
+      mbar_init(full0 + 8 * s, GEN ? 1 + GEN_WARPS : 1);
       mbar_init(empty0 + 8 * s, njobs);
     }
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == njobs) {  // ---- producer
+  if (GEN && warp >= njobs) {  // ---- producers that compute the tile: A_ij = K(p_i, q_j)
+    if constexpr (GEN) gen_producer<TILE, STAGES>(gen, rowsA, colsA, ents, offs, e_stride, o_stride, c_lo, c_hi,
+                                                  E_BYTES, O_BYTES, tiles_sa, ents_sa, smem_u32(sh_o), full0,
+                                                  empty0, o_lo, warp - njobs, lane, rg.u0, rg.u1, err);
+  } else if (warp == njobs) {  // ---- producer
     if (lane == 0 && rg.u1 > rg.u0) {
       tma_prefetch_desc(&tmA);
       int k = 0;
@@ -574,7 +713,8 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
     auto kern = sjlt_cols_kernel<T, TILE, NB_COLS, STAGES>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride,
-                                                rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err);
+                                                rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err,
+                                                KGen{});
     note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
@@ -610,6 +750,36 @@ int launch_rows(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
   return SK_OK;
 }
 
+template <int STAGES>
+int launch_cols_gen(sk_op* h, const KGen& g, int64_t n, int64_t m, const TiledCcs& C, int c_lo, int c_hi,
+                    float scale, float* S, int64_t ldS, cudaStream_t s) {
+  constexpr int TILE = SJLT_TILE_F32, BW = 128;
+  JLS_CHECK(zero_columns(S, ldS, m, c_lo, c_hi, s));
+  const size_t tile_b = (size_t)TILE * BW * sizeof(float);
+  const size_t o_max = (GEN_JOBS * NB_COLS + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
+  const long fit = blocks_that_fit<STAGES>(tile_b, o_max, e_blk);
+  if (fit < 1) return SK_ERR_UNSUPPORTED;
+  const int64_t nblk = (m + BW - 1) / BW;  // blocks of output rows; see launch_cols
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
+  CUtensorMap unused{};
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, GEN_JOBS * NB_COLS)) {
+    const Jobs J = plan_jobs(rg.hi - rg.lo, GEN_JOBS);
+    const uint32_t e_bytes = (uint32_t)(e_blk * rg.nblk);
+    const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
+    const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
+    if ((long)smem > SMEM_MAX) return SK_ERR_UNSUPPORTED;
+    auto kern = sjlt_cols_kernel<float, TILE, NB_COLS, STAGES, true>;
+    JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, (J.njobs + GEN_WARPS) * 32, smem, s>>>(unused, n, m, C.ents, C.offs, C.e_stride, C.o_stride,
+                                                        rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, S, ldS, scale,
+                                                        h->d_err, g);
+    note_launch();
+    JLS_CHECK_CUDA(cudaGetLastError());
+  }
+  return SK_OK;
+}
+
 // Three stages when one block's entries fit beside them, else two.
 template <typename T, int TILE>
 int launch_cols_any(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
@@ -632,6 +802,22 @@ int launch_rows_any(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, i
 }
 
 }  // namespace
+
+int sjlt_kernel_apply(sk_op* h, const float* P, int64_t n, const float* Q, int64_t m, double hbw, double shift,
+                      double scale, float* S, int64_t ldS, cudaStream_t s) {
+  JLS_CHECK(build_ccs(h, 0, s));
+  const TiledCcs& C = h->ccs[0];
+  KGen g;
+  g.P = P;
+  g.Q = Q;
+  g.c2 = (float)(1.4426950408889634 / (2.0 * hbw * hbw));  // log2(e) / (2 h^2)
+  g.shift = (float)shift;
+  const size_t tile_b = (size_t)SJLT_TILE_F32 * 512, o_max = (GEN_JOBS * NB_COLS + 8) * 4;
+  const size_t e_blk = (size_t)h->alpha * SJLT_TILE_F32 * ENTRY_BYTES;
+  if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
+    return launch_cols_gen<3>(h, g, n, m, C, 0, h->d_total, (float)scale, S, ldS, s);
+  return launch_cols_gen<2>(h, g, n, m, C, 0, h->d_total, (float)scale, S, ldS, s);
+}
 
 int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
                void* St, int64_t ldSt, cudaStream_t s) {

@@ -46,7 +46,8 @@ SK_BOTH = 3
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
-           "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_dims", "sketch_export",
+           "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
+           "sketch_kernel_adjoint", "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_launch_count", "sketch_srht_route", "sketch_destroy",
            "sketch_strerror"]
 
@@ -88,6 +89,8 @@ def lib() -> ctypes.CDLL:
         "sketch_project_norms_noalloc": (i32, [vp, i64, i32, vp, i64, i64, i32, i32, vp, i64, dbl, dbl, P(i32),
                                                P(dbl), P(dbl), vp]),
         "kernel_matrix": (i32, [P(SkMatrix), vp, i64, vp]),
+        "sketch_kernel_apply": (i32, [vp, vp, i64, vp, dbl, dbl, vp, i64, vp]),
+        "sketch_kernel_adjoint": (i32, [vp, vp, dbl, vp, i64, vp, vp, vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
         "sketch_device_status": (i32, [vp, vp]),
@@ -238,6 +241,30 @@ def sketch_project_norms_noalloc(Q, S_tilde, S_hat, eps_rel: float, eps_abs: flo
 def kernel_matrix(gen: SkMatrix, A, stream=None) -> None:
     _check_2d(A, "A")
     _check(lib().kernel_matrix(ctypes.byref(gen), A.data_ptr(), A.stride(0), _stream(stream)), "kernel_matrix")
+
+
+def _check_points(t, name):
+    import torch
+    if t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous() or not t.is_cuda or t.dtype != torch.float32:
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape (m, 3)")
+
+
+def sketch_kernel_apply(h, X, Y, h_bw: float, S, shift: float = 0.0, stream=None) -> None:
+    """S = K(X, Y; h) R (+ shift on the diagonal), K never formed (SJLT handles, FP32)."""
+    _check_points(X, "X")
+    _check_points(Y, "Y")
+    _check_2d(S, "S")
+    _check(lib().sketch_kernel_apply(h, X.data_ptr(), X.shape[0], Y.data_ptr(), float(h_bw), float(shift),
+                                     S.data_ptr(), S.stride(0), _stream(stream)), "sketch_kernel_apply")
+
+
+def sketch_kernel_adjoint(h, X, h_bw: float, dS, dX, dh, stream=None) -> None:
+    """dX (n x 3) and dh (one float64 on the device) of <dS, K(X, X; h) R>."""
+    _check_points(X, "X")
+    _check_points(dX, "dX")
+    _check_2d(dS, "dS")
+    _check(lib().sketch_kernel_adjoint(h, X.data_ptr(), float(h_bw), dS.data_ptr(), dS.stride(0), dX.data_ptr(),
+                                       dh.data_ptr(), _stream(stream)), "sketch_kernel_adjoint")
 
 
 def sketch_dims(h) -> dict:
