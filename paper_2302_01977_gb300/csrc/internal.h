@@ -58,7 +58,25 @@ struct KGen {
   float shift = 0.f;
 };
 constexpr int GEN_WARPS = 3;   // tile-computing warps per CTA
-constexpr int GEN_JOBS = 13;   // consumer warps per CTA beside them (16 warps in all)
+// Warps per CTA of the SJLT apply kernels and output columns per consumer warp
+// (the accumulators of SJLT_NB columns, 4 values each, live in registers).  The
+// consumers wait on shared-memory loads, so more warps with fewer columns each
+// hide more latency; measured on GB300 (n = 32768, d = 256, S / S' ms):
+// 16 x 20: 1.66 / 1.27, 20 x 16: 1.54 / 1.13, 24 x 12: 1.42 / 1.03,
+// 28 x 10: 1.36 / 0.96, 32 x 9: 1.40 / 0.94 (72 registers per thread at 28).
+#ifndef SJLT_WARPS_OVERRIDE
+constexpr int SJLT_WARPS = 28;
+constexpr int SJLT_NB = 10;
+#else
+constexpr int SJLT_WARPS = SJLT_WARPS_OVERRIDE;
+constexpr int SJLT_NB = SJLT_NB_OVERRIDE;
+#endif
+// The tile-computing kernel keeps 16 warps: its producers need registers for
+// the points and the exponentials, and 28 warps measured slower (165 vs 141 ms
+// for the n = 262144 forward).
+constexpr int GEN_CTA_WARPS = 16;
+constexpr int GEN_JOBS = GEN_CTA_WARPS - GEN_WARPS;      // consumer warps beside the tile-computing ones
+constexpr int GEN_NB = (256 + GEN_JOBS - 1) / GEN_JOBS;  // d = 256 in one launch
 
 struct Basis {                // orthonormal basis Q of earlier sketch columns
   void* Q = nullptr;          // rows x d_max, row-major (ld = d_max), dtype

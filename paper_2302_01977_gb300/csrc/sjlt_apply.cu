@@ -19,8 +19,9 @@
 //    column, the warp walks them column by column with compile-time
 //    accumulator indices.  Each entry is one broadcast 16-byte shared load
 //    (byte offset + sign), one 32-bit add for the address, one data load and
-//    two paired FP32 FMAs (FFMA2).  Each CTA has 16 warps (4 per SM
-//    sub-partition) so that every thread can hold 128 registers.
+//    two paired FP32 FMAs (FFMA2).  The chain shared load -> shared load ->
+//    FMA is latency-bound, so a CTA runs SJLT_WARPS = 28 warps (7 per SM
+//    sub-partition, 72 registers each) with SJLT_NB = 10 columns per warp.
 //  * S' (cols kernel): lanes own VEC consecutive columns of A (one 16-byte
 //    vector).  Tiles of TILE rows x 32*VEC columns arrive by TMA into a dense
 //    layout; an entry makes each lane read one 16-byte vector of row r
@@ -261,7 +262,7 @@ __device__ __forceinline__ void gen_producer(const KGen& g, int64_t rowsA, int64
 }
 
 template <typename T, int TILE, int NB, int STAGES, bool GEN = false>
-__global__ void __launch_bounds__(16 * 32, 1)
+__global__ void __launch_bounds__((GEN ? GEN_CTA_WARPS : SJLT_WARPS) * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
                      const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
                      int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
@@ -428,7 +429,7 @@ struct RowsAcc<double> {
 };
 
 template <typename T, int TILE, int NB, int STAGES>
-__global__ void __launch_bounds__(16 * 32, 1)
+__global__ void __launch_bounds__(SJLT_WARPS * 32, 1)
     sjlt_rows_kernel(const T* __restrict__ A, int64_t lda, int64_t rowsA, int64_t colsA,
                      const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
                      int64_t o_stride, int c_lo, int c_hi, int nbw, int njobs, uint32_t E_BYTES,
@@ -613,15 +614,16 @@ int num_sms() {
 
 namespace {
 
-// 16 warps per CTA (4 per SM sub-partition, 128 registers each): the cols
-// kernel runs 15 consumer warps + 1 TMA producer, the rows kernel 14 consumer
-// warps + NPROD = 2 cp.async producers.  A consumer warp owns <= NB columns.
-constexpr int COLS_JOBS = 15;
-constexpr int ROWS_JOBS = 16 - NPROD;
-constexpr int NB_COLS = 20;
+// SJLT_WARPS warps per CTA: the cols kernel runs SJLT_WARPS - 1 consumer warps
+// + 1 TMA producer, the rows kernel SJLT_WARPS - NPROD consumer warps + NPROD
+// cp.async producers, the tile-computing cols kernel GEN_JOBS consumers +
+// GEN_WARPS producers.  A consumer warp owns <= NB columns.
+constexpr int COLS_JOBS = SJLT_WARPS - 1;
+constexpr int ROWS_JOBS = SJLT_WARPS - NPROD;
+constexpr int NB_COLS = SJLT_NB;
 template <typename T>
 constexpr int nb_rows() {
-  return sizeof(T) == 4 ? 20 : 10;
+  return sizeof(T) == 4 ? SJLT_NB : SJLT_NB / 2;
 }
 constexpr size_t ENTRY_BYTES = sizeof(uint4);
 constexpr long SMEM_MAX = 227 * 1024;
@@ -756,20 +758,20 @@ int launch_cols_gen(sk_op* h, const KGen& g, int64_t n, int64_t m, const TiledCc
   constexpr int TILE = SJLT_TILE_F32, BW = 128;
   JLS_CHECK(zero_columns(S, ldS, m, c_lo, c_hi, s));
   const size_t tile_b = (size_t)TILE * BW * sizeof(float);
-  const size_t o_max = (GEN_JOBS * NB_COLS + 8) * 4;
+  const size_t o_max = (GEN_JOBS * GEN_NB + 8) * 4;
   const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
   const long fit = blocks_that_fit<STAGES>(tile_b, o_max, e_blk);
   if (fit < 1) return SK_ERR_UNSUPPORTED;
   const int64_t nblk = (m + BW - 1) / BW;  // blocks of output rows; see launch_cols
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), nblk));
   CUtensorMap unused{};
-  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, GEN_JOBS * NB_COLS)) {
+  for (const Range& rg : plan_ranges(h, c_lo, c_hi, (int)fit, GEN_JOBS * GEN_NB)) {
     const Jobs J = plan_jobs(rg.hi - rg.lo, GEN_JOBS);
     const uint32_t e_bytes = (uint32_t)(e_blk * rg.nblk);
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
     const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
     if ((long)smem > SMEM_MAX) return SK_ERR_UNSUPPORTED;
-    auto kern = sjlt_cols_kernel<float, TILE, NB_COLS, STAGES, true>;
+    auto kern = sjlt_cols_kernel<float, TILE, GEN_NB, STAGES, true>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, (J.njobs + GEN_WARPS) * 32, smem, s>>>(unused, n, m, C.ents, C.offs, C.e_stride, C.o_stride,
                                                         rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, S, ldS, scale,
@@ -812,7 +814,7 @@ int sjlt_kernel_apply(sk_op* h, const float* P, int64_t n, const float* Q, int64
   g.Q = Q;
   g.c2 = (float)(1.4426950408889634 / (2.0 * hbw * hbw));  // log2(e) / (2 h^2)
   g.shift = (float)shift;
-  const size_t tile_b = (size_t)SJLT_TILE_F32 * 512, o_max = (GEN_JOBS * NB_COLS + 8) * 4;
+  const size_t tile_b = (size_t)SJLT_TILE_F32 * 512, o_max = (GEN_JOBS * GEN_NB + 8) * 4;
   const size_t e_blk = (size_t)h->alpha * SJLT_TILE_F32 * ENTRY_BYTES;
   if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
     return launch_cols_gen<3>(h, g, n, m, C, 0, h->d_total, (float)scale, S, ldS, s);
