@@ -570,6 +570,123 @@ def run_differentiation(args):
     print(json.dumps(line))
 
 
+BATCH = dict(name="batch_kernel_fp32_1024", count=1024, n_lo=256, n_hi=4096, h_lo=0.05, h_hi=0.5,
+             d0=(64, 128, 256), dd=32, alpha=4, rounds=3, seed=20230203 + 3)
+
+
+def run_batching(args):
+    """1024 independent FP32 Gaussian kernel matrices A_i = K(X_i, X_i; h_i),
+    n_i uniform over multiples of 64 in [256, 4096], h_i uniform in [0.05, 0.5],
+    points uniform in [0,1]^3; block SJLT (alpha = 4) with d0_i in {64, 128, 256}
+    and Delta-d = 32.  One batched launch sketches Algorithm 1's first d0_i + 32
+    columns of every instance; then increments of 32 columns run as replays of a
+    captured CUDA graph of the same launch.  value = bytes of all A_i streamed per
+    run / run time (A_i is symmetric, so S_i = A_i R_i = A_i^T R_i)."""
+    import numpy as np
+    import torch
+
+    from oracle import sketch as osk
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = BATCH
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(w["seed"])
+    ns = 64 * rng.integers(w["n_lo"] // 64, w["n_hi"] // 64 + 1, size=w["count"])
+    hs = rng.uniform(w["h_lo"], w["h_hi"], size=w["count"])
+    d0s = rng.choice(w["d0"], size=w["count"])
+    dd, R = w["dd"], w["rounds"]
+    ops, As, Sts = [], [], []
+    for i in range(w["count"]):
+        n = int(ns[i])
+        X = torch.from_numpy(inputs.points(n, seed=w["seed"] + 17 * i)).cuda()
+        A = torch.empty((n, n), device="cuda")
+        jl.kernel_matrix(jl.generator(X, X, float(hs[i])), A)
+        # Algorithm 1: the first operator is one JL(d0 + Delta-d), then R increments of Delta-d
+        op = jl.Sketch("sjlt_block", n, int(d0s[i]) + dd, w["alpha"], w["seed"] + i,
+                       d_max=int(d0s[i]) + (R + 1) * dd)
+        for _ in range(R):
+            jl.sketch_increment(op.h, dd)
+        ops.append(op)
+        As.append(A)
+        Sts.append(torch.empty((n, int(d0s[i]) + (R + 1) * dd), device="cuda"))
+    bytes_a = float(sum(int(n) * int(n) * 4 for n in ns))
+    items = [(op.h, A, St, 0, int(d0) + dd) for op, A, St, d0 in zip(ops, As, Sts, d0s)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = jl.Batch(items)
+    t_create = time.perf_counter() - t0
+    info = B.info()
+    clocks = Clocks(0)
+    clocks.start()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    l0 = jl.sketch_launch_count()
+    t_first = timed(B.run, args.steps)
+    launches_first = (jl.sketch_launch_count() - l0) / (args.steps + args.warmup)
+    B.status()
+    # parity on a seeded sample of instances (first sketch)
+    errs = []
+    for i in rng.choice(w["count"], 4, replace=False):
+        Rd = jl.sketch_export(ops[i].h, dense=True)["R"]
+        hi = int(d0s[i]) + dd
+        ref = osk.apply(As[i].double().cpu().numpy(), Rd)[1][:, :hi]
+        got = Sts[i][:, :hi].double().cpu().numpy()
+        errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    # increments: a captured graph of the batched launch, replayed with new column ranges
+    first_info = info
+    B.set(None, [int(d0) + dd for d0 in d0s], [int(d0) + 2 * dd for d0 in d0s])
+    B.tune()  # the shape for Delta-d = 32 columns
+    info = B.info()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        B.run(stream=s)
+    s.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        B.run(stream=s)
+    inc_ms = []
+    for r in range(1, R + 1):
+        torch.cuda.synchronize()
+        B.set(None, [int(d0) + r * dd for d0 in d0s], [int(d0) + (r + 1) * dd for d0 in d0s])
+        inc_ms.append(timed(g.replay, args.steps))
+    B.status()
+    ck = clocks.stop()
+    hbm, _, _, peak_kind = peaks()
+    t_inc = statistics.median(inc_ms)
+    line = {"metric": METRIC, "value": round(bytes_a / t_first / 1e6, 1), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_first, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+            "config": {"workload": w["name"], "instances": w["count"], "n_range": [w["n_lo"], w["n_hi"]],
+                       "h_range": [w["h_lo"], w["h_hi"]], "d0": list(w["d0"]), "dd": dd, "alpha": w["alpha"],
+                       "bytes_of_A": bytes_a, "l2": "inputs larger than L2 (24 GB of A), no flush"},
+            "first_sketch_ms": round(t_first, 3), "first_sketch_pct_hbm": round(100 * bytes_a / t_first / 1e6 / hbm, 1),
+            "increment_graph_replay_ms": round(t_inc, 3),
+            "increment_gbs": round(bytes_a / t_inc / 1e6, 1),
+            "increment_pct_hbm": round(100 * bytes_a / t_inc / 1e6 / hbm, 1),
+            "launches_per_run": launches_first, "autotune_first": first_info, "autotune_increment": info,
+            "batch_create_s": round(t_create, 2),
+            "rel_err_vs_oracle_sample": [float(f"{e:.3e}") for e in errs], "peak_source": peak_kind,
+            "gpu_launches": int(launches_first * args.steps), "clocks": ck}
+    B.close()
+    for op in ops:
+        op.close()
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,7 +701,7 @@ def main():
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
     ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536",
-                                           "kernel_sketch_grad_n262144"],
+                                           "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",
@@ -598,6 +715,8 @@ def main():
         run_precision(args)
     elif args.workload == "kernel_sketch_grad_n262144":
         run_differentiation(args)
+    elif args.workload == "batch_kernel_fp32_1024":
+        run_batching(args)
     else:
         run_ours(args)
 

@@ -250,6 +250,86 @@ int sketch_kernel_apply(sk_handle h, const float* X, int64_t m, const float* Y, 
 int sketch_kernel_adjoint(sk_handle h, const float* X, double h_bw, const float* dS, int64_t ldS,
                           float* dX, double* dh, void* stream);
 
+/* ---- batches: many independent SJLT sketches in one launch ------------------ */
+
+typedef struct sk_batch* sk_batch_handle;
+
+/* One instance of a batch: S'_i = A_i^T R_i for columns [c_lo, c_hi) of R_i. */
+typedef struct sk_batch_item {
+  sk_handle op;        /* SJLT operator R_i (SK_SJLT_BLOCK or SK_SJLT_GRAPH), n_i rows      */
+  const float* A;      /* device FP32, rows x cols, row-major, 16-byte aligned, ld*4 % 16 == 0 */
+  int64_t rows, cols;  /* rows == n_i                                                       */
+  int64_t ld;          /* leading dimension of A (elements), >= cols                          */
+  float* St;           /* device FP32, cols x d_total(R_i), leading dimension ldSt          */
+  int64_t ldSt;
+  int32_t c_lo, c_hi;  /* columns of R_i to sketch, 0 <= c_lo < c_hi <= d_total(R_i)          */
+  double scale;        /* multiplies the signed sums; 0 = the operator's 1/sqrt(alpha*blocks) */
+} sk_batch_item;
+
+/*
+ * sketch_batch_create -- prepare a batch of independent, uneven S' = A^T R
+ * products (Sec. 6.3) to run as ONE persistent kernel launch (for example the
+ * sketches of Algorithm 1's first d0 + Delta-d columns, then of each Delta-d
+ * increment, for many kernel matrices; a symmetric A_i gives S_i = S'_i).
+ * Builds each operator's tiled CCS for its current d_total, encodes a TMA
+ * tensor map per A_i, copies the item table to the device, and picks the
+ * kernel shape (warps per CTA x columns per warp) by timing the batch once per
+ * shape (the autotuner; it writes the outputs).  Synchronizes `stream`.  The
+ * operators must not be incremented or applied to other data of a different
+ * d_total while the batch exists (their CCS arrays are referenced).  Every
+ * range c_hi - c_lo must be at most 300 columns (the widest shape's 15 x 20).
+ * Errors: INVALID_ARG, ALIGN, NOMEM, UNSUPPORTED, DEVICE.
+ */
+int sketch_batch_create(sk_batch_handle* out, const sk_batch_item* items, int32_t count, void* stream);
+
+/*
+ * sketch_batch_set -- host-only update of the next run: per instance an active
+ * flag and a column range (host arrays of `count` values; NULL keeps the
+ * current values).  Inactive instances are skipped.  Writes the pinned host
+ * mirror of the item table that sketch_batch_run copies to the device, so call
+ * it only when no earlier run is still pending on the GPU.
+ * Errors: INVALID_ARG (range outside d_total), UNSUPPORTED (range too wide).
+ */
+int sketch_batch_set(sk_batch_handle b, const int32_t* active, const int32_t* c_lo, const int32_t* c_hi);
+
+/*
+ * sketch_batch_run -- copy the item table to the device, zero the columns
+ * [c_lo, c_hi) of every active output, and run the batched sketch: one
+ * persistent launch whose CTAs (one per SM) stream equal shares of all active
+ * instances' (block, tile) units.  Asynchronous, allocates nothing and takes
+ * no host synchronization, so it can be captured in a CUDA graph; a replay
+ * uses the table sketch_batch_set last wrote, with the shared-memory staging
+ * sized at capture: ranges set later must touch no more blocks of their
+ * operators than the captured ones did (otherwise the kernel sets the device
+ * flag that sketch_batch_status reports).  Errors: INVALID_ARG, DEVICE.
+ */
+int sketch_batch_run(sk_batch_handle b, void* stream);
+
+/*
+ * sketch_batch_tune -- rerun the autotuner on the ranges sketch_batch_set last
+ * wrote (each shape: one warm-up and three timed runs on `stream`, which write
+ * the outputs) and keep the fastest shape for later runs; e.g. once for the
+ * first sketch and once for the Delta-d increments, before capturing a graph
+ * of the latter.  Synchronizes `stream`; not capturable.  The paper has no
+ * counterpart.  Errors: UNSUPPORTED (no shape takes the ranges), DEVICE.
+ */
+int sketch_batch_tune(sk_batch_handle b, void* stream);
+
+/* sketch_batch_info -- the chosen shape, the active units of the next run and
+ * the autotuner's measured ms per run for each shape, in the order 24 x 13,
+ * 20 x 16, 16 x 20, 32 x 2 warps x columns (-1 = not eligible; `tuned_ms`
+ * holds 4 floats).  Any pointer may be NULL.  The paper has no counterpart. */
+int sketch_batch_info(sk_batch_handle b, int32_t* warps, int32_t* cols_per_warp, int64_t* units,
+                      float* tuned_ms);
+
+/* sketch_batch_status -- synchronize `stream`, report and clear the batch's
+ * device error flag: SK_OK, SK_ERR_TIMEOUT or SK_ERR_DEVICE. */
+int sketch_batch_status(sk_batch_handle b, void* stream);
+
+/* sketch_batch_destroy -- free the batch (NULL is a no-op); the operators are
+ * not freed. */
+void sketch_batch_destroy(sk_batch_handle b);
+
 /* sketch_dims -- shape of the current operator (host outputs; any may be NULL). */
 int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha,
                 int32_t* blocks);

@@ -3,7 +3,8 @@
 * ``apply(A, R)``: S = A R and S' = A^T R in FP64 (Sec. 6.3: the sketch of the
   rows and of the columns of A; with real A the conjugate transpose is the
   transpose).  The product is the plain definition; numpy's matmul is the
-  library primitive that evaluates it.
+  library primitive that evaluates it.  ``apply_t(A, R)``: S' alone, for
+  rectangular A.
 * ``apply_sjlt_outer(A, cols, signs, scale, d)``: the outer-product form of
   Sec. 6.3 written out: every column A_{:i} is added to or subtracted from the
   solution columns named by row i of R, then the result is scaled once.
@@ -30,6 +31,11 @@ def apply(A: np.ndarray, R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     A = np.asarray(A, dtype=np.float64)
     R = np.asarray(R, dtype=np.float64)
     return A @ R, A.T @ R
+
+
+def apply_t(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """S' = A^T R alone (Sec. 6.3, the sketch of the columns), for A of any shape with rows(A) = rows(R)."""
+    return np.asarray(A, dtype=np.float64).T @ np.asarray(R, dtype=np.float64)
 
 
 def apply_sjlt_outer(A: np.ndarray, cols: np.ndarray, signs: np.ndarray,

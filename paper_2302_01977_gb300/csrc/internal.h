@@ -207,6 +207,7 @@ int num_sms();
 
 // --- jlsketch.cu helpers ---
 void note_launch();  // counts kernel launches (sketch_launch_count)
+double op_scale(const sk_op* h);  // SJLT 1/sqrt(alpha * blocks); SRHT, Gaussian 1/sqrt(d_total)
 int cuda_status(cudaError_t e);
 size_t elem_size(int dtype);
 

@@ -47,7 +47,9 @@ KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": 
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
            "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
-           "sketch_kernel_adjoint", "sketch_dims", "sketch_export",
+           "sketch_kernel_adjoint", "sketch_batch_create", "sketch_batch_set", "sketch_batch_run",
+           "sketch_batch_tune",
+           "sketch_batch_info", "sketch_batch_status", "sketch_batch_destroy", "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_launch_count", "sketch_srht_route", "sketch_destroy",
            "sketch_strerror"]
 
@@ -56,6 +58,13 @@ class JLSketchError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         super().__init__(f"{where}: {sketch_strerror(status)} (status {status})")
+
+
+class SkBatchItem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("A", ctypes.c_void_p), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("St", ctypes.c_void_p),
+                ("ldSt", ctypes.c_int64), ("c_lo", ctypes.c_int32), ("c_hi", ctypes.c_int32),
+                ("scale", ctypes.c_double)]
 
 
 class SkMatrix(ctypes.Structure):
@@ -91,6 +100,13 @@ def lib() -> ctypes.CDLL:
         "kernel_matrix": (i32, [P(SkMatrix), vp, i64, vp]),
         "sketch_kernel_apply": (i32, [vp, vp, i64, vp, dbl, dbl, vp, i64, vp]),
         "sketch_kernel_adjoint": (i32, [vp, vp, dbl, vp, i64, vp, vp, vp]),
+        "sketch_batch_create": (i32, [P(vp), P(SkBatchItem), i32, vp]),
+        "sketch_batch_set": (i32, [vp, vp, vp, vp]),
+        "sketch_batch_run": (i32, [vp, vp]),
+        "sketch_batch_tune": (i32, [vp, vp]),
+        "sketch_batch_info": (i32, [vp, P(i32), P(i32), P(i64), P(ctypes.c_float)]),
+        "sketch_batch_status": (i32, [vp, vp]),
+        "sketch_batch_destroy": (None, [vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
         "sketch_device_status": (i32, [vp, vp]),
@@ -265,6 +281,75 @@ def sketch_kernel_adjoint(h, X, h_bw: float, dS, dX, dh, stream=None) -> None:
     _check_2d(dS, "dS")
     _check(lib().sketch_kernel_adjoint(h, X.data_ptr(), float(h_bw), dS.data_ptr(), dS.stride(0), dX.data_ptr(),
                                        dh.data_ptr(), _stream(stream)), "sketch_kernel_adjoint")
+
+
+class Batch:
+    """Many S'_i = A_i^T R_i (columns [c_lo_i, c_hi_i) of SJLT handles) in one persistent launch.
+
+    ``items``: sequence of (op_handle, A, St, c_lo, c_hi) with A and St float32 CUDA tensors.
+    The tensors must outlive the batch.  ``run()`` is asynchronous and capturable in a
+    CUDA graph; ``set(active, c_lo, c_hi)`` changes what the next run (or replay) does.
+    """
+
+    def __init__(self, items, stream=None):
+        arr = (SkBatchItem * len(items))()
+        self._keep = []
+        for k, (op, A, St, lo, hi) in enumerate(items):
+            _check_2d(A, "A")
+            _check_2d(St, "St")
+            self._keep.append((A, St))
+            arr[k] = SkBatchItem(op=op, A=A.data_ptr(), rows=A.shape[0], cols=A.shape[1], ld=A.stride(0),
+                                 St=St.data_ptr(), ldSt=St.stride(0), c_lo=int(lo), c_hi=int(hi), scale=0.0)
+        self.count = len(items)
+        self.b = ctypes.c_void_p()
+        _check(lib().sketch_batch_create(ctypes.byref(self.b), arr, self.count, _stream(stream)),
+               "sketch_batch_create")
+
+    def set(self, active=None, c_lo=None, c_hi=None) -> None:
+        def arr(x):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+            if a.shape != (self.count,):
+                raise ValueError("one value per instance")
+            return a
+        a, lo, hi = arr(active), arr(c_lo), arr(c_hi)
+        p = lambda x: None if x is None else x.ctypes.data  # noqa: E731
+        _check(lib().sketch_batch_set(self.b, p(a), p(lo), p(hi)), "sketch_batch_set")
+
+    def run(self, stream=None) -> None:
+        _check(lib().sketch_batch_run(self.b, _stream(stream)), "sketch_batch_run")
+
+    def tune(self, stream=None) -> None:
+        """Re-pick the kernel shape by timing the current ranges (synchronizes; not capturable)."""
+        _check(lib().sketch_batch_tune(self.b, _stream(stream)), "sketch_batch_tune")
+
+    def info(self) -> dict:
+        w, nb, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        ms = (ctypes.c_float * 4)()
+        _check(lib().sketch_batch_info(self.b, ctypes.byref(w), ctypes.byref(nb), ctypes.byref(u), ms),
+               "sketch_batch_info")
+        return dict(warps=w.value, cols_per_warp=nb.value, units=u.value, tuned_ms=[round(x, 4) for x in ms])
+
+    def status(self, stream=None) -> None:
+        _check(lib().sketch_batch_status(self.b, _stream(stream)), "sketch_batch_status")
+
+    def close(self):
+        if self.b:
+            lib().sketch_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sketch_dims(h) -> dict:
