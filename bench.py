@@ -520,7 +520,10 @@ def run_differentiation(args):
 
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    w = DIFF
+    w = dict(DIFF)
+    if args.points:
+        w["n"] = args.points
+        w["name"] = f"kernel_sketch_grad_n{args.points}"
     n, d = w["n"], w["d"]
     torch.cuda.set_device(0)
     X = torch.from_numpy(inputs.points(n, seed=w["seed"]).astype("float32")).cuda()
@@ -591,7 +594,10 @@ def run_batching(args):
 
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    w = BATCH
+    w = dict(BATCH)
+    if args.instances:
+        w["count"] = args.instances
+        w["name"] = f"batch_kernel_fp32_{args.instances}"
     torch.cuda.set_device(0)
     rng = np.random.default_rng(w["seed"])
     ns = 64 * rng.integers(w["n_lo"] // 64, w["n_hi"] // 64 + 1, size=w["count"])
@@ -704,6 +710,10 @@ def main():
                                            "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
+    ap.add_argument("--points", type=int, default=0,
+                    help="kernel_sketch_grad workload: number of points (default 262144; smaller for captures)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="batch workload: number of instances (default 1024; fewer for captures)")
     ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",
                     help="restrict the step (profiling captures); the benchmark runs all")
     args = ap.parse_args()

@@ -31,11 +31,15 @@ constexpr int F8_KTILE = 128;  // values of K per FP8 scale tile
 // `tile` rows): for tile t, entries[t*e_stride + p] sorted by column (rows
 // ascending inside a column), and offs[t*o_stride + c] = first entry of
 // column c (offs[.. + d_total] = count).  An entry for row r of the tile is a
-// 16-byte record read with one shared-memory load by the apply kernels:
+// 16-byte record:
 //   x = r * CCS_ROW_BYTES   (byte offset of row r in an S' kernel tile)
 //   y, z = the sign as +-1.0 (FP32 tiles: the float twice; FP64 tiles: the
 //          double's low and high words)
 //   w = r * element size    (byte offset of column r in an S kernel tile row)
+// In FP32 tiles x and w also carry the sign in bit 31, so the FP32 kernels
+// read one 32-bit word per entry (a broadcast 4-byte shared load takes one
+// shared-memory wavefront, a 16-byte one two); the FP64 kernels read the
+// whole record.
 constexpr int CCS_ROW_BYTES = 512;  // S' tiles: 128 FP32 or 64 FP64 columns per row
 struct TiledCcs {
   int tile = 0;

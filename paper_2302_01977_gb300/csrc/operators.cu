@@ -175,10 +175,13 @@ __global__ void __launch_bounds__(CCS_THREADS)
           const uint32_t pos = sh_cnt[e & 0x7fffffff]++;
           // {S' offset of row r, sign, sign, S offset of row r}, see TiledCcs
           uint4 rec;
+          const uint32_t neg = e < 0 ? 0x80000000u : 0u;
           rec.x = (uint32_t)r * CCS_ROW_BYTES;
           rec.w = (uint32_t)(r * esize);
-          if (esize == 4) {
-            rec.y = rec.z = (e < 0) ? 0xbf800000u : 0x3f800000u;
+          if (esize == 4) {  // FP32 kernels load one word: offset | sign bit
+            rec.x |= neg;
+            rec.w |= neg;
+            rec.y = rec.z = neg | 0x3f800000u;
           } else {
             rec.y = 0u;
             rec.z = (e < 0) ? 0xbff00000u : 0x3ff00000u;

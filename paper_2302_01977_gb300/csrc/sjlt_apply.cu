@@ -17,9 +17,9 @@
 //  * A consumer warp owns <= NB output columns of R and keeps their sums in
 //    registers for the whole block; because a tile's entries are grouped by
 //    column, the warp walks them column by column with compile-time
-//    accumulator indices.  Each entry is one broadcast 16-byte shared load
-//    (byte offset + sign), one 32-bit add for the address, one data load and
-//    two paired FP32 FMAs (FFMA2).  The chain shared load -> shared load ->
+//    accumulator indices.  Each entry is one broadcast 4-byte shared load
+//    (byte offset | sign bit), one 32-bit add for the address, one data load
+//    and two paired FP32 FMAs (FFMA2).  The chain shared load -> shared load ->
 //    FMA is latency-bound, so a CTA runs SJLT_WARPS = 28 warps (7 per SM
 //    sub-partition, 72 registers each) with SJLT_NB = 10 columns per warp.
 //  * S' (cols kernel): lanes own VEC consecutive columns of A (one 16-byte
@@ -290,12 +290,12 @@ __global__ void __launch_bounds__((GEN ? GEN_CTA_WARPS : SJLT_WARPS) * 32, 1)
               const uint32_t e = O[cw0 + b + 1];
               uint32_t ea = ebase + p * 16;
               for (; p + 1 < e; p += 2, ea += 32) {
-                const uint4 r0 = lds_u4(ea), r1 = lds_u4(ea + 16);
+                const auto r0 = CcsRec<T>::cols(ea), r1 = CcsRec<T>::cols(ea + 16);
                 acc[b].add(xaddr, r0);
                 acc[b].add(xaddr, r1);
               }
               if (p < e) {
-                acc[b].add(xaddr, lds_u4(ea));
+                acc[b].add(xaddr, CcsRec<T>::cols(ea));
                 ++p;
               }
             }
@@ -322,11 +322,13 @@ template <>
 struct RowsAcc<float> {
   float2 a, b;  // rows (q0, q1), (q2, q3)
   __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
+  // w: the record's S word, column offset | sign bit
   template <uint32_t STEP>
-  __device__ __forceinline__ void add(uint32_t raddr, const uint4& r) {
-    const uint32_t x = raddr + r.w;
+  __device__ __forceinline__ void add(uint32_t raddr, uint32_t w) {
+    const uint32_t x = raddr + (w & 0x7fffffffu);
     const float v0 = lds_f1(x), v1 = lds_f1(x + STEP), v2 = lds_f1(x + 2 * STEP), v3 = lds_f1(x + 3 * STEP);
-    const float2 s = f2(__uint_as_float(r.y), __uint_as_float(r.z));
+    const float sg = __uint_as_float((w & 0x80000000u) | 0x3f800000u);
+    const float2 s = f2(sg, sg);
     a = __ffma2_rn(f2(v0, v1), s, a);
     b = __ffma2_rn(f2(v2, v3), s, b);
   }
@@ -485,12 +487,12 @@ __global__ void __launch_bounds__(SJLT_WARPS * 32, 1)
               const uint32_t e = O[cw0 + b + 1];
               uint32_t ea = ebase + p * 16;
               for (; p + 1 < e; p += 2, ea += 32) {
-                const uint4 r0 = lds_u4(ea), r1 = lds_u4(ea + 16);
+                const auto r0 = CcsRec<T>::rows(ea), r1 = CcsRec<T>::rows(ea + 16);
                 acc[b].template add<ROW_STEP>(raddr, r0);
                 acc[b].template add<ROW_STEP>(raddr, r1);
               }
               if (p < e) {
-                acc[b].template add<ROW_STEP>(raddr, lds_u4(ea));
+                acc[b].template add<ROW_STEP>(raddr, CcsRec<T>::rows(ea));
                 ++p;
               }
             }

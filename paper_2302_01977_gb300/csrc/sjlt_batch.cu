@@ -182,12 +182,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
             const uint32_t e = O[o_cw0 + b + 1];
             uint32_t ea = ebase + p * 16;
             for (; p + 1 < e; p += 2, ea += 32) {
-              const uint4 r0 = lds_u4(ea), r1 = lds_u4(ea + 16);
+              const uint32_t r0 = CcsRec<float>::cols(ea), r1 = CcsRec<float>::cols(ea + 16);
               acc[b].add(xaddr, r0);
               acc[b].add(xaddr, r1);
             }
             if (p < e) {
-              acc[b].add(xaddr, lds_u4(ea));
+              acc[b].add(xaddr, CcsRec<float>::cols(ea));
               ++p;
             }
           }

@@ -63,6 +63,21 @@ __device__ __forceinline__ SplitK cta_range(int64_t units) {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double sign_d(const uint4& r) { return __hiloint2double((int)r.z, (int)r.y); }
 
+// What the kernels load of an entry record at shared address ea (see TiledCcs):
+// FP32 tiles one word (S': x, S: w), FP64 tiles the whole record.
+template <typename T>
+struct CcsRec;
+template <>
+struct CcsRec<float> {
+  __device__ __forceinline__ static uint32_t cols(uint32_t ea) { return lds_u32(ea); }
+  __device__ __forceinline__ static uint32_t rows(uint32_t ea) { return lds_u32(ea + 12); }
+};
+template <>
+struct CcsRec<double> {
+  __device__ __forceinline__ static uint4 cols(uint32_t ea) { return lds_u4(ea); }
+  __device__ __forceinline__ static uint4 rows(uint32_t ea) { return lds_u4(ea); }
+};
+
 // ---------------------------------------------------------------------------
 // S' = A^T R : lanes over columns of A, TMA-fed.
 // Accumulators per bucket: FP32 -> 2 float2 (the lane's 4 columns),
@@ -73,9 +88,11 @@ template <>
 struct ColsAcc<float> {
   float2 a, b;
   __device__ __forceinline__ void zero() { a = b = make_float2(0.f, 0.f); }
-  __device__ __forceinline__ void add(uint32_t xaddr, const uint4& r) {
-    const float4 v = lds_f4(xaddr + r.x);
-    const float2 s = f2(__uint_as_float(r.y), __uint_as_float(r.z));
+  // x: the record's S' word, row offset | sign bit
+  __device__ __forceinline__ void add(uint32_t xaddr, uint32_t x) {
+    const float4 v = lds_f4(xaddr + (x & 0x7fffffffu));
+    const float sg = __uint_as_float((x & 0x80000000u) | 0x3f800000u);
+    const float2 s = f2(sg, sg);
     a = __ffma2_rn(f2(v.x, v.y), s, a);
     b = __ffma2_rn(f2(v.z, v.w), s, b);
   }
