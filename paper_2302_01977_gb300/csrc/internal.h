@@ -61,7 +61,16 @@ struct KGen {
   float c2 = 0.f;
   float shift = 0.f;
 };
-constexpr int GEN_WARPS = 3;   // tile-computing warps per CTA
+// The matrix-free forward is bound by its tile-computing warps: measured at n =
+// 262144, d = 256 with 16 warps per CTA, 3 producers 137 ms, 4 producers 112 ms
+// (5 of 20 warps 111 ms, with spills); more warps in all only take issue slots
+// from the producers (16 / 20 / 24 / 28 warps with 3 producers: 137 / 146 /
+// 154 / 169 ms).
+#ifndef GEN_WARPS_OVERRIDE
+constexpr int GEN_WARPS = 4;   // tile-computing warps per CTA
+#else
+constexpr int GEN_WARPS = GEN_WARPS_OVERRIDE;
+#endif
 // Warps per CTA of the SJLT apply kernels and output columns per consumer warp
 // (the accumulators of SJLT_NB columns, 4 values each, live in registers).  The
 // consumers wait on shared-memory loads, so more warps with fewer columns each
@@ -75,10 +84,12 @@ constexpr int SJLT_NB = 10;
 constexpr int SJLT_WARPS = SJLT_WARPS_OVERRIDE;
 constexpr int SJLT_NB = SJLT_NB_OVERRIDE;
 #endif
-// The tile-computing kernel keeps 16 warps: its producers need registers for
-// the points and the exponentials, and 28 warps measured slower (165 vs 141 ms
-// for the n = 262144 forward).
+// The tile-computing kernel keeps 16 warps (see GEN_WARPS).
+#ifndef GEN_CTA_WARPS_OVERRIDE
 constexpr int GEN_CTA_WARPS = 16;
+#else
+constexpr int GEN_CTA_WARPS = GEN_CTA_WARPS_OVERRIDE;
+#endif
 constexpr int GEN_JOBS = GEN_CTA_WARPS - GEN_WARPS;      // consumer warps beside the tile-computing ones
 constexpr int GEN_NB = (256 + GEN_JOBS - 1) / GEN_JOBS;  // d = 256 in one launch
 
