@@ -693,6 +693,71 @@ def run_batching(args):
     print(json.dumps(line))
 
 
+COMPLEX = dict(name="complex_helmholtz_fp32_n16384", n=16384, d=256, alpha=4, kappa=20.0, seed=20230203 + 5)
+
+
+def run_complex(args):
+    """S = A R and S' = A* R for a complex Helmholtz-type kernel A_ij =
+    exp(i kappa r_ij) / (1 + kappa r_ij) of 16384 points uniform in [0,1]^3
+    (complex64, 2.1 GB), block SJLT d = 256, alpha = 4.  value = bytes of A / time."""
+    import torch
+
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = COMPLEX
+    n, d = w["n"], w["d"]
+    torch.cuda.set_device(0)
+    X = torch.from_numpy(inputs.points(n, seed=w["seed"])).cuda().double()
+    A = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    for r0 in range(0, n, 2048):  # input generation in row blocks (torch), not timed
+        r = torch.cdist(X[r0:r0 + 2048], X)
+        A[r0:r0 + 2048] = (torch.exp(1j * w["kappa"] * r) / (1.0 + w["kappa"] * r)).to(torch.complex64)
+    del X
+    op = jl.Sketch("sjlt_block", n, d, w["alpha"], w["seed"])
+    S = torch.empty((n, d), dtype=torch.complex64, device="cuda")
+    St = torch.empty_like(S)
+    bytes_a = float(n) * n * 8
+    hbm, _, _, peak_kind = peaks()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    clocks = Clocks(0)
+    clocks.start()
+    l0 = jl.sketch_launch_count()
+    t_s = timed(lambda: jl.sketch_apply(op.h, A, jl.SK_S, S=S))
+    t_st = timed(lambda: jl.sketch_apply(op.h, A, jl.SK_ST, St=St))
+    launches = jl.sketch_launch_count() - l0
+    ck = clocks.stop()
+    jl.sketch_device_status(op.h)
+    sym = float((torch.linalg.norm(St - S.conj()) / torch.linalg.norm(S)).item())  # A symmetric: A* R = conj(A R)
+    op.close()
+    line = {"metric": METRIC, "value": round(bytes_a / t_st / 1e6, 1), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_s + t_st, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 parts)",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": w["name"], "n": n, "d": d, "alpha": w["alpha"], "kappa": w["kappa"],
+                       "l2": "inputs larger than L2 (A = 2.1 GB), no flush"},
+            "S_ms": round(t_s, 4), "St_ms": round(t_st, 4),
+            "S_gbs": round(bytes_a / t_s / 1e6, 1), "St_gbs": round(bytes_a / t_st / 1e6, 1),
+            "pct_hbm_S": round(100 * bytes_a / t_s / 1e6 / hbm, 1),
+            "pct_hbm_St": round(100 * bytes_a / t_st / 1e6 / hbm, 1), "peak_source": peak_kind,
+            "symmetry_rel_diff": float(f"{sym:.3e}"), "gpu_launches": int(launches), "clocks": ck}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -707,7 +772,8 @@ def main():
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
                     help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
     ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536",
-                                           "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024"],
+                                           "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024",
+                                           "complex_helmholtz_fp32_n16384"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--points", type=int, default=0,
@@ -727,6 +793,8 @@ def main():
         run_differentiation(args)
     elif args.workload == "batch_kernel_fp32_1024":
         run_batching(args)
+    elif args.workload == "complex_helmholtz_fp32_n16384":
+        run_complex(args)
     else:
         run_ours(args)
 

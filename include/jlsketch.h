@@ -62,6 +62,10 @@ extern "C" {
 /* ---- element types ------------------------------------------------------ */
 #define SK_F64 1
 #define SK_F32 2
+#define SK_C64 3  /* complex with FP32 real and imaginary parts, interleaved (re, im);
+                     leading dimensions count complex elements.  Explicit A with an
+                     SJLT operator and SK_PREC_NATIVE: S = A R and S' = A* R, the
+                     conjugate transpose of Sec. 6.3 (R is real).               */
 
 /* ---- arithmetic of an apply -------------------------------------------- */
 #define SK_PREC_NATIVE 0  /* F64 data: FP64; F32 data: FP32 on CUDA cores          */
@@ -83,7 +87,7 @@ typedef struct sk_op* sk_handle;
 
 /* An input matrix: explicit, or generated from points (a Gaussian kernel). */
 typedef struct sk_matrix {
-  int32_t dtype;       /* SK_F32 or SK_F64 (also the type of X, Y)                 */
+  int32_t dtype;       /* SK_F32, SK_F64 (also the type of X, Y), or SK_C64 (explicit) */
   int32_t generator;   /* 0: explicit A; 1: A_ij = exp(-|x_i-y_j|^2/(2h^2)) + shift*[i==j] */
   int64_t rows, cols;  /* A is rows x cols                                          */
   const void* A;       /* explicit: device, row-major, 16-byte aligned               */
@@ -132,6 +136,10 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream);
  *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 / SK_PREC_FP8 (F32, SRHT/Gaussian).
  *   S      device, rows x d_total (ldS >= d_total) of A's dtype; used if which & SK_S.
  *   St     device, cols x d_total (ldSt >= d_total);             used if which & SK_ST.
+ *          For SK_C64 data S = A R and S' = A* R are complex (interleaved FP32
+ *          pairs, leading dimensions in complex elements).  S' runs the S'
+ *          kernel over the real view of A and conjugates while writing; S runs
+ *          the S kernel over the real view with R (x) I_2.
  * Asynchronous.  Errors: INVALID_ARG, ALIGN, DTYPE, UNSUPPORTED, NOMEM, DEVICE.
  */
 int sketch_apply(sk_handle h, const sk_matrix* A, int32_t which, int32_t prec,

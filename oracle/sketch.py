@@ -4,7 +4,8 @@
   rows and of the columns of A; with real A the conjugate transpose is the
   transpose).  The product is the plain definition; numpy's matmul is the
   library primitive that evaluates it.  ``apply_t(A, R)``: S' alone, for
-  rectangular A.
+  rectangular A.  ``complex_s``, ``complex_t``, ``apply_complex``: S = A R
+  and S' = A* R (conjugate transpose) for complex A (Sec. 2: A in C^{m x n}).
 * ``apply_sjlt_outer(A, cols, signs, scale, d)``: the outer-product form of
   Sec. 6.3 written out: every column A_{:i} is added to or subtracted from the
   solution columns named by row i of R, then the result is scaled once.
@@ -36,6 +37,21 @@ def apply(A: np.ndarray, R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 def apply_t(A: np.ndarray, R: np.ndarray) -> np.ndarray:
     """S' = A^T R alone (Sec. 6.3, the sketch of the columns), for A of any shape with rows(A) = rows(R)."""
     return np.asarray(A, dtype=np.float64).T @ np.asarray(R, dtype=np.float64)
+
+
+def complex_s(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """S = A R for complex A (m x n) and real R (n x d), in complex128."""
+    return np.asarray(A, dtype=np.complex128) @ np.asarray(R, dtype=np.float64)
+
+
+def complex_t(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """S' = A* R (conjugate transpose, Sec. 6.3 "A* R") for complex A (m x n) and real R (m x d)."""
+    return np.asarray(A, dtype=np.complex128).conj().T @ np.asarray(R, dtype=np.float64)
+
+
+def apply_complex(A: np.ndarray, R: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(A R, A* R) for a square complex A and real R."""
+    return complex_s(A, R), complex_t(A, R)
 
 
 def apply_sjlt_outer(A: np.ndarray, cols: np.ndarray, signs: np.ndarray,

@@ -119,7 +119,9 @@ struct sk_op {
   // SJLT: packed entries [block][n][alpha] = column | (sign < 0) << 31
   int32_t* sjlt_ents = nullptr;
   int sjlt_blocks_cap = 0;
-  jls::TiledCcs ccs[2];        // [0] tile for F32, [1] tile for F64
+  jls::TiledCcs ccs[3];        // [0] tile for F32, [1] tile for F64, [2] R (x) I_2 for complex S = A R
+  int32_t* sjlt_ents2 = nullptr;  // entries of R (x) I_2
+  size_t ents2_bytes = 0;
 
   // SRHT: D signs, sampled columns, sampling state (next counter)
   int8_t* srht_diag = nullptr;
@@ -163,6 +165,7 @@ namespace jls {
 // --- operators.cu ---
 int gen_sjlt_block(sk_op* h, int block, int col_off, int width, cudaStream_t s);
 int build_ccs(sk_op* h, int which_tile, cudaStream_t s);
+int build_ccs_complex(sk_op* h, cudaStream_t s);  // ccs[2]: R (x) I_2
 int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s);
 int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s);  // plane: 0 f32, 1 f64, 2 bf16x2
 int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s);
@@ -175,6 +178,9 @@ int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s);
 // [c_lo, c_hi) of R, writing scale * (signed sums).
 int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale,
                void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
+// the same for an interleaved complex A (SK_C64): S = A R, S' = A* R
+int sjlt_apply_complex(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S,
+                       int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);
 
 // Matrix-free S = K(Q, P; h) R (+ shift on the diagonal) for an SJLT R with n
 // rows (P: n points) and m output rows (Q: m points), FP32, never forming K.

@@ -22,7 +22,7 @@ int cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? SK_ERR_NOMEM : SK_ERR_DEVICE;
 }
 
-size_t elem_size(int dtype) { return dtype == SK_F64 ? 8 : 4; }
+size_t elem_size(int dtype) { return dtype == SK_F64 || dtype == SK_C64 ? 8 : 4; }
 
 double op_scale(const sk_op* h) {
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
@@ -45,7 +45,10 @@ static int check_device() {
 static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, const void* S, int64_t ldS,
                        const void* St, int64_t ldSt) {
   if (!A || which < SK_S || which > SK_BOTH) return SK_ERR_INVALID_ARG;
-  if (A->dtype != SK_F32 && A->dtype != SK_F64) return SK_ERR_DTYPE;
+  if (A->dtype != SK_F32 && A->dtype != SK_F64 && A->dtype != SK_C64) return SK_ERR_DTYPE;
+  if (A->dtype == SK_C64 &&
+      (A->generator || prec != SK_PREC_NATIVE || (h->kind != SK_SJLT_BLOCK && h->kind != SK_SJLT_GRAPH)))
+    return SK_ERR_DTYPE;  // complex data: explicit A, SJLT operators
   if (A->generator) {
     if (A->generator != 1 || A->rows < 1 || A->cols < 1 || !A->X || !A->Y || !(A->h > 0)) return SK_ERR_INVALID_ARG;
   } else {
@@ -128,6 +131,7 @@ static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo,
     which &= ~SK_S;
     if (!which) return SK_OK;
   }
+  if (A->dtype == SK_C64) return sjlt_apply_complex(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
     return sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
@@ -140,7 +144,8 @@ static void free_handle(sk_op* h) {
   void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
                   h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
-                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch, h->ksk_u};
+                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch, h->ksk_u, h->ccs[2].ents,
+                  h->ccs[2].offs, h->sjlt_ents2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->host_norms) cudaFreeHost(h->host_norms);
@@ -300,8 +305,13 @@ int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32
   else
     old_scale = 1.0 / std::sqrt((double)d_old);
   const double factor = op_scale(h) / old_scale;
-  if (which & SK_S) JLS_CHECK(scale_columns(S, A->dtype, A->rows, ldS, 0, d_old, factor, s));
-  if (which & SK_ST) JLS_CHECK(scale_columns(St, A->dtype, A->cols, ldSt, 0, d_old, factor, s));
+  if (A->dtype == SK_C64) {  // complex columns are (re, im) pairs of FP32
+    if (which & SK_S) JLS_CHECK(scale_columns(S, SK_F32, A->rows, 2 * ldS, 0, 2 * d_old, factor, s));
+    if (which & SK_ST) JLS_CHECK(scale_columns(St, SK_F32, A->cols, 2 * ldSt, 0, 2 * d_old, factor, s));
+  } else {
+    if (which & SK_S) JLS_CHECK(scale_columns(S, A->dtype, A->rows, ldS, 0, d_old, factor, s));
+    if (which & SK_ST) JLS_CHECK(scale_columns(St, A->dtype, A->cols, ldSt, 0, d_old, factor, s));
+  }
   return run_apply(h, A, which, prec, d_old, h->d_total, S, ldS, St, ldSt, s);
 }
 

@@ -239,6 +239,78 @@ int build_ccs(sk_op* h, int which_tile, cudaStream_t s) {
   return SK_OK;
 }
 
+// R (x) I_2 for complex data (S = A R of an interleaved complex A): row 2j + t
+// of it carries row j's nonzeros at columns 2c + t with the same signs.
+__global__ void sjlt_expand2_kernel(const int32_t* __restrict__ ents, int64_t n, int alpha, int blocks,
+                                    int32_t* __restrict__ out) {
+  const int64_t total = (int64_t)blocks * n * alpha;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q / (n * alpha), rem = q - b * n * alpha;
+    const int64_t j = rem / alpha, k = rem - j * alpha;
+    const uint32_t e = (uint32_t)ents[q], col = e & 0x7fffffffu, neg = e & 0x80000000u;
+#pragma unroll
+    for (uint32_t t = 0; t < 2; ++t)
+      out[((b * 2 * n) + 2 * j + t) * alpha + k] = (int32_t)((2 * col + t) | neg);
+  }
+}
+
+int build_ccs_complex(sk_op* h, cudaStream_t s) {
+  TiledCcs& C = h->ccs[2];
+  if (C.built_d == h->d_total && C.tile == SJLT_TILE_F32) return SK_OK;
+  const int B = (int)h->blocks.size();
+  if (B > MAX_BLOCKS) return SK_ERR_UNSUPPORTED;
+  const int64_t n2 = 2 * h->n;
+  const int d2 = 2 * h->d_total;
+  const size_t need = (size_t)B * n2 * h->alpha * sizeof(int32_t);
+  if (need > h->ents2_bytes) {
+    if (h->sjlt_ents2) cudaFree(h->sjlt_ents2);
+    h->sjlt_ents2 = nullptr;
+    h->ents2_bytes = 0;
+    JLS_CHECK_CUDA(cudaMalloc(&h->sjlt_ents2, need));
+    h->ents2_bytes = need;
+  }
+  sjlt_expand2_kernel<<<4 * 152, 256, 0, s>>>(h->sjlt_ents, h->n, h->alpha, B, h->sjlt_ents2);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  const int tile = SJLT_TILE_F32;
+  C.tile = tile;
+  C.ntiles = (int)((n2 + tile - 1) / tile);
+  C.e_stride = (int64_t)h->alpha * B * tile;
+  C.o_stride = ((int64_t)d2 + 1 + 3) / 4 * 4;
+  const size_t eb = (size_t)C.e_stride * C.ntiles * sizeof(uint4);
+  const size_t ob = (size_t)C.o_stride * C.ntiles * sizeof(uint32_t);
+  if (eb > C.ents_cap) {
+    if (C.ents) cudaFree(C.ents);
+    C.ents = nullptr;
+    C.ents_cap = 0;
+    JLS_CHECK_CUDA(cudaMalloc(&C.ents, eb));
+    C.ents_cap = eb;
+  }
+  if (ob > C.offs_cap) {
+    if (C.offs) cudaFree(C.offs);
+    C.offs = nullptr;
+    C.offs_cap = 0;
+    JLS_CHECK_CUDA(cudaMalloc(&C.offs, ob));
+    C.offs_cap = ob;
+  }
+  BlockOffsets bo;
+  bo.n = B;
+  int off = 0;
+  for (int b = 0; b < B; ++b) {
+    bo.off[b] = off;
+    off += 2 * h->blocks[b];
+  }
+  bo.off[B] = off;
+  const size_t shm = sizeof(uint32_t) * (d2 + 1);
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(ccs_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  ccs_build_kernel<<<C.ntiles, CCS_THREADS, shm, s>>>(h->sjlt_ents2, n2, h->alpha, bo, d2, tile, 4, C.e_stride,
+                                                      C.o_stride, C.ents, C.offs);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  C.built_d = h->d_total;
+  return SK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // SRHT
 __global__ void srht_diag_kernel(int64_t n, uint64_t seed, int8_t* __restrict__ diag) {

@@ -179,7 +179,10 @@ __device__ __forceinline__ void gen_producer(const KGen& g, int64_t rowsA, int64
   }
 }
 
-template <typename T, int TILE, int NB, int STAGES, bool GEN = false>
+// CPLX: A is the real view of an interleaved complex matrix (2 m real columns
+// for m complex ones); lane quads hold (re, im) of two complex columns, and the
+// flush writes St as complex (row j, column c = (re, -im)): S' = A* R.
+template <typename T, int TILE, int NB, int STAGES, bool GEN = false, bool CPLX = false>
 __global__ void __launch_bounds__((GEN ? GEN_CTA_WARPS : SJLT_WARPS) * 32, 1)
     sjlt_cols_kernel(const __grid_constant__ CUtensorMap tmA, int64_t rowsA, int64_t colsA,
                      const uint4* __restrict__ ents, const uint32_t* __restrict__ offs, int64_t e_stride,
@@ -255,14 +258,30 @@ __global__ void __launch_bounds__((GEN ? GEN_CTA_WARPS : SJLT_WARPS) * 32, 1)
     const uint32_t lane_off = lane * 16;
     int k = 0;
     auto flush = [&](int64_t blk) {
+      if constexpr (CPLX) {
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        const int64_t j = blk * BW + lane * VEC + q;
-        if (j < colsA) {
-          T v[NB];
+        for (int hq = 0; hq < VEC / 2; ++hq) {
+          const int64_t jc = (blk * BW + lane * VEC) / 2 + hq;  // complex column of A = row of S'
+          if (2 * jc < colsA) {
+            T re[NB], im[NB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) v[b] = acc[b].get(q);
-          flush_row<NB>(St + j * ldSt + cw0, v, nb, scale, vec_ok);
+            for (int b = 0; b < NB; ++b) {
+              re[b] = acc[b].get(2 * hq);
+              im[b] = acc[b].get(2 * hq + 1);
+            }
+            flush_row_conj<NB>(St + jc * ldSt + 2 * cw0, re, im, nb, scale);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          const int64_t j = blk * BW + lane * VEC + q;
+          if (j < colsA) {
+            T v[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) v[b] = acc[b].get(q);
+            flush_row<NB>(St + j * ldSt + cw0, v, nb, scale, vec_ok);
+          }
         }
       }
     };
@@ -600,7 +619,7 @@ int zero_columns(T* out, int64_t ld, int64_t rows, int c_lo, int c_hi, cudaStrea
   return SK_OK;
 }
 
-template <typename T, int TILE, int STAGES>
+template <typename T, int TILE, int STAGES, bool CPLX = false>
 int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c_hi, T scale, T* St,
                 int64_t ldSt, cudaStream_t s) {
   constexpr int VEC = 16 / sizeof(T), BW = 32 * VEC;
@@ -616,7 +635,10 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return SK_ERR_ALIGN;
-  JLS_CHECK(zero_columns(St, ldSt, A->cols, c_lo, c_hi, s));
+  if (CPLX)  // St: A->cols / 2 complex rows, ldSt floats; columns [c_lo, c_hi) are (re, im) pairs
+    JLS_CHECK(zero_columns(St, ldSt, A->cols / 2, 2 * c_lo, 2 * c_hi, s));
+  else
+    JLS_CHECK(zero_columns(St, ldSt, A->cols, c_lo, c_hi, s));
   const size_t tile_b = (size_t)TILE * BW * sizeof(T);
   const size_t o_max = (COLS_JOBS * NB_COLS + 8) * 4;
   const size_t e_blk = (size_t)h->alpha * TILE * ENTRY_BYTES;
@@ -632,7 +654,7 @@ int launch_cols(sk_op* h, const sk_matrix* A, const TiledCcs& C, int c_lo, int c
     const uint32_t o_bytes = (uint32_t)((((rg.hi + 1 + 3) & ~3) - (rg.lo & ~3)) * 4);
     const size_t smem = STAGES * (tile_b + e_bytes + o_bytes) + 2 * STAGES * 8;
     if ((long)smem > SMEM_MAX) return SK_ERR_UNSUPPORTED;
-    auto kern = sjlt_cols_kernel<T, TILE, NB_COLS, STAGES>;
+    auto kern = sjlt_cols_kernel<T, TILE, NB_COLS, STAGES, false, CPLX>;
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, (J.njobs + 1) * 32, smem, s>>>(tm, A->rows, A->cols, C.ents, C.offs, C.e_stride, C.o_stride,
                                                 rg.lo, rg.hi, J.nbw, J.njobs, e_bytes, St, ldSt, scale, h->d_err,
@@ -739,6 +761,48 @@ int sjlt_kernel_apply(sk_op* h, const float* P, int64_t n, const float* Q, int64
   if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
     return launch_cols_gen<3>(h, g, n, m, C, 0, h->d_total, (float)scale, S, ldS, s);
   return launch_cols_gen<2>(h, g, n, m, C, 0, h->d_total, (float)scale, S, ldS, s);
+}
+
+// Complex A (interleaved FP32 parts; rows x cols complex, ld in complex
+// elements; S, S' complex with ldS, ldSt in complex elements), real R:
+//  * S' = A* R: the cols kernel over the real view (2 cols real columns), whose
+//    lanes hold the real and imaginary parts of two complex columns, with the
+//    conjugating flush;
+//  * S = A R: the rows kernel over the real view with the operator R (x) I_2
+//    (row 2j + t of it has R's nonzeros of row j at columns 2c + t), whose
+//    output columns are the (re, im) pairs of S.
+int sjlt_apply_complex(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S,
+                       int64_t ldS, void* St, int64_t ldSt, cudaStream_t s) {
+  sk_matrix V = *A;  // the real view
+  V.dtype = SK_F32;
+  V.cols = 2 * A->cols;
+  V.ld = 2 * A->ld;
+  if (which & SK_ST) {
+    JLS_CHECK(build_ccs(h, 0, s));
+    const TiledCcs& C = h->ccs[0];
+    const size_t tile_b = (size_t)SJLT_TILE_F32 * 512, o_max = (COLS_JOBS * NB_COLS + 8) * 4;
+    const size_t e_blk = (size_t)h->alpha * SJLT_TILE_F32 * ENTRY_BYTES;
+    if (blocks_that_fit<3>(tile_b, o_max, e_blk) >= 1)
+      JLS_CHECK((launch_cols<float, SJLT_TILE_F32, 3, true>(h, &V, C, c_lo, c_hi, (float)scale, (float*)St,
+                                                             2 * ldSt, s)));
+    else
+      JLS_CHECK((launch_cols<float, SJLT_TILE_F32, 2, true>(h, &V, C, c_lo, c_hi, (float)scale, (float*)St,
+                                                             2 * ldSt, s)));
+  }
+  if (which & SK_S) {
+    JLS_CHECK(build_ccs_complex(h, s));
+    // R (x) I_2 as an operator: twice the rows, columns and block widths of R
+    sk_op R2;
+    R2.kind = h->kind;
+    R2.n = 2 * h->n;
+    R2.alpha = h->alpha;
+    R2.d_total = 2 * h->d_total;
+    for (int w : h->blocks) R2.blocks.push_back(2 * w);
+    R2.d_err = h->d_err;
+    JLS_CHECK((launch_rows_any<float, SJLT_TILE_F32>(&R2, &V, h->ccs[2], 2 * c_lo, 2 * c_hi, (float)scale,
+                                                    (float*)S, 2 * ldS, s)));
+  }
+  return SK_OK;
 }
 
 int sjlt_apply(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S, int64_t ldS,

@@ -52,6 +52,20 @@ __device__ __forceinline__ void flush_row(double* out_row, const double (&v)[NB]
     if (b < nb) red_add1(out_row + b, v[b] * scale);
 }
 
+// Add scale * (re[b], -im[b]) (b < nb) to the complex output row `out` (FP32 pairs).
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1,%2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+template <int NB>
+__device__ __forceinline__ void flush_row_conj(float* out, const float (&re)[NB], const float (&im)[NB], int nb,
+                                               float scale) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (b < nb) red_add2(out + 2 * b, re[b] * scale, -im[b] * scale);
+}
+template <int NB>
+__device__ __forceinline__ void flush_row_conj(double*, const double (&)[NB], const double (&)[NB], int, double) {}
+
 struct SplitK {  // stream-K range of this CTA
   int64_t u0, u1;
 };

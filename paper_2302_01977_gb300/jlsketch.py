@@ -36,6 +36,7 @@ SK_SRHT = 3
 SK_GAUSS = 4
 SK_F64 = 1
 SK_F32 = 2
+SK_C64 = 3
 SK_PREC_NATIVE = 0
 SK_PREC_BF16X2 = 3
 SK_PREC_FP8 = 4
@@ -160,6 +161,8 @@ def _dtype_code(t) -> int:
         return SK_F32
     if t.dtype == torch.float64:
         return SK_F64
+    if t.dtype == torch.complex64:
+        return SK_C64
     raise TypeError(f"unsupported dtype {t.dtype}")
 
 

@@ -272,3 +272,29 @@ def test_bisection_order_is_a_valid_median_split():
     Q = P[perm]
     axis = int(np.argmax(P.max(0) - P.min(0)))
     assert Q[:500, axis].max() <= Q[500:, axis].min()
+
+
+def test_apply_complex_against_real_parts():
+    """S = A R and S' = A* R for A = B + iC equal B R + i C R and B^T R - i C^T R
+    (R real), and reduce to the real products for real A."""
+    from oracle import sketch as osk
+    rng = np.random.default_rng(21)
+    B, C = rng.standard_normal((7, 9)), rng.standard_normal((7, 9))
+    R9, R7 = rng.standard_normal((9, 4)), rng.standard_normal((7, 4))
+    S = osk.complex_s(B + 1j * C, R9)
+    np.testing.assert_allclose(S, B @ R9 + 1j * (C @ R9), rtol=1e-14, atol=1e-14)
+    St = osk.complex_t(B + 1j * C, R7)
+    np.testing.assert_allclose(St, B.T @ R7 - 1j * (C.T @ R7), rtol=1e-14, atol=1e-14)
+    A = rng.standard_normal((6, 6))
+    R = rng.standard_normal((6, 3))
+    S, St = osk.apply_complex(A, R)
+    S0, St0 = osk.apply(A, R)
+    np.testing.assert_allclose(S, S0, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(St, St0, rtol=1e-14, atol=1e-14)
+    # entry by entry: S'_jc = sum_i conj(A_ij) R_ic
+    Z = B[:, :7] + 1j * C[:, :7]
+    St = osk.complex_t(Z, R7)
+    for j in range(7):
+        for c in range(4):
+            want = sum(np.conj(Z[i, j]) * R7[i, c] for i in range(7))
+            assert abs(St[j, c] - want) <= 1e-13
