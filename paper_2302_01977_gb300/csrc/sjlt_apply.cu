@@ -333,7 +333,11 @@ __global__ void __launch_bounds__((GEN ? GEN_CTA_WARPS : SJLT_WARPS) * 32, 1)
 // S = A R : lanes over rows of A (RPL rows each), cp.async-fed, pitch TILE + 1.
 constexpr int RPL = 4;  // rows per lane
 constexpr int ROWS_BLK = 32 * RPL;
+#ifndef SJLT_NPROD_OVERRIDE
 constexpr int NPROD = 2;  // producer warps
+#else
+constexpr int NPROD = SJLT_NPROD_OVERRIDE;
+#endif
 
 template <typename T>
 struct RowsAcc;
@@ -561,8 +565,8 @@ constexpr int COLS_JOBS = SJLT_WARPS - 1;
 constexpr int ROWS_JOBS = SJLT_WARPS - NPROD;
 constexpr int NB_COLS = SJLT_NB;
 template <typename T>
-constexpr int nb_rows() {
-  return sizeof(T) == 4 ? SJLT_NB : SJLT_NB / 2;
+constexpr int nb_rows() {  // d = 256 (FP32) and 128 (FP64) in one launch
+  return sizeof(T) == 4 ? (256 + ROWS_JOBS - 1) / ROWS_JOBS : (128 + ROWS_JOBS - 1) / ROWS_JOBS;
 }
 constexpr size_t ENTRY_BYTES = sizeof(uint4);
 constexpr long SMEM_MAX = 227 * 1024;
