@@ -334,6 +334,53 @@ int sketch_batch_info(sk_batch_handle b, int32_t* warps, int32_t* cols_per_warp,
  * device error flag: SK_OK, SK_ERR_TIMEOUT or SK_ERR_DEVICE. */
 int sketch_batch_status(sk_batch_handle b, void* stream);
 
+/*
+ * sketch_batch_adaptive_setup -- prepare Algorithm 1's adaptive loop for every
+ * instance of the batch, run on the device by sketch_batch_adaptive_run.
+ * Instance i's operator must be R_i = JL(d0[i] + dd) grown by dd-column
+ * increments (sketch_increment) up to the most columns the loop may use,
+ * d_total(R_i) (the increments are drawn up front; the loop sketches them one
+ * at a time).  The test of Eq. (3.1) runs on S'_i = A_i^T R_i (S_i for a
+ * symmetric A_i) with eps_rel and eps_abs (0 disables the absolute test).
+ * d0[i] (host array of `count`) and dd are multiples of 8, 8 <= dd <= 32, and
+ * d_total(R_i) - dd <= 512.  Rebuilds the tiles of operators grown since the
+ * batch was made, tunes the kernel shape for the first sketch and for the
+ * increments (the tuning runs write the outputs), allocates each instance's
+ * orthonormal basis (cols_i x (d_total_i - dd) FP32) and a cols_i x 32 block,
+ * and leaves the batch's ranges at [0, d0[i] + dd).  Synchronizes `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, NOMEM, DEVICE.
+ */
+int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel, double eps_abs,
+                                void* stream);
+
+/*
+ * sketch_batch_adaptive_run -- enqueue the whole loop on `stream`: reset the
+ * device tables, then per round one batched sketch launch (round 0: columns
+ * [0, d0 + dd); later rounds: the next dd columns of the instances still
+ * active), one launch of the stopping test (a cluster of CTAs per instance:
+ * the columns before the tested block are absorbed into the instance's basis,
+ * S^ = (I - Q Q^T)^2 S~, the decision, and on failure Q <- [Q, orth(S^)]) and
+ * one launch that renumbers the active instances' work for the next round; a
+ * final launch rescales S'_i[:, :d_i] to R_i[:, :d_i]'s scale 1/sqrt(alpha B_i).
+ * At most max_rounds rounds (0 = until every instance could have finished);
+ * finished instances cost nothing in later rounds.  No host synchronization,
+ * no allocation: capturable in one CUDA graph.  Columns of S'_i past d_i are
+ * left as they were.  Errors: INVALID_ARG (no setup), DEVICE.
+ */
+int sketch_batch_adaptive_run(sk_batch_handle b, int32_t max_rounds, void* stream);
+
+/*
+ * sketch_batch_adaptive_result -- synchronize `stream` and read each
+ * instance's outcome (host arrays of `count`; any may be NULL): d_reached =
+ * the columns of S'_i sketched (d + dd at the last test), state = 1 converged,
+ * 2 stopped because R_i has no further increment, 0 still running when
+ * max_rounds ran out; tests = stopping tests taken; nh, nt = ||S^||_F and
+ * ||S~||_F of the last test.  Then reports the device error flag as
+ * sketch_batch_status does.  Errors: INVALID_ARG, TIMEOUT, DEVICE.
+ */
+int sketch_batch_adaptive_result(sk_batch_handle b, int32_t* d_reached, int32_t* state, int32_t* tests, double* nh,
+                                 double* nt, void* stream);
+
 /* sketch_batch_destroy -- free the batch (NULL is a no-op); the operators are
  * not freed. */
 void sketch_batch_destroy(sk_batch_handle b);

@@ -1,0 +1,615 @@
+// batch_adaptive.cu -- the stopping test of Eq. (3.1) for every instance of a
+// batch, on the device, and the update of the batch's item table it decides.
+//
+// Algorithm 1 per instance i: after the batched launch has sketched the columns
+// [c_hi - dd, c_hi) of S'_i, the test takes S~ = those dd columns,
+// S^ = (I - Q Q^T)^2 S~ (two block Gram-Schmidt passes, the remark after
+// Eq. (3.1)) and stops when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
+// Q is an orthonormal basis of the earlier columns, kept per instance in HBM:
+// the first d0 columns are absorbed before the first test (32 at a time,
+// each block projected against Q, then two Cholesky-QR passes), and after a
+// failed test the projected S^ is absorbed, so the next test starts from the
+// basis of every earlier column.  A Cholesky pivot at or below 1e-26 of the
+// largest Gram diagonal drops its column (a zero column of Q, which leaves
+// Q Q^T unchanged).  The decision moves the instance's column range on by dd,
+// or retires it (converged, or no room left in R_i); a one-CTA kernel then
+// renumbers the units of the active instances for the next batched launch.
+// Nothing returns to the host between rounds, so a whole adaptive run, all
+// rounds, is one CUDA graph.
+//
+// One thread-block cluster of CL CTAs per instance: CTA rank k owns a quarter
+// of S'_i's rows.  The tall-skinny products Q^T W, W^T W are reduced across
+// the cluster through distributed shared memory; W - Q G, the triangular
+// solves and the norms are row-local.  Every CTA factors the same reduced Gram
+// matrix, so all of them take the same decisions without exchanging them.
+//
+// Scale: the loop sketches with the per-block scale 1/sqrt(alpha); R_i with
+// B blocks carries 1/sqrt(alpha B), so the norms are reported (and compared
+// with eps_abs) times 1/sqrt(B), and the finished columns are rescaled once.
+#include <cooperative_groups.h>
+
+#include "batch.cuh"
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace jls {
+namespace {
+
+constexpr int CL = 4;     // CTAs per instance
+constexpr int AT = 512;   // threads per CTA
+constexpr int QMAX = ADAPT_QMAX;
+constexpr int BW = ADAPT_BW;
+constexpr int QCH = 32768;  // bytes of Q per staged chunk of Q^T W
+constexpr int RCMAX = 64;   // rows per staged chunk of Q^T W, at most
+constexpr int PR = 256;     // rows per pass of W - Q G
+constexpr int KC = 32;      // columns of Q per staged step of W - Q G
+constexpr int GR = 64;      // rows per staged chunk of W^T W
+constexpr int LD = BW + 1;
+constexpr int NW = AT / 32;
+
+// shared memory, bytes
+constexpr int SM_QS = 2 * QCH;                // Q chunks, double-buffered
+constexpr int SM_WS = 2 * RCMAX * BW * 4;     // W chunks
+constexpr int SM_STAGE = SM_QS + SM_WS;       // also: this CTA's part of G, Q^T staging, Gram partial
+constexpr int SM_G = QMAX * BW * 4;           // G = Q^T W, FP32
+constexpr int SM_GRAM = BW * LD * 8;          // reduced Gram matrix, FP64
+constexpr int SM_L = BW * LD * 4;             // Cholesky factor for the solves, FP32
+constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8;  // reciprocal pivots, reduction slots
+constexpr int SM_TOTAL = SM_STAGE + SM_G + SM_GRAM + SM_L + SM_MISC;
+static_assert(QMAX * BW * 4 <= SM_STAGE, "the CTA's part of G fits the staging area");
+static_assert(KC * (PR + 4) * 4 <= SM_STAGE, "Q^T staging fits");
+static_assert(BW * BW * 8 + GR * BW * 4 <= SM_STAGE, "Gram partial and W chunk fit");
+static_assert(SM_TOTAL <= 227 * 1024, "one CTA per SM");
+
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+template <typename T>
+__device__ __forceinline__ T* cl_map(T* p, int rank) {
+  return cg::this_cluster().map_shared_rank(p, (unsigned)rank);
+}
+
+struct Ctx {
+  int rank;
+  int64_t r0, r1;  // this CTA's rows of S'_i
+  const float* Q;
+  float* Qw;
+  int64_t ldq;
+  float* W;  // ld BW
+  uint8_t* stage;
+  float* Gs;
+  double* gram;
+  float* Lf;
+  float* rinv;
+  double* red;  // [0, NW): warp sums; [NW]: the CTA's sum, read by the cluster
+};
+
+__device__ __forceinline__ void cp_async_16z(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void fma8x8(float (&acc)[8][8], const float4& a0, const float4& a1, const float4& b0,
+                                       const float4& b1) {
+  const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+}
+
+// sum over the CTA, the same value in every thread (fixed order)
+__device__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// sum over the cluster, the same value in every thread of every CTA
+__device__ double cluster_sum(Ctx& c, double v) {
+  const double s = cta_sum(v, c.red);
+  if (threadIdx.x == 0) c.red[NW] = s;
+  cl_sync();
+  double t = 0.0;
+#pragma unroll
+  for (int r = 0; r < CL; ++r) t += *cl_map(c.red + NW, r);
+  cl_sync();  // the slot is rewritten by the next call
+  return t;
+}
+
+// W[r][j] <- S[r][c0 + j] for j < b (zero for b <= j < BW) on this CTA's rows;
+// returns the thread's share of the sum of squares
+__device__ double load_block(const Ctx& c, const float* S, int64_t ldS, int c0, int b) {
+  float ss = 0.f;
+  const int64_t nr = c.r1 - c.r0;
+  for (int64_t e = threadIdx.x; e < nr * BW; e += AT) {
+    const int64_t r = c.r0 + (e >> 5);
+    const int j = (int)(e & 31);
+    const float v = j < b ? S[r * ldS + c0 + j] : 0.f;
+    c.W[r * BW + j] = v;
+    ss = fmaf(v, v, ss);
+  }
+  return (double)ss;
+}
+
+__device__ double sumsq_w(const Ctx& c) {
+  float ss = 0.f;
+  const int64_t nr = c.r1 - c.r0;
+  for (int64_t e = threadIdx.x; e < nr * BW; e += AT) {
+    const float v = c.W[(c.r0 + (e >> 5)) * BW + (e & 31)];
+    ss = fmaf(v, v, ss);
+  }
+  return (double)ss;
+}
+
+// Gs <- Q[:, :q]^T W over all rows of S'_i (q a multiple of 8, <= QMAX), in
+// every CTA of the cluster.  Each CTA forms the product over its rows with
+// 8 x 8 register tiles, q/2 tiles in all; when fewer than AT/2 tiles, the
+// rows of each staged chunk are split over RG groups of threads, whose sums
+// meet in shared-memory atomic adds.  Then CTA k adds up the k-th quarter of
+// the entries over the cluster's CTAs and writes the sums into every CTA's Gs.
+__device__ void qt_w(Ctx& c, int q) {
+  const int U = (q >> 3) * 4;  // tiles: 8 rows of G x 8 of its 32 columns
+  const int RG = max(1, AT / U);
+  const int t = threadIdx.x;
+  const bool act = t < RG * U;
+  const int g = act ? t / U : 0, lt = act ? t - g * U : 0;
+  const int kg = lt >> 2, cg4 = lt & 3;
+  int rc = 16;  // rows per chunk: QCH bytes of Q
+  while (rc < RCMAX && 2 * rc * q * 4 <= QCH) rc *= 2;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float* Qs = reinterpret_cast<float*>(c.stage);
+  float* Ws = reinterpret_cast<float*>(c.stage + SM_QS);
+  const int64_t nr = c.r1 - c.r0;
+  const int nch = (int)((nr + rc - 1) / rc);
+  const int q4 = q >> 2;
+  auto issue = [&](int ch, int buf) {
+    const int64_t rb = c.r0 + (int64_t)ch * rc;
+    float* qd = Qs + buf * (QCH / 4);
+    float* wd = Ws + buf * RCMAX * BW;
+    const int nq = rc * q4;
+    for (int e = t; e < nq + rc * (BW / 4); e += AT) {
+      if (e < nq) {
+        const int rr = e / q4, k4 = e - rr * q4;
+        const int64_t r = rb + rr;
+        const bool in = r < c.r1;
+        cp_async_16z(smem_u32(qd + rr * q + k4 * 4), in ? c.Q + r * c.ldq + k4 * 4 : c.Q, in);
+      } else {
+        const int e2 = e - nq, rr = e2 >> 3, j4 = e2 & 7;
+        const int64_t r = rb + rr;
+        const bool in = r < c.r1;
+        cp_async_16z(smem_u32(wd + rr * BW + j4 * 4), in ? c.W + r * BW + j4 * 4 : c.W, in);
+      }
+    }
+    cp_async_commit();
+  };
+  if (nch > 0) issue(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      issue(ch + 1, (ch + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (act) {
+      const float* qb = Qs + (ch & 1) * (QCH / 4) + kg * 8;
+      const float* wb = Ws + (ch & 1) * RCMAX * BW + cg4 * 8;
+      for (int rr = g; rr < rc; rr += RG) {
+        const float4 a0 = *reinterpret_cast<const float4*>(qb + rr * q);
+        const float4 a1 = *reinterpret_cast<const float4*>(qb + rr * q + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(wb + rr * BW);
+        const float4 b1 = *reinterpret_cast<const float4*>(wb + rr * BW + 4);
+        fma8x8(acc, a0, a1, b0, b1);
+      }
+    }
+    __syncthreads();
+  }
+  // this CTA's part of G over the staging area (every thread is past its last read of it)
+  float* P = reinterpret_cast<float*>(c.stage);
+  for (int e = t; e < q * BW; e += AT) P[e] = 0.f;
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) atomicAdd(P + (kg * 8 + i) * BW + cg4 * 8 + j, acc[i][j]);
+  }
+  cl_sync();
+  const int E4 = q * BW / 4;  // float4 entries of G
+  const int per = E4 / CL;
+  const int e0 = c.rank * per;
+  for (int e = t; e < per; e += AT) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < CL; ++r) {
+      const float4 v = reinterpret_cast<const float4*>(cl_map(P, r))[e0 + e];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < CL; ++r) reinterpret_cast<float4*>(cl_map(c.Gs, r))[e0 + e] = s;
+  }
+  cl_sync();
+}
+
+// W <- W - Q[:, :q] Gs on this CTA's rows: passes of PR rows, 4 x 4 register
+// tiles, Q staged transposed KC columns at a time (the next step's loads in flight)
+__device__ void w_minus_qg(const Ctx& c, int q) {
+  float* Qt = reinterpret_cast<float*>(c.stage);  // [KC][PR + 4]
+  const int rg = threadIdx.x >> 3, cg4 = threadIdx.x & 7;
+  const int srow = threadIdx.x & (PR - 1), spart = threadIdx.x / PR;  // staging: row, which KC/2 columns
+  for (int64_t p0 = c.r0; p0 < c.r1; p0 += PR) {
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int64_t rt = p0 + srow;
+    const bool rin = rt < c.r1;
+    float4 pre[KC / 8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int u = 0; u < KC / 8; ++u) {
+        const int k = k0 + spart * (KC / 2) + 4 * u;
+        pre[u] = (rin && k < q) ? *reinterpret_cast<const float4*>(c.Q + rt * c.ldq + k)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < q; k0 += KC) {
+#pragma unroll
+      for (int u = 0; u < KC / 8; ++u) {
+        float* d = Qt + (spart * (KC / 2) + 4 * u) * (PR + 4) + srow;
+        d[0] = pre[u].x;
+        d[PR + 4] = pre[u].y;
+        d[2 * (PR + 4)] = pre[u].z;
+        d[3 * (PR + 4)] = pre[u].w;
+      }
+      __syncthreads();
+      if (k0 + KC < q) fetch(k0 + KC);
+      const int kn = min(KC, q - k0);  // a multiple of 8
+      for (int kh = 0; kh < kn; kh += 8) {
+#pragma unroll
+        for (int k8 = 0; k8 < 8; ++k8) {
+          const int kk = kh + k8;
+          const float4 a = *reinterpret_cast<const float4*>(Qt + kk * (PR + 4) + rg * 4);
+          const float4 gq = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg4 * 4);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], gv[j], acc[i][j]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = p0 + rg * 4 + i;
+      if (r < c.r1) {
+        float4* wp = reinterpret_cast<float4*>(c.W + r * BW + cg4 * 4);
+        float4 w0 = *wp;
+        w0.x -= acc[i][0];
+        w0.y -= acc[i][1];
+        w0.z -= acc[i][2];
+        w0.w -= acc[i][3];
+        *wp = w0;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// W <- (I - Q Q^T)^2 W
+__device__ void project(Ctx& c, int q) {
+  if (q == 0) return;
+  for (int pass = 0; pass < 2; ++pass) {
+    qt_w(c, q);
+    w_minus_qg(c, q);
+  }
+}
+
+// Right-looking Cholesky G = L L^T in place on the BW x BW matrix L (type A,
+// leading dimension LD), one warp, lane i owning row i; a pivot at or below
+// 1e-26 of the largest diagonal (or an all-zero matrix) zeroes its column.
+// Writes the factor as FP32 into Lf (zero above the diagonal; Lf may be L
+// itself when A is float) and the reciprocal pivots (0 for a dropped column).
+template <typename A>
+__device__ void chol_drop(A* L, float* Lf, float* rinv) {
+  const int lane = threadIdx.x & 31;
+  A dmax = L[lane * LD + lane];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  for (int k = 0; k < BW; ++k) {
+    const A pk = L[k * LD + k];
+    const bool drop = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
+    const A iv = drop ? A(0) : A(1) / sqrt(pk);
+    __syncwarp();
+    if (lane > k) L[lane * LD + k] *= iv;
+    if (lane == k) {
+      L[k * LD + k] = drop ? A(0) : pk * iv;
+      rinv[k] = (float)iv;
+    }
+    __syncwarp();  // column k of L is final
+    if (lane > k) {
+      const A lik = L[lane * LD + k];
+      for (int j = k + 1; j <= lane; ++j) L[lane * LD + j] -= lik * L[j * LD + k];
+    }
+    __syncwarp();
+  }
+  for (int j = 0; j < BW; ++j) {
+    const float v = j <= lane ? (float)L[lane * LD + j] : 0.f;
+    __syncwarp();  // Lf may alias L
+    Lf[lane * LD + j] = v;
+  }
+}
+
+// One Cholesky-QR pass on the b <= BW columns of W (the rest are zero):
+// the Gram matrix over all rows (FP32 runs of 4 GR rows added in FP64, the
+// CTAs' partials added in rank order in every CTA), its factor (FP64 in the
+// first pass, where the Gram matrix squares W's condition number; FP32 in
+// the second, where it is the identity up to the first pass's rounding),
+// then W <- W L^{-T} row by row.
+__device__ void cholqr_pass(Ctx& c, bool fp64) {
+  double* gp = reinterpret_cast<double*>(c.stage);                // [BW][BW], this CTA's partial
+  float* Wc = reinterpret_cast<float*>(c.stage + BW * BW * 8);     // [GR][BW]
+  const int i = threadIdx.x >> 4, j0 = (threadIdx.x & 15) * 2;
+  double d[2] = {0.0, 0.0};
+  float f[2] = {0.f, 0.f};
+  int run = 0;
+  for (int64_t p0 = c.r0; p0 < c.r1; p0 += GR) {
+    for (int e = threadIdx.x; e < GR * BW / 4; e += AT) {
+      const int rr = e >> 3, j4 = e & 7;
+      const int64_t r = p0 + rr;
+      reinterpret_cast<float4*>(Wc)[e] =
+          r < c.r1 ? *reinterpret_cast<const float4*>(c.W + r * BW + j4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GR; ++rr) {
+      const float wi = Wc[rr * BW + i];
+      const float2 wj = *reinterpret_cast<const float2*>(Wc + rr * BW + j0);
+      f[0] = fmaf(wi, wj.x, f[0]);
+      f[1] = fmaf(wi, wj.y, f[1]);
+    }
+    __syncthreads();
+    if (++run == 4) {
+      d[0] += (double)f[0];
+      d[1] += (double)f[1];
+      f[0] = f[1] = 0.f;
+      run = 0;
+    }
+  }
+  gp[i * BW + j0] = d[0] + (double)f[0];
+  gp[i * BW + j0 + 1] = d[1] + (double)f[1];
+  cl_sync();
+  for (int e = threadIdx.x; e < BW * BW; e += AT) {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < CL; ++r) s += cl_map(gp, r)[e];
+    c.gram[(e >> 5) * LD + (e & 31)] = s;
+  }
+  cl_sync();  // the partials are overwritten after this
+  if (threadIdx.x < 32) {
+    if (fp64) {
+      chol_drop<double>(c.gram, c.Lf, c.rinv);
+    } else {
+      for (int j = 0; j < BW; ++j) c.Lf[threadIdx.x * LD + j] = (float)c.gram[threadIdx.x * LD + j];
+      __syncwarp();
+      chol_drop<float>(c.Lf, c.Lf, c.rinv);
+    }
+  }
+  __syncthreads();
+  // x_j = (w_j - sum_{m < j} x_m L[j][m]) / L[j][j], one row per thread
+  for (int64_t r = c.r0 + threadIdx.x; r < c.r1; r += AT) {
+    float x[BW];
+    float4* wp = reinterpret_cast<float4*>(c.W + r * BW);
+#pragma unroll
+    for (int u = 0; u < BW / 4; ++u) {
+      const float4 v = wp[u];
+      x[4 * u] = v.x;
+      x[4 * u + 1] = v.y;
+      x[4 * u + 2] = v.z;
+      x[4 * u + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < BW; ++j) {
+      float a0 = x[j], a1 = 0.f;
+#pragma unroll
+      for (int m = 0; m + 1 < j; m += 2) {
+        a0 = fmaf(-x[m], c.Lf[j * LD + m], a0);
+        a1 = fmaf(-x[m + 1], c.Lf[j * LD + m + 1], a1);
+      }
+      if (j & 1) a0 = fmaf(-x[j - 1], c.Lf[j * LD + j - 1], a0);
+      x[j] = (a0 + a1) * c.rinv[j];
+    }
+#pragma unroll
+    for (int u = 0; u < BW / 4; ++u) wp[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+  }
+  __syncthreads();
+}
+
+// Orthonormalize W's b columns (two Cholesky-QR passes) and append them to Q
+__device__ void absorb(Ctx& c, int& q, int b) {
+  cholqr_pass(c, true);
+  cholqr_pass(c, false);
+  const int64_t nr = c.r1 - c.r0;
+  for (int64_t e = threadIdx.x; e < nr * b; e += AT) {
+    const int64_t rr = e / b;
+    const int j = (int)(e - rr * b);
+    const int64_t r = c.r0 + rr;
+    c.Qw[r * c.ldq + q + j] = c.W[r * BW + j];
+  }
+  __syncthreads();
+  q += b;
+}
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(AT, 1)
+    batch_test_kernel(BItem* __restrict__ items, ATest* __restrict__ tests, const int* __restrict__ order,
+                      double eps_rel, double eps_abs) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  Ctx c;
+  c.rank = (int)cg::this_cluster().block_rank();
+  const int inst = order[blockIdx.x / CL];
+  ATest* T = tests + inst;
+  BItem* I = items + inst;
+  if (T->state != ADAPT_ACTIVE) return;  // the same in every CTA of the cluster
+  const int dd = T->dd, c_end = I->c_hi, c_split = c_end - dd;
+  int q = T->q, covered = T->covered;
+  const int64_t n = T->rows;
+  const int64_t rpr = ((n + CL - 1) / CL + 15) / 16 * 16;
+  c.r0 = min64(n, (int64_t)c.rank * rpr);
+  c.r1 = min64(n, c.r0 + rpr);
+  c.Q = T->Q;
+  c.Qw = T->Q;
+  c.ldq = T->qcap;
+  c.W = T->W;
+  c.stage = smem;
+  c.Gs = reinterpret_cast<float*>(smem + SM_STAGE);
+  c.gram = reinterpret_cast<double*>(smem + SM_STAGE + SM_G);
+  c.Lf = reinterpret_cast<float*>(smem + SM_STAGE + SM_G + SM_GRAM);
+  c.rinv = reinterpret_cast<float*>(smem + SM_STAGE + SM_G + SM_GRAM + SM_L);
+  c.red = reinterpret_cast<double*>(smem + SM_STAGE + SM_G + SM_GRAM + SM_L + 32 * 4);  // NW + 1 slots
+  const float* S = T->S;
+  const int64_t ldS = T->ldS;
+
+  // columns before the tested block that Q does not cover yet (the first d0)
+  while (covered < c_split) {
+    const int b = min(BW, c_split - covered);
+    load_block(c, S, ldS, covered, b);
+    __syncthreads();
+    project(c, q);
+    absorb(c, q, b);
+    covered += b;
+  }
+  // the test, Eq. (3.1)
+  const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
+  project(c, q);
+  const double nh2 = cluster_sum(c, sumsq_w(c));
+  const int blocks = 1 + (c_end - T->first_w) / dd;
+  const double sc = 1.0 / sqrt((double)blocks);
+  const double nh = sqrt(nh2) * sc, nt = sqrt(nt2) * sc;
+  const bool stop = (nh < eps_abs) || (nh < eps_rel * nt);
+  const bool room = c_end + dd <= T->d_cap;
+  if (!stop && room) {  // Algorithm 1 goes on: Q <- [Q, orth(S^)]
+    absorb(c, q, dd);
+    covered = c_end;
+  }
+  if (c.rank == 0 && threadIdx.x == 0) {
+    T->nh = nh;
+    T->nt = nt;
+    T->tests += 1;
+    T->d_reached = c_end;
+    if (stop || !room) {
+      T->state = stop ? ADAPT_CONVERGED : ADAPT_CAPPED;
+      I->units = 0;
+    } else {
+      T->q = q;
+      T->covered = covered;
+      I->c_lo = c_end;
+      I->c_hi = c_end + dd;
+    }
+  }
+}
+
+// Units of the active instances for the next batched launch, numbered in
+// item order (one CTA): per item its blocks x tiles and its columns per warp.
+__global__ void __launch_bounds__(1024)
+    batch_renumber_kernel(BItem* __restrict__ items, int count, BHeader* __restrict__ hdr, int njobs, int nb,
+                          int* err) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (count + 1023) / 1024;
+  const int i0 = min(count, t * per), i1 = min(count, i0 + per);
+  int64_t s = 0;
+  for (int i = i0; i < i1; ++i) {
+    BItem& I = items[i];
+    if (I.units) {
+      const int nbw = (I.c_hi - I.c_lo + njobs - 1) / njobs;
+      if (nbw > nb) {
+        set_err(err, ERRF_BOUNDS);  // the host checks dd against the shape before the run
+        I.units = 0;
+      } else {
+        I.nbw = nbw;
+        I.units = (int64_t)((I.cols + 127) / 128) * I.ntiles;
+      }
+    }
+    s += I.units;
+  }
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t run = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const int64_t v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    hdr->total_units = run;
+  }
+  __syncthreads();
+  int64_t u = part[t];
+  for (int i = i0; i < i1; ++i) {
+    items[i].unit0 = u;
+    u += items[i].units;
+  }
+}
+
+// S'_i[:, :d_reached] *= 1/sqrt(B), B = blocks of R_i[:, :d_reached]
+__global__ void __launch_bounds__(256) batch_rescale_kernel(const ATest* __restrict__ tests) {
+  const ATest& T = tests[blockIdx.x];
+  const int d = T.d_reached;
+  if (d <= 0) return;
+  const int blocks = 1 + (d - T.first_w) / T.dd;
+  if (blocks <= 1) return;
+  const float f = (float)(1.0 / sqrt((double)blocks));
+  float* S = const_cast<float*>(T.S);
+  for (int64_t r = blockIdx.y; r < T.rows; r += gridDim.y)
+    for (int j = threadIdx.x; j < d; j += blockDim.x) S[r * T.ldS + j] *= f;
+}
+
+}  // namespace
+
+int adaptive_prepare() {
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(batch_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
+  return SK_OK;
+}
+
+int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, double eps_rel, double eps_abs,
+                         cudaStream_t s) {
+  batch_test_kernel<<<(unsigned)(count * CL), AT, SM_TOTAL, s>>>(items, tests, order, eps_rel, eps_abs);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+int adaptive_renumber_launch(BItem* items, int count, BHeader* hdr, int njobs, int nb, int* err, cudaStream_t s) {
+  batch_renumber_kernel<<<1, 1024, 0, s>>>(items, count, hdr, njobs, nb, err);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+int adaptive_rescale_launch(const ATest* tests, int count, cudaStream_t s) {
+  batch_rescale_kernel<<<dim3((unsigned)count, 16), 256, 0, s>>>(tests);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+}  // namespace jls

@@ -15,7 +15,9 @@
 // lives in the device-resident item table), the tile's entry records and
 // column offsets ride along as bulk copies, and consumer warps accumulate
 // their columns of R_i in registers and add them into the zeroed output when
-// the CTA leaves a block (at most two CTAs share a block).
+// the CTA leaves a block (atomically: a block spans several CTAs' ranges when
+// the batch has fewer units than a few per CTA, so the order of those adds,
+// and the last bit of the sums, can differ between runs).
 //
 // The item table and a header (total units, staging sizes) are device memory
 // written from a pinned host mirror by the run call itself, so a captured CUDA
@@ -25,31 +27,16 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
 #include "sjlt_common.cuh"
 
 namespace jls {
-
-struct alignas(128) BItem {
-  CUtensorMap tm;  // A_i: cols (inner) x rows, box 128 x 128, FP32
-  const uint4* ents;
-  const uint32_t* offs;
-  float* St;
-  int64_t e_stride, o_stride;
-  int64_t rows, cols, ldSt;
-  int64_t unit0, units;  // this instance's units in the batch order (0 when inactive)
-  int32_t ntiles, c_lo, c_hi, nbw;
-  float scale;
-  int32_t pad[3];
-};
-struct BHeader {
-  int64_t total_units;
-  uint32_t e_bytes, o_bytes;  // staging per stage: entry records, column offsets
-};
 
 namespace {
 
@@ -245,30 +232,39 @@ struct sk_batch {
   int* d_err = nullptr;
   int config = -1;  // index into kConfigs, chosen by measurement
   float tuned_ms[jls::kNumConfigs] = {};
+  // the adaptive loop (sketch_batch_adaptive_setup)
+  bool adaptive = false;
+  int cfg_first = -1, cfg_inc = -1;  // shapes for the first sketch and for the increments
+  int a_stages = 0, max_tests = 0;
+  size_t a_smem = 0;
+  double eps_rel = 0.0, eps_abs = 0.0;
+  jls::BItem* d_items0 = nullptr;  // the item table and header of round 0
+  jls::BHeader* d_hdr0 = nullptr;
+  jls::ATest* d_tests = nullptr;   // per-instance loop state, and its initial value
+  jls::ATest* d_tests0 = nullptr;
+  int* d_order = nullptr;          // instances, largest first (the test kernel's cluster order)
+  float* d_basis = nullptr;        // Q_i and W_i of every instance
 };
 
 namespace jls {
 namespace {
 
-int batch_layout(sk_batch* b, int* stages, size_t* smem) {
-  // staging sizes for the widest column range of any active instance
-  uint32_t e_max = 16, o_max = 16;
-  for (int i = 0; i < b->count; ++i) {
-    const BItem& I = b->h_items[i];
-    if (!I.units) continue;
-    const sk_op* h = b->items[i].op;
-    // entries of a tile that fall in [c_lo, c_hi): alpha per row for each block the range touches
-    int off = 0, touched = 0;
-    for (int w : h->blocks) {
-      if (off < I.c_hi && off + w > I.c_lo) ++touched;
-      off += w;
-    }
-    e_max = std::max<uint32_t>(e_max, (uint32_t)(BTILE * h->alpha * touched * 16));
-    o_max = std::max<uint32_t>(o_max, (uint32_t)((((I.c_hi + 1 + 3) & ~3) - (I.c_lo & ~3)) * 4));
+// staging bytes a tile of the range [lo, hi) of R's columns needs: alpha entry
+// records per row for each block the range touches, and the column offsets
+void range_staging(const sk_op* h, int lo, int hi, uint32_t* e_max, uint32_t* o_max) {
+  int off = 0, touched = 0;
+  for (int w : h->blocks) {
+    if (off < hi && off + w > lo) ++touched;
+    off += w;
   }
+  *e_max = std::max<uint32_t>(*e_max, (uint32_t)(BTILE * h->alpha * touched * 16));
+  *o_max = std::max<uint32_t>(*o_max, (uint32_t)((((hi + 1 + 3) & ~3) - (lo & ~3)) * 4));
+}
+
+int staging_fit(uint32_t e_max, uint32_t o_max, BHeader* hdr, int* stages, size_t* smem) {
   o_max = (o_max + 15) / 16 * 16;
-  b->h_hdr->e_bytes = e_max;
-  b->h_hdr->o_bytes = o_max;
+  hdr->e_bytes = e_max;
+  hdr->o_bytes = o_max;
   for (int st = 3; st >= 2; --st) {
     const size_t need = (size_t)st * (BTILE_BYTES + e_max + o_max) + 2 * st * 8;
     if ((long)need <= BSMEM_MAX) {
@@ -278,6 +274,16 @@ int batch_layout(sk_batch* b, int* stages, size_t* smem) {
     }
   }
   return SK_ERR_UNSUPPORTED;
+}
+
+int batch_layout(sk_batch* b, int* stages, size_t* smem) {
+  // staging sizes for the widest column range of any active instance
+  uint32_t e_max = 16, o_max = 16;
+  for (int i = 0; i < b->count; ++i) {
+    const BItem& I = b->h_items[i];
+    if (I.units) range_staging(b->items[i].op, I.c_lo, I.c_hi, &e_max, &o_max);
+  }
+  return staging_fit(e_max, o_max, b->h_hdr, stages, smem);
 }
 
 int batch_launch(sk_batch* b, int cfg, cudaStream_t s) {
@@ -294,6 +300,19 @@ int batch_launch(sk_batch* b, int cfg, cudaStream_t s) {
   auto kern = stages == 3 ? C.k3 : C.k2;  // shared-memory limit raised at creation
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(num_sms(), b->h_hdr->total_units));
   kern<<<grid, C.warps * 32, smem, s>>>(b->d_items, b->count, b->d_hdr, b->d_err);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// zero and sketch on the device table as it stands (its units are counted on
+// the device, so the grid is one CTA per SM; CTAs without units exit)
+int batch_launch_device(sk_batch* b, int cfg, cudaStream_t s) {
+  batch_zero_kernel<<<b->count, 256, 0, s>>>(b->d_items, b->count);
+  note_launch();
+  const BConfig& C = kConfigs[cfg];
+  auto kern = b->a_stages == 3 ? C.k3 : C.k2;
+  kern<<<num_sms(), C.warps * 32, b->a_smem, s>>>(b->d_items, b->count, b->d_hdr, b->d_err);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -381,6 +400,21 @@ static int batch_fill(sk_batch* b, const int32_t* active, const int32_t* c_lo, c
     I.scale = (float)(sc != 0.0 ? sc : op_scale(h));
   }
   return SK_OK;
+}
+
+static void adaptive_free(sk_batch* b) {
+  if (b->d_items0) cudaFree(b->d_items0);
+  if (b->d_hdr0) cudaFree(b->d_hdr0);
+  if (b->d_tests) cudaFree(b->d_tests);
+  if (b->d_tests0) cudaFree(b->d_tests0);
+  if (b->d_order) cudaFree(b->d_order);
+  if (b->d_basis) cudaFree(b->d_basis);
+  b->d_items0 = nullptr;
+  b->d_hdr0 = nullptr;
+  b->d_tests = b->d_tests0 = nullptr;
+  b->d_order = nullptr;
+  b->d_basis = nullptr;
+  b->adaptive = false;
 }
 
 int sketch_batch_create(sk_batch_handle* out, const sk_batch_item* items, int32_t count, void* stream) {
@@ -500,7 +534,174 @@ void sketch_batch_destroy(sk_batch_handle b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_hdr) cudaFree(b->d_hdr);
   if (b->d_err) cudaFree(b->d_err);
+  adaptive_free(b);
   delete b;
+}
+
+// ---- the adaptive loop ----------------------------------------------------------------
+
+int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel, double eps_abs,
+                                void* stream) {
+  if (!b || !d0 || dd < 8 || dd > ADAPT_BW || dd % 8 || !(eps_rel >= 0.0) || !(eps_abs >= 0.0))
+    return SK_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int count = b->count;
+  for (int i = 0; i < count; ++i) {
+    const sk_op* h = b->items[i].op;
+    const int first = d0[i] + dd;
+    if (d0[i] < 0 || d0[i] % 8 || h->blocks.empty() || h->blocks[0] != first) return SK_ERR_INVALID_ARG;
+    for (size_t j = 1; j < h->blocks.size(); ++j)
+      if (h->blocks[j] != dd) return SK_ERR_INVALID_ARG;  // R_i = JL(d0 + dd) grown by dd-column increments
+    if (b->items[i].ldSt < h->d_total) return SK_ERR_INVALID_ARG;
+    if (h->d_total - dd > ADAPT_QMAX) return SK_ERR_UNSUPPORTED;
+  }
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  adaptive_free(b);
+  // operators grown since the batch was made: rebuild their tiles, refresh the table
+  for (int i = 0; i < count; ++i) {
+    sk_op* h = b->items[i].op;
+    JLS_CHECK(build_ccs(h, 0, s));
+    const TiledCcs& C = h->ccs[0];
+    BItem& I = b->h_items[i];
+    I.ents = C.ents;
+    I.offs = C.offs;
+    I.e_stride = C.e_stride;
+    I.o_stride = C.o_stride;
+    I.ntiles = C.ntiles;
+  }
+  // the kernel shapes: one for the increments [d0 + dd, d0 + 2 dd), one for the first sketch [0, d0 + dd)
+  std::vector<int32_t> act(count), lo(count), hi(count);
+  bool any = false;
+  for (int i = 0; i < count; ++i) {
+    const bool on = d0[i] + 2 * dd <= b->items[i].op->d_total;
+    act[i] = on;
+    lo[i] = on ? d0[i] + dd : 0;
+    hi[i] = on ? d0[i] + 2 * dd : dd;
+    any |= on;
+  }
+  if (any) {
+    JLS_CHECK(batch_fill(b, act.data(), lo.data(), hi.data()));
+    JLS_CHECK(batch_tune(b, s));
+  }
+  const int cfg_inc = b->config;
+  for (int i = 0; i < count; ++i) {
+    act[i] = 1;
+    lo[i] = 0;
+    hi[i] = d0[i] + dd;
+  }
+  JLS_CHECK(batch_fill(b, act.data(), lo.data(), hi.data()));
+  JLS_CHECK(batch_tune(b, s));
+  const int cfg_first = b->config;
+  if ((kConfigs[cfg_inc].warps - 1) * kConfigs[cfg_inc].nb < dd) return SK_ERR_UNSUPPORTED;
+  // staging for every range the loop can sketch
+  uint32_t e_max = 16, o_max = 16;
+  int max_tests = 0;
+  for (int i = 0; i < count; ++i) {
+    const sk_op* h = b->items[i].op;
+    range_staging(h, 0, d0[i] + dd, &e_max, &o_max);
+    for (int c = d0[i] + dd; c + dd <= h->d_total; c += dd) range_staging(h, c, c + dd, &e_max, &o_max);
+    max_tests = std::max(max_tests, 1 + (h->d_total - d0[i] - dd) / dd);
+  }
+  BHeader hdr0 = *b->h_hdr;  // units of round 0, numbered for cfg_first by the tuner
+  int stages = 0;
+  size_t smem = 0;
+  JLS_CHECK(staging_fit(e_max, o_max, &hdr0, &stages, &smem));
+  // round 0's table: every instance sketches [0, d0 + dd) at the per-block scale 1/sqrt(alpha)
+  std::vector<BItem> t0(b->h_items, b->h_items + count);
+  for (int i = 0; i < count; ++i) t0[i].scale = (float)(1.0 / std::sqrt((double)b->items[i].op->alpha));
+  // per-instance state; Q_i (cols_i x qcap_i) and W_i (cols_i x 32) in one allocation
+  std::vector<ATest> a0(count);
+  std::vector<size_t> off(count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    const sk_op* h = b->items[i].op;
+    const int qcap = std::max(8, (h->d_total - dd + 7) / 8 * 8);
+    off[i] = total;
+    total += (size_t)b->items[i].cols * (qcap + ADAPT_BW);
+    ATest& T = a0[i];
+    std::memset(&T, 0, sizeof(T));
+    T.S = b->items[i].St;
+    T.rows = b->items[i].cols;
+    T.ldS = b->items[i].ldSt;
+    T.qcap = qcap;
+    T.dd = dd;
+    T.d_cap = h->d_total;
+    T.first_w = d0[i] + dd;
+    T.state = ADAPT_ACTIVE;
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->items[x].cols * (int64_t)b->items[x].op->d_total > b->items[y].cols * (int64_t)b->items[y].op->d_total;
+  });
+  if (cudaMalloc(&b->d_items0, sizeof(BItem) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_hdr0, sizeof(BHeader)) != cudaSuccess ||
+      cudaMalloc(&b->d_tests, sizeof(ATest) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_tests0, sizeof(ATest) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_basis, total * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    adaptive_free(b);
+    return SK_ERR_NOMEM;
+  }
+  for (int i = 0; i < count; ++i) {
+    const int qcap = a0[i].qcap;
+    a0[i].Q = b->d_basis + off[i];
+    a0[i].W = b->d_basis + off[i] + (size_t)b->items[i].cols * qcap;
+  }
+  int rc = adaptive_prepare();
+  if (rc == SK_OK &&
+      (cudaMemcpy(b->d_items0, t0.data(), sizeof(BItem) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_hdr0, &hdr0, sizeof(BHeader), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_tests0, a0.data(), sizeof(ATest) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = SK_ERR_DEVICE;
+  if (rc != SK_OK) {
+    adaptive_free(b);
+    return rc;
+  }
+  b->cfg_first = cfg_first;
+  b->cfg_inc = cfg_inc;
+  b->a_stages = stages;
+  b->a_smem = smem;
+  b->max_tests = max_tests;
+  b->eps_rel = eps_rel;
+  b->eps_abs = eps_abs;
+  b->adaptive = true;
+  return SK_OK;
+}
+
+int sketch_batch_adaptive_run(sk_batch_handle b, int32_t max_rounds, void* stream) {
+  if (!b || !b->adaptive || max_rounds < 0) return SK_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int count = b->count;
+  const int rounds = max_rounds ? std::min<int>(max_rounds, b->max_tests) : b->max_tests;
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_items, b->d_items0, sizeof(BItem) * count, cudaMemcpyDeviceToDevice, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_hdr, b->d_hdr0, sizeof(BHeader), cudaMemcpyDeviceToDevice, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_tests, b->d_tests0, sizeof(ATest) * count, cudaMemcpyDeviceToDevice, s));
+  const BConfig& Ci = kConfigs[b->cfg_inc];
+  for (int r = 0; r < rounds; ++r) {
+    JLS_CHECK(batch_launch_device(b, r == 0 ? b->cfg_first : b->cfg_inc, s));
+    JLS_CHECK(adaptive_test_launch(b->d_items, b->d_tests, b->d_order, count, b->eps_rel, b->eps_abs, s));
+    if (r + 1 < rounds) JLS_CHECK(adaptive_renumber_launch(b->d_items, count, b->d_hdr, Ci.warps - 1, Ci.nb, b->d_err, s));
+  }
+  return adaptive_rescale_launch(b->d_tests, count, s);
+}
+
+int sketch_batch_adaptive_result(sk_batch_handle b, int32_t* d_reached, int32_t* state, int32_t* tests, double* nh,
+                                 double* nt, void* stream) {
+  if (!b || !b->adaptive) return SK_ERR_INVALID_ARG;
+  JLS_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  std::vector<ATest> a(b->count);
+  JLS_CHECK_CUDA(cudaMemcpy(a.data(), b->d_tests, sizeof(ATest) * b->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < b->count; ++i) {
+    if (d_reached) d_reached[i] = a[i].d_reached;
+    if (state) state[i] = a[i].state;
+    if (tests) tests[i] = a[i].tests;
+    if (nh) nh[i] = a[i].nh;
+    if (nt) nt[i] = a[i].nt;
+  }
+  return sketch_batch_status(b, stream);
 }
 
 }  // extern "C"
