@@ -51,8 +51,8 @@ constexpr int ADAPT_BW = 32;     // widest increment dd
 
 // Kernels of batch_adaptive.cu (all asynchronous on `s`, capturable).
 int adaptive_prepare();  // shared-memory limit of the test kernel (call outside capture)
-int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, double eps_rel, double eps_abs,
-                         cudaStream_t s);
+int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
+                         double eps_abs, cudaStream_t s);
 int adaptive_renumber_launch(BItem* items, int count, BHeader* hdr, int njobs, int nb, int* err, cudaStream_t s);
 int adaptive_rescale_launch(const ATest* tests, int count, cudaStream_t s);
 

@@ -17,8 +17,9 @@
 // Nothing returns to the host between rounds, so a whole adaptive run, all
 // rounds, is one CUDA graph.
 //
-// One thread-block cluster of CL CTAs per instance: CTA rank k owns a quarter
-// of S'_i's rows.  The tall-skinny products Q^T W, W^T W are reduced across
+// One thread-block cluster of ncl CTAs per instance (1 for batches of many
+// instances; 4 when there are fewer instances than SMs): CTA rank k owns the
+// k-th share of S'_i's rows.  The tall-skinny products Q^T W, W^T W are reduced across
 // the cluster through distributed shared memory; W - Q G, the triangular
 // solves and the norms are row-local.  Every CTA factors the same reduced Gram
 // matrix, so all of them take the same decisions without exchanging them.
@@ -37,29 +38,31 @@ namespace cg = cooperative_groups;
 namespace jls {
 namespace {
 
-constexpr int CL = 4;     // CTAs per instance
+constexpr int CLMAX = 4;  // CTAs per instance, at most (a cluster)
 constexpr int AT = 512;   // threads per CTA
 constexpr int QMAX = ADAPT_QMAX;
 constexpr int BW = ADAPT_BW;
-constexpr int QCH = 32768;  // bytes of Q per staged chunk of Q^T W
+constexpr int QCH = 57344;  // bytes of Q per staged chunk of Q^T W
 constexpr int RCMAX = 64;   // rows per staged chunk of Q^T W, at most
 constexpr int PR = 256;     // rows per pass of W - Q G
-constexpr int KC = 32;      // columns of Q per staged step of W - Q G
-constexpr int GR = 64;      // rows per staged chunk of W^T W
-constexpr int LD = BW + 1;
+constexpr int KC = 32;      // columns of Q per staged step of W - Q G (8 for each of 4 thread groups)
+constexpr int GR = 256;     // rows per staged chunk of W^T W
+constexpr int QT_FLOATS = KC * (PR + 4);  // one Q^T staging buffer of W - Q G
+constexpr int LD = BW + 1;  // Gram matrix and Cholesky working arrays
+constexpr int LF = BW + 4;  // the factor as the solves read it (16-byte rows)
 constexpr int NW = AT / 32;
 
 // shared memory, bytes
 constexpr int SM_QS = 2 * QCH;                // Q chunks, double-buffered
 constexpr int SM_WS = 2 * RCMAX * BW * 4;     // W chunks
-constexpr int SM_STAGE = SM_QS + SM_WS;       // also: this CTA's part of G, Q^T staging, Gram partial
+constexpr int SM_STAGE = SM_QS + SM_WS;       // also: partial products, Q^T staging, Gram partial
 constexpr int SM_G = QMAX * BW * 4;           // G = Q^T W, FP32
 constexpr int SM_GRAM = BW * LD * 8;          // reduced Gram matrix, FP64
-constexpr int SM_L = BW * LD * 4;             // Cholesky factor for the solves, FP32
-constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8;  // reciprocal pivots, reduction slots
+constexpr int SM_L = BW * LF * 4;             // Cholesky factor, FP32
+constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8 + 2 * BW * 8;  // reciprocal pivots, reduction slots, Cholesky scratch
 constexpr int SM_TOTAL = SM_STAGE + SM_G + SM_GRAM + SM_L + SM_MISC;
-static_assert(QMAX * BW * 4 <= SM_STAGE, "the CTA's part of G fits the staging area");
-static_assert(KC * (PR + 4) * 4 <= SM_STAGE, "Q^T staging fits");
+static_assert(2 * QMAX * BW * 4 <= SM_STAGE, "the row groups' parts of G fit the staging area");
+static_assert(4 * PR * BW * 4 <= SM_STAGE && 2 * QT_FLOATS * 4 <= SM_STAGE, "W - Q G staging fits");
 static_assert(BW * BW * 8 + GR * BW * 4 <= SM_STAGE, "Gram partial and W chunk fit");
 static_assert(SM_TOTAL <= 227 * 1024, "one CTA per SM");
 
@@ -70,7 +73,7 @@ __device__ __forceinline__ T* cl_map(T* p, int rank) {
 }
 
 struct Ctx {
-  int rank;
+  int ncl, rank;  // CTAs of the instance (cluster size) and this CTA's rank
   int64_t r0, r1;  // this CTA's rows of S'_i
   const float* Q;
   float* Qw;
@@ -82,6 +85,7 @@ struct Ctx {
   float* Lf;
   float* rinv;
   double* red;  // [0, NW): warp sums; [NW]: the CTA's sum, read by the cluster
+  double* cs;   // Cholesky scratch, 2 BW entries
 };
 
 __device__ __forceinline__ void cp_async_16z(uint32_t dst, const void* src, bool valid) {
@@ -119,7 +123,7 @@ __device__ double cluster_sum(Ctx& c, double v) {
   cl_sync();
   double t = 0.0;
 #pragma unroll
-  for (int r = 0; r < CL; ++r) t += *cl_map(c.red + NW, r);
+  for (int r = 0; r < c.ncl; ++r) t += *cl_map(c.red + NW, r);
   cl_sync();  // the slot is rewritten by the next call
   return t;
 }
@@ -151,10 +155,11 @@ __device__ double sumsq_w(const Ctx& c) {
 
 // Gs <- Q[:, :q]^T W over all rows of S'_i (q a multiple of 8, <= QMAX), in
 // every CTA of the cluster.  Each CTA forms the product over its rows with
-// 8 x 8 register tiles, q/2 tiles in all; when fewer than AT/2 tiles, the
-// rows of each staged chunk are split over RG groups of threads, whose sums
-// meet in shared-memory atomic adds.  Then CTA k adds up the k-th quarter of
-// the entries over the cluster's CTAs and writes the sums into every CTA's Gs.
+// 8 x 8 register tiles, q/2 tiles in all; the rows of each staged chunk are
+// split over RG = AT / (q/2) groups of threads, whose partial products are
+// added in shared memory (group order).  Then CTA k adds up the k-th quarter
+// of the entries over the cluster's CTAs and writes the sums into every
+// CTA's Gs.
 __device__ void qt_w(Ctx& c, int q) {
   const int U = (q >> 3) * 4;  // tiles: 8 rows of G x 8 of its 32 columns
   const int RG = max(1, AT / U);
@@ -216,50 +221,68 @@ __device__ void qt_w(Ctx& c, int q) {
     }
     __syncthreads();
   }
-  // this CTA's part of G over the staging area (every thread is past its last read of it)
+  // the groups' parts of G over the staging area (every thread is past its last read of it)
   float* P = reinterpret_cast<float*>(c.stage);
-  for (int e = t; e < q * BW; e += AT) P[e] = 0.f;
-  __syncthreads();
+  const int E4 = q * BW / 4;  // float4 entries of G
   if (act) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) atomicAdd(P + (kg * 8 + i) * BW + cg4 * 8 + j, acc[i][j]);
+    for (int i = 0; i < 8; ++i) {
+      float4* p = reinterpret_cast<float4*>(P + ((int64_t)g * q + kg * 8 + i) * BW + cg4 * 8);
+      p[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      p[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+  }
+  __syncthreads();
+  if (RG > 1) {  // this CTA's part: the groups' sum, into group 0's slot
+    float4* P4 = reinterpret_cast<float4*>(P);
+    for (int e = t; e < E4; e += AT) {
+      float4 s = P4[e];
+      for (int gg = 1; gg < RG; ++gg) {
+        const float4 v = P4[gg * E4 + e];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+      }
+      P4[e] = s;
+    }
   }
   cl_sync();
-  const int E4 = q * BW / 4;  // float4 entries of G
-  const int per = E4 / CL;
+  const int per = E4 / c.ncl;
   const int e0 = c.rank * per;
   for (int e = t; e < per; e += AT) {
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int r = 0; r < CL; ++r) {
+    for (int r = 0; r < c.ncl; ++r) {
       const float4 v = reinterpret_cast<const float4*>(cl_map(P, r))[e0 + e];
       s.x += v.x;
       s.y += v.y;
       s.z += v.z;
       s.w += v.w;
     }
-#pragma unroll
-    for (int r = 0; r < CL; ++r) reinterpret_cast<float4*>(cl_map(c.Gs, r))[e0 + e] = s;
+    for (int r = 0; r < c.ncl; ++r) reinterpret_cast<float4*>(cl_map(c.Gs, r))[e0 + e] = s;
   }
   cl_sync();
 }
 
-// W <- W - Q[:, :q] Gs on this CTA's rows: passes of PR rows, 4 x 4 register
-// tiles, Q staged transposed KC columns at a time (the next step's loads in flight)
+// W <- W - Q[:, :q] Gs on this CTA's rows: passes of PR rows; Q staged
+// transposed KC columns at a time (the next step's loads in flight); four
+// groups of threads take 8 of each step's columns with 8 x 8 register tiles,
+// and their partial products are added in shared memory at the end of a pass.
 __device__ void w_minus_qg(const Ctx& c, int q) {
-  float* Qt = reinterpret_cast<float*>(c.stage);  // [KC][PR + 4]
-  const int rg = threadIdx.x >> 3, cg4 = threadIdx.x & 7;
+  float* Qt = reinterpret_cast<float*>(c.stage);  // [2][KC][PR + 4]
+  float* Pw = reinterpret_cast<float*>(c.stage);  // [4][PR][BW], after a pass's last step
+  const int kq = threadIdx.x >> 7, lt = threadIdx.x & 127;
+  const int rg = lt >> 2, cg = lt & 3;  // rows rg*8 .. +7, columns cg*8 .. +7
   const int srow = threadIdx.x & (PR - 1), spart = threadIdx.x / PR;  // staging: row, which KC/2 columns
   for (int64_t p0 = c.r0; p0 < c.r1; p0 += PR) {
-    float acc[4][4];
+    float acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
     const int64_t rt = p0 + srow;
     const bool rin = rt < c.r1;
+    const bool busy = p0 + rg * 8 < c.r1;  // this thread's rows are not all past the end
     float4 pre[KC / 8];
     auto fetch = [&](int k0) {
 #pragma unroll
@@ -269,50 +292,72 @@ __device__ void w_minus_qg(const Ctx& c, int q) {
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    fetch(0);
-    for (int k0 = 0; k0 < q; k0 += KC) {
+    auto stage_q = [&](int buf) {
 #pragma unroll
       for (int u = 0; u < KC / 8; ++u) {
-        float* d = Qt + (spart * (KC / 2) + 4 * u) * (PR + 4) + srow;
+        float* d = Qt + buf * QT_FLOATS + (spart * (KC / 2) + 4 * u) * (PR + 4) + srow;
         d[0] = pre[u].x;
         d[PR + 4] = pre[u].y;
         d[2 * (PR + 4)] = pre[u].z;
         d[3 * (PR + 4)] = pre[u].w;
       }
-      __syncthreads();
-      if (k0 + KC < q) fetch(k0 + KC);
-      const int kn = min(KC, q - k0);  // a multiple of 8
-      for (int kh = 0; kh < kn; kh += 8) {
+    };
+    fetch(0);
+    stage_q(0);
+    if (KC < q) fetch(KC);
+    __syncthreads();
+    for (int k0 = 0, st = 0; k0 < q; k0 += KC, ++st) {
+      // the next step's columns go to the other buffer while this step's are read
+      if (k0 + KC < q) {
+        stage_q((st + 1) & 1);
+        if (k0 + 2 * KC < q) fetch(k0 + 2 * KC);
+      }
+      if (busy && k0 + kq * 8 < q) {  // q - k0 is a multiple of 8
+        const float* Qb = Qt + (st & 1) * QT_FLOATS;
 #pragma unroll
         for (int k8 = 0; k8 < 8; ++k8) {
-          const int kk = kh + k8;
-          const float4 a = *reinterpret_cast<const float4*>(Qt + kk * (PR + 4) + rg * 4);
-          const float4 gq = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg4 * 4);
-          const float av[4] = {a.x, a.y, a.z, a.w};
-          const float gv[4] = {gq.x, gq.y, gq.z, gq.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], gv[j], acc[i][j]);
+          const int kk = kq * 8 + k8;
+          const float4 a0 = *reinterpret_cast<const float4*>(Qb + kk * (PR + 4) + rg * 8);
+          const float4 a1 = *reinterpret_cast<const float4*>(Qb + kk * (PR + 4) + rg * 8 + 4);
+          const float4 g0 = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg * 8);
+          const float4 g1 = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg * 8 + 4);
+          fma8x8(acc, a0, a1, g0, g1);
         }
       }
       __syncthreads();
     }
+    // the four groups' parts, then W -= their sum
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t r = p0 + rg * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+      float4* p = reinterpret_cast<float4*>(Pw + ((kq * PR) + rg * 8 + i) * BW + cg * 8);
+      p[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      p[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+    __syncthreads();
+    const float4* P4 = reinterpret_cast<const float4*>(Pw);
+    for (int f = threadIdx.x; f < PR * BW / 4; f += AT) {
+      const int64_t r = p0 + (f >> 3);
       if (r < c.r1) {
-        float4* wp = reinterpret_cast<float4*>(c.W + r * BW + cg4 * 4);
+        float4 s = P4[f];
+#pragma unroll
+        for (int gq = 1; gq < 4; ++gq) {
+          const float4 v = P4[gq * (PR * BW / 4) + f];
+          s.x += v.x;
+          s.y += v.y;
+          s.z += v.z;
+          s.w += v.w;
+        }
+        float4* wp = reinterpret_cast<float4*>(c.W + r * BW + (f & 7) * 4);
         float4 w0 = *wp;
-        w0.x -= acc[i][0];
-        w0.y -= acc[i][1];
-        w0.z -= acc[i][2];
-        w0.w -= acc[i][3];
+        w0.x -= s.x;
+        w0.y -= s.y;
+        w0.z -= s.z;
+        w0.w -= s.w;
         *wp = w0;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // W <- (I - Q Q^T)^2 W
@@ -324,39 +369,71 @@ __device__ void project(Ctx& c, int q) {
   }
 }
 
-// Right-looking Cholesky G = L L^T in place on the BW x BW matrix L (type A,
-// leading dimension LD), one warp, lane i owning row i; a pivot at or below
-// 1e-26 of the largest diagonal (or an all-zero matrix) zeroes its column.
-// Writes the factor as FP32 into Lf (zero above the diagonal; Lf may be L
-// itself when A is float) and the reciprocal pivots (0 for a dropped column).
+// 1/sqrt(x) for x > 0: the FP32 estimate refined by Newton steps
+// y <- y (3 - x y^2) / 2 in type A (two in FP64, none in FP32)
 template <typename A>
-__device__ void chol_drop(A* L, float* Lf, float* rinv) {
-  const int lane = threadIdx.x & 31;
-  A dmax = L[lane * LD + lane];
+__device__ __forceinline__ A rsqrt_newton(A x) {
+  if constexpr (sizeof(A) == 8) {
+    if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+  } else {
+    return 1.0f / sqrtf(x);
+  }
+}
+
+// 1/sqrt(p_k), or 0 (the column is dropped) for a pivot at or below 1e-26 of
+// the largest diagonal dmax or an all-zero matrix; kept out of line so that
+// it does not crowd the registers of the loops around its call
+template <typename A>
+__device__ __noinline__ A chol_pivot(A pk, A dmax) {
+  const bool drop = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
+  return drop ? A(0) : rsqrt_newton<A>(pk);
+}
+
+// Right-looking Cholesky G = L L^T of the BW x BW matrix in L (type A,
+// leading dimension LDA, overwritten), by all AT threads.  Step k: thread 0
+// takes the pivot p_k (chol_pivot), then each element (i, j), k < j <= i, of
+// the trailing block gets one thread, L[i][j] -= L[i][k] L[j][k] / p_k
+// (column k is scaled by 1/sqrt(p_k) only at the end).  Writes the
+// factor as FP32 into Lf (leading dimension LF, zero above the diagonal and
+// in dropped columns) and the reciprocal diagonal into rinv (0 for a dropped
+// column).  iv and u are shared scratch of BW entries each.
+template <typename A, int LDA>
+__device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u) {
+  const int t = threadIdx.x;
+  if (t < 32) {
+    A v = L[t * LDA + t];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (t == 0) u[0] = v;
+  }
+  __syncthreads();
+  const A dmax = u[0];
+  auto pivot = [&](int k) { iv[k] = chol_pivot<A>(L[k * LDA + k], dmax); };  // thread 0
+  __syncthreads();
   for (int k = 0; k < BW; ++k) {
-    const A pk = L[k * LD + k];
-    const bool drop = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
-    const A iv = drop ? A(0) : A(1) / sqrt(pk);
-    __syncwarp();
-    if (lane > k) L[lane * LD + k] *= iv;
-    if (lane == k) {
-      L[k * LD + k] = drop ? A(0) : pk * iv;
-      rinv[k] = (float)iv;
+    if (t == 0) pivot(k);
+    __syncthreads();
+    const int m = BW - 1 - k;  // order of the trailing block
+    if (t < m * (m + 1) / 2) {
+      int ii = min(m - 1, (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f));  // t = ii (ii + 1) / 2 + jj
+      if (t < ii * (ii + 1) / 2) --ii;
+      const int jj = t - ii * (ii + 1) / 2;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      const A ip = iv[k] * iv[k];
+      L[i * LDA + j] -= (L[i * LDA + k] * ip) * L[j * LDA + k];
     }
-    __syncwarp();  // column k of L is final
-    if (lane > k) {
-      const A lik = L[lane * LD + k];
-      for (int j = k + 1; j <= lane; ++j) L[lane * LD + j] -= lik * L[j * LD + k];
-    }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int j = 0; j < BW; ++j) {
-    const float v = j <= lane ? (float)L[lane * LD + j] : 0.f;
-    __syncwarp();  // Lf may alias L
-    Lf[lane * LD + j] = v;
+  for (int e = t; e < BW * BW; e += AT) {
+    const int i = e >> 5, j = e & 31;
+    Lf[i * LF + j] = j <= i ? (float)(L[i * LDA + j] * iv[j]) : 0.f;
   }
+  if (t < BW) rinv[t] = (float)iv[t];
+  __syncthreads();
 }
 
 // One Cholesky-QR pass on the b <= BW columns of W (the rest are zero):
@@ -371,7 +448,6 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
   const int i = threadIdx.x >> 4, j0 = (threadIdx.x & 15) * 2;
   double d[2] = {0.0, 0.0};
   float f[2] = {0.f, 0.f};
-  int run = 0;
   for (int64_t p0 = c.r0; p0 < c.r1; p0 += GR) {
     for (int e = threadIdx.x; e < GR * BW / 4; e += AT) {
       const int rr = e >> 3, j4 = e & 7;
@@ -388,33 +464,28 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
       f[1] = fmaf(wi, wj.y, f[1]);
     }
     __syncthreads();
-    if (++run == 4) {
-      d[0] += (double)f[0];
-      d[1] += (double)f[1];
-      f[0] = f[1] = 0.f;
-      run = 0;
-    }
+    d[0] += (double)f[0];
+    d[1] += (double)f[1];
+    f[0] = f[1] = 0.f;
   }
-  gp[i * BW + j0] = d[0] + (double)f[0];
-  gp[i * BW + j0 + 1] = d[1] + (double)f[1];
+  gp[i * BW + j0] = d[0];
+  gp[i * BW + j0 + 1] = d[1];
   cl_sync();
   for (int e = threadIdx.x; e < BW * BW; e += AT) {
     double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < CL; ++r) s += cl_map(gp, r)[e];
+    for (int r = 0; r < c.ncl; ++r) s += cl_map(gp, r)[e];
     c.gram[(e >> 5) * LD + (e & 31)] = s;
   }
   cl_sync();  // the partials are overwritten after this
-  if (threadIdx.x < 32) {
-    if (fp64) {
-      chol_drop<double>(c.gram, c.Lf, c.rinv);
-    } else {
-      for (int j = 0; j < BW; ++j) c.Lf[threadIdx.x * LD + j] = (float)c.gram[threadIdx.x * LD + j];
-      __syncwarp();
-      chol_drop<float>(c.Lf, c.Lf, c.rinv);
-    }
+  if (fp64) {
+    chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW);
+  } else {
+    float* Lw = reinterpret_cast<float*>(c.stage);  // FP32 working copy (the partials are no longer read)
+    for (int e = threadIdx.x; e < BW * BW; e += AT) Lw[(e >> 5) * LD + (e & 31)] = (float)c.gram[(e >> 5) * LD + (e & 31)];
+    __syncthreads();
+    float* fs = reinterpret_cast<float*>(c.cs);
+    chol_drop<float, LD>(Lw, c.Lf, c.rinv, fs, fs + BW);
   }
-  __syncthreads();
   // x_j = (w_j - sum_{m < j} x_m L[j][m]) / L[j][j], one row per thread
   for (int64_t r = c.r0 + threadIdx.x; r < c.r1; r += AT) {
     float x[BW];
@@ -431,11 +502,14 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
     for (int j = 0; j < BW; ++j) {
       float a0 = x[j], a1 = 0.f;
 #pragma unroll
-      for (int m = 0; m + 1 < j; m += 2) {
-        a0 = fmaf(-x[m], c.Lf[j * LD + m], a0);
-        a1 = fmaf(-x[m + 1], c.Lf[j * LD + m + 1], a1);
+      for (int m4 = 0; m4 < BW / 4; ++m4) {
+        if (4 * m4 >= j) break;
+        const float4 l = *reinterpret_cast<const float4*>(c.Lf + j * LF + m4 * 4);
+        if (4 * m4 + 0 < j) a0 = fmaf(-x[4 * m4 + 0], l.x, a0);
+        if (4 * m4 + 1 < j) a1 = fmaf(-x[4 * m4 + 1], l.y, a1);
+        if (4 * m4 + 2 < j) a0 = fmaf(-x[4 * m4 + 2], l.z, a0);
+        if (4 * m4 + 3 < j) a1 = fmaf(-x[4 * m4 + 3], l.w, a1);
       }
-      if (j & 1) a0 = fmaf(-x[j - 1], c.Lf[j * LD + j - 1], a0);
       x[j] = (a0 + a1) * c.rinv[j];
     }
 #pragma unroll
@@ -459,20 +533,23 @@ __device__ void absorb(Ctx& c, int& q, int b) {
   q += b;
 }
 
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(AT, 1)
-    batch_test_kernel(BItem* __restrict__ items, ATest* __restrict__ tests, const int* __restrict__ order,
+// One instance per cluster of ncl CTAs (launched with that cluster size; 1: a
+// CTA alone, whose cluster barriers are CTA barriers).
+__global__ void __launch_bounds__(AT, 1)
+    batch_test_kernel(BItem* __restrict__ items, ATest* __restrict__ tests, const int* __restrict__ order, int ncl,
                       double eps_rel, double eps_abs) {
   extern __shared__ __align__(16) uint8_t smem[];
   Ctx c;
+  c.ncl = ncl;
   c.rank = (int)cg::this_cluster().block_rank();
-  const int inst = order[blockIdx.x / CL];
+  const int inst = order[blockIdx.x / ncl];
   ATest* T = tests + inst;
   BItem* I = items + inst;
   if (T->state != ADAPT_ACTIVE) return;  // the same in every CTA of the cluster
   const int dd = T->dd, c_end = I->c_hi, c_split = c_end - dd;
   int q = T->q, covered = T->covered;
   const int64_t n = T->rows;
-  const int64_t rpr = ((n + CL - 1) / CL + 15) / 16 * 16;
+  const int64_t rpr = ((n + ncl - 1) / ncl + 15) / 16 * 16;
   c.r0 = min64(n, (int64_t)c.rank * rpr);
   c.r1 = min64(n, c.r0 + rpr);
   c.Q = T->Q;
@@ -485,6 +562,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(AT, 1)
   c.Lf = reinterpret_cast<float*>(smem + SM_STAGE + SM_G + SM_GRAM);
   c.rinv = reinterpret_cast<float*>(smem + SM_STAGE + SM_G + SM_GRAM + SM_L);
   c.red = reinterpret_cast<double*>(smem + SM_STAGE + SM_G + SM_GRAM + SM_L + 32 * 4);  // NW + 1 slots
+  c.cs = c.red + NW + 8;
   const float* S = T->S;
   const int64_t ldS = T->ldS;
 
@@ -590,11 +668,23 @@ int adaptive_prepare() {
   return SK_OK;
 }
 
-int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, double eps_rel, double eps_abs,
-                         cudaStream_t s) {
-  batch_test_kernel<<<(unsigned)(count * CL), AT, SM_TOTAL, s>>>(items, tests, order, eps_rel, eps_abs);
+int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
+                         double eps_abs, cudaStream_t s) {
+  if (ncl != 1 && ncl != 2 && ncl != CLMAX) return SK_ERR_INVALID_ARG;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * ncl));
+  cfg.blockDim = dim3(AT);
+  cfg.dynamicSmemBytes = SM_TOTAL;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)ncl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel, items, tests, order, ncl, eps_rel, eps_abs));
   note_launch();
-  JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 

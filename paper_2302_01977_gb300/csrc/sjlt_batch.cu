@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -236,6 +237,7 @@ struct sk_batch {
   bool adaptive = false;
   int cfg_first = -1, cfg_inc = -1;  // shapes for the first sketch and for the increments
   int a_stages = 0, max_tests = 0;
+  int a_ncl = 1;  // CTAs per instance in the test kernel
   size_t a_smem = 0;
   double eps_rel = 0.0, eps_abs = 0.0;
   jls::BItem* d_items0 = nullptr;  // the item table and header of round 0
@@ -665,6 +667,11 @@ int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd
   b->a_stages = stages;
   b->a_smem = smem;
   b->max_tests = max_tests;
+  // the stopping test: one CTA per instance amortizes its fixed costs best; a
+  // cluster of 4 per instance when the instances would not fill the GPU
+  const char* env = std::getenv("JLS_ADAPT_CLUSTER");
+  b->a_ncl = env ? std::atoi(env) : (count >= num_sms() ? 1 : 4);
+  if (b->a_ncl != 1 && b->a_ncl != 2 && b->a_ncl != 4) b->a_ncl = 4;
   b->eps_rel = eps_rel;
   b->eps_abs = eps_abs;
   b->adaptive = true;
@@ -682,7 +689,7 @@ int sketch_batch_adaptive_run(sk_batch_handle b, int32_t max_rounds, void* strea
   const BConfig& Ci = kConfigs[b->cfg_inc];
   for (int r = 0; r < rounds; ++r) {
     JLS_CHECK(batch_launch_device(b, r == 0 ? b->cfg_first : b->cfg_inc, s));
-    JLS_CHECK(adaptive_test_launch(b->d_items, b->d_tests, b->d_order, count, b->eps_rel, b->eps_abs, s));
+    JLS_CHECK(adaptive_test_launch(b->d_items, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs, s));
     if (r + 1 < rounds) JLS_CHECK(adaptive_renumber_launch(b->d_items, count, b->d_hdr, Ci.warps - 1, Ci.nb, b->d_err, s));
   }
   return adaptive_rescale_launch(b->d_tests, count, s);
