@@ -63,7 +63,8 @@ constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8 + 2 * BW * 8;  // reciprocal pivot
 constexpr int SM_TOTAL = SM_STAGE + SM_G + SM_GRAM + SM_L + SM_MISC;
 static_assert(2 * QMAX * BW * 4 <= SM_STAGE, "the row groups' parts of G fit the staging area");
 static_assert(4 * PR * BW * 4 <= SM_STAGE && 2 * QT_FLOATS * 4 <= SM_STAGE, "W - Q G staging fits");
-static_assert(BW * BW * 8 + GR * BW * 4 <= SM_STAGE, "Gram partial and W chunk fit");
+static_assert(5 * BW * BW * 8 + 2 * GR * BW * 4 <= SM_STAGE, "Gram partials and W chunks fit");
+static_assert(GR * BW / 4 % AT == 0 && AT == 512, "thread mappings assume 512 threads");
 static_assert(SM_TOTAL <= 227 * 1024, "one CTA per SM");
 
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
@@ -129,28 +130,44 @@ __device__ double cluster_sum(Ctx& c, double v) {
 }
 
 // W[r][j] <- S[r][c0 + j] for j < b (zero for b <= j < BW) on this CTA's rows;
-// returns the thread's share of the sum of squares
+// returns the thread's share of the sum of squares.  A warp takes a row (32
+// consecutive floats of S); four rows per thread are in flight at a time.
 __device__ double load_block(const Ctx& c, const float* S, int64_t ldS, int c0, int b) {
+  constexpr int RS = AT / 32;  // rows per sweep of the CTA
+  const int j = threadIdx.x & 31;
+  const bool jin = j < b;
   float ss = 0.f;
-  const int64_t nr = c.r1 - c.r0;
-  for (int64_t e = threadIdx.x; e < nr * BW; e += AT) {
-    const int64_t r = c.r0 + (e >> 5);
-    const int j = (int)(e & 31);
-    const float v = j < b ? S[r * ldS + c0 + j] : 0.f;
+  int64_t r = c.r0 + (threadIdx.x >> 5);
+  for (; r + 3 * RS < c.r1; r += 4 * RS) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = jin ? S[(r + u * RS) * ldS + c0 + j] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c.W[(r + u * RS) * BW + j] = v[u];
+      ss = fmaf(v[u], v[u], ss);
+    }
+  }
+  for (; r < c.r1; r += RS) {
+    const float v = jin ? S[r * ldS + c0 + j] : 0.f;
     c.W[r * BW + j] = v;
     ss = fmaf(v, v, ss);
   }
   return (double)ss;
 }
 
+// the thread's share of the sum of squares of W on this CTA's rows (float4 loads)
 __device__ double sumsq_w(const Ctx& c) {
-  float ss = 0.f;
-  const int64_t nr = c.r1 - c.r0;
-  for (int64_t e = threadIdx.x; e < nr * BW; e += AT) {
-    const float v = c.W[(c.r0 + (e >> 5)) * BW + (e & 31)];
-    ss = fmaf(v, v, ss);
+  constexpr int RS = AT / 8;
+  const float4* W4 = reinterpret_cast<const float4*>(c.W);
+  const int f = threadIdx.x & 7;
+  float s0 = 0.f, s1 = 0.f;
+  for (int64_t r = c.r0 + (threadIdx.x >> 3); r < c.r1; r += RS) {
+    const float4 v = W4[r * (BW / 4) + f];
+    s0 = fmaf(v.x, v.x, fmaf(v.y, v.y, s0));
+    s1 = fmaf(v.z, v.z, fmaf(v.w, v.w, s1));
   }
-  return (double)ss;
+  return (double)(s0 + s1);
 }
 
 // Gs <- Q[:, :q]^T W over all rows of S'_i (q a multiple of 8, <= QMAX), in
@@ -443,33 +460,59 @@ __device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u) {
 // the second, where it is the identity up to the first pass's rounding),
 // then W <- W L^{-T} row by row.
 __device__ void cholqr_pass(Ctx& c, bool fp64) {
-  double* gp = reinterpret_cast<double*>(c.stage);                // [BW][BW], this CTA's partial
-  float* Wc = reinterpret_cast<float*>(c.stage + BW * BW * 8);     // [GR][BW]
-  const int i = threadIdx.x >> 4, j0 = (threadIdx.x & 15) * 2;
-  double d[2] = {0.0, 0.0};
-  float f[2] = {0.f, 0.f};
-  for (int64_t p0 = c.r0; p0 < c.r1; p0 += GR) {
-    for (int e = threadIdx.x; e < GR * BW / 4; e += AT) {
-      const int rr = e >> 3, j4 = e & 7;
+  double* gp = reinterpret_cast<double*>(c.stage);                 // [BW][BW], this CTA's partial
+  float* Wc = reinterpret_cast<float*>(c.stage + BW * BW * 8);      // [2][GR][BW], double-buffered
+  double* gg = reinterpret_cast<double*>(c.stage + BW * BW * 8 + 2 * GR * BW * 4);  // [4][BW][BW], the groups'
+  const int grp = threadIdx.x >> 7, lt = threadIdx.x & 127;
+  const int i = lt >> 2, j0 = (lt & 3) * 8;  // entries (i, j0 .. j0 + 7); rows rr = grp (mod 4)
+  double d[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) d[u] = 0.0;
+  auto issue = [&](int64_t p0, int buf) {
+#pragma unroll
+    for (int u = 0; u < GR * BW / 4 / AT; ++u) {
+      const int e = threadIdx.x + u * AT, rr = e >> 3, j4 = e & 7;
       const int64_t r = p0 + rr;
-      reinterpret_cast<float4*>(Wc)[e] =
-          r < c.r1 ? *reinterpret_cast<const float4*>(c.W + r * BW + j4 * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool in = r < c.r1;
+      cp_async_16z(smem_u32(Wc + buf * GR * BW + e * 4), in ? c.W + r * BW + j4 * 4 : c.W, in);
+    }
+    cp_async_commit();
+  };
+  if (c.r0 < c.r1) issue(c.r0, 0);
+  for (int64_t p0 = c.r0, ch = 0; p0 < c.r1; p0 += GR, ++ch) {
+    if (p0 + GR < c.r1) {
+      issue(p0 + GR, (int)((ch + 1) & 1));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < GR; ++rr) {
-      const float wi = Wc[rr * BW + i];
-      const float2 wj = *reinterpret_cast<const float2*>(Wc + rr * BW + j0);
-      f[0] = fmaf(wi, wj.x, f[0]);
-      f[1] = fmaf(wi, wj.y, f[1]);
+    const float* Wb = Wc + (ch & 1) * GR * BW;
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f[u] = 0.f;
+#pragma unroll 4
+    for (int rr = grp; rr < GR; rr += 4) {
+      const float wi = Wb[rr * BW + i];
+      const float4 w0 = *reinterpret_cast<const float4*>(Wb + rr * BW + j0);
+      const float4 w1 = *reinterpret_cast<const float4*>(Wb + rr * BW + j0 + 4);
+      f[0] = fmaf(wi, w0.x, f[0]);
+      f[1] = fmaf(wi, w0.y, f[1]);
+      f[2] = fmaf(wi, w0.z, f[2]);
+      f[3] = fmaf(wi, w0.w, f[3]);
+      f[4] = fmaf(wi, w1.x, f[4]);
+      f[5] = fmaf(wi, w1.y, f[5]);
+      f[6] = fmaf(wi, w1.z, f[6]);
+      f[7] = fmaf(wi, w1.w, f[7]);
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) d[u] += (double)f[u];
     __syncthreads();
-    d[0] += (double)f[0];
-    d[1] += (double)f[1];
-    f[0] = f[1] = 0.f;
   }
-  gp[i * BW + j0] = d[0];
-  gp[i * BW + j0 + 1] = d[1];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) gg[grp * BW * BW + i * BW + j0 + u] = d[u];
+  __syncthreads();
+  for (int e = threadIdx.x; e < BW * BW; e += AT) gp[e] = ((gg[e] + gg[BW * BW + e]) + gg[2 * BW * BW + e]) + gg[3 * BW * BW + e];
   cl_sync();
   for (int e = threadIdx.x; e < BW * BW; e += AT) {
     double s = 0.0;
@@ -500,17 +543,17 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
     }
 #pragma unroll
     for (int j = 0; j < BW; ++j) {
-      float a0 = x[j], a1 = 0.f;
+      float a0 = x[j], a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
       for (int m4 = 0; m4 < BW / 4; ++m4) {
         if (4 * m4 >= j) break;
         const float4 l = *reinterpret_cast<const float4*>(c.Lf + j * LF + m4 * 4);
         if (4 * m4 + 0 < j) a0 = fmaf(-x[4 * m4 + 0], l.x, a0);
         if (4 * m4 + 1 < j) a1 = fmaf(-x[4 * m4 + 1], l.y, a1);
-        if (4 * m4 + 2 < j) a0 = fmaf(-x[4 * m4 + 2], l.z, a0);
-        if (4 * m4 + 3 < j) a1 = fmaf(-x[4 * m4 + 3], l.w, a1);
+        if (4 * m4 + 2 < j) a2 = fmaf(-x[4 * m4 + 2], l.z, a2);
+        if (4 * m4 + 3 < j) a3 = fmaf(-x[4 * m4 + 3], l.w, a3);
       }
-      x[j] = (a0 + a1) * c.rinv[j];
+      x[j] = ((a0 + a1) + (a2 + a3)) * c.rinv[j];
     }
 #pragma unroll
     for (int u = 0; u < BW / 4; ++u) wp[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
@@ -522,12 +565,13 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
 __device__ void absorb(Ctx& c, int& q, int b) {
   cholqr_pass(c, true);
   cholqr_pass(c, false);
-  const int64_t nr = c.r1 - c.r0;
-  for (int64_t e = threadIdx.x; e < nr * b; e += AT) {
-    const int64_t rr = e / b;
-    const int j = (int)(e - rr * b);
-    const int64_t r = c.r0 + rr;
-    c.Qw[r * c.ldq + q + j] = c.W[r * BW + j];
+  // Q[:, q : q + b] <- W[:, :b], float4 at a time (b, q and the row pitch of Q are multiples of 8)
+  const int f = threadIdx.x & 7;
+  if (f < (b >> 2)) {
+    const float4* W4 = reinterpret_cast<const float4*>(c.W);
+#pragma unroll 4
+    for (int64_t r = c.r0 + (threadIdx.x >> 3); r < c.r1; r += AT / 8)
+      *reinterpret_cast<float4*>(c.Qw + r * c.ldq + q + 4 * f) = W4[r * (BW / 4) + f];
   }
   __syncthreads();
   q += b;
