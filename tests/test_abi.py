@@ -80,6 +80,14 @@ def test_null_handle_calls(L):
     assert L.sketch_device_status(None, None) == jl.SK_ERR_INVALID_ARG
     L.sketch_destroy(None)  # no-op
     assert L.kernel_matrix(None, None, 0, None) == jl.SK_ERR_INVALID_ARG
+    # batches and their adaptive loop
+    assert L.sketch_batch_create(None, None, 0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_batch_run(None, None) == jl.SK_ERR_INVALID_ARG
+    d0 = (ctypes.c_int32 * 1)(32)
+    assert L.sketch_batch_adaptive_setup(None, d0, 32, 1e-3, 0.0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_batch_adaptive_run(None, 0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_batch_adaptive_result(None, None, None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    L.sketch_batch_destroy(None)  # no-op
 
 
 def test_no_gpu_fails_loudly(L):
