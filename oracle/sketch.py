@@ -20,6 +20,11 @@
   log2(nu) butterfly stages (the O(n log n) transform of Sec. 7.1).
 * ``srht_by_fwht(A, D, mu, d_total)``: S = A D H P sqrt(nu/d) computed through
   the transform of the zero-padded rows (Sec. 7.1, A padded to nu columns).
+* ``srht_by_split(A, D, mu, d_total)``: the same product for n not a power of
+  two through the two smaller transforms of Sec. 7.1 (Eqs. had1 and hadiden):
+  with k = 2^floor(log2 n), n = k + r, p = 2^ceil(log2 r) and q = k / p,
+  A H_{2k} = [A_k H_k + T, A_k H_k - T] where T = (A^ H_p)[I ... I] repeats
+  the p-point transform of the last r columns (zero-padded to p) q times.
 """
 from __future__ import annotations
 
@@ -140,3 +145,22 @@ def srht_by_fwht(A: np.ndarray, D: np.ndarray, mu: np.ndarray, d_total: int) -> 
     X[:, :n] = A * np.asarray(D, dtype=np.float64)[None, :]
     Y = fwht(X)
     return Y[:, np.asarray(mu)] / math.sqrt(d_total)
+
+
+def srht_by_split(A: np.ndarray, D: np.ndarray, mu: np.ndarray, d_total: int) -> np.ndarray:
+    """S = A D H P (scale 1/sqrt(d)) for n = k + r, 0 < r < k, by Sec. 7.1's split:
+    transforms of orders k and p instead of one of order nu = 2k."""
+    A = np.asarray(A, dtype=np.float64) * np.asarray(D, dtype=np.float64)[None, :]
+    m, n = A.shape
+    k = 1 << (n.bit_length() - 1)  # 2^floor(log2 n)
+    r = n - k
+    if r == 0:
+        raise ValueError("n is a power of two: no split")
+    p = 1 << (r - 1).bit_length()  # 2^ceil(log2 r)
+    q = k // p
+    AkHk = A[:, :k] @ hadamard(k)                       # A_{m,k} H_k
+    Ahat = np.zeros((m, p), dtype=np.float64)           # A^ = [A_{m,r}  0_{m,p-r}]
+    Ahat[:, :r] = A[:, k:]
+    T = (Ahat @ hadamard(p)) @ np.hstack([np.eye(p)] * q)  # A^ H_p [I ... I], m x k
+    AH = np.hstack([AkHk + T, AkHk - T])                 # A H_{2k}, Eq. had1
+    return AH[:, np.asarray(mu)] / math.sqrt(d_total)

@@ -141,6 +141,32 @@ def test_srht_fwht_route_equals_element_formula(n, d):
     assert np.allclose(S_def, S_fwht, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("n", [3, 5, 6, 12, 100, 130, 777, 1100])
+def test_srht_split_equals_element_formula_and_padded_transform(n):
+    """Sec. 7.1's H_k / H_p split of a non-power-of-two order gives the product with
+    R from the element formula of Sec. 7.2 and the transform of zero-padded rows."""
+    d = min(16, 1 << (n - 1).bit_length())
+    op = ops.Operator("srht", n, d, 1, seed=n)
+    A = np.random.default_rng(n).standard_normal((7, n))
+    S_split = sk.srht_by_split(A, op.srht_diag(), op.srht_samples(), op.d_total)
+    assert np.allclose(S_split, A @ op.dense(), rtol=0, atol=1e-12 * max(1.0, np.abs(A).sum()))
+    S_pad = sk.srht_by_fwht(A, op.srht_diag(), op.srht_samples(), op.d_total)
+    assert np.allclose(S_split, S_pad, rtol=0, atol=1e-12 * max(1.0, np.abs(A).sum()))
+
+
+def test_srht_split_tail_is_a_periodic_transform():
+    """Eq. hadiden: the padded order-k transform of a vector whose nonzeros are its
+    first r <= p entries repeats its order-p transform k/p times."""
+    k, r = 64, 11
+    p = 16
+    x = np.zeros(k)
+    x[:r] = np.random.default_rng(1).standard_normal(r)
+    y = sk.fwht(x)
+    assert np.allclose(y, np.tile(sk.fwht(x[:p]), k // p), rtol=0, atol=1e-12)
+    with pytest.raises(ValueError):
+        sk.srht_by_split(np.ones((2, 8)), np.ones(8), np.arange(4), 4)
+
+
 def test_srht_nu_too_small_rejected():
     with pytest.raises(ValueError):
         ops.Operator("srht", 8, 9)
