@@ -802,6 +802,85 @@ def run_batch_adaptive(args):
     print(json.dumps(line))
 
 
+SRHT_SPLIT = dict(name="srht_nonpow2_fp32_n24000", n=24000, d=256, h=0.1, sample_rows=256, seed=20230203 + 6)
+
+
+def run_srht_split(args):
+    """SRHT S = A D H P/sqrt(d) for a non-power-of-two order (n = 24000 = k + r,
+    k = 16384, r = 7616, p = 8192) through the row FWHT: Sec. 7.1's split into
+    transforms of orders k and p against the transform of rows zero-padded to
+    nu = 32768.  A = K(X, Y; h) in FP32 (X != Y, 2.3 GB); value = GB/s of A of
+    the split.  Errors on sampled rows against an FP64 numpy A R with the
+    exported operator."""
+    import numpy as np
+    import torch
+
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = SRHT_SPLIT
+    n, d = w["n"], w["d"]
+    torch.cuda.set_device(0)
+    X = torch.from_numpy(inputs.points(n, seed=w["seed"])).cuda()
+    Y = torch.from_numpy(inputs.points(n, seed=w["seed"] + 1)).cuda()
+    ld = (n + 3) // 4 * 4
+    Abuf = torch.empty((n, ld), dtype=torch.float32, device="cuda")
+    A = Abuf[:, :n]
+    jl.kernel_matrix(jl.generator(X, Y, w["h"]), A)
+    h = jl.sketch_create("srht", n, d, 1, w["seed"], d)
+    rng = np.random.default_rng(w["seed"])
+    rows = np.sort(rng.choice(n, w["sample_rows"], replace=False))
+    rows_t = torch.from_numpy(rows).cuda()
+    hbm, _, _, peak_kind = peaks()
+    os.environ["JLS_SRHT_ROUTE"] = "fwht"
+    res = {}
+    clocks = Clocks(0)
+    clocks.start()
+    try:
+        for name, split in (("split", "1"), ("padded", "0")):
+            os.environ["JLS_SRHT_SPLIT"] = split
+            S = torch.empty((n, d), dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup):
+                jl.sketch_apply(h, A, jl.SK_S, S=S)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = jl.sketch_launch_count()
+            e0.record()
+            for _ in range(args.steps):
+                jl.sketch_apply(h, A, jl.SK_S, S=S)
+            e1.record()
+            torch.cuda.synchronize()
+            jl.sketch_device_status(h)
+            ms = e0.elapsed_time(e1) / args.steps
+            res[name] = {"ms": round(ms, 3), "gbs_of_A": round(4.0 * n * n / ms / 1e6, 1),
+                         "pct_hbm": round(100 * 4.0 * n * n / ms / 1e6 / hbm, 1),
+                         "launches_per_apply": (jl.sketch_launch_count() - l0) / args.steps,
+                         "S_rows": S.index_select(0, rows_t).double().cpu().numpy()}
+    finally:
+        ck = clocks.stop()
+        os.environ.pop("JLS_SRHT_ROUTE", None)
+        os.environ.pop("JLS_SRHT_SPLIT", None)
+    R = jl.sketch_export(h, dense=True)["R"]
+    jl.sketch_destroy(h)
+    ref = A.index_select(0, rows_t).double().cpu().numpy() @ R
+    for r in res.values():
+        r["rel_err_vs_fp64"] = float(f"{np.linalg.norm(r.pop('S_rows') - ref) / np.linalg.norm(ref):.3e}")
+    best = res["split"]
+    line = {"metric": METRIC, "value": best["gbs_of_A"], "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+            "config": {"workload": w["name"], "n": n, "d": d, "h": w["h"], "operator": "srht", "which": "S",
+                       "k": 16384, "r": n - 16384, "p": 8192, "nu": 32768,
+                       "l2": "inputs larger than L2 (2.3 GB of A), no flush"},
+            "split": res["split"], "padded": res["padded"],
+            "speedup_split_vs_padded": round(res["padded"]["ms"] / res["split"]["ms"], 3),
+            "peak_source": peak_kind, "gpu_launches": int(res["split"]["launches_per_apply"] * args.steps),
+            "clocks": ck}
+    print(json.dumps(line))
+
+
 COMPLEX = dict(name="complex_helmholtz_fp32_n16384", n=16384, d=256, alpha=4, kappa=20.0, seed=20230203 + 5)
 
 
@@ -882,7 +961,8 @@ def main():
                     help="matrix order (the benchmark workload is 32768; smaller n for profiling captures)")
     ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536",
                                            "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024",
-                                           "batch_adaptive_fp32_1024", "complex_helmholtz_fp32_n16384"],
+                                           "batch_adaptive_fp32_1024", "complex_helmholtz_fp32_n16384",
+                                           "srht_nonpow2_fp32_n24000"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--points", type=int, default=0,
@@ -904,6 +984,8 @@ def main():
         run_batching(args)
     elif args.workload == "batch_adaptive_fp32_1024":
         run_batch_adaptive(args)
+    elif args.workload == "srht_nonpow2_fp32_n24000":
+        run_srht_split(args)
     elif args.workload == "complex_helmholtz_fp32_n16384":
         run_complex(args)
     else:

@@ -10,7 +10,7 @@
  *     S' = A^T R      (sketch of the columns of A, Sec. 6.3 "A* R"; real A)
  *
  * for three JL operators R (n x d): the SJLT (Sec. 2.4.3, data structure
- * Sec. 6.1), the SRHT R = D H P (Sec. 2.4.2, element formula the element formula of Sec. 7.2) and the
+ * Sec. 6.1), the SRHT R = D H P (Sec. 2.4.2; element formula of Sec. 7.2) and the
  * Gaussian operator N(0, 1/d) (Sec. 2.4.1); R grows by Delta-d columns
  * (Sec. 6.2, Algorithm 1: R <- [R R_bar], S <- [S A R_bar]) until the Frobenius
  * stopping test of Eq. (3.1) passes.
@@ -416,7 +416,13 @@ int64_t sketch_launch_count(void);
  * of Sec. 7.2, -1 not measured yet.  The first apply of a shape times both
  * routes on its stream (one synchronization) and keeps the faster; only FP32
  * data with nu in [2^14, 2^16] and SK_PREC_NATIVE or SK_PREC_BF16X2 has both
- * routes.  A diagnostic query; the paper has no counterpart. */
+ * routes.  For n not a power of two the FWHT takes Sec. 7.1's split into
+ * transforms of orders k = 2^floor(log2 n) and p = 2^ceil(log2(n - k)) when
+ * n - k <= 8192 and k >= 2^14 (otherwise, or with JLS_SRHT_SPLIT=0 in the
+ * environment, it transforms the zero-padded rows; both give the same S).
+ * The environment variable JLS_SRHT_ROUTE=fwht or =product pins the route for
+ * the process (shapes served that way are not recorded, and report -1).  A
+ * diagnostic query; the paper has no counterpart. */
 int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int32_t prec);
 
 /* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -81,8 +82,23 @@ static int srht_s_gemm(sk_op* h, const sk_matrix* A, int prec, int c_lo, int c_h
   return dense_apply_simt(h, A, SK_S, c_lo, c_hi, scale, S, ldS, nullptr, 0, s);
 }
 
+// JLS_SRHT_ROUTE=fwht or =product pins the route instead of timing both (for
+// tests and profiling of one route; such shapes are not recorded as measured)
+static int srht_route_override() {
+  const char* e = std::getenv("JLS_SRHT_ROUTE");
+  if (!e) return -1;
+  if (!std::strcmp(e, "fwht")) return 1;
+  if (!std::strcmp(e, "product")) return 0;
+  return -1;
+}
+
 static int srht_pick_fwht(sk_op* h, const sk_matrix* A, int prec, int c_lo, int c_hi, double scale, void* S,
                           int64_t ldS, cudaStream_t s, bool* fwht) {
+  const int forced = srht_route_override();
+  if (forced >= 0) {
+    *fwht = forced == 1;
+    return SK_OK;
+  }
   const SrhtPick key{h->nu, A->rows, A->cols, c_hi - c_lo, prec, false};
   {
     std::lock_guard<std::mutex> lock(g_pick_mu);

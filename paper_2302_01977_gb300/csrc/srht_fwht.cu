@@ -17,7 +17,19 @@
 // more stages.  The transformed unit is written back to the buffer and the
 // sampled columns whose output index falls in segment p are gathered and
 // stored (plain stores: every column belongs to one unit).
+//
+// n not a power of two (Sec. 7.1's split, Eqs. had1 and hadiden): with
+// k = 2^floor(log2 n), n = k + r and p = 2^ceil(log2 r), the padded order-2k
+// transform is A_k H_k + T in its first half and A_k H_k - T in its second,
+// T repeating the order-p transform of the last r columns (zero-padded to p).
+// The units above then transform only the first k columns (outputs taken at
+// mu mod k) and store scale (A_k H_k)_mu; a second kernel transforms each
+// row's last r columns in shared memory and adds +-scale (A^ H_p)_{mu mod p}
+// (+ below k, - above).  Per row that is k log k + p log p butterflies instead
+// of 2k log 2k; the split is taken for r <= 8192 (p fits one CTA's shared
+// memory), the padded transform otherwise.
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -75,8 +87,8 @@ __device__ __forceinline__ void stage(float (&x)[N], int s) {
 // k = j + 128 t, and round B transforms bits 0..6.
 __global__ void __launch_bounds__(FW_THREADS, 3)
     srht_fwht_rows_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t n, int nseg,
-                          const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, int c_lo, int c_hi,
-                          float scale, float* __restrict__ S, int64_t ldS) {
+                          const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, uint32_t omask,
+                          int c_lo, int c_hi, float scale, float* __restrict__ S, int64_t ldS) {
   extern __shared__ float buf[];                                        // FW_BUF floats
   uint32_t* dbits = reinterpret_cast<uint32_t*>(buf + FW_BUF);          // [seg][word][thread]
   const int t = threadIdx.x;
@@ -174,10 +186,109 @@ __global__ void __launch_bounds__(FW_THREADS, 3)
 #pragma unroll
     for (int j = 0; j < FW_E; ++j) buf[j + 129 * t] = x[j];
     __syncthreads();
-    // sampled columns whose output index is in segment p
+    // sampled columns whose output index (mod the transform order) is in segment p
     for (int c = c_lo + t; c < c_hi; c += FW_THREADS) {
-      const int o = mu[c];
+      const int o = (int)((uint32_t)mu[c] & omask);
       if ((o >> FW_LOG_L) == p) S[i * ldS + c] = scale * buf[pad(o & (FW_L - 1))];
+    }
+    __syncthreads();
+  }
+}
+
+// The H_p part of the split: row i's columns k .. k + r - 1, sign-flipped by D
+// and zero-padded to p, are transformed, and every sampled column adds
+// +-scale (A^ H_p)_{mu mod p} to the scale (A_k H_k)_{mu mod k} already stored
+// (one read-modify-write per output: deterministic).
+constexpr int TAIL_THREADS = 128;
+constexpr int TAIL_MAX = 8192;
+
+// p = 128 E (E = 8 .. 64) values of a row in registers, 128 threads.  Thread t
+// loads k^ = t + 128 j (j < E); round A transforms bits 7 .. (the register
+// index) by FFMA2 butterfly pairs; a transpose through shared memory gives
+// thread t' = G h + g (G = 128 / E) the values k^ = 128 h + g + G j', so round
+// B1 transforms bits log2 G .. 6 in registers and round B2 bits 0 .. log2 G - 1
+// across the G lanes of a group by shuffles.  The buffer index of k^ is
+// k^ + G (k^ >> 7): conflict-free for both the write and the read.
+template <int E>
+__global__ void __launch_bounds__(TAIL_THREADS)
+    srht_fwht_tail_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t k, int r,
+                          const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, int c_lo, int c_hi,
+                          float scale, float* __restrict__ S, int64_t ldS) {
+  constexpr int P = 128 * E, G = 128 / E;
+  constexpr int LOG_E = E == 8 ? 3 : E == 16 ? 4 : E == 32 ? 5 : 6;
+  __shared__ float tb[P + E * G];
+  const int t = threadIdx.x;
+  auto idx = [](int kk) { return kk + G * (kk >> 7); };
+  uint64_t neg = 0;  // D's sign of k^ = t + 128 j, bit j
+  for (int j = 0; j < E; ++j) {
+    const int kk = t + 128 * j;
+    if (kk < r && diag[k + kk] < 0) neg |= 1ull << j;
+  }
+  const int h = t / G, g = t % G;
+  for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+    const float* a = A + i * lda + k;
+    float x[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const int kk = t + 128 * j;
+      const float v = kk < r ? __ldg(a + kk) : 0.f;
+      x[j] = ((neg >> j) & 1) ? -v : v;
+    }
+#pragma unroll
+    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+#pragma unroll
+    for (int j = 0; j < E; ++j) tb[idx(t + 128 * j)] = x[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < E; ++j) x[j] = tb[idx(128 * h + g + G * j)];
+#pragma unroll
+    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+#pragma unroll
+    for (int b = 1; b < G; b <<= 1) {
+      const bool upper = (g & b) != 0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const float u = __shfl_xor_sync(0xffffffffu, x[j], b);
+        x[j] = upper ? u - x[j] : x[j] + u;
+      }
+    }
+    __syncthreads();  // every thread has read its transposed values
+#pragma unroll
+    for (int j = 0; j < E; ++j) tb[idx(128 * h + g + G * j)] = x[j];
+    __syncthreads();
+    for (int c = c_lo + t; c < c_hi; c += TAIL_THREADS) {
+      const int o = mu[c];
+      const float v = scale * tb[idx(o & (P - 1))];
+      S[i * ldS + c] += o < k ? v : -v;
+    }
+    __syncthreads();
+  }
+}
+
+// p < 1024: the transform in shared memory, log2 p butterfly stages over the CTA
+__global__ void __launch_bounds__(TAIL_THREADS)
+    srht_fwht_tail_small_kernel(const float* __restrict__ A, int64_t lda, int64_t rows, int64_t k, int r, int p,
+                                const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, int c_lo, int c_hi,
+                                float scale, float* __restrict__ S, int64_t ldS) {
+  __shared__ float tb[1024];
+  const int t = threadIdx.x;
+  for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+    const float* a = A + i * lda + k;
+    for (int j = t; j < p; j += TAIL_THREADS) tb[j] = j < r ? (diag[k + j] < 0 ? -a[j] : a[j]) : 0.f;
+    __syncthreads();
+    for (int hh = 1; hh < p; hh <<= 1) {
+      for (int b = t; b < p / 2; b += TAIL_THREADS) {
+        const int j0 = ((b & ~(hh - 1)) << 1) | (b & (hh - 1)), j1 = j0 + hh;
+        const float x = tb[j0], y = tb[j1];
+        tb[j0] = x + y;
+        tb[j1] = x - y;
+      }
+      __syncthreads();
+    }
+    for (int c = c_lo + t; c < c_hi; c += TAIL_THREADS) {
+      const int o = mu[c];
+      const float v = scale * tb[o & (p - 1)];
+      S[i * ldS + c] += o < k ? v : -v;
     }
     __syncthreads();
   }
@@ -194,18 +305,57 @@ int srht_apply_fwht(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double sca
   const int nseg = fwht_segments(h->nu);
   if (!nseg || A->dtype != SK_F32) return SK_ERR_UNSUPPORTED;
   if (c_hi <= c_lo) return SK_OK;
+  // Sec. 7.1's split for n = k + r, 0 < r <= TAIL_MAX, when the order-k transform is one of ours
+  int64_t k = 1;
+  while (2 * k <= h->n) k *= 2;
+  const int64_t r = h->n - k;
+  int p = 1;
+  while (p < r) p *= 2;
+  const char* env = std::getenv("JLS_SRHT_SPLIT");  // "0": transform the zero-padded rows instead
+  const bool split = r > 0 && r <= TAIL_MAX && fwht_segments(k) > 0 && !(env && env[0] == '0' && !env[1]);
   const size_t smem = FW_BUF * sizeof(float) + FW_DWORDS * sizeof(uint32_t);
   static bool attr = false;
   if (!attr) {
     JLS_CHECK_CUDA(cudaFuncSetAttribute(srht_fwht_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  const int64_t units = A->rows * nseg;
+  const int segs = split ? fwht_segments(k) : nseg;
+  const int64_t units = A->rows * segs;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(3 * num_sms(), units));
-  srht_fwht_rows_kernel<<<grid, FW_THREADS, smem, s>>>(static_cast<const float*>(A->A), A->ld, A->rows, h->n, nseg,
-                                                        h->srht_diag, h->srht_mu, c_lo, c_hi, (float)scale, S, ldS);
+  srht_fwht_rows_kernel<<<grid, FW_THREADS, smem, s>>>(static_cast<const float*>(A->A), A->ld, A->rows,
+                                                        split ? k : h->n, segs, h->srht_diag, h->srht_mu,
+                                                        (uint32_t)((split ? k : h->nu) - 1), c_lo, c_hi,
+                                                        (float)scale, S, ldS);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
+  if (split) {
+    const unsigned tgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(8 * num_sms(), A->rows));
+    const float* Ap = static_cast<const float*>(A->A);
+    const float sc = (float)scale;
+    switch (p) {
+      case 8192:
+        srht_fwht_tail_kernel<64><<<tgrid, TAIL_THREADS, 0, s>>>(Ap, A->ld, A->rows, k, (int)r, h->srht_diag,
+                                                                  h->srht_mu, c_lo, c_hi, sc, S, ldS);
+        break;
+      case 4096:
+        srht_fwht_tail_kernel<32><<<tgrid, TAIL_THREADS, 0, s>>>(Ap, A->ld, A->rows, k, (int)r, h->srht_diag,
+                                                                  h->srht_mu, c_lo, c_hi, sc, S, ldS);
+        break;
+      case 2048:
+        srht_fwht_tail_kernel<16><<<tgrid, TAIL_THREADS, 0, s>>>(Ap, A->ld, A->rows, k, (int)r, h->srht_diag,
+                                                                  h->srht_mu, c_lo, c_hi, sc, S, ldS);
+        break;
+      case 1024:
+        srht_fwht_tail_kernel<8><<<tgrid, TAIL_THREADS, 0, s>>>(Ap, A->ld, A->rows, k, (int)r, h->srht_diag,
+                                                                 h->srht_mu, c_lo, c_hi, sc, S, ldS);
+        break;
+      default:
+        srht_fwht_tail_small_kernel<<<tgrid, TAIL_THREADS, 0, s>>>(Ap, A->ld, A->rows, k, (int)r, p, h->srht_diag,
+                                                                    h->srht_mu, c_lo, c_hi, sc, S, ldS);
+    }
+    note_launch();
+    JLS_CHECK_CUDA(cudaGetLastError());
+  }
   return SK_OK;
 }
 

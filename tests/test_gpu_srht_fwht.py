@@ -8,7 +8,10 @@ kept where it must win by a wide margin (FP32 CUDA-core product of 4096 rows,
 n = 16384, d = 256: about 34 GFLOP against one read of 268 MB).  Shapes cover
 one, two and four 16384-value segments (the top bits folded in while
 loading), zero padding (n not a power of two) and increments whose first
-column is not a multiple of 4.
+column is not a multiple of 4.  For n = k + r not a power of two, Sec. 7.1's
+split (transforms of orders k and p = 2^ceil(log2 r)) is checked against the
+oracle and against the zero-padded transform of the same shape, with the FWHT
+route pinned (JLS_SRHT_ROUTE=fwht).
 """
 import numpy as np
 import pytest
@@ -97,3 +100,33 @@ def test_fwht_identity_rows_give_R():
     A[np.arange(256), cols] = 1.0
     S, R = run(A, d, 17, jl.SK_PREC_NATIVE)
     assert np.array_equal(S.astype(np.float64), np.float32(R[cols]).astype(np.float64))
+
+
+SPLIT_SHAPES = [(512, 16384 + 3000, 256),   # k = 2^14, p = 4096
+                (300, 16384 + 1, 64),       # r = 1: p = 1
+                (256, 16384 + 8192, 128),   # r = 8192: the largest tail
+                (200, 32768 + 5000, 100),   # k = 2^15 (two segments), p = 8192
+                (256, 16384 + 8193, 64)]    # r > 8192: the zero-padded transform
+
+
+@pytest.mark.parametrize("rows,n,d", SPLIT_SHAPES)
+def test_fwht_split_parity(rows, n, d, monkeypatch):
+    jl = jlmod()
+    monkeypatch.setenv("JLS_SRHT_ROUTE", "fwht")
+    A = inputs.dense_matrix(rows, n, seed=n + 1).astype(np.float32)
+    S_split, R = run(A, d, 23 + n, jl.SK_PREC_NATIVE)
+    ref = A.astype(np.float64) @ R
+    assert rel_fro(S_split, ref) <= TOL["f32"]
+    monkeypatch.setenv("JLS_SRHT_SPLIT", "0")
+    S_pad, _ = run(A, d, 23 + n, jl.SK_PREC_NATIVE)
+    assert rel_fro(S_pad, ref) <= TOL["f32"]
+    assert rel_fro(S_split, S_pad) <= TOL["f32"]
+
+
+def test_fwht_split_increments_unaligned(monkeypatch):
+    jl = jlmod()
+    monkeypatch.setenv("JLS_SRHT_ROUTE", "fwht")
+    rows, n = 300, 16384 + 2500
+    A = inputs.dense_matrix(rows, n, seed=9).astype(np.float32)
+    S, R = run(A, 37, 29, jl.SK_PREC_NATIVE, incs=(10, 21))
+    assert rel_fro(S, A.astype(np.float64) @ R) <= TOL["f32"]
