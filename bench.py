@@ -345,24 +345,48 @@ def run_ours(args):
             "per_operator": per_op, "time_share": step_share, "roofline": roofline,
             "gpu_launches": int(launches), "clocks": clk}
 
-    # ---- end to end: A from pinned host memory, results back to the host
+    # ---- end to end: A from pinned host memory, results back to the host.  Every step copies
+    # its A to the device and its results back; the copies run on a copy stream into the other
+    # of two device buffers, so the next step's input and the previous step's results move
+    # while the current step computes (ordered by events).
     if not args.no_e2e:
         A_host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
         A_host.copy_(A)
-        step_e = Step(A, n, prec_dense, timed_events=False, only=args.only)
-        outs = list(step_e.bufs.values()) + [step_e.adS, step_e.adSt]
-        hosts = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        bufs_e = [A, torch.empty_like(A)]
+        steps_e = [Step(b, n, prec_dense, timed_events=False, only=args.only) for b in bufs_e]
+        outs = [list(se.bufs.values()) + [se.adS, se.adSt] for se in steps_e]
+        hosts = [[torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in oo] for oo in outs]
+        comp = torch.cuda.current_stream()
+        copy = torch.cuda.Stream()
+        in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+        computed = [None, None]
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+        e0.record(comp)
+        copy.wait_stream(comp)
+        with torch.cuda.stream(copy):
+            bufs_e[0].copy_(A_host, non_blocking=True)
+            in_ready[0].record(copy)
         p2 = 0
         for i in range(args.steps):
-            A.copy_(A_host, non_blocking=True)
-            p2 += step_e.run(1000 + i)
-            for o, hh in zip(outs, hosts):
-                hh.copy_(o, non_blocking=True)
-        e1.record()
+            b = i % 2
+            if i + 1 < args.steps:  # the next step's A, once the step that last used that buffer is done
+                with torch.cuda.stream(copy):
+                    if computed[1 - b] is not None:
+                        copy.wait_event(computed[1 - b])
+                    bufs_e[1 - b].copy_(A_host, non_blocking=True)
+                    in_ready[1 - b].record(copy)
+            comp.wait_event(in_ready[b])
+            p2 += steps_e[b].run(1000 + i)
+            computed[b] = torch.cuda.Event()
+            computed[b].record(comp)
+            with torch.cuda.stream(copy):  # this step's results back to the host
+                copy.wait_event(computed[b])
+                for o, hh in zip(outs[b], hosts[b]):
+                    hh.copy_(o, non_blocking=True)
+        comp.wait_stream(copy)
+        e1.record(comp)
         torch.cuda.synchronize()
         te = e0.elapsed_time(e1) / 1e3
         if world > 1:
@@ -371,8 +395,9 @@ def run_ours(args):
             te = float(t.item())
         line["e2e"] = {"value": round(bytes_a * p2 * world / te / 1e9, 1), "unit": "GB/s",
                        "h2d_bytes_per_step": bytes_a,
-                       "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs))}
-        del A_host, hosts
+                       "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs[0])),
+                       "overlap": "next step's H2D and previous step's D2H on a copy stream, two A buffers"}
+        del A_host, hosts, bufs_e, steps_e
 
     # ---- CPU baseline (oracle) on rank 0, N = 1 only; also checks the GPU results
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.only == "all":
