@@ -149,8 +149,8 @@ class Step:
             ad_passes = 2
             while True:
                 wd = d + w["dd"]
-                s1 = jl.adaptive_norm_test(h, 0, self.adS[:, :wd], w["dd"], w["eps_rel"], w["eps_abs"])
-                s2 = jl.adaptive_norm_test(h, 1, self.adSt[:, :wd], w["dd"], w["eps_rel"], w["eps_abs"])
+                s1, s2 = jl.adaptive_norm_test_pair(h, self.adS[:, :wd], self.adSt[:, :wd], w["dd"], w["eps_rel"],
+                                                    w["eps_abs"])
                 hist.append((d, s1[1] / s1[2], s2[1] / s2[2]))
                 if (s1[0] and s2[0]) or wd + w["dd"] > w["d_max"]:
                     converged = s1[0] and s2[0]

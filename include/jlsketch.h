@@ -179,6 +179,23 @@ int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, i
                        int32_t* stop, double* norm_hat, double* norm_tilde, void* stream);
 
 /*
+ * adaptive_norm_test_pair -- the test of adaptive_norm_test on S (slot 0) and
+ * on S' (slot 1) at once, for callers that sketch both (Algorithm 1 stops when
+ * both tests pass).  The S' test runs on a stream the handle owns, started
+ * after the work already queued on `stream`, the S test on `stream`; the two
+ * chains of small kernels overlap on the GPU.  Before returning, `stream` is
+ * made to wait for all of the S' test, so later work on `stream` (the next
+ * increment) is ordered after both.  rows_S / rows_St: rows of S and S';
+ * ldS, ldSt: their leading dimensions (>= d_total).  Host outputs: stop[2],
+ * norm_hat[2], norm_tilde[2] (index 0 for S, 1 for S'; the norm arrays may be
+ * NULL).  Synchronizes on the two norm copies only.  The results equal two
+ * adaptive_norm_test calls'.  Errors: as adaptive_norm_test.
+ */
+int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t ldS, const void* St, int64_t rows_St,
+                            int64_t ldSt, int32_t dtype, int32_t delta_d, double eps_rel, double eps_abs, int32_t* stop,
+                            double* norm_hat, double* norm_tilde, void* stream);
+
+/*
  * sketch_project_norms_noalloc -- the projection and norms of the stopping
  * test, for callers that cannot allocate device memory.  (The paper has no
  * counterpart: this is an interface variant of adaptive_norm_test's arithmetic.)

@@ -40,9 +40,12 @@ def adaptive_sketch(A, kind, d0: int, dd: int, alpha: int = 1, seed: int = 0, d_
         w = d + dd
         stop_s, nh_s, nt_s = (True, 0.0, 0.0)
         stop_t, nh_t, nt_t = (True, 0.0, 0.0)
-        if which & jl.SK_S:
+        if which == jl.SK_BOTH:  # the two tests overlap on two streams
+            (stop_s, nh_s, nt_s), (stop_t, nh_t, nt_t) = jl.adaptive_norm_test_pair(
+                h, S[:, :w], St[:, :w], dd, eps_rel, eps_abs, stream)
+        elif which & jl.SK_S:
             stop_s, nh_s, nt_s = jl.adaptive_norm_test(h, 0, S[:, :w], dd, eps_rel, eps_abs, stream)
-        if which & jl.SK_ST:
+        elif which & jl.SK_ST:
             stop_t, nh_t, nt_t = jl.adaptive_norm_test(h, 1, St[:, :w], dd, eps_rel, eps_abs, stream)
         stop = stop_s and stop_t
         history.append((d, stop, nh_s, nt_s, nh_t, nt_t))

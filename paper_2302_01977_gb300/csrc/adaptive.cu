@@ -378,20 +378,20 @@ struct Scratch {
   size_t part_elems;
 };
 
-int ensure_scratch(sk_op* h, int64_t rows, int dtype, int wmax, Scratch* sc, int nchunks) {
+int ensure_scratch(sk_op* h, int slot, int64_t rows, int dtype, int wmax, Scratch* sc, int nchunks) {
   const size_t es = elem_size(dtype);
   const size_t wb = ((size_t)rows * wmax * es + 255) / 256 * 256;
   const size_t part_elems = (size_t)nchunks * h->d_max * wmax;
   const size_t gb = (size_t)h->d_max * wmax * sizeof(double);
   const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 2 * NORM_GRID * sizeof(double);
-  if (h->scratch_bytes < need) {
-    if (h->scratch) cudaFree(h->scratch);
-    h->scratch = nullptr;
-    h->scratch_bytes = 0;
-    JLS_CHECK_CUDA(cudaMalloc(&h->scratch, need));
-    h->scratch_bytes = need;
+  if (h->scratch_bytes[slot] < need) {
+    if (h->scratch[slot]) cudaFree(h->scratch[slot]);
+    h->scratch[slot] = nullptr;
+    h->scratch_bytes[slot] = 0;
+    JLS_CHECK_CUDA(cudaMalloc(&h->scratch[slot], need));
+    h->scratch_bytes[slot] = need;
   }
-  uint8_t* p = static_cast<uint8_t*>(h->scratch);
+  uint8_t* p = static_cast<uint8_t*>(h->scratch[slot]);
   sc->W = p;
   p += wb;
   sc->part = reinterpret_cast<double*>(p);
@@ -489,11 +489,14 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
 // extension of Q by the QR of S^ (made at once, so that the next test, on the
 // next Delta-d columns, starts from the basis of every earlier column).
 // Columns of S before c_split that Q does not cover yet (the first d0, or
-// after a restart) are absorbed first.  The two norms are copied to pinned
-// host memory and read after an event, while the extension of Q runs on.
+// after a restart) are absorbed first.  The two norms are copied to the
+// slot's pinned host buffer and an event is recorded, while the extension of
+// Q runs on; norm_test_finish waits for that event.  Each slot (S, S') has its
+// own basis, scratch, host buffer and event, so the two tests can run on two
+// streams at once.
 template <typename T>
-int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
-                double eps_rel, double eps_abs, int* stop, double* nh, double* nt, cudaStream_t s) {
+int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
+                        cudaStream_t s) {
   Basis& B = h->basis[slot];
   if (!B.Q || B.rows != rows || B.dtype != dtype || c_split < B.covered) {
     if (B.Q) cudaFree(B.Q);
@@ -505,14 +508,14 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
     B.cols = 0;
     B.covered = 0;
   }
-  if (!h->host_norms) JLS_CHECK_CUDA(cudaMallocHost(&h->host_norms, 2 * NORM_GRID * sizeof(double)));
-  if (!h->norms_ready) JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->norms_ready, cudaEventDisableTiming));
+  if (!h->host_norms[slot]) JLS_CHECK_CUDA(cudaMallocHost(&h->host_norms[slot], 2 * NORM_GRID * sizeof(double)));
+  if (!h->norms_ready[slot]) JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->norms_ready[slot], cudaEventDisableTiming));
   const int bt = c_end - c_split;
   const int wmax = std::max(64, bt);
   if (bt > 512) return SK_ERR_UNSUPPORTED;
   const int nchunks = (int)std::min<int64_t>(64, (rows + 511) / 512);
   Scratch sc;
-  JLS_CHECK(ensure_scratch(h, rows, dtype, wmax, &sc, nchunks));
+  JLS_CHECK(ensure_scratch(h, slot, rows, dtype, wmax, &sc, nchunks));
   T* W = static_cast<T*>(sc.W);
   const unsigned cgrid = 152 * 4;
   // columns [covered, c_split) not in Q yet, 64 at a time
@@ -528,8 +531,9 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
   JLS_CHECK(project_twice<T>(h, B, W, wmax, bt, rows, sc, nchunks, s));
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms + NORM_GRID, s));
-  JLS_CHECK_CUDA(cudaMemcpyAsync(h->host_norms, sc.norms, 2 * NORM_GRID * sizeof(double), cudaMemcpyDeviceToHost, s));
-  JLS_CHECK_CUDA(cudaEventRecord(h->norms_ready, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(h->host_norms[slot], sc.norms, 2 * NORM_GRID * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s));
+  JLS_CHECK_CUDA(cudaEventRecord(h->norms_ready[slot], s));
   // extend Q by S^ (64 columns at a time; later chunks are first made
   // orthogonal to the chunks just added)
   for (int j0 = 0; j0 < bt; j0 += 64) {
@@ -537,11 +541,25 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
     JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, s));
   }
   B.covered = c_end;
-  JLS_CHECK_CUDA(cudaEventSynchronize(h->norms_ready));
+  return SK_OK;
+}
+
+}  // namespace
+
+int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
+                      int c_end, cudaStream_t s) {
+  if (dtype == SK_F32)
+    return norm_test_enqueue_t<float>(h, slot, (const float*)S, rows, ldS, dtype, c_split, c_end, s);
+  return norm_test_enqueue_t<double>(h, slot, (const double*)S, rows, ldS, dtype, c_split, c_end, s);
+}
+
+int norm_test_finish(sk_op* h, int slot, double eps_rel, double eps_abs, int* stop, double* nh, double* nt) {
+  JLS_CHECK_CUDA(cudaEventSynchronize(h->norms_ready[slot]));
   double t2 = 0, h2 = 0;
+  const double* hn = h->host_norms[slot];
   for (int i = 0; i < NORM_GRID; ++i) {  // fixed order: deterministic
-    t2 += h->host_norms[i];
-    h2 += h->host_norms[NORM_GRID + i];
+    t2 += hn[i];
+    h2 += hn[NORM_GRID + i];
   }
   *nt = std::sqrt(t2);
   *nh = std::sqrt(h2);
@@ -549,15 +567,10 @@ int norm_test_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int d
   return SK_OK;
 }
 
-}  // namespace
-
 int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
               double eps_rel, double eps_abs, int* stop, double* nh, double* nt, cudaStream_t s) {
-  if (dtype == SK_F32)
-    return norm_test_t<float>(h, slot, (const float*)S, rows, ldS, dtype, c_split, c_end, eps_rel, eps_abs, stop,
-                              nh, nt, s);
-  return norm_test_t<double>(h, slot, (const double*)S, rows, ldS, dtype, c_split, c_end, eps_rel, eps_abs, stop,
-                             nh, nt, s);
+  JLS_CHECK(norm_test_enqueue(h, slot, S, rows, ldS, dtype, c_split, c_end, s));
+  return norm_test_finish(h, slot, eps_rel, eps_abs, stop, nh, nt);
 }
 
 }  // namespace jls

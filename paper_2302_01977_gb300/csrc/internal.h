@@ -150,14 +150,16 @@ struct sk_op {
   int q8_cols = 0;
 
   jls::Basis basis[2];
-  void* scratch = nullptr;
-  size_t scratch_bytes = 0;
+  void* scratch[2] = {nullptr, nullptr};  // stopping-test scratch, per slot (S, S')
+  size_t scratch_bytes[2] = {0, 0};
   void* gen_scratch = nullptr;        // row blocks of a generated kernel matrix
   float* ksk_u = nullptr;             // kernel-sketch adjoint: second sums, n x 4
   size_t ksk_u_bytes = 0;
   size_t gen_scratch_bytes = 0;
-  double* host_norms = nullptr;       // pinned: the stopping test's norm partials
-  cudaEvent_t norms_ready = nullptr;  // recorded after their copy
+  double* host_norms[2] = {nullptr, nullptr};       // pinned: each slot's norm partials
+  cudaEvent_t norms_ready[2] = {nullptr, nullptr};  // recorded after their copy
+  cudaStream_t aux_stream = nullptr;                // the S' test of adaptive_norm_test_pair
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
 };
 
 namespace jls {
@@ -218,6 +220,10 @@ int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, 
 int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
               int c_end, double eps_rel, double eps_abs, int* stop, double* nh, double* nt,
               cudaStream_t s);
+// the same test in two parts: everything enqueued on s (no host wait), then the wait and the decision
+int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
+                      int c_end, cudaStream_t s);
+int norm_test_finish(sk_op* h, int slot, double eps_rel, double eps_abs, int* stop, double* nh, double* nt);
 
 // --- sjlt_apply.cu host helpers (also used by gemm_tc.cu) ---
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

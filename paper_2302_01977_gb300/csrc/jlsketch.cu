@@ -160,12 +160,17 @@ static void free_handle(sk_op* h) {
   void* ptrs[] = {h->d_err, h->sjlt_ents, h->ccs[0].ents, h->ccs[0].offs, h->ccs[1].ents, h->ccs[1].offs,
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
                   h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
-                  h->basis[0].Q, h->basis[1].Q, h->scratch, h->gen_scratch, h->ksk_u, h->ccs[2].ents,
-                  h->ccs[2].offs, h->sjlt_ents2};
+                  h->basis[0].Q, h->basis[1].Q, h->scratch[0], h->scratch[1], h->gen_scratch, h->ksk_u,
+                  h->ccs[2].ents, h->ccs[2].offs, h->sjlt_ents2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (h->host_norms) cudaFreeHost(h->host_norms);
-  if (h->norms_ready) cudaEventDestroy(h->norms_ready);
+  for (int k = 0; k < 2; ++k) {
+    if (h->host_norms[k]) cudaFreeHost(h->host_norms[k]);
+    if (h->norms_ready[k]) cudaEventDestroy(h->norms_ready[k]);
+  }
+  if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+  if (h->aux_join) cudaEventDestroy(h->aux_join);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   delete h;
 }
 
@@ -344,6 +349,39 @@ int adaptive_norm_test(sk_handle h, int32_t slot, const void* S, int64_t rows, i
   *stop = st;
   if (norm_hat) *norm_hat = nh;
   if (norm_tilde) *norm_tilde = nt;
+  return SK_OK;
+}
+
+int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t ldS, const void* St, int64_t rows_St,
+                            int64_t ldSt, int32_t dtype, int32_t delta_d, double eps_rel, double eps_abs, int32_t* stop,
+                            double* norm_hat, double* norm_tilde, void* stream) {
+  if (!h || !S || !St || !stop || rows_S < 1 || rows_St < 1 || ldS < h->d_total || ldSt < h->d_total)
+    return SK_ERR_INVALID_ARG;
+  if (dtype != SK_F32 && dtype != SK_F64) return SK_ERR_DTYPE;
+  if (delta_d < 1 || delta_d >= h->d_total) return SK_ERR_STATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->aux_stream) {
+    JLS_CHECK_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+    JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming));
+    JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->aux_join, cudaEventDisableTiming));
+  }
+  const int c_split = h->d_total - delta_d, c_end = h->d_total;
+  // the S' test on the handle's second stream, after the work already on `stream`
+  JLS_CHECK_CUDA(cudaEventRecord(h->aux_fork, s));
+  JLS_CHECK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->aux_fork, 0));
+  JLS_CHECK(norm_test_enqueue(h, 1, St, rows_St, ldSt, dtype, c_split, c_end, h->aux_stream));
+  JLS_CHECK(norm_test_enqueue(h, 0, S, rows_S, ldS, dtype, c_split, c_end, s));
+  // later work on `stream` waits for all of the S' test (its extension of Q included)
+  JLS_CHECK_CUDA(cudaEventRecord(h->aux_join, h->aux_stream));
+  JLS_CHECK_CUDA(cudaStreamWaitEvent(s, h->aux_join, 0));
+  int st[2] = {0, 0};
+  double nh[2] = {0, 0}, nt[2] = {0, 0};
+  for (int k = 0; k < 2; ++k) JLS_CHECK(norm_test_finish(h, k, eps_rel, eps_abs, &st[k], &nh[k], &nt[k]));
+  for (int k = 0; k < 2; ++k) {
+    stop[k] = st[k];
+    if (norm_hat) norm_hat[k] = nh[k];
+    if (norm_tilde) norm_tilde[k] = nt[k];
+  }
   return SK_OK;
 }
 

@@ -47,7 +47,7 @@ SK_BOTH = 3
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
 EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
-           "adaptive_norm_test", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
+           "adaptive_norm_test", "adaptive_norm_test_pair", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
            "sketch_kernel_adjoint", "sketch_batch_create", "sketch_batch_set", "sketch_batch_run",
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
            "sketch_batch_adaptive_result",
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         "sketch_apply": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
         "sketch_apply_increment": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
         "adaptive_norm_test": (i32, [vp, i32, vp, i64, i64, i32, i32, dbl, dbl, P(i32), P(dbl), P(dbl), vp]),
+        "adaptive_norm_test_pair": (i32, [vp, vp, i64, i64, vp, i64, i64, i32, i32, dbl, dbl, P(i32), P(dbl),
+                                          P(dbl), vp]),
         "sketch_project_norms_noalloc": (i32, [vp, i64, i32, vp, i64, i64, i32, i32, vp, i64, dbl, dbl, P(i32),
                                                P(dbl), P(dbl), vp]),
         "kernel_matrix": (i32, [P(SkMatrix), vp, i64, vp]),
@@ -240,6 +242,23 @@ def adaptive_norm_test(h, slot: int, S, delta_d: int, eps_rel: float, eps_abs: f
                                   ctypes.byref(nh), ctypes.byref(nt), _stream(stream))
     _check(rc, "adaptive_norm_test")
     return bool(stop.value), nh.value, nt.value
+
+
+def adaptive_norm_test_pair(h, S, St, delta_d: int, eps_rel: float, eps_abs: float, stream=None):
+    """Both tests at once (S on `stream`, S' on the handle's second stream); returns
+    ((stop, ||S^||, ||S~||) for S, the same for S')."""
+    _check_2d(S, "S")
+    _check_2d(St, "St")
+    if _dtype_code(S) != _dtype_code(St):
+        raise ValueError("S and St must have the same dtype")
+    stop = (ctypes.c_int32 * 2)()
+    nh = (ctypes.c_double * 2)()
+    nt = (ctypes.c_double * 2)()
+    rc = lib().adaptive_norm_test_pair(h, S.data_ptr(), S.shape[0], S.stride(0), St.data_ptr(), St.shape[0],
+                                       St.stride(0), _dtype_code(S), int(delta_d), float(eps_rel), float(eps_abs),
+                                       stop, nh, nt, _stream(stream))
+    _check(rc, "adaptive_norm_test_pair")
+    return (bool(stop[0]), nh[0], nt[0]), (bool(stop[1]), nh[1], nt[1])
 
 
 def sketch_project_norms_noalloc(Q, S_tilde, S_hat, eps_rel: float, eps_abs: float, stream=None):

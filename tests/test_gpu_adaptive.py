@@ -87,3 +87,41 @@ def test_flat_spectrum_runs_to_d_max():
                    eps_abs=1e-300)
     assert not res["converged"] and res["d"] == 64
     assert [hh[0] for hh in res["history"]] == [16, 32, 48]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_pair_equals_two_single_tests(dtype):
+    """adaptive_norm_test_pair (S and S' on two streams) returns what two
+    adaptive_norm_test calls return, increment after increment (same kernels,
+    same order of sums: equal to the last bit)."""
+    from paper_2302_01977_gb300 import jlsketch as jl
+    n, d0, dd, d_max = 640, 32, 32, 192
+    A = inputs.spectrum_matrix(n, 0.9 ** np.arange(n), seed=12)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Ad = dev_padded(A.astype(np.float64), tdt)
+    outs = []
+    for pair in (True, False):
+        h = jl.sketch_create("sjlt_block", n, d0 + dd, 4, 21, d_max)
+        try:
+            S = torch.zeros((n, d_max), dtype=tdt, device="cuda")
+            St = torch.zeros((n, d_max), dtype=tdt, device="cuda")
+            jl.sketch_apply(h, Ad, jl.SK_BOTH, 0, S=S, St=St)
+            res, w = [], d0 + dd
+            while w <= d_max:
+                if pair:
+                    r = jl.adaptive_norm_test_pair(h, S[:, :w], St[:, :w], dd, 1e-12, 0.0)
+                else:
+                    r = (jl.adaptive_norm_test(h, 0, S[:, :w], dd, 1e-12, 0.0),
+                         jl.adaptive_norm_test(h, 1, St[:, :w], dd, 1e-12, 0.0))
+                res.append(r)
+                if w + dd > d_max:
+                    break
+                jl.sketch_increment(h, dd)
+                jl.sketch_apply_increment(h, Ad, jl.SK_BOTH, 0, S=S, St=St)
+                w += dd
+            jl.sketch_device_status(h)
+            outs.append(res)
+        finally:
+            jl.sketch_destroy(h)
+    assert len(outs[0]) == len(outs[1]) == 5
+    assert outs[0] == outs[1]
