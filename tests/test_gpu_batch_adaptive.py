@@ -118,7 +118,8 @@ def test_adaptive_batch_matches_oracle(eps_rel):
 def test_adaptive_batch_small_increments_and_round_limit():
     dd, eps_rel, eps_abs = 16, 1e-3, 0.0
     specs = [("sjlt_block", 300, 8, 4, 6, 0.1, 1.0), ("sjlt_graph", 784, 48, 4, 6, 0.15, 1.0),
-             ("sjlt_block", 1200, 16, 4, 6, 0.25, 1.0)]
+             ("sjlt_block", 1200, 16, 4, 6, 0.25, 1.0),
+             ("sjlt_block", 272, 16, 4, 0, 0.05, 1.0)]  # no increment: one test, then out of columns
     inst = make(specs, dd, seed=77)
     items = [(x["op"].h, x["A"], x["St"], 0, x["d0"] + dd) for x in inst]
     with jl.Batch(items) as B:
