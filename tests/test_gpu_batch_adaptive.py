@@ -15,6 +15,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import adaptive as oad  # noqa: E402
+from oracle import operators as ops  # noqa: E402
 from paper_2302_01977_gb300 import inputs  # noqa: E402
 from paper_2302_01977_gb300 import jlsketch as jl  # noqa: E402
 from tests.util import ensure_built  # noqa: E402
@@ -191,3 +192,57 @@ def test_adaptive_batch_argument_checks():
         with pytest.raises(jl.JLSketchError):
             B.adaptive_run()  # no setup
     x["op"].close()
+
+
+def test_adaptive_batch_full_size_1024():
+    """The benchmark's batched adaptive workload in the launch configuration it
+    times: 1024 kernel matrices K(X_i, X_i; h_i), n_i over multiples of 64 in
+    [256, 4096], d0_i in {64, 128, 256}, dd = 32, eps_rel = 1e-6, up to 8
+    increments.  Every instance must end in a valid state (the width a whole
+    number of increments, the number of tests to match, converged only with
+    ||S^|| below eps_rel ||S~||, out of increments only at d_max); on sampled
+    small instances the final S'_i[:, :d_i] equals the FP64 A_i^T R_i[:, :d_i]
+    and the last test's norms equal the oracle's test on it."""
+    count, dd, incs, alpha, eps_rel, seed = 1024, 32, 8, 4, 1e-6, 20230203 + 3
+    rng = np.random.default_rng(seed)
+    ns = 64 * rng.integers(256 // 64, 4096 // 64 + 1, size=count)
+    hs = rng.uniform(0.05, 0.5, size=count)
+    d0s = rng.choice((64, 128, 256), size=count)
+    inst = []
+    for i in range(count):
+        n = int(ns[i])
+        X = torch.from_numpy(inputs.points(n, seed=seed + 17 * i)).cuda()
+        A = torch.empty((n, n), device="cuda")
+        jl.kernel_matrix(jl.generator(X, X, float(hs[i])), A)
+        d_max = int(d0s[i]) + (incs + 1) * dd
+        op = jl.Sketch("sjlt_block", n, int(d0s[i]) + dd, alpha, seed + i, d_max=d_max)
+        for _ in range(incs):
+            jl.sketch_increment(op.h, dd)
+        inst.append(dict(op=op, A=A, St=torch.empty((n, d_max), device="cuda"), n=n, d0=int(d0s[i]), d_max=d_max))
+    items = [(x["op"].h, x["A"], x["St"], 0, x["d0"] + dd) for x in inst]
+    with jl.Batch(items) as B:
+        B.adaptive_setup([x["d0"] for x in inst], dd, eps_rel, 0.0)
+        B.adaptive_run()
+        res = B.adaptive_result()
+    d, state, tests, nh, nt = res["d"], res["state"], res["tests"], res["nh"], res["nt"]
+    d0 = np.array([x["d0"] for x in inst])
+    d_max = np.array([x["d_max"] for x in inst])
+    assert set(np.unique(state)) <= {1, 2}
+    assert np.all((d - d0 - dd) % dd == 0) and np.all(d >= d0 + dd) and np.all(d <= d_max)
+    assert np.array_equal(tests, (d - d0 - dd) // dd + 1)
+    assert np.all(nt > 0)
+    assert np.all(nh[state == 1] < eps_rel * nt[state == 1])
+    assert np.all(d[state == 2] == d_max[state == 2])
+    small = [i for i in range(count) if inst[i]["n"] <= 512]
+    for i in np.random.default_rng(5).choice(small, 3, replace=False):
+        x, di = inst[i], int(d[i])
+        R = ops.Operator("sjlt_block", x["n"], x["d0"] + dd, alpha, seed + int(i))
+        for _ in range((di - x["d0"] - dd) // dd):
+            R.increment(dd)
+        ref = x["A"].double().cpu().numpy().T @ R.dense()
+        got = x["St"][:, :di].double().cpu().numpy()
+        assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), i
+        _, nh0, nt0 = oad.norm_test(ref, di - dd, dd, eps_rel, 0.0)
+        assert abs(nt[i] - nt0) <= TOL * nt0 and abs(nh[i] - nh0) <= TOL * nt0, (i, nh[i], nh0, nt[i], nt0)
+    for x in inst:
+        x["op"].close()

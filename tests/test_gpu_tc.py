@@ -152,3 +152,34 @@ def test_tc_rejects_fp64_and_sjlt():
         assert e.value.status == jl.SK_ERR_DTYPE
     finally:
         jl.sketch_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["srht", "gauss"])
+def test_full_size_bf16x2_sampled_rows(kind):
+    """The benchmark's n = 32768 FP32 kernel matrix (X != Y, h = 0.1), d = 256,
+    SK_PREC_BF16X2 as the benchmark runs it (the SRHT S product may take the row
+    FWHT, whichever route measured faster); the oracle recomputes 128 sampled
+    rows of S and of S' in FP64."""
+    from paper_2302_01977_gb300 import jlsketch as jl
+    w = inputs.WORKLOADS["kernel_fp32_n32768"]
+    n, d = w["n"], w["d"]
+    X = inputs.points(n, seed=w["seed"])
+    Y = inputs.points(n, seed=w["seed"] + 1000)
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    jl.kernel_matrix(jl.generator(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), w["h"]), A)
+    h = jl.sketch_create(kind, n, d, 1, w["seed"] + 3, d)
+    try:
+        S = torch.full((n, d), np.nan, dtype=torch.float32, device="cuda")
+        St = torch.full((n, d), np.nan, dtype=torch.float32, device="cuda")
+        jl.sketch_apply(h, A, jl.SK_S, jl.SK_PREC_BF16X2, S=S)
+        jl.sketch_apply(h, A, jl.SK_ST, jl.SK_PREC_BF16X2, St=St)
+        jl.sketch_device_status(h)
+    finally:
+        jl.sketch_destroy(h)
+    rows = np.sort(np.random.default_rng(2).choice(n, 128, replace=False))
+    R = ops.Operator(kind, n, d, 1, w["seed"] + 3).dense()
+    A_rows = osk.kernel_matrix(X[rows], Y, w["h"]).astype(np.float32).astype(np.float64)
+    A_cols = osk.kernel_matrix(X, Y[rows], w["h"]).T.astype(np.float32).astype(np.float64)
+    assert rel_fro(host(S)[rows], A_rows @ R) <= TOL["bf16x2"]
+    assert rel_fro(host(St)[rows], A_cols @ R) <= TOL["bf16x2"]
+    assert torch.isfinite(S).all() and torch.isfinite(St).all()
