@@ -40,6 +40,26 @@ WORKLOAD = dict(name="kernel_fp32_n32768", n=32768, d=256, alpha=4, h=0.1, seed=
                 d0=128, dd=64, d_max=512, eps_rel=1e-2, eps_abs=1e-8)
 
 
+# ---------------------------------------------------------------------------
+# Multi-rank bookkeeping (N independent replicas, one per GPU): the job's time
+# is the slowest rank's, and the job's value counts every rank's work.
+def reduce_time_max(elapsed: float, world: int, device) -> float:
+    """Max of `elapsed` over the ranks of the default process group (NCCL on
+    the GPUs, gloo on CPU); `elapsed` itself when world == 1."""
+    if world <= 1:
+        return float(elapsed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_pass: float, passes_per_rank: int, world: int, elapsed: float) -> float:
+    """GB/s of A for the whole job: all ranks' passes over their A / the job's time."""
+    return bytes_per_pass * passes_per_rank * world / elapsed / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -282,14 +302,9 @@ def run_ours(args):
         dist.barrier()
     launches = jl.sketch_launch_count() - launches0
     clk = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = reduce_time_max(t_start.elapsed_time(t_end) / 1e3, world, "cuda")
     bytes_a = n * n * 4
-    total_bytes = bytes_a * passes * world
-    value = total_bytes / elapsed / 1e9
+    value = job_value(bytes_a, passes, world, elapsed)
     times = kernel_times(step.events)
     hbm, bf16, bf16s, peak_kind = peaks()
 
@@ -388,12 +403,8 @@ def run_ours(args):
         comp.wait_stream(copy)
         e1.record(comp)
         torch.cuda.synchronize()
-        te = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        line["e2e"] = {"value": round(bytes_a * p2 * world / te / 1e9, 1), "unit": "GB/s",
+        te = reduce_time_max(e0.elapsed_time(e1) / 1e3, world, "cuda")
+        line["e2e"] = {"value": round(job_value(bytes_a, p2, world, te), 1), "unit": "GB/s",
                        "h2d_bytes_per_step": bytes_a,
                        "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs[0])),
                        "overlap": "next step's H2D and previous step's D2H on a copy stream, two A buffers"}
