@@ -423,6 +423,13 @@ int sketch_export(sk_handle h, int32_t* cols, int8_t* signs, int8_t* diag, int32
  * handle's device-side error flag: SK_OK, SK_ERR_TIMEOUT or SK_ERR_DEVICE. */
 int sketch_device_status(sk_handle h, void* stream);
 
+/* sketch_selftest_wait -- exercise the failure path of the device-side waits:
+ * one thread waits, with the same bounded wait the kernels use, on a barrier
+ * that nothing completes; after the limit (2 s) it sets the error flag and the
+ * kernel returns.  Expected result: SK_ERR_TIMEOUT, with the context still
+ * usable.  Synchronizes `stream`.  A diagnostic; the paper has no counterpart. */
+int sketch_selftest_wait(void* stream);
+
 /* sketch_launch_count -- number of kernels this library has launched in the
  * process so far (all handles); a diagnostic for counting device work. */
 int64_t sketch_launch_count(void);

@@ -385,6 +385,39 @@ int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t 
   return SK_OK;
 }
 
+// One thread waits, with the bounded wait every kernel of this library uses, on
+// an mbarrier that nothing arrives at: after WAIT_LIMIT_NS the wait gives up,
+// sets ERRF_TIMEOUT in the flag and the kernel returns.
+__global__ void selftest_wait_kernel(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err);
+}
+
+int sketch_selftest_wait(void* stream) {
+  JLS_CHECK(check_device());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d_err = nullptr;
+  JLS_CHECK_CUDA(cudaMalloc(&d_err, sizeof(int)));
+  int flag = 0;
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    selftest_wait_kernel<<<1, 32, 0, s>>>(d_err);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (flag & ERRF_TIMEOUT) return SK_ERR_TIMEOUT;
+  return flag ? SK_ERR_DEVICE : SK_OK;
+}
+
 int kernel_matrix(const sk_matrix* gen, void* A, int64_t ld, void* stream) {
   if (!gen || !A || !gen->X || !gen->Y || gen->rows < 1 || gen->cols < 1 || ld < gen->cols || !(gen->h > 0))
     return SK_ERR_INVALID_ARG;

@@ -52,7 +52,8 @@ EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_in
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
            "sketch_batch_adaptive_result",
            "sketch_batch_info", "sketch_batch_status", "sketch_batch_destroy", "sketch_dims", "sketch_export",
-           "sketch_device_status", "sketch_launch_count", "sketch_srht_route", "sketch_destroy",
+           "sketch_device_status", "sketch_selftest_wait", "sketch_launch_count", "sketch_srht_route",
+           "sketch_destroy",
            "sketch_strerror"]
 
 
@@ -115,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "sketch_batch_info": (i32, [vp, P(i32), P(i32), P(i64), P(ctypes.c_float)]),
         "sketch_batch_status": (i32, [vp, vp]),
         "sketch_batch_destroy": (None, [vp]),
+        "sketch_selftest_wait": (i32, [vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
         "sketch_device_status": (i32, [vp, vp]),
@@ -477,3 +479,8 @@ class Sketch:
             self.close()
         except Exception:
             pass
+
+
+def sketch_selftest_wait(stream=None) -> int:
+    """Run the bounded-wait self test; returns the status code (SK_ERR_TIMEOUT expected)."""
+    return int(lib().sketch_selftest_wait(_stream(stream)))

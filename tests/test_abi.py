@@ -96,6 +96,7 @@ def test_no_gpu_fails_loudly(L):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert L.sketch_create(ctypes.byref(h), jl.SK_GAUSS, 64, 16, 1, 1, 16, None) == jl.SK_ERR_DEVICE
+    assert L.sketch_selftest_wait(None) == jl.SK_ERR_DEVICE
     with pytest.raises(jl.JLSketchError):
         jl.sketch_create("gauss", 64, 16, stream=0)
 
