@@ -200,9 +200,9 @@ def test_adaptive_batch_full_size_1024():
     [256, 4096], d0_i in {64, 128, 256}, dd = 32, eps_rel = 1e-6, up to 8
     increments.  Every instance must end in a valid state (the width a whole
     number of increments, the number of tests to match, converged only with
-    ||S^|| below eps_rel ||S~||, out of increments only at d_max); on sampled
-    small instances the final S'_i[:, :d_i] equals the FP64 A_i^T R_i[:, :d_i]
-    and the last test's norms equal the oracle's test on it."""
+    ||S^|| below eps_rel ||S~||, out of increments only at d_max); on 16 sampled
+    instances (n_i <= 1024) the final S'_i[:, :d_i] equals the FP64
+    A_i^T R_i[:, :d_i] and the last test's norms equal the oracle's test on it."""
     count, dd, incs, alpha, eps_rel, seed = 1024, 32, 8, 4, 1e-6, 20230203 + 3
     rng = np.random.default_rng(seed)
     ns = 64 * rng.integers(256 // 64, 4096 // 64 + 1, size=count)
@@ -233,8 +233,8 @@ def test_adaptive_batch_full_size_1024():
     assert np.all(nt > 0)
     assert np.all(nh[state == 1] < eps_rel * nt[state == 1])
     assert np.all(d[state == 2] == d_max[state == 2])
-    small = [i for i in range(count) if inst[i]["n"] <= 512]
-    for i in np.random.default_rng(5).choice(small, 3, replace=False):
+    small = [i for i in range(count) if inst[i]["n"] <= 1024]
+    for i in np.random.default_rng(5).choice(small, 16, replace=False):
         x, di = inst[i], int(d[i])
         R = ops.Operator("sjlt_block", x["n"], x["d0"] + dd, alpha, seed + int(i))
         for _ in range((di - x["d0"] - dd) // dd):
