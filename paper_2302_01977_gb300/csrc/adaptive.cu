@@ -202,17 +202,20 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 
 // Cholesky G = L L^T of the b x b (b <= 64) FP64 Gram matrix, right-looking,
 // in arithmetic type A, with column dropping: a pivot <= 1e-26 of the largest
-// diagonal (or a zero Gram matrix) zeroes that column of L.  Writes L (lower,
+// diagonal, or <= tau times the sum of the nref partials in `ref` (the
+// block's sum of squares before its projection against Q), or a zero Gram
+// matrix zeroes that column of L.  Writes L (lower,
 // b x b row-major, type T, zeros above the diagonal) and rinv[j] = 1 / L[j][j]
 // (0 for a dropped column).  One CTA of 256 threads; the pivot of step k + 1
 // is taken by thread 0 while warps 1..7 finish step k's trailing update.
 template <typename A, typename T, int NR>
 __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restrict__ Gm, int b, T* __restrict__ Lo,
-                                                          T* __restrict__ rinv_out) {
+                                                          T* __restrict__ rinv_out, const double* __restrict__ ref,
+                                                          int nref, double tau) {
   __shared__ A L[64][65];
   __shared__ A rinv[64];
   __shared__ A s_sq[2], s_iv[2];
-  __shared__ A s_dmax;
+  __shared__ A s_dmax, s_floor;
   const int tid = threadIdx.x;
   for (int e = tid; e < b * b; e += 256) L[e / b][e % b] = (A)Gm[e];
   __syncthreads();
@@ -221,12 +224,17 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
     for (int i = tid; i < b; i += 32) m = fmax(m, L[i][i]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (tid == 0) s_dmax = m;
+    if (tid == 0) {
+      s_dmax = m;
+      double dref = 0;  // the block's sum of squares before its projection (fixed order)
+      for (int k = 0; k < nref; ++k) dref += ref[k];
+      s_floor = (A)(tau * dref);
+    }
   }
   __syncthreads();
   auto pivot = [&](int k) {  // thread 0 only
     const A dmax = s_dmax, pk = L[k][k];
-    const bool dk = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
+    const bool dk = !(pk > A(1e-26) * dmax) || !(pk > s_floor) || !(dmax > A(0));
     A iv = A(0);
     if (!dk) {
       if constexpr (sizeof(A) == 8) iv = rsqrt_nr<NR>(pk);
@@ -375,6 +383,7 @@ struct Scratch {
   double* G;      // up to d_max x wmax
   double* U;      // Cholesky factor (64 x 64) and reciprocal pivots (64), type T
   double* norms;  // 2 x NORM_GRID partials (||S~||^2, ||S^||^2)
+  double* ref;    // NORM_GRID partials: a block's sum of squares before its projection
   size_t part_elems;
 };
 
@@ -383,7 +392,7 @@ int ensure_scratch(sk_op* h, int slot, int64_t rows, int dtype, int wmax, Scratc
   const size_t wb = ((size_t)rows * wmax * es + 255) / 256 * 256;
   const size_t part_elems = (size_t)nchunks * h->d_max * wmax;
   const size_t gb = (size_t)h->d_max * wmax * sizeof(double);
-  const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 2 * NORM_GRID * sizeof(double);
+  const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 3 * NORM_GRID * sizeof(double);
   if (h->scratch_bytes[slot] < need) {
     if (h->scratch[slot]) cudaFree(h->scratch[slot]);
     h->scratch[slot] = nullptr;
@@ -401,6 +410,7 @@ int ensure_scratch(sk_op* h, int slot, int64_t rows, int dtype, int wmax, Scratc
   sc->U = reinterpret_cast<double*>(p);
   p += 64 * 65 * sizeof(double);
   sc->norms = reinterpret_cast<double*>(p);
+  sc->ref = sc->norms + 2 * NORM_GRID;
   sc->part_elems = part_elems;
   return SK_OK;
 }
@@ -461,20 +471,26 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
 // in FP32.
 template <typename T>
 int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
-                 bool project, cudaStream_t s) {
+                 bool project, const double* ref, cudaStream_t s) {
   if (project) JLS_CHECK(project_twice<T>(h, B, W, ldw, b, rows, sc, nchunks, s));
   T* Lf = reinterpret_cast<T*>(sc.U);
   T* rinv = Lf + 64 * 64;
   constexpr int RT = trsm_rows<T>();
   const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
+  // the first pass drops columns whose residual is at the data's noise level
+  // relative to the block before its projection (ref: NORM_GRID partials of
+  // its sum of squares): FP32 3.2e-6, FP64 1e-13
+  const double tau = sizeof(T) == 4 ? 1e-11 : 1e-26;
   for (int pass = 0; pass < 2; ++pass) {
     JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
+    const double* r = pass == 0 ? ref : nullptr;
+    const int nr = r ? NORM_GRID : 0;
     if (sizeof(T) == 8)
-      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
     else if (pass == 0)
-      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
     else
-      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv);
+      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
     note_launch();
     rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, ldw, b, Lf, rinv, rows); note_launch();
   }
@@ -522,7 +538,8 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   while (B.covered < c_split) {
     const int b = std::min(64, c_split - B.covered);
     copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b); note_launch();
-    JLS_CHECK(absorb_block<T>(h, B, W, 64, b, rows, sc, nchunks, true, s));
+    JLS_CHECK(sumsq_launch<T>(W, 64, rows, b, sc.ref, s));
+    JLS_CHECK(absorb_block<T>(h, B, W, 64, b, rows, sc, nchunks, true, sc.ref, s));
     B.covered += b;
   }
   // the test block: both norms summed on the device
@@ -538,7 +555,7 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   // orthogonal to the chunks just added)
   for (int j0 = 0; j0 < bt; j0 += 64) {
     const int b = std::min(64, bt - j0);
-    JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, s));
+    JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, sc.norms, s));
   }
   B.covered = c_end;
   return SK_OK;

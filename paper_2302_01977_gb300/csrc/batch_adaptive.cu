@@ -9,9 +9,10 @@
 // the first d0 columns are absorbed before the first test (32 at a time,
 // each block projected against Q, then two Cholesky-QR passes), and after a
 // failed test the projected S^ is absorbed, so the next test starts from the
-// basis of every earlier column.  A Cholesky pivot at or below 1e-26 of the
-// largest Gram diagonal drops its column (a zero column of Q, which leaves
-// Q Q^T unchanged).  The decision moves the instance's column range on by dd,
+// basis of every earlier column.  A Cholesky pivot at or below 1e-11 of the
+// block's sum of squares before the projection (its FP32 noise level), or
+// at or below 1e-26 of the largest Gram diagonal, drops its column (a zero
+// column of Q, which leaves Q Q^T unchanged).  The decision moves the instance's column range on by dd,
 // or retires it (converged, or no room left in R_i); a one-CTA kernel then
 // renumbers the units of the active instances for the next batched launch.
 // Nothing returns to the host between rounds, so a whole adaptive run, all
@@ -225,15 +226,20 @@ __device__ void qt_w(Ctx& c, int q) {
       cp_async_wait<0>();
     }
     __syncthreads();
-    if (act) {
+    if (act && g < rc) {
       const float* qb = Qs + (ch & 1) * (QCH / 4) + kg * 8;
       const float* wb = Ws + (ch & 1) * RCMAX * BW + cg4 * 8;
+      // the next row's operands are loaded while this row's products issue
+      float4 a0 = *reinterpret_cast<const float4*>(qb + g * q);
+      float4 a1 = *reinterpret_cast<const float4*>(qb + g * q + 4);
       for (int rr = g; rr < rc; rr += RG) {
-        const float4 a0 = *reinterpret_cast<const float4*>(qb + rr * q);
-        const float4 a1 = *reinterpret_cast<const float4*>(qb + rr * q + 4);
-        const float4 b0 = *reinterpret_cast<const float4*>(wb + rr * BW);
-        const float4 b1 = *reinterpret_cast<const float4*>(wb + rr * BW + 4);
-        fma8x8(acc, a0, a1, b0, b1);
+        const float4 c0 = a0, c1 = a1;
+        const float4 d0 = *reinterpret_cast<const float4*>(wb + rr * BW);
+        const float4 d1 = *reinterpret_cast<const float4*>(wb + rr * BW + 4);
+        const int rn = rr + RG < rc ? rr + RG : rr;
+        a0 = *reinterpret_cast<const float4*>(qb + rn * q);
+        a1 = *reinterpret_cast<const float4*>(qb + rn * q + 4);
+        fma8x8(acc, c0, c1, d0, d1);
       }
     }
     __syncthreads();
@@ -402,11 +408,12 @@ __device__ __forceinline__ A rsqrt_newton(A x) {
 }
 
 // 1/sqrt(p_k), or 0 (the column is dropped) for a pivot at or below 1e-26 of
-// the largest diagonal dmax or an all-zero matrix; kept out of line so that
-// it does not crowd the registers of the loops around its call
+// the largest diagonal dmax or at or below `floor`, or an all-zero matrix;
+// kept out of line so that it does not crowd the registers of the loops
+// around its call
 template <typename A>
-__device__ __noinline__ A chol_pivot(A pk, A dmax) {
-  const bool drop = !(pk > A(1e-26) * dmax) || !(dmax > A(0));
+__device__ __noinline__ A chol_pivot(A pk, A dmax, A floor) {
+  const bool drop = !(pk > A(1e-26) * dmax) || !(pk > floor) || !(dmax > A(0));
   return drop ? A(0) : rsqrt_newton<A>(pk);
 }
 
@@ -414,12 +421,12 @@ __device__ __noinline__ A chol_pivot(A pk, A dmax) {
 // leading dimension LDA, overwritten), by all AT threads.  Step k: thread 0
 // takes the pivot p_k (chol_pivot), then each element (i, j), k < j <= i, of
 // the trailing block gets one thread, L[i][j] -= L[i][k] L[j][k] / p_k
-// (column k is scaled by 1/sqrt(p_k) only at the end).  Writes the
-// factor as FP32 into Lf (leading dimension LF, zero above the diagonal and
+// (column k is scaled by 1/sqrt(p_k) only at the end).  A pivot at or
+// below `floor` also drops its column.  Writes the factor as FP32 into Lf (leading dimension LF, zero above the diagonal and
 // in dropped columns) and the reciprocal diagonal into rinv (0 for a dropped
 // column).  iv and u are shared scratch of BW entries each.
 template <typename A, int LDA>
-__device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u) {
+__device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u, A floor) {
   const int t = threadIdx.x;
   if (t < 32) {
     A v = L[t * LDA + t];
@@ -429,7 +436,7 @@ __device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u) {
   }
   __syncthreads();
   const A dmax = u[0];
-  auto pivot = [&](int k) { iv[k] = chol_pivot<A>(L[k * LDA + k], dmax); };  // thread 0
+  auto pivot = [&](int k) { iv[k] = chol_pivot<A>(L[k * LDA + k], dmax, floor); };  // thread 0
   __syncthreads();
   for (int k = 0; k < BW; ++k) {
     if (t == 0) pivot(k);
@@ -459,7 +466,7 @@ __device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u) {
 // first pass, where the Gram matrix squares W's condition number; FP32 in
 // the second, where it is the identity up to the first pass's rounding),
 // then W <- W L^{-T} row by row.
-__device__ void cholqr_pass(Ctx& c, bool fp64) {
+__device__ void cholqr_pass(Ctx& c, bool fp64, double floor) {
   double* gp = reinterpret_cast<double*>(c.stage);                 // [BW][BW], this CTA's partial
   float* Wc = reinterpret_cast<float*>(c.stage + BW * BW * 8);      // [2][GR][BW], double-buffered
   double* gg = reinterpret_cast<double*>(c.stage + BW * BW * 8 + 2 * GR * BW * 4);  // [4][BW][BW], the groups'
@@ -521,13 +528,13 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
   }
   cl_sync();  // the partials are overwritten after this
   if (fp64) {
-    chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW);
+    chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW, floor);
   } else {
     float* Lw = reinterpret_cast<float*>(c.stage);  // FP32 working copy (the partials are no longer read)
     for (int e = threadIdx.x; e < BW * BW; e += AT) Lw[(e >> 5) * LD + (e & 31)] = (float)c.gram[(e >> 5) * LD + (e & 31)];
     __syncthreads();
     float* fs = reinterpret_cast<float*>(c.cs);
-    chol_drop<float, LD>(Lw, c.Lf, c.rinv, fs, fs + BW);
+    chol_drop<float, LD>(Lw, c.Lf, c.rinv, fs, fs + BW, (float)floor);
   }
   // x_j = (w_j - sum_{m < j} x_m L[j][m]) / L[j][j], one row per thread
   for (int64_t r = c.r0 + threadIdx.x; r < c.r1; r += AT) {
@@ -561,10 +568,19 @@ __device__ void cholqr_pass(Ctx& c, bool fp64) {
   __syncthreads();
 }
 
-// Orthonormalize W's b columns (two Cholesky-QR passes) and append them to Q
-__device__ void absorb(Ctx& c, int& q, int b) {
-  cholqr_pass(c, true);
-  cholqr_pass(c, false);
+// Orthonormalize W's b columns (two Cholesky-QR passes) and append them to Q.
+// dref: the block's sum of squares before it was projected against Q.  A
+// column whose residual after the projection is at or below the FP32 noise
+// level of that block (pivot <= DROP_FP32 dref) lies in span(Q) as far as the
+// data can tell: normalizing it would turn rounding errors, which point along
+// Q, into a basis column, and Q would lose its orthogonality.  Such columns
+// are dropped (zero columns of Q).  The second pass sees normalized columns
+// and drops only numerically zero ones.
+constexpr double DROP_FP32 = 1e-11;  // (3.2e-6)^2: the residual relative to the block, FP32 data
+
+__device__ void absorb(Ctx& c, int& q, int b, double dref) {
+  cholqr_pass(c, true, DROP_FP32 * dref);
+  cholqr_pass(c, false, 0.0);
   // Q[:, q : q + b] <- W[:, :b], float4 at a time (b, q and the row pitch of Q are multiples of 8)
   const int f = threadIdx.x & 7;
   if (f < (b >> 2)) {
@@ -613,10 +629,9 @@ __global__ void __launch_bounds__(AT, 1)
   // columns before the tested block that Q does not cover yet (the first d0)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
-    load_block(c, S, ldS, covered, b);
-    __syncthreads();
+    const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
     project(c, q);
-    absorb(c, q, b);
+    absorb(c, q, b, dref);
     covered += b;
   }
   // the test, Eq. (3.1)
@@ -629,7 +644,7 @@ __global__ void __launch_bounds__(AT, 1)
   const bool stop = (nh < eps_abs) || (nh < eps_rel * nt);
   const bool room = c_end + dd <= T->d_cap;
   if (!stop && room) {  // Algorithm 1 goes on: Q <- [Q, orth(S^)]
-    absorb(c, q, dd);
+    absorb(c, q, dd, nt2);
     covered = c_end;
   }
   if (c.rank == 0 && threadIdx.x == 0) {

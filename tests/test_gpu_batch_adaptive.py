@@ -24,6 +24,12 @@ pytestmark = pytest.mark.gpu
 
 SENTINEL = 12345.0
 TOL = 1e-5
+# ||S^||_F computed in FP32 has a floor near 1e-5 ||S~||_F once the basis has hundreds of
+# columns: S' itself carries FP32 rounding (about 4e-7 relative per entry for these kernel
+# sums), each projection pass forms Q^T W and Q G in FP32 over up to 512 columns (about
+# sqrt(q) 2^-24 each), and Q is orthonormal to about 1e-5.  A block that lies in span(Q)
+# (the oracle's ||S^|| ~ 1e-28) therefore reads ~1e-5 ||S~||; the bound allows 5x that.
+TOL_NH_WIDE = 5e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -243,6 +249,7 @@ def test_adaptive_batch_full_size_1024():
         got = x["St"][:, :di].double().cpu().numpy()
         assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), i
         _, nh0, nt0 = oad.norm_test(ref, di - dd, dd, eps_rel, 0.0)
-        assert abs(nt[i] - nt0) <= TOL * nt0 and abs(nh[i] - nh0) <= TOL * nt0, (i, nh[i], nh0, nt[i], nt0)
+        assert abs(nt[i] - nt0) <= TOL * nt0, (i, nt[i], nt0)
+        assert abs(nh[i] - nh0) <= TOL_NH_WIDE * nt0, (i, nh[i], nh0, nt0)
     for x in inst:
         x["op"].close()
