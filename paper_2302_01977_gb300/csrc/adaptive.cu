@@ -5,9 +5,12 @@
 //   S^ = (I - Q Q^T)^2 S~,  stop = ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
 // Q is an orthonormal basis of the earlier sketch columns kept per handle and
 // slot.  New columns are absorbed 64 at a time: two block Gram-Schmidt passes
-// against Q, then two Cholesky-QR passes (Gram matrix and factor in FP64; a
-// pivot below 1e-13 of the largest drops that column, so a rank-deficient
-// block adds zero columns to Q, which do not change Q Q^T).
+// against Q, then two Cholesky-QR passes (Gram matrix and factor in FP64).
+// A column whose residual is at the data's noise level relative to the block
+// before its projection (a pivot at or below 1e-11 of that block's sum of
+// squares for FP32 data, 1e-26 for FP64) is dropped, so a rank-deficient
+// block adds zero columns to Q, which do not change Q Q^T: normalizing such
+// a residual, which is rounding error along Q, would cost Q its orthogonality.
 //
 // Tall-skinny products X^T Y (rows ~ n, widths <= 512) run on CUDA cores: each
 // CTA reduces a chunk of rows into a 64 x 64 tile of partial sums, chunks are
