@@ -364,8 +364,11 @@ int sketch_batch_status(sk_batch_handle b, void* stream);
  * batch was made, tunes the kernel shape for the first sketch and for the
  * increments (the tuning runs write the outputs), allocates each instance's
  * orthonormal basis (cols_i x (d_total_i - dd) FP32) and a cols_i x 32 block,
- * and leaves the batch's ranges at [0, d0[i] + dd).  Synchronizes `stream`.
- * Errors: INVALID_ARG, UNSUPPORTED, NOMEM, DEVICE.
+ * and leaves the batch's ranges at [0, d0[i] + dd).  The stopping test runs one
+ * CTA per instance when the batch has at least as many instances as the GPU
+ * has SMs, a thread-block cluster of 4 CTAs per instance otherwise (the
+ * environment variable JLS_ADAPT_CLUSTER=1, 2 or 4 overrides the choice).
+ * Synchronizes `stream`.  Errors: INVALID_ARG, UNSUPPORTED, NOMEM, DEVICE.
  */
 int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel, double eps_abs,
                                 void* stream);
