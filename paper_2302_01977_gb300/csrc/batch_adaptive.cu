@@ -6,15 +6,15 @@
 // S^ = (I - Q Q^T)^2 S~ (two block Gram-Schmidt passes, the remark after
 // Eq. (3.1)) and stops when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
 // Q is an orthonormal basis of the earlier columns, kept per instance in HBM:
-// the first d0 columns are absorbed before the first test (32 at a time,
-// each block projected against Q, then two Cholesky-QR passes), and after a
-// failed test the projected S^ is absorbed, so the next test starts from the
-// basis of every earlier column.  A Cholesky pivot at or below 1e-11 of the
-// block's sum of squares before the projection (its FP32 noise level), or
-// at or below 1e-26 of the largest Gram diagonal, drops its column (a zero
-// column of Q, which leaves Q Q^T unchanged).  The decision moves the instance's column range on by dd,
-// or retires it (converged, or no room left in R_i); a one-CTA kernel then
-// renumbers the units of the active instances for the next batched launch.
+// the first d0 columns are absorbed before the first test (32 at a time), and
+// after a failed test the projected S^ is absorbed, so the next test starts
+// from the basis of every earlier column.  Blocks are absorbed by [project,
+// Cholesky-QR] twice; a Cholesky pivot at or below 1e-13 of the block's sum of
+// squares before the projection (its FP32 noise level), or at or below 1e-26
+// of the largest Gram diagonal, drops its column (a zero column of Q, which
+// leaves Q Q^T unchanged).  The decision moves the instance's column range on
+// by dd, or retires it (converged, or no room left in R_i); a one-CTA kernel
+// then renumbers the units of the active instances for the next batched launch.
 // Nothing returns to the host between rounds, so a whole adaptive run, all
 // rounds, is one CUDA graph.
 //
@@ -568,18 +568,25 @@ __device__ void cholqr_pass(Ctx& c, bool fp64, double floor) {
   __syncthreads();
 }
 
-// Orthonormalize W's b columns (two Cholesky-QR passes) and append them to Q.
+// Orthonormalize W's b columns and append them to Q.  W arrives projected
+// against Q.  The first Cholesky-QR pass is followed by one more projection
+// against Q and the second pass ([project, Cholesky-QR] twice): the first
+// pass's FP32 triangular solve can magnify rounding along Q by the block's
+// condition number, and only a projection removes that again.
 // dref: the block's sum of squares before it was projected against Q.  A
-// column whose residual after the projection is at or below the FP32 noise
-// level of that block (pivot <= DROP_FP32 dref) lies in span(Q) as far as the
-// data can tell: normalizing it would turn rounding errors, which point along
-// Q, into a basis column, and Q would lose its orthogonality.  Such columns
-// are dropped (zero columns of Q).  The second pass sees normalized columns
-// and drops only numerically zero ones.
-constexpr double DROP_FP32 = 1e-11;  // (3.2e-6)^2: the residual relative to the block, FP32 data
+// column whose residual is at or below the FP32 noise level of that block
+// (pivot <= DROP_FP32 dref) lies in span(Q) as far as the data can tell:
+// normalizing it would turn rounding errors, which point along Q, into a
+// basis column.  Such columns are dropped (zero columns of Q).  The second
+// pass sees normalized columns and drops only numerically zero ones.
+constexpr double DROP_FP32 = 1e-13;  // (3.2e-7)^2: the residual relative to the block, FP32 data
 
 __device__ void absorb(Ctx& c, int& q, int b, double dref) {
   cholqr_pass(c, true, DROP_FP32 * dref);
+  if (q > 0) {
+    qt_w(c, q);
+    w_minus_qg(c, q);
+  }
   cholqr_pass(c, false, 0.0);
   // Q[:, q : q + b] <- W[:, :b], float4 at a time (b, q and the row pitch of Q are multiples of 8)
   const int f = threadIdx.x & 7;
@@ -630,7 +637,10 @@ __global__ void __launch_bounds__(AT, 1)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
     const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
-    project(c, q);
+    if (q > 0) {  // one pass here, the second inside absorb
+      qt_w(c, q);
+      w_minus_qg(c, q);
+    }
     absorb(c, q, b, dref);
     covered += b;
   }
