@@ -4,11 +4,11 @@
 // remark after it; Algorithm 1's S~ = last Delta-d columns):
 //   S^ = (I - Q Q^T)^2 S~,  stop = ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
 // Q is an orthonormal basis of the earlier sketch columns kept per handle and
-// slot.  New columns are absorbed 64 at a time: two block Gram-Schmidt passes
-// against Q, then two Cholesky-QR passes (Gram matrix and factor in FP64).
-// A column whose residual is at the data's noise level relative to the block
-// before its projection (a pivot at or below 1e-11 of that block's sum of
-// squares for FP32 data, 1e-26 for FP64) is dropped, so a rank-deficient
+// slot.  New columns are absorbed 64 at a time by [block Gram-Schmidt pass
+// against Q, Cholesky-QR pass] twice (the first Gram matrix and factor in
+// FP64).  A column whose residual is at the data's noise level relative to the
+// block before its projection (a pivot at or below 1e-13 of that block's sum
+// of squares for FP32 data, 1e-26 for FP64) is dropped, so a rank-deficient
 // block adds zero columns to Q, which do not change Q Q^T: normalizing such
 // a residual, which is rounding error along Q, would cost Q its orthogonality.
 //
@@ -445,17 +445,23 @@ int sub_qg(T* W, int64_t ldw, int b, const T* Q, int64_t ldq, int p, const doubl
   return SK_OK;
 }
 
-// W (rows x b, ld ldw) <- (I - Q Q^T)^2 W
+// W (rows x b, ld ldw) <- (I - Q Q^T)^passes W; project_twice: the test's two passes
 template <typename T>
-int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc,
-                  int nchunks, cudaStream_t s) {
+int project_passes(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc,
+                   int nchunks, int passes, cudaStream_t s) {
   if (B.cols == 0) return SK_OK;
   const T* Q = static_cast<const T*>(B.Q);
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     JLS_CHECK(tsgemm<T>(Q, h->d_max, B.cols, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
     JLS_CHECK(sub_qg<T>(W, ldw, b, Q, h->d_max, B.cols, sc.G, rows, s));
   }
   return SK_OK;
+}
+
+template <typename T>
+int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc,
+                  int nchunks, cudaStream_t s) {
+  return project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 2, s);
 }
 
 // NORM_GRID partial sums of squares of W into `part` (no synchronization)
@@ -466,25 +472,29 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
   return SK_OK;
 }
 
-// Orthonormalize the b <= 64 columns of W (ld ldw) by Cholesky QR twice and
-// append them to Q.  With `project`, W is first made orthogonal to Q by two
-// block Gram-Schmidt passes.  The first factorization is in FP64 (the Gram
-// matrix squares W's condition number); the second Gram matrix is the
-// identity up to the first pass's rounding, so with FP32 data it is factored
-// in FP32.
+// Orthonormalize the b <= 64 columns of W (ld ldw) and append them to Q, by
+// [project against Q, Cholesky-QR] twice.  With `project`, W arrives as it
+// is and the first projection is made here; without, W arrives projected
+// (the tested block, projected twice for the test).  The first factorization
+// is in FP64 (the Gram matrix squares W's condition number); the second Gram
+// matrix is the identity up to the first pass's rounding, so with FP32 data
+// it is factored in FP32.  The projection between the passes removes the
+// rounding along Q that the first pass's triangular solve magnifies by the
+// block's condition number.
 template <typename T>
 int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
                  bool project, const double* ref, cudaStream_t s) {
-  if (project) JLS_CHECK(project_twice<T>(h, B, W, ldw, b, rows, sc, nchunks, s));
+  if (project) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
   T* Lf = reinterpret_cast<T*>(sc.U);
   T* rinv = Lf + 64 * 64;
   constexpr int RT = trsm_rows<T>();
   const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
   // the first pass drops columns whose residual is at the data's noise level
   // relative to the block before its projection (ref: NORM_GRID partials of
-  // its sum of squares): FP32 3.2e-6, FP64 1e-13
-  const double tau = sizeof(T) == 4 ? 1e-11 : 1e-26;
+  // its sum of squares): FP32 3.2e-7, FP64 1e-13
+  const double tau = sizeof(T) == 4 ? 1e-13 : 1e-26;
   for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
     JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
     const double* r = pass == 0 ? ref : nullptr;
     const int nr = r ? NORM_GRID : 0;
