@@ -11,6 +11,10 @@
 // of squares for FP32 data, 1e-26 for FP64) is dropped, so a rank-deficient
 // block adds zero columns to Q, which do not change Q Q^T: normalizing such
 // a residual, which is rounding error along Q, would cost Q its orthogonality.
+// The tested block's second projection is the one between its two Cholesky-QR
+// passes: with W = (I - Q Q^T) S~ = W1 L1^T after the first pass,
+// ||S^||_F^2 = ||(I - Q Q^T) W1 L1^T||_F^2 = tr(L1 G2 L1^T), G2 the second
+// pass's Gram matrix, so a test costs two projections, not three.
 //
 // Tall-skinny products X^T Y (rows ~ n, widths <= 512) run on CUDA cores: each
 // CTA reduces a chunk of rows into a 64 x 64 tile of partial sums, chunks are
@@ -206,15 +210,15 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 // Cholesky G = L L^T of the b x b (b <= 64) FP64 Gram matrix, right-looking,
 // in arithmetic type A, with column dropping: a pivot <= 1e-26 of the largest
 // diagonal, or <= tau times the sum of the nref partials in `ref` (the
-// block's sum of squares before its projection against Q), or a zero Gram
-// matrix zeroes that column of L.  Writes L (lower,
+// block's sum of squares before its projection against Q), or <= floor_abs,
+// or a zero Gram matrix zeroes that column of L.  Writes L (lower,
 // b x b row-major, type T, zeros above the diagonal) and rinv[j] = 1 / L[j][j]
 // (0 for a dropped column).  One CTA of 256 threads; the pivot of step k + 1
 // is taken by thread 0 while warps 1..7 finish step k's trailing update.
 template <typename A, typename T, int NR>
 __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restrict__ Gm, int b, T* __restrict__ Lo,
                                                           T* __restrict__ rinv_out, const double* __restrict__ ref,
-                                                          int nref, double tau) {
+                                                          int nref, double tau, double floor_abs) {
   __shared__ A L[64][65];
   __shared__ A rinv[64];
   __shared__ A s_sq[2], s_iv[2];
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
       s_dmax = m;
       double dref = 0;  // the block's sum of squares before its projection (fixed order)
       for (int k = 0; k < nref; ++k) dref += ref[k];
-      s_floor = (A)(tau * dref);
+      s_floor = (A)fmax(tau * dref, floor_abs);
     }
   }
   __syncthreads();
@@ -380,6 +384,54 @@ namespace {
 
 constexpr int NORM_GRID = 256;
 
+// ||W2 L^T||_F^2 = tr(L G2 L^T) for the b x b factor L (row-major, type T,
+// zero above the diagonal) of the first Cholesky-QR pass and the FP64 Gram
+// matrix G2 = W2^T W2 of its projected output W2 = (I - Q Q^T) W L^{-T}:
+// with W the block after one projection, W2 L^T = (I - Q Q^T)^2 S~ up to the
+// dropped columns' residuals, so this is the test's ||S^||^2 without
+// projecting the block a second time before its factorization.  One CTA of
+// 256 threads; thread t takes column k = t % 64 of rows t / 64, t / 64 + 4,
+// ...; the sum is reduced in a fixed order into out[0], out[1 .. nout) = 0.
+template <typename T>
+__global__ void __launch_bounds__(256) lgl_trace_kernel(const T* __restrict__ L, const double* __restrict__ G2, int b,
+                                                        double* __restrict__ out, int nout) {
+  __shared__ double Gs[64][65];
+  __shared__ double red[8];
+  const int t = threadIdx.x;
+  for (int e = t; e < b * b; e += 256) Gs[e / b][e % b] = G2[e];
+  __syncthreads();
+  const int k = t & 63;
+  double acc = 0.0;
+  if (k < b) {
+    for (int i = t >> 6; i < b; i += 4) {
+      const T* Li = L + (int64_t)i * b;
+      double m = 0.0;  // (L G2)[i][k]
+      for (int j = 0; j <= i; ++j) m = fma((double)Li[j], Gs[j][k], m);
+      acc = fma(m, (double)Li[k], acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((t & 31) == 0) red[t >> 5] = acc;
+  __syncthreads();
+  if (t == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w];
+    out[0] = v > 0.0 ? v : 0.0;
+  }
+  for (int e = 1 + t; e < nout; e += 256) out[e] = 0.0;
+}
+
+// Where the tested block's ||S^||^2 goes once the second Gram matrix exists
+// (NORM_GRID partials after the ||S~||^2 ones), and the host copy of both.
+constexpr double kDropPass2 = 1e-2;
+
+struct TestOut {
+  double* norms;  // 2 x NORM_GRID: ||S~||^2 partials, then ||S^||^2
+  double* host;
+  cudaEvent_t ready;
+};
+
 struct Scratch {
   void* W;        // rows x wmax (T)
   double* part;   // partial products
@@ -475,15 +527,17 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
 // Orthonormalize the b <= 64 columns of W (ld ldw) and append them to Q, by
 // [project against Q, Cholesky-QR] twice.  With `project`, W arrives as it
 // is and the first projection is made here; without, W arrives projected
-// (the tested block, projected twice for the test).  The first factorization
-// is in FP64 (the Gram matrix squares W's condition number); the second Gram
-// matrix is the identity up to the first pass's rounding, so with FP32 data
-// it is factored in FP32.  The projection between the passes removes the
-// rounding along Q that the first pass's triangular solve magnifies by the
-// block's condition number.
+// (the later chunks of a wide tested block, projected twice for the test).
+// The first factorization is in FP64 (the Gram matrix squares W's condition
+// number); the second Gram matrix is the identity up to the first pass's
+// rounding, so with FP32 data it is factored in FP32.  The projection between
+// the passes removes the rounding along Q that the first pass's triangular
+// solve magnifies by the block's condition number.  With `test`, W is the
+// tested block and its ||S^||^2 is taken from the second Gram matrix
+// (lgl_trace_kernel), copied to the host with ||S~||^2 and signalled.
 template <typename T>
 int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
-                 bool project, const double* ref, cudaStream_t s) {
+                 bool project, const double* ref, cudaStream_t s, const TestOut* test = nullptr) {
   if (project) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
   T* Lf = reinterpret_cast<T*>(sc.U);
   T* rinv = Lf + 64 * 64;
@@ -491,19 +545,29 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
   const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
   // the first pass drops columns whose residual is at the data's noise level
   // relative to the block before its projection (ref: NORM_GRID partials of
-  // its sum of squares): FP32 3.2e-7, FP64 1e-13
+  // its sum of squares): FP32 3.2e-7, FP64 1e-13.  The second pass's columns
+  // had unit norm before the projection between the passes; one that it
+  // shrinks below 0.1 (pivot <= kDropPass2) was rounding along Q that the
+  // first pass normalized, and is dropped rather than renormalized.
   const double tau = sizeof(T) == 4 ? 1e-13 : 1e-26;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
     JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
+    if (pass == 1 && test) {  // Lf still holds the first pass's factor
+      lgl_trace_kernel<T><<<1, 256, 0, s>>>(Lf, sc.G, b, test->norms + NORM_GRID, NORM_GRID); note_launch();
+      JLS_CHECK_CUDA(cudaMemcpyAsync(test->host, test->norms, 2 * NORM_GRID * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+      JLS_CHECK_CUDA(cudaEventRecord(test->ready, s));
+    }
     const double* r = pass == 0 ? ref : nullptr;
     const int nr = r ? NORM_GRID : 0;
+    const double fa = pass == 0 ? 0.0 : kDropPass2;
     if (sizeof(T) == 8)
-      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
+      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
     else if (pass == 0)
-      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
+      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
     else
-      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau);
+      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
     note_launch();
     rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, ldw, b, Lf, rinv, rows); note_launch();
   }
@@ -518,9 +582,13 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
 // extension of Q by the QR of S^ (made at once, so that the next test, on the
 // next Delta-d columns, starts from the basis of every earlier column).
 // Columns of S before c_split that Q does not cover yet (the first d0, or
-// after a restart) are absorbed first.  The two norms are copied to the
-// slot's pinned host buffer and an event is recorded, while the extension of
-// Q runs on; norm_test_finish waits for that event.  Each slot (S, S') has its
+// after a restart) are absorbed first.  A tested block of up to 64 columns is
+// projected once, factored, projected again, and ||S^||^2 = tr(L1 G2 L1^T)
+// comes from the first factor and the second Gram matrix (lgl_trace_kernel);
+// a wider one is projected twice and its norm summed before it is absorbed.
+// The two norms are copied to the slot's pinned host buffer and an event is
+// recorded, while the extension of Q runs on; norm_test_finish waits for
+// that event.  Each slot (S, S') has its
 // own basis, scratch, host buffer and event, so the two tests can run on two
 // streams at once.
 template <typename T>
@@ -559,6 +627,12 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
+  if (bt <= 64) {  // one chunk: ||S^|| from its absorption's second Gram matrix
+    const TestOut out{sc.norms, h->host_norms[slot], h->norms_ready[slot]};
+    JLS_CHECK(absorb_block<T>(h, B, W, wmax, bt, rows, sc, nchunks, true, sc.norms, s, &out));
+    B.covered = c_end;
+    return SK_OK;
+  }
   JLS_CHECK(project_twice<T>(h, B, W, wmax, bt, rows, sc, nchunks, s));
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms + NORM_GRID, s));
   JLS_CHECK_CUDA(cudaMemcpyAsync(h->host_norms[slot], sc.norms, 2 * NORM_GRID * sizeof(double), cudaMemcpyDeviceToHost,

@@ -5,6 +5,9 @@
 // [c_hi - dd, c_hi) of S'_i, the test takes S~ = those dd columns,
 // S^ = (I - Q Q^T)^2 S~ (two block Gram-Schmidt passes, the remark after
 // Eq. (3.1)) and stops when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
+// The two passes are those of S~'s own absorption: S~ is projected, factored
+// (W = W1 L1^T), projected again, and ||S^||_F^2 = tr(L1 G2 L1^T) with G2 the
+// Gram matrix of (I - Q Q^T) W1, so a test costs two projections.
 // Q is an orthonormal basis of the earlier columns, kept per instance in HBM:
 // the first d0 columns are absorbed before the first test (32 at a time), and
 // after a failed test the projected S^ is absorbed, so the next test starts
@@ -155,20 +158,6 @@ __device__ double load_block(const Ctx& c, const float* S, int64_t ldS, int c0, 
     ss = fmaf(v, v, ss);
   }
   return (double)ss;
-}
-
-// the thread's share of the sum of squares of W on this CTA's rows (float4 loads)
-__device__ double sumsq_w(const Ctx& c) {
-  constexpr int RS = AT / 8;
-  const float4* W4 = reinterpret_cast<const float4*>(c.W);
-  const int f = threadIdx.x & 7;
-  float s0 = 0.f, s1 = 0.f;
-  for (int64_t r = c.r0 + (threadIdx.x >> 3); r < c.r1; r += RS) {
-    const float4 v = W4[r * (BW / 4) + f];
-    s0 = fmaf(v.x, v.x, fmaf(v.y, v.y, s0));
-    s1 = fmaf(v.z, v.z, fmaf(v.w, v.w, s1));
-  }
-  return (double)(s0 + s1);
 }
 
 // Gs <- Q[:, :q]^T W over all rows of S'_i (q a multiple of 8, <= QMAX), in
@@ -383,15 +372,6 @@ __device__ void w_minus_qg(const Ctx& c, int q) {
   }
 }
 
-// W <- (I - Q Q^T)^2 W
-__device__ void project(Ctx& c, int q) {
-  if (q == 0) return;
-  for (int pass = 0; pass < 2; ++pass) {
-    qt_w(c, q);
-    w_minus_qg(c, q);
-  }
-}
-
 // 1/sqrt(x) for x > 0: the FP32 estimate refined by Newton steps
 // y <- y (3 - x y^2) / 2 in type A (two in FP64, none in FP32)
 template <typename A>
@@ -460,13 +440,10 @@ __device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u, A floor) {
   __syncthreads();
 }
 
-// One Cholesky-QR pass on the b <= BW columns of W (the rest are zero):
-// the Gram matrix over all rows (FP32 runs of 4 GR rows added in FP64, the
-// CTAs' partials added in rank order in every CTA), its factor (FP64 in the
-// first pass, where the Gram matrix squares W's condition number; FP32 in
-// the second, where it is the identity up to the first pass's rounding),
-// then W <- W L^{-T} row by row.
-__device__ void cholqr_pass(Ctx& c, bool fp64, double floor) {
+// c.gram <- W^T W for the b <= BW columns of W (the rest are zero), over all
+// rows: FP32 runs of 4 GR rows added in FP64, the CTAs' partials added in rank
+// order in every CTA.
+__device__ void gram_pass(Ctx& c) {
   double* gp = reinterpret_cast<double*>(c.stage);                 // [BW][BW], this CTA's partial
   float* Wc = reinterpret_cast<float*>(c.stage + BW * BW * 8);      // [2][GR][BW], double-buffered
   double* gg = reinterpret_cast<double*>(c.stage + BW * BW * 8 + 2 * GR * BW * 4);  // [4][BW][BW], the groups'
@@ -527,6 +504,12 @@ __device__ void cholqr_pass(Ctx& c, bool fp64, double floor) {
     c.gram[(e >> 5) * LD + (e & 31)] = s;
   }
   cl_sync();  // the partials are overwritten after this
+}
+
+// The factor of c.gram (FP64 in the first Cholesky-QR pass, where the Gram
+// matrix squares W's condition number; FP32 in the second, where it is the
+// identity up to the first pass's rounding), then W <- W L^{-T} row by row.
+__device__ void factor_solve(Ctx& c, bool fp64, double floor) {
   if (fp64) {
     chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW, floor);
   } else {
@@ -568,27 +551,63 @@ __device__ void cholqr_pass(Ctx& c, bool fp64, double floor) {
   __syncthreads();
 }
 
-// Orthonormalize W's b columns and append them to Q.  W arrives projected
-// against Q.  The first Cholesky-QR pass is followed by one more projection
-// against Q and the second pass ([project, Cholesky-QR] twice): the first
-// pass's FP32 triangular solve can magnify rounding along Q by the block's
-// condition number, and only a projection removes that again.
+// Orthonormalize W's b columns and append them to Q by [project against Q,
+// Cholesky-QR] twice: the first pass's FP32 triangular solve can magnify
+// rounding along Q by the block's condition number, and only a projection
+// removes that again.
 // dref: the block's sum of squares before it was projected against Q.  A
 // column whose residual is at or below the FP32 noise level of that block
 // (pivot <= DROP_FP32 dref) lies in span(Q) as far as the data can tell:
 // normalizing it would turn rounding errors, which point along Q, into a
-// basis column.  Such columns are dropped (zero columns of Q).  The second
-// pass sees normalized columns and drops only numerically zero ones.
+// basis column.  Such columns are dropped (zero columns of Q).
+// The second pass's input columns have unit norm (or are zero) before the
+// projection between the passes.  A column that this projection shrinks below
+// 0.1 of its length (pivot <= DROP_PASS2) was mostly rounding along Q that the
+// first pass normalized: renormalizing what is left would make a basis column
+// that is not orthogonal to Q, so it is dropped as well.  What it can hold of
+// S~ itself is below the FP32 resolution of the test (about 1e-7 of S~'s
+// column, with one projection in front of the first pass).
 constexpr double DROP_FP32 = 1e-13;  // (3.2e-7)^2: the residual relative to the block, FP32 data
+constexpr double DROP_PASS2 = 1e-2;
 
-__device__ void absorb(Ctx& c, int& q, int b, double dref) {
-  cholqr_pass(c, true, DROP_FP32 * dref);
+// W arrives as it is: [project, Cholesky-QR (with the drop rule)], then the
+// second projection and its Gram matrix; absorb_end finishes the pass.
+__device__ void absorb_begin(Ctx& c, int q, double dref) {
   if (q > 0) {
     qt_w(c, q);
     w_minus_qg(c, q);
   }
-  cholqr_pass(c, false, 0.0);
-  // Q[:, q : q + b] <- W[:, :b], float4 at a time (b, q and the row pitch of Q are multiples of 8)
+  gram_pass(c);
+  factor_solve(c, true, DROP_FP32 * dref);
+  if (q > 0) {
+    qt_w(c, q);
+    w_minus_qg(c, q);
+  }
+  gram_pass(c);
+}
+
+// tr(L1 G2 L1^T), L1 the first pass's factor (c.Lf) and G2 the second Gram
+// matrix (c.gram): with the projected block W = W1 L1^T, this is
+// ||(I - Q Q^T) W||_F^2 = ||(I - Q Q^T)^2 S~||_F^2 up to the residuals of
+// dropped columns.  Every CTA of the cluster holds the same L1 and G2 and
+// sums in the same order, so all of them get the same value.
+__device__ double lgl_trace(Ctx& c) {
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < BW * BW; e += AT) {
+    const int i = e / BW, k = e % BW;
+    double m = 0.0;  // (L1 G2)[i][k]
+    for (int j = 0; j <= i; ++j) m = fma((double)c.Lf[i * LF + j], c.gram[j * LD + k], m);
+    acc = fma(m, (double)c.Lf[i * LF + k], acc);
+  }
+  const double v = cta_sum(acc, c.red);
+  return v > 0.0 ? v : 0.0;
+}
+
+// The second Cholesky-QR pass on the output of absorb_begin, then
+// Q[:, q : q + b] <- W[:, :b].
+__device__ void absorb_end(Ctx& c, int& q, int b) {
+  factor_solve(c, false, DROP_PASS2);
+  // float4 at a time (b, q and the row pitch of Q are multiples of 8)
   const int f = threadIdx.x & 7;
   if (f < (b >> 2)) {
     const float4* W4 = reinterpret_cast<const float4*>(c.W);
@@ -637,24 +656,21 @@ __global__ void __launch_bounds__(AT, 1)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
     const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
-    if (q > 0) {  // one pass here, the second inside absorb
-      qt_w(c, q);
-      w_minus_qg(c, q);
-    }
-    absorb(c, q, b, dref);
+    absorb_begin(c, q, dref);
+    absorb_end(c, q, b);
     covered += b;
   }
-  // the test, Eq. (3.1)
+  // the test, Eq. (3.1): its two projections are those of the absorption
   const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
-  project(c, q);
-  const double nh2 = cluster_sum(c, sumsq_w(c));
+  absorb_begin(c, q, nt2);
+  const double nh2 = lgl_trace(c);
   const int blocks = 1 + (c_end - T->first_w) / dd;
   const double sc = 1.0 / sqrt((double)blocks);
   const double nh = sqrt(nh2) * sc, nt = sqrt(nt2) * sc;
   const bool stop = (nh < eps_abs) || (nh < eps_rel * nt);
   const bool room = c_end + dd <= T->d_cap;
   if (!stop && room) {  // Algorithm 1 goes on: Q <- [Q, orth(S^)]
-    absorb(c, q, dd, nt2);
+    absorb_end(c, q, dd);
     covered = c_end;
   }
   if (c.rank == 0 && threadIdx.x == 0) {
