@@ -270,7 +270,7 @@ def run_ours(args):
     prec_dense = jl.SK_PREC_BF16X2 if args.prec == "bf16x2" else jl.SK_PREC_NATIVE
     if args.prec == "auto":
         prec_dense = jl.SK_PREC_NATIVE
-        try:  # use the tensor-core path when this build provides it
+        try:  # use the tensor-core path when the library provides it
             h = jl.sketch_create("gauss", 1024, 64, 1, 1, 64)
             T = torch.zeros((1024, 1024), device="cuda")
             O = torch.zeros((1024, 64), device="cuda")

@@ -51,7 +51,7 @@ extern "C" {
 #define SK_ERR_STATE         -6  /* call out of order (e.g. increment apply before increment) */
 #define SK_ERR_TIMEOUT       -7  /* a bounded device-side wait gave up */
 #define SK_ERR_DEVICE        -8  /* CUDA error or device-side error flag */
-#define SK_ERR_UNSUPPORTED   -9  /* valid request this build does not implement */
+#define SK_ERR_UNSUPPORTED   -9  /* valid request this library does not implement */
 
 /* ---- operator kinds (Sec. 2.4) ------------------------------------------ */
 #define SK_SJLT_GRAPH 1  /* alpha distinct positions uniform in each row's block  */

@@ -17,7 +17,7 @@ Operators and the sections they follow:
 * Increments (Sec. 6.2 "Adaptive SJLT sketching", Algorithm 1): Delta-d columns
   are appended and the scaling factor adjusted.
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
 
 * Random streams: Philox4x64-10 keyed by (seed, tag), see ``oracle.rng``.
   SJLT row i, block b: draws t = 0, 1, 2, ... at counter (i, t, 0, 0) with key

@@ -191,7 +191,7 @@ const char* sketch_strerror(int status) {
     case SK_ERR_STATE: return "call out of order";
     case SK_ERR_TIMEOUT: return "device-side wait timed out";
     case SK_ERR_DEVICE: return "CUDA or device-side error";
-    case SK_ERR_UNSUPPORTED: return "not supported by this build";
+    case SK_ERR_UNSUPPORTED: return "not supported by this library";
     default: return "unknown status";
   }
 }
