@@ -390,25 +390,38 @@ constexpr int NORM_GRID = 256;
 // with W the block after one projection, W2 L^T = (I - Q Q^T)^2 S~ up to the
 // dropped columns' residuals, so this is the test's ||S^||^2 without
 // projecting the block a second time before its factorization.  One CTA of
-// 256 threads; thread t takes column k = t % 64 of rows t / 64, t / 64 + 4,
-// ...; the sum is reduced in a fixed order into out[0], out[1 .. nout) = 0.
+// 256 threads; thread t takes row i = t / 4 of L G2 in the data's type T (FP32
+// for FP32 data: each term l_i^T G2 l_i = ||W2 l_i||^2 is a sum of nonnegative
+// parts up to rounding) with its 16 columns k = 16 (t % 4) + 0..15 as 16
+// independent accumulation chains, then dots them with row i of L in FP64;
+// the sum is reduced in a fixed order into out[0], out[1 .. nout) = 0.
 template <typename T>
 __global__ void __launch_bounds__(256) lgl_trace_kernel(const T* __restrict__ L, const double* __restrict__ G2, int b,
                                                         double* __restrict__ out, int nout) {
-  __shared__ double Gs[64][65];
+  __shared__ __align__(16) T Gs[64][64];
   __shared__ double red[8];
   const int t = threadIdx.x;
-  for (int e = t; e < b * b; e += 256) Gs[e / b][e % b] = G2[e];
+  for (int e = t; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    Gs[r][c] = (r < b && c < b) ? (T)G2[r * b + c] : (T)0;
+  }
   __syncthreads();
-  const int k = t & 63;
+  const int i = t >> 2, k0 = 16 * (t & 3);
   double acc = 0.0;
-  if (k < b) {
-    for (int i = t >> 6; i < b; i += 4) {
-      const T* Li = L + (int64_t)i * b;
-      double m = 0.0;  // (L G2)[i][k]
-      for (int j = 0; j <= i; ++j) m = fma((double)Li[j], Gs[j][k], m);
-      acc = fma(m, (double)Li[k], acc);
+  if (i < b) {
+    const T* Li = L + (int64_t)i * b;
+    T m[16];  // (L G2)[i][k0 + kk]
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) m[kk] = (T)0;
+#pragma unroll 4
+    for (int j = 0; j <= i; ++j) {
+      const T lj = Li[j];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) m[kk] = fma(lj, Gs[j][k0 + kk], m[kk]);
     }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+      if (k0 + kk <= i) acc = fma((double)m[kk], (double)Li[k0 + kk], acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
