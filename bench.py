@@ -621,7 +621,9 @@ def run_batching(args):
     and Delta-d = 32.  One batched launch sketches Algorithm 1's first d0_i + 32
     columns of every instance; then increments of 32 columns run as replays of a
     captured CUDA graph of the same launch.  value = bytes of all A_i streamed per
-    run / run time (A_i is symmetric, so S_i = A_i R_i = A_i^T R_i)."""
+    run / run time (A_i is symmetric, so S_i = A_i R_i = A_i^T R_i).  The same
+    instances are then sketched with SRHT operators by the batched row transform
+    (first sketch and graph-replayed increments, reported under "srht")."""
     import numpy as np
     import torch
 
@@ -706,9 +708,54 @@ def run_batching(args):
         B.set(None, [int(d0) + r * dd for d0 in d0s], [int(d0) + (r + 1) * dd for d0 in d0s])
         inc_ms.append(timed(g.replay, args.steps))
     B.status()
+    B.close()
+    # the same instances with SRHT operators: S_i = A_i R_i by the batched row transform
+    # (A_i symmetric, so S_i = A_i^T R_i as above); an SRHT samples at most nu_i columns
+    sr_ops, sr_items, sr_d0 = [], [], []
+    for i in range(w["count"]):
+        n = int(ns[i])
+        nu = 1 << (n - 1).bit_length()
+        d0 = min(int(d0s[i]), nu - (R + 1) * dd)
+        op = jl.Sketch("srht", n, d0 + dd, 1, w["seed"] + i, d_max=d0 + (R + 1) * dd)
+        for _ in range(R):
+            jl.sketch_increment(op.h, dd)
+        sr_ops.append(op)
+        sr_d0.append(d0)
+        sr_items.append((op.h, As[i], Sts[i], 0, d0 + dd))
+    SB = jl.SrhtBatch(sr_items)
+    sr_first_info = SB.info()
+    sr_first = timed(SB.run, args.steps)
+    sr_errs = []
+    for i in rng.choice(w["count"], 4, replace=False):
+        Rd = jl.sketch_export(sr_ops[i].h, dense=True)["R"]
+        hi = sr_d0[i] + dd
+        ref = (As[i].double().cpu().numpy() @ Rd)[:, :hi]
+        got = Sts[i][:, :hi].double().cpu().numpy()
+        sr_errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    SB.set([d0 + dd for d0 in sr_d0], [d0 + 2 * dd for d0 in sr_d0])
+    s2 = torch.cuda.Stream()
+    g2 = torch.cuda.CUDAGraph()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g2, stream=s2):
+        SB.run(stream=s2)
+    sr_inc = []
+    for r in range(1, R + 1):
+        torch.cuda.synchronize()
+        SB.set([d0 + r * dd for d0 in sr_d0], [d0 + (r + 1) * dd for d0 in sr_d0])
+        sr_inc.append(timed(g2.replay, args.steps))
+    SB.close()
+    for op in sr_ops:
+        op.close()
     ck = clocks.stop()
     hbm, _, _, peak_kind = peaks()
     t_inc = statistics.median(inc_ms)
+    t_sr_inc = statistics.median(sr_inc)
+    srht = {"first_sketch_ms": round(sr_first, 3), "first_sketch_gbs": round(bytes_a / sr_first / 1e6, 1),
+            "first_sketch_pct_hbm": round(100 * bytes_a / sr_first / 1e6 / hbm, 1),
+            "increment_graph_replay_ms": round(t_sr_inc, 3), "increment_gbs": round(bytes_a / t_sr_inc / 1e6, 1),
+            "increment_pct_hbm": round(100 * bytes_a / t_sr_inc / 1e6 / hbm, 1), "autotune": sr_first_info,
+            "rel_err_vs_fp64_sample": [float(f"{e:.3e}") for e in sr_errs],
+            "d0_cap": "d0_i <= nu_i - (increments + 1) * dd"}
     line = {"metric": METRIC, "value": round(bytes_a / t_first / 1e6, 1), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_first, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
@@ -722,8 +769,7 @@ def run_batching(args):
             "launches_per_run": launches_first, "autotune_first": first_info, "autotune_increment": info,
             "batch_create_s": round(t_create, 2),
             "rel_err_vs_fp64_sample": [float(f"{e:.3e}") for e in errs], "peak_source": peak_kind,
-            "gpu_launches": int(launches_first * args.steps), "clocks": ck}
-    B.close()
+            "gpu_launches": int(launches_first * args.steps), "clocks": ck, "srht": srht}
     for op in ops:
         op.close()
     print(json.dumps(line))

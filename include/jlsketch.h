@@ -405,6 +405,71 @@ int sketch_batch_adaptive_result(sk_batch_handle b, int32_t* d_reached, int32_t*
  * not freed. */
 void sketch_batch_destroy(sk_batch_handle b);
 
+/* ---- batches of SRHT sketches: S_i = A_i R_i in one launch ------------------
+ *
+ * The SRHT of Sec. 2.4.2 applied through the row transform of Sec. 7.1: row r
+ * of A_i, sign-flipped by D_i and zero-padded to nu_i = 2^ceil(log2 n_i), is
+ * transformed by the unnormalized Sylvester-Hadamard matrix and the outputs at
+ * the sampled columns mu_c are kept, S_i[r, c] = scale * sum_k A_i[r, k] d_k
+ * (-1)^popcount(k & mu_c) (the element formula of Sec. 7.2).  This is the
+ * product S = A R; for a symmetric A_i (a kernel matrix K(X, X)) it equals
+ * S' = A_i^T R_i, the product the SJLT batch computes.  Orders nu_i <= 4096.
+ */
+typedef struct sk_srht_batch* sk_srht_batch_handle;
+
+typedef struct sk_srht_batch_item {
+  sk_handle op;        /* SRHT operator R_i (SK_SRHT), n_i rows, nu_i <= 4096             */
+  const float* A;      /* device FP32, rows x n_i, row-major                             */
+  int64_t rows;        /* rows of A_i (>= 1)                                             */
+  int64_t ld;          /* leading dimension of A (elements), >= n_i                     */
+  float* S;            /* device FP32, rows x d_total(R_i), leading dimension ldS        */
+  int64_t ldS;
+  int32_t c_lo, c_hi;  /* columns of R_i to sketch, 0 <= c_lo <= c_hi <= d_total(R_i)     */
+  double scale;        /* multiplies the transform; 0 = the operator's 1/sqrt(d_total)   */
+} sk_srht_batch_item;
+
+/*
+ * sketch_srht_batch_create -- prepare a batch of independent, uneven SRHT
+ * sketches (synchronous set-up on `stream`).  The rows of all instances with
+ * a non-empty column range are numbered into one list of units that one
+ * persistent launch of 128-thread CTAs splits into contiguous ranges; the
+ * number of CTAs per SM (3, 6 or 12) is picked by timing one run of each.
+ * The items are copied; A_i, S_i and the operators must outlive the batch,
+ * and the operators must not grow past the columns named here while it
+ * exists.  Errors: INVALID_ARG (a kind other than SK_SRHT, bad sizes or
+ * ranges), UNSUPPORTED (nu_i > 4096), NOMEM, DEVICE.
+ */
+int sketch_srht_batch_create(sk_srht_batch_handle* out, const sk_srht_batch_item* items, int32_t count,
+                             void* stream);
+
+/*
+ * sketch_srht_batch_set -- host-only update of the next run's column ranges
+ * (NULL keeps an array; c_lo == c_hi leaves that instance out of the run).
+ * Writes the pinned host mirror that sketch_srht_batch_run copies to the
+ * device, so call it only when no earlier run is still pending on the GPU.
+ * Errors: INVALID_ARG (a range outside [0, d_total]).
+ */
+int sketch_srht_batch_set(sk_srht_batch_handle b, const int32_t* c_lo, const int32_t* c_hi);
+
+/*
+ * sketch_srht_batch_run -- copy the item table from its pinned host mirror
+ * to the device and launch the batched transform on `stream` (asynchronous;
+ * copies and one kernel only, so a CUDA graph can capture it and replay the
+ * ranges sketch_srht_batch_set last wrote).  Columns [c_lo, c_hi) of every
+ * S_i are overwritten; other columns are untouched.  Errors: INVALID_ARG,
+ * DEVICE.
+ */
+int sketch_srht_batch_run(sk_srht_batch_handle b, void* stream);
+
+/* sketch_srht_batch_info -- the chosen CTAs per SM, the units (rows) of the
+ * next run and the tuner's times (ms) for 3, 6 and 12 CTAs per SM; any
+ * pointer may be NULL. */
+int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms);
+
+/* sketch_srht_batch_destroy -- free the batch (NULL is a no-op); the operators
+ * are not freed. */
+void sketch_srht_batch_destroy(sk_srht_batch_handle b);
+
 /* sketch_dims -- shape of the current operator (host outputs; any may be NULL). */
 int sketch_dims(sk_handle h, int32_t* kind, int64_t* n, int32_t* d_total, int32_t* alpha,
                 int32_t* blocks);

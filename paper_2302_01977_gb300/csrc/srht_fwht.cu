@@ -29,7 +29,10 @@
 // of 2k log 2k; the split is taken for r <= 8192 (p fits one CTA's shared
 // memory), the padded transform otherwise.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -359,4 +362,321 @@ int srht_apply_fwht(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double sca
   return SK_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batches of SRHT sketches S_i = A_i D_i H_i P_i scale_i (nu_i <= 4096): the
+// rows of every instance with a non-empty column range are numbered into one
+// list of units (one row each, instances in order) and a persistent grid of
+// 128-thread CTAs takes contiguous ranges of it.  A row of order nu = 128 E
+// (E = 4 .. 32) is transformed in registers as in srht_fwht_tail_kernel; a
+// row of order below 512 in shared memory.  Outputs are plain stores (each
+// sampled column belongs to one row transform), so runs are deterministic.
+constexpr int SB_THREADS = 128;
+constexpr int SB_MAX_NU = 4096;
+
+struct SbItem {
+  const float* A;
+  float* S;
+  const int8_t* diag;
+  const int32_t* mu;
+  int64_t lda, ldS;
+  int64_t unit0;  // first unit of this instance
+  int64_t rows;   // units of this instance in the next run (0: left out)
+  int32_t n, nu, c_lo, c_hi;
+  float scale;
+  int32_t flags;  // bit 0: rows start on 16-byte boundaries (A and lda * 4)
+};
+
+// row r of an instance into `stg` (nu floats, zero past n) by cp.async: 16-byte
+// copies when its rows start on 16-byte boundaries, 4-byte copies otherwise
+template <int P>
+__device__ __forceinline__ void sb_prefetch(const SbItem& it, int64_t r, float* stg) {
+  const float* a = it.A + r * it.lda;
+  const uint32_t st = smem_u32(stg);
+  if (it.flags & 1) {
+    for (int q = threadIdx.x; q < P / 4; q += SB_THREADS) {
+      const int rem = it.n - 4 * q;
+      const uint32_t bytes = rem >= 4 ? 16u : rem > 0 ? 4u * rem : 0u;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + 16 * q),
+                   "l"(bytes ? a + 4 * q : a), "r"(bytes) : "memory");
+    }
+  } else {
+    for (int k = threadIdx.x; k < P; k += SB_THREADS) cp_async_4(st + 4 * k, k < it.n ? a + k : a, k < it.n ? 4 : 0);
+  }
+  cp_async_commit();
+}
+
+// rows [r0, r1) of one instance, order P = 128 E; the next row is staged by
+// cp.async while this one is transformed
+template <int E>
+__device__ void sb_rows_reg(const SbItem& it, int64_t r0, int64_t r1, float* tb, float* stg) {
+  constexpr int P = 128 * E, G = 128 / E;
+  constexpr int LOG_E = E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : 5;
+  static_assert(P <= SB_MAX_NU && G <= 32, "register path: 512 <= nu <= 4096");
+  const int t = threadIdx.x;
+  auto idx = [](int kk) { return kk + G * (kk >> 7); };
+  uint32_t neg = 0;  // D's sign of k = t + 128 j, bit j
+  for (int j = 0; j < E; ++j) {
+    const int kk = t + 128 * j;
+    if (kk < it.n && it.diag[kk] < 0) neg |= 1u << j;
+  }
+  const int h = t / G, g = t % G;
+  sb_prefetch<P>(it, r0, stg);
+  for (int64_t r = r0; r < r1; ++r) {
+    cp_async_wait<0>();
+    __syncthreads();  // row r is staged
+    float x[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+      const float v = stg[t + 128 * j];
+      x[j] = ((neg >> j) & 1) ? -v : v;
+    }
+#pragma unroll
+    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+#pragma unroll
+    for (int j = 0; j < E; ++j) tb[idx(t + 128 * j)] = x[j];
+    __syncthreads();  // every thread has read the staged row and written tb
+    if (r + 1 < r1) sb_prefetch<P>(it, r + 1, stg);
+#pragma unroll
+    for (int j = 0; j < E; ++j) x[j] = tb[idx(128 * h + g + G * j)];
+#pragma unroll
+    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+#pragma unroll
+    for (int b = 1; b < G; b <<= 1) {
+      const bool upper = (g & b) != 0;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const float u = __shfl_xor_sync(0xffffffffu, x[j], b);
+        x[j] = upper ? u - x[j] : x[j] + u;
+      }
+    }
+    __syncthreads();  // every thread has read its transposed values
+#pragma unroll
+    for (int j = 0; j < E; ++j) tb[idx(128 * h + g + G * j)] = x[j];
+    __syncthreads();
+    float* srow = it.S + r * it.ldS;
+    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[idx(it.mu[c])];
+    __syncthreads();
+  }
+}
+
+// rows [r0, r1) of one instance, order nu < 512: butterflies in shared memory
+__device__ void sb_rows_smem(const SbItem& it, int64_t r0, int64_t r1, float* tb) {
+  const int t = threadIdx.x, p = it.nu;
+  for (int64_t r = r0; r < r1; ++r) {
+    const float* a = it.A + r * it.lda;
+    for (int j = t; j < p; j += SB_THREADS) tb[j] = j < it.n ? (it.diag[j] < 0 ? -__ldg(a + j) : __ldg(a + j)) : 0.f;
+    __syncthreads();
+    for (int hh = 1; hh < p; hh <<= 1) {
+      for (int b = t; b < p / 2; b += SB_THREADS) {
+        const int j0 = ((b & ~(hh - 1)) << 1) | (b & (hh - 1)), j1 = j0 + hh;
+        const float x = tb[j0], y = tb[j1];
+        tb[j0] = x + y;
+        tb[j1] = x - y;
+      }
+      __syncthreads();
+    }
+    float* srow = it.S + r * it.ldS;
+    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[it.mu[c]];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SB_THREADS, 6)
+    srht_batch_kernel(const SbItem* __restrict__ items, int count, int64_t total) {
+  __shared__ float tb[SB_MAX_NU + SB_MAX_NU / 128 * 4];  // order 4096: P + E G = 4096 + 32 * 4
+  __shared__ __align__(16) float stg[SB_MAX_NU];            // the next row, staged by cp.async
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t u0 = (int64_t)blockIdx.x * per, u1 = min64(total, u0 + per);
+  if (u0 >= u1) return;
+  int lo = 0, hi = count - 1;  // the last instance whose first unit is <= u0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (items[mid].unit0 <= u0) lo = mid;
+    else hi = mid - 1;
+  }
+  int64_t u = u0;
+  for (int i = lo; i < count && u < u1; ++i) {
+    const SbItem it = items[i];
+    const int64_t end = min64(u1, it.unit0 + it.rows);
+    if (u >= end) continue;  // an instance left out of this run
+    const int64_t r0 = u - it.unit0, r1 = end - it.unit0;
+    switch (it.nu) {
+      case 4096: sb_rows_reg<32>(it, r0, r1, tb, stg); break;
+      case 2048: sb_rows_reg<16>(it, r0, r1, tb, stg); break;
+      case 1024: sb_rows_reg<8>(it, r0, r1, tb, stg); break;
+      case 512: sb_rows_reg<4>(it, r0, r1, tb, stg); break;
+      default: sb_rows_smem(it, r0, r1, tb);
+    }
+    u = end;
+  }
+}
+
 }  // namespace jls
+
+// ---------------------------------------------------------------------------
+// host side of the SRHT batch
+struct sk_srht_batch {
+  int device = 0;
+  int count = 0;
+  std::vector<sk_srht_batch_item> items;
+  jls::SbItem* h_items = nullptr;  // pinned mirror of the item table
+  jls::SbItem* d_items = nullptr;
+  int64_t total = 0;               // units of the next run
+  int ctas_per_sm = 6;
+  float tuned_ms[3] = {};
+};
+
+namespace jls {
+namespace {
+
+constexpr int SB_CTAS[3] = {3, 6, 12};  // 6 CTAs of 80 registers x 128 threads fill an SM
+
+void sb_number(sk_srht_batch* b) {
+  int64_t u = 0;
+  for (int i = 0; i < b->count; ++i) {
+    SbItem& I = b->h_items[i];
+    I.unit0 = u;
+    I.rows = I.c_hi > I.c_lo ? b->items[i].rows : 0;
+    u += I.rows;
+  }
+  b->total = u;
+}
+
+int sb_launch(sk_srht_batch* b, cudaStream_t s) {
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(SbItem) * b->count, cudaMemcpyHostToDevice, s));
+  if (b->total == 0) return SK_OK;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->ctas_per_sm * num_sms(),
+                                                                         b->total));
+  srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, b->count, b->total);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// one timed run per CTAs-per-SM choice (after one untimed run); keeps the fastest
+int sb_tune(sk_srht_batch* b, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  JLS_CHECK_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SK_ERR_DEVICE;
+  }
+  int rc = SK_OK, best = 0;
+  for (int k = 0; k < 3 && rc == SK_OK; ++k) {
+    b->ctas_per_sm = SB_CTAS[k];
+    if ((rc = sb_launch(b, s)) != SK_OK) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess || (rc = sb_launch(b, s)) != SK_OK ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&b->tuned_ms[k], e0, e1) != cudaSuccess) {
+      rc = rc == SK_OK ? SK_ERR_DEVICE : rc;
+      break;
+    }
+    if (k == 0 || b->tuned_ms[k] < b->tuned_ms[best]) best = k;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->ctas_per_sm = SB_CTAS[best];
+  return rc;
+}
+
+}  // namespace
+}  // namespace jls
+
+using namespace jls;
+
+extern "C" {
+
+int sketch_srht_batch_create(sk_srht_batch_handle* out, const sk_srht_batch_item* items, int32_t count,
+                             void* stream) {
+  if (!out || !items || count < 1) return SK_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    const sk_srht_batch_item& it = items[i];
+    const sk_op* h = it.op;
+    if (!h || h->kind != SK_SRHT) return SK_ERR_INVALID_ARG;
+    if (!it.A || !it.S || it.rows < 1 || it.ld < h->n || it.ldS < h->d_total) return SK_ERR_INVALID_ARG;
+    if (it.c_lo < 0 || it.c_hi < it.c_lo || it.c_hi > h->d_total) return SK_ERR_INVALID_ARG;
+    if (h->nu > SB_MAX_NU) return SK_ERR_UNSUPPORTED;
+  }
+  sk_srht_batch* b = new sk_srht_batch();
+  b->count = count;
+  b->items.assign(items, items + count);
+  cudaGetDevice(&b->device);
+  auto fail = [&](int code) {
+    sketch_srht_batch_destroy(b);
+    return code;
+  };
+  if (cudaMallocHost(&b->h_items, sizeof(SbItem) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_items, sizeof(SbItem) * count) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SK_ERR_NOMEM);
+  }
+  std::memset(b->h_items, 0, sizeof(SbItem) * count);
+  for (int i = 0; i < count; ++i) {
+    const sk_srht_batch_item& it = items[i];
+    const sk_op* h = it.op;
+    SbItem& I = b->h_items[i];
+    I.A = it.A;
+    I.S = it.S;
+    I.diag = h->srht_diag;
+    I.mu = h->srht_mu;
+    I.lda = it.ld;
+    I.ldS = it.ldS;
+    I.n = (int32_t)h->n;
+    I.nu = (int32_t)h->nu;
+    I.c_lo = it.c_lo;
+    I.c_hi = it.c_hi;
+    I.scale = (float)(it.scale != 0.0 ? it.scale : 1.0 / std::sqrt((double)h->d_total));
+    I.flags = ((reinterpret_cast<uintptr_t>(it.A) & 15u) == 0 && (it.ld * 4) % 16 == 0) ? 1 : 0;
+  }
+  sb_number(b);
+  // six CTAs of 33 KB of shared memory per SM: ask for the largest shared-memory carveout
+  if (cudaFuncSetAttribute(srht_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SK_ERR_DEVICE);
+  }
+  const int rc = sb_tune(b, s);
+  if (rc != SK_OK) return fail(rc);
+  *out = b;
+  return SK_OK;
+}
+
+int sketch_srht_batch_set(sk_srht_batch_handle b, const int32_t* c_lo, const int32_t* c_hi) {
+  if (!b) return SK_ERR_INVALID_ARG;
+  for (int i = 0; i < b->count; ++i) {
+    const int lo = c_lo ? c_lo[i] : b->h_items[i].c_lo, hi = c_hi ? c_hi[i] : b->h_items[i].c_hi;
+    if (lo < 0 || hi < lo || hi > b->items[i].op->d_total) return SK_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < b->count; ++i) {
+    if (c_lo) b->h_items[i].c_lo = c_lo[i];
+    if (c_hi) b->h_items[i].c_hi = c_hi[i];
+  }
+  sb_number(b);
+  return SK_OK;
+}
+
+int sketch_srht_batch_run(sk_srht_batch_handle b, void* stream) {
+  if (!b) return SK_ERR_INVALID_ARG;
+  return sb_launch(b, static_cast<cudaStream_t>(stream));
+}
+
+int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms) {
+  if (!b) return SK_ERR_INVALID_ARG;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (units) *units = b->total;
+  if (tuned_ms)
+    for (int k = 0; k < 3; ++k) tuned_ms[k] = b->tuned_ms[k];
+  return SK_OK;
+}
+
+void sketch_srht_batch_destroy(sk_srht_batch_handle b) {
+  if (!b) return;
+  if (b->h_items) cudaFreeHost(b->h_items);
+  if (b->d_items) cudaFree(b->d_items);
+  delete b;
+}
+
+}  // extern "C"

@@ -51,7 +51,9 @@ EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_in
            "sketch_kernel_adjoint", "sketch_batch_create", "sketch_batch_set", "sketch_batch_run",
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
            "sketch_batch_adaptive_result",
-           "sketch_batch_info", "sketch_batch_status", "sketch_batch_destroy", "sketch_dims", "sketch_export",
+           "sketch_batch_info", "sketch_batch_status", "sketch_batch_destroy", "sketch_srht_batch_create",
+           "sketch_srht_batch_set", "sketch_srht_batch_run", "sketch_srht_batch_info", "sketch_srht_batch_destroy",
+           "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_selftest_wait", "sketch_launch_count", "sketch_srht_route",
            "sketch_destroy",
            "sketch_strerror"]
@@ -68,6 +70,12 @@ class SkBatchItem(ctypes.Structure):
                 ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("St", ctypes.c_void_p),
                 ("ldSt", ctypes.c_int64), ("c_lo", ctypes.c_int32), ("c_hi", ctypes.c_int32),
                 ("scale", ctypes.c_double)]
+
+
+class SkSrhtBatchItem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("A", ctypes.c_void_p), ("rows", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("S", ctypes.c_void_p), ("ldS", ctypes.c_int64),
+                ("c_lo", ctypes.c_int32), ("c_hi", ctypes.c_int32), ("scale", ctypes.c_double)]
 
 
 class SkMatrix(ctypes.Structure):
@@ -116,6 +124,11 @@ def lib() -> ctypes.CDLL:
         "sketch_batch_info": (i32, [vp, P(i32), P(i32), P(i64), P(ctypes.c_float)]),
         "sketch_batch_status": (i32, [vp, vp]),
         "sketch_batch_destroy": (None, [vp]),
+        "sketch_srht_batch_create": (i32, [P(vp), P(SkSrhtBatchItem), i32, vp]),
+        "sketch_srht_batch_set": (i32, [vp, vp, vp]),
+        "sketch_srht_batch_run": (i32, [vp, vp]),
+        "sketch_srht_batch_info": (i32, [vp, P(i32), P(i64), P(ctypes.c_float)]),
+        "sketch_srht_batch_destroy": (None, [vp]),
         "sketch_selftest_wait": (i32, [vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
         "sketch_export": (i32, [vp, vp, vp, vp, vp, vp, i32]),
@@ -393,6 +406,70 @@ class Batch:
     def close(self):
         if self.b:
             lib().sketch_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SrhtBatch:
+    """Many S_i = A_i R_i (columns [c_lo_i, c_hi_i) of SRHT handles, orders nu_i <= 4096) in
+    one persistent launch.
+
+    ``items``: sequence of (op_handle, A, S, c_lo, c_hi) with A (rows x n_i) and S float32
+    CUDA tensors that outlive the batch.  ``run()`` is asynchronous and capturable in a CUDA
+    graph; ``set(c_lo, c_hi)`` changes the ranges of the next run (or replay).
+    """
+
+    def __init__(self, items, stream=None):
+        arr = (SkSrhtBatchItem * len(items))()
+        self._keep = []
+        for k, (op, A, S, lo, hi) in enumerate(items):
+            _check_2d(A, "A")
+            _check_2d(S, "S")
+            if str(A.dtype) != "torch.float32" or str(S.dtype) != "torch.float32":
+                raise ValueError("A and S must be float32")
+            self._keep.append((A, S))
+            arr[k] = SkSrhtBatchItem(op=op, A=A.data_ptr(), rows=A.shape[0], ld=A.stride(0), S=S.data_ptr(),
+                                     ldS=S.stride(0), c_lo=int(lo), c_hi=int(hi), scale=0.0)
+        self.count = len(items)
+        self.b = ctypes.c_void_p()
+        _check(lib().sketch_srht_batch_create(ctypes.byref(self.b), arr, self.count, _stream(stream)),
+               "sketch_srht_batch_create")
+
+    def set(self, c_lo=None, c_hi=None) -> None:
+        def arr(x):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+            if a.shape != (self.count,):
+                raise ValueError("one value per instance")
+            return a
+        lo, hi = arr(c_lo), arr(c_hi)
+        p = lambda x: None if x is None else x.ctypes.data  # noqa: E731
+        _check(lib().sketch_srht_batch_set(self.b, p(lo), p(hi)), "sketch_srht_batch_set")
+
+    def run(self, stream=None) -> None:
+        _check(lib().sketch_srht_batch_run(self.b, _stream(stream)), "sketch_srht_batch_run")
+
+    def info(self) -> dict:
+        c, u = ctypes.c_int32(), ctypes.c_int64()
+        ms = (ctypes.c_float * 3)()
+        _check(lib().sketch_srht_batch_info(self.b, ctypes.byref(c), ctypes.byref(u), ms), "sketch_srht_batch_info")
+        return dict(ctas_per_sm=c.value, units=u.value, tuned_ms=[round(x, 4) for x in ms])
+
+    def close(self):
+        if self.b:
+            lib().sketch_srht_batch_destroy(self.b)
             self.b = None
 
     def __enter__(self):

@@ -88,6 +88,12 @@ def test_null_handle_calls(L):
     assert L.sketch_batch_adaptive_run(None, 0, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_batch_adaptive_result(None, None, None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
     L.sketch_batch_destroy(None)  # no-op
+    # batches of SRHT sketches
+    assert L.sketch_srht_batch_create(None, None, 0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_srht_batch_set(None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_srht_batch_run(None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_srht_batch_info(None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    L.sketch_srht_batch_destroy(None)  # no-op
 
 
 def test_no_gpu_fails_loudly(L):
