@@ -297,6 +297,21 @@ __global__ void __launch_bounds__(TAIL_THREADS)
   }
 }
 
+// butterfly stage on register index bit `s`, one FADD per output: the batched
+// kernel's short rows change the pairing from stage to stage, where packing
+// operands for FFMA2 pairs would cost register moves
+template <int N>
+__device__ __forceinline__ void stage_s(float (&x)[N], int s) {
+  const int d = 1 << s;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if ((j >> s) & 1) continue;
+    const float a = x[j], b = x[j + d];
+    x[j] = a + b;
+    x[j + d] = a - b;
+  }
+}
+
 // Unit length and segment count for nu; 0 if the FWHT path does not apply.
 int fwht_segments(int64_t nu) {
   if (nu < FW_L || nu > (int64_t)FW_L * FW_MAX_SEG) return 0;
@@ -432,7 +447,7 @@ __device__ void sb_rows_reg(const SbItem& it, int64_t r0, int64_t r1, float* tb,
       x[j] = ((neg >> j) & 1) ? -v : v;
     }
 #pragma unroll
-    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+    for (int st = 0; st < LOG_E; ++st) stage_s<E>(x, st);
 #pragma unroll
     for (int j = 0; j < E; ++j) tb[idx(t + 128 * j)] = x[j];
     __syncthreads();  // every thread has read the staged row and written tb
@@ -440,15 +455,12 @@ __device__ void sb_rows_reg(const SbItem& it, int64_t r0, int64_t r1, float* tb,
 #pragma unroll
     for (int j = 0; j < E; ++j) x[j] = tb[idx(128 * h + g + G * j)];
 #pragma unroll
-    for (int st = 0; st < LOG_E; ++st) stage<E>(x, st);
+    for (int st = 0; st < LOG_E; ++st) stage_s<E>(x, st);
 #pragma unroll
     for (int b = 1; b < G; b <<= 1) {
-      const bool upper = (g & b) != 0;
+      const float sg = (g & b) ? -1.f : 1.f;  // lower lane x + u, upper lane u - x
 #pragma unroll
-      for (int j = 0; j < E; ++j) {
-        const float u = __shfl_xor_sync(0xffffffffu, x[j], b);
-        x[j] = upper ? u - x[j] : x[j] + u;
-      }
+      for (int j = 0; j < E; ++j) x[j] = fmaf(sg, x[j], __shfl_xor_sync(0xffffffffu, x[j], b));
     }
     __syncthreads();  // every thread has read its transposed values
 #pragma unroll
