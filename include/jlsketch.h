@@ -466,6 +466,47 @@ int sketch_srht_batch_run(sk_srht_batch_handle b, void* stream);
  * pointer may be NULL. */
 int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms);
 
+/*
+ * sketch_srht_batch_adaptive_setup -- prepare Algorithm 1's adaptive loop for
+ * every instance of an SRHT batch (Sec. 6.2, Algorithm 1; Eq. (3.1)), run on
+ * the device by sketch_srht_batch_adaptive_run.  Each operator must have been
+ * created with d0[i] + dd columns and grown by dd-column increments up to the
+ * columns the loop may use (the increments of Algorithm 1 are
+ * data-independent draws).  Round 0 sketches S_i[:, 0 : d0 + dd); each round
+ * tests the last dd columns sketched against an orthonormal basis of the
+ * earlier ones (kept per instance on the device), stops the instance when
+ * ||S^|| < eps_abs or ||S^|| < eps_rel ||S~||, and otherwise extends the
+ * basis and sketches the next dd columns.  The loop sketches every column with
+ * 1/sqrt(d0 + dd); norms are reported at the scale of R_i[:, :d] (1/sqrt(d))
+ * and the finished columns are rescaled once, so S_i[:, :d] = A_i R_i[:, :d].
+ * The loop is the SJLT batch's (same test kernel, FP32 sketch and basis, FP64
+ * norms).  Limits: 8 <= dd <= 32, dd and d0 multiples of 8, d_total - dd <=
+ * 512.  Synchronous, not capturable.  Errors: INVALID_ARG, UNSUPPORTED,
+ * NOMEM, DEVICE.
+ */
+int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel,
+                                     double eps_abs, void* stream);
+
+/*
+ * sketch_srht_batch_adaptive_run -- enqueue the whole loop on `stream`
+ * (asynchronous; copies and kernels only, so one CUDA graph can capture every
+ * round): reset the device tables, then per round the numbering of the active
+ * instances' rows, one batched transform and the stopping test of every
+ * active instance; max_rounds = 0 runs until every instance has stopped.
+ * Errors: INVALID_ARG, DEVICE.
+ */
+int sketch_srht_batch_adaptive_run(sk_srht_batch_handle b, int32_t max_rounds, void* stream);
+
+/*
+ * sketch_srht_batch_adaptive_result -- synchronize `stream` and read each
+ * instance's columns sketched (d_reached), state (1 converged, 2 out of
+ * columns, 0 still running), stopping tests taken and the last test's
+ * ||S^||_F and ||S~||_F (host arrays of `count` values; any may be NULL).
+ * Errors: INVALID_ARG, DEVICE.
+ */
+int sketch_srht_batch_adaptive_result(sk_srht_batch_handle b, int32_t* d_reached, int32_t* state, int32_t* tests,
+                                      double* nh, double* nt, void* stream);
+
 /* sketch_srht_batch_destroy -- free the batch (NULL is a no-op); the operators
  * are not freed. */
 void sketch_srht_batch_destroy(sk_srht_batch_handle b);

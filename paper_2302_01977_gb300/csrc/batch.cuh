@@ -1,5 +1,6 @@
 // batch.cuh -- the device tables of a batch of SJLT sketches S'_i = A_i^T R_i
-// and of its adaptive loop (Algorithm 1 run per instance on the device).
+// and of the adaptive loop (Algorithm 1 run per instance on the device) that
+// batches of SJLT sketches and of SRHT sketches S_i = A_i R_i share.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -41,7 +42,8 @@ struct alignas(16) ATest {
   int32_t state;    // ADAPT_ACTIVE, ADAPT_CONVERGED or ADAPT_CAPPED
   int32_t tests;    // stopping tests taken
   int32_t d_reached;
-  int32_t pad;
+  int32_t srht;     // the scale the loop sketches with: 0 (SJLT) 1/sqrt(alpha) per block, R_i[:, :d] carries
+                    // 1/sqrt(alpha B); 1 (SRHT) 1/sqrt(first_w), R_i[:, :d] carries 1/sqrt(d)
   double nh, nt;    // ||S^||_F and ||S~||_F of the last test, at the scale of R_i[:, :d_reached]
 };
 enum : int32_t { ADAPT_ACTIVE = 0, ADAPT_CONVERGED = 1, ADAPT_CAPPED = 2 };

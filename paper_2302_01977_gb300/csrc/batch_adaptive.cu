@@ -31,6 +31,8 @@
 // Scale: the loop sketches with the per-block scale 1/sqrt(alpha); R_i with
 // B blocks carries 1/sqrt(alpha B), so the norms are reported (and compared
 // with eps_abs) times 1/sqrt(B), and the finished columns are rescaled once.
+// An SRHT loop sketches every column with 1/sqrt(d0 + dd) and R_i[:, :d]
+// carries 1/sqrt(d): the factor is sqrt((d0 + dd) / d).
 #include <cooperative_groups.h>
 
 #include "batch.cuh"
@@ -664,8 +666,8 @@ __global__ void __launch_bounds__(AT, 1)
   const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
   absorb_begin(c, q, nt2);
   const double nh2 = lgl_trace(c);
-  const int blocks = 1 + (c_end - T->first_w) / dd;
-  const double sc = 1.0 / sqrt((double)blocks);
+  const double sc = T->srht ? sqrt((double)T->first_w / (double)c_end)
+                            : 1.0 / sqrt((double)(1 + (c_end - T->first_w) / dd));
   const double nh = sqrt(nh2) * sc, nt = sqrt(nt2) * sc;
   const bool stop = (nh < eps_abs) || (nh < eps_rel * nt);
   const bool room = c_end + dd <= T->d_cap;
@@ -733,14 +735,14 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// S'_i[:, :d_reached] *= 1/sqrt(B), B = blocks of R_i[:, :d_reached]
+// S'_i[:, :d_reached] *= 1/sqrt(B), B = blocks of R_i[:, :d_reached] (SJLT), or
+// S_i[:, :d_reached] *= sqrt(first_w / d_reached) (SRHT)
 __global__ void __launch_bounds__(256) batch_rescale_kernel(const ATest* __restrict__ tests) {
   const ATest& T = tests[blockIdx.x];
   const int d = T.d_reached;
-  if (d <= 0) return;
-  const int blocks = 1 + (d - T.first_w) / T.dd;
-  if (blocks <= 1) return;
-  const float f = (float)(1.0 / sqrt((double)blocks));
+  if (d <= T.first_w) return;
+  const float f = (float)(T.srht ? sqrt((double)T.first_w / (double)d)
+                                 : 1.0 / sqrt((double)(1 + (d - T.first_w) / T.dd)));
   float* S = const_cast<float*>(T.S);
   for (int64_t r = blockIdx.y; r < T.rows; r += gridDim.y)
     for (int j = threadIdx.x; j < d; j += blockDim.x) S[r * T.ldS + j] *= f;

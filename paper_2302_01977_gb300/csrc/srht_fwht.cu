@@ -34,6 +34,7 @@
 #include <cstring>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -397,6 +398,7 @@ struct SbItem {
   int64_t lda, ldS;
   int64_t unit0;  // first unit of this instance
   int64_t rows;   // units of this instance in the next run (0: left out)
+  int64_t nrows;  // rows of A_i
   int32_t n, nu, c_lo, c_hi;
   float scale;
   int32_t flags;  // bit 0: rows start on 16-byte boundaries (A and lda * 4)
@@ -495,7 +497,9 @@ __device__ void sb_rows_smem(const SbItem& it, int64_t r0, int64_t r1, float* tb
 }
 
 __global__ void __launch_bounds__(SB_THREADS, 6)
-    srht_batch_kernel(const SbItem* __restrict__ items, int count, int64_t total) {
+    srht_batch_kernel(const SbItem* __restrict__ items, int count, int64_t total_host,
+                      const int64_t* __restrict__ total_dev) {
+  const int64_t total = total_dev ? *total_dev : total_host;
   __shared__ float tb[SB_MAX_NU + SB_MAX_NU / 128 * 4];  // order 4096: P + E G = 4096 + 32 * 4
   __shared__ __align__(16) float stg[SB_MAX_NU];            // the next row, staged by cp.async
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
@@ -524,6 +528,43 @@ __global__ void __launch_bounds__(SB_THREADS, 6)
   }
 }
 
+// Between the rounds of the adaptive loop: the test kernel has left each
+// instance's next column range (or units = 0 when it stopped) in the shared
+// loop table; copy the ranges into the SRHT items and number the rows of the
+// instances still active (one CTA of 1024 threads, in item order).
+__global__ void __launch_bounds__(1024)
+    sb_renumber_kernel(const BItem* __restrict__ bi, SbItem* __restrict__ sb, int count, int64_t* __restrict__ total) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (count + 1023) / 1024;
+  const int i0 = min(count, t * per), i1 = min(count, i0 + per);
+  int64_t sum = 0;
+  for (int i = i0; i < i1; ++i) {
+    SbItem& I = sb[i];
+    I.c_lo = bi[i].c_lo;
+    I.c_hi = bi[i].c_hi;
+    I.rows = (bi[i].units && I.c_hi > I.c_lo) ? I.nrows : 0;
+    sum += I.rows;
+  }
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int64_t run = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const int64_t v = part[k];
+      part[k] = run;
+      run += v;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  int64_t u = part[t];
+  for (int i = i0; i < i1; ++i) {
+    sb[i].unit0 = u;
+    u += sb[i].rows;
+  }
+}
+
 }  // namespace jls
 
 // ---------------------------------------------------------------------------
@@ -537,6 +578,18 @@ struct sk_srht_batch {
   int64_t total = 0;               // units of the next run
   int ctas_per_sm = 6;
   float tuned_ms[3] = {};
+  // the adaptive loop (sketch_srht_batch_adaptive_setup)
+  bool adaptive = false;
+  int max_tests = 0, a_ncl = 1;
+  double eps_rel = 0.0, eps_abs = 0.0;
+  jls::SbItem* d_sb0 = nullptr;   // round 0's items: [0, d0 + dd) at the loop's scale 1/sqrt(d0 + dd)
+  jls::BItem* d_loop = nullptr;   // the loop table the test kernel updates (c_lo, c_hi, units)
+  jls::BItem* d_loop0 = nullptr;
+  jls::ATest* d_tests = nullptr;  // per-instance loop state, and its initial value
+  jls::ATest* d_tests0 = nullptr;
+  int* d_order = nullptr;         // instances, largest first
+  float* d_basis = nullptr;       // Q_i and W_i of every instance
+  int64_t* d_units = nullptr;     // rows of the next round
 };
 
 namespace jls {
@@ -560,7 +613,7 @@ int sb_launch(sk_srht_batch* b, cudaStream_t s) {
   if (b->total == 0) return SK_OK;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->ctas_per_sm * num_sms(),
                                                                          b->total));
-  srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, b->count, b->total);
+  srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, b->count, b->total, nullptr);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -640,6 +693,7 @@ int sketch_srht_batch_create(sk_srht_batch_handle* out, const sk_srht_batch_item
     I.nu = (int32_t)h->nu;
     I.c_lo = it.c_lo;
     I.c_hi = it.c_hi;
+    I.nrows = it.rows;
     I.scale = (float)(it.scale != 0.0 ? it.scale : 1.0 / std::sqrt((double)h->d_total));
     I.flags = ((reinterpret_cast<uintptr_t>(it.A) & 15u) == 0 && (it.ld * 4) % 16 == 0) ? 1 : 0;
   }
@@ -684,8 +738,150 @@ int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t
   return SK_OK;
 }
 
+static void sb_adaptive_free(sk_srht_batch* b) {
+  void* ps[] = {b->d_sb0, b->d_loop, b->d_loop0, b->d_tests, b->d_tests0, b->d_order, b->d_basis, b->d_units};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  b->d_sb0 = nullptr;
+  b->d_loop = b->d_loop0 = nullptr;
+  b->d_tests = b->d_tests0 = nullptr;
+  b->d_order = nullptr;
+  b->d_basis = nullptr;
+  b->d_units = nullptr;
+  b->adaptive = false;
+}
+
+int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel,
+                                     double eps_abs, void* stream) {
+  if (!b || !d0 || dd < 8 || dd > ADAPT_BW || dd % 8 || !(eps_rel >= 0.0) || !(eps_abs >= 0.0))
+    return SK_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int count = b->count;
+  for (int i = 0; i < count; ++i) {
+    const sk_op* h = b->items[i].op;
+    const int first = d0[i] + dd;
+    if (d0[i] < 0 || d0[i] % 8 || h->blocks.empty() || h->blocks[0] != first) return SK_ERR_INVALID_ARG;
+    for (size_t j = 1; j < h->blocks.size(); ++j)
+      if (h->blocks[j] != dd) return SK_ERR_INVALID_ARG;  // R_i = SRHT(d0 + dd) grown by dd-column increments
+    if (b->items[i].ldS < h->d_total) return SK_ERR_INVALID_ARG;
+    if (h->d_total - dd > ADAPT_QMAX) return SK_ERR_UNSUPPORTED;
+  }
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  sb_adaptive_free(b);
+  std::vector<SbItem> sb0(b->h_items, b->h_items + count);
+  std::vector<BItem> loop0(count);
+  std::vector<ATest> a0(count);
+  std::vector<size_t> off(count);
+  size_t total = 0;
+  int max_tests = 0;
+  for (int i = 0; i < count; ++i) {
+    const sk_op* h = b->items[i].op;
+    const int first = d0[i] + dd;
+    sb0[i].scale = (float)(1.0 / std::sqrt((double)first));
+    std::memset(&loop0[i], 0, sizeof(BItem));
+    loop0[i].c_lo = 0;
+    loop0[i].c_hi = first;
+    loop0[i].units = 1;
+    const int qcap = std::max(8, (h->d_total - dd + 7) / 8 * 8);
+    off[i] = total;
+    total += (size_t)b->items[i].rows * (qcap + ADAPT_BW);
+    ATest& T = a0[i];
+    std::memset(&T, 0, sizeof(T));
+    T.S = b->items[i].S;
+    T.rows = b->items[i].rows;
+    T.ldS = b->items[i].ldS;
+    T.qcap = qcap;
+    T.dd = dd;
+    T.d_cap = h->d_total;
+    T.first_w = first;
+    T.state = ADAPT_ACTIVE;
+    T.srht = 1;
+    max_tests = std::max(max_tests, 1 + (h->d_total - first) / dd);
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->items[x].rows * (int64_t)b->items[x].op->d_total > b->items[y].rows * (int64_t)b->items[y].op->d_total;
+  });
+  if (cudaMalloc(&b->d_sb0, sizeof(SbItem) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_loop, sizeof(BItem) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_loop0, sizeof(BItem) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_tests, sizeof(ATest) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_tests0, sizeof(ATest) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_basis, total * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->d_units, sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    sb_adaptive_free(b);
+    return SK_ERR_NOMEM;
+  }
+  for (int i = 0; i < count; ++i) {
+    a0[i].Q = b->d_basis + off[i];
+    a0[i].W = b->d_basis + off[i] + (size_t)b->items[i].rows * a0[i].qcap;
+  }
+  int rc = adaptive_prepare();
+  if (rc == SK_OK &&
+      (cudaMemcpy(b->d_sb0, sb0.data(), sizeof(SbItem) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_loop0, loop0.data(), sizeof(BItem) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_tests0, a0.data(), sizeof(ATest) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = SK_ERR_DEVICE;
+  if (rc != SK_OK) {
+    sb_adaptive_free(b);
+    return rc;
+  }
+  b->max_tests = max_tests;
+  // the stopping test: one CTA per instance when the instances fill the GPU, else a cluster of 4
+  const char* env = std::getenv("JLS_ADAPT_CLUSTER");
+  b->a_ncl = env ? std::atoi(env) : (count >= num_sms() ? 1 : 4);
+  if (b->a_ncl != 1 && b->a_ncl != 2 && b->a_ncl != 4) b->a_ncl = 4;
+  b->eps_rel = eps_rel;
+  b->eps_abs = eps_abs;
+  b->adaptive = true;
+  return SK_OK;
+}
+
+int sketch_srht_batch_adaptive_run(sk_srht_batch_handle b, int32_t max_rounds, void* stream) {
+  if (!b || !b->adaptive || max_rounds < 0) return SK_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int count = b->count;
+  const int rounds = max_rounds ? std::min<int>(max_rounds, b->max_tests) : b->max_tests;
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_items, b->d_sb0, sizeof(SbItem) * count, cudaMemcpyDeviceToDevice, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_loop, b->d_loop0, sizeof(BItem) * count, cudaMemcpyDeviceToDevice, s));
+  JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_tests, b->d_tests0, sizeof(ATest) * count, cudaMemcpyDeviceToDevice, s));
+  int64_t rows_all = 0;
+  for (const sk_srht_batch_item& it : b->items) rows_all += it.rows;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->ctas_per_sm * num_sms(), rows_all));
+  for (int r = 0; r < rounds; ++r) {
+    sb_renumber_kernel<<<1, 1024, 0, s>>>(b->d_loop, b->d_items, count, b->d_units);
+    note_launch();
+    srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, count, 0, b->d_units);
+    note_launch();
+    JLS_CHECK_CUDA(cudaGetLastError());
+    JLS_CHECK(adaptive_test_launch(b->d_loop, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs, s));
+  }
+  return adaptive_rescale_launch(b->d_tests, count, s);
+}
+
+int sketch_srht_batch_adaptive_result(sk_srht_batch_handle b, int32_t* d_reached, int32_t* state, int32_t* tests,
+                                      double* nh, double* nt, void* stream) {
+  if (!b || !b->adaptive) return SK_ERR_INVALID_ARG;
+  JLS_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  std::vector<ATest> a(b->count);
+  JLS_CHECK_CUDA(cudaMemcpy(a.data(), b->d_tests, sizeof(ATest) * b->count, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < b->count; ++i) {
+    if (d_reached) d_reached[i] = a[i].d_reached;
+    if (state) state[i] = a[i].state;
+    if (tests) tests[i] = a[i].tests;
+    if (nh) nh[i] = a[i].nh;
+    if (nt) nt[i] = a[i].nt;
+  }
+  return SK_OK;
+}
+
 void sketch_srht_batch_destroy(sk_srht_batch_handle b) {
   if (!b) return;
+  sb_adaptive_free(b);
   if (b->h_items) cudaFreeHost(b->h_items);
   if (b->d_items) cudaFree(b->d_items);
   delete b;

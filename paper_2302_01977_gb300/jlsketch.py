@@ -52,7 +52,9 @@ EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_in
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
            "sketch_batch_adaptive_result",
            "sketch_batch_info", "sketch_batch_status", "sketch_batch_destroy", "sketch_srht_batch_create",
-           "sketch_srht_batch_set", "sketch_srht_batch_run", "sketch_srht_batch_info", "sketch_srht_batch_destroy",
+           "sketch_srht_batch_set", "sketch_srht_batch_run", "sketch_srht_batch_info",
+           "sketch_srht_batch_adaptive_setup", "sketch_srht_batch_adaptive_run", "sketch_srht_batch_adaptive_result",
+           "sketch_srht_batch_destroy",
            "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_selftest_wait", "sketch_launch_count", "sketch_srht_route",
            "sketch_destroy",
@@ -128,6 +130,10 @@ def lib() -> ctypes.CDLL:
         "sketch_srht_batch_set": (i32, [vp, vp, vp]),
         "sketch_srht_batch_run": (i32, [vp, vp]),
         "sketch_srht_batch_info": (i32, [vp, P(i32), P(i64), P(ctypes.c_float)]),
+        "sketch_srht_batch_adaptive_setup": (i32, [vp, P(i32), i32, ctypes.c_double, ctypes.c_double, vp]),
+        "sketch_srht_batch_adaptive_run": (i32, [vp, i32, vp]),
+        "sketch_srht_batch_adaptive_result": (i32, [vp, P(i32), P(i32), P(i32), P(ctypes.c_double),
+                                                    P(ctypes.c_double), vp]),
         "sketch_srht_batch_destroy": (None, [vp]),
         "sketch_selftest_wait": (i32, [vp]),
         "sketch_dims": (i32, [vp, P(i32), P(i64), P(i32), P(i32), P(i32)]),
@@ -460,6 +466,33 @@ class SrhtBatch:
 
     def run(self, stream=None) -> None:
         _check(lib().sketch_srht_batch_run(self.b, _stream(stream)), "sketch_srht_batch_run")
+
+    def adaptive_setup(self, d0, dd: int, eps_rel: float, eps_abs: float = 0.0, stream=None) -> None:
+        """Prepare Algorithm 1's loop per instance (operators SRHT(d0_i + dd) grown by dd-column
+        increments up to the columns the loop may use); synchronizes, not capturable."""
+        a = np.ascontiguousarray(np.asarray(d0, dtype=np.int32))
+        if a.shape != (self.count,):
+            raise ValueError("one d0 per instance")
+        _check(lib().sketch_srht_batch_adaptive_setup(self.b, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                      int(dd), float(eps_rel), float(eps_abs), _stream(stream)),
+               "sketch_srht_batch_adaptive_setup")
+
+    def adaptive_run(self, max_rounds: int = 0, stream=None) -> None:
+        """Enqueue the whole adaptive loop (asynchronous; capturable in one CUDA graph)."""
+        _check(lib().sketch_srht_batch_adaptive_run(self.b, int(max_rounds), _stream(stream)),
+               "sketch_srht_batch_adaptive_run")
+
+    def adaptive_result(self, stream=None) -> dict:
+        """Per instance: d, state (1 converged, 2 out of columns, 0 still running), tests, and
+        the last test's ||S^||_F and ||S~||_F."""
+        n = self.count
+        d, st, t = (np.zeros(n, np.int32) for _ in range(3))
+        nh, nt = np.zeros(n), np.zeros(n)
+        pi = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))  # noqa: E731
+        pd = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        _check(lib().sketch_srht_batch_adaptive_result(self.b, pi(d), pi(st), pi(t), pd(nh), pd(nt),
+                                                       _stream(stream)), "sketch_srht_batch_adaptive_result")
+        return dict(d=d, state=st, tests=t, nh=nh, nt=nt)
 
     def info(self) -> dict:
         c, u = ctypes.c_int32(), ctypes.c_int64()

@@ -209,3 +209,101 @@ def test_srht_batch_full_size_1024():
         assert err <= TOL, (int(i), err)
     for x in inst:
         x["op"].close()
+
+
+# ---- Algorithm 1 on the device for SRHT batches ------------------------------------------
+from oracle import adaptive as oad  # noqa: E402
+
+
+def make_adaptive(specs, dd, seed):
+    """specs: (n, d0, increments, h, amplitude); symmetric A_i = amplitude * K(X_i, X_i; h)."""
+    out = []
+    for k, (n, d0, incs, h, amp) in enumerate(specs):
+        X = torch.from_numpy(inputs.points(n, seed=seed + k)).cuda()
+        A = torch.empty((n, n), device="cuda")
+        jl.kernel_matrix(jl.generator(X, X, h), A)
+        A *= amp
+        d_max = d0 + (incs + 1) * dd
+        op = jl.Sketch("srht", n, d0 + dd, 1, 700 + k, d_max=d_max)
+        for _ in range(incs):
+            jl.sketch_increment(op.h, dd)
+        S = torch.full((n, d_max), SENTINEL, device="cuda")
+        out.append(dict(op=op, A=A, S=S, n=n, d0=d0, d_max=d_max, seed=700 + k))
+    return out
+
+
+def compare_adaptive(inst, res, dd, eps_rel, eps_abs):
+    for i, x in enumerate(inst):
+        ref = oad.adaptive(x["A"].double().cpu().numpy(), "srht", x["d0"], dd, 1, x["seed"], x["d_max"], eps_rel,
+                           eps_abs, which="S")
+        hist = ref["history"]
+        # decisions are compared up to the first test within the FP32 margin of a threshold
+        near = [h[3] > 0 and (abs(h[2] / h[3] - eps_rel) <= 2 * TOL or abs(h[2] - eps_abs) <= 2 * TOL * h[3])
+                for h in hist]
+        if any(near):
+            assert res["tests"][i] >= near.index(True) + 1, (i, res["tests"][i], near)
+            continue
+        assert res["tests"][i] == len(hist), (i, res["tests"][i], len(hist))
+        assert res["state"][i] == (1 if ref["converged"] else 2), (i, res["state"][i])
+        d = hist[-1][0] + dd
+        assert res["d"][i] == d, (i, res["d"][i], d)
+        nh0, nt0 = hist[-1][2], hist[-1][3]
+        assert abs(res["nt"][i] - nt0) <= TOL * nt0, (i, res["nt"][i], nt0)
+        assert abs(res["nh"][i] - nh0) <= TOL * nt0, (i, res["nh"][i], nh0, nt0)
+        got = x["S"][:, :d].double().cpu().numpy()
+        want = ref["S"][:, :d]
+        assert np.linalg.norm(got - want) <= TOL * np.linalg.norm(want), i
+        assert torch.all(x["S"][:, d:] == SENTINEL)
+
+
+SPECS_ADAPT = [(256, 64, 4, 0.5, 1.0),     # smooth: stops at once
+               (448, 32, 5, 0.12, 1.0),
+               (1000, 64, 4, 0.08, 1.0),   # order 1024, ragged rows
+               (2048, 128, 3, 0.2, 1.0),
+               (512, 96, 2, 0.03, 1.0),    # rough kernel: runs out of columns
+               (640, 64, 3, 0.3, 1e-9)]    # tiny entries: the absolute test stops it
+
+
+@pytest.mark.parametrize("eps_rel", [1e-2, 1e-4])
+def test_srht_batch_adaptive_matches_oracle(eps_rel):
+    dd, eps_abs = 32, 1e-7
+    inst = make_adaptive(SPECS_ADAPT, dd, seed=61)
+    items = [(x["op"].h, x["A"], x["S"], 0, x["d0"] + dd) for x in inst]
+    with jl.SrhtBatch(items) as B:
+        B.adaptive_setup([x["d0"] for x in inst], dd, eps_rel, eps_abs)
+        for x in inst:  # the tuner's runs wrote the first range: start from the sentinel again
+            x["S"].fill_(SENTINEL)
+        B.adaptive_run()
+        res = B.adaptive_result()
+        # the whole loop replayed from one captured CUDA graph gives the same result
+        first = [x["S"].clone() for x in inst]
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            B.adaptive_run(stream=s)
+        for x in inst:
+            x["S"].fill_(SENTINEL)
+        torch.cuda.synchronize()
+        g.replay()
+        res2 = B.adaptive_result(stream=s)
+    compare_adaptive(inst, res, dd, eps_rel, eps_abs)
+    for k in ("d", "state", "tests"):
+        assert np.array_equal(res[k], res2[k])
+    for x, f in zip(inst, first):
+        assert torch.equal(x["S"], f)
+        x["op"].close()
+
+
+def test_srht_batch_adaptive_argument_checks():
+    dd = 32
+    inst = make_adaptive([(300, 64, 2, 0.2, 1.0)], dd, seed=3)
+    x = inst[0]
+    with jl.SrhtBatch([(x["op"].h, x["A"], x["S"], 0, 96)]) as B:
+        with pytest.raises(jl.JLSketchError):
+            B.adaptive_setup([32], dd, 1e-3)  # the first block is d0 + dd = 96 wide, not 64
+        with pytest.raises(jl.JLSketchError):
+            B.adaptive_setup([64], 40, 1e-3)  # dd > 32
+        with pytest.raises(jl.JLSketchError):
+            B.adaptive_run()  # no setup yet
+    x["op"].close()
