@@ -881,7 +881,62 @@ def run_batch_adaptive(args):
     B.close()
     for op in ops:
         op.close()
+    line["srht"] = batch_adaptive_srht(args, w, ns, d0s, As, Sts)
     print(json.dumps(line))
+
+
+def batch_adaptive_srht(args, w, ns, d0s, As, Sts):
+    """The same loop with SRHT operators (S_i = A_i R_i = A_i^T R_i, A_i symmetric): an SRHT
+    samples at most nu_i columns, so d0_i <= nu_i - 64 and the increments stop at nu_i."""
+    import numpy as np
+    import torch
+
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    dd, incs = w["dd"], w["incs"]
+    ops, items, d0c = [], [], []
+    for i in range(w["count"]):
+        n = int(ns[i])
+        nu = 1 << (n - 1).bit_length()
+        d0 = min(int(d0s[i]), nu - 2 * dd)
+        k = min(incs, (nu - d0) // dd - 1)
+        op = jl.Sketch("srht", n, d0 + dd, 1, w["seed"] + i, d_max=d0 + (k + 1) * dd)
+        for _ in range(k):
+            jl.sketch_increment(op.h, dd)
+        ops.append(op)
+        d0c.append(d0)
+        items.append((op.h, As[i], Sts[i], 0, d0 + dd))
+    B = jl.SrhtBatch(items)
+    B.adaptive_setup(d0c, dd, w["eps_rel"], w["eps_abs"])
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=s):
+        B.adaptive_run(stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    with torch.cuda.stream(s):
+        for _ in range(args.steps):
+            g.replay()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_run = e0.elapsed_time(e1) / args.steps
+    res = B.adaptive_result()
+    bytes_streamed = float(sum(int(t) * int(n) * int(n) * 4 for t, n in zip(res["tests"], ns)))
+    hbm, _, _, _ = peaks()
+    out = {"adaptive_run_ms": round(t_run, 3), "gbs_of_streamed_bytes": round(bytes_streamed / t_run / 1e6, 1),
+           "pct_hbm_of_streamed_bytes": round(100 * bytes_streamed / t_run / 1e6 / hbm, 1),
+           "converged": int((res["state"] == 1).sum()), "out_of_columns": int((res["state"] == 2).sum()),
+           "still_running": int((res["state"] == 0).sum()), "tests_taken": int(res["tests"].sum()),
+           "mean_d": round(float(res["d"].mean()), 1), "ctas_per_sm": B.info()["ctas_per_sm"],
+           "d_cap": "d0_i <= nu_i - 64, d_max_i <= nu_i"}
+    B.close()
+    for op in ops:
+        op.close()
+    return out
 
 
 SRHT_SPLIT = dict(name="srht_nonpow2_fp32_n24000", n=24000, d=256, h=0.1, sample_rows=256, seed=20230203 + 6)
