@@ -200,13 +200,16 @@ int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t 
  * test, for callers that cannot allocate device memory.  (The paper has no
  * counterpart: this is an interface variant of adaptive_norm_test's arithmetic.)
  *
- * Who needs it: code that runs while a stream is being captured into a CUDA
- * graph (an allocation there breaks the capture), processes whose device memory
- * is owned by another allocator or a fixed pool, and callers that must not take
- * the device-wide synchronization that cudaMalloc/cudaFree can imply.  This call
+ * Who needs it: processes whose device memory is owned by another allocator or
+ * a fixed pool (a framework's caching allocator, an embedding application that
+ * hands the library no memory of its own), and callers that must not take the
+ * device-wide synchronization that cudaMalloc/cudaFree can imply.  This call
  * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  * Its scratch is a file-scope device array of 4.5 MiB inside the library, which
  * every GPU that loads the library holds until the process exits.
+ * It is not a call for code inside CUDA stream capture: it reads its norm
+ * partials back into pageable host memory and synchronizes `stream`, twice per
+ * call, and neither is allowed on a capturing stream.
  *
  *   Q        device, rows x q_cols, row-major (ldQ >= q_cols): an orthonormal
  *            basis supplied by the caller (may be NULL when q_cols == 0).
@@ -215,13 +218,16 @@ int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t 
  *   Writes *stop = ||S_hat||_F < eps_abs or ||S_hat||_F < eps_rel ||S_tilde||_F
  *   and, if not NULL, *norm_hat and *norm_tilde (host; FP64 sums).
  * Limits: q_cols <= 1024 and b <= 64 (larger requests return
- * SK_ERR_INVALID_ARG without touching the device).  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * SK_ERR_INVALID_ARG without touching the device); device ordinals 0 .. 63
+ * (the per-device address cache has 64 entries; a call with a higher ordinal
+ * current returns SK_ERR_UNSUPPORTED).  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it.  Q, S_tilde and S_hat must have the same dtype and row count
+ * and S_hat at least b columns: the call sees only their pointers.  All calls
  * share the one array and nothing in it needs to start at zero (each call
  * writes every element it reads), but calls whose work overlaps on the GPU
  * (other streams, other host threads) race on it: serialize them.
- * Synchronizes `stream`.  Errors: INVALID_ARG, DTYPE, UNSUPPORTED, DEVICE.
+ * Synchronizes `stream` (twice).  Errors: INVALID_ARG, DTYPE, UNSUPPORTED, DEVICE.
  */
 int sketch_project_norms_noalloc(const void* Q, int64_t ldQ, int32_t q_cols,
                                  const void* S_tilde, int64_t ldS, int64_t rows, int32_t b,

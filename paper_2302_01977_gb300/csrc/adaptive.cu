@@ -41,7 +41,7 @@ __global__ void scale_cols_kernel(T* S, int64_t rows, int64_t ld, int c0, int c1
 
 int scale_columns(void* S, int dtype, int64_t rows, int64_t ld, int c0, int c1, double factor, cudaStream_t s) {
   if (c1 <= c0) return SK_OK;
-  const unsigned grid = 152 * 8;
+  const unsigned grid = (unsigned)(8 * num_sms());
   if (dtype == SK_F32)
     scale_cols_kernel<float><<<grid, 256, 0, s>>>((float*)S, rows, ld, c0, c1, (float)factor);
   else
@@ -584,7 +584,8 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
     note_launch();
     rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, ldw, b, Lf, rinv, rows); note_launch();
   }
-  copy_block_kernel<T><<<152 * 4, 256, 0, s>>>(W, ldw, static_cast<T*>(B.Q) + B.cols, h->d_max, rows, b);
+  copy_block_kernel<T><<<(unsigned)(4 * num_sms()), 256, 0, s>>>(W, ldw, static_cast<T*>(B.Q) + B.cols, h->d_max,
+                                                                  rows, b);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   B.cols += b;
@@ -627,7 +628,7 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   Scratch sc;
   JLS_CHECK(ensure_scratch(h, slot, rows, dtype, wmax, &sc, nchunks));
   T* W = static_cast<T*>(sc.W);
-  const unsigned cgrid = 152 * 4;
+  const unsigned cgrid = (unsigned)(4 * num_sms());
   // columns [covered, c_split) not in Q yet, 64 at a time
   while (B.covered < c_split) {
     const int b = std::min(64, c_split - B.covered);
@@ -695,10 +696,11 @@ int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the stopping test's projection and norms.
 //
-// Some callers cannot allocate device memory: code running inside CUDA stream
-// capture (where cudaMalloc would break the capture), processes whose device
-// memory is fully owned by another allocator or pool, and callers that must
-// not block on the synchronization cudaMalloc/cudaFree imply.  For them,
+// Some callers cannot allocate device memory: processes whose device memory
+// is fully owned by another allocator or pool, and callers that must not block
+// on the device-wide synchronization cudaMalloc/cudaFree imply.  (Code inside
+// CUDA stream capture is not served: the call reads its norms back to the host
+// and synchronizes its stream.)  For them,
 // sketch_project_norms_noalloc takes its scratch (the tall-skinny product's
 // partial sums, the reduced product Q^T S and the norm partials) from the
 // file-scope array below instead of a handle.  Every GPU that loads the library
@@ -761,7 +763,7 @@ int project_norms_noalloc_t(const T* Q, int64_t ldQ, int q_cols, const T* St, in
   double* part = scratch;
   double* G = scratch + NOALLOC_PART;
   double* norms = G + NOALLOC_G;
-  copy_block_kernel<T><<<152 * 4, 256, 0, s>>>(St, ldS, Sh, ldH, rows, b); note_launch();
+  copy_block_kernel<T><<<(unsigned)(4 * num_sms()), 256, 0, s>>>(St, ldS, Sh, ldH, rows, b); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   double t2 = 0, h2 = 0;
   JLS_CHECK(sumsq_noalloc<T>(Sh, ldH, rows, b, norms, &t2, s));

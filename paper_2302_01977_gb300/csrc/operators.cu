@@ -269,7 +269,7 @@ int build_ccs_complex(sk_op* h, cudaStream_t s) {
     JLS_CHECK_CUDA(cudaMalloc(&h->sjlt_ents2, need));
     h->ents2_bytes = need;
   }
-  sjlt_expand2_kernel<<<4 * 152, 256, 0, s>>>(h->sjlt_ents, h->n, h->alpha, B, h->sjlt_ents2);
+  sjlt_expand2_kernel<<<(unsigned)(4 * num_sms()), 256, 0, s>>>(h->sjlt_ents, h->n, h->alpha, B, h->sjlt_ents2);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   const int tile = SJLT_TILE_F32;

@@ -282,9 +282,30 @@ def adaptive_norm_test_pair(h, S, St, delta_d: int, eps_rel: float, eps_abs: flo
     return (bool(stop[0]), nh[0], nt[0]), (bool(stop[1]), nh[1], nt[1])
 
 
+def _noalloc_shapes(Q, S_tilde, S_hat):
+    """Shape and dtype agreement of the allocation-free call's operands.  The C
+    side sees only pointers and S_tilde's shape and dtype, so an S_hat or a Q
+    with fewer rows, or of another dtype, would be read or written past its end
+    on the device; such calls are refused here."""
+    for t, name in ((S_tilde, "S_tilde"), (S_hat, "S_hat")) + (((Q, "Q"),) if Q is not None else ()):
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be 2-D")
+    rows, b = S_tilde.shape
+    if S_hat.shape[0] != rows or S_hat.shape[1] < b:
+        raise ValueError(f"S_hat must have S_tilde's {rows} rows and at least its {b} columns")
+    if S_hat.dtype != S_tilde.dtype:
+        raise ValueError("S_hat must have S_tilde's dtype")
+    if Q is not None:
+        if Q.shape[0] != rows:
+            raise ValueError(f"Q must have S_tilde's {rows} rows")
+        if Q.dtype != S_tilde.dtype:
+            raise ValueError("Q must have S_tilde's dtype")
+
+
 def sketch_project_norms_noalloc(Q, S_tilde, S_hat, eps_rel: float, eps_abs: float, stream=None):
     """(I - Q Q^T)^2 S_tilde into S_hat without device allocation; returns
     (stop, ||S_hat||_F, ||S_tilde||_F).  Q may be None for an empty basis."""
+    _noalloc_shapes(Q, S_tilde, S_hat)
     _check_2d(S_tilde, "S_tilde")
     _check_2d(S_hat, "S_hat")
     q_ptr, ldq, qc = None, 0, 0

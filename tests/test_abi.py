@@ -115,3 +115,29 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(jl, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         jl.lib()
+
+
+def test_noalloc_wrapper_refuses_mismatched_operands():
+    """The allocation-free call's C side sees only pointers and S_tilde's shape
+    and dtype; the binding refuses operands that would be read or written past
+    their ends (checked on CPU tensors: the refusal comes before any device use)."""
+    import torch
+    St = torch.zeros((64, 8), dtype=torch.float32)
+    ok_hat = torch.zeros((64, 8), dtype=torch.float32)
+    ok_q = torch.zeros((64, 16), dtype=torch.float32)
+    bad = [
+        (ok_q, St, torch.zeros((63, 8)), "rows"),                      # S_hat has fewer rows
+        (ok_q, St, torch.zeros((64, 7)), "columns"),                   # S_hat has fewer columns
+        (ok_q, St, torch.zeros((64, 8), dtype=torch.float64), "dtype"),  # S_hat of another dtype
+        (torch.zeros((60, 16)), St, ok_hat, "rows"),                   # Q has fewer rows
+        (torch.zeros((64, 16), dtype=torch.float64), St, ok_hat, "dtype"),  # Q of another dtype
+        (ok_q, torch.zeros(64), ok_hat, "2-D"),                        # S_tilde not 2-D
+    ]
+    for Q, S_t, S_h, what in bad:
+        with pytest.raises(ValueError, match=what):
+            jl.sketch_project_norms_noalloc(Q, S_t, S_h, 1e-2, 0.0)
+    # consistent operands pass the shape checks and stop at the device check
+    with pytest.raises(ValueError, match="CUDA"):
+        jl.sketch_project_norms_noalloc(ok_q, St, ok_hat, 1e-2, 0.0)
+    with pytest.raises(ValueError, match="CUDA"):
+        jl.sketch_project_norms_noalloc(None, St, torch.zeros((64, 9)), 1e-2, 0.0)

@@ -106,6 +106,32 @@ def test_sjlt_outer_and_inner_forms_brute_force(kind):
         assert np.allclose(X, St_bf, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("kind,alpha", [("sjlt_block", 4), ("srht", 1), ("gauss", 1)])
+def test_apply_t_rectangular_brute_force(kind, alpha):
+    """S' = A^T R for a rectangular, nonsymmetric A (m x n, R m x d): a triple
+    loop over S'[j, c] = sum_i A[i, j] R[i, c], a unit matrix e_i e_j^T that
+    must move row i of R to row j of S', and the shape, which a transposed
+    operand would change."""
+    m, n, d = 40, 23, 8
+    A = inputs.dense_matrix(m, n, seed=12)
+    R = ops.Operator(kind, m, d, alpha, seed=13).dense()
+    St = sk.apply_t(A, R)
+    assert St.shape == (n, d)
+    bf = np.zeros((n, d))
+    for j in range(n):
+        for c in range(d):
+            bf[j, c] = sum(A[i, j] * R[i, c] for i in range(m))
+    assert np.allclose(St, bf, rtol=1e-13, atol=1e-13)
+    E = np.zeros((m, n))
+    E[31, 5] = 1.0
+    pick = sk.apply_t(E, R)
+    expect = np.zeros((n, d))
+    expect[5] = R[31]
+    assert np.array_equal(pick, expect)
+    with pytest.raises(ValueError):
+        sk.apply_t(A.T, R)  # rows(A) must equal rows(R)
+
+
 # --- SRHT ----------------------------------------------------------------
 
 @pytest.mark.parametrize("nu", [1, 2, 4, 16, 64])

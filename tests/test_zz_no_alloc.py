@@ -1,11 +1,12 @@
 """The allocation-free projection/norms entry point against adaptive_norm_test.
 
 sketch_project_norms_noalloc serves callers that cannot allocate device memory
-(code inside stream capture, processes whose memory belongs to another pool).
+(processes whose device memory belongs to another allocator or a fixed pool).
 Here it is called through the C ABI twice in a row (before and after an
 increment) and its norms and stop decision are compared with the handle-based
 adaptive_norm_test on the same sketch, to the parity tolerances used elsewhere
-(FP64 1e-9 of ||S~||_F, FP32 1e-5).  The basis it needs is built on the host
+(FP64 1e-9 of ||S~||_F, FP32 1e-5); around the second call the device's free
+memory must not change.  The basis it needs is built on the host
 with numpy from the GPU sketch.  This file is collected last on purpose.
 """
 import numpy as np
@@ -44,7 +45,13 @@ def test_noalloc_matches_adaptive_norm_test_twice(dtype):
             Q = np.linalg.qr(Sh[:, :d])[0]
             Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(tdt).cuda()
             S_hat = torch.full((n, dd), np.nan, dtype=tdt, device="cuda")
+            if call == 1:  # every kernel of the call has run once: nothing is loaded lazily now
+                torch.cuda.synchronize()
+                free0 = torch.cuda.mem_get_info()[0]
             stop1, nh1, nt1 = jl.sketch_project_norms_noalloc(Qd, S[:, d:w], S_hat, 1e-3, 1e-30)
+            if call == 1:  # the call took no device memory
+                torch.cuda.synchronize()
+                assert torch.cuda.mem_get_info()[0] == free0
             assert abs(nt1 - nt0) <= tol * nt0
             assert abs(nh1 - nh0) <= tol * nt0
             if abs(nh0 / nt0 - 1e-3) > 2 * tol:
