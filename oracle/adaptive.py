@@ -5,7 +5,13 @@ which is this project's reading of the stopping test's scope (the paper applies
 it per HSS node, with eps / level(tau)):
 
 1. R <- JL-Operator(d0 + Delta-d, n); S <- A R (and S' <- A^T R).
-2. Q <- orthonormal basis of S(:, 1:d)   (QR of the first d columns).
+2. Q <- orthonormal basis of the range of S(:, 1:d).  Sec. 3 defines S^ as
+   the projection of the new columns onto the orthogonal complement of the
+   current sketch; when S(:, 1:d) is rank deficient (an SJLT column without
+   entries, an exactly low-rank A) a d-column QR factor would also span
+   directions outside that range, so the basis is the left singular vectors
+   of S(:, 1:d) above the numerical rank threshold sigma_1 max(m, d) eps
+   (numpy's matrix_rank default; an SVD is the library step).
 3. S~ <- S(:, d+1 : d+Delta-d)             (the last Delta-d columns).
 4. S^ <- (I - Q Q^T)^2 S~                  (two steps of block Gram-Schmidt,
    the remark after Eq. (3.1)).
@@ -16,7 +22,7 @@ it per HSS node, with eps / level(tau)):
 
 S is recomputed from the grown R at every step (the plain definition), so the
 CUDA path's incremental update (rescale old columns, sketch only the new ones)
-is checked against it.  QR is numpy's (LAPACK Householder), a library step.
+is checked against it.
 When both S and S' are tested, the loop stops when both tests pass.
 """
 from __future__ import annotations
@@ -33,9 +39,21 @@ def project_twice(Q: np.ndarray, B: np.ndarray) -> np.ndarray:
     return B - Q @ (Q.T @ B)
 
 
+def range_basis(M: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of the range of M: its left singular vectors whose
+    singular values exceed sigma_1 max(M.shape) eps (FP64)."""
+    if M.shape[1] == 0:
+        return np.zeros((M.shape[0], 0))
+    U, sv, _ = np.linalg.svd(M, full_matrices=False)
+    if sv[0] == 0.0:
+        return U[:, :0]
+    r = int(np.count_nonzero(sv > sv[0] * max(M.shape) * np.finfo(np.float64).eps))
+    return U[:, :r]
+
+
 def norm_test(S: np.ndarray, d: int, dd: int, eps_rel: float, eps_abs: float):
     """One stopping test on the columns of S: returns (stop, ||S^||_F, ||S~||_F)."""
-    Q = np.linalg.qr(S[:, :d])[0]
+    Q = range_basis(np.asarray(S[:, :d], dtype=np.float64))
     St = S[:, d:d + dd]
     Sh = project_twice(Q, St)
     nh = float(np.linalg.norm(Sh))

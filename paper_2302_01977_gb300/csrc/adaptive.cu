@@ -4,17 +4,18 @@
 // remark after it; Algorithm 1's S~ = last Delta-d columns):
 //   S^ = (I - Q Q^T)^2 S~,  stop = ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
 // Q is an orthonormal basis of the earlier sketch columns kept per handle and
-// slot.  New columns are absorbed 64 at a time by [block Gram-Schmidt pass
-// against Q, Cholesky-QR pass] twice (the first Gram matrix and factor in
-// FP64).  A column whose residual is at the data's noise level relative to the
-// block before its projection (a pivot at or below 1e-13 of that block's sum
-// of squares for FP32 data, 1e-26 for FP64) is dropped, so a rank-deficient
-// block adds zero columns to Q, which do not change Q Q^T: normalizing such
-// a residual, which is rounding error along Q, would cost Q its orthogonality.
-// The tested block's second projection is the one between its two Cholesky-QR
-// passes: with W = (I - Q Q^T) S~ = W1 L1^T after the first pass,
-// ||S^||_F^2 = ||(I - Q Q^T) W1 L1^T||_F^2 = tr(L1 G2 L1^T), G2 the second
-// pass's Gram matrix, so a test costs two projections, not three.
+// slot.  New columns are absorbed 64 at a time by [two block Gram-Schmidt
+// passes against Q, Cholesky-QR, one more pass, Cholesky-QR] (the first Gram
+// matrix and factor in FP64).  For FP32 data the first pass forms W - Q G in
+// double-FP32: FP32 rounding of W - Q G is about 1e-7 of W, spread over every
+// direction, as large as the residual near eps_rel = 1e-6; the second pass
+// removes the part along Q that the FP32 product Q^T W leaves.  A column whose
+// residual is below 1e-10 (FP32 data) or 1e-13 (FP64) of the block before its
+// projection is dropped (a zero column of Q, which does not change Q Q^T), so
+// a block with zero columns (an SJLT column without entries) adds zero columns.
+// The tested block's ||S^||_F^2 = ||(I - Q Q^T)^2 S~||_F^2 is the trace of the
+// Gram matrix its first Cholesky-QR pass factors, so a test costs only the
+// projections of its absorption.
 //
 // Tall-skinny products X^T Y (rows ~ n, widths <= 512) run on CUDA cores: each
 // CTA reduces a chunk of rows into a 64 x 64 tile of partial sums, chunks are
@@ -188,6 +189,90 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < 4; ++c) {
       const int j = tx * 4 + c;
       if (j < q) Y[r * ldy + j] = SUB ? Y[r * ldy + j] - acc[a][c] : acc[a][c];
+    }
+  }
+}
+
+// (hi, lo) <- (hi, lo) - a m as an unevaluated double-FP32 sum: the product
+// is split exactly (p + pe = a m, pe from an FMA) and the subtraction of p by
+// Knuth's TwoSum (s + e = hi - p exactly); lo collects e - pe.  The _rn
+// intrinsics keep the compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float a, float m) {
+  const float p = __fmul_rn(a, m);
+  const float pe = __fmaf_rn(a, m, -p);
+  const float s = __fsub_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fsub_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fadd_rn(p, bb));
+  lo = __fsub_rn(__fadd_rn(lo, e), pe);
+  hi = s;
+}
+
+// Y[r][j] -= sum_{i < p} X[r][i] M[i][j] for FP32 data with the difference
+// formed in double-FP32 and rounded once (about 44 bits of Y's scale): the
+// first projection of a block against Q, where Y - X M is small next to Y and
+// FP32 rounding of Y's size would reach the residual the stopping test
+// measures.  Same tiling as rows_small_gemm (M rounded to FP32); Y must not
+// alias X.
+__global__ void __launch_bounds__(256)
+    rows_small_gemm_df(const float* __restrict__ X, int64_t ldx, int p, const double* __restrict__ M, int64_t ldm,
+                       int q, float* __restrict__ Y, int64_t ldy, int64_t rows) {
+  __shared__ __align__(16) float xs[32][68];  // [i][row]
+  __shared__ __align__(16) float ms[32][68];  // [i][col]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int xi = threadIdx.x & 31, xr0 = threadIdx.x >> 5;
+  const int mc = threadIdx.x & 63, mi0 = threadIdx.x >> 6;
+  float xv_n[8], mv_n[8];
+  auto fetch = [&](int i0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t r = r0 + xr0 + 8 * u;
+      xv_n[u] = (r < rows && i0 + xi < p) ? X[r * ldx + i0 + xi] : 0.f;
+      const int i = i0 + mi0 + 4 * u;
+      mv_n[u] = (i < p && mc < q) ? (float)M[(int64_t)i * ldm + mc] : 0.f;
+    }
+  };
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = r0 + ty * 4 + a;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = tx * 4 + c;
+      hi[a][c] = (r < rows && j < q) ? Y[r * ldy + j] : 0.f;
+      lo[a][c] = 0.f;
+    }
+  }
+  fetch(0);
+  for (int i0 = 0; i0 < p; i0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      xs[xi][xr0 + 8 * u] = xv_n[u];
+      ms[mi0 + 4 * u][mc] = mv_n[u];
+    }
+    __syncthreads();
+    if (i0 + 32 < p) fetch(i0 + 32);
+#pragma unroll 4
+    for (int ii = 0; ii < 32; ++ii) {
+      const float4 xv = *reinterpret_cast<const float4*>(&xs[ii][ty * 4]);
+      const float4 mv = *reinterpret_cast<const float4*>(&ms[ii][tx * 4]);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+      const float ma[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) df_sub(hi[a][c], lo[a][c], xa[a], ma[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = r0 + ty * 4 + a;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = tx * 4 + c;
+      if (j < q) Y[r * ldy + j] = __fadd_rn(hi[a][c], lo[a][c]);
     }
   }
 }
@@ -384,6 +469,18 @@ namespace {
 
 constexpr int NORM_GRID = 256;
 
+// out[0] = tr(G) for the b x b FP64 Gram matrix G = W^T W of the tested block
+// after its two projections (the precise absorption), i.e.
+// ||(I - Q Q^T)^2 S~||_F^2, summed in a fixed order; out[1 .. nout) = 0.  One warp.
+__global__ void gram_trace_kernel(const double* __restrict__ G, int b, double* __restrict__ out, int nout) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < b; i += 32) v += G[(int64_t)i * b + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) out[0] = v > 0.0 ? v : 0.0;
+  for (int e = 1 + threadIdx.x; e < nout; e += 32) out[e] = 0.0;
+}
+
 // ||W2 L^T||_F^2 = tr(L G2 L^T) for the b x b factor L (row-major, type T,
 // zero above the diagonal) of the first Cholesky-QR pass and the FP64 Gram
 // matrix G2 = W2^T W2 of its projected output W2 = (I - Q Q^T) W L^{-T}:
@@ -435,8 +532,8 @@ __global__ void __launch_bounds__(256) lgl_trace_kernel(const T* __restrict__ L,
   for (int e = 1 + t; e < nout; e += 256) out[e] = 0.0;
 }
 
-// Where the tested block's ||S^||^2 goes once the second Gram matrix exists
-// (NORM_GRID partials after the ||S~||^2 ones), and the host copy of both.
+// Where the tested block's ||S^||^2 goes once it is known (NORM_GRID partials
+// after the ||S~||^2 ones), and the host copy of both.
 constexpr double kDropPass2 = 1e-2;
 
 struct TestOut {
@@ -498,35 +595,47 @@ int tsgemm(const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q, int64
   return SK_OK;
 }
 
-// W (rows x b, ld ldw) <- W - Q G for G = Q^T W (p x b, FP64, ld b), 64 columns at a time
+// W (rows x b, ld ldw) <- W - Q G for G = Q^T W (p x b, FP64, ld b), 64 columns at a time;
+// with `df` (FP32 data) the difference is formed in double-FP32
 template <typename T>
-int sub_qg(T* W, int64_t ldw, int b, const T* Q, int64_t ldq, int p, const double* G, int64_t rows, cudaStream_t s) {
+int sub_qg(T* W, int64_t ldw, int b, const T* Q, int64_t ldq, int p, const double* G, int64_t rows, cudaStream_t s,
+           bool df = false) {
   for (int j0 = 0; j0 < b; j0 += 64) {
     const int q = std::min(64, b - j0);
-    rows_small_gemm<T, true><<<(unsigned)((rows + 63) / 64), 256, 0, s>>>(Q, ldq, p, G + j0, b, q, W + j0, ldw,
-                                                                            rows); note_launch();
+    const unsigned grid = (unsigned)((rows + 63) / 64);
+    if constexpr (sizeof(T) == 4) {
+      if (df) {
+        rows_small_gemm_df<<<grid, 256, 0, s>>>(Q, ldq, p, G + j0, b, q, W + j0, ldw, rows); note_launch();
+        continue;
+      }
+    }
+    rows_small_gemm<T, true><<<grid, 256, 0, s>>>(Q, ldq, p, G + j0, b, q, W + j0, ldw, rows); note_launch();
   }
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 
-// W (rows x b, ld ldw) <- (I - Q Q^T)^passes W; project_twice: the test's two passes
+// W (rows x b, ld ldw) <- (I - Q Q^T)^passes W.  With df_first the first
+// difference is formed in double-FP32 (FP32 data): W - Q G is then exact to
+// about 1e-13 of W, and the part along Q that the FP32 product Q^T W leaves
+// (about sqrt(q) 2^-24 of W) is removed by the next pass.
 template <typename T>
 int project_passes(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc,
-                   int nchunks, int passes, cudaStream_t s) {
+                   int nchunks, int passes, cudaStream_t s, bool df_first = false) {
   if (B.cols == 0) return SK_OK;
   const T* Q = static_cast<const T*>(B.Q);
   for (int pass = 0; pass < passes; ++pass) {
     JLS_CHECK(tsgemm<T>(Q, h->d_max, B.cols, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
-    JLS_CHECK(sub_qg<T>(W, ldw, b, Q, h->d_max, B.cols, sc.G, rows, s));
+    JLS_CHECK(sub_qg<T>(W, ldw, b, Q, h->d_max, B.cols, sc.G, rows, s, df_first && pass == 0));
   }
   return SK_OK;
 }
 
+// the test's two passes, (I - Q Q^T)^2 W (the first in double-FP32 with the precise steps)
 template <typename T>
 int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc,
                   int nchunks, cudaStream_t s) {
-  return project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 2, s);
+  return project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 2, s, B.precise);
 }
 
 // NORM_GRID partial sums of squares of W into `part` (no synchronization)
@@ -537,37 +646,53 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
   return SK_OK;
 }
 
-// Orthonormalize the b <= 64 columns of W (ld ldw) and append them to Q, by
-// [project against Q, Cholesky-QR] twice.  With `project`, W arrives as it
-// is and the first projection is made here; without, W arrives projected
-// (the later chunks of a wide tested block, projected twice for the test).
+// Orthonormalize the b <= 64 columns of W (ld ldw) and append them to Q.
+// Plain steps: [project against Q, Cholesky-QR] twice.  Precise steps (FP32
+// data, B.precise): [project twice, Cholesky-QR, project, Cholesky-QR], the
+// first projection's difference formed in double-FP32.  With `project`, W
+// arrives as it is and its first projection(s) are made here; without, W
+// arrives projected (the later chunks of a wide tested block, projected twice
+// for the test).
 // The first factorization is in FP64 (the Gram matrix squares W's condition
 // number); the second Gram matrix is the identity up to the first pass's
 // rounding, so with FP32 data it is factored in FP32.  The projection between
 // the passes removes the rounding along Q that the first pass's triangular
 // solve magnifies by the block's condition number.  With `test`, W is the
-// tested block and its ||S^||^2 is taken from the second Gram matrix
-// (lgl_trace_kernel), copied to the host with ||S~||^2 and signalled.
+// tested block; its ||S^||^2 = ||(I - Q Q^T)^2 S~||^2 is the trace of the
+// first Gram matrix with the precise steps (gram_trace_kernel), and
+// tr(L1 G2 L1^T) from the first factor and the second Gram matrix with the
+// plain ones (lgl_trace_kernel: the block projected once, factored, projected
+// again); it is copied to the host with ||S~||^2 and signalled.
 template <typename T>
 int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
                  bool project, const double* ref, cudaStream_t s, const TestOut* test = nullptr) {
-  if (project) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
+  const bool precise = B.precise;
+  if (project) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, precise ? 2 : 1, s, precise));
   T* Lf = reinterpret_cast<T*>(sc.U);
   T* rinv = Lf + 64 * 64;
   constexpr int RT = trsm_rows<T>();
   const unsigned tgrid = (unsigned)((rows + RT - 1) / RT);
-  // the first pass drops columns whose residual is at the data's noise level
-  // relative to the block before its projection (ref: NORM_GRID partials of
-  // its sum of squares): FP32 3.2e-7, FP64 1e-13.  The second pass's columns
-  // had unit norm before the projection between the passes; one that it
-  // shrinks below 0.1 (pivot <= kDropPass2) was rounding along Q that the
-  // first pass normalized, and is dropped rather than renormalized.
-  const double tau = sizeof(T) == 4 ? 1e-13 : 1e-26;
+  // The first pass drops columns whose residual is at the noise level of the
+  // block before its projection (ref: NORM_GRID partials of its sum of
+  // squares).  Plain steps on FP32 data: 3.2e-7 of the block, the rounding of
+  // an FP32 projection (normalizing it, rounding along Q, would cost Q its
+  // orthogonality).  Precise steps: 1e-10, a column that is zero in the data
+  // (an SJLT column without entries) or rounding.  FP64 data: 1e-13.  The
+  // second pass's columns had unit norm before the projection between the
+  // passes; one that it shrinks below 0.1 (pivot <= kDropPass2) was rounding
+  // along Q that the first pass normalized, and is dropped rather than
+  // renormalized.
+  const double tau = sizeof(T) == 8 ? 1e-26 : (precise ? 1e-20 : 1e-13);
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
     JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
-    if (pass == 1 && test) {  // Lf still holds the first pass's factor
-      lgl_trace_kernel<T><<<1, 256, 0, s>>>(Lf, sc.G, b, test->norms + NORM_GRID, NORM_GRID); note_launch();
+    if (test && pass == (precise ? 0 : 1)) {
+      if (precise) {
+        gram_trace_kernel<<<1, 32, 0, s>>>(sc.G, b, test->norms + NORM_GRID, NORM_GRID);
+      } else {  // Lf still holds the first pass's factor
+        lgl_trace_kernel<T><<<1, 256, 0, s>>>(Lf, sc.G, b, test->norms + NORM_GRID, NORM_GRID);
+      }
+      note_launch();
       JLS_CHECK_CUDA(cudaMemcpyAsync(test->host, test->norms, 2 * NORM_GRID * sizeof(double),
                                      cudaMemcpyDeviceToHost, s));
       JLS_CHECK_CUDA(cudaEventRecord(test->ready, s));
@@ -597,28 +722,35 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
 // next Delta-d columns, starts from the basis of every earlier column).
 // Columns of S before c_split that Q does not cover yet (the first d0, or
 // after a restart) are absorbed first.  A tested block of up to 64 columns is
-// projected once, factored, projected again, and ||S^||^2 = tr(L1 G2 L1^T)
-// comes from the first factor and the second Gram matrix (lgl_trace_kernel);
-// a wider one is projected twice and its norm summed before it is absorbed.
+// projected twice and ||S^||^2 is the trace of the Gram matrix its first
+// Cholesky-QR pass factors (gram_trace_kernel); a wider one is projected
+// twice and its norm summed before it is absorbed in chunks of 64.
 // The two norms are copied to the slot's pinned host buffer and an event is
 // recorded, while the extension of Q runs on; norm_test_finish waits for
 // that event.  Each slot (S, S') has its
 // own basis, scratch, host buffer and event, so the two tests can run on two
 // streams at once.
 template <typename T>
-int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
-                        cudaStream_t s) {
+int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ldS, int dtype, double eps_rel,
+                        int c_split, int c_end, cudaStream_t s) {
   Basis& B = h->basis[slot];
-  if (!B.Q || B.rows != rows || B.dtype != dtype || c_split < B.covered) {
-    if (B.Q) cudaFree(B.Q);
-    B.Q = nullptr;
-    JLS_CHECK_CUDA(cudaMalloc(&B.Q, (size_t)rows * h->d_max * sizeof(T)));
+  // FP32 data with a tight eps_rel takes the precise steps; a basis built by
+  // the other steps is started again
+  const bool precise = sizeof(T) == 4 && eps_rel < kPreciseBelow;
+  const bool same_shape = B.Q && B.rows == rows && B.dtype == dtype;
+  if (!same_shape || c_split < B.covered || B.precise != precise) {
+    if (!same_shape) {
+      if (B.Q) cudaFree(B.Q);
+      B.Q = nullptr;
+      JLS_CHECK_CUDA(cudaMalloc(&B.Q, (size_t)rows * h->d_max * sizeof(T)));
+    }
     JLS_CHECK_CUDA(cudaMemsetAsync(B.Q, 0, (size_t)rows * h->d_max * sizeof(T), s));
     B.rows = rows;
     B.dtype = dtype;
     B.cols = 0;
     B.covered = 0;
   }
+  B.precise = precise;
   if (!h->host_norms[slot]) JLS_CHECK_CUDA(cudaMallocHost(&h->host_norms[slot], 2 * NORM_GRID * sizeof(double)));
   if (!h->norms_ready[slot]) JLS_CHECK_CUDA(cudaEventCreateWithFlags(&h->norms_ready[slot], cudaEventDisableTiming));
   const int bt = c_end - c_split;
@@ -641,7 +773,7 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
-  if (bt <= 64) {  // one chunk: ||S^|| from its absorption's second Gram matrix
+  if (bt <= 64) {  // one chunk: ||S^|| from its absorption's first Gram matrix
     const TestOut out{sc.norms, h->host_norms[slot], h->norms_ready[slot]};
     JLS_CHECK(absorb_block<T>(h, B, W, wmax, bt, rows, sc, nchunks, true, sc.norms, s, &out));
     B.covered = c_end;
@@ -664,11 +796,11 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
 
 }  // namespace
 
-int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
-                      int c_end, cudaStream_t s) {
+int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, double eps_rel,
+                      int c_split, int c_end, cudaStream_t s) {
   if (dtype == SK_F32)
-    return norm_test_enqueue_t<float>(h, slot, (const float*)S, rows, ldS, dtype, c_split, c_end, s);
-  return norm_test_enqueue_t<double>(h, slot, (const double*)S, rows, ldS, dtype, c_split, c_end, s);
+    return norm_test_enqueue_t<float>(h, slot, (const float*)S, rows, ldS, dtype, eps_rel, c_split, c_end, s);
+  return norm_test_enqueue_t<double>(h, slot, (const double*)S, rows, ldS, dtype, eps_rel, c_split, c_end, s);
 }
 
 int norm_test_finish(sk_op* h, int slot, double eps_rel, double eps_abs, int* stop, double* nh, double* nt) {
@@ -687,7 +819,7 @@ int norm_test_finish(sk_op* h, int slot, double eps_rel, double eps_abs, int* st
 
 int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split, int c_end,
               double eps_rel, double eps_abs, int* stop, double* nh, double* nt, cudaStream_t s) {
-  JLS_CHECK(norm_test_enqueue(h, slot, S, rows, ldS, dtype, c_split, c_end, s));
+  JLS_CHECK(norm_test_enqueue(h, slot, S, rows, ldS, dtype, eps_rel, c_split, c_end, s));
   return norm_test_finish(h, slot, eps_rel, eps_abs, stop, nh, nt);
 }
 

@@ -5,17 +5,19 @@
 // [c_hi - dd, c_hi) of S'_i, the test takes S~ = those dd columns,
 // S^ = (I - Q Q^T)^2 S~ (two block Gram-Schmidt passes, the remark after
 // Eq. (3.1)) and stops when ||S^||_F < eps_abs or ||S^||_F < eps_rel ||S~||_F.
-// The two passes are those of S~'s own absorption: S~ is projected, factored
-// (W = W1 L1^T), projected again, and ||S^||_F^2 = tr(L1 G2 L1^T) with G2 the
-// Gram matrix of (I - Q Q^T) W1, so a test costs two projections.
+// The two passes are those of S~'s own absorption.  At eps_rel below
+// kPreciseBelow (the precise steps) S~ is projected twice, the first
+// difference W - Q G in double-FP32, and ||S^||_F^2 is the trace of the Gram
+// matrix its first Cholesky-QR pass factors; otherwise S~ is projected,
+// factored (W = W1 L1^T), projected again, and ||S^||_F^2 = tr(L1 G2 L1^T)
+// with G2 the Gram matrix of (I - Q Q^T) W1.  Either way a test costs the
+// absorption's projections only.
 // Q is an orthonormal basis of the earlier columns, kept per instance in HBM:
 // the first d0 columns are absorbed before the first test (32 at a time), and
 // after a failed test the projected S^ is absorbed, so the next test starts
-// from the basis of every earlier column.  Blocks are absorbed by [project,
-// Cholesky-QR] twice; a Cholesky pivot at or below 1e-13 of the block's sum of
-// squares before the projection (its FP32 noise level), or at or below 1e-26
-// of the largest Gram diagonal, drops its column (a zero column of Q, which
-// leaves Q Q^T unchanged).  The decision moves the instance's column range on
+// from the basis of every earlier column.  A Cholesky pivot below the drop
+// level (absorb_begin) drops its column (a zero column of Q, which leaves
+// Q Q^T unchanged).  The decision moves the instance's column range on
 // by dd, or retires it (converged, or no room left in R_i); a one-CTA kernel
 // then renumbers the units of the active instances for the next batched launch.
 // Nothing returns to the host between rounds, so a whole adaptive run, all
@@ -374,6 +376,110 @@ __device__ void w_minus_qg(const Ctx& c, int q) {
   }
 }
 
+// (hi, lo) <- (hi, lo) - a g as an unevaluated double-FP32 sum: the product is
+// split exactly (p + pe = a g, pe from an FMA) and the subtraction of p by
+// Knuth's TwoSum (s + e = hi - p exactly); lo collects e - pe.  The explicit
+// _rn intrinsics keep the compiler from contracting or reassociating the steps.
+__device__ __forceinline__ void df_sub(float& hi, float& lo, float a, float g) {
+  const float p = __fmul_rn(a, g);
+  const float pe = __fmaf_rn(a, g, -p);
+  const float s = __fsub_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fsub_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fadd_rn(p, bb));
+  lo = __fsub_rn(__fadd_rn(lo, e), pe);
+  hi = s;
+}
+
+// W <- W - Q[:, :q] Gs on this CTA's rows with the difference formed in
+// double-FP32 (about 44 bits of W's scale), for the first projection of a
+// block: there W - Q G is small next to W, and FP32 rounding of that size
+// (about 1e-7 of W, spread over every direction) would reach the residual the
+// stopping test measures.  Passes of PR rows; Q staged transposed KC columns at
+// a time as in w_minus_qg; a thread owns a 4 x 4 tile (rows 4 rg .. 4 rg + 3,
+// columns 4 cg .. 4 cg + 3) over all q columns of Q, so no partial sums are
+// exchanged.  The result is rounded to FP32 once.
+__device__ void w_minus_qg_df(const Ctx& c, int q) {
+  float* Qt = reinterpret_cast<float*>(c.stage);  // [2][KC][PR + 4]
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;  // 8 column groups x 64 row groups
+  const int srow = threadIdx.x & (PR - 1), spart = threadIdx.x / PR;  // staging: row, which KC/2 columns
+  static_assert(AT == 512 && PR == 256 && BW == 32, "a 4 x 4 tile per thread covers a pass");
+  for (int64_t p0 = c.r0; p0 < c.r1; p0 += PR) {
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = p0 + rg * 4 + i;
+      const float4 w = r < c.r1 ? *reinterpret_cast<const float4*>(c.W + r * BW + cg * 4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      hi[i][0] = w.x;
+      hi[i][1] = w.y;
+      hi[i][2] = w.z;
+      hi[i][3] = w.w;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lo[i][j] = 0.f;
+    }
+    const int64_t rt = p0 + srow;
+    const bool rin = rt < c.r1;
+    const bool busy = p0 + rg * 4 < c.r1;
+    float4 pre[KC / 8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int u = 0; u < KC / 8; ++u) {
+        const int k = k0 + spart * (KC / 2) + 4 * u;
+        pre[u] = (rin && k < q) ? *reinterpret_cast<const float4*>(c.Q + rt * c.ldq + k)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto stage_q = [&](int buf) {
+#pragma unroll
+      for (int u = 0; u < KC / 8; ++u) {
+        float* d = Qt + buf * QT_FLOATS + (spart * (KC / 2) + 4 * u) * (PR + 4) + srow;
+        d[0] = pre[u].x;
+        d[PR + 4] = pre[u].y;
+        d[2 * (PR + 4)] = pre[u].z;
+        d[3 * (PR + 4)] = pre[u].w;
+      }
+    };
+    fetch(0);
+    stage_q(0);
+    if (KC < q) fetch(KC);
+    __syncthreads();
+    for (int k0 = 0, st = 0; k0 < q; k0 += KC, ++st) {
+      if (k0 + KC < q) {
+        stage_q((st + 1) & 1);
+        if (k0 + 2 * KC < q) fetch(k0 + 2 * KC);
+      }
+      if (busy) {
+        const float* Qb = Qt + (st & 1) * QT_FLOATS + rg * 4;
+        const float* Gb = c.Gs + k0 * BW + cg * 4;
+        const int kn = min(KC, q - k0);  // a multiple of 8
+        for (int k8 = 0; k8 < kn; k8 += 8) {
+#pragma unroll
+          for (int kk = k8; kk < k8 + 8; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(Qb + kk * (PR + 4));
+            const float4 g = *reinterpret_cast<const float4*>(Gb + kk * BW);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) df_sub(hi[i][j], lo[i][j], av[i], gv[j]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = p0 + rg * 4 + i;
+      if (r < c.r1)
+        *reinterpret_cast<float4*>(c.W + r * BW + cg * 4) =
+            make_float4(__fadd_rn(hi[i][0], lo[i][0]), __fadd_rn(hi[i][1], lo[i][1]),
+                        __fadd_rn(hi[i][2], lo[i][2]), __fadd_rn(hi[i][3], lo[i][3]));
+    }
+    __syncthreads();
+  }
+}
+
 // 1/sqrt(x) for x > 0: the FP32 estimate refined by Newton steps
 // y <- y (3 - x y^2) / 2 in type A (two in FP64, none in FP32)
 template <typename A>
@@ -553,39 +659,60 @@ __device__ void factor_solve(Ctx& c, bool fp64, double floor) {
   __syncthreads();
 }
 
-// Orthonormalize W's b columns and append them to Q by [project against Q,
-// Cholesky-QR] twice: the first pass's FP32 triangular solve can magnify
-// rounding along Q by the block's condition number, and only a projection
-// removes that again.
+// Orthonormalize W's b columns and append them to Q.  Plain steps: [project
+// against Q, Cholesky-QR] twice.  Precise steps (a batch tested at eps_rel
+// below kPreciseBelow): the first projection forms W - Q G in double-FP32
+// (w_minus_qg_df) and is followed by a second, FP32 projection before the
+// first factorization.  The FP32 difference W - Q G errs by about 1e-7 of W in
+// every direction, and the FP32 product Q^T W by about sqrt(q) 2^-24 of W
+// along Q; near eps_rel = 1e-6 both are as large as the residual the test
+// measures.  The double-FP32 difference removes the first and the second
+// projection the second, so the factored block (and the tested norm) is
+// (I - Q Q^T)^2 W formed to about 1e-13 of W.  The first pass's FP32
+// triangular solve can magnify rounding along Q by the block's condition
+// number, and the projection before the second Cholesky-QR removes that again.
 // dref: the block's sum of squares before it was projected against Q.  A
-// column whose residual is at or below the FP32 noise level of that block
-// (pivot <= DROP_FP32 dref) lies in span(Q) as far as the data can tell:
-// normalizing it would turn rounding errors, which point along Q, into a
-// basis column.  Such columns are dropped (zero columns of Q).
+// column whose pivot is at or below the drop level times dref, or at or below
+// 1e-26 of the largest pivot, is dropped (a zero column of Q, which leaves
+// Q Q^T unchanged).  Plain steps: DROP_FP32 = (3.2e-7)^2, the FP32 noise level
+// of the block (normalizing such a residual, rounding along Q, would cost Q
+// its orthogonality).  Precise steps: DROP_PRECISE, a residual of 1e-10 of
+// the block, a column that is zero in the data (an SJLT column without
+// entries) or rounding.
 // The second pass's input columns have unit norm (or are zero) before the
 // projection between the passes.  A column that this projection shrinks below
 // 0.1 of its length (pivot <= DROP_PASS2) was mostly rounding along Q that the
 // first pass normalized: renormalizing what is left would make a basis column
-// that is not orthogonal to Q, so it is dropped as well.  What it can hold of
-// S~ itself is below the FP32 resolution of the test (about 1e-7 of S~'s
-// column, with one projection in front of the first pass).
-constexpr double DROP_FP32 = 1e-13;  // (3.2e-7)^2: the residual relative to the block, FP32 data
+// that is not orthogonal to Q, so it is dropped as well.
+constexpr double DROP_FP32 = 1e-13;
+constexpr double DROP_PRECISE = 1e-20;
 constexpr double DROP_PASS2 = 1e-2;
 
-// W arrives as it is: [project, Cholesky-QR (with the drop rule)], then the
-// second projection and its Gram matrix; absorb_end finishes the pass.
-__device__ void absorb_begin(Ctx& c, int q, double dref) {
+// W arrives as it is: its projection(s), the first Gram matrix, Cholesky-QR
+// (with the drop rule), then the projection between the passes and its Gram
+// matrix; absorb_end finishes the pass.  Returns the trace of the first Gram
+// matrix (the same value in every CTA of the cluster): with the precise steps
+// ||(I - Q Q^T)^2 W||_F^2.
+__device__ double absorb_begin(Ctx& c, int q, double dref, bool precise) {
+  if (q > 0) {
+    qt_w(c, q);
+    if (precise) {
+      w_minus_qg_df(c, q);
+      qt_w(c, q);
+    }
+    w_minus_qg(c, q);
+  }
+  gram_pass(c);
+  double tr = 0.0;
+#pragma unroll 8
+  for (int i = 0; i < BW; ++i) tr += c.gram[i * LD + i];
+  factor_solve(c, true, (precise ? DROP_PRECISE : DROP_FP32) * dref);
   if (q > 0) {
     qt_w(c, q);
     w_minus_qg(c, q);
   }
   gram_pass(c);
-  factor_solve(c, true, DROP_FP32 * dref);
-  if (q > 0) {
-    qt_w(c, q);
-    w_minus_qg(c, q);
-  }
-  gram_pass(c);
+  return tr > 0.0 ? tr : 0.0;
 }
 
 // tr(L1 G2 L1^T), L1 the first pass's factor (c.Lf) and G2 the second Gram
@@ -625,7 +752,7 @@ __device__ void absorb_end(Ctx& c, int& q, int b) {
 // CTA alone, whose cluster barriers are CTA barriers).
 __global__ void __launch_bounds__(AT, 1)
     batch_test_kernel(BItem* __restrict__ items, ATest* __restrict__ tests, const int* __restrict__ order, int ncl,
-                      double eps_rel, double eps_abs) {
+                      double eps_rel, double eps_abs, bool precise) {
   extern __shared__ __align__(16) uint8_t smem[];
   Ctx c;
   c.ncl = ncl;
@@ -658,14 +785,14 @@ __global__ void __launch_bounds__(AT, 1)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
     const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
-    absorb_begin(c, q, dref);
+    absorb_begin(c, q, dref, precise);
     absorb_end(c, q, b);
     covered += b;
   }
   // the test, Eq. (3.1): its two projections are those of the absorption
   const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
-  absorb_begin(c, q, nt2);
-  const double nh2 = lgl_trace(c);
+  const double tr1 = absorb_begin(c, q, nt2, precise);
+  const double nh2 = precise ? tr1 : lgl_trace(c);
   const double sc = T->srht ? sqrt((double)T->first_w / (double)c_end)
                             : 1.0 / sqrt((double)(1 + (c_end - T->first_w) / dd));
   const double nh = sqrt(nh2) * sc, nt = sqrt(nt2) * sc;
@@ -770,7 +897,8 @@ int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel, items, tests, order, ncl, eps_rel, eps_abs));
+  const bool precise = eps_rel < kPreciseBelow;
+  JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel, items, tests, order, ncl, eps_rel, eps_abs, precise));
   note_launch();
   return SK_OK;
 }

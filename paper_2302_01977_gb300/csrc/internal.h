@@ -99,7 +99,15 @@ struct Basis {                // orthonormal basis Q of earlier sketch columns
   int64_t rows = 0;
   int cols = 0;               // columns of Q so far
   int covered = 0;            // sketch columns already absorbed into Q
+  bool precise = false;       // absorbed by the precise steps (FP32 data, eps_rel below kPreciseBelow)
 };
+
+// Stopping tests of FP32 data with eps_rel below this take the precise
+// absorption (first projection's difference in double-FP32, a second
+// projection before the first Cholesky-QR pass): the plain FP32 steps resolve
+// ||S^|| / ||S~|| to about 1e-6, which decides a test to 1 % only from about
+// 1e-5 up.
+constexpr double kPreciseBelow = 1e-4;
 
 }  // namespace jls
 
@@ -221,7 +229,7 @@ int norm_test(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int 
               int c_end, double eps_rel, double eps_abs, int* stop, double* nh, double* nt,
               cudaStream_t s);
 // the same test in two parts: everything enqueued on s (no host wait), then the wait and the decision
-int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, int c_split,
+int norm_test_enqueue(sk_op* h, int slot, const void* S, int64_t rows, int64_t ldS, int dtype, double eps_rel, int c_split,
                       int c_end, cudaStream_t s);
 int norm_test_finish(sk_op* h, int slot, double eps_rel, double eps_abs, int* stop, double* nh, double* nt);
 

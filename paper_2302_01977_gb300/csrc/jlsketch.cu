@@ -369,8 +369,8 @@ int adaptive_norm_test_pair(sk_handle h, const void* S, int64_t rows_S, int64_t 
   // the S' test on the handle's second stream, after the work already on `stream`
   JLS_CHECK_CUDA(cudaEventRecord(h->aux_fork, s));
   JLS_CHECK_CUDA(cudaStreamWaitEvent(h->aux_stream, h->aux_fork, 0));
-  JLS_CHECK(norm_test_enqueue(h, 1, St, rows_St, ldSt, dtype, c_split, c_end, h->aux_stream));
-  JLS_CHECK(norm_test_enqueue(h, 0, S, rows_S, ldS, dtype, c_split, c_end, s));
+  JLS_CHECK(norm_test_enqueue(h, 1, St, rows_St, ldSt, dtype, eps_rel, c_split, c_end, h->aux_stream));
+  JLS_CHECK(norm_test_enqueue(h, 0, S, rows_S, ldS, dtype, eps_rel, c_split, c_end, s));
   // later work on `stream` waits for all of the S' test (its extension of Q included)
   JLS_CHECK_CUDA(cudaEventRecord(h->aux_join, h->aux_stream));
   JLS_CHECK_CUDA(cudaStreamWaitEvent(s, h->aux_join, 0));

@@ -12,7 +12,7 @@ import pytest
 
 from oracle import adaptive as oad
 from paper_2302_01977_gb300 import inputs
-from tests.util import dev_padded, ensure_built
+from tests.util import dev_padded, ensure_built, same_s_check
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +125,40 @@ def test_pair_equals_two_single_tests(dtype):
             jl.sketch_destroy(h)
     assert len(outs[0]) == len(outs[1]) == 5
     assert outs[0] == outs[1]
+
+
+@pytest.mark.parametrize("kind,alpha", [("sjlt_block", 4), ("gauss", 1)])
+def test_tight_tolerance_decisions_on_the_device_sketch(kind, alpha):
+    """eps_rel = 1e-6 on an FP32 kernel matrix (X != Y): every test of S and of
+    S' against the FP64 test on the sketch as the device held it at that test
+    (a copy taken after each test), decisions outside a 1 % band around
+    eps_rel, ratios within 1 % plus the device arithmetic's resolution."""
+    from paper_2302_01977_gb300 import jlsketch as jl
+    n, d0, dd, d_max, eps = 2048, 64, 32, 448, 1e-6
+    X = torch.from_numpy(inputs.points(n, seed=31)).cuda()
+    Y = torch.from_numpy(inputs.points(n, seed=32)).cuda()
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    jl.kernel_matrix(jl.generator(X, Y, 0.3), A)
+    h = jl.sketch_create(kind, n, d0 + dd, alpha, 41, d_max)
+    snaps, stopped = [], False
+    try:
+        S = torch.zeros((n, d_max), device="cuda")
+        St = torch.zeros((n, d_max), device="cuda")
+        jl.sketch_apply(h, A, jl.SK_BOTH, jl.SK_PREC_NATIVE, S=S, St=St)
+        w = d0 + dd
+        while True:
+            rs, rt = jl.adaptive_norm_test_pair(h, S[:, :w], St[:, :w], dd, eps, 0.0)
+            snaps.append((w, S[:, :w].double().cpu().numpy(), St[:, :w].double().cpu().numpy(), rs, rt))
+            if (rs[0] and rt[0]) or w + dd > d_max:
+                stopped = rs[0] and rt[0]
+                break
+            jl.sketch_increment(h, dd)
+            jl.sketch_apply_increment(h, A, jl.SK_BOTH, jl.SK_PREC_NATIVE, S=S, St=St)
+            w += dd
+        jl.sketch_device_status(h)
+    finally:
+        jl.sketch_destroy(h)
+    assert stopped  # this kernel converges within d_max
+    for w, Sn, Stn, rs, rt in snaps:
+        same_s_check(Sn, [(w - dd, rs[0], rs[1], rs[2])], dd, eps, what=("S", w))
+        same_s_check(Stn, [(w - dd, rt[0], rt[1], rt[2])], dd, eps, what=("St", w))

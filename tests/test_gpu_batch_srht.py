@@ -295,6 +295,29 @@ def test_srht_batch_adaptive_matches_oracle(eps_rel):
         x["op"].close()
 
 
+def test_srht_batch_adaptive_tight_tolerance_same_sketch():
+    """eps_rel = 1e-6: each decision against the FP64 test on the device's own
+    sketch (outside a 1 % band around eps_rel), the last test's ratio within
+    1 % plus the device arithmetic's resolution."""
+    from tests.util import batch_same_s
+    dd, eps_rel = 32, 1e-6
+    specs = [(256, 64, 4, 0.5, 1.0), (448, 32, 7, 0.2, 1.0), (1000, 64, 6, 0.3, 1.0), (2048, 128, 5, 0.25, 1.0),
+             (1088, 96, 6, 0.35, 1.0), (512, 96, 2, 0.03, 1.0)]
+    inst = make_adaptive(specs, dd, seed=67)
+    items = [(x["op"].h, x["A"], x["S"], 0, x["d0"] + dd) for x in inst]
+    with jl.SrhtBatch(items) as B:
+        B.adaptive_setup([x["d0"] for x in inst], dd, eps_rel, 0.0)
+        B.adaptive_run()
+        res = B.adaptive_result()
+    for i, x in enumerate(inst):
+        d = int(res["d"][i])
+        batch_same_s(x["S"][:, :d].double().cpu().numpy(), x["d0"], dd, d, int(res["state"][i]), res["nh"][i],
+                     res["nt"][i], eps_rel, srht=True, what=i)
+    assert 1 in set(res["state"])
+    for x in inst:
+        x["op"].close()
+
+
 def test_srht_batch_adaptive_argument_checks():
     dd = 32
     inst = make_adaptive([(300, 64, 2, 0.2, 1.0)], dd, seed=3)

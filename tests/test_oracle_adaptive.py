@@ -5,6 +5,9 @@
 * A matrix with a prescribed geometric singular spectrum reaches a larger d for
   a smaller eps_rel (the test is monotone in its tolerance).
 * The two-pass projection leaves a block orthogonal to Q.
+* With a rank-deficient S(:, 1:d) (a zero column, a repeated column) the test
+  projects onto the orthogonal complement of the range of S(:, 1:d) (Sec. 3),
+  with a closed-form ||S^||.
 * A full-rank matrix with a flat spectrum never passes a tight test and stops
   at d_max without converging.
 """
@@ -67,3 +70,20 @@ def test_absolute_tolerance_stops():
     res = ad.adaptive(A, "sjlt_block", d0=16, dd=8, alpha=4, seed=1, d_max=64,
                       eps_rel=1e-12, eps_abs=1e-6)
     assert res["converged"] and len(res["history"]) == 1
+
+
+def test_rank_deficient_sketch_projects_on_its_range():
+    """S(:, 1:6) = [u1, u2, 0, u3, 2 u1, u4] has rank 4; the tested block
+    [v1 + u2, 3 v2] with v1, v2 orthogonal to span(u) has ||S^|| = sqrt(10)
+    and ||S~|| = sqrt(11) exactly.  A 6-column QR factor of S(:, 1:6) would
+    span two directions outside its range and could take parts of v1, v2."""
+    n = 50
+    B, _ = np.linalg.qr(inputs.dense_matrix(n, 6, seed=10))
+    u, v = B[:, :4], B[:, 4:]
+    S = np.column_stack([u[:, 0], u[:, 1], np.zeros(n), u[:, 2], 2 * u[:, 0], u[:, 3],
+                         v[:, 0] + u[:, 1], 3 * v[:, 1]])
+    assert ad.range_basis(S[:, :6]).shape[1] == 4
+    stop, nh, nt = ad.norm_test(S, 6, 2, 0.5, 0.0)
+    assert abs(nh - np.sqrt(10.0)) < 1e-13 and abs(nt - np.sqrt(11.0)) < 1e-13
+    assert not stop  # sqrt(10 / 11) > 0.5
+    assert ad.range_basis(np.zeros((n, 3))).shape[1] == 0
