@@ -15,6 +15,15 @@ kernel-matrix workload (A_ij = exp(-||x_i - y_j||^2 / (2 * 0.1^2)), X != Y,
 value = bytes of A streamed by all sketch products of the step / step time.
 A is larger than L2 (126 MB), so no flush is needed between steps.
 
+The same line carries, measured in the same run on rank 0 at N = 1 (skip with
+--no-extra), the precision comparison (key "precision": the Gaussian S = A R
+of the 65536 x 65536 FP32 kernel matrix at d = 512 on FP32 CUDA cores, as a
+bf16 hi+lo split and in scaled FP8 on the tensor cores, each error on 4096
+sampled rows) and the differentiation workload (key "differentiation": the
+matrix-free S = K(X, X; h) R of 262144 points and its adjoint, against the
+explicit-K path, with their ALU rooflines and the FP64 oracle gradient timed
+on a 4096-point problem as their CPU baseline).
+
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores.  Under torchrun every rank runs an independent
 replica (the path is not sharded); rank 0 prints one JSON line.
@@ -426,6 +435,14 @@ def run_ours(args):
         line["cpu_baseline"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in cb.items()}
         for name in errs:
             line["per_operator"][name]["rel_err_vs_oracle"] = float(f"{errs[name]:.3e}")
+    # ---- the precision and differentiation workloads, measured in the same run (rank 0, N = 1)
+    if rank == 0 and world == 1 and args.only == "all" and not args.no_extra:
+        del step, A
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["precision"] = precision_measure(args)
+        torch.cuda.empty_cache()
+        line["differentiation"] = differentiation_measure(args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -467,7 +484,7 @@ def run_reference(args):
 PRECISION = dict(name="precision_fp32_n65536", n=65536, d=512, h=0.05, seed=20230203 + 2, sample_rows=4096)
 
 
-def run_precision(args):
+def precision_measure(args, sample_rows=None):
     """The Gaussian sketch S = A R of the 65536 x 65536 FP32 kernel matrix
     (h = 0.05, A = 17.2 GB) at d = 512 in each arithmetic: FP32 CUDA cores,
     the bf16 split and scaled FP8 on the tensor cores.  Each result's error is
@@ -480,22 +497,22 @@ def run_precision(args):
     from paper_2302_01977_gb300 import inputs
     from paper_2302_01977_gb300 import jlsketch as jl
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
     w = PRECISION
     n, d = w["n"], w["d"]
+    sample_rows = sample_rows or w["sample_rows"]
     torch.cuda.set_device(0)
     X = torch.from_numpy(inputs.points(n, seed=w["seed"])).cuda()
     A = torch.empty((n, n), dtype=torch.float32, device="cuda")
     jl.kernel_matrix(jl.generator(X, X, w["h"], 0.0), A)
     h = jl.sketch_create("gauss", n, d, 1, w["seed"], d)
     rng = np.random.default_rng(w["seed"])
-    rows = np.sort(rng.choice(n, w["sample_rows"], replace=False))
+    rows = np.sort(rng.choice(n, sample_rows, replace=False))
     rows_t = torch.from_numpy(rows).cuda()
     hbm, bf16, _, peak_kind = peaks()
     results = {}
     clocks = Clocks(0)
     clocks.start()
+    l0 = jl.sketch_launch_count()
     try:
         for name, prec in (("fp32", jl.SK_PREC_NATIVE), ("bf16x2", jl.SK_PREC_BF16X2), ("fp8", jl.SK_PREC_FP8)):
             S = torch.empty((n, d), dtype=torch.float32, device="cuda")
@@ -517,7 +534,10 @@ def run_precision(args):
             del S
     finally:
         ck = clocks.stop()
+    launches = jl.sketch_launch_count() - l0
     A_rows = A.index_select(0, rows_t).cpu().numpy().astype(np.float64)
+    del A
+    torch.cuda.empty_cache()
     Rd = jl.sketch_export(h, dense=True)["R"]
     jl.sketch_destroy(h)
     t0 = time.perf_counter()
@@ -529,38 +549,59 @@ def run_precision(args):
     tol = {"fp32": 1e-5, "bf16x2": 1e-5, "fp8": 2e-2}
     for name, r in results.items():
         r["tolerance"] = tol[name]
+        r["within_tolerance"] = r["rel_err_vs_fp64"] <= tol[name]
         r["pct_of_bf16_peak"] = round(100 * r["useful_tflops"] / bf16, 1)
-    best = results["bf16x2"]
+    return {"config": {"workload": w["name"], "n": n, "d": d, "h": w["h"], "operator": "gaussian", "which": "S",
+                       "error_sample_rows": int(sample_rows), "l2": "inputs larger than L2 (A = 17.2 GB)"},
+            "per_precision": results,
+            "bf16x2_speedup_vs_fp32": round(results["fp32"]["ms"] / results["bf16x2"]["ms"], 2),
+            "peak_bf16_tflops": bf16, "peak_source": peak_kind,
+            "fp64_seconds_on_sample": round(t_ref, 1), "gpu_launches": int(launches), "clocks": ck}
+
+
+def run_precision(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    m = precision_measure(args)
+    best = m["per_precision"]["bf16x2"]
     line = {"metric": METRIC, "value": best["gbs_of_A"], "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 data; bf16 split", "data": "synthetic", "impl": "ours",
-            "config": {"workload": w["name"], "n": n, "d": d, "h": w["h"], "operator": "gaussian", "which": "S",
-                       "error_sample_rows": w["sample_rows"], "l2": "inputs larger than L2 (A = 17.2 GB)"},
-            "per_precision": results, "peak_bf16_tflops": bf16, "peak_source": peak_kind,
-            "fp64_seconds_on_sample": round(t_ref, 1), "clocks": ck}
+            "vs_baseline": None, "dtype": "f32 data; bf16 split", "data": "synthetic", "impl": "ours"}
+    line.update(m)
     print(json.dumps(line))
 
 
 DIFF = dict(name="kernel_sketch_grad_n262144", n=262144, d=256, alpha=4, h=0.05, seed=20230203 + 4)
 
 
-def run_differentiation(args):
+# ALU work per kernel pair (i, j) as the kernels issue it: the forward computes
+# K_ij in 7 FP32 operations (3 differences, 2 FMAs and a product for r^2, the
+# scale) and one MUFU ex2, and the sketch sum adds alpha = 4 FMAs; the adjoint
+# spends 17 FP32 operations on the pair's K_ij, weight and five running sums,
+# 4 on G_ij = sum_k s dS[i, c_k], and one ex2.  Peaks are derived from the unit
+# counts (128 FP32 lanes and 16 MUFU lanes per SM per clock), the SM count and
+# the SM clock sampled during the run.
+ALU_OPS = {"forward": (11, 1), "adjoint": (21, 1)}
+
+
+def differentiation_measure(args, n=None, subset=4096):
     """Matrix-free S = K(X, X; h) R (K never formed) and its adjoint (dX, dh)
     for 262144 points uniform in [0,1]^3, h = 0.05, block SJLT d = 256,
     alpha = 4, upstream dS ~ N(0, 1); against the explicit-K plain path (the
     generator mode of sketch_apply: K written block by block, 20480 rows at a
-    time, then the SJLT S = A R product of each block)."""
+    time, then the SJLT S = A R product of each block).  On a `subset`-point
+    problem of the same kind, the forward and the gradient are also checked
+    against the FP64 oracle (oracle.kernel_grad)."""
+    import numpy as np
     import torch
 
     from paper_2302_01977_gb300 import inputs
     from paper_2302_01977_gb300 import jlsketch as jl
 
-    if int(os.environ.get("RANK", "0")) != 0:
-        return
     w = dict(DIFF)
-    if args.points:
-        w["n"] = args.points
-        w["name"] = f"kernel_sketch_grad_n{args.points}"
+    if n:
+        w["n"] = n
+        w["name"] = f"kernel_sketch_grad_n{n}"
     n, d = w["n"], w["d"]
     torch.cuda.set_device(0)
     X = torch.from_numpy(inputs.points(n, seed=w["seed"]).astype("float32")).cuda()
@@ -594,19 +635,72 @@ def run_differentiation(args):
     ck = clocks.stop()
     jl.sketch_device_status(op.h)
     fwd_err = float((torch.linalg.norm(S - S2) / torch.linalg.norm(S2)).item())
+    op.close()
+    del S, S2, dS, dX
     pairs = float(n) * n
-    line = {"metric": METRIC, "value": round(pairs / (t_fwd + t_adj) / 1e6, 1), "unit": "G kernel pairs/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_fwd + t_adj, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "impl": "ours",
-            "config": {"workload": w["name"], "n": n, "d": d, "alpha": w["alpha"], "h": w["h"],
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = ck.get("sm_mhz") or 2070.0
+    fp32_rate, xu_rate = sms * 128 * mhz * 1e6, sms * 16 * mhz * 1e6
+    alu = {}
+    for name, t in (("forward", t_fwd), ("adjoint", t_adj)):
+        fo, xo = ALU_OPS[name]
+        floor_ms = 1e3 * max(fo * pairs / fp32_rate, xo * pairs / xu_rate)
+        alu[name] = {"fp32_ops_per_pair": fo, "ex2_per_pair": xo, "floor_ms": round(floor_ms, 2),
+                     "frac": round(floor_ms / t, 3)}
+    # CPU baseline leg: the FP64 oracle (oracle.kernel_grad) timed on a subset-point problem of the
+    # same kind, and the GPU forward and gradient of that problem checked against it
+    cb = None
+    if not args.no_cpu_baseline:
+        from oracle import kernel_grad as okg
+        Xs = inputs.points(subset, seed=w["seed"] + 11).astype(np.float32)
+        Xt = torch.from_numpy(Xs).cuda()
+        ops_ = jl.Sketch("sjlt_block", subset, d, w["alpha"], w["seed"] + 13)
+        Ss = torch.empty((subset, d), device="cuda")
+        dSs = torch.randn((subset, d), device="cuda", generator=torch.Generator("cuda").manual_seed(6))
+        dXs = torch.empty_like(Xt)
+        dhs = torch.empty(1, dtype=torch.float64, device="cuda")
+        jl.sketch_kernel_apply(ops_.h, Xt, Xt, w["h"], Ss)
+        jl.sketch_kernel_adjoint(ops_.h, Xt, w["h"], dSs, dXs, dhs)
+        torch.cuda.synchronize()
+        R = jl.sketch_export(ops_.h, dense=True)["R"]
+        ops_.close()
+        X64 = Xs.astype(np.float64)
+        dS64 = dSs.double().cpu().numpy()
+        t0 = time.perf_counter()
+        S0 = okg.kernel_sketch(X64, w["h"], R)
+        gX, gh = okg.kernel_sketch_grad(X64, w["h"], R, dS64)
+        dt = time.perf_counter() - t0
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        cb = {"value": round(float(subset) * subset / dt / 1e9, 4), "unit": "G kernel pairs/s (forward + adjoint)",
+              "cores": cores, "kind": "oracle",
+              "sample": f"{subset}-point problem of the same kind (forward S and gradient dX, dh in FP64), {dt:.1f} s",
+              "gpu_rel_err": {
+                  "forward": float(f"{np.linalg.norm(Ss.double().cpu().numpy() - S0) / np.linalg.norm(S0):.3e}"),
+                  "dX": float(f"{np.linalg.norm(dXs.double().cpu().numpy() - gX) / np.linalg.norm(gX):.3e}"),
+                  "dh": float(f"{abs(float(dhs.item()) - gh) / abs(gh):.3e}"),
+                  "tolerances": {"forward": 1e-5, "gradient": 1e-4}}}
+    return {"config": {"workload": w["name"], "n": n, "d": d, "alpha": w["alpha"], "h": w["h"],
                        "upstream": "dS ~ N(0,1)", "l2": "A never formed; X (3 MB) and dS (268 MB)"},
             "forward_ms": round(t_fwd, 3), "adjoint_ms": round(t_adj, 3),
             "explicit_k_forward_ms": round(t_exp, 3), "forward_speedup_vs_explicit": round(t_exp / t_fwd, 2),
             "forward_rel_diff_vs_explicit": float(f"{fwd_err:.3e}"),
-            "forward_gpairs_per_s": round(pairs / t_fwd / 1e6, 1), "adjoint_gpairs_per_s": round(pairs / t_adj / 1e6, 1),
-            "gpu_launches": int(launches), "clocks": ck}
-    op.close()
+            "forward_gpairs_per_s": round(pairs / t_fwd / 1e6, 1),
+            "adjoint_gpairs_per_s": round(pairs / t_adj / 1e6, 1),
+            "roofline": {"bound": "alu", "unit": "ms", "peak_source": f"derived: {sms} SMs x (128 FP32, 16 MUFU) "
+                                                                      f"lanes x {mhz:.0f} MHz sampled", **alu},
+            "cpu_baseline": cb, "gpu_launches": int(launches), "clocks": ck}
+
+
+def run_differentiation(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    m = differentiation_measure(args, n=args.points or None)
+    line = {"metric": METRIC, "value": round(m["forward_gpairs_per_s"] * m["adjoint_gpairs_per_s"]
+                                             / (m["forward_gpairs_per_s"] + m["adjoint_gpairs_per_s"]), 1),
+            "unit": "G kernel pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(m["forward_ms"] + m["adjoint_ms"], 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours"}
+    line.update(m)
     print(json.dumps(line))
 
 
@@ -1092,6 +1186,8 @@ def main():
     ap.add_argument("--prec", choices=["auto", "fp32", "bf16x2"], default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the precision (n = 65536) and differentiation (n = 262144) sections of the default run")
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
