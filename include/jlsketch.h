@@ -56,7 +56,8 @@ extern "C" {
 /* ---- operator kinds (Sec. 2.4) ------------------------------------------ */
 #define SK_SJLT_GRAPH 1  /* alpha distinct positions uniform in each row's block  */
 #define SK_SJLT_BLOCK 2  /* one position in each of alpha chunks of width/alpha    */
-#define SK_SRHT       3  /* R = D H P, nu = 2^ceil(log2 n), columns w/o replacement */
+#define SK_SRHT       3  /* R = D H P, nu = 2^ceil(log2 n), columns w/o replacement
+                            unless SK_SRHT_REPLACE */
 #define SK_GAUSS      4  /* i.i.d. N(0, 1/d)                                      */
 
 /* ---- element types ------------------------------------------------------ */
@@ -79,6 +80,17 @@ extern "C" {
                              relative error of order 1e-3 (tolerance 2e-2)         */
 
 /* ---- which sketch ------------------------------------------------------- */
+/* Creation flags (sketch_create_flags), combined by bitwise or. */
+#define SK_SCALE_BLOCK  1u  /* every block of R keeps the scale of a JL operator of its own width
+                               (Algorithm 1 appends an independent JL(Delta-d)): SJLT 1/sqrt(alpha),
+                               SRHT 1/sqrt(w_b), Gaussian variance 1/w_b for a block of width w_b;
+                               increments leave earlier columns unscaled.  Default: the grown R is
+                               renormalized to one JL operator of width d_total (Sec. 6.2). */
+#define SK_SRHT_REPLACE 2u  /* SRHT columns sampled with replacement ("independently and
+                               uniformly", Sec. 2.4.2): the sampled index mu_j is the j-th accepted
+                               draw, repeats kept, and d_max may exceed nu.  Default: without
+                               replacement, the first d distinct draws.  SRHT operators only. */
+
 #define SK_S    1  /* S  = A R   */
 #define SK_ST   2  /* S' = A^T R */
 #define SK_BOTH 3
@@ -115,12 +127,26 @@ int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t al
                   uint64_t seed, int32_t d_max, void* stream);
 
 /*
+ * sketch_create_flags -- sketch_create with creation flags (the scale mode and
+ * the SRHT sampling; the paper's readings in the flag definitions above).
+ *   flags  0, or SK_SCALE_BLOCK and/or SK_SRHT_REPLACE; sketch_create is
+ *          flags == 0.  With SK_SRHT_REPLACE, d_max <= 8192 only.
+ * Errors: INVALID_ARG (unknown flag bits; SK_SRHT_REPLACE on a non-SRHT
+ * kind; as sketch_create otherwise), NOMEM, DEVICE.
+ */
+int sketch_create_flags(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t alpha,
+                        uint64_t seed, int32_t d_max, uint32_t flags, void* stream);
+
+/*
  * sketch_increment -- append Delta-d columns to R (Algorithm 1, R <- [R R_bar]).
  *   SJLT: a new block of alpha nonzeros per row in the new columns; the scale
  *   becomes 1/sqrt(alpha * blocks) ("adjusting the scaling factor", Sec. 6.2).
- *   SRHT: the next delta_d distinct sampled columns of the same D H.
+ *   SRHT: the next delta_d distinct sampled columns of the same D H (with
+ *   SK_SRHT_REPLACE: the next delta_d draws).
  *   Gaussian: delta_d new N(0,1) columns; all columns scale as 1/sqrt(d_total).
- *   Block SJLT needs alpha | delta_d; SRHT needs d_total <= nu.
+ *   With SK_SCALE_BLOCK no column is rescaled: the new block takes its own
+ *   scale (see the flag).
+ *   Block SJLT needs alpha | delta_d; SRHT without replacement needs d_total <= nu.
  * Errors: INVALID_ARG, D_MAX, NOMEM, DEVICE.
  */
 int sketch_increment(sk_handle h, int32_t delta_d, void* stream);

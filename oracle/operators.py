@@ -35,9 +35,16 @@ Readings where the paper is silent:
   u1 = (w0 >> 11 + 1) 2^-53 in (0, 1], u2 = (w1 >> 11) 2^-53 in [0, 1),
   z = sqrt(-2 ln u1) * cos(2 pi u2) for even c and * sin(2 pi u2) for odd c
   (Box-Muller), R_ic = z_ic / sqrt(d_total).
-* Scale after increments: the grown R is rescaled to be one JL operator of the
-  new width: SJLT values +-1/sqrt(alpha * blocks), SRHT 1/sqrt(d_total),
-  Gaussian variance 1/d_total.
+* Scale after increments (scale="renorm", the default): the grown R is
+  rescaled to be one JL operator of the new width: SJLT values
+  +-1/sqrt(alpha * blocks), SRHT 1/sqrt(d_total), Gaussian variance 1/d_total.
+  scale="block": each block keeps the scale of a JL operator of its own width,
+  as Algorithm 1 appends an independent JL(Delta-d): SJLT +-1/sqrt(alpha) in
+  every block, SRHT 1/sqrt(w_b) and Gaussian variance 1/w_b for a block of
+  width w_b.
+* SRHT sampling with replacement (replace=True): mu_j is the j-th accepted
+  draw lemire(word0, nu) over the same counters, repeats kept ("independently
+  and uniformly", Sec. 2.4.2), so more than nu columns may be drawn.
 """
 from __future__ import annotations
 
@@ -115,9 +122,10 @@ def srht_diag(n: int, seed: int) -> np.ndarray:
     return rng.sign_of(w0)
 
 
-def srht_samples(nu: int, count: int, seed: int) -> np.ndarray:
-    """First ``count`` distinct draws of lemire(word0, nu) in order (int64)."""
-    if count > nu:
+def srht_samples(nu: int, count: int, seed: int, replace: bool = False) -> np.ndarray:
+    """First ``count`` distinct draws of lemire(word0, nu) in order (int64);
+    with ``replace`` the first ``count`` accepted draws, repeats kept."""
+    if count > nu and not replace:
         raise ValueError("cannot sample more distinct columns than nu")
     chosen: list[int] = []
     seen = set()
@@ -130,7 +138,7 @@ def srht_samples(nu: int, count: int, seed: int) -> np.ndarray:
         w0, _, _, _ = rng.philox4x64_10(ctr, 0, 0, 0, key0, key1)
         v, ok = rng.lemire(w0, nu)
         for val, good in zip(v.tolist(), ok.tolist()):
-            if good and val not in seen:
+            if good and (replace or val not in seen):
                 seen.add(val)
                 chosen.append(val)
                 if len(chosen) == count:
@@ -159,11 +167,18 @@ def gaussian_z(n: int, c_begin: int, c_end: int, seed: int) -> np.ndarray:
 class Operator:
     """A JL operator R (n x d_total) grown by increments, formed from definitions."""
 
-    def __init__(self, kind: str, n: int, d: int, alpha: int = 1, seed: int = 0):
+    def __init__(self, kind: str, n: int, d: int, alpha: int = 1, seed: int = 0, scale: str = "renorm",
+                 replace: bool = False):
         if kind not in KINDS:
             raise ValueError(kind)
         if n < 1 or d < 1:
             raise ValueError("n and d must be positive")
+        if scale not in ("renorm", "block"):
+            raise ValueError(scale)
+        if replace and kind != "srht":
+            raise ValueError("sampling with replacement is an SRHT option")
+        self.scale_mode = scale
+        self.replace = bool(replace)
         self.kind = kind
         self.n = int(n)
         self.alpha = int(alpha)
@@ -180,7 +195,7 @@ class Operator:
                 raise ValueError("SJLT needs 1 <= alpha <= block width")
             if self.kind == "sjlt_block" and w % self.alpha:
                 raise ValueError("block construction needs alpha | width")
-        if self.kind == "srht" and self.d_total + w > self.nu:
+        if self.kind == "srht" and not self.replace and self.d_total + w > self.nu:
             raise ValueError("SRHT cannot sample more than nu columns")
 
     @property
@@ -195,9 +210,18 @@ class Operator:
         self.blocks.append(int(dd))
 
     def scale(self) -> float:
+        """The scale of every column (renorm), or of the last block's columns (block)."""
         if self.kind.startswith("sjlt"):
-            return 1.0 / math.sqrt(self.alpha * len(self.blocks))
+            return 1.0 / math.sqrt(self.alpha * (1 if self.scale_mode == "block" else len(self.blocks)))
+        if self.scale_mode == "block":
+            return 1.0 / math.sqrt(self.blocks[-1])
         return 1.0 / math.sqrt(self.d_total)
+
+    def column_scales(self) -> np.ndarray:
+        """Scale of each of the d_total columns."""
+        if self.scale_mode == "renorm" or self.kind.startswith("sjlt"):
+            return np.full(self.d_total, self.scale())
+        return np.concatenate([np.full(w, 1.0 / math.sqrt(w)) for w in self.blocks])
 
     # -- random parts ------------------------------------------------------
     def sjlt_entries(self) -> tuple[np.ndarray, np.ndarray]:
@@ -216,7 +240,7 @@ class Operator:
         return srht_diag(self.n, self.seed)
 
     def srht_samples(self) -> np.ndarray:
-        return srht_samples(self.nu, self.d_total, self.seed)
+        return srht_samples(self.nu, self.d_total, self.seed, self.replace)
 
     def gaussian_z(self) -> np.ndarray:
         return gaussian_z(self.n, 0, self.d_total, self.seed)
@@ -230,14 +254,14 @@ class Operator:
             R = np.zeros((n, d), dtype=np.float64)
             rows = np.repeat(np.arange(n), cols.shape[1])
             R[rows, cols.ravel()] = signs.ravel().astype(np.float64)
-            return R * self.scale()
+            return R * self.column_scales()[None, :]
         if self.kind == "srht":
             D = self.srht_diag().astype(np.float64)
             mu = self.srht_samples()
             i = np.arange(n, dtype=np.int64)[:, None]
             H = np.where(popcount_parity(i & mu[None, :]) == 1, -1.0, 1.0)
-            return D[:, None] * H * self.scale()
-        return self.gaussian_z() * self.scale()
+            return D[:, None] * H * self.column_scales()[None, :]
+        return self.gaussian_z() * self.column_scales()[None, :]
 
 
 def crs_ccs(cols: np.ndarray, signs: np.ndarray, d: int):

@@ -116,6 +116,7 @@ struct sk_op {
   int64_t n = 0;
   int alpha = 1;
   int d_total = 0;
+  uint32_t flags = 0;          // SK_SCALE_BLOCK, SK_SRHT_REPLACE
   int d_max = 0;
   int64_t nu = 1;
   uint64_t seed = 0;
@@ -242,7 +243,8 @@ int num_sms();
 
 // --- jlsketch.cu helpers ---
 void note_launch();  // counts kernel launches (sketch_launch_count)
-double op_scale(const sk_op* h);  // SJLT 1/sqrt(alpha * blocks); SRHT, Gaussian 1/sqrt(d_total)
+double op_scale(const sk_op* h);  // SJLT 1/sqrt(alpha * blocks); SRHT, Gaussian 1/sqrt(d_total) (block scale: see jlsketch.cu)
+bool block_scaled(const sk_op* h);  // SK_SCALE_BLOCK on an SRHT or Gaussian operator: column scales differ by block
 int cuda_status(cudaError_t e);
 size_t elem_size(int dtype);
 

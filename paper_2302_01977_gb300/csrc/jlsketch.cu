@@ -25,10 +25,21 @@ int cuda_status(cudaError_t e) {
 
 size_t elem_size(int dtype) { return dtype == SK_F64 || dtype == SK_C64 ? 8 : 4; }
 
+// The scale of R's columns: SJLT +-1/sqrt(alpha * blocks), SRHT and Gaussian
+// 1/sqrt(d_total) (one JL operator of the grown width, Sec. 6.2).  With
+// SK_SCALE_BLOCK every block keeps its own JL scale: SJLT 1/sqrt(alpha) (the
+// same in every block), SRHT and Gaussian 1/sqrt(w_b) for a block of width w_b;
+// op_scale then returns the last block's scale, and block_scaled() says whether
+// the columns' scales differ by block.
 double op_scale(const sk_op* h) {
+  const bool block = (h->flags & SK_SCALE_BLOCK) != 0;
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
-    return 1.0 / std::sqrt((double)h->alpha * (double)h->blocks.size());
-  return 1.0 / std::sqrt((double)h->d_total);
+    return 1.0 / std::sqrt((double)h->alpha * (block ? 1.0 : (double)h->blocks.size()));
+  return 1.0 / std::sqrt((double)(block ? h->blocks.back() : h->d_total));
+}
+
+bool block_scaled(const sk_op* h) {
+  return (h->flags & SK_SCALE_BLOCK) && h->kind != SK_SJLT_BLOCK && h->kind != SK_SJLT_GRAPH;
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -135,9 +146,8 @@ static int srht_pick_fwht(sk_op* h, const sk_matrix* A, int prec, int c_lo, int 
   return SK_OK;
 }
 
-static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, void* S, int64_t ldS,
-                    void* St, int64_t ldSt, cudaStream_t s) {
-  const double scale = op_scale(h);
+static int dispatch_range(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, double scale,
+                          void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s) {
   if (h->kind == SK_SRHT && (which & SK_S) && A->dtype == SK_F32 &&
       (prec == SK_PREC_NATIVE || prec == SK_PREC_BF16X2) && fwht_segments(h->nu) && c_hi > c_lo) {
     bool fwht = false;
@@ -153,6 +163,21 @@ static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo,
   if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (prec == SK_PREC_FP8) return dense_apply_fp8(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   return dense_apply_simt(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+}
+
+// Columns [c_lo, c_hi) at their scales: one range, or (SK_SCALE_BLOCK with
+// SRHT or Gaussian operators) one range per block.
+static int dispatch(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, void* S, int64_t ldS,
+                    void* St, int64_t ldSt, cudaStream_t s) {
+  if (!block_scaled(h)) return dispatch_range(h, A, which, prec, c_lo, c_hi, op_scale(h), S, ldS, St, ldSt, s);
+  int b0 = 0;
+  for (const int w : h->blocks) {
+    const int lo = std::max(c_lo, b0), hi = std::min(c_hi, b0 + w);
+    if (lo < hi)
+      JLS_CHECK(dispatch_range(h, A, which, prec, lo, hi, 1.0 / std::sqrt((double)w), S, ldS, St, ldSt, s));
+    b0 += w;
+  }
+  return SK_OK;
 }
 
 static void free_handle(sk_op* h) {
@@ -198,16 +223,23 @@ const char* sketch_strerror(int status) {
 
 int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t alpha, uint64_t seed,
                   int32_t d_max, void* stream) {
+  return sketch_create_flags(out, kind, n, d, alpha, seed, d_max, 0u, stream);
+}
+
+int sketch_create_flags(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t alpha, uint64_t seed,
+                        int32_t d_max, uint32_t flags, void* stream) {
   if (!out) return SK_ERR_INVALID_ARG;
   *out = nullptr;
   if (kind < SK_SJLT_GRAPH || kind > SK_GAUSS) return SK_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(SK_SCALE_BLOCK | SK_SRHT_REPLACE)) return SK_ERR_INVALID_ARG;
+  if ((flags & SK_SRHT_REPLACE) && kind != SK_SRHT) return SK_ERR_INVALID_ARG;
   if (n < 1 || n >= (1ll << 31) || d < 1 || d_max < d || d_max > MAX_D) return SK_ERR_INVALID_ARG;
   const bool sjlt = kind == SK_SJLT_BLOCK || kind == SK_SJLT_GRAPH;
   if (sjlt && (alpha < 1 || alpha > d || alpha > SJLT_MAX_ALPHA)) return SK_ERR_INVALID_ARG;
   if (kind == SK_SJLT_BLOCK && d % alpha) return SK_ERR_INVALID_ARG;
   int64_t nu = 1;
   while (nu < n) nu <<= 1;
-  if (kind == SK_SRHT && d_max > nu) return SK_ERR_INVALID_ARG;
+  if (kind == SK_SRHT && !(flags & SK_SRHT_REPLACE) && d_max > nu) return SK_ERR_INVALID_ARG;
   JLS_CHECK(check_device());
   sk_op* h = new (std::nothrow) sk_op();
   if (!h) return SK_ERR_NOMEM;
@@ -218,6 +250,7 @@ int sketch_create(sk_handle* out, int32_t kind, int64_t n, int32_t d, int32_t al
   h->d_max = d_max;
   h->nu = nu;
   h->seed = seed;
+  h->flags = flags;
   h->blocks.push_back(d);
   cudaGetDevice(&h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -319,14 +352,17 @@ int sketch_apply_increment(sk_handle h, const sk_matrix* A, int32_t which, int32
   JLS_CHECK(check_apply(h, A, which, prec, S, ldS, St, ldSt));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int d_old = h->pending_old_d;
-  // scale of the operator before the last increment, and now
+  // scale of the operator before the last increment, and now (with
+  // SK_SCALE_BLOCK the earlier columns keep theirs: factor 1)
   double old_scale;
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
     old_scale = 1.0 / std::sqrt((double)h->alpha * (double)(h->blocks.size() - 1));
   else
     old_scale = 1.0 / std::sqrt((double)d_old);
-  const double factor = op_scale(h) / old_scale;
-  if (A->dtype == SK_C64) {  // complex columns are (re, im) pairs of FP32
+  const double factor = (h->flags & SK_SCALE_BLOCK) ? 1.0 : op_scale(h) / old_scale;
+  if (factor == 1.0) {
+    // nothing to rescale
+  } else if (A->dtype == SK_C64) {  // complex columns are (re, im) pairs of FP32
     if (which & SK_S) JLS_CHECK(scale_columns(S, SK_F32, A->rows, 2 * ldS, 0, 2 * d_old, factor, s));
     if (which & SK_ST) JLS_CHECK(scale_columns(St, SK_F32, A->cols, 2 * ldSt, 0, 2 * d_old, factor, s));
   } else {

@@ -323,11 +323,22 @@ __global__ void srht_diag_kernel(int64_t n, uint64_t seed, int8_t* __restrict__ 
 // One thread: continue the sequence of candidate columns from the saved
 // counter until d_new distinct columns exist.  Membership uses an
 // open-addressing table in shared memory (capacity `cap`, a power of two).
-__global__ void srht_mu_kernel(int64_t nu, uint64_t seed, int d_old, int d_new, int cap,
+__global__ void srht_mu_kernel(int64_t nu, uint64_t seed, int d_old, int d_new, int cap, bool replace,
                                int32_t* __restrict__ mu, unsigned long long* __restrict__ state,
                                int* err) {
   extern __shared__ int32_t table[];
   if (threadIdx.x != 0) return;
+  if (replace) {  // every accepted draw, repeats kept (sampling with replacement)
+    unsigned long long t = state[0];
+    for (int have = d_old; have < d_new;) {
+      const u64x4 w = philox4x64_10((uint64_t)t, 0, 0, 0, seed, TAG_SRHT_MU);
+      ++t;
+      uint64_t v;
+      if (lemire(w.x0, (uint64_t)nu, &v)) mu[have++] = (int32_t)v;
+    }
+    state[0] = t;
+    return;
+  }
   for (int q = 0; q < cap; ++q) table[q] = -1;
   auto insert = [&](int32_t v) -> bool {  // true if newly inserted
     uint32_t hsh = ((uint32_t)v * 2654435761u) & (cap - 1);
@@ -369,13 +380,14 @@ int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s) {
                                                                                     h->srht_diag); note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
   }
+  const bool replace = (h->flags & SK_SRHT_REPLACE) != 0;
   int cap = 1;
-  while (cap < 2 * d_new) cap <<= 1;
+  while (!replace && cap < 2 * d_new) cap <<= 1;
   const size_t shm = sizeof(int32_t) * cap;
   if (shm > 48 * 1024)
     JLS_CHECK_CUDA(
         cudaFuncSetAttribute(srht_mu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  srht_mu_kernel<<<1, 32, shm, s>>>(h->nu, h->seed, d_old, d_new, cap, h->srht_mu, h->srht_state,
+  srht_mu_kernel<<<1, 32, shm, s>>>(h->nu, h->seed, d_old, d_new, cap, replace, h->srht_mu, h->srht_state,
                                     h->d_err); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -566,12 +578,11 @@ __global__ void dense_R_kernel(int kind, int64_t n, int d_total, int alpha, int 
   }
 }
 
-double op_scale(const sk_op* h);
-
 int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s) {
   const int threads = 128;
   const unsigned grid = (unsigned)((h->n + threads - 1) / threads);
-  const double sc = op_scale(h);
+  const bool per_block = block_scaled(h);  // written unscaled, then each block's columns at its scale
+  const double sc = per_block ? 1.0 : op_scale(h);
   if (dtype == SK_F64)
     dense_R_kernel<double><<<grid, threads, 0, s>>>(h->kind, h->n, h->d_total, h->alpha,
                                                     (int)h->blocks.size(), sc, h->sjlt_ents, h->srht_diag,
@@ -581,6 +592,13 @@ int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s) {
                                                    (int)h->blocks.size(), sc, h->sjlt_ents, h->srht_diag,
                                                    h->srht_mu, h->seed, (float*)R_dev); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
+  if (per_block) {
+    int b0 = 0;
+    for (const int w : h->blocks) {
+      JLS_CHECK(scale_columns(R_dev, dtype, h->n, h->d_total, b0, b0 + w, 1.0 / std::sqrt((double)w), s));
+      b0 += w;
+    }
+  }
   return SK_OK;
 }
 

@@ -43,10 +43,12 @@ SK_PREC_FP8 = 4
 SK_S = 1
 SK_ST = 2
 SK_BOTH = 3
+SK_SCALE_BLOCK = 1
+SK_SRHT_REPLACE = 2
 
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
-EXPORTS = ["sketch_create", "sketch_increment", "sketch_apply", "sketch_apply_increment",
+EXPORTS = ["sketch_create", "sketch_create_flags", "sketch_increment", "sketch_apply", "sketch_apply_increment",
            "adaptive_norm_test", "adaptive_norm_test_pair", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
            "sketch_kernel_adjoint", "sketch_batch_create", "sketch_batch_set", "sketch_batch_run",
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
@@ -104,6 +106,7 @@ def lib() -> ctypes.CDLL:
     P = ctypes.POINTER
     sig = {
         "sketch_create": (i32, [P(vp), i32, i64, i32, i32, u64, i32, vp]),
+        "sketch_create_flags": (i32, [P(vp), i32, i64, i32, i32, u64, i32, ctypes.c_uint32, vp]),
         "sketch_increment": (i32, [vp, i32, vp]),
         "sketch_apply": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
         "sketch_apply_increment": (i32, [vp, P(SkMatrix), i32, i32, vp, i64, vp, i64, vp]),
@@ -218,12 +221,18 @@ def generator(X, Y, h: float, shift: float = 0.0) -> SkMatrix:
 
 
 def sketch_create(kind, n: int, d: int, alpha: int = 1, seed: int = 0, d_max: int | None = None,
-                  stream=None) -> ctypes.c_void_p:
+                  stream=None, flags: int = 0) -> ctypes.c_void_p:
+    """flags: 0 (sketch_create), or SK_SCALE_BLOCK | SK_SRHT_REPLACE (sketch_create_flags)."""
     k = KIND_NAMES.get(kind, kind) if isinstance(kind, str) else int(kind)
     h = ctypes.c_void_p()
-    rc = lib().sketch_create(ctypes.byref(h), k, int(n), int(d), int(alpha), int(seed) & (2**64 - 1),
-                             int(d if d_max is None else d_max), _stream(stream))
-    _check(rc, "sketch_create")
+    dm = int(d if d_max is None else d_max)
+    if flags:
+        rc = lib().sketch_create_flags(ctypes.byref(h), k, int(n), int(d), int(alpha), int(seed) & (2**64 - 1), dm,
+                                       int(flags), _stream(stream))
+    else:
+        rc = lib().sketch_create(ctypes.byref(h), k, int(n), int(d), int(alpha), int(seed) & (2**64 - 1), dm,
+                                 _stream(stream))
+    _check(rc, "sketch_create_flags" if flags else "sketch_create")
     return h
 
 
@@ -591,8 +600,8 @@ def sketch_destroy(h) -> None:
 class Sketch:
     """Owning wrapper of a handle (closes it on exit / garbage collection)."""
 
-    def __init__(self, kind, n, d, alpha=1, seed=0, d_max=None, stream=None):
-        self.h = sketch_create(kind, n, d, alpha, seed, d_max, stream)
+    def __init__(self, kind, n, d, alpha=1, seed=0, d_max=None, stream=None, flags=0):
+        self.h = sketch_create(kind, n, d, alpha, seed, d_max, stream, flags)
 
     def close(self):
         if self.h:

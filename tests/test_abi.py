@@ -141,3 +141,13 @@ def test_noalloc_wrapper_refuses_mismatched_operands():
         jl.sketch_project_norms_noalloc(ok_q, St, ok_hat, 1e-2, 0.0)
     with pytest.raises(ValueError, match="CUDA"):
         jl.sketch_project_norms_noalloc(None, St, torch.zeros((64, 9)), 1e-2, 0.0)
+
+
+def test_create_flags_argument_checks(L):
+    """Flag checks come before any device use (no GPU needed)."""
+    h = ctypes.c_void_p()
+    assert L.sketch_create_flags(ctypes.byref(h), jl.SK_GAUSS, 64, 16, 1, 1, 16, jl.SK_SRHT_REPLACE,
+                                 None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_create_flags(ctypes.byref(h), jl.SK_SRHT, 64, 16, 1, 1, 16, 4, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_create_flags(ctypes.byref(h), jl.SK_SRHT, 64, 16, 1, 1, 80, 0, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_create_flags(None, jl.SK_SRHT, 64, 16, 1, 1, 16, 0, None) == jl.SK_ERR_INVALID_ARG

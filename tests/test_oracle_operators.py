@@ -350,3 +350,85 @@ def test_apply_complex_against_real_parts():
         for c in range(4):
             want = sum(np.conj(Z[i, j]) * R7[i, c] for i in range(7))
             assert abs(St[j, c] - want) <= 1e-13
+
+
+# --- creation flags: per-block scale (Algorithm 1's independent JL(Delta-d)) and
+# --- SRHT sampling with replacement (Sec. 2.4.2, "independently and uniformly")
+
+@pytest.mark.parametrize("kind,alpha", [("sjlt_block", 4), ("sjlt_graph", 4), ("srht", 1), ("gauss", 1)])
+def test_block_scale_each_block_is_its_own_jl_operator(kind, alpha):
+    n, d0, dd = 96, 24, 8
+    ren = ops.Operator(kind, n, d0, alpha, seed=21)
+    blk = ops.Operator(kind, n, d0, alpha, seed=21, scale="block")
+    for _ in range(2):
+        ren.increment(dd)
+        blk.increment(dd)
+    Rr, Rb = ren.dense(), blk.dense()
+    widths = [d0, dd, dd]
+    c0 = 0
+    for w in widths:
+        cols = slice(c0, c0 + w)
+        nz = Rb[:, cols][Rb[:, cols] != 0]
+        if kind.startswith("sjlt"):
+            assert np.allclose(np.abs(nz), 1.0 / math.sqrt(alpha), rtol=0, atol=1e-15)
+            assert np.count_nonzero(Rb[:, cols], axis=1).tolist() == [alpha] * n
+        elif kind == "srht":
+            assert np.allclose(np.abs(Rb[:, cols]), 1.0 / math.sqrt(w), rtol=0, atol=1e-15)
+        # the same random draws as the renormalized operator, another scale per block
+        ratio = math.sqrt(3) if kind.startswith("sjlt") else math.sqrt((d0 + 2 * dd) / w)
+        assert np.allclose(Rb[:, cols], Rr[:, cols] * ratio, rtol=1e-14, atol=0)
+        c0 += w
+
+
+def test_block_scale_gaussian_block_variance():
+    n, d0, dd = 4000, 64, 16
+    op = ops.Operator("gauss", n, d0, seed=5, scale="block")
+    op.increment(dd)
+    R = op.dense()
+    for cols, w in ((slice(0, d0), d0), (slice(d0, d0 + dd), dd)):
+        v = R[:, cols].var()
+        k = n * w
+        assert abs(v * w - 1.0) < 5 * math.sqrt(2.0 / k)  # variance 1/w_b within 5 sigma
+
+
+def test_srht_with_replacement_draws():
+    nu, count, seed = 64, 200, 8
+    rep = ops.srht_samples(nu, count, seed, replace=True)
+    assert rep.shape == (count,) and rep.min() >= 0 and rep.max() < nu  # more than nu columns allowed
+    # the sample without replacement is this sequence with its repeats removed, in order
+    first = list(dict.fromkeys(rep.tolist()))
+    k = min(len(first), nu)
+    assert ops.srht_samples(nu, k, seed).tolist() == first[:k]
+    # repeats at the rate of independent uniform draws: E[distinct] = nu (1 - (1 - 1/nu)^count)
+    distinct = []
+    for s in range(200):
+        distinct.append(len(set(ops.srht_samples(nu, 40, 1000 + s, replace=True).tolist())))
+    e = nu * (1 - (1 - 1 / nu) ** 40)
+    assert abs(np.mean(distinct) - e) < 5 * np.std(distinct) / math.sqrt(len(distinct))
+    # uniform over [0, nu): chi-square over many draws
+    big = ops.srht_samples(nu, 64 * 200, 77, replace=True)
+    cnt = np.bincount(big, minlength=nu)
+    chi2 = ((cnt - 200.0) ** 2 / 200.0).sum()
+    assert chi2 < nu - 1 + 5 * math.sqrt(2 * (nu - 1))
+    with pytest.raises(ValueError):
+        ops.srht_samples(nu, nu + 1, seed)
+
+
+def test_srht_with_replacement_operator():
+    n, d = 40, 80  # nu = 64 < d: only possible with replacement
+    op = ops.Operator("srht", n, d, seed=3, replace=True)
+    R = op.dense()
+    mu = op.srht_samples()
+    assert np.allclose(np.abs(R), 1.0 / math.sqrt(d), rtol=0, atol=1e-15)
+    # a repeated sample gives a repeated column (the element formula depends on mu_j only)
+    a, b = [(i, j) for i in range(d) for j in range(i + 1, d) if mu[i] == mu[j]][0]
+    assert np.array_equal(R[:, a], R[:, b])
+    # E ||x^T R||^2 = ||x||^2 over the random signs D (Definition 2.2), Monte Carlo, 5 sigma
+    x = inputs.dense_matrix(1, n, seed=4)[0]
+    vals = np.array([np.sum((x @ ops.Operator("srht", n, d, seed=s, replace=True).dense()) ** 2)
+                     for s in range(300)])
+    assert abs(vals.mean() - x @ x) < 5 * vals.std() / math.sqrt(vals.size)
+    with pytest.raises(ValueError):
+        ops.Operator("srht", n, d, seed=3)  # without replacement d <= nu
+    with pytest.raises(ValueError):
+        ops.Operator("gauss", n, 8, seed=3, replace=True)
