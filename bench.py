@@ -1118,7 +1118,9 @@ COMPLEX = dict(name="complex_helmholtz_fp32_n16384", n=16384, d=256, alpha=4, ka
 def run_complex(args):
     """S = A R and S' = A* R for a complex Helmholtz-type kernel A_ij =
     exp(i kappa r_ij) / (1 + kappa r_ij) of 16384 points uniform in [0,1]^3
-    (complex64, 2.1 GB), block SJLT d = 256, alpha = 4.  value = bytes of A / time."""
+    (complex64, 2.1 GB), block SJLT d = 256, alpha = 4 (and SRHT and Gaussian
+    operators, d = 256, in the bf16 split).  value = bytes of A / time of the
+    SJLT S'."""
     import torch
 
     from paper_2302_01977_gb300 import inputs
@@ -1158,11 +1160,23 @@ def run_complex(args):
     l0 = jl.sketch_launch_count()
     t_s = timed(lambda: jl.sketch_apply(op.h, A, jl.SK_S, S=S))
     t_st = timed(lambda: jl.sketch_apply(op.h, A, jl.SK_ST, St=St))
-    launches = jl.sketch_launch_count() - l0
-    ck = clocks.stop()
     jl.sketch_device_status(op.h)
     sym = float((torch.linalg.norm(St - S.conj()) / torch.linalg.norm(S)).item())  # A symmetric: A* R = conj(A R)
     op.close()
+    # SRHT and Gaussian operators on the same A: the bf16 split on tensor cores (S through R (x) I_2,
+    # S' through the transpose product and a conjugating interleave)
+    dense = {}
+    for kind in ("srht", "gauss"):
+        with jl.Sketch(kind, n, d, 1, w["seed"] + 1) as dop:
+            ts = timed(lambda: jl.sketch_apply(dop.h, A, jl.SK_S, jl.SK_PREC_BF16X2, S=S))
+            tst = timed(lambda: jl.sketch_apply(dop.h, A, jl.SK_ST, jl.SK_PREC_BF16X2, St=St))
+            jl.sketch_device_status(dop.h)
+        dsym = float((torch.linalg.norm(St - S.conj()) / torch.linalg.norm(S)).item())
+        dense[kind] = {"prec": "bf16x2", "S_ms": round(ts, 4), "St_ms": round(tst, 4),
+                       "S_gbs": round(bytes_a / ts / 1e6, 1), "St_gbs": round(bytes_a / tst / 1e6, 1),
+                       "symmetry_rel_diff": float(f"{dsym:.3e}")}
+    launches = jl.sketch_launch_count() - l0
+    ck = clocks.stop()
     line = {"metric": METRIC, "value": round(bytes_a / t_st / 1e6, 1), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_s + t_st, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 parts)",
@@ -1173,7 +1187,8 @@ def run_complex(args):
             "S_gbs": round(bytes_a / t_s / 1e6, 1), "St_gbs": round(bytes_a / t_st / 1e6, 1),
             "pct_hbm_S": round(100 * bytes_a / t_s / 1e6 / hbm, 1),
             "pct_hbm_St": round(100 * bytes_a / t_st / 1e6 / hbm, 1), "peak_source": peak_kind,
-            "symmetry_rel_diff": float(f"{sym:.3e}"), "gpu_launches": int(launches), "clocks": ck}
+            "symmetry_rel_diff": float(f"{sym:.3e}"), "srht": dense["srht"], "gauss": dense["gauss"],
+            "gpu_launches": int(launches), "clocks": ck}
     print(json.dumps(line))
 
 

@@ -19,7 +19,11 @@ constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4;
 constexpr int CHUNK_K = 256;
 }
 
-template <typename T, bool TRANS, bool SRHT>
+// CPLX (S = A R for complex A, real operator): A is the real view of the
+// complex matrix (K = 2n interleaved (re, im) columns) and B the operator
+// R (x) I_2: B[k][c] = R[k / 2][c / 2] when k and c have the same parity, 0
+// otherwise; the output columns c are the interleaved (re, im) parts of S's.
+template <typename T, bool TRANS, bool SRHT, bool CPLX = false>
 __global__ void __launch_bounds__(256)
     dense_simt_kernel(const T* __restrict__ A, int64_t lda, int64_t M, int64_t K, const T* __restrict__ zt,
                       const int8_t* __restrict__ diag, const int32_t* __restrict__ mu, int64_t n, int c_lo,
@@ -59,13 +63,15 @@ __global__ void __launch_bounds__(256)
       const int64_t gk = k0 + kk;
       const int gc = c0 + cc;
       T v = T(0);
-      if (gk < K && gc < c_hi) {
+      if (gk < K && gc < c_hi && (!CPLX || ((gk ^ gc) & 1) == 0)) {
+        const int64_t rk = CPLX ? (gk >> 1) : gk;
+        const int rc = CPLX ? (gc >> 1) : gc;
         if (SRHT) {
-          const int neg = (__popcll((unsigned long long)gk & (unsigned long long)(uint32_t)mu[gc]) & 1) ^
-                          (diag[gk] < 0);
+          const int neg = (__popcll((unsigned long long)rk & (unsigned long long)(uint32_t)mu[rc]) & 1) ^
+                          (diag[rk] < 0);
           v = neg ? T(-1) : T(1);
         } else {
-          v = zt[(int64_t)gc * n + gk];
+          v = zt[(int64_t)rc * n + rk];
         }
       }
       Bs[kk][cc] = v;
@@ -124,6 +130,28 @@ static int launch_dense(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int 
   else if (srht) JLS_LAUNCH(false, true);
   else JLS_LAUNCH(false, false);
 #undef JLS_LAUNCH
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// S = A R for complex A (interleaved FP32 parts, rows x n complex) on CUDA
+// cores: the real view times R (x) I_2, written straight into S's interleaved
+// parts (columns [2 c_lo, 2 c_hi) of the real view of S).
+int dense_apply_simt_complex_s(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
+                               cudaStream_t s) {
+  if (h->kind == SK_GAUSS) JLS_CHECK(gen_gauss(h, 0, h->d_total, s));
+  const int64_t M = A->rows, K = 2 * A->cols;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((2 * (c_hi - c_lo) + BN - 1) / BN));
+  const float* a = static_cast<const float*>(A->A);
+  if (h->kind == SK_SRHT)
+    dense_simt_kernel<float, false, true, true><<<grid, 256, 0, s>>>(
+        a, 2 * A->ld, M, K, nullptr, h->srht_diag, h->srht_mu, h->n, 2 * c_lo, 2 * c_hi, (float)scale,
+        static_cast<float*>(S), 2 * ldS);
+  else
+    dense_simt_kernel<float, false, false, true><<<grid, 256, 0, s>>>(
+        a, 2 * A->ld, M, K, h->z32, h->srht_diag, h->srht_mu, h->n, 2 * c_lo, 2 * c_hi, (float)scale,
+        static_cast<float*>(S), 2 * ldS);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;

@@ -435,16 +435,18 @@ int encode_plane(CUtensorMap* tm, const uint16_t* plane, int64_t n, int rows, in
   return r == CUDA_SUCCESS ? SK_OK : SK_ERR_ALIGN;
 }
 
-int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, float scale, float* out, int64_t ldo,
-              cudaStream_t s) {
-  const int planes = h->kind == SK_GAUSS ? 2 : 1;
-  const uint16_t* p0 = h->kind == SK_GAUSS ? h->zhi : h->srht_pm1;
-  const uint16_t* p1 = h->kind == SK_GAUSS ? h->zlo : h->srht_pm1;
+}  // namespace
+
+// The tensor-core sketch of FP32 A with operator planes p0 (and p1 with
+// planes == 2): rows [c_lo, c_hi) of the planes, each k_len bf16 values with
+// rows of bf_pitch(k_len), are the operator's columns.
+int launch_tc_planes(int* d_err, const sk_matrix* A, bool trans, int planes, const uint16_t* p0, const uint16_t* p1,
+                     int64_t k_len, int c_lo, int c_hi, float scale, float* out, int64_t ldo, cudaStream_t s) {
   TcWork w{};
   w.m_rows = trans ? A->cols : A->rows;
-  w.k_len = h->n;
+  w.k_len = k_len;
   w.mtiles = (w.m_rows + TC_BM - 1) / TC_BM;
-  w.kst = (int)((h->n + TC_BK - 1) / TC_BK);
+  w.kst = (int)((k_len + TC_BK - 1) / TC_BK);
   const int ncols = c_hi - c_lo;
   const int ntiles = (ncols + TC_NMAX - 1) / TC_NMAX;
   w.nt = ((ncols + ntiles - 1) / ntiles + 15) / 16 * 16;
@@ -458,8 +460,8 @@ int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, floa
   if (w.tmem_cols > 512) return SK_ERR_UNSUPPORTED;
 
   CUtensorMap t0, t1;
-  JLS_CHECK(encode_plane(&t0, p0, h->n, c_hi, w.nt));
-  JLS_CHECK(encode_plane(&t1, p1, h->n, c_hi, w.nt));
+  JLS_CHECK(encode_plane(&t0, p0, k_len, c_hi, w.nt));
+  JLS_CHECK(encode_plane(&t1, p1, k_len, c_hi, w.nt));
   JLS_CHECK_CUDA(cudaMemset2DAsync(out + c_lo, ldo * sizeof(float), 0, (size_t)ncols * sizeof(float),
                                    (size_t)w.m_rows, s));
   const int64_t tiles = (int64_t)ntiles * w.mtiles;
@@ -471,7 +473,7 @@ int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, floa
   do {                                                                                                       \
     auto kern = tc_sketch_kernel<TR, PL>;                                                                   \
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-    kern<<<grid, TC_THREADS, smem, s>>>(a, A->ld, t0, t1, w, scale, out, ldo, vec_ok, h->d_err);            \
+    kern<<<grid, TC_THREADS, smem, s>>>(a, A->ld, t0, t1, w, scale, out, ldo, vec_ok, d_err);               \
   } while (0)
   if (trans && planes == 2) JLS_TC_LAUNCH(true, 2);
   else if (trans) JLS_TC_LAUNCH(true, 1);
@@ -481,6 +483,16 @@ int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, floa
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
+}
+
+namespace {
+
+int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, float scale, float* out, int64_t ldo,
+              cudaStream_t s) {
+  const int planes = h->kind == SK_GAUSS ? 2 : 1;
+  const uint16_t* p0 = h->kind == SK_GAUSS ? h->zhi : h->srht_pm1;
+  const uint16_t* p1 = h->kind == SK_GAUSS ? h->zlo : h->srht_pm1;
+  return launch_tc_planes(h->d_err, A, trans, planes, p0, p1, h->n, c_lo, c_hi, scale, out, ldo, s);
 }
 
 }  // namespace

@@ -147,6 +147,14 @@ struct sk_op {
   // SRHT +-1 plane for the tensor-core path (bf16 bits, d_max rows of bf_pitch(n))
   uint16_t* srht_pm1 = nullptr;
   int pm1_cols = 0;
+  // complex A with SRHT / Gaussian operators: expanded tensor-core planes of
+  // R (x) I_2 (2 d_max rows of bf_pitch(2n)), columns expanded so far, and the
+  // V^T R buffer of S' = A* R
+  void* cplx_p0 = nullptr;
+  void* cplx_p1 = nullptr;
+  int cplx_cols = 0;
+  void* cplx_T = nullptr;
+  size_t cplx_T_bytes = 0;
 
   // FP8 path: e4m3 planes (d_max rows of f8_pitch(n) bytes).  Gaussian: z_hi,
   // z_lo in units of the scale of each (128-value K tile, column), scales
@@ -244,7 +252,13 @@ int num_sms();
 // --- jlsketch.cu helpers ---
 void note_launch();  // counts kernel launches (sketch_launch_count)
 double op_scale(const sk_op* h);  // SJLT 1/sqrt(alpha * blocks); SRHT, Gaussian 1/sqrt(d_total) (block scale: see jlsketch.cu)
-bool block_scaled(const sk_op* h);  // SK_SCALE_BLOCK on an SRHT or Gaussian operator: column scales differ by block
+bool block_scaled(const sk_op* h);
+int launch_tc_planes(int* d_err, const sk_matrix* A, bool trans, int planes, const uint16_t* p0, const uint16_t* p1,
+                     int64_t k_len, int c_lo, int c_hi, float scale, float* out, int64_t ldo, cudaStream_t s);
+int dense_apply_simt_complex_s(sk_op* h, const sk_matrix* A, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
+                               cudaStream_t s);
+int dense_apply_complex(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, double scale,
+                        void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s);  // SK_SCALE_BLOCK on an SRHT or Gaussian operator: column scales differ by block
 int cuda_status(cudaError_t e);
 size_t elem_size(int dtype);
 

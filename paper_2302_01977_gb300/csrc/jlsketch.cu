@@ -58,9 +58,10 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
                        const void* St, int64_t ldSt) {
   if (!A || which < SK_S || which > SK_BOTH) return SK_ERR_INVALID_ARG;
   if (A->dtype != SK_F32 && A->dtype != SK_F64 && A->dtype != SK_C64) return SK_ERR_DTYPE;
-  if (A->dtype == SK_C64 &&
-      (A->generator || prec != SK_PREC_NATIVE || (h->kind != SK_SJLT_BLOCK && h->kind != SK_SJLT_GRAPH)))
-    return SK_ERR_DTYPE;  // complex data: explicit A, SJLT operators
+  if (A->dtype == SK_C64 && A->generator) return SK_ERR_DTYPE;  // complex data: explicit A
+  if (A->dtype == SK_C64 && prec != SK_PREC_NATIVE &&
+      (prec != SK_PREC_BF16X2 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
+    return SK_ERR_DTYPE;  // SJLT: FP32 sums; SRHT, Gaussian: FP32 or the bf16 split
   if (A->generator) {
     if (A->generator != 1 || A->rows < 1 || A->cols < 1 || !A->X || !A->Y || !(A->h > 0)) return SK_ERR_INVALID_ARG;
   } else {
@@ -70,8 +71,9 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
   if ((which & SK_S) && (A->cols != h->n || !S || ldS < h->d_total)) return SK_ERR_INVALID_ARG;
   if ((which & SK_ST) && (A->rows != h->n || !St || ldSt < h->d_total)) return SK_ERR_INVALID_ARG;
   if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2 && prec != SK_PREC_FP8) return SK_ERR_DTYPE;
-  if (prec != SK_PREC_NATIVE && (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
+  if (prec != SK_PREC_NATIVE && ((A->dtype != SK_F32 && A->dtype != SK_C64) || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
     return SK_ERR_DTYPE;
+  if (A->dtype == SK_C64 && prec == SK_PREC_FP8) return SK_ERR_DTYPE;
   return SK_OK;
 }
 
@@ -157,7 +159,11 @@ static int dispatch_range(sk_op* h, const sk_matrix* A, int which, int prec, int
     which &= ~SK_S;
     if (!which) return SK_OK;
   }
-  if (A->dtype == SK_C64) return sjlt_apply_complex(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+  if (A->dtype == SK_C64) {
+    if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
+      return sjlt_apply_complex(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+    return dense_apply_complex(h, A, which, prec, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+  }
   if (h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH)
     return sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
   if (prec == SK_PREC_BF16X2) return dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
@@ -186,7 +192,7 @@ static void free_handle(sk_op* h) {
                   h->srht_diag, h->srht_mu, h->srht_state, h->z32, h->z64, h->zhi, h->zlo, h->srht_pm1,
                   h->z8_hi, h->z8_lo, h->z8_scale, h->srht_q8,
                   h->basis[0].Q, h->basis[1].Q, h->scratch[0], h->scratch[1], h->gen_scratch, h->ksk_u,
-                  h->ccs[2].ents, h->ccs[2].offs, h->sjlt_ents2};
+                  h->ccs[2].ents, h->ccs[2].offs, h->sjlt_ents2, h->cplx_p0, h->cplx_p1, h->cplx_T};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 2; ++k) {
