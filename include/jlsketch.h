@@ -494,9 +494,15 @@ int sketch_srht_batch_set(sk_srht_batch_handle b, const int32_t* c_lo, const int
 int sketch_srht_batch_run(sk_srht_batch_handle b, void* stream);
 
 /* sketch_srht_batch_info -- the chosen CTAs per SM, the units (rows) of the
- * next run and the tuner's times (ms) for 3, 6 and 12 CTAs per SM; any
- * pointer may be NULL. */
-int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms);
+ * next run, the tuner's times (ms; 6 floats: 3, 6 and 12 CTAs per SM with
+ * Sec. 7.1's split of rows with n = k + r, 0 < r <= k / 2, k = nu / 2, then
+ * the same without it, on zero-padded rows; 0 where not timed) and whether
+ * the split was kept (*split = 1); any pointer may be NULL.  The split
+ * transforms such a row at orders k and p = 2^ceil(log2 r) in two passes (the
+ * second adds +-(A^ H_p)_{mu mod p} to the sampled outputs) instead of at
+ * order nu. */
+int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms,
+                           int32_t* split);
 
 /*
  * sketch_srht_batch_adaptive_setup -- prepare Algorithm 1's adaptive loop for

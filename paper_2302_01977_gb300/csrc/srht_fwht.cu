@@ -401,7 +401,8 @@ struct SbItem {
   int64_t nrows;  // rows of A_i
   int32_t n, nu, c_lo, c_hi;
   float scale;
-  int32_t flags;  // bit 0: rows start on 16-byte boundaries (A and lda * 4)
+  int32_t flags;   // bit 0: rows start on 16-byte boundaries (A and lda * 4)
+  int32_t tail_p;  // Sec. 7.1's split: n = k + r with k = nu / 2 and 0 < r <= k / 2, p = 2^ceil(log2 r); 0: none
 };
 
 // row r of an instance into `stg` (nu floats, zero past n) by cp.async: 16-byte
@@ -469,7 +470,7 @@ __device__ void sb_rows_reg(const SbItem& it, int64_t r0, int64_t r1, float* tb,
     for (int j = 0; j < E; ++j) tb[idx(128 * h + g + G * j)] = x[j];
     __syncthreads();
     float* srow = it.S + r * it.ldS;
-    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[idx(it.mu[c])];
+    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[idx(it.mu[c] & (P - 1))];
     __syncthreads();
   }
 }
@@ -491,7 +492,7 @@ __device__ void sb_rows_smem(const SbItem& it, int64_t r0, int64_t r1, float* tb
       __syncthreads();
     }
     float* srow = it.S + r * it.ldS;
-    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[it.mu[c]];
+    for (int c = it.c_lo + t; c < it.c_hi; c += SB_THREADS) srow[c] = it.scale * tb[it.mu[c] & (p - 1)];
     __syncthreads();
   }
 }
@@ -513,10 +514,14 @@ __global__ void __launch_bounds__(SB_THREADS, 6)
   }
   int64_t u = u0;
   for (int i = lo; i < count && u < u1; ++i) {
-    const SbItem it = items[i];
+    SbItem it = items[i];
     const int64_t end = min64(u1, it.unit0 + it.rows);
     if (u >= end) continue;  // an instance left out of this run
     const int64_t r0 = u - it.unit0, r1 = end - it.unit0;
+    if (it.tail_p) {  // Sec. 7.1's split: this pass transforms the first k = nu / 2 columns at order k
+      it.nu /= 2;
+      it.n = it.nu;
+    }
     switch (it.nu) {
       case 4096: sb_rows_reg<32>(it, r0, r1, tb, stg); break;
       case 2048: sb_rows_reg<16>(it, r0, r1, tb, stg); break;
@@ -526,6 +531,81 @@ __global__ void __launch_bounds__(SB_THREADS, 6)
     }
     u = end;
   }
+}
+
+// The second pass of Sec. 7.1's split (Eqs. had1, hadiden) for the rows of
+// instances with tail_p > 0 (n = k + r, k = nu / 2, 0 < r <= k / 2): the
+// first pass wrote scale (A_k H_k)_{mu mod k}; this adds
+// +- scale (A^ H_p)_{mu mod p} (+ below k, - above), A^ the last r columns
+// with D's signs, zero-padded to p.  One warp per row: lane l holds tail
+// values l + 32 j (j < PER = max(1, p / 32)); the bits of j by butterflies in
+// registers, the lane bits by shuffles; the transform goes through a warp-owned
+// shared buffer to the lanes that add it to the sampled columns (a read and a
+// write per output, after the first pass in stream order: deterministic).
+// Grid: (instance, group of rows), TAIL_WARPS warps per CTA.
+constexpr int TAIL_WARPS = 4;
+constexpr int TAIL_ROWS_PER_CTA_Y = 32;  // gridDim.y = ceil(max rows / this)
+
+template <int PER>
+__device__ void sb_tail_row(const SbItem& it, int64_t r, float* buf) {
+  const int lane = threadIdx.x & 31, k = it.nu / 2, p = it.tail_p, rr = it.n - k;
+  const float* a = it.A + r * it.lda + k;
+  float x[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = lane + 32 * j;
+    const float v = i < rr ? __ldg(a + i) : 0.f;
+    x[j] = (i < rr && it.diag[k + i] < 0) ? -v : v;
+  }
+#pragma unroll
+  for (int st = 0; (1 << st) < PER; ++st) stage_s<PER>(x, st);
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1) {
+    if (b >= p) break;  // uniform
+    const float sg = (lane & b) ? -1.f : 1.f;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) x[j] = fmaf(sg, x[j], __shfl_xor_sync(0xffffffffu, x[j], b));
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j)
+    if (lane + 32 * j < p) buf[lane + 32 * j] = x[j];
+  __syncwarp();
+  float* srow = it.S + r * it.ldS;
+  for (int c = it.c_lo + lane; c < it.c_hi; c += 32) {
+    const int m = it.mu[c];
+    const float w = buf[m & (p - 1)];
+    srow[c] += it.scale * (m < k ? w : -w);
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(TAIL_WARPS * 32) srht_batch_tail_kernel(const SbItem* __restrict__ items) {
+  __shared__ float buf[TAIL_WARPS][SB_MAX_NU / 4];  // p <= nu / 4
+  const SbItem& it = items[blockIdx.x];
+  if (!it.tail_p || !it.rows || it.c_hi <= it.c_lo) return;
+  const int warp = threadIdx.x >> 5;
+  const int per = it.tail_p <= 32 ? 1 : it.tail_p / 32;
+  for (int64_t r = (int64_t)blockIdx.y * TAIL_WARPS + warp; r < it.nrows; r += (int64_t)gridDim.y * TAIL_WARPS) {
+    switch (per) {
+      case 1: sb_tail_row<1>(it, r, buf[warp]); break;
+      case 2: sb_tail_row<2>(it, r, buf[warp]); break;
+      case 4: sb_tail_row<4>(it, r, buf[warp]); break;
+      case 8: sb_tail_row<8>(it, r, buf[warp]); break;
+      case 16: sb_tail_row<16>(it, r, buf[warp]); break;
+      default: sb_tail_row<32>(it, r, buf[warp]); break;
+    }
+  }
+}
+
+// The tail order p of Sec. 7.1's split for a batched row of n values and
+// padded order nu (n = k + r, k = nu / 2, 0 < r <= k / 2), or 0 (transform the
+// zero-padded row).
+static int srht_batch_split_p(int64_t n, int64_t nu) {
+  const int64_t k = nu / 2, r = n - k;
+  if (nu < 4 || r <= 0 || r > k / 2) return 0;
+  int p = 1;
+  while (p < r) p *= 2;
+  return p;
 }
 
 // Between the rounds of the adaptive loop: the test kernel has left each
@@ -577,7 +657,10 @@ struct sk_srht_batch {
   jls::SbItem* d_items = nullptr;
   int64_t total = 0;               // units of the next run
   int ctas_per_sm = 6;
-  float tuned_ms[3] = {};
+  bool has_tail = false;           // some instance takes Sec. 7.1's split (a second, tail pass)
+  int64_t max_rows = 0;
+  float tuned_ms[6] = {};          // per tuner candidate: CTAs per SM 3, 6, 12 with the split, then without
+  bool split_used = false;         // the tuner kept Sec. 7.1's split
   // the adaptive loop (sketch_srht_batch_adaptive_setup)
   bool adaptive = false;
   int max_tests = 0, a_ncl = 1;
@@ -608,6 +691,17 @@ void sb_number(sk_srht_batch* b) {
   b->total = u;
 }
 
+// the tail pass of Sec. 7.1's split, after the order-k pass in stream order
+int sb_tail_launch(sk_srht_batch* b, cudaStream_t s) {
+  if (!b->has_tail) return SK_OK;
+  const dim3 grid((unsigned)b->count,
+                  (unsigned)std::max<int64_t>(1, (b->max_rows + TAIL_ROWS_PER_CTA_Y - 1) / TAIL_ROWS_PER_CTA_Y));
+  srht_batch_tail_kernel<<<grid, TAIL_WARPS * 32, 0, s>>>(b->d_items);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
 int sb_launch(sk_srht_batch* b, cudaStream_t s) {
   JLS_CHECK_CUDA(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(SbItem) * b->count, cudaMemcpyHostToDevice, s));
   if (b->total == 0) return SK_OK;
@@ -616,10 +710,24 @@ int sb_launch(sk_srht_batch* b, cudaStream_t s) {
   srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, b->count, b->total, nullptr);
   note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
-  return SK_OK;
+  return sb_tail_launch(b, s);
 }
 
 // one timed run per CTAs-per-SM choice (after one untimed run); keeps the fastest
+// Sets every item's tail order (Sec. 7.1's split on) or clears them (the
+// zero-padded rows).
+void sb_set_split(sk_srht_batch* b, bool on) {
+  b->has_tail = false;
+  for (int i = 0; i < b->count; ++i) {
+    SbItem& I = b->h_items[i];
+    I.tail_p = on ? srht_batch_split_p(I.n, I.nu) : 0;
+    b->has_tail |= I.tail_p > 0;
+  }
+}
+
+// CTAs per SM (3, 6 or 12) and, where some instance qualifies, Sec. 7.1's
+// split on or off: each candidate is timed once on the caller's stream (after
+// one untimed run) and the fastest is kept.
 int sb_tune(sk_srht_batch* b, cudaStream_t s) {
   cudaEvent_t e0, e1;
   JLS_CHECK_CUDA(cudaEventCreate(&e0));
@@ -627,9 +735,15 @@ int sb_tune(sk_srht_batch* b, cudaStream_t s) {
     cudaEventDestroy(e0);
     return SK_ERR_DEVICE;
   }
-  int rc = SK_OK, best = 0;
-  for (int k = 0; k < 3 && rc == SK_OK; ++k) {
-    b->ctas_per_sm = SB_CTAS[k];
+  // JLS_SRHT_SPLIT=1 or =0 pins the split on or off instead of timing both
+  const char* env = std::getenv("JLS_SRHT_SPLIT");
+  const int pin = env && !env[1] ? (env[0] == '1' ? 1 : env[0] == '0' ? 0 : -1) : -1;
+  sb_set_split(b, true);
+  const int k_lo = (pin == 0 || !b->has_tail) ? 3 : 0, k_hi = (pin == 1 && b->has_tail) ? 3 : 6;
+  int rc = SK_OK, best = k_lo;
+  for (int k = k_lo; k < k_hi && rc == SK_OK; ++k) {
+    b->ctas_per_sm = SB_CTAS[k % 3];
+    sb_set_split(b, k < 3);
     if ((rc = sb_launch(b, s)) != SK_OK) break;
     if (cudaEventRecord(e0, s) != cudaSuccess || (rc = sb_launch(b, s)) != SK_OK ||
         cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -637,11 +751,13 @@ int sb_tune(sk_srht_batch* b, cudaStream_t s) {
       rc = rc == SK_OK ? SK_ERR_DEVICE : rc;
       break;
     }
-    if (k == 0 || b->tuned_ms[k] < b->tuned_ms[best]) best = k;
+    if (k == k_lo || b->tuned_ms[k] < b->tuned_ms[best]) best = k;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->ctas_per_sm = SB_CTAS[best];
+  b->ctas_per_sm = SB_CTAS[best % 3];
+  sb_set_split(b, best < 3);
+  b->split_used = b->has_tail;
   return rc;
 }
 
@@ -696,6 +812,7 @@ int sketch_srht_batch_create(sk_srht_batch_handle* out, const sk_srht_batch_item
     I.nrows = it.rows;
     I.scale = (float)(it.scale != 0.0 ? it.scale : 1.0 / std::sqrt((double)h->d_total));
     I.flags = ((reinterpret_cast<uintptr_t>(it.A) & 15u) == 0 && (it.ld * 4) % 16 == 0) ? 1 : 0;
+    b->max_rows = std::max<int64_t>(b->max_rows, it.rows);
   }
   sb_number(b);
   // six CTAs of 33 KB of shared memory per SM: ask for the largest shared-memory carveout
@@ -729,12 +846,14 @@ int sketch_srht_batch_run(sk_srht_batch_handle b, void* stream) {
   return sb_launch(b, static_cast<cudaStream_t>(stream));
 }
 
-int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms) {
+int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t* units, float* tuned_ms,
+                           int32_t* split) {
   if (!b) return SK_ERR_INVALID_ARG;
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (units) *units = b->total;
   if (tuned_ms)
-    for (int k = 0; k < 3; ++k) tuned_ms[k] = b->tuned_ms[k];
+    for (int k = 0; k < 6; ++k) tuned_ms[k] = b->tuned_ms[k];
+  if (split) *split = b->split_used ? 1 : 0;
   return SK_OK;
 }
 
@@ -858,6 +977,7 @@ int sketch_srht_batch_adaptive_run(sk_srht_batch_handle b, int32_t max_rounds, v
     srht_batch_kernel<<<grid, SB_THREADS, 0, s>>>(b->d_items, count, 0, b->d_units);
     note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
+    JLS_CHECK(sb_tail_launch(b, s));
     JLS_CHECK(adaptive_test_launch(b->d_loop, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs, s));
   }
   return adaptive_rescale_launch(b->d_tests, count, s);

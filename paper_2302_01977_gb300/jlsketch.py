@@ -132,7 +132,7 @@ def lib() -> ctypes.CDLL:
         "sketch_srht_batch_create": (i32, [P(vp), P(SkSrhtBatchItem), i32, vp]),
         "sketch_srht_batch_set": (i32, [vp, vp, vp]),
         "sketch_srht_batch_run": (i32, [vp, vp]),
-        "sketch_srht_batch_info": (i32, [vp, P(i32), P(i64), P(ctypes.c_float)]),
+        "sketch_srht_batch_info": (i32, [vp, P(i32), P(i64), P(ctypes.c_float), P(i32)]),
         "sketch_srht_batch_adaptive_setup": (i32, [vp, P(i32), i32, ctypes.c_double, ctypes.c_double, vp]),
         "sketch_srht_batch_adaptive_run": (i32, [vp, i32, vp]),
         "sketch_srht_batch_adaptive_result": (i32, [vp, P(i32), P(i32), P(i32), P(ctypes.c_double),
@@ -525,10 +525,11 @@ class SrhtBatch:
         return dict(d=d, state=st, tests=t, nh=nh, nt=nt)
 
     def info(self) -> dict:
-        c, u = ctypes.c_int32(), ctypes.c_int64()
-        ms = (ctypes.c_float * 3)()
-        _check(lib().sketch_srht_batch_info(self.b, ctypes.byref(c), ctypes.byref(u), ms), "sketch_srht_batch_info")
-        return dict(ctas_per_sm=c.value, units=u.value, tuned_ms=[round(x, 4) for x in ms])
+        c, u, sp = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        ms = (ctypes.c_float * 6)()
+        _check(lib().sketch_srht_batch_info(self.b, ctypes.byref(c), ctypes.byref(u), ms, ctypes.byref(sp)),
+               "sketch_srht_batch_info")
+        return dict(ctas_per_sm=c.value, units=u.value, split=bool(sp.value), tuned_ms=[round(x, 4) for x in ms])
 
     def close(self):
         if self.b:

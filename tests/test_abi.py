@@ -92,7 +92,7 @@ def test_null_handle_calls(L):
     assert L.sketch_srht_batch_create(None, None, 0, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_srht_batch_set(None, None, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_srht_batch_run(None, None) == jl.SK_ERR_INVALID_ARG
-    assert L.sketch_srht_batch_info(None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.sketch_srht_batch_info(None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_srht_batch_adaptive_setup(None, d0, 32, 1e-3, 0.0, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_srht_batch_adaptive_run(None, 0, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_srht_batch_adaptive_result(None, None, None, None, None, None, None) == jl.SK_ERR_INVALID_ARG

@@ -82,6 +82,28 @@ def test_srht_batch_matches_oracle():
         x["op"].close()
 
 
+@pytest.mark.parametrize("n", [65, 300, 576, 700, 1088, 1500, 2112, 3000])
+def test_srht_batch_split_equals_padded_transform(n, monkeypatch):
+    """Rows with n = k + r, 0 < r <= k / 2 (k = nu / 2) can take Sec. 7.1's
+    split (orders k and p = 2^ceil(log2 r), two passes); JLS_SRHT_SPLIT=1 pins
+    it on and =0 pins the zero-padded rows of order nu (by default the batch's
+    tuner times both).  Both equal the oracle's A R and each other to FP32
+    rounding."""
+    outs = []
+    for split in ("0", "1"):
+        monkeypatch.setenv("JLS_SRHT_SPLIT", split)
+        inst = make([(150, n, 48, 1, 16, 0.15)], seed=100 + n)
+        x = inst[0]
+        with jl.SrhtBatch([(x["op"].h, x["A"], x["S"], 0, x["d"])]) as B:
+            B.run()
+            torch.cuda.synchronize()
+            assert B.info()["split"] == (split == "1")
+        check(x, 0, x["d"])
+        outs.append(x["S"].double().cpu().numpy())
+        x["op"].close()
+    assert np.linalg.norm(outs[1] - outs[0]) <= 1e-6 * np.linalg.norm(outs[0])
+
+
 def test_srht_batch_graph_replay_of_increments():
     specs = [(512, 512, 64, 3, 32, 0.2), (384, 384, 128, 3, 32, 0.1), (1000, 1000, 96, 3, 32, 0.3),
              (2500, 2500, 64, 3, 32, 0.05)]
@@ -295,11 +317,14 @@ def test_srht_batch_adaptive_matches_oracle(eps_rel):
         x["op"].close()
 
 
-def test_srht_batch_adaptive_tight_tolerance_same_sketch():
+@pytest.mark.parametrize("split", ["0", "1"])
+def test_srht_batch_adaptive_tight_tolerance_same_sketch(split, monkeypatch):
     """eps_rel = 1e-6: each decision against the FP64 test on the device's own
     sketch (outside a 1 % band around eps_rel), the last test's ratio within
-    1 % plus the device arithmetic's resolution."""
+    1 % plus the device arithmetic's resolution; with the rows zero-padded and
+    with Sec. 7.1's split (n = 1088, 1000, 448 qualify)."""
     from tests.util import batch_same_s
+    monkeypatch.setenv("JLS_SRHT_SPLIT", split)
     dd, eps_rel = 32, 1e-6
     specs = [(256, 64, 4, 0.5, 1.0), (448, 32, 7, 0.2, 1.0), (1000, 64, 6, 0.3, 1.0), (2048, 128, 5, 0.25, 1.0),
              (1088, 96, 6, 0.35, 1.0), (512, 96, 2, 0.03, 1.0)]
