@@ -870,15 +870,15 @@ def run_batching(args):
 
 
 BATCH_ADAPT = dict(name="batch_adaptive_fp32_1024", count=1024, n_lo=256, n_hi=4096, h_lo=0.05, h_hi=0.5,
-                   d0=(64, 128, 256), dd=32, alpha=4, incs=8, eps_rel=1e-6, eps_abs=0.0, seed=20230203 + 3)
+                   d0=(64, 128, 256), dd=32, alpha=4, eps_rel=1e-6, eps_abs=0.0, seed=20230203 + 3)
 
 
 def run_batch_adaptive(args):
     """Algorithm 1 for 1024 independent FP32 Gaussian kernel matrices (the batch
     workload's instances) on the device: per round one batched SJLT launch over the
     instances still active, the stopping test of Eq. (3.1) per instance (a CTA cluster
-    each), and the table update; Delta-d = 32, eps_rel = 1e-6, at most 8 increments
-    (R_i grown up front to d0_i + 9 * 32 columns).  The whole loop is one captured
+    each), and the table update; Delta-d = 32, eps_rel = 1e-6, increments up to d_max_i = n_i
+    (R_i grown up front to d_max_i columns).  The whole loop is one captured
     CUDA graph; value = bytes of A_i streamed (one pass per test taken) / run time."""
     import numpy as np
     import torch
@@ -897,16 +897,19 @@ def run_batch_adaptive(args):
     ns = 64 * rng.integers(w["n_lo"] // 64, w["n_hi"] // 64 + 1, size=w["count"])
     hs = rng.uniform(w["h_lo"], w["h_hi"], size=w["count"])
     d0s = rng.choice(w["d0"], size=w["count"])
-    dd, incs = w["dd"], w["incs"]
+    dd = w["dd"]
+    # increments per instance: up to d_max_i = n_i (the configuration as written), or a fixed count
+    incs_i = [max(0, (int(ns[i]) - int(d0s[i])) // dd - 1) if not args.max_increments else args.max_increments
+              for i in range(w["count"])]  # d_max_i = n_i, and at least d0_i + dd (one test)
     ops, As, Sts = [], [], []
     for i in range(w["count"]):
         n = int(ns[i])
         X = torch.from_numpy(inputs.points(n, seed=w["seed"] + 17 * i)).cuda()
         A = torch.empty((n, n), device="cuda")
         jl.kernel_matrix(jl.generator(X, X, float(hs[i])), A)
-        d_max = int(d0s[i]) + (incs + 1) * dd
+        d_max = int(d0s[i]) + (incs_i[i] + 1) * dd
         op = jl.Sketch("sjlt_block", n, int(d0s[i]) + dd, w["alpha"], w["seed"] + i, d_max=d_max)
-        for _ in range(incs):
+        for _ in range(incs_i[i]):
             jl.sketch_increment(op.h, dd)
         ops.append(op)
         As.append(A)
@@ -950,7 +953,7 @@ def run_batch_adaptive(args):
     for i in rng.choice(small, min(3, len(small)), replace=False):
         d = int(res["d"][i])
         blocks_d = 1 + (d - int(d0s[i]) - dd) // dd
-        Rd = jl.sketch_export(ops[i].h, dense=True)["R"][:, :d] * np.sqrt((incs + 1) / blocks_d)
+        Rd = jl.sketch_export(ops[i].h, dense=True)["R"][:, :d] * np.sqrt((incs_i[i] + 1) / blocks_d)
         ref = As[i].double().cpu().numpy().T @ Rd
         got = Sts[i][:, :d].double().cpu().numpy()
         errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
@@ -960,7 +963,9 @@ def run_batch_adaptive(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
             "config": {"workload": w["name"], "instances": w["count"], "n_range": [w["n_lo"], w["n_hi"]],
                        "h_range": [w["h_lo"], w["h_hi"]], "d0": list(w["d0"]), "dd": dd, "alpha": w["alpha"],
-                       "max_increments": incs, "eps_rel": w["eps_rel"], "eps_abs": w["eps_abs"],
+                       "d_max": ("max(n_i, d0_i + dd)" if not args.max_increments
+                                 else f"d0_i + {args.max_increments + 1} * dd"),
+                       "eps_rel": w["eps_rel"], "eps_abs": w["eps_abs"],
                        "l2": "inputs larger than L2 (24 GB of A), no flush"},
             "adaptive_run_ms": round(t_run, 3), "rounds": rounds,
             "pct_hbm_of_streamed_bytes": round(100 * bytes_streamed / t_run / 1e6 / hbm, 1),
@@ -975,25 +980,26 @@ def run_batch_adaptive(args):
     B.close()
     for op in ops:
         op.close()
-    line["srht"] = batch_adaptive_srht(args, w, ns, d0s, As, Sts)
+    line["srht"] = batch_adaptive_srht(args, w, ns, d0s, As, Sts, incs_i)
     print(json.dumps(line))
 
 
-def batch_adaptive_srht(args, w, ns, d0s, As, Sts):
+def batch_adaptive_srht(args, w, ns, d0s, As, Sts, incs_i):
     """The same loop with SRHT operators (S_i = A_i R_i = A_i^T R_i, A_i symmetric): an SRHT
-    samples at most nu_i columns, so d0_i <= nu_i - 64 and the increments stop at nu_i."""
+    samples at most nu_i columns, so d0_i <= nu_i - 64 and the increments stop at nu_i (and at
+    the SJLT loop's d_max_i)."""
     import numpy as np
     import torch
 
     from paper_2302_01977_gb300 import jlsketch as jl
 
-    dd, incs = w["dd"], w["incs"]
+    dd = w["dd"]
     ops, items, d0c = [], [], []
     for i in range(w["count"]):
         n = int(ns[i])
         nu = 1 << (n - 1).bit_length()
         d0 = min(int(d0s[i]), nu - 2 * dd)
-        k = min(incs, (nu - d0) // dd - 1)
+        k = min(incs_i[i], (nu - d0) // dd - 1, (Sts[i].shape[1] - d0) // dd - 1)
         op = jl.Sketch("srht", n, d0 + dd, 1, w["seed"] + i, d_max=d0 + (k + 1) * dd)
         for _ in range(k):
             jl.sketch_increment(op.h, dd)
@@ -1026,7 +1032,7 @@ def batch_adaptive_srht(args, w, ns, d0s, As, Sts):
            "converged": int((res["state"] == 1).sum()), "out_of_columns": int((res["state"] == 2).sum()),
            "still_running": int((res["state"] == 0).sum()), "tests_taken": int(res["tests"].sum()),
            "mean_d": round(float(res["d"].mean()), 1), "ctas_per_sm": B.info()["ctas_per_sm"],
-           "d_cap": "d0_i <= nu_i - 64, d_max_i <= nu_i"}
+           "d_cap": "d0_i <= nu_i - 64, d_max_i <= min(nu_i, the SJLT loop's d_max_i)"}
     B.close()
     for op in ops:
         op.close()
@@ -1215,6 +1221,8 @@ def main():
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--points", type=int, default=0,
                     help="kernel_sketch_grad workload: number of points (default 262144; smaller for captures)")
+    ap.add_argument("--max-increments", type=int, default=0,
+                    help="batch_adaptive workload: increments per instance (default 0: up to d_max_i = n_i)")
     ap.add_argument("--instances", type=int, default=0,
                     help="batch workload: number of instances (default 1024; fewer for captures)")
     ap.add_argument("--only", choices=["all", "sjlt", "srht", "gauss", "adaptive"], default="all",

@@ -392,10 +392,11 @@ int sketch_batch_status(sk_batch_handle b, void* stream);
  * at a time).  The test of Eq. (3.1) runs on S'_i = A_i^T R_i (S_i for a
  * symmetric A_i) with eps_rel and eps_abs (0 disables the absolute test).
  * d0[i] (host array of `count`) and dd are multiples of 8, 8 <= dd <= 32, and
- * d_total(R_i) - dd <= 512.  Rebuilds the tiles of operators grown since the
+ * d_total(R_i) - dd <= 8192.  Rebuilds the tiles of operators grown since the
  * batch was made, tunes the kernel shape for the first sketch and for the
  * increments (the tuning runs write the outputs), allocates each instance's
- * orthonormal basis (cols_i x (d_total_i - dd) FP32) and a cols_i x 32 block,
+ * orthonormal basis (cols_i x (d_total_i - dd) FP32), a cols_i x 32 block and,
+ * for bases wider than 512 columns, a (d_total_i - dd) x 32 product Q^T W,
  * and leaves the batch's ranges at [0, d0[i] + dd).  The stopping test runs one
  * CTA per instance when the batch has at least as many instances as the GPU
  * has SMs, a thread-block cluster of 4 CTAs per instance otherwise (the
@@ -519,7 +520,7 @@ int sketch_srht_batch_info(sk_srht_batch_handle b, int32_t* ctas_per_sm, int64_t
  * and the finished columns are rescaled once, so S_i[:, :d] = A_i R_i[:, :d].
  * The loop is the SJLT batch's (same test kernel, FP32 sketch and basis, FP64
  * norms).  Limits: 8 <= dd <= 32, dd and d0 multiples of 8, d_total - dd <=
- * 512.  Synchronous, not capturable.  Errors: INVALID_ARG, UNSUPPORTED,
+ * 8192.  Synchronous, not capturable.  Errors: INVALID_ARG, UNSUPPORTED,
  * NOMEM, DEVICE.
  */
 int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, int32_t dd, double eps_rel,

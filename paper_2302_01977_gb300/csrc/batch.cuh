@@ -35,6 +35,7 @@ struct alignas(16) ATest {
   const float* S;   // S'_i: rows x ldS (the batch item's output)
   float* Q;         // rows x qcap: orthonormal basis of S'_i[:, :covered] (zero columns where a pivot dropped)
   float* W;         // rows x 32: the block under test or being absorbed
+  float* G;         // qcap x 32: Q^T W when the basis is wider than ADAPT_QSMEM (else unused, may be null)
   int64_t rows, ldS;
   int32_t qcap, q, covered, dd;
   int32_t d_cap;    // columns of R_i (the loop stops, unconverged, when the next increment would pass it)
@@ -48,13 +49,15 @@ struct alignas(16) ATest {
 };
 enum : int32_t { ADAPT_ACTIVE = 0, ADAPT_CONVERGED = 1, ADAPT_CAPPED = 2 };
 
-constexpr int ADAPT_QMAX = 512;  // basis columns per instance
+constexpr int ADAPT_QMAX = 8192;  // basis columns per instance
+constexpr int ADAPT_QSMEM = 512;  // basis columns whose Q^T W stays in shared memory; wider bases keep it in G
 constexpr int ADAPT_BW = 32;     // widest increment dd
 
 // Kernels of batch_adaptive.cu (all asynchronous on `s`, capturable).
 int adaptive_prepare();  // shared-memory limit of the test kernel (call outside capture)
-int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
-                         double eps_abs, cudaStream_t s);
+// a round's tests with the cluster size picked on the device by the active count (list, n_active: scratch)
+int adaptive_test_round(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
+                        double eps_abs, bool wide, int* list, int* n_active, cudaStream_t s);
 int adaptive_renumber_launch(BItem* items, int count, BHeader* hdr, int njobs, int nb, int* err, cudaStream_t s);
 int adaptive_rescale_launch(const ATest* tests, int count, cudaStream_t s);
 

@@ -46,9 +46,10 @@ namespace cg = cooperative_groups;
 namespace jls {
 namespace {
 
-constexpr int CLMAX = 4;  // CTAs per instance, at most (a cluster)
+constexpr int CLMAX = 4;  // CTAs per instance chosen at setup, at most (a cluster; rounds with few active
+                          // instances left use clusters of 8)
 constexpr int AT = 512;   // threads per CTA
-constexpr int QMAX = ADAPT_QMAX;
+constexpr int QMAX = ADAPT_QSMEM;  // Q^T W in shared memory per chunk of the basis
 constexpr int BW = ADAPT_BW;
 constexpr int QCH = 57344;  // bytes of Q per staged chunk of Q^T W
 constexpr int RCMAX = 64;   // rows per staged chunk of Q^T W, at most
@@ -76,6 +77,10 @@ static_assert(GR * BW / 4 % AT == 0 && AT == 512, "thread mappings assume 512 th
 static_assert(SM_TOTAL <= 227 * 1024, "one CTA per SM");
 
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+
+// The instance's global Q^T W (ATest::G) for bases wider than QMAX, kept in
+// shared memory rather than in a register for the whole kernel.
+__shared__ float* s_gg;
 template <typename T>
 __device__ __forceinline__ T* cl_map(T* p, int rank) {
   return cg::this_cluster().map_shared_rank(p, (unsigned)rank);
@@ -171,7 +176,7 @@ __device__ double load_block(const Ctx& c, const float* S, int64_t ldS, int c0, 
 // added in shared memory (group order).  Then CTA k adds up the k-th quarter
 // of the entries over the cluster's CTAs and writes the sums into every
 // CTA's Gs.
-__device__ void qt_w(Ctx& c, int q) {
+__device__ void qt_w(Ctx& c, int q, const float* Qb) {
   const int U = (q >> 3) * 4;  // tiles: 8 rows of G x 8 of its 32 columns
   const int RG = max(1, AT / U);
   const int t = threadIdx.x;
@@ -200,7 +205,7 @@ __device__ void qt_w(Ctx& c, int q) {
         const int rr = e / q4, k4 = e - rr * q4;
         const int64_t r = rb + rr;
         const bool in = r < c.r1;
-        cp_async_16z(smem_u32(qd + rr * q + k4 * 4), in ? c.Q + r * c.ldq + k4 * 4 : c.Q, in);
+        cp_async_16z(smem_u32(qd + rr * q + k4 * 4), in ? Qb + r * c.ldq + k4 * 4 : Qb, in);
       } else {
         const int e2 = e - nq, rr = e2 >> 3, j4 = e2 & 7;
         const int64_t r = rb + rr;
@@ -280,11 +285,37 @@ __device__ void qt_w(Ctx& c, int q) {
   cl_sync();
 }
 
+// G = Q[:, :q]^T W for any q (a multiple of 8): in shared memory (c.Gs) for
+// q <= QMAX, else chunk by chunk of QMAX columns into the instance's global G
+// (written by the cluster's rank 0, read by all CTAs after the closing
+// cluster barrier).
+template <bool WIDE>
+__device__ void qt_w_all(Ctx& c, int q) {
+  if constexpr (!WIDE) {
+    qt_w(c, q, c.Q);
+    return;
+  }
+  if (q <= QMAX) {
+    qt_w(c, q, c.Q);
+    return;
+  }
+  for (int q0 = 0; q0 < q; q0 += QMAX) {
+    const int qc = min(QMAX, q - q0);
+    qt_w(c, qc, c.Q + q0);
+    if (c.rank == 0)
+      for (int e = threadIdx.x; e < qc * BW / 4; e += AT)
+        reinterpret_cast<float4*>(s_gg + (int64_t)q0 * BW)[e] = reinterpret_cast<const float4*>(c.Gs)[e];
+    cl_sync();  // the chunk is stored before Gs is overwritten, and G is complete after the last one
+  }
+}
+
 // W <- W - Q[:, :q] Gs on this CTA's rows: passes of PR rows; Q staged
 // transposed KC columns at a time (the next step's loads in flight); four
 // groups of threads take 8 of each step's columns with 8 x 8 register tiles,
 // and their partial products are added in shared memory at the end of a pass.
+template <bool GG>
 __device__ void w_minus_qg(const Ctx& c, int q) {
+  const float* G = GG ? s_gg : c.Gs;
   float* Qt = reinterpret_cast<float*>(c.stage);  // [2][KC][PR + 4]
   float* Pw = reinterpret_cast<float*>(c.stage);  // [4][PR][BW], after a pass's last step
   const int kq = threadIdx.x >> 7, lt = threadIdx.x & 127;
@@ -335,8 +366,8 @@ __device__ void w_minus_qg(const Ctx& c, int q) {
           const int kk = kq * 8 + k8;
           const float4 a0 = *reinterpret_cast<const float4*>(Qb + kk * (PR + 4) + rg * 8);
           const float4 a1 = *reinterpret_cast<const float4*>(Qb + kk * (PR + 4) + rg * 8 + 4);
-          const float4 g0 = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg * 8);
-          const float4 g1 = *reinterpret_cast<const float4*>(c.Gs + (k0 + kk) * BW + cg * 8 + 4);
+          const float4 g0 = *reinterpret_cast<const float4*>(G + (k0 + kk) * BW + cg * 8);
+          const float4 g1 = *reinterpret_cast<const float4*>(G + (k0 + kk) * BW + cg * 8 + 4);
           fma8x8(acc, a0, a1, g0, g1);
         }
       }
@@ -398,7 +429,9 @@ __device__ __forceinline__ void df_sub(float& hi, float& lo, float a, float g) {
 // a time as in w_minus_qg; a thread owns a 4 x 4 tile (rows 4 rg .. 4 rg + 3,
 // columns 4 cg .. 4 cg + 3) over all q columns of Q, so no partial sums are
 // exchanged.  The result is rounded to FP32 once.
+template <bool GG>
 __device__ void w_minus_qg_df(const Ctx& c, int q) {
+  const float* G = GG ? s_gg : c.Gs;
   float* Qt = reinterpret_cast<float*>(c.stage);  // [2][KC][PR + 4]
   const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;  // 8 column groups x 64 row groups
   const int srow = threadIdx.x & (PR - 1), spart = threadIdx.x / PR;  // staging: row, which KC/2 columns
@@ -450,7 +483,7 @@ __device__ void w_minus_qg_df(const Ctx& c, int q) {
       }
       if (busy) {
         const float* Qb = Qt + (st & 1) * QT_FLOATS + rg * 4;
-        const float* Gb = c.Gs + k0 * BW + cg * 4;
+        const float* Gb = G + k0 * BW + cg * 4;
         const int kn = min(KC, q - k0);  // a multiple of 8
         for (int k8 = 0; k8 < kn; k8 += 8) {
 #pragma unroll
@@ -693,14 +726,18 @@ constexpr double DROP_PASS2 = 1e-2;
 // matrix; absorb_end finishes the pass.  Returns the trace of the first Gram
 // matrix (the same value in every CTA of the cluster): with the precise steps
 // ||(I - Q Q^T)^2 W||_F^2.
+template <bool WIDE>
 __device__ double absorb_begin(Ctx& c, int q, double dref, bool precise) {
+  const bool gg = WIDE && q > QMAX;
   if (q > 0) {
-    qt_w(c, q);
+    qt_w_all<WIDE>(c, q);
     if (precise) {
-      w_minus_qg_df(c, q);
-      qt_w(c, q);
+      if (gg) w_minus_qg_df<WIDE>(c, q);
+      else w_minus_qg_df<false>(c, q);
+      qt_w_all<WIDE>(c, q);
     }
-    w_minus_qg(c, q);
+    if (gg) w_minus_qg<WIDE>(c, q);
+    else w_minus_qg<false>(c, q);
   }
   gram_pass(c);
   double tr = 0.0;
@@ -708,8 +745,9 @@ __device__ double absorb_begin(Ctx& c, int q, double dref, bool precise) {
   for (int i = 0; i < BW; ++i) tr += c.gram[i * LD + i];
   factor_solve(c, true, (precise ? DROP_PRECISE : DROP_FP32) * dref);
   if (q > 0) {
-    qt_w(c, q);
-    w_minus_qg(c, q);
+    qt_w_all<WIDE>(c, q);
+    if (gg) w_minus_qg<WIDE>(c, q);
+    else w_minus_qg<false>(c, q);
   }
   gram_pass(c);
   return tr > 0.0 ? tr : 0.0;
@@ -749,14 +787,23 @@ __device__ void absorb_end(Ctx& c, int& q, int b) {
 }
 
 // One instance per cluster of ncl CTAs (launched with that cluster size; 1: a
-// CTA alone, whose cluster barriers are CTA barriers).
+// CTA alone, whose cluster barriers are CTA barriers).  WIDE: some instance's
+// basis may pass QMAX columns (Q^T W then goes through the instance's global
+// G); a separate instantiation, so that batches of narrower bases keep the
+// kernel's registers without spills.
+template <bool WIDE>
 __global__ void __launch_bounds__(AT, 1)
     batch_test_kernel(BItem* __restrict__ items, ATest* __restrict__ tests, const int* __restrict__ order, int ncl,
-                      double eps_rel, double eps_abs, bool precise) {
+                      double eps_rel, double eps_abs, bool precise, const int* __restrict__ active, int act_lo,
+                      int act_hi) {
   extern __shared__ __align__(16) uint8_t smem[];
   Ctx c;
   c.ncl = ncl;
   c.rank = (int)cg::this_cluster().block_rank();
+  if (active) {  // order: the active instances, largest first (active_list_kernel); this launch's share
+    const int a = *active;
+    if (a < act_lo || a >= act_hi || (int)(blockIdx.x / ncl) >= a) return;  // uniform over a cluster
+  }
   const int inst = order[blockIdx.x / ncl];
   ATest* T = tests + inst;
   BItem* I = items + inst;
@@ -771,6 +818,7 @@ __global__ void __launch_bounds__(AT, 1)
   c.Qw = T->Q;
   c.ldq = T->qcap;
   c.W = T->W;
+  if (threadIdx.x == 0) s_gg = T->G;  // read after the first barrier
   c.stage = smem;
   c.Gs = reinterpret_cast<float*>(smem + SM_STAGE);
   c.gram = reinterpret_cast<double*>(smem + SM_STAGE + SM_G);
@@ -785,13 +833,13 @@ __global__ void __launch_bounds__(AT, 1)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
     const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
-    absorb_begin(c, q, dref, precise);
+    absorb_begin<WIDE>(c, q, dref, precise);
     absorb_end(c, q, b);
     covered += b;
   }
   // the test, Eq. (3.1): its two projections are those of the absorption
   const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
-  const double tr1 = absorb_begin(c, q, nt2, precise);
+  const double tr1 = absorb_begin<WIDE>(c, q, nt2, precise);
   const double nh2 = precise ? tr1 : lgl_trace(c);
   const double sc = T->srht ? sqrt((double)T->first_w / (double)c_end)
                             : 1.0 / sqrt((double)(1 + (c_end - T->first_w) / dd));
@@ -878,13 +926,42 @@ __global__ void __launch_bounds__(256) batch_rescale_kernel(const ATest* __restr
 }  // namespace
 
 int adaptive_prepare() {
-  JLS_CHECK_CUDA(cudaFuncSetAttribute(batch_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
+  JLS_CHECK_CUDA(
+      cudaFuncSetAttribute(batch_test_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(batch_test_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL));
   return SK_OK;
 }
 
-int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
-                         double eps_abs, cudaStream_t s) {
-  if (ncl != 1 && ncl != 2 && ncl != CLMAX) return SK_ERR_INVALID_ARG;
+// The instances still active, in the order of `order` (largest first), and
+// how many (one CTA).
+__global__ void __launch_bounds__(1024)
+    active_list_kernel(const ATest* __restrict__ tests, const int* __restrict__ order, int count,
+                       int* __restrict__ list, int* __restrict__ n_active) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (count + 1023) / 1024;
+  const int i0 = min(count, t * per), i1 = min(count, i0 + per);
+  int k = 0;
+  for (int i = i0; i < i1; ++i) k += tests[order[i]].state == ADAPT_ACTIVE;
+  part[t] = k;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int j = 0; j < 1024; ++j) {
+      const int v = part[j];
+      part[j] = run;
+      run += v;
+    }
+    *n_active = run;
+  }
+  __syncthreads();
+  int o = part[t];
+  for (int i = i0; i < i1; ++i)
+    if (tests[order[i]].state == ADAPT_ACTIVE) list[o++] = order[i];
+}
+
+static int launch_test(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
+                       double eps_abs, bool wide, const int* active, int act_lo, int act_hi, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(count * ncl));
   cfg.blockDim = dim3(AT);
@@ -898,9 +975,35 @@ int adaptive_test_launch(BItem* items, ATest* tests, const int* order, int count
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const bool precise = eps_rel < kPreciseBelow;
-  JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel, items, tests, order, ncl, eps_rel, eps_abs, precise));
+  if (wide)
+    JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel<true>, items, tests, order, ncl, eps_rel, eps_abs, precise,
+                                      active, act_lo, act_hi));
+  else
+    JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, batch_test_kernel<false>, items, tests, order, ncl, eps_rel, eps_abs,
+                                      precise, active, act_lo, act_hi));
   note_launch();
   return SK_OK;
+}
+
+// One round's tests.  A batch of fewer instances than SMs runs clusters of
+// ncl CTAs per instance.  Larger batches list their active instances on the
+// device first and then make three launches, of which only the one that fits
+// the count runs: one CTA per instance while at least as many instances as
+// SMs are active, clusters of 4 from a quarter of that, clusters of 8 below
+// (as instances converge, the remaining ones get more SMs each).  `list`
+// (count ints) and `n_active` are device scratch.
+int adaptive_test_round(BItem* items, ATest* tests, const int* order, int count, int ncl, double eps_rel,
+                        double eps_abs, bool wide, int* list, int* n_active, cudaStream_t s) {
+  if (ncl != 1 && ncl != 2 && ncl != CLMAX) return SK_ERR_INVALID_ARG;
+  const int sms = num_sms();
+  if (count < sms || !list || !n_active)
+    return launch_test(items, tests, order, count, ncl, eps_rel, eps_abs, wide, nullptr, 0, 0, s);
+  active_list_kernel<<<1, 1024, 0, s>>>(tests, order, count, list, n_active);
+  note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  JLS_CHECK(launch_test(items, tests, list, count, 1, eps_rel, eps_abs, wide, n_active, sms, 1 << 30, s));
+  JLS_CHECK(launch_test(items, tests, list, count, 4, eps_rel, eps_abs, wide, n_active, sms / 4, sms, s));
+  return launch_test(items, tests, list, count, 8, eps_rel, eps_abs, wide, n_active, 0, sms / 4, s);
 }
 
 int adaptive_renumber_launch(BItem* items, int count, BHeader* hdr, int njobs, int nb, int* err, cudaStream_t s) {

@@ -238,6 +238,7 @@ struct sk_batch {
   int cfg_first = -1, cfg_inc = -1;  // shapes for the first sketch and for the increments
   int a_stages = 0, max_tests = 0;
   int a_ncl = 1;  // CTAs per instance in the test kernel
+  bool a_wide = false;  // some instance's basis passes ADAPT_QSMEM columns
   size_t a_smem = 0;
   double eps_rel = 0.0, eps_abs = 0.0;
   jls::BItem* d_items0 = nullptr;  // the item table and header of round 0
@@ -615,11 +616,14 @@ int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd
   std::vector<ATest> a0(count);
   std::vector<size_t> off(count);
   size_t total = 0;
+  bool wide = false;  // some basis passes ADAPT_QSMEM columns
   for (int i = 0; i < count; ++i) {
     const sk_op* h = b->items[i].op;
     const int qcap = std::max(8, (h->d_total - dd + 7) / 8 * 8);
     off[i] = total;
     total += (size_t)b->items[i].cols * (qcap + ADAPT_BW);
+    if (qcap > ADAPT_QSMEM) total += (size_t)qcap * ADAPT_BW;  // Q^T W of a wide basis
+    wide |= qcap > ADAPT_QSMEM;
     ATest& T = a0[i];
     std::memset(&T, 0, sizeof(T));
     T.S = b->items[i].St;
@@ -640,7 +644,7 @@ int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd
       cudaMalloc(&b->d_hdr0, sizeof(BHeader)) != cudaSuccess ||
       cudaMalloc(&b->d_tests, sizeof(ATest) * count) != cudaSuccess ||
       cudaMalloc(&b->d_tests0, sizeof(ATest) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_order, sizeof(int) * (2 * count + 1)) != cudaSuccess ||  // order, active list, count
       cudaMalloc(&b->d_basis, total * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     adaptive_free(b);
@@ -650,6 +654,7 @@ int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd
     const int qcap = a0[i].qcap;
     a0[i].Q = b->d_basis + off[i];
     a0[i].W = b->d_basis + off[i] + (size_t)b->items[i].cols * qcap;
+    a0[i].G = qcap > ADAPT_QSMEM ? a0[i].W + (size_t)b->items[i].cols * ADAPT_BW : nullptr;
   }
   int rc = adaptive_prepare();
   if (rc == SK_OK &&
@@ -667,6 +672,7 @@ int sketch_batch_adaptive_setup(sk_batch_handle b, const int32_t* d0, int32_t dd
   b->a_stages = stages;
   b->a_smem = smem;
   b->max_tests = max_tests;
+  b->a_wide = wide;
   // the stopping test: one CTA per instance amortizes its fixed costs best; a
   // cluster of 4 per instance when the instances would not fill the GPU
   const char* env = std::getenv("JLS_ADAPT_CLUSTER");
@@ -689,7 +695,8 @@ int sketch_batch_adaptive_run(sk_batch_handle b, int32_t max_rounds, void* strea
   const BConfig& Ci = kConfigs[b->cfg_inc];
   for (int r = 0; r < rounds; ++r) {
     JLS_CHECK(batch_launch_device(b, r == 0 ? b->cfg_first : b->cfg_inc, s));
-    JLS_CHECK(adaptive_test_launch(b->d_items, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs, s));
+    JLS_CHECK(adaptive_test_round(b->d_items, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs,
+                                  b->a_wide, b->d_order + count, b->d_order + 2 * count, s));
     if (r + 1 < rounds) JLS_CHECK(adaptive_renumber_launch(b->d_items, count, b->d_hdr, Ci.warps - 1, Ci.nb, b->d_err, s));
   }
   return adaptive_rescale_launch(b->d_tests, count, s);

@@ -664,6 +664,7 @@ struct sk_srht_batch {
   // the adaptive loop (sketch_srht_batch_adaptive_setup)
   bool adaptive = false;
   int max_tests = 0, a_ncl = 1;
+  bool a_wide = false;  // some instance's basis passes ADAPT_QSMEM columns
   double eps_rel = 0.0, eps_abs = 0.0;
   jls::SbItem* d_sb0 = nullptr;   // round 0's items: [0, d0 + dd) at the loop's scale 1/sqrt(d0 + dd)
   jls::BItem* d_loop = nullptr;   // the loop table the test kernel updates (c_lo, c_hi, units)
@@ -892,6 +893,7 @@ int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, 
   std::vector<ATest> a0(count);
   std::vector<size_t> off(count);
   size_t total = 0;
+  bool wide = false;  // some basis passes ADAPT_QSMEM columns
   int max_tests = 0;
   for (int i = 0; i < count; ++i) {
     const sk_op* h = b->items[i].op;
@@ -904,6 +906,8 @@ int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, 
     const int qcap = std::max(8, (h->d_total - dd + 7) / 8 * 8);
     off[i] = total;
     total += (size_t)b->items[i].rows * (qcap + ADAPT_BW);
+    if (qcap > ADAPT_QSMEM) total += (size_t)qcap * ADAPT_BW;  // Q^T W of a wide basis
+    wide |= qcap > ADAPT_QSMEM;
     ATest& T = a0[i];
     std::memset(&T, 0, sizeof(T));
     T.S = b->items[i].S;
@@ -927,7 +931,7 @@ int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, 
       cudaMalloc(&b->d_loop0, sizeof(BItem) * count) != cudaSuccess ||
       cudaMalloc(&b->d_tests, sizeof(ATest) * count) != cudaSuccess ||
       cudaMalloc(&b->d_tests0, sizeof(ATest) * count) != cudaSuccess ||
-      cudaMalloc(&b->d_order, sizeof(int) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_order, sizeof(int) * (2 * count + 1)) != cudaSuccess ||  // order, active list, count
       cudaMalloc(&b->d_basis, total * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&b->d_units, sizeof(int64_t)) != cudaSuccess) {
     cudaGetLastError();
@@ -937,6 +941,7 @@ int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, 
   for (int i = 0; i < count; ++i) {
     a0[i].Q = b->d_basis + off[i];
     a0[i].W = b->d_basis + off[i] + (size_t)b->items[i].rows * a0[i].qcap;
+    a0[i].G = a0[i].qcap > ADAPT_QSMEM ? a0[i].W + (size_t)b->items[i].rows * ADAPT_BW : nullptr;
   }
   int rc = adaptive_prepare();
   if (rc == SK_OK &&
@@ -950,6 +955,7 @@ int sketch_srht_batch_adaptive_setup(sk_srht_batch_handle b, const int32_t* d0, 
     return rc;
   }
   b->max_tests = max_tests;
+  b->a_wide = wide;
   // the stopping test: one CTA per instance when the instances fill the GPU, else a cluster of 4
   const char* env = std::getenv("JLS_ADAPT_CLUSTER");
   b->a_ncl = env ? std::atoi(env) : (count >= num_sms() ? 1 : 4);
@@ -978,7 +984,8 @@ int sketch_srht_batch_adaptive_run(sk_srht_batch_handle b, int32_t max_rounds, v
     note_launch();
     JLS_CHECK_CUDA(cudaGetLastError());
     JLS_CHECK(sb_tail_launch(b, s));
-    JLS_CHECK(adaptive_test_launch(b->d_loop, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs, s));
+    JLS_CHECK(adaptive_test_round(b->d_loop, b->d_tests, b->d_order, count, b->a_ncl, b->eps_rel, b->eps_abs,
+                                  b->a_wide, b->d_order + count, b->d_order + 2 * count, s));
   }
   return adaptive_rescale_launch(b->d_tests, count, s);
 }

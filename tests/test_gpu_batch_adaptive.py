@@ -230,6 +230,37 @@ def test_adaptive_batch_tight_tolerance_same_sketch(eps_rel):
         x["op"].close()
 
 
+@pytest.mark.parametrize("eps_rel", [1e-6, 1e-3])
+def test_adaptive_batch_wide_basis(eps_rel):
+    """Bases wider than the 512 columns whose Q^T W stays in shared memory (the
+    loop runs to d_max = n for rough kernels): Q^T W goes through each
+    instance's global G in chunks of 512 columns.  Decisions and the last
+    ratio against the FP64 test on the device's sketch, the sketch against the
+    FP64 A^T R."""
+    dd = 32
+    specs = [("sjlt_block", 800, 64, 4, 22, 0.03, 1.0),    # rough: every increment, basis up to 768 columns
+             ("sjlt_block", 704, 32, 4, 20, 0.12, 1.0),
+             ("sjlt_graph", 640, 96, 4, 16, 0.05, 1.0)]
+    inst = make(specs, dd, seed=23)
+    items = [(x["op"].h, x["A"], x["St"], 0, x["d0"] + dd) for x in inst]
+    with jl.Batch(items) as B:
+        B.adaptive_setup([x["d0"] for x in inst], dd, eps_rel, 0.0)
+        B.adaptive_run()
+        res = B.adaptive_result()
+    assert int(res["d"][0]) - dd > 512  # the first instance's basis passed 512 columns
+    for i, x in enumerate(inst):
+        batch_same_s(x, res, i, dd, eps_rel)
+        d = int(res["d"][i])
+        R = ops.Operator(x["kind"], x["n"], x["d0"] + dd, x["alpha"], x["seed"])
+        for _ in range((d - x["d0"] - dd) // dd):
+            R.increment(dd)
+        want = x["A"].double().cpu().numpy().T @ R.dense()
+        got = x["St"][:, :d].double().cpu().numpy()
+        assert np.linalg.norm(got - want) <= TOL * np.linalg.norm(want), i
+    for x in inst:
+        x["op"].close()
+
+
 def test_adaptive_batch_full_size_1024():
     """The benchmark's batched adaptive workload in the launch configuration it
     times: 1024 kernel matrices K(X_i, X_i; h_i), n_i over multiples of 64 in
