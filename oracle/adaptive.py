@@ -62,6 +62,31 @@ def norm_test(S: np.ndarray, d: int, dd: int, eps_rel: float, eps_abs: float):
     return stop, nh, nt
 
 
+def norm_tests(S: np.ndarray, d0: int, dd: int, d_end: int):
+    """Every test of norm_test on one sketch: for b0 = d0, d0 + dd, ...,
+    d_end - dd, (||S^||_F, ||S~||_F) of S~ = S[:, b0 : b0 + dd] against the
+    range of S[:, :b0].  The same definitions as norm_test, with the range
+    basis grown block by block: range(S[:, :b0 + dd]) is range(S[:, :b0])
+    plus the range of the projected block S^, whose directions are kept above
+    ||S[:, :d_end]||_F max(m, b) eps (the Frobenius norm bounds the sigma_1 of
+    norm_test's threshold from above; the two differ only for directions at
+    the FP64 rounding level of S)."""
+    S = np.asarray(S, dtype=np.float64)
+    m = S.shape[0]
+    eps = np.finfo(np.float64).eps
+    s1 = float(np.linalg.norm(S[:, :d_end]))
+    Q = range_basis(S[:, :d0])
+    out = []
+    for b0 in range(d0, d_end - dd + 1, dd):
+        W = S[:, b0:b0 + dd]
+        Sh = project_twice(Q, W) if Q.shape[1] else W.copy()
+        out.append((float(np.linalg.norm(Sh)), float(np.linalg.norm(W))))
+        U, sv, _ = np.linalg.svd(Sh, full_matrices=False)
+        keep = sv > s1 * max(m, b0 + dd) * eps
+        Q = np.hstack([Q, U[:, keep]])
+    return out
+
+
 def adaptive(A: np.ndarray, kind: str, d0: int, dd: int, alpha: int, seed: int,
              d_max: int, eps_rel: float, eps_abs: float, which: str = "both"):
     """Run the loop; returns a dict with the operator, final S, S', the

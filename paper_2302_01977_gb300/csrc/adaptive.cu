@@ -30,6 +30,8 @@
 
 namespace jls {
 
+constexpr int NORM_GRID_C = 256;  // CTAs of the norm and column-norm partial sums
+
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void scale_cols_kernel(T* S, int64_t rows, int64_t ld, int c0, int c1, T f) {
@@ -303,13 +305,22 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 template <typename A, typename T, int NR>
 __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restrict__ Gm, int b, T* __restrict__ Lo,
                                                           T* __restrict__ rinv_out, const double* __restrict__ ref,
-                                                          int nref, double tau, double floor_abs) {
+                                                          int nref, double tau, double floor_abs,
+                                                          const double* __restrict__ colpart, int col_ld,
+                                                          double tau_col) {
   __shared__ A L[64][65];
   __shared__ A rinv[64];
   __shared__ A s_sq[2], s_iv[2];
   __shared__ A s_dmax, s_floor;
+  __shared__ A s_colfloor[64];  // tau_col times each column's sum of squares before the projection
   const int tid = threadIdx.x;
   for (int e = tid; e < b * b; e += 256) L[e / b][e % b] = (A)Gm[e];
+  if (tid < 64) {
+    double v = 0.0;
+    if (colpart && tid < b)
+      for (int g = 0; g < NORM_GRID_C; ++g) v += colpart[(int64_t)g * col_ld + tid];  // fixed order
+    s_colfloor[tid] = (A)(tau_col * v);
+  }
   __syncthreads();
   if (tid < 32) {
     A m = 0;
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
   __syncthreads();
   auto pivot = [&](int k) {  // thread 0 only
     const A dmax = s_dmax, pk = L[k][k];
-    const bool dk = !(pk > A(1e-26) * dmax) || !(pk > s_floor) || !(dmax > A(0));
+    const bool dk = !(pk > A(1e-26) * dmax) || !(pk > s_floor) || !(pk > s_colfloor[k]) || !(dmax > A(0));
     A iv = A(0);
     if (!dk) {
       if constexpr (sizeof(A) == 8) iv = rsqrt_nr<NR>(pk);
@@ -464,10 +475,42 @@ __global__ void __launch_bounds__(256) sumsq_partial(const T* __restrict__ W, in
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// Each column's sum of squares of a rows x b block (b <= 512), one FP64
+// partial per CTA and column: part[blockIdx.x * b + j].  256 threads: column
+// t % w of the rows t / w (mod 256 / w), w = min(b, 256), over the CTA's rows.
+template <typename T>
+__global__ void __launch_bounds__(256) colsumsq_partial(const T* __restrict__ W, int64_t ldw, int64_t rows, int b,
+                                                        double* __restrict__ part) {
+  __shared__ double red[256];
+  const int64_t rpb = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min64(rows, r0 + rpb);
+  for (int c0 = 0; c0 < b; c0 += 256) {
+    const int w = min(256, b - c0), per = 256 / w;
+    const int t = threadIdx.x, j = t % w, ro = t / w;
+    double acc = 0.0;
+    if (t < per * w) {
+      T sq = T(0);
+      for (int64_t r = r0 + ro; r < r1; r += per) {
+        const T v = W[r * ldw + c0 + j];
+        sq = fma(v, v, sq);
+      }
+      acc = (double)sq;
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < w) {
+      double v = 0.0;
+      for (int g = 0; g < per; ++g) v += red[g * w + t];
+      part[(int64_t)blockIdx.x * b + c0 + t] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int NORM_GRID = 256;
+constexpr int NORM_GRID = NORM_GRID_C;
 
 // out[0] = tr(G) for the b x b FP64 Gram matrix G = W^T W of the tested block
 // after its two projections (the precise absorption), i.e.
@@ -549,6 +592,8 @@ struct Scratch {
   double* U;      // Cholesky factor (64 x 64) and reciprocal pivots (64), type T
   double* norms;  // 2 x NORM_GRID partials (||S~||^2, ||S^||^2)
   double* ref;    // NORM_GRID partials: a block's sum of squares before its projection
+  double* colref;  // NORM_GRID x wmax partials: each column's sum of squares before its projection
+  int col_ld;      // columns per partial row of colref (the block width they were taken over)
   size_t part_elems;
 };
 
@@ -557,7 +602,8 @@ int ensure_scratch(sk_op* h, int slot, int64_t rows, int dtype, int wmax, Scratc
   const size_t wb = ((size_t)rows * wmax * es + 255) / 256 * 256;
   const size_t part_elems = (size_t)nchunks * h->d_max * wmax;
   const size_t gb = (size_t)h->d_max * wmax * sizeof(double);
-  const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 3 * NORM_GRID * sizeof(double);
+  const size_t need = wb + part_elems * sizeof(double) + gb + 64 * 65 * sizeof(double) + 3 * NORM_GRID * sizeof(double) +
+                      (size_t)NORM_GRID * wmax * sizeof(double);
   if (h->scratch_bytes[slot] < need) {
     if (h->scratch[slot]) cudaFree(h->scratch[slot]);
     h->scratch[slot] = nullptr;
@@ -576,6 +622,8 @@ int ensure_scratch(sk_op* h, int slot, int64_t rows, int dtype, int wmax, Scratc
   p += 64 * 65 * sizeof(double);
   sc->norms = reinterpret_cast<double*>(p);
   sc->ref = sc->norms + 2 * NORM_GRID;
+  sc->colref = sc->ref + NORM_GRID;
+  sc->col_ld = wmax;
   sc->part_elems = part_elems;
   return SK_OK;
 }
@@ -638,6 +686,14 @@ int project_twice(const sk_op* h, const Basis& B, T* W, int64_t ldw, int b, int6
   return project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 2, s, B.precise);
 }
 
+// NORM_GRID x b partial column sums of squares of W into `part` (no synchronization)
+template <typename T>
+int colsumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cudaStream_t s) {
+  colsumsq_partial<T><<<NORM_GRID, 256, 0, s>>>(W, ldw, rows, b, part); note_launch();
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
 // NORM_GRID partial sums of squares of W into `part` (no synchronization)
 template <typename T>
 int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cudaStream_t s) {
@@ -665,7 +721,8 @@ int sumsq_launch(const T* W, int64_t ldw, int64_t rows, int b, double* part, cud
 // again); it is copied to the host with ||S~||^2 and signalled.
 template <typename T>
 int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, const Scratch& sc, int nchunks,
-                 bool project, const double* ref, cudaStream_t s, const TestOut* test = nullptr) {
+                 bool project, const double* ref, cudaStream_t s, const TestOut* test = nullptr,
+                 const double* colref = nullptr, int col_ld = 0) {
   const bool precise = B.precise;
   if (project) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, precise ? 2 : 1, s, precise));
   T* Lf = reinterpret_cast<T*>(sc.U);
@@ -683,6 +740,13 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
   // along Q that the first pass normalized, and is dropped rather than
   // renormalized.
   const double tau = sizeof(T) == 8 ? 1e-26 : (precise ? 1e-20 : 1e-13);
+  // Precise steps also drop a column whose residual is at or below 1e-7 of its
+  // own norm before the projection (colref: each column's sum of squares):
+  // the FP32 basis represents the span of the earlier columns only to about
+  // that level, so a column in that span in exact arithmetic (an SJLT column
+  // with the one entry of an earlier column's row) leaves a residual there,
+  // which normalized would be a direction outside the sketch's range.
+  const double tau_col = (precise && colref) ? 1e-14 : 0.0;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) JLS_CHECK(project_passes<T>(h, B, W, ldw, b, rows, sc, nchunks, 1, s));
     JLS_CHECK(tsgemm<T>(W, ldw, b, W, ldw, b, rows, nchunks, sc.part, sc.G, s));
@@ -700,12 +764,13 @@ int absorb_block(sk_op* h, Basis& B, T* W, int64_t ldw, int b, int64_t rows, con
     const double* r = pass == 0 ? ref : nullptr;
     const int nr = r ? NORM_GRID : 0;
     const double fa = pass == 0 ? 0.0 : kDropPass2;
+    const double* cr = pass == 0 && tau_col > 0.0 ? colref : nullptr;
     if (sizeof(T) == 8)
-      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
+      chol_factor_kernel<double, T, 2><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa, cr, col_ld, tau_col);
     else if (pass == 0)
-      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
+      chol_factor_kernel<double, T, 1><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa, cr, col_ld, tau_col);
     else
-      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa);
+      chol_factor_kernel<float, T, 0><<<1, 256, 0, s>>>(sc.G, b, Lf, rinv, r, nr, tau, fa, nullptr, 0, 0.0);
     note_launch();
     rows_trsm_kernel<T><<<tgrid, RT, 0, s>>>(W, ldw, b, Lf, rinv, rows); note_launch();
   }
@@ -766,16 +831,20 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
     const int b = std::min(64, c_split - B.covered);
     copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + B.covered, ldS, W, 64, rows, b); note_launch();
     JLS_CHECK(sumsq_launch<T>(W, 64, rows, b, sc.ref, s));
-    JLS_CHECK(absorb_block<T>(h, B, W, 64, b, rows, sc, nchunks, true, sc.ref, s));
+    if (precise) JLS_CHECK(colsumsq_launch<T>(W, 64, rows, b, sc.colref, s));
+    JLS_CHECK(absorb_block<T>(h, B, W, 64, b, rows, sc, nchunks, true, sc.ref, s, nullptr,
+                              precise ? sc.colref : nullptr, b));
     B.covered += b;
   }
   // the test block: both norms summed on the device
   copy_block_kernel<T><<<cgrid, 256, 0, s>>>(S + c_split, ldS, W, wmax, rows, bt); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   JLS_CHECK(sumsq_launch<T>(W, wmax, rows, bt, sc.norms, s));
+  if (precise) JLS_CHECK(colsumsq_launch<T>(W, wmax, rows, bt, sc.colref, s));
+  const double* cref = precise ? sc.colref : nullptr;
   if (bt <= 64) {  // one chunk: ||S^|| from its absorption's first Gram matrix
     const TestOut out{sc.norms, h->host_norms[slot], h->norms_ready[slot]};
-    JLS_CHECK(absorb_block<T>(h, B, W, wmax, bt, rows, sc, nchunks, true, sc.norms, s, &out));
+    JLS_CHECK(absorb_block<T>(h, B, W, wmax, bt, rows, sc, nchunks, true, sc.norms, s, &out, cref, bt));
     B.covered = c_end;
     return SK_OK;
   }
@@ -788,7 +857,8 @@ int norm_test_enqueue_t(sk_op* h, int slot, const T* S, int64_t rows, int64_t ld
   // orthogonal to the chunks just added)
   for (int j0 = 0; j0 < bt; j0 += 64) {
     const int b = std::min(64, bt - j0);
-    JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, sc.norms, s));
+    JLS_CHECK(absorb_block<T>(h, B, W + j0, wmax, b, rows, sc, nchunks, j0 > 0, sc.norms, s, nullptr,
+                              cref ? cref + j0 : nullptr, bt));
   }
   B.covered = c_end;
   return SK_OK;

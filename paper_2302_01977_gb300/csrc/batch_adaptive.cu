@@ -68,7 +68,9 @@ constexpr int SM_STAGE = SM_QS + SM_WS;       // also: partial products, Q^T sta
 constexpr int SM_G = QMAX * BW * 4;           // G = Q^T W, FP32
 constexpr int SM_GRAM = BW * LD * 8;          // reduced Gram matrix, FP64
 constexpr int SM_L = BW * LF * 4;             // Cholesky factor, FP32
-constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8 + 2 * BW * 8;  // reciprocal pivots, reduction slots, Cholesky scratch
+constexpr int SM_MISC = 32 * 4 + (NW + 8) * 8 + 4 * BW * 8;  // reciprocal pivots, reduction slots, Cholesky
+                                                              // scratch, the block's column sums of squares (own
+                                                              // part, then the cluster's)
 constexpr int SM_TOTAL = SM_STAGE + SM_G + SM_GRAM + SM_L + SM_MISC;
 static_assert(2 * QMAX * BW * 4 <= SM_STAGE, "the row groups' parts of G fit the staging area");
 static_assert(4 * PR * BW * 4 <= SM_STAGE && 2 * QT_FLOATS * 4 <= SM_STAGE, "W - Q G staging fits");
@@ -99,7 +101,7 @@ struct Ctx {
   float* Lf;
   float* rinv;
   double* red;  // [0, NW): warp sums; [NW]: the CTA's sum, read by the cluster
-  double* cs;   // Cholesky scratch, 2 BW entries
+  double* cs;   // Cholesky scratch (2 BW entries), then the column sums of squares (colsq: 2 BW entries)
 };
 
 __device__ __forceinline__ void cp_async_16z(uint32_t dst, const void* src, bool valid) {
@@ -130,18 +132,6 @@ __device__ double cta_sum(double v, double* red) {
   return s;
 }
 
-// sum over the cluster, the same value in every thread of every CTA
-__device__ double cluster_sum(Ctx& c, double v) {
-  const double s = cta_sum(v, c.red);
-  if (threadIdx.x == 0) c.red[NW] = s;
-  cl_sync();
-  double t = 0.0;
-#pragma unroll
-  for (int r = 0; r < c.ncl; ++r) t += *cl_map(c.red + NW, r);
-  cl_sync();  // the slot is rewritten by the next call
-  return t;
-}
-
 // W[r][j] <- S[r][c0 + j] for j < b (zero for b <= j < BW) on this CTA's rows;
 // returns the thread's share of the sum of squares.  A warp takes a row (32
 // consecutive floats of S); four rows per thread are in flight at a time.
@@ -167,6 +157,35 @@ __device__ double load_block(const Ctx& c, const float* S, int64_t ldS, int c0, 
     ss = fmaf(v, v, ss);
   }
   return (double)ss;
+}
+
+// W <- S[:, c0 : c0 + b] as load_block, and each column's sum of squares over
+// all rows of S'_i (the block before its projection) into colsq(c)[j], the
+// same in every CTA of the cluster (warp partials added in warp order, the
+// CTAs' in rank order); returns the block's sum of squares (their sum).
+__device__ __forceinline__ double* colsq(const Ctx& c) { return c.cs + 2 * BW; }
+__device__ double load_block_cols(Ctx& c, const float* S, int64_t ldS, int c0, int b) {
+  const double ss = load_block(c, S, ldS, c0, b);
+  double* part = reinterpret_cast<double*>(c.stage);  // [NW][32]: the stage area is free while a block loads
+  part[threadIdx.x] = ss;  // warp w, lane j: column j
+  __syncthreads();
+  double* own = colsq(c) + BW;
+  if (threadIdx.x < BW) {
+    double v = 0.0;
+    for (int w = 0; w < NW; ++w) v += part[w * 32 + threadIdx.x];
+    own[threadIdx.x] = v;
+  }
+  cl_sync();
+  if (threadIdx.x < BW) {
+    double v = 0.0;
+    for (int r = 0; r < c.ncl; ++r) v += cl_map(own, r)[threadIdx.x];
+    colsq(c)[threadIdx.x] = v;
+  }
+  cl_sync();  // own is rewritten by the next load
+  double t = 0.0;
+#pragma unroll 8
+  for (int j = 0; j < BW; ++j) t += colsq(c)[j];
+  return t;
 }
 
 // Gs <- Q[:, :q]^T W over all rows of S'_i (q a multiple of 8, <= QMAX), in
@@ -533,8 +552,8 @@ __device__ __forceinline__ A rsqrt_newton(A x) {
 // kept out of line so that it does not crowd the registers of the loops
 // around its call
 template <typename A>
-__device__ __noinline__ A chol_pivot(A pk, A dmax, A floor) {
-  const bool drop = !(pk > A(1e-26) * dmax) || !(pk > floor) || !(dmax > A(0));
+__device__ __noinline__ A chol_pivot(A pk, A dmax, A floor, A col_floor) {
+  const bool drop = !(pk > A(1e-26) * dmax) || !(pk > floor) || !(pk > col_floor) || !(dmax > A(0));
   return drop ? A(0) : rsqrt_newton<A>(pk);
 }
 
@@ -547,7 +566,8 @@ __device__ __noinline__ A chol_pivot(A pk, A dmax, A floor) {
 // in dropped columns) and the reciprocal diagonal into rinv (0 for a dropped
 // column).  iv and u are shared scratch of BW entries each.
 template <typename A, int LDA>
-__device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u, A floor) {
+__device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u, A floor, const double* colref = nullptr,
+                          double tau_col = 0.0) {
   const int t = threadIdx.x;
   if (t < 32) {
     A v = L[t * LDA + t];
@@ -557,7 +577,9 @@ __device__ void chol_drop(A* L, float* Lf, float* rinv, A* iv, A* u, A floor) {
   }
   __syncthreads();
   const A dmax = u[0];
-  auto pivot = [&](int k) { iv[k] = chol_pivot<A>(L[k * LDA + k], dmax, floor); };  // thread 0
+  auto pivot = [&](int k) {  // thread 0
+    iv[k] = chol_pivot<A>(L[k * LDA + k], dmax, floor, colref ? (A)(tau_col * colref[k]) : A(0));
+  };
   __syncthreads();
   for (int k = 0; k < BW; ++k) {
     if (t == 0) pivot(k);
@@ -650,9 +672,10 @@ __device__ void gram_pass(Ctx& c) {
 // The factor of c.gram (FP64 in the first Cholesky-QR pass, where the Gram
 // matrix squares W's condition number; FP32 in the second, where it is the
 // identity up to the first pass's rounding), then W <- W L^{-T} row by row.
-__device__ void factor_solve(Ctx& c, bool fp64, double floor) {
+__device__ void factor_solve(Ctx& c, bool fp64, double floor, double tau_col = 0.0) {
   if (fp64) {
-    chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW, floor);
+    chol_drop<double, LD>(c.gram, c.Lf, c.rinv, c.cs, c.cs + BW, floor, tau_col > 0.0 ? colsq(c) : nullptr,
+                          tau_col);
   } else {
     float* Lw = reinterpret_cast<float*>(c.stage);  // FP32 working copy (the partials are no longer read)
     for (int e = threadIdx.x; e < BW * BW; e += AT) Lw[(e >> 5) * LD + (e & 31)] = (float)c.gram[(e >> 5) * LD + (e & 31)];
@@ -711,7 +734,13 @@ __device__ void factor_solve(Ctx& c, bool fp64, double floor) {
 // of the block (normalizing such a residual, rounding along Q, would cost Q
 // its orthogonality).  Precise steps: DROP_PRECISE, a residual of 1e-10 of
 // the block, a column that is zero in the data (an SJLT column without
-// entries) or rounding.
+// entries) or rounding; and a column whose residual is at or below 1e-7 of
+// its own norm before the projection (DROP_COL on its sum of squares): the
+// FP32 basis represents the span of the earlier columns only to about that
+// level, so a column that lies in that span in exact arithmetic (an SJLT
+// column with the one entry of an earlier column's row: the same column of S
+// up to its sign) leaves a residual there, which normalized would be a basis
+// direction outside the sketch's range.
 // The second pass's input columns have unit norm (or are zero) before the
 // projection between the passes.  A column that this projection shrinks below
 // 0.1 of its length (pivot <= DROP_PASS2) was mostly rounding along Q that the
@@ -719,6 +748,7 @@ __device__ void factor_solve(Ctx& c, bool fp64, double floor) {
 // that is not orthogonal to Q, so it is dropped as well.
 constexpr double DROP_FP32 = 1e-13;
 constexpr double DROP_PRECISE = 1e-20;
+constexpr double DROP_COL = 1e-14;  // precise steps: a pivot at or below 1e-14 of its own column's sum of squares
 constexpr double DROP_PASS2 = 1e-2;
 
 // W arrives as it is: its projection(s), the first Gram matrix, Cholesky-QR
@@ -743,7 +773,7 @@ __device__ double absorb_begin(Ctx& c, int q, double dref, bool precise) {
   double tr = 0.0;
 #pragma unroll 8
   for (int i = 0; i < BW; ++i) tr += c.gram[i * LD + i];
-  factor_solve(c, true, (precise ? DROP_PRECISE : DROP_FP32) * dref);
+  factor_solve(c, true, (precise ? DROP_PRECISE : DROP_FP32) * dref, precise ? DROP_COL : 0.0);
   if (q > 0) {
     qt_w_all<WIDE>(c, q);
     if (gg) w_minus_qg<WIDE>(c, q);
@@ -832,13 +862,13 @@ __global__ void __launch_bounds__(AT, 1)
   // columns before the tested block that Q does not cover yet (the first d0)
   while (covered < c_split) {
     const int b = min(BW, c_split - covered);
-    const double dref = cluster_sum(c, load_block(c, S, ldS, covered, b));
+    const double dref = load_block_cols(c, S, ldS, covered, b);
     absorb_begin<WIDE>(c, q, dref, precise);
     absorb_end(c, q, b);
     covered += b;
   }
   // the test, Eq. (3.1): its two projections are those of the absorption
-  const double nt2 = cluster_sum(c, load_block(c, S, ldS, c_split, dd));
+  const double nt2 = load_block_cols(c, S, ldS, c_split, dd);
   const double tr1 = absorb_begin<WIDE>(c, q, nt2, precise);
   const double nh2 = precise ? tr1 : lgl_trace(c);
   const double sc = T->srht ? sqrt((double)T->first_w / (double)c_end)

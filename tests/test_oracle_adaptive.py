@@ -10,6 +10,9 @@
   with a closed-form ||S^||.
 * A full-rank matrix with a flat spectrum never passes a tight test and stops
   at d_max without converging.
+* norm_tests (every test of one sketch, the range basis grown block by block)
+  equals norm_test test by test, on decaying, rank-deficient and exactly
+  low-rank sketches.
 """
 import numpy as np
 import pytest
@@ -87,3 +90,23 @@ def test_rank_deficient_sketch_projects_on_its_range():
     assert abs(nh - np.sqrt(10.0)) < 1e-13 and abs(nt - np.sqrt(11.0)) < 1e-13
     assert not stop  # sqrt(10 / 11) > 0.5
     assert ad.range_basis(np.zeros((n, 3))).shape[1] == 0
+
+
+@pytest.mark.parametrize("case", ["decay", "zero_cols", "low_rank"])
+def test_norm_tests_equal_norm_test(case):
+    rng = np.random.default_rng(12)
+    m, d0, dd, d_end = 300, 24, 8, 120
+    if case == "decay":
+        A = inputs.spectrum_matrix(m, 0.85 ** np.arange(m), seed=13)
+        S = A @ rng.standard_normal((m, d_end))
+    elif case == "zero_cols":
+        S = inputs.spectrum_matrix(m, 0.9 ** np.arange(m), seed=14) @ rng.standard_normal((m, d_end))
+        S[:, [3, 30, 31, 77]] = 0.0  # columns without entries
+        S[:, 50] = 2.0 * S[:, 10]    # a repeated direction
+    else:
+        S = inputs.low_rank_matrix(m, 40, seed=15) @ rng.standard_normal((m, d_end))
+    got = ad.norm_tests(S, d0, dd, d_end)
+    for k, b0 in enumerate(range(d0, d_end - dd + 1, dd)):
+        _, nh, nt = ad.norm_test(S, b0, dd, 0.0, 0.0)
+        assert abs(got[k][1] - nt) <= 1e-12 * nt
+        assert abs(got[k][0] - nh) <= 1e-9 * nt + 1e-9 * nh, (case, b0, got[k][0], nh)
