@@ -155,7 +155,7 @@ class Step:
         seed = w["seed"] + 7919 * step_idx
         hs = []
         try:
-            ops = [("sjlt", "sjlt_block", w["alpha"], jl.SK_PREC_NATIVE),
+            ops = [("sjlt", "sjlt_block", w["alpha"], self.prec_dense),
                    ("srht", "srht", 1, self.prec_dense), ("gauss", "gauss", 1, self.prec_dense)]
             passes = 0
             for name, kind, alpha, prec in ops:
@@ -172,7 +172,8 @@ class Step:
             # adaptive SJLT run (Algorithm 1 on the global sketch)
             h = jl.sketch_create("sjlt_block", self.n, w["d0"] + w["dd"], w["alpha"], seed + 1, w["d_max"])
             hs.append(h)
-            self._ev("adaptive.apply", lambda: jl.sketch_apply(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
+            self._ev("adaptive.apply",
+                     lambda: jl.sketch_apply(h, A, jl.SK_BOTH, self.prec_dense, S=self.adS, St=self.adSt))
             d, hist = w["d0"], []
             passes += 2
             ad_passes = 2
@@ -186,7 +187,8 @@ class Step:
                     break
                 jl.sketch_increment(h, w["dd"])
                 self._ev("adaptive.increment",
-                         lambda: jl.sketch_apply_increment(h, A, jl.SK_BOTH, 0, S=self.adS, St=self.adSt))
+                         lambda: jl.sketch_apply_increment(h, A, jl.SK_BOTH, self.prec_dense, S=self.adS,
+                                                           St=self.adSt))
                 passes += 2
                 ad_passes += 2
                 d += w["dd"]
@@ -329,8 +331,14 @@ def run_ours(args):
     for name in ("srht", "gauss"):
         if name in per_op:
             per_op[name]["prec"] = "bf16x2" if prec_dense == jl.SK_PREC_BF16X2 else "fp32"
+    sjlt_routes = {"S": -1, "St": -1}
     if "sjlt" in per_op:
-        per_op["sjlt"]["prec"] = "fp32"
+        if prec_dense == jl.SK_PREC_BF16X2:  # each product's route, picked by timing on its first call
+            sjlt_routes = {"S": jl.sketch_sjlt_route("sjlt_block", n, n, n, w["d"], jl.SK_S),
+                           "St": jl.sketch_sjlt_route("sjlt_block", n, n, n, w["d"], jl.SK_ST)}
+        per_op["sjlt"]["prec"] = "bf16x2 allowed" if prec_dense == jl.SK_PREC_BF16X2 else "fp32"
+        per_op["sjlt"]["route"] = {k: {1: "tensor-core +-1 product", 0: "SJLT kernel", -1: "SJLT kernel"}[v]
+                                   for k, v in sjlt_routes.items()}
     if step.adaptive_info:
         per_op["adaptive_sjlt"] = dict(step.adaptive_info)
 
@@ -339,6 +347,14 @@ def run_ours(args):
     cls = {"sjlt_rows": totals.get("sjlt.S", 0), "sjlt_cols": totals.get("sjlt.St", 0),
            "srht": totals.get("srht.S", 0) + totals.get("srht.St", 0),
            "gauss": totals.get("gauss.S", 0) + totals.get("gauss.St", 0)}
+    # where the step's time goes: the sketch products by operator, the adaptive run's sketches
+    # (S and S' of its first sketch and increments), and the rest (stopping tests, host)
+    step_ms = 1e3 * elapsed / args.steps
+    sketched = {"sjlt": cls["sjlt_rows"] + cls["sjlt_cols"], "srht": cls["srht"], "gauss": cls["gauss"],
+                "adaptive_sketches": totals.get("adaptive.apply", 0) + totals.get("adaptive.increment", 0)}
+    per_step = {k: v / args.steps for k, v in sketched.items()}
+    per_step["stopping_tests_and_host"] = max(0.0, step_ms - sum(per_step.values()))
+    step_share = {k: round(v / step_ms, 3) for k, v in per_step.items()}
     d_out_bytes = n * w["d"] * 4
     ccs_bytes = n * w["alpha"] * 2 + (n // 512) * (w["d"] + 4) * 4
     # the SJLT kernels are the ones the roofline tracks (HBM-bound, one pass of A)
@@ -351,11 +367,16 @@ def run_ours(args):
     traffic = None
     if prof:
         traffic = prof.get("cols_bytes_per_launch" if sj == "sjlt_cols" else "rows_bytes_per_launch")
-    roofline = {"kernel": "sjlt_cols_kernel (S' = A^T R)" if sj == "sjlt_cols" else "sjlt_rows_kernel (S = A R)",
+    tc_route = sjlt_routes["St" if sj == "sjlt_cols" else "S"] == 1
+    if tc_route:
+        kname = "tc_sketch_kernel (SJLT " + ("S' = A^T R" if sj == "sjlt_cols" else "S = A R") + ", +-1 product)"
+        traffic = None  # the profile's counters are of the SJLT kernels
+    else:
+        kname = "sjlt_cols_kernel (S' = A^T R)" if sj == "sjlt_cols" else "sjlt_rows_kernel (S = A R)"
+    roofline = {"kernel": kname,
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes}
-    step_share = {k: round(v / max(1e-9, sum(cls.values())), 3) for k, v in cls.items()}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * elapsed / args.steps, 3),

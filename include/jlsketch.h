@@ -597,6 +597,18 @@ int64_t sketch_launch_count(void);
  * diagnostic query; the paper has no counterpart. */
 int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int32_t prec);
 
+/* sketch_sjlt_route -- which route an SJLT product of FP32 data with
+ * SK_PREC_BF16X2 takes for a shape (kind, n = rows of R, A's rows and cols,
+ * the number of columns applied, which = SK_S or SK_ST): 1 the tensor-core
+ * +-1 product (R's {0, +-1} pattern is exact in bf16, A is split into bf16
+ * hi + lo), 0 the SJLT kernels (FP32 sums over R's entries), -1 not measured
+ * yet.  The first product of a shape times both routes on its stream (one
+ * synchronization) and keeps the faster; SK_PREC_NATIVE always takes the SJLT
+ * kernels.  JLS_SJLT_ROUTE=tc or =sjlt pins the route for the process (shapes
+ * served that way are not recorded, and report -1).  A diagnostic query; the
+ * paper has no counterpart. */
+int sketch_sjlt_route(int32_t kind, int64_t n, int64_t rows, int64_t cols, int32_t width, int32_t which);
+
 /* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */
 void sketch_destroy(sk_handle h);
 

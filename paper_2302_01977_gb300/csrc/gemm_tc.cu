@@ -499,10 +499,11 @@ int launch_tc(sk_op* h, const sk_matrix* A, bool trans, int c_lo, int c_hi, floa
 
 int dense_apply_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S, int64_t ldS,
                    void* St, int64_t ldSt, cudaStream_t s) {
-  if (A->dtype != SK_F32 || (h->kind != SK_SRHT && h->kind != SK_GAUSS)) return SK_ERR_DTYPE;
+  if (A->dtype != SK_F32) return SK_ERR_DTYPE;
   if (c_hi <= c_lo) return SK_OK;
   if (h->kind == SK_GAUSS) JLS_CHECK(gen_gauss(h, 2, h->d_total, s));
-  else JLS_CHECK(gen_srht_pm1(h, h->d_total, s));
+  else if (h->kind == SK_SRHT) JLS_CHECK(gen_srht_pm1(h, h->d_total, s));
+  else JLS_CHECK(gen_sjlt_pm1(h, h->d_total, s));  // SJLT: R's {0, +-1} pattern is exact in bf16
   if (which & SK_S) JLS_CHECK(launch_tc(h, A, false, c_lo, c_hi, (float)scale, (float*)S, ldS, s));
   if (which & SK_ST) JLS_CHECK(launch_tc(h, A, true, c_lo, c_hi, (float)scale, (float*)St, ldSt, s));
   return SK_OK;

@@ -188,6 +188,7 @@ int build_ccs_complex(sk_op* h, cudaStream_t s);  // ccs[2]: R (x) I_2
 int gen_srht(sk_op* h, int d_old, int d_new, cudaStream_t s);
 int gen_gauss(sk_op* h, int plane, int c_end, cudaStream_t s);  // plane: 0 f32, 1 f64, 2 bf16x2
 int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s);
+int gen_sjlt_pm1(sk_op* h, int c_end, cudaStream_t s);  // the SJLT's +-1 plane (tensor-core route)
 int gen_gauss_fp8(sk_op* h, int c_end, cudaStream_t s);
 int gen_srht_fp8(sk_op* h, int c_end, cudaStream_t s);
 int export_dense_R(sk_op* h, void* R_dev, int dtype, cudaStream_t s);

@@ -71,8 +71,10 @@ static int check_apply(const sk_op* h, const sk_matrix* A, int which, int prec, 
   if ((which & SK_S) && (A->cols != h->n || !S || ldS < h->d_total)) return SK_ERR_INVALID_ARG;
   if ((which & SK_ST) && (A->rows != h->n || !St || ldSt < h->d_total)) return SK_ERR_INVALID_ARG;
   if (prec != SK_PREC_NATIVE && prec != SK_PREC_BF16X2 && prec != SK_PREC_FP8) return SK_ERR_DTYPE;
-  if (prec != SK_PREC_NATIVE && ((A->dtype != SK_F32 && A->dtype != SK_C64) || (h->kind != SK_SRHT && h->kind != SK_GAUSS)))
-    return SK_ERR_DTYPE;
+  const bool sjlt = h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH;
+  if (prec != SK_PREC_NATIVE && A->dtype != SK_F32 && A->dtype != SK_C64) return SK_ERR_DTYPE;
+  if (prec == SK_PREC_FP8 && sjlt) return SK_ERR_DTYPE;  // SJLT: FP32 sums, or the bf16 split's +-1 product
+  if (prec == SK_PREC_BF16X2 && sjlt && A->dtype != SK_F32) return SK_ERR_DTYPE;
   if (A->dtype == SK_C64 && prec == SK_PREC_FP8) return SK_ERR_DTYPE;
   return SK_OK;
 }
@@ -148,8 +150,89 @@ static int srht_pick_fwht(sk_op* h, const sk_matrix* A, int prec, int c_lo, int 
   return SK_OK;
 }
 
+// SJLT products of FP32 data where the caller allows the bf16 split
+// (SK_PREC_BF16X2) have two routes: the SJLT kernels (FP32 sums over R's
+// entries) and the tensor-core +-1 product (R's {0, +-1} pattern exact in bf16,
+// A split into bf16 hi + lo).  The first product of a shape times both on the
+// caller's stream and the faster is kept; JLS_SJLT_ROUTE=tc|sjlt pins it.
+struct SjltPick {
+  int kind, which;
+  int64_t n, rows, cols;
+  int width;
+  bool tc;
+};
+static std::vector<SjltPick> g_sjlt_picks;
+
+static int sjlt_route_override() {
+  const char* e = std::getenv("JLS_SJLT_ROUTE");
+  if (!e) return -1;
+  if (!std::strcmp(e, "tc")) return 1;
+  if (!std::strcmp(e, "sjlt")) return 0;
+  return -1;
+}
+
+static int sjlt_one(sk_op* h, const sk_matrix* A, int which, bool tc, int c_lo, int c_hi, double scale, void* S,
+                    int64_t ldS, void* St, int64_t ldSt, cudaStream_t s) {
+  return tc ? dense_apply_tc(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s)
+            : sjlt_apply(h, A, which, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+}
+
+static int sjlt_pick_tc(sk_op* h, const sk_matrix* A, int which, int c_lo, int c_hi, double scale, void* S,
+                        int64_t ldS, void* St, int64_t ldSt, cudaStream_t s, bool* tc) {
+  const int forced = sjlt_route_override();
+  if (forced >= 0) {
+    *tc = forced == 1;
+    return SK_OK;
+  }
+  const SjltPick key{h->kind, which, h->n, A->rows, A->cols, c_hi - c_lo, false};
+  {
+    std::lock_guard<std::mutex> lock(g_pick_mu);
+    for (const SjltPick& p : g_sjlt_picks)
+      if (p.kind == key.kind && p.which == key.which && p.n == key.n && p.rows == key.rows && p.cols == key.cols &&
+          p.width == key.width) {
+        *tc = p.tc;
+        return SK_OK;
+      }
+  }
+  cudaEvent_t ev[3];
+  for (auto& e : ev) JLS_CHECK_CUDA(cudaEventCreate(&e));
+  int rc = SK_OK;
+  float t_t = 0.f, t_s = 0.f;
+  // warm both once (operator planes and tiles, attributes), then time one call of each
+  if ((rc = sjlt_one(h, A, which, true, c_lo, c_hi, scale, S, ldS, St, ldSt, s)) == SK_OK &&
+      (rc = sjlt_one(h, A, which, false, c_lo, c_hi, scale, S, ldS, St, ldSt, s)) == SK_OK) {
+    cudaEventRecord(ev[0], s);
+    rc = sjlt_one(h, A, which, true, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+    cudaEventRecord(ev[1], s);
+    if (rc == SK_OK) rc = sjlt_one(h, A, which, false, c_lo, c_hi, scale, S, ldS, St, ldSt, s);
+    cudaEventRecord(ev[2], s);
+    if (rc == SK_OK && cudaEventSynchronize(ev[2]) == cudaSuccess) {
+      cudaEventElapsedTime(&t_t, ev[0], ev[1]);
+      cudaEventElapsedTime(&t_s, ev[1], ev[2]);
+    } else if (rc == SK_OK) {
+      rc = cuda_status(cudaGetLastError());
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc != SK_OK) return rc;
+  *tc = t_t < t_s;
+  std::lock_guard<std::mutex> lock(g_pick_mu);
+  g_sjlt_picks.push_back({key.kind, key.which, key.n, key.rows, key.cols, key.width, *tc});
+  return SK_OK;
+}
+
 static int dispatch_range(sk_op* h, const sk_matrix* A, int which, int prec, int c_lo, int c_hi, double scale,
                           void* S, int64_t ldS, void* St, int64_t ldSt, cudaStream_t s) {
+  if ((h->kind == SK_SJLT_BLOCK || h->kind == SK_SJLT_GRAPH) && A->dtype == SK_F32 && prec == SK_PREC_BF16X2 &&
+      c_hi > c_lo) {
+    for (const int part : {SK_S, SK_ST}) {
+      if (!(which & part)) continue;
+      bool tc = false;
+      JLS_CHECK(sjlt_pick_tc(h, A, part, c_lo, c_hi, scale, S, ldS, St, ldSt, s, &tc));
+      JLS_CHECK(sjlt_one(h, A, part, tc, c_lo, c_hi, scale, S, ldS, St, ldSt, s));
+    }
+    return SK_OK;
+  }
   if (h->kind == SK_SRHT && (which & SK_S) && A->dtype == SK_F32 &&
       (prec == SK_PREC_NATIVE || prec == SK_PREC_BF16X2) && fwht_segments(h->nu) && c_hi > c_lo) {
     bool fwht = false;
@@ -549,6 +632,14 @@ int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int
   std::lock_guard<std::mutex> lock(g_pick_mu);
   for (const SrhtPick& p : g_picks)
     if (p.nu == nu && p.rows == rows && p.cols == cols && p.width == width && p.prec == prec) return p.fwht ? 1 : 0;
+  return -1;
+}
+
+int sketch_sjlt_route(int32_t kind, int64_t n, int64_t rows, int64_t cols, int32_t width, int32_t which) {
+  std::lock_guard<std::mutex> lock(g_pick_mu);
+  for (const SjltPick& p : g_sjlt_picks)
+    if (p.kind == kind && p.which == which && p.n == n && p.rows == rows && p.cols == cols && p.width == width)
+      return p.tc ? 1 : 0;
   return -1;
 }
 

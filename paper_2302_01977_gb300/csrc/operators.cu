@@ -484,6 +484,42 @@ int gen_srht_pm1(sk_op* h, int c_end, cudaStream_t s) {
   return SK_OK;
 }
 
+// SJLT sign plane for the tensor-core route: out[c][i] = +-1 (bf16) where row i
+// of R has an entry in column c, 0 elsewhere (exact in bf16; the scale is the
+// product's).  One thread per row of R for one block's entries.
+__global__ void sjlt_pm1_kernel(int64_t n, int alpha, const int32_t* __restrict__ ents, uint16_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < alpha; ++k) {
+    const int32_t e = ents[i * alpha + k];
+    out[(int64_t)(e & 0x7fffffff) * bf_pitch(n) + i] = e < 0 ? (uint16_t)0xBF80 : (uint16_t)0x3F80;
+  }
+}
+
+// The SJLT's +-1 plane up to column c_end (whole blocks; kept in the handle's
+// +-1 plane buffer, which SJLT operators do not otherwise use).
+int gen_sjlt_pm1(sk_op* h, int c_end, cudaStream_t s) {
+  const size_t pitch_b = (size_t)bf_pitch(h->n) * sizeof(uint16_t);
+  if (!h->srht_pm1) JLS_CHECK_CUDA(cudaMalloc(&h->srht_pm1, (size_t)h->d_max * pitch_b));
+  if (h->pm1_cols >= c_end) return SK_OK;
+  int b0 = 0;
+  for (size_t b = 0; b < h->blocks.size(); ++b) {
+    const int w = h->blocks[b];
+    if (b0 >= h->pm1_cols && b0 < c_end) {
+      JLS_CHECK_CUDA(cudaMemsetAsync(reinterpret_cast<uint8_t*>(h->srht_pm1) + (size_t)b0 * pitch_b, 0,
+                                     (size_t)w * pitch_b, s));
+      sjlt_pm1_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, s>>>(h->n, h->alpha,
+                                                                     h->sjlt_ents + (size_t)b * h->n * h->alpha,
+                                                                     h->srht_pm1);
+      note_launch();
+      JLS_CHECK_CUDA(cudaGetLastError());
+    }
+    b0 += w;
+  }
+  h->pm1_cols = std::max(h->pm1_cols, std::min(c_end, b0));
+  return SK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // FP8 planes.  Gaussian: one CTA of 128 threads per (K tile of 128, column c)
 // draws the tile's FP32 z (as for the FP32 plane), takes its amax, and writes

@@ -48,7 +48,7 @@ SK_SRHT_REPLACE = 2
 
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
-EXPORTS = ["sketch_create", "sketch_create_flags", "sketch_increment", "sketch_apply", "sketch_apply_increment",
+EXPORTS = ["sketch_create", "sketch_create_flags", "sketch_sjlt_route", "sketch_increment", "sketch_apply", "sketch_apply_increment",
            "adaptive_norm_test", "adaptive_norm_test_pair", "sketch_project_norms_noalloc", "kernel_matrix", "sketch_kernel_apply",
            "sketch_kernel_adjoint", "sketch_batch_create", "sketch_batch_set", "sketch_batch_run",
            "sketch_batch_tune", "sketch_batch_adaptive_setup", "sketch_batch_adaptive_run",
@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
         "sketch_device_status": (i32, [vp, vp]),
         "sketch_launch_count": (i64, []),
         "sketch_srht_route": (i32, [i64, i64, i64, i32, i32]),
+        "sketch_sjlt_route": (i32, [i32, i64, i64, i64, i32, i32]),
         "sketch_destroy": (None, [vp]),
         "sketch_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -591,6 +592,12 @@ def sketch_launch_count() -> int:
 def sketch_srht_route(nu: int, rows: int, cols: int, width: int, prec: int) -> int:
     """1: row FWHT, 0: +-1 product, -1: shape not measured yet (SRHT S = A R)."""
     return int(lib().sketch_srht_route(int(nu), int(rows), int(cols), int(width), int(prec)))
+
+
+def sketch_sjlt_route(kind, n: int, rows: int, cols: int, width: int, which: int) -> int:
+    """1 tensor-core +-1 product, 0 SJLT kernels, -1 not measured (SK_PREC_BF16X2 products of FP32 data)."""
+    k = KIND_NAMES.get(kind, kind) if isinstance(kind, str) else int(kind)
+    return int(lib().sketch_sjlt_route(k, int(n), int(rows), int(cols), int(width), int(which)))
 
 
 def sketch_destroy(h) -> None:

@@ -132,7 +132,7 @@ def test_tc_deterministic():
     assert np.array_equal(g1, g2)
 
 
-def test_tc_rejects_fp64_and_sjlt():
+def test_tc_rejects_fp64_and_sjlt_fp8():
     jl = jlmod()
     A = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
     S = torch.zeros((64, 16), dtype=torch.float64, device="cuda")
@@ -148,10 +148,47 @@ def test_tc_rejects_fp64_and_sjlt():
     h = jl.sketch_create("sjlt_block", 64, 16, 4, 1, 16)
     try:
         with pytest.raises(jl.JLSketchError) as e:
-            jl.sketch_apply(h, A32, which=jl.SK_S, prec=jl.SK_PREC_BF16X2, S=S32)
+            jl.sketch_apply(h, A32, which=jl.SK_S, prec=jl.SK_PREC_FP8, S=S32)
         assert e.value.status == jl.SK_ERR_DTYPE
     finally:
         jl.sketch_destroy(h)
+
+
+@pytest.mark.parametrize("route", ["tc", "sjlt", "pick"])
+@pytest.mark.parametrize("kind,alpha", [("sjlt_block", 4), ("sjlt_graph", 3)])
+def test_sjlt_bf16x2_routes(kind, alpha, route, monkeypatch):
+    """SJLT products with SK_PREC_BF16X2 through the tensor-core +-1 product
+    (R's {0, +-1} plane exact in bf16, A split hi + lo), the SJLT kernels, or
+    whichever measures faster, with an increment: S and S' against the FP64
+    oracle (1e-5 relative Frobenius; each term of the split within 2.5e-4 of
+    |A||R| elementwise)."""
+    jl = jlmod()
+    if route != "pick":
+        monkeypatch.setenv("JLS_SJLT_ROUTE", route)
+    m, n, d, dd = 900, 1500, 96, 32
+    A_np = inputs.dense_matrix(m, n, seed=31).astype(np.float32)
+    A = dev_padded(A_np, torch.float32)
+    Ae = host(A).astype(np.float64)
+    for which, rows_r in ((jl.SK_S, n), (jl.SK_ST, m)):
+        h = jl.sketch_create(kind, rows_r, d, alpha, 41, d + dd)
+        try:
+            out_rows = m if which == jl.SK_S else n
+            O = torch.full((out_rows, d + dd), np.nan, dtype=torch.float32, device="cuda")
+            kw = {"S": O} if which == jl.SK_S else {"St": O}
+            jl.sketch_apply(h, A, which=which, prec=jl.SK_PREC_BF16X2, **kw)
+            jl.sketch_increment(h, dd)
+            jl.sketch_apply_increment(h, A, which=which, prec=jl.SK_PREC_BF16X2, **kw)
+            jl.sketch_device_status(h)
+        finally:
+            jl.sketch_destroy(h)
+        op = ops.Operator(kind, rows_r, d, alpha, 41)
+        op.increment(dd)
+        R = op.dense()
+        want = Ae @ R if which == jl.SK_S else Ae.T @ R
+        got = host(O).astype(np.float64)
+        assert rel_fro(got, want) <= TOL["bf16x2"]
+        bound = (np.abs(Ae) @ np.abs(R)) if which == jl.SK_S else (np.abs(Ae).T @ np.abs(R))
+        assert np.all(np.abs(got - want) <= ELEM_BOUND * bound + 1e-30)
 
 
 @pytest.mark.parametrize("kind", ["srht", "gauss"])
