@@ -87,6 +87,23 @@ def spectrum_matrix(n: int, sigma: np.ndarray, seed: int, dtype=np.float64) -> n
     return np.ascontiguousarray(((u * sigma) @ v.T).astype(dtype))
 
 
+def hss_test_matrix(n: int, leaf: int, rank: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Symmetric n x n matrix blockdiag(D_1, ..., D_b) + U C U^T with dense
+    symmetric diagonal blocks of ``leaf`` rows (the last one ragged), U n x rank
+    and C rank x rank symmetric, all N(0,1): every off-diagonal block of any
+    contiguous row range has rank <= ``rank``."""
+    g = _rng(seed)
+    A = np.zeros((n, n))
+    for lo in range(0, n, leaf):
+        hi = min(n, lo + leaf)
+        b = g.standard_normal((hi - lo, hi - lo))
+        A[lo:hi, lo:hi] = b + b.T
+    u = g.standard_normal((n, rank))
+    c = g.standard_normal((rank, rank))
+    A += u @ (c + c.T) @ u.T / n
+    return np.ascontiguousarray(A.astype(dtype))
+
+
 # --- workload descriptors -------------------------------------------------
 # The five workloads, by what they are.  Sizes are the full ones; tests shrink
 # them where the oracle has to finish in seconds.
