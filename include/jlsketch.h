@@ -609,6 +609,88 @@ int sketch_srht_route(int64_t nu, int64_t rows, int64_t cols, int32_t width, int
  * paper has no counterpart. */
 int sketch_sjlt_route(int32_t kind, int64_t n, int64_t rows, int64_t cols, int32_t width, int32_t which);
 
+/* ---- per-node adaptive HSS compression (Algorithm 1) -------------------- */
+/*
+ * hss_compress_adaptive -- Algorithm 1 (HSSCompressAdaptive, Supplementary D)
+ * for a symmetric A: compress every node of a binary cluster tree from one
+ * growing global sketch S = A R.
+ *   Tree: node [lo, hi) with more than `leaf` indices splits into
+ *   [lo, lo + (hi-lo)/2) and the rest; level(root) = 0.
+ *   Per node tau, visited level by level from the leaves (the nodes of a
+ *   level together):
+ *     leaf      S_tau(:, iota) = S(I_tau, iota) - D_tau R(I_tau, iota), D_tau = A(I_tau, I_tau)
+ *     internal  S_tau(:, iota) = [S_nu1(J_nu1, iota) - B_tau R_nu2(:, iota);
+ *                                 S_nu2(J_nu2, iota) - B_tau^T R_nu1(:, iota)],
+ *               B_tau = A(I~_nu1, I~_nu2)
+ *     (iota = all d + Delta-d columns on the first visit, the new Delta-d later);
+ *     a node not yet compressed takes the test of Eq. (3.1) with
+ *     eps^tau = eps / level(tau): S~ = its last Delta-d columns,
+ *     S^ = (I - Q Q^T)^2 S~ against a basis Q of the earlier columns' range;
+ *     passed, or min |diag Om^| of {Q^, Om^} = QR(S^) below eps_abs^tau or
+ *     eps_rel^tau |(Om_tau)_11| (the rank-deficiency test): compress by the row
+ *     interpolative decomposition S_tau ~ U_tau S_tau(J_tau, :) (column-pivoted
+ *     QR of S_tau^T, rank = pivots above eps_abs^tau and eps_rel^tau |R_11|),
+ *     R_tau = U_tau^T R(I_tau) or U_tau^T [R_nu1; R_nu2],
+ *     I~_tau = I_tau(J_tau) or [I~_nu1, I~_nu2](J_tau).
+ *     Otherwise the sweep ends after this level, R grows by Delta-d columns
+ *     (each block keeps its own scale, SK_SCALE_BLOCK), S <- [S  A R_bar],
+ *     d <- d + Delta-d, and the next sweep starts from the leaves; the loop
+ *     also ends, unconverged, when R would exceed d_max columns.
+ *   A      device, n x n FP64, row-major, symmetric (not checked), 16-byte
+ *          aligned, lda >= n with lda * 8 % 16 == 0.  Read during the call
+ *          only (D and B are copied).
+ *   leaf   1 .. 4096; kind, alpha, seed as sketch_create; d0, dd >= 1 with
+ *          d0 + dd <= d_max <= 2048, d_max even.
+ *   eps_rel, eps_abs >= 0: the tolerances before the level division.
+ * Every step runs on the device in FP64; the host reads each level's
+ * outcomes and ranks (it synchronizes `stream` a few times per level).
+ * Out: *out owns the generators until hss_destroy.  Errors: INVALID_ARG,
+ * ALIGN, UNSUPPORTED (a local sketch of more than 4096 rows), NOMEM, DEVICE.
+ */
+typedef struct sk_hss* sk_hss_handle;
+int hss_compress_adaptive(sk_hss_handle* out, const double* A, int64_t n, int64_t lda, int32_t leaf,
+                          int32_t kind, int32_t d0, int32_t dd, int32_t alpha, uint64_t seed, int32_t d_max,
+                          double eps_rel, double eps_abs, void* stream);
+
+/* hss_info -- host outputs (each may be NULL): node count, final d, columns
+ * of R, sweeps run, converged (1: the root was reached), stopping tests run. */
+int hss_info(sk_hss_handle h, int32_t* nodes, int32_t* d, int32_t* d_total, int32_t* sweeps,
+             int32_t* converged, int32_t* tests);
+
+/* hss_node -- node `node` (0 = root, preorder): lohi[2] = {lo, hi} and
+ * info[7] = {level, parent, child 1, child 2 (-1: none), state (0 untouched,
+ * 1 partially compressed, 2 compressed), m = rows of S_tau, k = rank}. */
+int hss_node(sk_hss_handle h, int32_t node, int64_t* lohi, int32_t* info);
+
+/* hss_node_get -- copy one generator of a node to host memory `dst`:
+ *   SK_HSS_U   U_tau, m x k FP64 column-major     SK_HSS_J   J_tau, k int32 (0-based rows of S_tau)
+ *   SK_HSS_IT  I~_tau, k int32 (rows of A)        SK_HSS_D   D_tau (leaf), m x m FP64 column-major
+ *   SK_HSS_B   B_tau (internal, root), k_nu1 x k_nu2 FP64 column-major
+ *   SK_HSS_S   S_tau, m x (d + Delta-d) FP64 column-major
+ *   SK_HSS_R   R_tau, k x (d + Delta-d) FP64 column-major
+ * Synchronous.  Errors: INVALID_ARG, STATE (not computed for this node). */
+#define SK_HSS_U  1
+#define SK_HSS_J  2
+#define SK_HSS_IT 3
+#define SK_HSS_D  4
+#define SK_HSS_B  5
+#define SK_HSS_S  6
+#define SK_HSS_R  7
+int hss_node_get(sk_hss_handle h, int32_t node, int32_t what, void* dst);
+
+/* hss_history -- the stopping tests in the order run: ints[4 t] = {sweep,
+ * level, node, outcome (0 passed Eq. (3.1), 1 compressed by the rank test,
+ * 2 needs more columns)}, reals[3 t] = {||S^||_F, ||S~||_F, min |diag Om^|
+ * (0 when not computed)}; host arrays of hss_info's `tests` records. */
+int hss_history(sk_hss_handle h, int32_t* ints, double* reals);
+
+/* hss_launch_count -- kernels the handle launched (the sketch kernels of S
+ * excluded). */
+int64_t hss_launch_count(sk_hss_handle h);
+
+/* hss_destroy -- free the generators and scratch (NULL is a no-op). */
+void hss_destroy(sk_hss_handle h);
+
 /* sketch_destroy -- free the handle and its device memory (NULL is a no-op). */
 void sketch_destroy(sk_handle h);
 

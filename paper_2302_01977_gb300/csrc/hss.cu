@@ -1,0 +1,970 @@
+// hss.cu -- the per-node adaptive loop of Algorithm 1 (HSSCompressAdaptive,
+// Supplementary D) on the device, in FP64, for a symmetric explicit A.
+//
+// The nodes of one level of the cluster tree are processed together (the
+// leaves of the walk-through are compressed in parallel): one launch computes
+// every local sketch of the level, one launch runs every node's stopping and
+// rank-deficiency tests, one launch the interpolative decompositions of the
+// nodes that compress, one launch their R_tau columns.  The host reads each
+// level's outcomes (a few bytes) to decide the next launch; a node that needs
+// more columns ends the sweep after its level, R grows by Delta-d columns
+// (S <- [S  A R_bar] by the sketch kernels) and the next sweep starts again
+// from the leaves.
+//
+// Per node tau (m rows of the local sketch, k = rank after compression):
+//   S_tau  m x d_max, column-major          local sketch (leaf: S(I, iota) - D R(I, iota);
+//                                            internal: [S_nu1(J_nu1) - B R_nu2; S_nu2(J_nu2) - B^T R_nu1])
+//   Q_tau  m x (min(m, d_max) + Delta-d)    orthonormal basis of the tested columns' range
+//   U_tau  m x k, column-major              row interpolative decomposition S_tau ~ U_tau S_tau(J_tau, :)
+//   J_tau  k positions in 0..m-1;  I~_tau  k global indices
+//   R_tau  k x d_max, column-major          U_tau^T R(I_tau) (leaf) or U_tau^T [R_nu1; R_nu2]
+//   D_tau  (leaf) m x m, B_tau (internal, root) k_nu1 x k_nu2, column-major, copied from A
+//
+// All FP64: the local sketch is a difference of two large terms (S(I, :)
+// holds the diagonal block's product), and the tests and the decomposition
+// resolve eps / level(tau) relative to it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace jls {
+namespace {
+
+constexpr int HSS_MAX_ROWS = 4096;  // rows of a node's local sketch (a column lives in shared memory)
+constexpr int HSS_MAX_D = 2048;     // columns of R
+constexpr int HT = 256;             // threads of the per-node kernels
+constexpr int GT = 64;              // GEMM tile (rows and columns of the output)
+constexpr int GK = 16;              // GEMM tile depth
+
+// ---- operands of the batched GEMM jobs -------------------------------------
+// Element (r, c) of an operand: rows [0, split) come from p (row r -> idx[r]
+// when idx is set), rows [split, ...) from p2 the same way, at
+// base[row * rs + c * cs].
+struct Opnd {
+  const double* p = nullptr;
+  int64_t rs = 0, cs = 0;
+  const int32_t* idx = nullptr;
+  int32_t split = 1 << 30;
+  const double* p2 = nullptr;
+  int64_t rs2 = 0, cs2 = 0;
+  const int32_t* idx2 = nullptr;
+};
+
+__device__ __forceinline__ double opnd_at(const Opnd& o, int r, int c) {
+  if (r < o.split) {
+    const int64_t rr = o.idx ? o.idx[r] : r;
+    return o.p[rr * o.rs + (int64_t)c * o.cs];
+  }
+  r -= o.split;
+  const int64_t rr = o.idx2 ? o.idx2[r] : r;
+  return o.p2[rr * o.rs2 + (int64_t)c * o.cs2];
+}
+
+// out(r, c) = [c_in(r, c)] + alpha * sum_k a(r, k) b(k, c), r < M, c < N.
+struct GemmJob {
+  Opnd a, b, c;
+  double* out = nullptr;
+  int64_t ors = 1, ocs = 0;
+  int32_t M = 0, N = 0, K = 0;
+  int32_t has_c = 0;
+  double alpha = 1.0;
+  int32_t tile0 = 0, tiles_n = 0;
+};
+
+// One 64 x 64 output tile per CTA; 256 threads, 4 x 4 outputs each.
+__global__ void __launch_bounds__(256) hss_gemm_kernel(const GemmJob* __restrict__ jobs, int njobs) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const int tile = blockIdx.x;
+  int lo = 0, hi = njobs - 1;  // last job with tile0 <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  const GemmJob& J = jobs[lo];
+  const int t = tile - J.tile0;
+  const int m0 = (t / J.tiles_n) * GT, n0 = (t % J.tiles_n) * GT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < J.K; k0 += GK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int kk = e / GT, mm = e % GT;
+      const int r = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (r < J.M && k < J.K) ? opnd_at(J.a, r, k) : 0.0;
+      const int cc = n0 + mm;
+      Bs[kk][mm] = (cc < J.N && k < J.K) ? opnd_at(J.b, k, cc) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = m0 + ty * 4 + i;
+    if (r >= J.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + tx * 4 + j;
+      if (c >= J.N) continue;
+      double v = J.alpha * acc[i][j];
+      if (J.has_c) v += opnd_at(J.c, r, c);
+      J.out[(int64_t)r * J.ors + (int64_t)c * J.ocs] = v;
+    }
+  }
+}
+
+// ---- gathers of A's entries: out(r, c) = A(row(r), col(c)), column-major ---
+struct GatherJob {
+  double* out = nullptr;
+  int32_t rows = 0, cols = 0;
+  const int32_t* ri = nullptr;  // global row indices, or rows r0 + r
+  const int32_t* ci = nullptr;
+  int64_t r0 = 0, c0 = 0;
+};
+
+__global__ void hss_gather_kernel(const GatherJob* __restrict__ jobs, const double* __restrict__ A, int64_t lda) {
+  const GatherJob& J = jobs[blockIdx.x];
+  const int64_t total = (int64_t)J.rows * J.cols;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = (int)(e % J.rows), c = (int)(e / J.rows);
+    const int64_t gr = J.ri ? J.ri[r] : J.r0 + r;
+    const int64_t gc = J.ci ? J.ci[c] : J.c0 + c;
+    J.out[e] = A[gr * lda + gc];
+  }
+}
+
+// ---- block reductions ---------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result.  red: >= 33 doubles.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double x = l < (int)(blockDim.x / 32) ? red[l] : 0.0;
+    x = warp_sum(x);
+    if (l == 0) red[32] = x;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// w <- (I - Q Q^T)^2 w for the columns [c_lo, c_hi) of Q (m x ldQ column-major);
+// w and h (>= c_hi - c_lo doubles) in shared memory.
+__device__ void project2(const double* __restrict__ Q, int64_t ldQ, int m, int c_lo, int c_hi, double* w,
+                         double* h) {
+  const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = c_lo + wid; j < c_hi; j += nw) {
+      const double* q = Q + (int64_t)j * ldQ;
+      double s = 0.0;
+      for (int i = lane; i < m; i += 32) s = fma(q[i], w[i], s);
+      s = warp_sum(s);
+      if (lane == 0) h[j - c_lo] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = c_lo; j < c_hi; ++j) s = fma(Q[(int64_t)j * ldQ + i], h[j - c_lo], s);
+      w[i] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- per-node stopping and rank-deficiency tests ----------------------------
+struct TestJob {
+  const double* S = nullptr;  // local sketch, m x ..., column-major, ld = m
+  double* Q = nullptr;        // basis, ld = m
+  int32_t m = 0, d = 0, dd = 0;
+  int32_t q = -1;             // basis columns so far; -1: build it from S(:, 0:d)
+  int32_t qcap = 0;           // columns Q can hold
+  double er = 0, ea = 0;
+  double om11 = 0;            // |(Omega_tau)_11| once the basis exists
+};
+struct TestOut {
+  double nh, nt, mind, om11;
+  int32_t q, outcome;         // outcome: 0 passed (Eq. (3.1)), 1 rank-deficient, 2 needs more columns
+};
+
+__global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict__ jobs, TestOut* __restrict__ outs) {
+  extern __shared__ double sm[];
+  const TestJob J = jobs[blockIdx.x];
+  const int m = J.m;
+  double* w = sm;                       // m
+  double* h = sm + HSS_MAX_ROWS;        // projection coefficients
+  double* red = h + HSS_MAX_D + 128;    // 33
+  int q = J.q;
+  double om11 = J.om11;
+  if (q < 0) {
+    // Q_tau: orthonormal basis of the range of S_tau(:, 0:d), columns kept
+    // above max(m, d) eps ||S_tau(:, 0:d)||_F (two Gram-Schmidt passes each)
+    double f2 = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * J.d; e += blockDim.x) f2 = fma(J.S[e], J.S[e], f2);
+    f2 = block_sum(f2, red);
+    const double thr = (double)max(m, J.d) * 2.220446049250313e-16 * sqrt(f2);
+    q = 0;
+    for (int j = 0; j < J.d; ++j) {
+      double c2 = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double v = J.S[(int64_t)j * m + i];
+        w[i] = v;
+        c2 = fma(v, v, c2);
+      }
+      c2 = block_sum(c2, red);
+      if (j == 0) om11 = sqrt(c2);
+      if (q > 0) project2(J.Q, m, m, 0, q, w, h);
+      double r2 = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) r2 = fma(w[i], w[i], r2);
+      r2 = block_sum(r2, red);
+      const double r = sqrt(r2);
+      if (r > thr && r > 0.0) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) J.Q[(int64_t)q * m + i] = w[i] / r;
+        ++q;
+      }
+      __syncthreads();
+    }
+  }
+  if (q + J.dd > J.qcap) {
+    // more basis columns than Q holds: only when q = m (the basis spans all
+    // of R^m and S^ = 0); counted as passed with ||S^|| = 0
+    if (threadIdx.x == 0) {
+      TestOut o;
+      o.nh = 0.0; o.nt = 0.0; o.mind = 0.0; o.om11 = om11; o.q = q; o.outcome = 0;
+      outs[blockIdx.x] = o;
+    }
+    return;
+  }
+  // S~ = S_tau(:, d : d + dd), S^ = (I - Q Q^T)^2 S~ into Q(:, q : q + dd)
+  double nt2 = 0.0, nh2 = 0.0;
+  for (int jj = 0; jj < J.dd; ++jj) {
+    double c2 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = J.S[(int64_t)(J.d + jj) * m + i];
+      w[i] = v;
+      c2 = fma(v, v, c2);
+    }
+    nt2 += block_sum(c2, red);
+    if (q > 0) project2(J.Q, m, m, 0, q, w, h);
+    double r2 = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      r2 = fma(w[i], w[i], r2);
+      J.Q[(int64_t)(q + jj) * m + i] = w[i];
+    }
+    nh2 += block_sum(r2, red);
+  }
+  const double nh = sqrt(nh2), nt = sqrt(nt2);
+  int outcome = 0;
+  double mind = 0.0;
+  if (!(nt == 0.0 || nh < J.ea || nh < J.er * nt)) {
+    // {Q^, Om^} = QR(S^) column by column; |diag Om^| = the residual norms
+    mind = INFINITY;
+    for (int jj = 0; jj < J.dd; ++jj) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = J.Q[(int64_t)(q + jj) * m + i];
+      __syncthreads();
+      if (jj > 0) project2(J.Q, m, m, q, q + jj, w, h);
+      double r2 = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) r2 = fma(w[i], w[i], r2);
+      const double r = sqrt(block_sum(r2, red));
+      mind = fmin(mind, r);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) J.Q[(int64_t)(q + jj) * m + i] = r > 0.0 ? w[i] / r : 0.0;
+      __syncthreads();
+    }
+    if (mind < J.ea || mind < J.er * om11) {
+      outcome = 1;
+    } else {
+      outcome = 2;
+      q += J.dd;
+    }
+  }
+  if (threadIdx.x == 0) {
+    TestOut o;
+    o.nh = nh; o.nt = nt; o.mind = mind; o.om11 = om11; o.q = q; o.outcome = outcome;
+    outs[blockIdx.x] = o;
+  }
+}
+
+// ---- row interpolative decomposition S ~ U S(J, :) --------------------------
+// Column-pivoted QR of S^T by modified Gram-Schmidt on the rows of S: the
+// pivot is the remaining row of largest partial norm (the lowest index on a
+// tie); the partial norms are summed afresh in each update pass (no
+// downdating); rank k = the pivots whose norm exceeds eps_a and
+// eps_r |R_11|; U^T = [I, R11^{-1} R12] P^T.
+struct IdJob {
+  const double* S = nullptr;  // m x C, column-major, ld = m
+  int32_t m = 0, C = 0;
+  double er = 0, ea = 0;
+  double* W = nullptr;        // m x C scratch
+  double* Rf = nullptr;       // min(m, C) x m scratch
+  double* nrm = nullptr;      // m scratch: partial norms
+  double* U = nullptr;        // m x min(m, C) output, ld = m
+  int32_t* Jl = nullptr;      // local pivots
+  int32_t* It = nullptr;      // global skeleton indices
+  int64_t lo = 0;             // leaf: I_tau = lo + [0, m)
+  const int32_t* It1 = nullptr;  // internal: [I~_nu1, I~_nu2]
+  const int32_t* It2 = nullptr;
+  int32_t k1 = 0;
+};
+
+__global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jobs, int32_t* __restrict__ ranks) {
+  extern __shared__ double sm[];
+  const IdJob J = jobs[blockIdx.x];
+  const int m = J.m, C = J.C, kmax = min(m, C);
+  double* qv = sm;                                   // C
+  double* red = qv + HSS_MAX_D + 128;                // 33
+  int* perm = reinterpret_cast<int*>(red + 40);      // m (pivot order), then m used flags
+  int* used = perm + HSS_MAX_ROWS;
+  __shared__ int s_idx[32];
+  __shared__ int s_arg;
+  double* nrm = J.nrm;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < C; ++c) {
+      const double v = J.S[(int64_t)c * m + i];
+      J.W[(int64_t)c * m + i] = v;
+      s = fma(v, v, s);
+    }
+    nrm[i] = s;
+    used[i] = 0;
+  }
+  __syncthreads();
+  int k = 0;
+  double r11 = 0.0;
+  for (int t = 0; t < kmax; ++t) {
+    // pivot: the largest partial norm among unused rows, lowest index on ties
+    double bv = -1.0;
+    int bi = m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      if (!used[i] && nrm[i] > bv) { bv = nrm[i]; bi = i; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+    __syncthreads();
+    if (lane == 0) { red[wid] = bv; s_idx[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int a = m;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+        const double v = red[w];
+        const int ai = s_idx[w];
+        if (v > b || (v == b && ai < a)) { b = v; a = ai; }
+      }
+      s_arg = a;
+    }
+    __syncthreads();
+    const int p = s_arg;
+    if (p >= m) break;
+    // exact norm of the pivot row
+    double s = 0.0;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      const double v = J.W[(int64_t)c * m + p];
+      qv[c] = v;
+      s = fma(v, v, s);
+    }
+    const double rpp = sqrt(block_sum(s, red));
+    if (t == 0) r11 = rpp;
+    if (!(rpp > J.ea) || !(rpp > J.er * r11)) break;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) qv[c] /= rpp;
+    if (threadIdx.x == 0) {
+      used[p] = 1;
+      perm[t] = p;
+      J.Rf[(int64_t)t * m + p] = rpp;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      if (used[i]) continue;
+      double r = 0.0;
+      for (int c = 0; c < C; ++c) r = fma(J.W[(int64_t)c * m + i], qv[c], r);
+      double n2 = 0.0;
+      for (int c = 0; c < C; ++c) {
+        const double v = fma(-r, qv[c], J.W[(int64_t)c * m + i]);
+        J.W[(int64_t)c * m + i] = v;
+        n2 = fma(v, v, n2);
+      }
+      J.Rf[(int64_t)t * m + i] = r;
+      nrm[i] = n2;
+    }
+    k = t + 1;
+    __syncthreads();
+  }
+  // U: identity rows at the pivots, X = R11^{-1} R12 elsewhere
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    if (used[i]) {
+      for (int s2 = 0; s2 < k; ++s2) J.U[(int64_t)s2 * m + i] = 0.0;
+      continue;
+    }
+    for (int s2 = k - 1; s2 >= 0; --s2) {
+      double b = J.Rf[(int64_t)s2 * m + i];
+      for (int t = s2 + 1; t < k; ++t) b -= J.Rf[(int64_t)s2 * m + perm[t]] * J.U[(int64_t)t * m + i];
+      J.U[(int64_t)s2 * m + i] = b / J.Rf[(int64_t)s2 * m + perm[s2]];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    const int p = perm[t];
+    J.U[(int64_t)t * m + p] = 1.0;
+    J.Jl[t] = p;
+    J.It[t] = J.It1 ? (p < J.k1 ? J.It1[p] : J.It2[p - J.k1]) : (int32_t)(J.lo + p);
+  }
+  if (threadIdx.x == 0) ranks[blockIdx.x] = k;
+}
+
+size_t test_smem() { return sizeof(double) * (HSS_MAX_ROWS + HSS_MAX_D + 128 + 40); }
+size_t id_smem() { return sizeof(double) * (HSS_MAX_D + 128 + 40) + sizeof(int) * 2 * HSS_MAX_ROWS; }
+
+}  // namespace
+}  // namespace jls
+
+using namespace jls;
+
+namespace {
+
+enum { UNTOUCHED = 0, PARTIAL = 1, COMPRESSED = 2 };
+
+struct HssNode {
+  int64_t lo = 0, hi = 0;
+  int level = 0, parent = -1, c1 = -1, c2 = -1;
+  int state = UNTOUCHED;
+  int m = 0, q = -1, k = 0, qcap = 0;
+  double om11 = 0.0;
+  double *S = nullptr, *Q = nullptr, *U = nullptr, *R = nullptr, *B = nullptr, *D = nullptr;
+  int32_t *J = nullptr, *It = nullptr;
+};
+
+struct HssRecord {
+  int32_t sweep, level, node, outcome;
+  double nh, nt, mind;
+};
+
+// Device memory in chunks with a bump pointer (256-byte aligned pieces).
+struct Arena {
+  std::vector<void*> chunks;
+  char* cur = nullptr;
+  size_t left = 0;
+  int take(size_t bytes, void** out) {
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes == 0) bytes = 256;
+    if (bytes > left) {
+      const size_t sz = std::max(bytes, (size_t)256 << 20);
+      void* p = nullptr;
+      if (cudaMalloc(&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return SK_ERR_NOMEM;
+      }
+      chunks.push_back(p);
+      cur = static_cast<char*>(p);
+      left = sz;
+    }
+    *out = cur;
+    cur += bytes;
+    left -= bytes;
+    return SK_OK;
+  }
+  void release() {
+    for (void* p : chunks) cudaFree(p);
+    chunks.clear();
+    cur = nullptr;
+    left = 0;
+  }
+};
+
+template <class T>
+int take(Arena& a, size_t count, T** out) {
+  void* p = nullptr;
+  JLS_CHECK(a.take(count * sizeof(T), &p));
+  *out = static_cast<T*>(p);
+  return SK_OK;
+}
+
+}  // namespace
+
+struct sk_hss {
+  int64_t n = 0, lda = 0;
+  const double* A = nullptr;
+  int leaf = 0, kind = 0, alpha = 1, d0 = 0, dd = 0, d_max = 0;
+  double eps_rel = 0, eps_abs = 0;
+  sk_handle op = nullptr;
+  std::vector<HssNode> nodes;                 // preorder; node 0 is the root
+  std::vector<std::vector<int>> levels;
+  std::vector<HssRecord> history;
+  int d = 0, sweeps = 0, converged = 0;
+  Arena arena;       // per-node generators
+  Arena scratch;     // per-level decomposition scratch, released after each level
+  double* S = nullptr;   // n x d_max, row-major
+  double* Rd = nullptr;  // n x d_total, row-major (exported after each increment)
+  void* jobs_dev = nullptr;
+  size_t jobs_cap = 0;
+  void* host_pin = nullptr;
+  size_t host_cap = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+int ensure_jobs(sk_hss* H, size_t bytes) {
+  if (bytes <= H->jobs_cap) return SK_OK;
+  if (H->jobs_dev) cudaFree(H->jobs_dev);
+  H->jobs_dev = nullptr;
+  H->jobs_cap = 0;
+  const size_t cap = std::max(bytes, (size_t)1 << 16);
+  JLS_CHECK_CUDA(cudaMalloc(&H->jobs_dev, cap));
+  H->jobs_cap = cap;
+  return SK_OK;
+}
+
+int ensure_pinned(sk_hss* H, size_t bytes) {
+  if (bytes <= H->host_cap) return SK_OK;
+  if (H->host_pin) cudaFreeHost(H->host_pin);
+  H->host_pin = nullptr;
+  H->host_cap = 0;
+  const size_t cap = std::max(bytes, (size_t)1 << 16);
+  JLS_CHECK_CUDA(cudaMallocHost(&H->host_pin, cap));
+  H->host_cap = cap;
+  return SK_OK;
+}
+
+// Copy a job array to the device (through pinned memory; the stream is
+// synchronized before the pinned buffer is reused).
+template <class T>
+int upload(sk_hss* H, const std::vector<T>& v, cudaStream_t s) {
+  const size_t bytes = v.size() * sizeof(T);
+  JLS_CHECK(ensure_jobs(H, bytes));
+  JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+  JLS_CHECK(ensure_pinned(H, bytes));
+  std::memcpy(H->host_pin, v.data(), bytes);
+  JLS_CHECK_CUDA(cudaMemcpyAsync(H->jobs_dev, H->host_pin, bytes, cudaMemcpyHostToDevice, s));
+  return SK_OK;
+}
+
+int run_gemms(sk_hss* H, std::vector<GemmJob>& jobs, cudaStream_t s) {
+  std::vector<GemmJob> live;
+  int tiles = 0;
+  for (GemmJob j : jobs) {
+    if (j.M <= 0 || j.N <= 0) continue;
+    j.tiles_n = (j.N + GT - 1) / GT;
+    j.tile0 = tiles;
+    tiles += ((j.M + GT - 1) / GT) * j.tiles_n;
+    live.push_back(j);
+  }
+  if (live.empty()) return SK_OK;
+  JLS_CHECK(upload(H, live, s));
+  hss_gemm_kernel<<<tiles, 256, 0, s>>>(static_cast<const GemmJob*>(H->jobs_dev), (int)live.size());
+  note_launch();
+  ++H->launches;
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+int run_gathers(sk_hss* H, std::vector<GatherJob>& jobs, cudaStream_t s) {
+  std::vector<GatherJob> live;
+  for (const GatherJob& j : jobs)
+    if (j.rows > 0 && j.cols > 0) live.push_back(j);
+  if (live.empty()) return SK_OK;
+  JLS_CHECK(upload(H, live, s));
+  hss_gather_kernel<<<(unsigned)live.size(), 256, 0, s>>>(static_cast<const GatherJob*>(H->jobs_dev), H->A, H->lda);
+  note_launch();
+  ++H->launches;
+  JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+void build_tree(sk_hss* H) {
+  H->nodes.clear();
+  std::vector<int> stack;
+  HssNode root;
+  root.lo = 0;
+  root.hi = H->n;
+  H->nodes.push_back(root);
+  stack.push_back(0);
+  // preorder numbering: children are appended as they are split
+  std::vector<int> order;
+  while (!stack.empty()) {
+    const int i = stack.back();
+    stack.pop_back();
+    const int64_t lo = H->nodes[i].lo, hi = H->nodes[i].hi;
+    if (hi - lo <= H->leaf) continue;
+    const int64_t mid = lo + (hi - lo) / 2;
+    HssNode a, b;
+    a.lo = lo; a.hi = mid; a.level = H->nodes[i].level + 1; a.parent = i;
+    b.lo = mid; b.hi = hi; b.level = a.level; b.parent = i;
+    const int ia = (int)H->nodes.size();
+    H->nodes.push_back(a);
+    H->nodes.push_back(b);
+    H->nodes[i].c1 = ia;
+    H->nodes[i].c2 = ia + 1;
+    stack.push_back(ia + 1);
+    stack.push_back(ia);
+  }
+  int depth = 0;
+  for (const HssNode& nd : H->nodes) depth = std::max(depth, nd.level);
+  H->levels.assign(depth + 1, {});
+  // left to right inside a level: sort each level's nodes by lo
+  for (int i = 0; i < (int)H->nodes.size(); ++i) H->levels[H->nodes[i].level].push_back(i);
+  for (auto& L : H->levels)
+    std::sort(L.begin(), L.end(), [&](int x, int y) { return H->nodes[x].lo < H->nodes[y].lo; });
+}
+
+// One sweep over the levels (leaves first); returns through *grow whether a
+// node needs more columns.
+int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
+  *grow = false;
+  const int d = H->d, dd = H->dd, dcap = H->d_max;
+  const int64_t ldS = H->d_max, ldR = H->op->d_total;
+  for (int L = (int)H->levels.size() - 1; L >= 1; --L) {
+    const std::vector<int>& lv = H->levels[L];
+    // first visits: sizes, storage, D_tau / B_tau
+    std::vector<GatherJob> gathers;
+    for (int i : lv) {
+      HssNode& nd = H->nodes[i];
+      if (nd.state != UNTOUCHED) continue;
+      const bool leaf = nd.c1 < 0;
+      nd.m = leaf ? (int)(nd.hi - nd.lo) : H->nodes[nd.c1].k + H->nodes[nd.c2].k;
+      if (nd.m > HSS_MAX_ROWS) return SK_ERR_UNSUPPORTED;
+      nd.qcap = std::min(nd.m, dcap) + dd;
+      JLS_CHECK(take(H->arena, (size_t)nd.m * dcap, &nd.S));
+      JLS_CHECK(take(H->arena, (size_t)nd.m * nd.qcap, &nd.Q));
+      GatherJob g;
+      if (leaf) {
+        JLS_CHECK(take(H->arena, (size_t)nd.m * nd.m, &nd.D));
+        g.out = nd.D; g.rows = nd.m; g.cols = nd.m; g.r0 = nd.lo; g.c0 = nd.lo;
+      } else {
+        const HssNode& a = H->nodes[nd.c1];
+        const HssNode& b = H->nodes[nd.c2];
+        JLS_CHECK(take(H->arena, (size_t)std::max(1, a.k * b.k), &nd.B));
+        g.out = nd.B; g.rows = a.k; g.cols = b.k; g.ri = a.It; g.ci = b.It;
+      }
+      gathers.push_back(g);
+    }
+    JLS_CHECK(run_gathers(H, gathers, s));
+    // local sketches of the level
+    std::vector<GemmJob> gj;
+    for (int i : lv) {
+      HssNode& nd = H->nodes[i];
+      const int c0 = nd.state == UNTOUCHED ? 0 : d;
+      const int nc = d + dd - c0;
+      if (nd.c1 < 0) {
+        GemmJob j;
+        j.out = nd.S + (int64_t)c0 * nd.m; j.ors = 1; j.ocs = nd.m;
+        j.c.p = H->S + nd.lo * ldS + c0; j.c.rs = ldS; j.c.cs = 1; j.has_c = 1;
+        j.a.p = nd.D; j.a.rs = 1; j.a.cs = nd.m;
+        j.b.p = H->Rd + nd.lo * ldR + c0; j.b.rs = ldR; j.b.cs = 1;
+        j.M = nd.m; j.N = nc; j.K = nd.m; j.alpha = -1.0;
+        gj.push_back(j);
+      } else {
+        const HssNode& a = H->nodes[nd.c1];
+        const HssNode& b = H->nodes[nd.c2];
+        GemmJob top;  // S_nu1(J_nu1, iota) - B R_nu2(:, iota)
+        top.out = nd.S + (int64_t)c0 * nd.m; top.ors = 1; top.ocs = nd.m;
+        top.c.p = a.S + (int64_t)c0 * a.m; top.c.rs = 1; top.c.cs = a.m; top.c.idx = a.J; top.has_c = 1;
+        top.a.p = nd.B; top.a.rs = 1; top.a.cs = std::max(1, a.k);
+        top.b.p = b.R + (int64_t)c0 * b.k; top.b.rs = 1; top.b.cs = b.k;
+        top.M = a.k; top.N = nc; top.K = b.k; top.alpha = -1.0;
+        GemmJob bot;  // S_nu2(J_nu2, iota) - B^T R_nu1(:, iota)
+        bot.out = nd.S + (int64_t)c0 * nd.m + a.k; bot.ors = 1; bot.ocs = nd.m;
+        bot.c.p = b.S + (int64_t)c0 * b.m; bot.c.rs = 1; bot.c.cs = b.m; bot.c.idx = b.J; bot.has_c = 1;
+        bot.a.p = nd.B; bot.a.rs = std::max(1, a.k); bot.a.cs = 1;
+        bot.b.p = a.R + (int64_t)c0 * a.k; bot.b.rs = 1; bot.b.cs = a.k;
+        bot.M = b.k; bot.N = nc; bot.K = a.k; bot.alpha = -1.0;
+        if (b.k == 0) { top.K = 0; }
+        if (a.k == 0) { bot.K = 0; }
+        gj.push_back(top);
+        gj.push_back(bot);
+      }
+    }
+    JLS_CHECK(run_gemms(H, gj, s));
+    // stopping and rank-deficiency tests of the nodes not yet compressed
+    std::vector<int> tested;
+    std::vector<TestJob> tj;
+    for (int i : lv) {
+      HssNode& nd = H->nodes[i];
+      if (nd.state == COMPRESSED) continue;
+      TestJob t;
+      t.S = nd.S; t.Q = nd.Q; t.m = nd.m; t.d = d; t.dd = dd;
+      t.q = nd.state == UNTOUCHED ? -1 : nd.q;
+      t.qcap = nd.qcap;
+      t.er = H->eps_rel / nd.level; t.ea = H->eps_abs / nd.level;
+      t.om11 = nd.om11;
+      tj.push_back(t);
+      tested.push_back(i);
+    }
+    std::vector<int> compress;
+    if (!tj.empty()) {
+      JLS_CHECK(upload(H, tj, s));
+      TestOut* outs = nullptr;
+      JLS_CHECK(take(H->scratch, tj.size(), &outs));
+      hss_test_kernel<<<(unsigned)tj.size(), HT, test_smem(), s>>>(static_cast<const TestJob*>(H->jobs_dev), outs);
+      note_launch();
+      ++H->launches;
+      JLS_CHECK_CUDA(cudaGetLastError());
+      std::vector<TestOut> ho(tj.size());
+      JLS_CHECK_CUDA(cudaMemcpyAsync(ho.data(), outs, sizeof(TestOut) * ho.size(), cudaMemcpyDeviceToHost, s));
+      JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+      for (size_t u = 0; u < tested.size(); ++u) {
+        HssNode& nd = H->nodes[tested[u]];
+        const TestOut& o = ho[u];
+        nd.q = o.q;
+        nd.om11 = o.om11;
+        H->history.push_back(HssRecord{H->sweeps, L, tested[u], o.outcome, o.nh, o.nt, o.mind});
+        if (o.outcome == 2) {
+          nd.state = PARTIAL;
+          *grow = true;
+        } else {
+          compress.push_back(tested[u]);
+        }
+      }
+    }
+    // interpolative decompositions of the nodes that compress now
+    if (!compress.empty()) {
+      std::vector<IdJob> ij;
+      const int C = d + dd;
+      for (int i : compress) {
+        HssNode& nd = H->nodes[i];
+        const int kmax = std::min(nd.m, C);
+        IdJob j;
+        j.S = nd.S; j.m = nd.m; j.C = C;
+        j.er = H->eps_rel / nd.level; j.ea = H->eps_abs / nd.level;
+        JLS_CHECK(take(H->scratch, (size_t)nd.m * C, &j.W));
+        JLS_CHECK(take(H->scratch, (size_t)kmax * nd.m, &j.Rf));
+        JLS_CHECK(take(H->scratch, (size_t)std::max(1, nd.m), &j.nrm));
+        JLS_CHECK(take(H->arena, (size_t)nd.m * kmax, &nd.U));
+        JLS_CHECK(take(H->arena, (size_t)kmax, &nd.J));
+        JLS_CHECK(take(H->arena, (size_t)kmax, &nd.It));
+        j.U = nd.U; j.Jl = nd.J; j.It = nd.It; j.lo = nd.lo;
+        if (nd.c1 >= 0) {
+          j.It1 = H->nodes[nd.c1].It; j.It2 = H->nodes[nd.c2].It; j.k1 = H->nodes[nd.c1].k;
+        }
+        ij.push_back(j);
+      }
+      JLS_CHECK(upload(H, ij, s));
+      int32_t* ranks = nullptr;
+      JLS_CHECK(take(H->scratch, ij.size(), &ranks));
+      hss_id_kernel<<<(unsigned)ij.size(), HT, id_smem(), s>>>(static_cast<const IdJob*>(H->jobs_dev), ranks);
+      note_launch();
+      ++H->launches;
+      JLS_CHECK_CUDA(cudaGetLastError());
+      std::vector<int32_t> hk(ij.size());
+      JLS_CHECK_CUDA(cudaMemcpyAsync(hk.data(), ranks, sizeof(int32_t) * hk.size(), cudaMemcpyDeviceToHost, s));
+      JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+      for (size_t u = 0; u < compress.size(); ++u) {
+        HssNode& nd = H->nodes[compress[u]];
+        nd.k = hk[u];
+        JLS_CHECK(take(H->arena, (size_t)std::max(1, nd.k) * dcap, &nd.R));
+      }
+    }
+    // R_tau over the columns it lacks: all of them for the nodes that just
+    // compressed, the new Delta-d for the earlier ones
+    std::vector<GemmJob> rj;
+    for (int i : lv) {
+      HssNode& nd = H->nodes[i];
+      const bool now = std::find(compress.begin(), compress.end(), i) != compress.end();
+      if (!now && nd.state != COMPRESSED) continue;
+      const int c0 = now ? 0 : d;
+      GemmJob j;
+      j.out = nd.R + (int64_t)c0 * nd.k; j.ors = 1; j.ocs = nd.k;
+      j.a.p = nd.U; j.a.rs = nd.m; j.a.cs = 1;  // U^T
+      if (nd.c1 < 0) {
+        j.b.p = H->Rd + nd.lo * ldR + c0; j.b.rs = ldR; j.b.cs = 1;
+      } else {
+        const HssNode& a = H->nodes[nd.c1];
+        const HssNode& b = H->nodes[nd.c2];
+        j.b.p = a.R + (int64_t)c0 * a.k; j.b.rs = 1; j.b.cs = a.k; j.b.split = a.k;
+        j.b.p2 = b.R + (int64_t)c0 * b.k; j.b.rs2 = 1; j.b.cs2 = b.k;
+      }
+      j.M = nd.k; j.N = d + dd - c0; j.K = nd.m; j.alpha = 1.0;
+      rj.push_back(j);
+    }
+    JLS_CHECK(run_gemms(H, rj, s));
+    for (int i : compress) H->nodes[i].state = COMPRESSED;
+    JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+    H->scratch.release();
+    if (*grow) return SK_OK;
+  }
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hss_compress_adaptive(sk_hss_handle* out, const double* A, int64_t n, int64_t lda, int32_t leaf, int32_t kind,
+                          int32_t d0, int32_t dd, int32_t alpha, uint64_t seed, int32_t d_max, double eps_rel,
+                          double eps_abs, void* stream) {
+  if (!out) return SK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || n < 1 || n >= (1ll << 31) || lda < n || leaf < 1 || leaf > HSS_MAX_ROWS) return SK_ERR_INVALID_ARG;
+  if (d0 < 1 || dd < 1 || d_max < d0 + dd || d_max > HSS_MAX_D || d_max % 2) return SK_ERR_INVALID_ARG;
+  if (!(eps_rel >= 0.0) || !(eps_abs >= 0.0)) return SK_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(A) & 15u) || (lda * 8) % 16) return SK_ERR_ALIGN;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  sk_hss* H = new (std::nothrow) sk_hss();
+  if (!H) return SK_ERR_NOMEM;
+  H->n = n; H->lda = lda; H->A = A; H->leaf = leaf; H->kind = kind; H->alpha = alpha;
+  H->d0 = d0; H->dd = dd; H->d_max = d_max; H->eps_rel = eps_rel; H->eps_abs = eps_abs;
+  int rc = sketch_create_flags(&H->op, kind, n, d0 + dd, alpha, seed, d_max, SK_SCALE_BLOCK, stream);
+  sk_matrix Am;
+  std::memset(&Am, 0, sizeof(Am));
+  Am.dtype = SK_F64; Am.rows = n; Am.cols = n; Am.A = A; Am.ld = lda;
+  if (rc == SK_OK)
+    rc = cuda_status(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)test_smem()));
+  if (rc == SK_OK)
+    rc = cuda_status(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)id_smem()));
+  if (rc == SK_OK) rc = cuda_status(cudaMalloc(&H->S, sizeof(double) * n * d_max));
+  if (rc == SK_OK) rc = cuda_status(cudaMalloc(&H->Rd, sizeof(double) * n * d_max));
+  if (rc == SK_OK) rc = sketch_apply(H->op, &Am, SK_S, SK_PREC_NATIVE, H->S, d_max, nullptr, 0, stream);
+  if (rc == SK_OK) rc = export_dense_R(H->op, H->Rd, SK_F64, s);
+  if (rc == SK_OK) {
+    build_tree(H);
+    H->d = d0;
+  }
+  while (rc == SK_OK) {
+    if (H->levels.size() <= 1) {  // the root is a leaf: D = A
+      H->converged = 1;
+      HssNode& r = H->nodes[0];
+      rc = take(H->arena, (size_t)n * n, &r.D);
+      std::vector<GatherJob> g(1);
+      g[0].out = r.D; g[0].rows = (int)n; g[0].cols = (int)n;
+      if (rc == SK_OK) rc = run_gathers(H, g, s);
+      r.state = COMPRESSED;
+      r.m = (int)n;
+      break;
+    }
+    bool grow = false;
+    rc = sweep(H, s, &grow);
+    if (rc != SK_OK) break;
+    if (!grow) {
+      HssNode& r = H->nodes[0];
+      const HssNode& a = H->nodes[r.c1];
+      const HssNode& b = H->nodes[r.c2];
+      rc = take(H->arena, (size_t)std::max(1, a.k * b.k), &r.B);
+      std::vector<GatherJob> g(1);
+      g[0].out = r.B; g[0].rows = a.k; g[0].cols = b.k; g[0].ri = a.It; g[0].ci = b.It;
+      if (rc == SK_OK) rc = run_gathers(H, g, s);
+      r.state = COMPRESSED;
+      H->converged = 1;
+      ++H->sweeps;
+      break;
+    }
+    ++H->sweeps;
+    if (H->op->d_total + dd > d_max) break;
+    rc = sketch_increment(H->op, dd, stream);
+    if (rc == SK_OK) rc = sketch_apply_increment(H->op, &Am, SK_S, SK_PREC_NATIVE, H->S, d_max, nullptr, 0, stream);
+    if (rc == SK_OK) rc = export_dense_R(H->op, H->Rd, SK_F64, s);
+    H->d += dd;
+  }
+  if (rc == SK_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == SK_OK) rc = sketch_device_status(H->op, stream);
+  if (rc != SK_OK) {
+    hss_destroy(H);
+    return rc;
+  }
+  *out = H;
+  return SK_OK;
+}
+
+int hss_info(sk_hss_handle h, int32_t* nodes, int32_t* d, int32_t* d_total, int32_t* sweeps, int32_t* converged,
+             int32_t* tests) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  if (nodes) *nodes = (int32_t)h->nodes.size();
+  if (d) *d = h->d;
+  if (d_total) *d_total = h->op ? h->op->d_total : 0;
+  if (sweeps) *sweeps = h->sweeps;
+  if (converged) *converged = h->converged;
+  if (tests) *tests = (int32_t)h->history.size();
+  return SK_OK;
+}
+
+int hss_node(sk_hss_handle h, int32_t node, int64_t* lohi, int32_t* info) {
+  if (!h || node < 0 || node >= (int32_t)h->nodes.size()) return SK_ERR_INVALID_ARG;
+  const HssNode& nd = h->nodes[node];
+  if (lohi) { lohi[0] = nd.lo; lohi[1] = nd.hi; }
+  if (info) {
+    info[0] = nd.level; info[1] = nd.parent; info[2] = nd.c1; info[3] = nd.c2;
+    info[4] = nd.state; info[5] = nd.m; info[6] = nd.k;
+  }
+  return SK_OK;
+}
+
+int hss_node_get(sk_hss_handle h, int32_t node, int32_t what, void* dst) {
+  if (!h || !dst || node < 0 || node >= (int32_t)h->nodes.size()) return SK_ERR_INVALID_ARG;
+  const HssNode& nd = h->nodes[node];
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (what) {
+    case SK_HSS_U: src = nd.U; bytes = sizeof(double) * nd.m * nd.k; break;
+    case SK_HSS_J: src = nd.J; bytes = sizeof(int32_t) * nd.k; break;
+    case SK_HSS_IT: src = nd.It; bytes = sizeof(int32_t) * nd.k; break;
+    case SK_HSS_D: src = nd.D; bytes = sizeof(double) * nd.m * nd.m; break;
+    case SK_HSS_B: {
+      if (nd.c1 < 0) return SK_ERR_INVALID_ARG;
+      src = nd.B;
+      bytes = sizeof(double) * h->nodes[nd.c1].k * h->nodes[nd.c2].k;
+      break;
+    }
+    case SK_HSS_S: src = nd.S; bytes = sizeof(double) * nd.m * (h->d + h->dd); break;
+    case SK_HSS_R: src = nd.R; bytes = sizeof(double) * nd.k * (h->d + h->dd); break;
+    default: return SK_ERR_INVALID_ARG;
+  }
+  if (bytes == 0) return SK_OK;
+  if (!src) return SK_ERR_STATE;
+  JLS_CHECK_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  return SK_OK;
+}
+
+int hss_history(sk_hss_handle h, int32_t* ints, double* reals) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  for (size_t u = 0; u < h->history.size(); ++u) {
+    const HssRecord& r = h->history[u];
+    if (ints) { ints[4 * u] = r.sweep; ints[4 * u + 1] = r.level; ints[4 * u + 2] = r.node; ints[4 * u + 3] = r.outcome; }
+    if (reals) { reals[3 * u] = r.nh; reals[3 * u + 1] = r.nt; reals[3 * u + 2] = r.mind; }
+  }
+  return SK_OK;
+}
+
+int64_t hss_launch_count(sk_hss_handle h) { return h ? h->launches : 0; }
+
+void hss_destroy(sk_hss_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->op) sketch_destroy(h->op);
+  h->arena.release();
+  h->scratch.release();
+  if (h->S) cudaFree(h->S);
+  if (h->Rd) cudaFree(h->Rd);
+  if (h->jobs_dev) cudaFree(h->jobs_dev);
+  if (h->host_pin) cudaFreeHost(h->host_pin);
+  delete h;
+}
+
+}  // extern "C"

@@ -45,6 +45,13 @@ SK_ST = 2
 SK_BOTH = 3
 SK_SCALE_BLOCK = 1
 SK_SRHT_REPLACE = 2
+SK_HSS_U = 1
+SK_HSS_J = 2
+SK_HSS_IT = 3
+SK_HSS_D = 4
+SK_HSS_B = 5
+SK_HSS_S = 6
+SK_HSS_R = 7
 
 KIND_NAMES = {"sjlt_graph": SK_SJLT_GRAPH, "sjlt_block": SK_SJLT_BLOCK, "srht": SK_SRHT, "gauss": SK_GAUSS}
 
@@ -60,7 +67,9 @@ EXPORTS = ["sketch_create", "sketch_create_flags", "sketch_sjlt_route", "sketch_
            "sketch_dims", "sketch_export",
            "sketch_device_status", "sketch_selftest_wait", "sketch_launch_count", "sketch_srht_route",
            "sketch_destroy",
-           "sketch_strerror"]
+           "sketch_strerror",
+           "hss_compress_adaptive", "hss_info", "hss_node", "hss_node_get", "hss_history", "hss_launch_count",
+           "hss_destroy"]
 
 
 class JLSketchError(RuntimeError):
@@ -147,6 +156,13 @@ def lib() -> ctypes.CDLL:
         "sketch_sjlt_route": (i32, [i32, i64, i64, i64, i32, i32]),
         "sketch_destroy": (None, [vp]),
         "sketch_strerror": (ctypes.c_char_p, [i32]),
+        "hss_compress_adaptive": (i32, [P(vp), vp, i64, i64, i32, i32, i32, i32, i32, u64, i32, dbl, dbl, vp]),
+        "hss_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
+        "hss_node": (i32, [vp, i32, P(i64), P(i32)]),
+        "hss_node_get": (i32, [vp, i32, i32, vp]),
+        "hss_history": (i32, [vp, vp, vp]),
+        "hss_launch_count": (i64, [vp]),
+        "hss_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -632,3 +648,99 @@ class Sketch:
 def sketch_selftest_wait(stream=None) -> int:
     """Run the bounded-wait self test; returns the status code (SK_ERR_TIMEOUT expected)."""
     return int(lib().sketch_selftest_wait(_stream(stream)))
+
+
+# --- per-node adaptive HSS compression (Algorithm 1) ------------------------
+OUTCOMES = {0: "passed", 1: "rank", 2: "failed"}
+
+
+class Hss:
+    """hss_compress_adaptive on a symmetric FP64 device matrix A (n x n); the
+    generators are read back to the host on request."""
+
+    def __init__(self, A, leaf: int, kind, d0: int, dd: int, alpha: int = 1, seed: int = 0,
+                 d_max: int = 512, eps_rel: float = 1e-6, eps_abs: float = 0.0, stream=None):
+        import torch
+        _check_2d(A, "A")
+        if A.dtype != torch.float64 or A.shape[0] != A.shape[1]:
+            raise TypeError("A must be a square float64 CUDA tensor")
+        k = KIND_NAMES[kind] if isinstance(kind, str) else int(kind)
+        h = ctypes.c_void_p()
+        _check(lib().hss_compress_adaptive(ctypes.byref(h), A.data_ptr(), A.shape[0], A.stride(0), int(leaf), k,
+                                           int(d0), int(dd), int(alpha), int(seed), int(d_max), float(eps_rel),
+                                           float(eps_abs), _stream(stream)), "hss_compress_adaptive")
+        self.h = h.value
+        self.n = A.shape[0]
+        self.dd = int(dd)
+
+    def info(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(6)]
+        _check(lib().hss_info(self.h, *[ctypes.byref(x) for x in v]), "hss_info")
+        keys = ("nodes", "d", "d_total", "sweeps", "converged", "tests")
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def node(self, i: int) -> dict:
+        lohi = (ctypes.c_int64 * 2)()
+        inf = (ctypes.c_int32 * 7)()
+        _check(lib().hss_node(self.h, int(i), lohi, inf), "hss_node")
+        return dict(lo=lohi[0], hi=lohi[1], level=inf[0], parent=inf[1], c1=inf[2], c2=inf[3], state=inf[4],
+                    m=inf[5], k=inf[6])
+
+    def get(self, i: int, what: int, shape, dtype) -> np.ndarray:
+        out = np.zeros(int(np.prod(shape)), dtype=dtype)
+        if out.size:
+            _check(lib().hss_node_get(self.h, int(i), int(what), out.ctypes.data), "hss_node_get")
+        return out.reshape(tuple(reversed(shape))).T if len(shape) == 2 else out
+
+    def generators(self, i: int) -> dict:
+        """U, J, It, R, S (and D for a leaf, B for a node with children) of node i."""
+        nd = self.node(i)
+        out = dict(nd)
+        m, k = nd["m"], nd["k"]
+        w = self.columns()
+        if nd["state"] == 2 and i != 0:
+            out["U"] = self.get(i, SK_HSS_U, (m, k), np.float64)
+            out["J"] = self.get(i, SK_HSS_J, (k,), np.int32)
+            out["It"] = self.get(i, SK_HSS_IT, (k,), np.int32)
+            out["R"] = self.get(i, SK_HSS_R, (k, w), np.float64)
+        if i != 0 and nd["state"] != 0:
+            out["S"] = self.get(i, SK_HSS_S, (m, w), np.float64)
+        if nd["c1"] < 0:
+            if nd["state"] != 0:
+                out["D"] = self.get(i, SK_HSS_D, (m, m), np.float64)
+        elif nd["state"] == 2:
+            k1, k2 = self.node(nd["c1"])["k"], self.node(nd["c2"])["k"]
+            out["B"] = self.get(i, SK_HSS_B, (k1, k2), np.float64)
+        return out
+
+    def columns(self) -> int:
+        """Columns of S_tau and R_tau held: d + Delta-d of the last sweep."""
+        return self.info()["d"] + self.dd
+
+    def history(self) -> list:
+        t = self.info()["tests"]
+        ints = np.zeros(4 * max(t, 1), dtype=np.int32)
+        reals = np.zeros(3 * max(t, 1), dtype=np.float64)
+        _check(lib().hss_history(self.h, ints.ctypes.data, reals.ctypes.data), "hss_history")
+        return [(int(ints[4 * u]), int(ints[4 * u + 1]), int(ints[4 * u + 2]), OUTCOMES[int(ints[4 * u + 3])],
+                 float(reals[3 * u]), float(reals[3 * u + 1]), float(reals[3 * u + 2])) for u in range(t)]
+
+    def launches(self) -> int:
+        return int(lib().hss_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            lib().hss_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
