@@ -725,6 +725,116 @@ def run_differentiation(args):
     print(json.dumps(line))
 
 
+HSS = dict(name="hss_fp64_n2048", n=2048, leaf=64, alpha=4, h=0.2, shift=1e-2, d0=96, dd=32, d_max=512,
+           eps_rel=1e-6, eps_abs=0.0, seed=20230203)
+HSS_LARGE = dict(HSS, name="hss_fp64_n16384", n=16384, leaf=256, d_max=1024)
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (nominal, per GPU)
+
+
+def hss_measure(args, w=None, cpu=True):
+    """Algorithm 1's per-node adaptive loop (hss_compress_adaptive) on a
+    symmetric FP64 Gaussian kernel matrix A_ij = exp(-|x_i - x_j|^2 / (2 h^2))
+    + shift [i == j] of points uniform in [0,1]^3 ordered by recursive median
+    bisection (leaf 64 at n = 2048, the covariance-type problem's shapes; leaf
+    256 at n = 16384), block SJLT alpha = 4, d0 = 96, Delta-d = 32,
+    eps_rel = 1e-6.  One step = one whole compression (global sketch, every
+    sweep, every node), timed with CUDA events around the call; the call's
+    own per-kind device times (hss_profile) give the roofline of its dominant
+    kernel against the nominal FP64 rate.  The CPU baseline is oracle.hss on
+    the same n = 2048 problem."""
+    import numpy as np
+    import torch
+
+    from paper_2302_01977_gb300 import inputs
+    from paper_2302_01977_gb300 import jlsketch as jl
+
+    w = dict(w or HSS)
+    n = w["n"]
+    torch.cuda.set_device(0)
+    X = inputs.points(n, seed=w["seed"]).astype(np.float64)
+    X = X[inputs.bisection_order(X, w["leaf"])]
+    Xd = torch.from_numpy(X).cuda()
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    jl.kernel_matrix(jl.generator(Xd, Xd, w["h"], w["shift"]), A)
+    torch.cuda.synchronize()
+
+    def once():
+        return jl.Hss(A, w["leaf"], "sjlt_block", w["d0"], w["dd"], w["alpha"], w["seed"], w["d_max"],
+                      w["eps_rel"], w["eps_abs"])
+
+    for _ in range(args.warmup):
+        once().close()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    times, profs = [], []
+    l0 = jl.sketch_launch_count()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H = once()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        profs.append(H.profile())
+        info = H.info()
+        ranks = [H.node(i)["k"] for i in range(1, info["nodes"])]
+        H.close()
+    launches = (jl.sketch_launch_count() - l0) / args.steps
+    ck = clocks.stop()
+    ms = statistics.median(times)
+    kinds = jl.Hss.PROFILE_KINDS
+    prof = {k: {"ms": round(statistics.median(p[k]["ms"] for p in profs), 3),
+                "gflop": round(profs[0][k]["flops"] / 1e9, 3),
+                "launches": profs[0][k]["launches"]} for k in kinds}
+    for k in kinds:
+        prof[k]["gflops"] = round(prof[k]["gflop"] / prof[k]["ms"] * 1e3, 1) if prof[k]["ms"] > 0 else None
+    dev_ms = sum(prof[k]["ms"] for k in kinds)
+    top = max((k for k in kinds if k != "gather"), key=lambda k: prof[k]["ms"])
+    mhz = ck.get("sm_mhz") or 2070.0
+    out = {"config": {"workload": w["name"], "n": n, "leaf": w["leaf"], "operator": "sjlt_block",
+                      "alpha": w["alpha"], "h": w["h"], "shift": w["shift"], "d0": w["d0"], "dd": w["dd"],
+                      "d_max": w["d_max"], "eps_rel": w["eps_rel"], "order": "recursive median bisection",
+                      "dtype": "f64"},
+           "ms_per_compression": round(ms, 3), "device_ms_by_kind": prof,
+           "host_and_gaps_ms": round(ms - dev_ms, 3),
+           "d": info["d"], "sweeps": info["sweeps"], "converged": info["converged"], "tests": info["tests"],
+           "nodes": info["nodes"], "max_rank": max(ranks) if ranks else 0,
+           "gpu_launches": int(launches),
+           "roofline": {"kernel": top, "bound": "alu", "unit": "GFLOP/s",
+                        "achieved": prof[top]["gflops"], "peak": FP64_NOMINAL_GFLOPS,
+                        "frac": round((prof[top]["gflops"] or 0) / FP64_NOMINAL_GFLOPS, 4),
+                        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)", "traffic": None},
+           "clocks": ck}
+    if cpu and not args.no_cpu_baseline:
+        from oracle import hss as ohss
+        Ah = A.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = ohss.compress_adaptive(Ah, w["leaf"], "sjlt_block", w["d0"], w["dd"], w["alpha"], w["seed"],
+                                     w["d_max"], w["eps_rel"], w["eps_abs"])
+        dt = time.perf_counter() - t0
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        out["cpu_baseline"] = {"value": round(dt * 1e3, 1), "unit": "ms per compression", "cores": cores,
+                               "kind": "oracle", "sample": f"the whole n = {n} compression (oracle.hss, FP64)",
+                               "same_d_and_sweeps": bool(ref["d"] == info["d"] and ref["sweeps"] == info["sweeps"])}
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_hss(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    w = HSS_LARGE if args.workload == "hss_fp64_n16384" else HSS
+    m = hss_measure(args, w, cpu=w is HSS)
+    line = {"metric": "per-node adaptive HSS compression time (Algorithm 1)", "value": m["ms_per_compression"],
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": m["ms_per_compression"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "ours"}
+    line.update(m)
+    print(json.dumps(line))
+
+
 BATCH = dict(name="batch_kernel_fp32_1024", count=1024, n_lo=256, n_hi=4096, h_lo=0.05, h_hi=0.5,
              d0=(64, 128, 256), dd=32, alpha=4, rounds=3, seed=20230203 + 3)
 
@@ -1237,7 +1347,7 @@ def main():
     ap.add_argument("--workload", choices=["kernel_fp32_n32768", "precision_fp32_n65536",
                                            "kernel_sketch_grad_n262144", "batch_kernel_fp32_1024",
                                            "batch_adaptive_fp32_1024", "complex_helmholtz_fp32_n16384",
-                                           "srht_nonpow2_fp32_n24000"],
+                                           "srht_nonpow2_fp32_n24000", "hss_fp64_n2048", "hss_fp64_n16384"],
                     default="kernel_fp32_n32768",
                     help="the benchmark (default), or the Gaussian precision comparison at n = 65536, d = 512")
     ap.add_argument("--points", type=int, default=0,
@@ -1265,6 +1375,8 @@ def main():
         run_srht_split(args)
     elif args.workload == "complex_helmholtz_fp32_n16384":
         run_complex(args)
+    elif args.workload in ("hss_fp64_n2048", "hss_fp64_n16384"):
+        run_hss(args)
     else:
         run_ours(args)
 

@@ -663,7 +663,7 @@ int hss_info(sk_hss_handle h, int32_t* nodes, int32_t* d, int32_t* d_total, int3
 int hss_node(sk_hss_handle h, int32_t node, int64_t* lohi, int32_t* info);
 
 /* hss_node_get -- copy one generator of a node to host memory `dst`:
- *   SK_HSS_U   U_tau, m x k FP64 column-major     SK_HSS_J   J_tau, k int32 (0-based rows of S_tau)
+ *   SK_HSS_U   U_tau, m x k FP64 row-major        SK_HSS_J   J_tau, k int32 (0-based rows of S_tau)
  *   SK_HSS_IT  I~_tau, k int32 (rows of A)        SK_HSS_D   D_tau (leaf), m x m FP64 column-major
  *   SK_HSS_B   B_tau (internal, root), k_nu1 x k_nu2 FP64 column-major
  *   SK_HSS_S   S_tau, m x (d + Delta-d) FP64 column-major
@@ -687,6 +687,18 @@ int hss_history(sk_hss_handle h, int32_t* ints, double* reals);
 /* hss_launch_count -- kernels the handle launched (the sketch kernels of S
  * excluded). */
 int64_t hss_launch_count(sk_hss_handle h);
+
+/* hss_profile -- device time (ms, from CUDA events on the stream around each
+ * launch), algorithmic FP64 FLOPs and launches per kind of work, host arrays
+ * of 6 entries each (any may be NULL):
+ *   0 copies of D_tau and B_tau from A     1 local sketches (GEMM)
+ *   2 stopping and rank tests              3 interpolative decompositions
+ *   4 R_tau (GEMM)                         5 global sketch S = A R, its
+ *                                            increments and R's dense copy
+ * FLOPs: 2 M N K per GEMM; 8 m q per vector projected twice against q basis
+ * columns; 6 C per remaining row and pivot step of a decomposition plus the
+ * triangular solves; 2 n^2 per column of S (dense count, also for SJLT). */
+int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches);
 
 /* hss_destroy -- free the generators and scratch (NULL is a no-op). */
 void hss_destroy(sk_hss_handle h);

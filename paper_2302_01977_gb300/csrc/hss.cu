@@ -29,8 +29,12 @@
 #include <new>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace jls {
 namespace {
@@ -151,7 +155,13 @@ __global__ void hss_gather_kernel(const GatherJob* __restrict__ jobs, const doub
   }
 }
 
-// ---- block reductions ---------------------------------------------------
+// ---- block and cluster reductions ----------------------------------------
+// The per-node kernels run one thread-block cluster of ncl CTAs per node
+// (ncl = 1 .. 16, chosen by the host from the level's node count); CTA r of
+// the cluster owns the rows [r0, r1) of the node's local sketch.  A sum over
+// the node's rows is a CTA partial per CTA, published in a double-buffered
+// shared-memory slot, a cluster barrier, and the partials added in rank order
+// by every CTA, so every CTA holds the same sums and takes the same decisions.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -174,27 +184,73 @@ __device__ double block_sum(double v, double* red) {
   return red[32];
 }
 
-// w <- (I - Q Q^T)^2 w for the columns [c_lo, c_hi) of Q (m x ldQ column-major);
-// w and h (>= c_hi - c_lo doubles) in shared memory.
-__device__ void project2(const double* __restrict__ Q, int64_t ldQ, int m, int c_lo, int c_hi, double* w,
+constexpr int HPS = HSS_MAX_D + 128;  // doubles per partial slot
+
+struct Cl {
+  int ncl, rank;
+  int r0, r1;        // this CTA's rows
+  int par;           // partial slot in use
+  double* hp;        // 2 slots of HPS doubles, read by the cluster
+  double* red;
+};
+
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+
+// out[j] = sum over the cluster's CTAs of slot[j], j < count (after every CTA
+// wrote its partials into c.hp + c.par * HPS).
+__device__ void cl_finish(Cl& c, int count, double* out) {
+  cl_sync();
+  const double* base = c.hp + c.par * HPS;
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < c.ncl; ++r) s += *cg::this_cluster().map_shared_rank(base + j, (unsigned)r);
+    out[j] = s;
+  }
+  c.par ^= 1;
+  __syncthreads();
+}
+
+// Sum of v over the node's rows (v: this thread's partial over its rows).
+__device__ double cl_sum(Cl& c, double v, double* scal) {
+  const double b = block_sum(v, c.red);
+  if (threadIdx.x == 0) c.hp[c.par * HPS] = b;
+  cl_finish(c, 1, scal);
+  return scal[0];
+}
+
+// w <- (I - Q Q^T)^2 w against the columns [c_lo, c_hi) of Q (ld = m); w and
+// the coefficients h (>= c_hi - c_lo doubles) in shared memory, w holding this
+// CTA's rows only.
+__device__ void project2(Cl& c, const double* __restrict__ Q, int64_t ldQ, int c_lo, int c_hi, double* w,
                          double* h) {
   const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mr = c.r1 - c.r0;
   for (int pass = 0; pass < 2; ++pass) {
+    double* part = c.hp + c.par * HPS;
     for (int j = c_lo + wid; j < c_hi; j += nw) {
-      const double* q = Q + (int64_t)j * ldQ;
+      const double* q = Q + (int64_t)j * ldQ + c.r0;
       double s = 0.0;
-      for (int i = lane; i < m; i += 32) s = fma(q[i], w[i], s);
+      for (int i = lane; i < mr; i += 32) s = fma(q[i], w[i], s);
       s = warp_sum(s);
-      if (lane == 0) h[j - c_lo] = s;
+      if (lane == 0) part[j - c_lo] = s;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    cl_finish(c, c_hi - c_lo, h);
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
       double s = 0.0;
-      for (int j = c_lo; j < c_hi; ++j) s = fma(Q[(int64_t)j * ldQ + i], h[j - c_lo], s);
+      for (int j = c_lo; j < c_hi; ++j) s = fma(Q[(int64_t)j * ldQ + c.r0 + i], h[j - c_lo], s);
       w[i] -= s;
     }
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ void cl_rows(Cl& c, int m) {
+  const cg::cluster_group cl = cg::this_cluster();
+  c.ncl = (int)cl.num_blocks();
+  c.rank = (int)cl.block_rank();
+  c.r0 = (int)((int64_t)m * c.rank / c.ncl);
+  c.r1 = (int)((int64_t)m * (c.rank + 1) / c.ncl);
+  c.par = 0;
 }
 
 // ---- per-node stopping and rank-deficiency tests ----------------------------
@@ -212,39 +268,51 @@ struct TestOut {
   int32_t q, outcome;         // outcome: 0 passed (Eq. (3.1)), 1 rank-deficient, 2 needs more columns
 };
 
+// Shared memory of the test kernel: w (this CTA's rows), h, 2 partial slots, red.
+constexpr size_t TEST_SMEM = sizeof(double) * (HSS_MAX_ROWS + HPS + 2 * HPS + 40);
+
 __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict__ jobs, TestOut* __restrict__ outs) {
   extern __shared__ double sm[];
-  const TestJob J = jobs[blockIdx.x];
+  const int node = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+  const TestJob J = jobs[node];
   const int m = J.m;
-  double* w = sm;                       // m
-  double* h = sm + HSS_MAX_ROWS;        // projection coefficients
-  double* red = h + HSS_MAX_D + 128;    // 33
+  Cl c;
+  cl_rows(c, m);
+  double* w = sm;                   // this CTA's rows
+  double* h = sm + HSS_MAX_ROWS;    // coefficients
+  c.hp = h + HPS;                   // 2 partial slots
+  c.red = c.hp + 2 * HPS;           // 33 + scalar out
+  double* scal = c.red + 36;
+  const int mr = c.r1 - c.r0;
   int q = J.q;
   double om11 = J.om11;
   if (q < 0) {
     // Q_tau: orthonormal basis of the range of S_tau(:, 0:d), columns kept
     // above max(m, d) eps ||S_tau(:, 0:d)||_F (two Gram-Schmidt passes each)
     double f2 = 0.0;
-    for (int64_t e = threadIdx.x; e < (int64_t)m * J.d; e += blockDim.x) f2 = fma(J.S[e], J.S[e], f2);
-    f2 = block_sum(f2, red);
+    for (int j = 0; j < J.d; ++j)
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+        const double v = J.S[(int64_t)j * m + c.r0 + i];
+        f2 = fma(v, v, f2);
+      }
+    f2 = cl_sum(c, f2, scal);
     const double thr = (double)max(m, J.d) * 2.220446049250313e-16 * sqrt(f2);
     q = 0;
     for (int j = 0; j < J.d; ++j) {
       double c2 = 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const double v = J.S[(int64_t)j * m + i];
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+        const double v = J.S[(int64_t)j * m + c.r0 + i];
         w[i] = v;
         c2 = fma(v, v, c2);
       }
-      c2 = block_sum(c2, red);
-      if (j == 0) om11 = sqrt(c2);
-      if (q > 0) project2(J.Q, m, m, 0, q, w, h);
+      if (j == 0) om11 = sqrt(cl_sum(c, c2, scal));
+      __syncthreads();
+      if (q > 0) project2(c, J.Q, m, 0, q, w, h);
       double r2 = 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) r2 = fma(w[i], w[i], r2);
-      r2 = block_sum(r2, red);
-      const double r = sqrt(r2);
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
+      const double r = sqrt(cl_sum(c, r2, scal));
       if (r > thr && r > 0.0) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) J.Q[(int64_t)q * m + i] = w[i] / r;
+        for (int i = threadIdx.x; i < mr; i += blockDim.x) J.Q[(int64_t)q * m + c.r0 + i] = w[i] / r;
         ++q;
       }
       __syncthreads();
@@ -253,30 +321,31 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
   if (q + J.dd > J.qcap) {
     // more basis columns than Q holds: only when q = m (the basis spans all
     // of R^m and S^ = 0); counted as passed with ||S^|| = 0
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && c.rank == 0) {
       TestOut o;
       o.nh = 0.0; o.nt = 0.0; o.mind = 0.0; o.om11 = om11; o.q = q; o.outcome = 0;
-      outs[blockIdx.x] = o;
+      outs[node] = o;
     }
+    cl_sync();  // no CTA leaves while its partial slots may still be read
     return;
   }
   // S~ = S_tau(:, d : d + dd), S^ = (I - Q Q^T)^2 S~ into Q(:, q : q + dd)
   double nt2 = 0.0, nh2 = 0.0;
   for (int jj = 0; jj < J.dd; ++jj) {
     double c2 = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double v = J.S[(int64_t)(J.d + jj) * m + i];
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+      const double v = J.S[(int64_t)(J.d + jj) * m + c.r0 + i];
       w[i] = v;
       c2 = fma(v, v, c2);
     }
-    nt2 += block_sum(c2, red);
-    if (q > 0) project2(J.Q, m, m, 0, q, w, h);
+    nt2 += cl_sum(c, c2, scal);
+    if (q > 0) project2(c, J.Q, m, 0, q, w, h);
     double r2 = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
       r2 = fma(w[i], w[i], r2);
-      J.Q[(int64_t)(q + jj) * m + i] = w[i];
+      J.Q[(int64_t)(q + jj) * m + c.r0 + i] = w[i];
     }
-    nh2 += block_sum(r2, red);
+    nh2 += cl_sum(c, r2, scal);
   }
   const double nh = sqrt(nh2), nt = sqrt(nt2);
   int outcome = 0;
@@ -285,14 +354,15 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
     // {Q^, Om^} = QR(S^) column by column; |diag Om^| = the residual norms
     mind = INFINITY;
     for (int jj = 0; jj < J.dd; ++jj) {
-      for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = J.Q[(int64_t)(q + jj) * m + i];
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = J.Q[(int64_t)(q + jj) * m + c.r0 + i];
       __syncthreads();
-      if (jj > 0) project2(J.Q, m, m, q, q + jj, w, h);
+      if (jj > 0) project2(c, J.Q, m, q, q + jj, w, h);
       double r2 = 0.0;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) r2 = fma(w[i], w[i], r2);
-      const double r = sqrt(block_sum(r2, red));
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
+      const double r = sqrt(cl_sum(c, r2, scal));
       mind = fmin(mind, r);
-      for (int i = threadIdx.x; i < m; i += blockDim.x) J.Q[(int64_t)(q + jj) * m + i] = r > 0.0 ? w[i] / r : 0.0;
+      for (int i = threadIdx.x; i < mr; i += blockDim.x)
+        J.Q[(int64_t)(q + jj) * m + c.r0 + i] = r > 0.0 ? w[i] / r : 0.0;
       __syncthreads();
     }
     if (mind < J.ea || mind < J.er * om11) {
@@ -302,11 +372,12 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
       q += J.dd;
     }
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && c.rank == 0) {
     TestOut o;
     o.nh = nh; o.nt = nt; o.mind = mind; o.om11 = om11; o.q = q; o.outcome = outcome;
-    outs[blockIdx.x] = o;
+    outs[node] = o;
   }
+  cl_sync();  // no CTA leaves while its partial slots may still be read
 }
 
 // ---- row interpolative decomposition S ~ U S(J, :) --------------------------
@@ -314,15 +385,18 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
 // pivot is the remaining row of largest partial norm (the lowest index on a
 // tie); the partial norms are summed afresh in each update pass (no
 // downdating); rank k = the pivots whose norm exceeds eps_a and
-// eps_r |R_11|; U^T = [I, R11^{-1} R12] P^T.
+// eps_r |R_11|; U^T = [I, R11^{-1} R12] P^T.  The rows are spread over the
+// cluster; every CTA finds the same pivot from the CTAs' candidates and reads
+// the pivot row itself (the same arithmetic in every CTA), so one cluster
+// barrier per pivot step orders the row updates.
 struct IdJob {
   const double* S = nullptr;  // m x C, column-major, ld = m
   int32_t m = 0, C = 0;
   double er = 0, ea = 0;
-  double* W = nullptr;        // m x C scratch
-  double* Rf = nullptr;       // min(m, C) x m scratch
-  double* nrm = nullptr;      // m scratch: partial norms
-  double* U = nullptr;        // m x min(m, C) output, ld = m
+  double* W = nullptr;        // m x C scratch, row-major (ld = C)
+  double* Rf = nullptr;       // min(m, C) x m scratch: Rf[t m + i] = r_ti
+  double* R11 = nullptr;      // min(m, C)^2 scratch: R11 in pivot order, row-major
+  double* U = nullptr;        // m x min(m, C) output, row-major (ld = k)
   int32_t* Jl = nullptr;      // local pivots
   int32_t* It = nullptr;      // global skeleton indices
   int64_t lo = 0;             // leaf: I_tau = lo + [0, m)
@@ -331,52 +405,75 @@ struct IdJob {
   int32_t k1 = 0;
 };
 
+// Shared memory of the decomposition kernel: qv (pivot row), red, candidates,
+// perm (every pivot), nrm and used (this CTA's rows).
+constexpr size_t ID_SMEM = sizeof(double) * (HPS + 40 + 4 + HSS_MAX_ROWS) + sizeof(int) * 2 * HSS_MAX_ROWS;
+
 __global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jobs, int32_t* __restrict__ ranks) {
   extern __shared__ double sm[];
-  const IdJob J = jobs[blockIdx.x];
+  const int node = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+  const IdJob J = jobs[node];
   const int m = J.m, C = J.C, kmax = min(m, C);
-  double* qv = sm;                                   // C
-  double* red = qv + HSS_MAX_D + 128;                // 33
-  int* perm = reinterpret_cast<int*>(red + 40);      // m (pivot order), then m used flags
-  int* used = perm + HSS_MAX_ROWS;
-  __shared__ int s_idx[32];
+  Cl c;
+  cl_rows(c, m);
+  const int mr = c.r1 - c.r0;
+  double* qv = sm;                     // C
+  double* red = qv + HPS;              // 33 (+ scalars)
+  double* cand = red + 40;             // 2 slots x (value, index)
+  double* nrm = cand + 4;              // this CTA's rows
+  int* perm = reinterpret_cast<int*>(nrm + HSS_MAX_ROWS);
+  int* used = perm + HSS_MAX_ROWS;     // this CTA's rows
   __shared__ int s_arg;
-  double* nrm = J.nrm;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // W = S (row-major) for this CTA's rows, their norms
+  for (int64_t e = threadIdx.x; e < (int64_t)mr * C; e += blockDim.x) {
+    const int i = (int)(e % mr), cc = (int)(e / mr);
+    J.W[(int64_t)(c.r0 + i) * C + cc] = J.S[(int64_t)cc * m + c.r0 + i];
+  }
+  __syncthreads();
+  for (int i = wid; i < mr; i += nw) {
+    const double* row = J.W + (int64_t)(c.r0 + i) * C;
     double s = 0.0;
-    for (int c = 0; c < C; ++c) {
-      const double v = J.S[(int64_t)c * m + i];
-      J.W[(int64_t)c * m + i] = v;
-      s = fma(v, v, s);
-    }
-    nrm[i] = s;
-    used[i] = 0;
+    for (int cc = lane; cc < C; cc += 32) s = fma(row[cc], row[cc], s);
+    s = warp_sum(s);
+    if (lane == 0) { nrm[i] = s; used[i] = 0; }
   }
   __syncthreads();
   int k = 0;
   double r11 = 0.0;
   for (int t = 0; t < kmax; ++t) {
-    // pivot: the largest partial norm among unused rows, lowest index on ties
+    // this CTA's candidate: the largest partial norm among its unused rows
     double bv = -1.0;
     int bi = m;
-    for (int i = threadIdx.x; i < m; i += blockDim.x)
-      if (!used[i] && nrm[i] > bv) { bv = nrm[i]; bi = i; }
+    for (int i = threadIdx.x; i < mr; i += blockDim.x)
+      if (!used[i] && nrm[i] > bv) { bv = nrm[i]; bi = c.r0 + i; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
-    const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
-    __syncthreads();
-    if (lane == 0) { red[wid] = bv; s_idx[wid] = bi; }
+    if (lane == 0) { red[wid] = bv; red[16 + wid] = (double)bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
       double b = -1.0;
       int a = m;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-        const double v = red[w];
-        const int ai = s_idx[w];
+      for (int u = 0; u < nw; ++u) {
+        const double v = red[u];
+        const int ai = (int)red[16 + u];
+        if (v > b || (v == b && ai < a)) { b = v; a = ai; }
+      }
+      cand[2 * (t & 1)] = b;
+      cand[2 * (t & 1) + 1] = (double)a;
+    }
+    cl_sync();  // candidates and the previous step's row updates are visible
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int a = m;
+      for (int r = 0; r < c.ncl; ++r) {
+        const double* rc = cg::this_cluster().map_shared_rank(cand + 2 * (t & 1), (unsigned)r);
+        const double v = rc[0];
+        const int ai = (int)rc[1];
         if (v > b || (v == b && ai < a)) { b = v; a = ai; }
       }
       s_arg = a;
@@ -384,63 +481,82 @@ __global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jo
     __syncthreads();
     const int p = s_arg;
     if (p >= m) break;
-    // exact norm of the pivot row
+    // the pivot row and its exact norm (the same in every CTA)
+    const double* prow = J.W + (int64_t)p * C;
     double s = 0.0;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-      const double v = J.W[(int64_t)c * m + p];
-      qv[c] = v;
+    for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+      const double v = prow[cc];
+      qv[cc] = v;
       s = fma(v, v, s);
     }
     const double rpp = sqrt(block_sum(s, red));
     if (t == 0) r11 = rpp;
     if (!(rpp > J.ea) || !(rpp > J.er * r11)) break;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) qv[c] /= rpp;
+    for (int cc = threadIdx.x; cc < C; cc += blockDim.x) qv[cc] /= rpp;
     if (threadIdx.x == 0) {
-      used[p] = 1;
       perm[t] = p;
-      J.Rf[(int64_t)t * m + p] = rpp;
+      if (p >= c.r0 && p < c.r1) {
+        used[p - c.r0] = 1;
+        J.Rf[(int64_t)t * m + p] = rpp;
+      }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = wid; i < mr; i += nw) {
       if (used[i]) continue;
+      double* row = J.W + (int64_t)(c.r0 + i) * C;
       double r = 0.0;
-      for (int c = 0; c < C; ++c) r = fma(J.W[(int64_t)c * m + i], qv[c], r);
+      for (int cc = lane; cc < C; cc += 32) r = fma(row[cc], qv[cc], r);
+      r = warp_sum(r);
       double n2 = 0.0;
-      for (int c = 0; c < C; ++c) {
-        const double v = fma(-r, qv[c], J.W[(int64_t)c * m + i]);
-        J.W[(int64_t)c * m + i] = v;
+      for (int cc = lane; cc < C; cc += 32) {
+        const double v = fma(-r, qv[cc], row[cc]);
+        row[cc] = v;
         n2 = fma(v, v, n2);
       }
-      J.Rf[(int64_t)t * m + i] = r;
-      nrm[i] = n2;
+      n2 = warp_sum(n2);
+      if (lane == 0) {
+        J.Rf[(int64_t)t * m + c.r0 + i] = r;
+        nrm[i] = n2;
+      }
     }
     k = t + 1;
     __syncthreads();
   }
-  // U: identity rows at the pivots, X = R11^{-1} R12 elsewhere
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  // R11 in pivot order (row-major, k x k upper triangle), rows split over the cluster
+  cl_sync();
+  for (int s2 = c.rank; s2 < k; s2 += c.ncl)
+    for (int t = s2 + threadIdx.x; t < k; t += blockDim.x)
+      J.R11[(int64_t)s2 * k + t] = J.Rf[(int64_t)s2 * m + perm[t]];
+  cl_sync();
+  // U (row-major, ld = k): identity rows at the pivots, X = R11^{-1} R12 elsewhere
+  for (int i = wid; i < mr; i += nw) {
+    double* x = J.U + (int64_t)(c.r0 + i) * k;
     if (used[i]) {
-      for (int s2 = 0; s2 < k; ++s2) J.U[(int64_t)s2 * m + i] = 0.0;
+      for (int s2 = lane; s2 < k; s2 += 32) x[s2] = 0.0;
       continue;
     }
     for (int s2 = k - 1; s2 >= 0; --s2) {
-      double b = J.Rf[(int64_t)s2 * m + i];
-      for (int t = s2 + 1; t < k; ++t) b -= J.Rf[(int64_t)s2 * m + perm[t]] * J.U[(int64_t)t * m + i];
-      J.U[(int64_t)s2 * m + i] = b / J.Rf[(int64_t)s2 * m + perm[s2]];
+      const double* rr = J.R11 + (int64_t)s2 * k;
+      double acc = 0.0;
+      for (int t = s2 + 1 + lane; t < k; t += 32) acc = fma(rr[t], x[t], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) x[s2] = (J.Rf[(int64_t)s2 * m + c.r0 + i] - acc) / rr[s2];
+      __syncwarp();
     }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < k; t += blockDim.x) {
     const int p = perm[t];
-    J.U[(int64_t)t * m + p] = 1.0;
-    J.Jl[t] = p;
-    J.It[t] = J.It1 ? (p < J.k1 ? J.It1[p] : J.It2[p - J.k1]) : (int32_t)(J.lo + p);
+    if (p >= c.r0 && p < c.r1) J.U[(int64_t)p * k + t] = 1.0;
+    if (c.rank == 0) {
+      J.Jl[t] = p;
+      J.It[t] = J.It1 ? (p < J.k1 ? J.It1[p] : J.It2[p - J.k1]) : (int32_t)(J.lo + p);
+    }
   }
-  if (threadIdx.x == 0) ranks[blockIdx.x] = k;
+  if (threadIdx.x == 0 && c.rank == 0) ranks[node] = k;
+  cl_sync();  // no CTA leaves while its candidates may still be read
 }
 
-size_t test_smem() { return sizeof(double) * (HSS_MAX_ROWS + HSS_MAX_D + 128 + 40); }
-size_t id_smem() { return sizeof(double) * (HSS_MAX_D + 128 + 40) + sizeof(int) * 2 * HSS_MAX_ROWS; }
 
 }  // namespace
 }  // namespace jls
@@ -450,6 +566,8 @@ using namespace jls;
 namespace {
 
 enum { UNTOUCHED = 0, PARTIAL = 1, COMPRESSED = 2 };
+// kinds of work timed separately (hss_profile)
+enum { CAT_GATHER = 0, CAT_LOCAL = 1, CAT_TEST = 2, CAT_ID = 3, CAT_RTAU = 4, CAT_SKETCH = 5, HSS_CATS = 6 };
 
 struct HssNode {
   int64_t lo = 0, hi = 0;
@@ -527,6 +645,13 @@ struct sk_hss {
   void* host_pin = nullptr;
   size_t host_cap = 0;
   int64_t launches = 0;
+  int max_ncl = 8;
+  // device time per kind of work, from events around every launch
+  struct Span { cudaEvent_t a, b; int cat; };
+  std::vector<Span> spans;
+  std::vector<cudaEvent_t> events;  // free events
+  double ms[HSS_CATS] = {}, flops[HSS_CATS] = {};
+  int64_t cat_launches[HSS_CATS] = {};
 };
 
 namespace {
@@ -553,6 +678,48 @@ int ensure_pinned(sk_hss* H, size_t bytes) {
   return SK_OK;
 }
 
+cudaEvent_t take_event(sk_hss* H) {
+  if (!H->events.empty()) {
+    cudaEvent_t e = H->events.back();
+    H->events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Bracket work on s with events; span_end adds the algorithmic FLOPs.
+int span_begin(sk_hss* H, cudaStream_t s) {
+  sk_hss::Span sp{take_event(H), take_event(H), -1};
+  if (sp.a) cudaEventRecord(sp.a, s);
+  H->spans.push_back(sp);
+  return (int)H->spans.size() - 1;
+}
+
+void span_end(sk_hss* H, cudaStream_t s, int span, int cat, double flops, int launches) {
+  sk_hss::Span& sp = H->spans[span];
+  if (sp.b) cudaEventRecord(sp.b, s);
+  sp.cat = cat;
+  H->flops[cat] += flops;
+  H->cat_launches[cat] += launches;
+}
+
+// After a synchronization of the stream: add up the finished spans.
+void spans_collect(sk_hss* H) {
+  for (sk_hss::Span& sp : H->spans) {
+    float t = 0.f;
+    if (sp.a && sp.b && sp.cat >= 0 && cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) H->ms[sp.cat] += t;
+    cudaGetLastError();
+    if (sp.a) H->events.push_back(sp.a);
+    if (sp.b) H->events.push_back(sp.b);
+  }
+  H->spans.clear();
+}
+
 // Copy a job array to the device (through pinned memory; the stream is
 // synchronized before the pinned buffer is reused).
 template <class T>
@@ -566,10 +733,12 @@ int upload(sk_hss* H, const std::vector<T>& v, cudaStream_t s) {
   return SK_OK;
 }
 
-int run_gemms(sk_hss* H, std::vector<GemmJob>& jobs, cudaStream_t s) {
+int run_gemms(sk_hss* H, std::vector<GemmJob>& jobs, cudaStream_t s, int cat) {
   std::vector<GemmJob> live;
   int tiles = 0;
+  double flops = 0.0;
   for (GemmJob j : jobs) {
+    flops += 2.0 * j.M * j.N * j.K;
     if (j.M <= 0 || j.N <= 0) continue;
     j.tiles_n = (j.N + GT - 1) / GT;
     j.tile0 = tiles;
@@ -578,7 +747,9 @@ int run_gemms(sk_hss* H, std::vector<GemmJob>& jobs, cudaStream_t s) {
   }
   if (live.empty()) return SK_OK;
   JLS_CHECK(upload(H, live, s));
+  const int sp = span_begin(H, s);
   hss_gemm_kernel<<<tiles, 256, 0, s>>>(static_cast<const GemmJob*>(H->jobs_dev), (int)live.size());
+  span_end(H, s, sp, cat, flops, 1);
   note_launch();
   ++H->launches;
   JLS_CHECK_CUDA(cudaGetLastError());
@@ -591,10 +762,68 @@ int run_gathers(sk_hss* H, std::vector<GatherJob>& jobs, cudaStream_t s) {
     if (j.rows > 0 && j.cols > 0) live.push_back(j);
   if (live.empty()) return SK_OK;
   JLS_CHECK(upload(H, live, s));
+  const int sp = span_begin(H, s);
   hss_gather_kernel<<<(unsigned)live.size(), 256, 0, s>>>(static_cast<const GatherJob*>(H->jobs_dev), H->A, H->lda);
+  span_end(H, s, sp, CAT_GATHER, 0.0, 1);
   note_launch();
   ++H->launches;
   JLS_CHECK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// Cluster size for a launch over `nodes` nodes of up to mmax rows: the
+// largest power of two that keeps nodes x ncl within the SMs and 32 rows per
+// CTA, at most max_ncl.
+int pick_ncl(const sk_hss* H, int nodes, int mmax) {
+  const int sms = num_sms();
+  int ncl = 1;
+  while (ncl < H->max_ncl && nodes * ncl * 2 <= sms && mmax >= 32 * ncl * 2) ncl *= 2;
+  return ncl;
+}
+
+template <typename... KArgs, typename... Args>
+int launch_cl(void (*kern)(KArgs...), unsigned nodes, int ncl, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nodes * (unsigned)ncl);
+  cfg.blockDim = dim3(HT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)ncl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  JLS_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+  note_launch();
+  return SK_OK;
+}
+
+// Opt in to the shared memory and cluster sizes of the per-node kernels;
+// clusters of 16 where the device can place one, else 8.
+int kernel_setup(sk_hss* H) {
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TEST_SMEM));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ID_SMEM));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  H->max_ncl = 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(HT);
+  cfg.dynamicSmemBytes = std::max(TEST_SMEM, ID_SMEM);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n1 = 0, n2 = 0;
+  if (cudaOccupancyMaxActiveClusters(&n1, hss_test_kernel, &cfg) == cudaSuccess &&
+      cudaOccupancyMaxActiveClusters(&n2, hss_id_kernel, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
+    H->max_ncl = 16;
+  cudaGetLastError();
   return SK_OK;
 }
 
@@ -701,7 +930,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
         gj.push_back(bot);
       }
     }
-    JLS_CHECK(run_gemms(H, gj, s));
+    JLS_CHECK(run_gemms(H, gj, s, CAT_LOCAL));
     // stopping and rank-deficiency tests of the nodes not yet compressed
     std::vector<int> tested;
     std::vector<TestJob> tj;
@@ -722,13 +951,29 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       JLS_CHECK(upload(H, tj, s));
       TestOut* outs = nullptr;
       JLS_CHECK(take(H->scratch, tj.size(), &outs));
-      hss_test_kernel<<<(unsigned)tj.size(), HT, test_smem(), s>>>(static_cast<const TestJob*>(H->jobs_dev), outs);
-      note_launch();
+      const int sp = span_begin(H, s);
+      int mmax = 0;
+      for (const TestJob& t : tj) mmax = std::max(mmax, t.m);
+      JLS_CHECK(launch_cl(hss_test_kernel, (unsigned)tj.size(), pick_ncl(H, (int)tj.size(), mmax), TEST_SMEM, s,
+                          static_cast<const TestJob*>(H->jobs_dev), outs));
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<TestOut> ho(tj.size());
       JLS_CHECK_CUDA(cudaMemcpyAsync(ho.data(), outs, sizeof(TestOut) * ho.size(), cudaMemcpyDeviceToHost, s));
       JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+      // algorithmic FLOPs: a projection pass of one m-vector against q
+      // columns is 4 m q (dots and update), two passes per vector
+      double tf = 0.0;
+      for (size_t u = 0; u < tested.size(); ++u) {
+        const TestJob& t = tj[u];
+        const double m = t.m;
+        const double q0 = t.q < 0 ? std::min(ho[u].q - (ho[u].outcome == 2 ? dd : 0), d) : t.q;
+        if (t.q < 0)
+          for (int j = 0; j < d; ++j) tf += 8.0 * m * std::min<double>(j, q0) + 2.0 * m;
+        tf += dd * (8.0 * m * q0 + 4.0 * m);
+        if (ho[u].mind != 0.0 || ho[u].outcome != 0) tf += 8.0 * m * dd * (dd - 1) / 2.0 + 3.0 * m * dd;
+      }
+      span_end(H, s, sp, CAT_TEST, tf, 1);
       for (size_t u = 0; u < tested.size(); ++u) {
         HssNode& nd = H->nodes[tested[u]];
         const TestOut& o = ho[u];
@@ -755,7 +1000,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
         j.er = H->eps_rel / nd.level; j.ea = H->eps_abs / nd.level;
         JLS_CHECK(take(H->scratch, (size_t)nd.m * C, &j.W));
         JLS_CHECK(take(H->scratch, (size_t)kmax * nd.m, &j.Rf));
-        JLS_CHECK(take(H->scratch, (size_t)std::max(1, nd.m), &j.nrm));
+        JLS_CHECK(take(H->scratch, (size_t)std::max(1, kmax * kmax), &j.R11));
         JLS_CHECK(take(H->arena, (size_t)nd.m * kmax, &nd.U));
         JLS_CHECK(take(H->arena, (size_t)kmax, &nd.J));
         JLS_CHECK(take(H->arena, (size_t)kmax, &nd.It));
@@ -768,13 +1013,24 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       JLS_CHECK(upload(H, ij, s));
       int32_t* ranks = nullptr;
       JLS_CHECK(take(H->scratch, ij.size(), &ranks));
-      hss_id_kernel<<<(unsigned)ij.size(), HT, id_smem(), s>>>(static_cast<const IdJob*>(H->jobs_dev), ranks);
-      note_launch();
+      const int sp = span_begin(H, s);
+      int mmax = 0;
+      for (const IdJob& t : ij) mmax = std::max(mmax, t.m);
+      JLS_CHECK(launch_cl(hss_id_kernel, (unsigned)ij.size(), pick_ncl(H, (int)ij.size(), mmax), ID_SMEM, s,
+                          static_cast<const IdJob*>(H->jobs_dev), ranks));
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<int32_t> hk(ij.size());
       JLS_CHECK_CUDA(cudaMemcpyAsync(hk.data(), ranks, sizeof(int32_t) * hk.size(), cudaMemcpyDeviceToHost, s));
       JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+      // algorithmic FLOPs: per pivot step a dot, an update and a norm over the
+      // remaining rows (6 (m - t) C), then the triangular solves (m - k) k^2
+      double idf = 0.0;
+      for (size_t u = 0; u < compress.size(); ++u) {
+        const double m = ij[u].m, k = hk[u];
+        idf += 2.0 * m * C + 6.0 * C * (m * k - k * (k - 1) / 2.0) + (m - k) * k * k;
+      }
+      span_end(H, s, sp, CAT_ID, idf, 1);
       for (size_t u = 0; u < compress.size(); ++u) {
         HssNode& nd = H->nodes[compress[u]];
         nd.k = hk[u];
@@ -791,7 +1047,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       const int c0 = now ? 0 : d;
       GemmJob j;
       j.out = nd.R + (int64_t)c0 * nd.k; j.ors = 1; j.ocs = nd.k;
-      j.a.p = nd.U; j.a.rs = nd.m; j.a.cs = 1;  // U^T
+      j.a.p = nd.U; j.a.rs = 1; j.a.cs = nd.k;  // U^T, U row-major
       if (nd.c1 < 0) {
         j.b.p = H->Rd + nd.lo * ldR + c0; j.b.rs = ldR; j.b.cs = 1;
       } else {
@@ -803,9 +1059,10 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       j.M = nd.k; j.N = d + dd - c0; j.K = nd.m; j.alpha = 1.0;
       rj.push_back(j);
     }
-    JLS_CHECK(run_gemms(H, rj, s));
+    JLS_CHECK(run_gemms(H, rj, s, CAT_RTAU));
     for (int i : compress) H->nodes[i].state = COMPRESSED;
     JLS_CHECK_CUDA(cudaStreamSynchronize(s));
+    spans_collect(H);
     H->scratch.release();
     if (*grow) return SK_OK;
   }
@@ -834,16 +1091,16 @@ int hss_compress_adaptive(sk_hss_handle* out, const double* A, int64_t n, int64_
   sk_matrix Am;
   std::memset(&Am, 0, sizeof(Am));
   Am.dtype = SK_F64; Am.rows = n; Am.cols = n; Am.A = A; Am.ld = lda;
-  if (rc == SK_OK)
-    rc = cuda_status(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)test_smem()));
-  if (rc == SK_OK)
-    rc = cuda_status(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)id_smem()));
+  if (rc == SK_OK) rc = kernel_setup(H);
   if (rc == SK_OK) rc = cuda_status(cudaMalloc(&H->S, sizeof(double) * n * d_max));
   if (rc == SK_OK) rc = cuda_status(cudaMalloc(&H->Rd, sizeof(double) * n * d_max));
-  if (rc == SK_OK) rc = sketch_apply(H->op, &Am, SK_S, SK_PREC_NATIVE, H->S, d_max, nullptr, 0, stream);
-  if (rc == SK_OK) rc = export_dense_R(H->op, H->Rd, SK_F64, s);
+  if (rc == SK_OK) {
+    const int sp = span_begin(H, s);
+    const long long l0 = sketch_launch_count();
+    rc = sketch_apply(H->op, &Am, SK_S, SK_PREC_NATIVE, H->S, d_max, nullptr, 0, stream);
+    if (rc == SK_OK) rc = export_dense_R(H->op, H->Rd, SK_F64, s);
+    span_end(H, s, sp, CAT_SKETCH, 2.0 * n * n * (d0 + dd), (int)(sketch_launch_count() - l0));
+  }
   if (rc == SK_OK) {
     build_tree(H);
     H->d = d0;
@@ -878,12 +1135,16 @@ int hss_compress_adaptive(sk_hss_handle* out, const double* A, int64_t n, int64_
     }
     ++H->sweeps;
     if (H->op->d_total + dd > d_max) break;
+    const int sp = span_begin(H, s);
+    const long long l0 = sketch_launch_count();
     rc = sketch_increment(H->op, dd, stream);
     if (rc == SK_OK) rc = sketch_apply_increment(H->op, &Am, SK_S, SK_PREC_NATIVE, H->S, d_max, nullptr, 0, stream);
     if (rc == SK_OK) rc = export_dense_R(H->op, H->Rd, SK_F64, s);
+    span_end(H, s, sp, CAT_SKETCH, 2.0 * n * n * dd, (int)(sketch_launch_count() - l0));
     H->d += dd;
   }
   if (rc == SK_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == SK_OK) spans_collect(H);
   if (rc == SK_OK) rc = sketch_device_status(H->op, stream);
   if (rc != SK_OK) {
     hss_destroy(H);
@@ -922,7 +1183,7 @@ int hss_node_get(sk_hss_handle h, int32_t node, int32_t what, void* dst) {
   const void* src = nullptr;
   size_t bytes = 0;
   switch (what) {
-    case SK_HSS_U: src = nd.U; bytes = sizeof(double) * nd.m * nd.k; break;
+    case SK_HSS_U: src = nd.U; bytes = sizeof(double) * nd.m * nd.k; break;  // row-major
     case SK_HSS_J: src = nd.J; bytes = sizeof(int32_t) * nd.k; break;
     case SK_HSS_IT: src = nd.It; bytes = sizeof(int32_t) * nd.k; break;
     case SK_HSS_D: src = nd.D; bytes = sizeof(double) * nd.m * nd.m; break;
@@ -954,6 +1215,16 @@ int hss_history(sk_hss_handle h, int32_t* ints, double* reals) {
 
 int64_t hss_launch_count(sk_hss_handle h) { return h ? h->launches : 0; }
 
+int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches) {
+  if (!h) return SK_ERR_INVALID_ARG;
+  for (int c = 0; c < HSS_CATS; ++c) {
+    if (ms) ms[c] = h->ms[c];
+    if (flops) flops[c] = h->flops[c];
+    if (launches) launches[c] = h->cat_launches[c];
+  }
+  return SK_OK;
+}
+
 void hss_destroy(sk_hss_handle h) {
   if (!h) return;
   cudaDeviceSynchronize();
@@ -964,6 +1235,8 @@ void hss_destroy(sk_hss_handle h) {
   if (h->Rd) cudaFree(h->Rd);
   if (h->jobs_dev) cudaFree(h->jobs_dev);
   if (h->host_pin) cudaFreeHost(h->host_pin);
+  spans_collect(h);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   delete h;
 }
 

@@ -69,7 +69,7 @@ EXPORTS = ["sketch_create", "sketch_create_flags", "sketch_sjlt_route", "sketch_
            "sketch_destroy",
            "sketch_strerror",
            "hss_compress_adaptive", "hss_info", "hss_node", "hss_node_get", "hss_history", "hss_launch_count",
-           "hss_destroy"]
+           "hss_profile", "hss_destroy"]
 
 
 class JLSketchError(RuntimeError):
@@ -162,6 +162,7 @@ def lib() -> ctypes.CDLL:
         "hss_node_get": (i32, [vp, i32, i32, vp]),
         "hss_history": (i32, [vp, vp, vp]),
         "hss_launch_count": (i64, [vp]),
+        "hss_profile": (i32, [vp, vp, vp, vp]),
         "hss_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -686,11 +687,15 @@ class Hss:
         return dict(lo=lohi[0], hi=lohi[1], level=inf[0], parent=inf[1], c1=inf[2], c2=inf[3], state=inf[4],
                     m=inf[5], k=inf[6])
 
-    def get(self, i: int, what: int, shape, dtype) -> np.ndarray:
+    def get(self, i: int, what: int, shape, dtype, order: str = "F") -> np.ndarray:
+        """One generator of node i as a host array of `shape` (column-major
+        unless order == "C")."""
         out = np.zeros(int(np.prod(shape)), dtype=dtype)
         if out.size:
             _check(lib().hss_node_get(self.h, int(i), int(what), out.ctypes.data), "hss_node_get")
-        return out.reshape(tuple(reversed(shape))).T if len(shape) == 2 else out
+        if len(shape) != 2:
+            return out
+        return out.reshape(shape) if order == "C" else out.reshape(tuple(reversed(shape))).T
 
     def generators(self, i: int) -> dict:
         """U, J, It, R, S (and D for a leaf, B for a node with children) of node i."""
@@ -699,7 +704,7 @@ class Hss:
         m, k = nd["m"], nd["k"]
         w = self.columns()
         if nd["state"] == 2 and i != 0:
-            out["U"] = self.get(i, SK_HSS_U, (m, k), np.float64)
+            out["U"] = self.get(i, SK_HSS_U, (m, k), np.float64, order="C")
             out["J"] = self.get(i, SK_HSS_J, (k,), np.int32)
             out["It"] = self.get(i, SK_HSS_IT, (k,), np.int32)
             out["R"] = self.get(i, SK_HSS_R, (k, w), np.float64)
@@ -727,6 +732,17 @@ class Hss:
 
     def launches(self) -> int:
         return int(lib().hss_launch_count(self.h))
+
+    PROFILE_KINDS = ("gather", "local_sketch", "test", "id", "r_tau", "global_sketch")
+
+    def profile(self) -> dict:
+        """Per kind of work: device ms, algorithmic FP64 FLOPs, launches."""
+        ms = np.zeros(6)
+        fl = np.zeros(6)
+        ln = np.zeros(6, dtype=np.int64)
+        _check(lib().hss_profile(self.h, ms.ctypes.data, fl.ctypes.data, ln.ctypes.data), "hss_profile")
+        return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(ln[i]))
+                for i, k in enumerate(self.PROFILE_KINDS)}
 
     def close(self):
         if self.h:
