@@ -203,7 +203,14 @@ __device__ void cl_finish(Cl& c, int count, double* out) {
   const double* base = c.hp + c.par * HPS;
   for (int j = threadIdx.x; j < count; j += blockDim.x) {
     double s = 0.0;
-    for (int r = 0; r < c.ncl; ++r) s += *cg::this_cluster().map_shared_rank(base + j, (unsigned)r);
+    for (int r0 = 0; r0 < c.ncl; r0 += 8) {  // 8 remote loads in flight, added in rank order
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = r0 + u < c.ncl ? *cg::this_cluster().map_shared_rank(base + j, (unsigned)(r0 + u)) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
     out[j] = s;
   }
   c.par ^= 1;
@@ -218,26 +225,64 @@ __device__ double cl_sum(Cl& c, double v, double* scal) {
   return scal[0];
 }
 
-// w <- (I - Q Q^T)^2 w against the columns [c_lo, c_hi) of Q (ld = m); w and
-// the coefficients h (>= c_hi - c_lo doubles) in shared memory, w holding this
-// CTA's rows only.
-__device__ void project2(Cl& c, const double* __restrict__ Q, int64_t ldQ, int c_lo, int c_hi, double* w,
-                         double* h) {
+// w <- (I - Q Q^T)^2 w against the columns [c_lo, c_hi) of Q; Qb points at
+// this CTA's rows of column 0 (column j at Qb + j ld: the CTA's cache in
+// shared memory or Q itself), w and the coefficients h (>= c_hi - c_lo
+// doubles) in shared memory, w holding this CTA's rows only.
+__device__ void project2(Cl& c, const double* __restrict__ Qb, int64_t ld, int c_lo, int c_hi, double* w,
+                         double* h, double* gp) {
   const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mr = c.r1 - c.r0;
   for (int pass = 0; pass < 2; ++pass) {
     double* part = c.hp + c.par * HPS;
-    for (int j = c_lo + wid; j < c_hi; j += nw) {
-      const double* q = Q + (int64_t)j * ldQ + c.r0;
-      double s = 0.0;
-      for (int i = lane; i < mr; i += 32) s = fma(q[i], w[i], s);
-      s = warp_sum(s);
-      if (lane == 0) part[j - c_lo] = s;
+    // Q^T w: a warp takes 4 columns at a time, so that each lane has 4
+    // (times the unrolled rows) independent loads in flight
+    for (int j0 = c_lo + 4 * wid; j0 < c_hi; j0 += 4 * nw) {
+      const int nj = min(4, c_hi - j0);
+      const double* q = Qb + (int64_t)j0 * ld;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 2
+      for (int i = lane; i < mr; i += 32) {
+        const double wi = w[i];
+        s0 = fma(q[i], wi, s0);
+        if (nj > 1) s1 = fma(q[ld + i], wi, s1);
+        if (nj > 2) s2 = fma(q[2 * ld + i], wi, s2);
+        if (nj > 3) s3 = fma(q[3 * ld + i], wi, s3);
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      s3 = warp_sum(s3);
+      if (lane == 0) {
+        part[j0 - c_lo] = s0;
+        if (nj > 1) part[j0 + 1 - c_lo] = s1;
+        if (nj > 2) part[j0 + 2 - c_lo] = s2;
+        if (nj > 3) part[j0 + 3 - c_lo] = s3;
+      }
     }
     cl_finish(c, c_hi - c_lo, h);
+    // w -= Q h: G groups of threads split the columns, each thread of a
+    // group a row; the groups' sums (gp: G x mr) are added in group order
+    const int G = mr > 0 ? max(1, min((int)blockDim.x / mr, 8)) : 1;
+    const int g = threadIdx.x / max(mr, 1);
+    if (mr > 0 && g < G) {
+      for (int i = threadIdx.x % mr; i < mr; i += blockDim.x) {
+        // 8 independent loads in flight per thread
+        const double* q = Qb + i;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int j = c_lo + g;
+        for (; j + 7 * G < c_hi; j += 8 * G) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a[u] = fma(q[(int64_t)(j + u * G) * ld], h[j + u * G - c_lo], a[u]);
+        }
+        for (; j < c_hi; j += G) a[0] = fma(q[(int64_t)j * ld], h[j - c_lo], a[0]);
+        gp[g * mr + i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+      }
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < mr; i += blockDim.x) {
       double s = 0.0;
-      for (int j = c_lo; j < c_hi; ++j) s = fma(Q[(int64_t)j * ldQ + c.r0 + i], h[j - c_lo], s);
+      for (int u = 0; u < G; ++u) s += gp[u * mr + i];
       w[i] -= s;
     }
     __syncthreads();
@@ -268,10 +313,22 @@ struct TestOut {
   int32_t q, outcome;         // outcome: 0 passed (Eq. (3.1)), 1 rank-deficient, 2 needs more columns
 };
 
-// Shared memory of the test kernel: w (this CTA's rows), h, 2 partial slots, red.
-constexpr size_t TEST_SMEM = sizeof(double) * (HSS_MAX_ROWS + HPS + 2 * HPS + 40);
+// Shared memory of the test kernel, laid out per launch from the largest rows
+// per CTA (mrx) and basis columns (qx, the basis after this test included):
+// w (this CTA's rows), h, 2 partial slots, red, the projection's group sums
+// (G x mr <= max(mrx, blockDim)), and this CTA's rows of Q (mrx x qx) when they
+// fit (qsm).
+struct TestLayout {
+  int mrx, qx, qsm;
+};
+__host__ __device__ inline size_t test_smem_bytes(const TestLayout& L) {
+  return sizeof(double) * ((size_t)L.mrx + 3 * HPS + 40 + (size_t)(L.mrx > HT ? L.mrx : HT) +
+                           (L.qsm ? (size_t)L.mrx * L.qx : 0));
+}
+constexpr size_t TEST_SMEM_MAX = 220 * 1024;
 
-__global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict__ jobs, TestOut* __restrict__ outs) {
+__global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict__ jobs, TestOut* __restrict__ outs,
+                                                      TestLayout L) {
   extern __shared__ double sm[];
   const int node = (int)(blockIdx.x / cg::this_cluster().num_blocks());
   const TestJob J = jobs[node];
@@ -279,13 +336,32 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
   Cl c;
   cl_rows(c, m);
   double* w = sm;                   // this CTA's rows
-  double* h = sm + HSS_MAX_ROWS;    // coefficients
+  double* h = w + L.mrx;            // coefficients
   c.hp = h + HPS;                   // 2 partial slots
   c.red = c.hp + 2 * HPS;           // 33 + scalar out
   double* scal = c.red + 36;
+  double* gp = c.red + 40;          // group sums
+  double* Qs = gp + (L.mrx > HT ? L.mrx : HT);
   const int mr = c.r1 - c.r0;
+  // this CTA's rows of the basis: cached in shared memory (qsm) or read from Q
+  const double* Qb = L.qsm ? Qs : J.Q + c.r0;
+  const int64_t ldb = L.qsm ? L.mrx : m;
+  auto put_col = [&](int j, double scale) {  // Q(:, j) = w / scale over this CTA's rows
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+      const double v = scale == 1.0 ? w[i] : w[i] / scale;
+      J.Q[(int64_t)j * m + c.r0 + i] = v;
+      if (L.qsm) Qs[(int64_t)j * L.mrx + i] = v;
+    }
+  };
   int q = J.q;
   double om11 = J.om11;
+  if (L.qsm && q > 0) {
+    for (int64_t e = threadIdx.x; e < (int64_t)mr * q; e += blockDim.x) {
+      const int i = (int)(e % mr), j = (int)(e / mr);
+      Qs[(int64_t)j * L.mrx + i] = J.Q[(int64_t)j * m + c.r0 + i];
+    }
+    __syncthreads();
+  }
   if (q < 0) {
     // Q_tau: orthonormal basis of the range of S_tau(:, 0:d), columns kept
     // above max(m, d) eps ||S_tau(:, 0:d)||_F (two Gram-Schmidt passes each)
@@ -307,18 +383,18 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
       }
       if (j == 0) om11 = sqrt(cl_sum(c, c2, scal));
       __syncthreads();
-      if (q > 0) project2(c, J.Q, m, 0, q, w, h);
+      if (q > 0) project2(c, Qb, ldb, 0, q, w, h, gp);
       double r2 = 0.0;
       for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
       const double r = sqrt(cl_sum(c, r2, scal));
       if (r > thr && r > 0.0) {
-        for (int i = threadIdx.x; i < mr; i += blockDim.x) J.Q[(int64_t)q * m + c.r0 + i] = w[i] / r;
+        put_col(q, r);
         ++q;
       }
       __syncthreads();
     }
   }
-  if (q + J.dd > J.qcap) {
+  if (q + J.dd > J.qcap || (L.qsm && q + J.dd > L.qx)) {
     // more basis columns than Q holds: only when q = m (the basis spans all
     // of R^m and S^ = 0); counted as passed with ||S^|| = 0
     if (threadIdx.x == 0 && c.rank == 0) {
@@ -339,12 +415,10 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
       c2 = fma(v, v, c2);
     }
     nt2 += cl_sum(c, c2, scal);
-    if (q > 0) project2(c, J.Q, m, 0, q, w, h);
+    if (q > 0) project2(c, Qb, ldb, 0, q, w, h, gp);
     double r2 = 0.0;
-    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
-      r2 = fma(w[i], w[i], r2);
-      J.Q[(int64_t)(q + jj) * m + c.r0 + i] = w[i];
-    }
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
+    put_col(q + jj, 1.0);
     nh2 += cl_sum(c, r2, scal);
   }
   const double nh = sqrt(nh2), nt = sqrt(nt2);
@@ -354,15 +428,19 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
     // {Q^, Om^} = QR(S^) column by column; |diag Om^| = the residual norms
     mind = INFINITY;
     for (int jj = 0; jj < J.dd; ++jj) {
-      for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = J.Q[(int64_t)(q + jj) * m + c.r0 + i];
+      for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = Qb[(int64_t)(q + jj) * ldb + i];
       __syncthreads();
-      if (jj > 0) project2(c, J.Q, m, q, q + jj, w, h);
+      if (jj > 0) project2(c, Qb, ldb, q, q + jj, w, h, gp);
       double r2 = 0.0;
       for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
       const double r = sqrt(cl_sum(c, r2, scal));
       mind = fmin(mind, r);
-      for (int i = threadIdx.x; i < mr; i += blockDim.x)
-        J.Q[(int64_t)(q + jj) * m + c.r0 + i] = r > 0.0 ? w[i] / r : 0.0;
+      if (r > 0.0) {
+        put_col(q + jj, r);
+      } else {
+        for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = 0.0;
+        put_col(q + jj, 1.0);
+      }
       __syncthreads();
     }
     if (mind < J.ea || mind < J.er * om11) {
@@ -383,9 +461,10 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
 // ---- row interpolative decomposition S ~ U S(J, :) --------------------------
 // Column-pivoted QR of S^T by modified Gram-Schmidt on the rows of S: the
 // pivot is the remaining row of largest partial norm (the lowest index on a
-// tie); the partial norms are summed afresh in each update pass (no
-// downdating); rank k = the pivots whose norm exceeds eps_a and
-// eps_r |R_11|; U^T = [I, R11^{-1} R12] P^T.  The rows are spread over the
+// tie); the partial norms are downdated, |a_i|^2 <- |a_i|^2 - r_ti^2, and
+// summed afresh when the downdate has cancelled below 1e-8 of the last exact
+// value (the safeguard of LAPACK's column-pivoted QR); rank k = the pivots
+// whose exact norm exceeds eps_a and eps_r |R_11|; U^T = [I, R11^{-1} R12] P^T.  The rows are spread over the
 // cluster; every CTA finds the same pivot from the CTAs' candidates and reads
 // the pivot row itself (the same arithmetic in every CTA), so one cluster
 // barrier per pivot step orders the row updates.
@@ -405,11 +484,21 @@ struct IdJob {
   int32_t k1 = 0;
 };
 
-// Shared memory of the decomposition kernel: qv (pivot row), red, candidates,
-// perm (every pivot), nrm and used (this CTA's rows).
-constexpr size_t ID_SMEM = sizeof(double) * (HPS + 40 + 4 + HSS_MAX_ROWS) + sizeof(int) * 2 * HSS_MAX_ROWS;
+// Shared memory of the decomposition kernel, laid out per launch from the
+// largest C, rows per CTA (mr) and pivots (kx) of its nodes: qv (the pivot
+// row), red, 2 candidate slots, nrm and ref (this CTA's rows), this CTA's
+// rows of W when they fit (wsm), perm (every pivot), used (this CTA's rows).
+struct IdLayout {
+  int Cx, mrx, kx, wsm;
+};
+__host__ __device__ inline size_t id_smem_bytes(const IdLayout& L) {
+  return sizeof(double) * ((size_t)L.Cx + 44 + 2 * (size_t)L.mrx + (L.wsm ? (size_t)L.mrx * L.Cx : 0)) +
+         sizeof(int) * ((size_t)L.kx + L.mrx);
+}
+constexpr size_t ID_SMEM_MAX = 200 * 1024;
 
-__global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jobs, int32_t* __restrict__ ranks) {
+__global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jobs, int32_t* __restrict__ ranks,
+                                                    IdLayout L) {
   extern __shared__ double sm[];
   const int node = (int)(blockIdx.x / cg::this_cluster().num_blocks());
   const IdJob J = jobs[node];
@@ -418,25 +507,29 @@ __global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jo
   cl_rows(c, m);
   const int mr = c.r1 - c.r0;
   double* qv = sm;                     // C
-  double* red = qv + HPS;              // 33 (+ scalars)
+  double* red = qv + L.Cx;             // 40
   double* cand = red + 40;             // 2 slots x (value, index)
-  double* nrm = cand + 4;              // this CTA's rows
-  int* perm = reinterpret_cast<int*>(nrm + HSS_MAX_ROWS);
-  int* used = perm + HSS_MAX_ROWS;     // this CTA's rows
+  double* nrm = cand + 4;              // this CTA's rows: partial norms
+  double* ref = nrm + L.mrx;           // their last exact values
+  double* Wsm = ref + L.mrx;           // this CTA's rows of W (wsm)
+  int* perm = reinterpret_cast<int*>(Wsm + (L.wsm ? (size_t)L.mrx * L.Cx : 0));
+  int* used = perm + L.kx;             // this CTA's rows
+  // this CTA's rows of W: in shared memory when they fit, else in J.W
+  double* Wmine = L.wsm ? Wsm : J.W + (int64_t)c.r0 * C;
   __shared__ int s_arg;
   const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
   // W = S (row-major) for this CTA's rows, their norms
   for (int64_t e = threadIdx.x; e < (int64_t)mr * C; e += blockDim.x) {
     const int i = (int)(e % mr), cc = (int)(e / mr);
-    J.W[(int64_t)(c.r0 + i) * C + cc] = J.S[(int64_t)cc * m + c.r0 + i];
+    Wmine[(int64_t)i * C + cc] = J.S[(int64_t)cc * m + c.r0 + i];
   }
   __syncthreads();
   for (int i = wid; i < mr; i += nw) {
-    const double* row = J.W + (int64_t)(c.r0 + i) * C;
+    const double* row = Wmine + (int64_t)i * C;
     double s = 0.0;
     for (int cc = lane; cc < C; cc += 32) s = fma(row[cc], row[cc], s);
     s = warp_sum(s);
-    if (lane == 0) { nrm[i] = s; used[i] = 0; }
+    if (lane == 0) { nrm[i] = s; ref[i] = s; used[i] = 0; }
   }
   __syncthreads();
   int k = 0;
@@ -482,7 +575,15 @@ __global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jo
     const int p = s_arg;
     if (p >= m) break;
     // the pivot row and its exact norm (the same in every CTA)
-    const double* prow = J.W + (int64_t)p * C;
+    const double* prow;
+    if (L.wsm) {
+      int owner = 0;
+      while ((int64_t)m * (owner + 1) / c.ncl <= p) ++owner;
+      const int o0 = (int)((int64_t)m * owner / c.ncl);
+      prow = cg::this_cluster().map_shared_rank(Wsm, (unsigned)owner) + (int64_t)(p - o0) * C;
+    } else {
+      prow = J.W + (int64_t)p * C;
+    }
     double s = 0.0;
     for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
       const double v = prow[cc];
@@ -503,17 +604,44 @@ __global__ void __launch_bounds__(HT) hss_id_kernel(const IdJob* __restrict__ jo
     __syncthreads();
     for (int i = wid; i < mr; i += nw) {
       if (used[i]) continue;
-      double* row = J.W + (int64_t)(c.r0 + i) * C;
+      double* row = Wmine + (int64_t)i * C;
       double r = 0.0;
-      for (int cc = lane; cc < C; cc += 32) r = fma(row[cc], qv[cc], r);
-      r = warp_sum(r);
-      double n2 = 0.0;
-      for (int cc = lane; cc < C; cc += 32) {
-        const double v = fma(-r, qv[cc], row[cc]);
-        row[cc] = v;
-        n2 = fma(v, v, n2);
+      if (C <= 512) {
+        // the lane's 16 entries of the row in registers: one load each
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int cc = lane + 32 * u;
+          v[u] = cc < C ? row[cc] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int cc = lane + 32 * u;
+          if (cc < C) r = fma(v[u], qv[cc], r);
+        }
+        r = warp_sum(r);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int cc = lane + 32 * u;
+          if (cc < C) row[cc] = fma(-r, qv[cc], v[u]);
+        }
+      } else {
+#pragma unroll 4
+        for (int cc = lane; cc < C; cc += 32) r = fma(row[cc], qv[cc], r);
+        r = warp_sum(r);
+#pragma unroll 4
+        for (int cc = lane; cc < C; cc += 32) row[cc] = fma(-r, qv[cc], row[cc]);
       }
-      n2 = warp_sum(n2);
+      // downdate; the whole warp takes the same branch (r and nrm[i] are uniform)
+      double n2 = nrm[i] - r * r;
+      if (!(n2 > 1e-8 * ref[i])) {
+        __syncwarp();
+        n2 = 0.0;
+        for (int cc = lane; cc < C; cc += 32) n2 = fma(row[cc], row[cc], n2);
+        n2 = warp_sum(n2);
+        if (lane == 0) ref[i] = n2;
+      }
+      __syncwarp();
       if (lane == 0) {
         J.Rf[(int64_t)t * m + c.r0 + i] = r;
         nrm[i] = n2;
@@ -645,7 +773,8 @@ struct sk_hss {
   void* host_pin = nullptr;
   size_t host_cap = 0;
   int64_t launches = 0;
-  int max_ncl = 8;
+  int max_ncl_test = 8, max_ncl_id = 8;
+  size_t test_smem16 = 0, id_smem16 = 0;  // shared memory a 16-CTA cluster of each kernel may take
   // device time per kind of work, from events around every launch
   struct Span { cudaEvent_t a, b; int cat; };
   std::vector<Span> spans;
@@ -774,10 +903,10 @@ int run_gathers(sk_hss* H, std::vector<GatherJob>& jobs, cudaStream_t s) {
 // Cluster size for a launch over `nodes` nodes of up to mmax rows: the
 // largest power of two that keeps nodes x ncl within the SMs and 32 rows per
 // CTA, at most max_ncl.
-int pick_ncl(const sk_hss* H, int nodes, int mmax) {
+int pick_ncl(int max_ncl, int nodes, int mmax) {
   const int sms = num_sms();
   int ncl = 1;
-  while (ncl < H->max_ncl && nodes * ncl * 2 <= sms && mmax >= 32 * ncl * 2) ncl *= 2;
+  while (ncl < max_ncl && nodes * ncl * 2 <= sms && mmax >= 32 * ncl * 2) ncl *= 2;
   return ncl;
 }
 
@@ -800,18 +929,14 @@ int launch_cl(void (*kern)(KArgs...), unsigned nodes, int ncl, size_t smem, cuda
   return SK_OK;
 }
 
-// Opt in to the shared memory and cluster sizes of the per-node kernels;
-// clusters of 16 where the device can place one, else 8.
-int kernel_setup(sk_hss* H) {
-  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TEST_SMEM));
-  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ID_SMEM));
-  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  H->max_ncl = 8;
+// Opt in to the shared memory and cluster sizes of the per-node kernels:
+// clusters of 16 where the device can place one (with the kernel's shared
+// memory, or with smaller row caches), else 8.
+bool cluster16_fits(const void* kern, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16);
   cfg.blockDim = dim3(HT);
-  cfg.dynamicSmemBytes = std::max(TEST_SMEM, ID_SMEM);
+  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 16;
@@ -819,11 +944,33 @@ int kernel_setup(sk_hss* H) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int n1 = 0, n2 = 0;
-  if (cudaOccupancyMaxActiveClusters(&n1, hss_test_kernel, &cfg) == cudaSuccess &&
-      cudaOccupancyMaxActiveClusters(&n2, hss_id_kernel, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
-    H->max_ncl = 16;
+  int n = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
   cudaGetLastError();
+  return ok;
+}
+
+int kernel_setup(sk_hss* H) {
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TEST_SMEM_MAX));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ID_SMEM_MAX));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_test_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  JLS_CHECK_CUDA(cudaFuncSetAttribute(hss_id_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  // the largest shared memory (of 220 / 200, 118, 64 KB) at which a 16-CTA
+  // cluster of each kernel fits, else clusters of 8
+  const size_t tries_test[3] = {TEST_SMEM_MAX, 118 * 1024, 64 * 1024};
+  const size_t tries_id[3] = {ID_SMEM_MAX, 118 * 1024, 64 * 1024};
+  H->max_ncl_test = H->max_ncl_id = 8;
+  H->test_smem16 = H->id_smem16 = 0;
+  for (size_t b : tries_test)
+    if (H->test_smem16 == 0 && cluster16_fits((const void*)hss_test_kernel, b)) {
+      H->max_ncl_test = 16;
+      H->test_smem16 = b;
+    }
+  for (size_t b : tries_id)
+    if (H->id_smem16 == 0 && cluster16_fits((const void*)hss_id_kernel, b)) {
+      H->max_ncl_id = 16;
+      H->id_smem16 = b;
+    }
   return SK_OK;
 }
 
@@ -952,10 +1099,16 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       TestOut* outs = nullptr;
       JLS_CHECK(take(H->scratch, tj.size(), &outs));
       const int sp = span_begin(H, s);
-      int mmax = 0;
-      for (const TestJob& t : tj) mmax = std::max(mmax, t.m);
-      JLS_CHECK(launch_cl(hss_test_kernel, (unsigned)tj.size(), pick_ncl(H, (int)tj.size(), mmax), TEST_SMEM, s,
-                          static_cast<const TestJob*>(H->jobs_dev), outs));
+      int mmax = 0, qx = 0;
+      for (const TestJob& t : tj) {
+        mmax = std::max(mmax, t.m);
+        qx = std::max(qx, (t.q < 0 ? std::min(t.m, d) : t.q) + dd);
+      }
+      const int ncl = pick_ncl(H->max_ncl_test, (int)tj.size(), mmax);
+      TestLayout lay{(mmax + ncl - 1) / ncl, qx, 1};
+      if (test_smem_bytes(lay) > (ncl == 16 ? H->test_smem16 : TEST_SMEM_MAX)) lay.qsm = 0;
+      JLS_CHECK(launch_cl(hss_test_kernel, (unsigned)tj.size(), ncl, test_smem_bytes(lay), s,
+                          static_cast<const TestJob*>(H->jobs_dev), outs, lay));
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<TestOut> ho(tj.size());
@@ -1016,8 +1169,11 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       const int sp = span_begin(H, s);
       int mmax = 0;
       for (const IdJob& t : ij) mmax = std::max(mmax, t.m);
-      JLS_CHECK(launch_cl(hss_id_kernel, (unsigned)ij.size(), pick_ncl(H, (int)ij.size(), mmax), ID_SMEM, s,
-                          static_cast<const IdJob*>(H->jobs_dev), ranks));
+      const int ncl = pick_ncl(H->max_ncl_id, (int)ij.size(), mmax);
+      IdLayout lay{C, (mmax + ncl - 1) / ncl, std::min(mmax, C), 1};
+      if (id_smem_bytes(lay) > (ncl == 16 ? H->id_smem16 : ID_SMEM_MAX)) lay.wsm = 0;
+      JLS_CHECK(launch_cl(hss_id_kernel, (unsigned)ij.size(), ncl, id_smem_bytes(lay), s,
+                          static_cast<const IdJob*>(H->jobs_dev), ranks, lay));
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<int32_t> hk(ij.size());
