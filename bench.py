@@ -240,9 +240,9 @@ def cpu_baseline(X, Y, S_gpu, rows_per_product, seed):
                 seconds=dt), errs
 
 
-def traffic_from_profile(kernel_file):
+def traffic_from_profile(kernel_file, record="sjlt_traffic.json.txt"):
     """dram bytes per launch recorded in profiles/ for the current source, else None."""
-    p = os.path.join(ROOT, "profiles", "sjlt_traffic.json.txt")
+    p = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(p):
         return None
     try:
@@ -370,7 +370,8 @@ def run_ours(args):
     tc_route = sjlt_routes["St" if sj == "sjlt_cols" else "S"] == 1
     if tc_route:
         kname = "tc_sketch_kernel (SJLT " + ("S' = A^T R" if sj == "sjlt_cols" else "S = A R") + ", +-1 product)"
-        traffic = None  # the profile's counters are of the SJLT kernels
+        tcp = traffic_from_profile("gemm_tc.cu", "tc_traffic.json.txt")  # the tensor-core kernel's counters
+        traffic = tcp.get("cols_bytes_per_launch" if sj == "sjlt_cols" else "rows_bytes_per_launch") if tcp else None
     else:
         kname = "sjlt_cols_kernel (S' = A^T R)" if sj == "sjlt_cols" else "sjlt_rows_kernel (S = A R)"
     roofline = {"kernel": kname,
