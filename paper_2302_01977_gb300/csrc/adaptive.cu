@@ -120,10 +120,20 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// out[e] = sum of the chunks' partials, added in chunk order; the loads of
+// eight chunks are issued before they are added (the sums' order is unchanged).
 __global__ void reduce_partials(const double* __restrict__ part, int nchunks, int64_t count, double* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     double s = 0;
-    for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * count + e];
+    int c = 0;
+    for (; c + 8 <= nchunks; c += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(c + u) * count + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; c < nchunks; ++c) s += part[(int64_t)c * count + e];
     out[e] = s;
   }
 }
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
 // row, with rinv[j] = 1 / L[j][j] (0 for a dropped column, whose x_j is then 0).
 // trsm_rows<T>() rows per CTA, staged through shared memory with coalesced accesses.
 template <typename T>
-constexpr int trsm_rows() {
+__host__ __device__ constexpr int trsm_rows() {
   return sizeof(T) == 4 ? 64 : 16;
 }
 template <typename T>
@@ -393,11 +403,13 @@ __global__ void __launch_bounds__(trsm_rows<T>()) rows_trsm_kernel(T* W, int64_t
   __shared__ T rv[64];
   __shared__ T ws[RT][65];
   const int64_t r0 = (int64_t)blockIdx.x * RT;
+#pragma unroll 8
   for (int e = threadIdx.x; e < 64 * 64; e += RT) {
     const int j = e >> 6, i = e & 63;
     ls[j][i] = (j < b && i < b) ? Lo[j * b + i] : T(0);
   }
   for (int j = threadIdx.x; j < 64; j += RT) rv[j] = j < b ? rinv[j] : T(0);
+#pragma unroll 8
   for (int e = threadIdx.x; e < RT * 64; e += RT) {
     const int rr = e >> 6, j = e & 63;
     const int64_t r = r0 + rr;
@@ -638,7 +650,8 @@ int tsgemm(const T* X, int64_t ldx, int p, const T* Y, int64_t ldy, int q, int64
   const int nch = (int)((rows + rpc - 1) / rpc);
   dim3 grid((p + 63) / 64, (q + 63) / 64, nch);
   tsgemm_tn_partial<T><<<grid, 256, 0, s>>>(X, ldx, p, Y, ldy, q, rows, rpc, part); note_launch();
-  reduce_partials<<<64, 256, 0, s>>>(part, nch, (int64_t)p * q, out); note_launch();
+  const unsigned rgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * num_sms(), ((int64_t)p * q + 255) / 256));
+  reduce_partials<<<rgrid, 256, 0, s>>>(part, nch, (int64_t)p * q, out); note_launch();
   JLS_CHECK_CUDA(cudaGetLastError());
   return SK_OK;
 }
