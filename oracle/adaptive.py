@@ -42,7 +42,7 @@ def project_twice(Q: np.ndarray, B: np.ndarray) -> np.ndarray:
 def range_basis(M: np.ndarray) -> np.ndarray:
     """Orthonormal basis of the range of M: its left singular vectors whose
     singular values exceed sigma_1 max(M.shape) eps (FP64)."""
-    if M.shape[1] == 0:
+    if M.shape[0] == 0 or M.shape[1] == 0:  # an empty matrix has an empty range
         return np.zeros((M.shape[0], 0))
     U, sv, _ = np.linalg.svd(M, full_matrices=False)
     if sv[0] == 0.0:
