@@ -19,10 +19,12 @@ The same line carries, measured in the same run on rank 0 at N = 1 (skip with
 --no-extra), the precision comparison (key "precision": the Gaussian S = A R
 of the 65536 x 65536 FP32 kernel matrix at d = 512 on FP32 CUDA cores, as a
 bf16 hi+lo split and in scaled FP8 on the tensor cores, each error on 4096
-sampled rows) and the differentiation workload (key "differentiation": the
+sampled rows), the differentiation workload (key "differentiation": the
 matrix-free S = K(X, X; h) R of 262144 points and its adjoint, against the
 explicit-K path, with their ALU rooflines and the FP64 oracle gradient timed
-on a 4096-point problem as their CPU baseline).
+on a 4096-point problem as their CPU baseline) and the per-node adaptive loop
+of Algorithm 1 (key "hss": the n = 2048 FP64 kernel matrix, leaf 64, whole
+compressions, with the FP64 oracle's time as its CPU baseline).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores.  Under torchrun every rank runs an independent
@@ -465,6 +467,8 @@ def run_ours(args):
         line["precision"] = precision_measure(args)
         torch.cuda.empty_cache()
         line["differentiation"] = differentiation_measure(args)
+        torch.cuda.empty_cache()
+        line["hss"] = hss_measure(args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -1340,7 +1344,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the precision (n = 65536) and differentiation (n = 262144) sections of the default run")
+                    help="skip the precision (n = 65536), differentiation (n = 262144) and per-node HSS (n = 2048) "
+                         "sections of the default run")
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--n", type=int, default=WORKLOAD["n"],
