@@ -289,6 +289,65 @@ __device__ void project2(Cl& c, const double* __restrict__ Qb, int64_t ld, int c
   }
 }
 
+// The same two passes for g <= 8 columns at once (independent columns, all
+// against the same q columns of Q): wg holds them at stride wld; one cluster
+// sum per pass serves all g columns (h: g x q coefficients).
+constexpr int GMAX = 8;
+__device__ void project2_group(Cl& c, const double* __restrict__ Qb, int64_t ld, int q, double* wg, int wld, int g,
+                               double* h) {
+  const int nw = blockDim.x / 32, wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mr = c.r1 - c.r0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* part = c.hp + c.par * HPS;
+    for (int j0 = 4 * wid; j0 < q; j0 += 4 * nw) {
+      const int nj = min(4, q - j0);
+      const double* qc = Qb + (int64_t)j0 * ld;
+      double sacc[4][GMAX];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < GMAX; ++u) sacc[a][u] = 0.0;
+      for (int i = lane; i < mr; i += 32) {
+        double qv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) qv[a] = a < nj ? qc[a * ld + i] : 0.0;
+#pragma unroll
+        for (int u = 0; u < GMAX; ++u) {
+          if (u < g) {
+            const double wv = wg[u * wld + i];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sacc[a][u] = fma(qv[a], wv, sacc[a][u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < GMAX; ++u)
+          if (a < nj && u < g) {  // uniform over the warp
+            const double v = warp_sum(sacc[a][u]);
+            if (lane == 0) part[u * q + j0 + a] = v;
+          }
+    }
+    cl_finish(c, g * q, h);
+    // w_u -= Q h_u over (row, column) pairs, 8 loads in flight per thread
+    for (int pr = threadIdx.x; pr < mr * g; pr += blockDim.x) {
+      const int i = pr % mr, u = pr / mr;
+      const double* hu = h + u * q;
+      const double* qi = Qb + i;
+      double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int j = 0;
+      for (; j + 8 <= q; j += 8) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v) a[v] = fma(qi[(int64_t)(j + v) * ld], hu[j + v], a[v]);
+      }
+      for (; j < q; ++j) a[0] = fma(qi[(int64_t)j * ld], hu[j], a[0]);
+      wg[u * wld + i] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ void cl_rows(Cl& c, int m) {
   const cg::cluster_group cl = cg::this_cluster();
   c.ncl = (int)cl.num_blocks();
@@ -320,9 +379,10 @@ struct TestOut {
 // fit (qsm).
 struct TestLayout {
   int mrx, qx, qsm;
+  int gw;  // columns of the tested block projected together (the w buffer holds gw x mrx)
 };
 __host__ __device__ inline size_t test_smem_bytes(const TestLayout& L) {
-  return sizeof(double) * ((size_t)L.mrx + 3 * HPS + 40 + (size_t)(L.mrx > HT ? L.mrx : HT) +
+  return sizeof(double) * ((size_t)L.gw * L.mrx + 3 * HPS + 40 + (size_t)(L.mrx > HT ? L.mrx : HT) +
                            (L.qsm ? (size_t)L.mrx * L.qx : 0));
 }
 constexpr size_t TEST_SMEM_MAX = 220 * 1024;
@@ -335,8 +395,8 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
   const int m = J.m;
   Cl c;
   cl_rows(c, m);
-  double* w = sm;                   // this CTA's rows
-  double* h = w + L.mrx;            // coefficients
+  double* w = sm;                   // this CTA's rows (gw columns of them for the tested block)
+  double* h = w + (size_t)L.gw * L.mrx;  // coefficients
   c.hp = h + HPS;                   // 2 partial slots
   c.red = c.hp + 2 * HPS;           // 33 + scalar out
   double* scal = c.red + 36;
@@ -405,22 +465,40 @@ __global__ void __launch_bounds__(HT) hss_test_kernel(const TestJob* __restrict_
     cl_sync();  // no CTA leaves while its partial slots may still be read
     return;
   }
-  // S~ = S_tau(:, d : d + dd), S^ = (I - Q Q^T)^2 S~ into Q(:, q : q + dd)
-  double nt2 = 0.0, nh2 = 0.0;
-  for (int jj = 0; jj < J.dd; ++jj) {
-    double c2 = 0.0;
-    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
-      const double v = J.S[(int64_t)(J.d + jj) * m + c.r0 + i];
-      w[i] = v;
-      c2 = fma(v, v, c2);
+  // S~ = S_tau(:, d : d + dd), S^ = (I - Q Q^T)^2 S~ into Q(:, q : q + dd): the columns are
+  // projected against the same Q, gw at a time; ||S~||^2 and ||S^||^2 are summed over this CTA's
+  // rows on the way and over the cluster once at the end
+  double nt2p = 0.0, nh2p = 0.0;
+  const int gq = q > 0 ? max(1, min(L.gw, HPS / q)) : L.gw;
+  for (int jj0 = 0; jj0 < J.dd; jj0 += gq) {
+    const int g = min(gq, J.dd - jj0);
+    for (int pr = threadIdx.x; pr < mr * g; pr += blockDim.x) {
+      const int i = pr % mr, u = pr / mr;
+      const double v = J.S[(int64_t)(J.d + jj0 + u) * m + c.r0 + i];
+      w[u * L.mrx + i] = v;
+      nt2p = fma(v, v, nt2p);
     }
-    nt2 += cl_sum(c, c2, scal);
-    if (q > 0) project2(c, Qb, ldb, 0, q, w, h, gp);
-    double r2 = 0.0;
-    for (int i = threadIdx.x; i < mr; i += blockDim.x) r2 = fma(w[i], w[i], r2);
-    put_col(q + jj, 1.0);
-    nh2 += cl_sum(c, r2, scal);
+    __syncthreads();
+    if (q > 0) project2_group(c, Qb, ldb, q, w, L.mrx, g, h);
+    for (int pr = threadIdx.x; pr < mr * g; pr += blockDim.x) {
+      const int i = pr % mr, u = pr / mr;
+      const double v = w[u * L.mrx + i];
+      nh2p = fma(v, v, nh2p);
+      J.Q[(int64_t)(q + jj0 + u) * m + c.r0 + i] = v;
+      if (L.qsm) Qs[(int64_t)(q + jj0 + u) * L.mrx + i] = v;
+    }
+    __syncthreads();
   }
+  {
+    const double t2 = block_sum(nt2p, c.red);
+    const double h2 = block_sum(nh2p, c.red);
+    if (threadIdx.x == 0) {
+      c.hp[c.par * HPS] = t2;
+      c.hp[c.par * HPS + 1] = h2;
+    }
+    cl_finish(c, 2, scal);
+  }
+  const double nt2 = scal[0], nh2 = scal[1];
   const double nh = sqrt(nh2), nt = sqrt(nt2);
   int outcome = 0;
   double mind = 0.0;
@@ -1105,7 +1183,8 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
         qx = std::max(qx, (t.q < 0 ? std::min(t.m, d) : t.q) + dd);
       }
       const int ncl = pick_ncl(H->max_ncl_test, (int)tj.size(), mmax);
-      TestLayout lay{(mmax + ncl - 1) / ncl, qx, 1};
+      const int mrx = (mmax + ncl - 1) / ncl;
+      TestLayout lay{mrx, qx, 1, std::max(1, std::min(GMAX, 4096 / std::max(1, mrx)))};
       if (test_smem_bytes(lay) > (ncl == 16 ? H->test_smem16 : TEST_SMEM_MAX)) lay.qsm = 0;
       JLS_CHECK(launch_cl(hss_test_kernel, (unsigned)tj.size(), ncl, test_smem_bytes(lay), s,
                           static_cast<const TestJob*>(H->jobs_dev), outs, lay));
