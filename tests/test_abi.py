@@ -151,3 +151,47 @@ def test_create_flags_argument_checks(L):
     assert L.sketch_create_flags(ctypes.byref(h), jl.SK_SRHT, 64, 16, 1, 1, 16, 4, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_create_flags(ctypes.byref(h), jl.SK_SRHT, 64, 16, 1, 1, 80, 0, None) == jl.SK_ERR_INVALID_ARG
     assert L.sketch_create_flags(None, jl.SK_SRHT, 64, 16, 1, 1, 16, 0, None) == jl.SK_ERR_INVALID_ARG
+
+
+def test_hss_argument_checks(L):
+    """hss_compress_adaptive refuses bad sizes, tolerances and alignment before it touches a device."""
+    h = ctypes.c_void_p()
+    A = ctypes.c_void_p(1 << 20)  # never dereferenced: every case below is refused first
+    good = dict(n=512, lda=512, leaf=64, kind=jl.SK_GAUSS, d0=16, dd=16, alpha=1, d_max=64, er=1e-6, ea=0.0)
+    bad = [dict(n=0), dict(lda=100), dict(leaf=0), dict(leaf=5000), dict(d0=0), dict(dd=0), dict(d_max=16),
+           dict(d_max=4096), dict(d_max=63), dict(er=-1.0), dict(ea=float("nan"))]
+    for b in bad:
+        a = dict(good, **b)
+        rc = L.hss_compress_adaptive(ctypes.byref(h), A, a["n"], a["lda"], a["leaf"], a["kind"], a["d0"], a["dd"],
+                                     a["alpha"], 1, a["d_max"], a["er"], a["ea"], None)
+        assert rc == jl.SK_ERR_INVALID_ARG, b
+    a = good
+    assert L.hss_compress_adaptive(None, A, 512, 512, 64, jl.SK_GAUSS, 16, 16, 1, 1, 64, 1e-6, 0.0,
+                                   None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_compress_adaptive(ctypes.byref(h), None, 512, 512, 64, jl.SK_GAUSS, 16, 16, 1, 1, 64, 1e-6, 0.0,
+                                   None) == jl.SK_ERR_INVALID_ARG
+    # A not 16-byte aligned, or a leading dimension whose rows are not
+    assert L.hss_compress_adaptive(ctypes.byref(h), ctypes.c_void_p((1 << 20) + 8), 512, 512, 64, jl.SK_GAUSS, 16,
+                                   16, 1, 1, 64, 1e-6, 0.0, None) == jl.SK_ERR_ALIGN
+    assert L.hss_compress_adaptive(ctypes.byref(h), A, 512, 513, 64, jl.SK_GAUSS, 16, 16, 1, 1, 64, 1e-6, 0.0,
+                                   None) == jl.SK_ERR_ALIGN
+
+
+def test_hss_null_handle_calls(L):
+    i32 = ctypes.c_int32()
+    assert L.hss_info(None, ctypes.byref(i32), None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_node(None, 0, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_node_get(None, 0, jl.SK_HSS_U, ctypes.c_void_p(1 << 20)) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_history(None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_profile(None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_launch_count(None) == 0
+    L.hss_destroy(None)  # no-op
+
+
+def test_hss_no_gpu_fails_loudly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert L.hss_compress_adaptive(ctypes.byref(h), ctypes.c_void_p(1 << 20), 512, 512, 64, jl.SK_GAUSS, 16, 16, 1,
+                                   1, 64, 1e-6, 0.0, None) == jl.SK_ERR_DEVICE
