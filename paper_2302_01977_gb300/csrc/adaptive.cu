@@ -324,6 +324,31 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const double* __restri
   __shared__ A s_dmax, s_floor;
   __shared__ A s_colfloor[64];  // tau_col times each column's sum of squares before the projection
   const int tid = threadIdx.x;
+  if constexpr (sizeof(A) == 4) {
+    // The FP32 factor is the second Cholesky-QR pass's: its Gram matrix is the
+    // identity up to the first pass's rounding, G = I + E.  When max |E| <=
+    // 1e-4, L = chol(G) is L_ij = G_ij / sqrt(G_jj) below the diagonal and
+    // sqrt(G_ii) on it up to terms of order |E|^2 (below FP32 rounding), every
+    // pivot is near 1 (no drop applies), and the factor is formed at once
+    // instead of in b dependent steps.
+    __shared__ int s_near;
+    double dev = 0.0;
+    for (int e = tid; e < b * b; e += 256) dev = fmax(dev, fabs(Gm[e] - (e / b == e % b ? 1.0 : 0.0)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if (tid == 0) s_near = 1;
+    __syncthreads();
+    if ((tid & 31) == 0 && !(dev <= 1e-4)) s_near = 0;
+    __syncthreads();
+    if (s_near && !colpart && floor_abs < 0.5 && nref == 0) {
+      for (int e = tid; e < b * b; e += 256) {
+        const int i = e / b, j = e % b;
+        Lo[e] = j < i ? (T)((A)Gm[e] / sqrtf((A)Gm[j * b + j])) : j == i ? (T)sqrtf((A)Gm[e]) : T(0);
+      }
+      if (tid < b) rinv_out[tid] = (T)(1.0f / sqrtf((A)Gm[tid * b + tid]));
+      return;
+    }
+  }
   for (int e = tid; e < b * b; e += 256) L[e / b][e % b] = (A)Gm[e];
   if (tid < 64) {
     double v = 0.0;
