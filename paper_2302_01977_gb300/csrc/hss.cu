@@ -14,8 +14,9 @@
 // Per node tau (m rows of the local sketch, k = rank after compression):
 //   S_tau  m x d_max, column-major          local sketch (leaf: S(I, iota) - D R(I, iota);
 //                                            internal: [S_nu1(J_nu1) - B R_nu2; S_nu2(J_nu2) - B^T R_nu1])
-//   Q_tau  m x (min(m, d_max) + Delta-d)    orthonormal basis of the tested columns' range
-//   U_tau  m x k, column-major              row interpolative decomposition S_tau ~ U_tau S_tau(J_tau, :)
+//   Q_tau  m x (min(m, d_max) + Delta-d),   orthonormal basis of the tested columns' range
+//          column-major
+//   U_tau  m x k, row-major                 row interpolative decomposition S_tau ~ U_tau S_tau(J_tau, :)
 //   J_tau  k positions in 0..m-1;  I~_tau  k global indices
 //   R_tau  k x d_max, column-major          U_tau^T R(I_tau) (leaf) or U_tau^T [R_nu1; R_nu2]
 //   D_tau  (leaf) m x m, B_tau (internal, root) k_nu1 x k_nu2, column-major, copied from A
