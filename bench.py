@@ -791,7 +791,8 @@ def hss_measure(args, w=None, cpu=True):
     kinds = jl.Hss.PROFILE_KINDS
     prof = {k: {"ms": round(statistics.median(p[k]["ms"] for p in profs), 3),
                 "gflop": round(profs[0][k]["flops"] / 1e9, 3),
-                "launches": profs[0][k]["launches"]} for k in kinds}
+                "launches": profs[0][k]["launches"],
+                "avg_sms": round(statistics.median(p[k]["avg_sms"] for p in profs), 1)} for k in kinds}
     for k in kinds:
         prof[k]["gflops"] = round(prof[k]["gflop"] / prof[k]["ms"] * 1e3, 1) if prof[k]["ms"] > 0 else None
     dev_ms = sum(prof[k]["ms"] for k in kinds)
@@ -809,7 +810,12 @@ def hss_measure(args, w=None, cpu=True):
            "roofline": {"kernel": top, "bound": "alu", "unit": "GFLOP/s",
                         "achieved": prof[top]["gflops"], "peak": FP64_NOMINAL_GFLOPS,
                         "frac": round((prof[top]["gflops"] or 0) / FP64_NOMINAL_GFLOPS, 4),
-                        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)", "traffic": None},
+                        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)", "traffic": None,
+                        # the same rate against the FP64 peak of the SMs the kernel's clusters held
+                        "avg_sms_held": prof[top]["avg_sms"],
+                        "frac_of_held_sms": round((prof[top]["gflops"] or 0) / (FP64_NOMINAL_GFLOPS * max(
+                            prof[top]["avg_sms"], 1e-9) / torch.cuda.get_device_properties(0).multi_processor_count),
+                            4)},
            "clocks": ck}
     if cpu and not args.no_cpu_baseline:
         from oracle import hss as ohss

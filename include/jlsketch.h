@@ -689,16 +689,18 @@ int hss_history(sk_hss_handle h, int32_t* ints, double* reals);
 int64_t hss_launch_count(sk_hss_handle h);
 
 /* hss_profile -- device time (ms, from CUDA events on the stream around each
- * launch), algorithmic FP64 FLOPs and launches per kind of work, host arrays
- * of 6 entries each (any may be NULL):
+ * launch), algorithmic FP64 FLOPs, launches and SM-milliseconds (the SMs a
+ * launch's grid occupies, at most one CTA per SM counted, times its ms) per
+ * kind of work, host arrays of 6 entries each (any may be NULL):
  *   0 copies of D_tau and B_tau from A     1 local sketches (GEMM)
  *   2 stopping and rank tests              3 interpolative decompositions
  *   4 R_tau (GEMM)                         5 global sketch S = A R, its
  *                                            increments and R's dense copy
  * FLOPs: 2 M N K per GEMM; 8 m q per vector projected twice against q basis
- * columns; 6 C per remaining row and pivot step of a decomposition plus the
- * triangular solves; 2 n^2 per column of S (dense count, also for SJLT). */
-int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches);
+ * columns; 2 m C for a decomposition's row norms plus 4 C per remaining row and
+ * pivot step, plus the triangular solves; 2 n^2 per column of S (dense count,
+ * also for SJLT).  sm_ms / ms is the average number of SMs a kind of work held. */
+int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches, double* sm_ms);
 
 /* hss_destroy -- free the generators and scratch (NULL is a no-op). */
 void hss_destroy(sk_hss_handle h);

@@ -855,10 +855,11 @@ struct sk_hss {
   int max_ncl_test = 8, max_ncl_id = 8;
   size_t test_smem16 = 0, id_smem16 = 0;  // shared memory a 16-CTA cluster of each kernel may take
   // device time per kind of work, from events around every launch
-  struct Span { cudaEvent_t a, b; int cat; };
+  struct Span { cudaEvent_t a, b; int cat; int sms; };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> events;  // free events
   double ms[HSS_CATS] = {}, flops[HSS_CATS] = {};
+  double sm_ms[HSS_CATS] = {};  // SMs a launch's grid occupies (at most one CTA each) times its ms
   int64_t cat_launches[HSS_CATS] = {};
 };
 
@@ -902,16 +903,17 @@ cudaEvent_t take_event(sk_hss* H) {
 
 // Bracket work on s with events; span_end adds the algorithmic FLOPs.
 int span_begin(sk_hss* H, cudaStream_t s) {
-  sk_hss::Span sp{take_event(H), take_event(H), -1};
+  sk_hss::Span sp{take_event(H), take_event(H), -1, 0};
   if (sp.a) cudaEventRecord(sp.a, s);
   H->spans.push_back(sp);
   return (int)H->spans.size() - 1;
 }
 
-void span_end(sk_hss* H, cudaStream_t s, int span, int cat, double flops, int launches) {
+void span_end(sk_hss* H, cudaStream_t s, int span, int cat, double flops, int launches, int64_t ctas = 0) {
   sk_hss::Span& sp = H->spans[span];
   if (sp.b) cudaEventRecord(sp.b, s);
   sp.cat = cat;
+  sp.sms = (int)std::min<int64_t>(ctas > 0 ? ctas : num_sms(), num_sms());
   H->flops[cat] += flops;
   H->cat_launches[cat] += launches;
 }
@@ -920,7 +922,10 @@ void span_end(sk_hss* H, cudaStream_t s, int span, int cat, double flops, int la
 void spans_collect(sk_hss* H) {
   for (sk_hss::Span& sp : H->spans) {
     float t = 0.f;
-    if (sp.a && sp.b && sp.cat >= 0 && cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) H->ms[sp.cat] += t;
+    if (sp.a && sp.b && sp.cat >= 0 && cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) {
+      H->ms[sp.cat] += t;
+      H->sm_ms[sp.cat] += (double)sp.sms * t;
+    }
     cudaGetLastError();
     if (sp.a) H->events.push_back(sp.a);
     if (sp.b) H->events.push_back(sp.b);
@@ -957,7 +962,7 @@ int run_gemms(sk_hss* H, std::vector<GemmJob>& jobs, cudaStream_t s, int cat) {
   JLS_CHECK(upload(H, live, s));
   const int sp = span_begin(H, s);
   hss_gemm_kernel<<<tiles, 256, 0, s>>>(static_cast<const GemmJob*>(H->jobs_dev), (int)live.size());
-  span_end(H, s, sp, cat, flops, 1);
+  span_end(H, s, sp, cat, flops, 1, tiles);
   note_launch();
   ++H->launches;
   JLS_CHECK_CUDA(cudaGetLastError());
@@ -972,7 +977,7 @@ int run_gathers(sk_hss* H, std::vector<GatherJob>& jobs, cudaStream_t s) {
   JLS_CHECK(upload(H, live, s));
   const int sp = span_begin(H, s);
   hss_gather_kernel<<<(unsigned)live.size(), 256, 0, s>>>(static_cast<const GatherJob*>(H->jobs_dev), H->A, H->lda);
-  span_end(H, s, sp, CAT_GATHER, 0.0, 1);
+  span_end(H, s, sp, CAT_GATHER, 0.0, 1, (int64_t)live.size());
   note_launch();
   ++H->launches;
   JLS_CHECK_CUDA(cudaGetLastError());
@@ -1189,6 +1194,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       if (test_smem_bytes(lay) > (ncl == 16 ? H->test_smem16 : TEST_SMEM_MAX)) lay.qsm = 0;
       JLS_CHECK(launch_cl(hss_test_kernel, (unsigned)tj.size(), ncl, test_smem_bytes(lay), s,
                           static_cast<const TestJob*>(H->jobs_dev), outs, lay));
+      const int64_t test_ctas = (int64_t)tj.size() * ncl;
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<TestOut> ho(tj.size());
@@ -1206,7 +1212,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
         tf += dd * (8.0 * m * q0 + 4.0 * m);
         if (ho[u].mind != 0.0 || ho[u].outcome != 0) tf += 8.0 * m * dd * (dd - 1) / 2.0 + 3.0 * m * dd;
       }
-      span_end(H, s, sp, CAT_TEST, tf, 1);
+      span_end(H, s, sp, CAT_TEST, tf, 1, test_ctas);
       for (size_t u = 0; u < tested.size(); ++u) {
         HssNode& nd = H->nodes[tested[u]];
         const TestOut& o = ho[u];
@@ -1254,19 +1260,21 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       if (id_smem_bytes(lay) > (ncl == 16 ? H->id_smem16 : ID_SMEM_MAX)) lay.wsm = 0;
       JLS_CHECK(launch_cl(hss_id_kernel, (unsigned)ij.size(), ncl, id_smem_bytes(lay), s,
                           static_cast<const IdJob*>(H->jobs_dev), ranks, lay));
+      const int64_t id_ctas = (int64_t)ij.size() * ncl;
       ++H->launches;
       JLS_CHECK_CUDA(cudaGetLastError());
       std::vector<int32_t> hk(ij.size());
       JLS_CHECK_CUDA(cudaMemcpyAsync(hk.data(), ranks, sizeof(int32_t) * hk.size(), cudaMemcpyDeviceToHost, s));
       JLS_CHECK_CUDA(cudaStreamSynchronize(s));
-      // algorithmic FLOPs: per pivot step a dot, an update and a norm over the
-      // remaining rows (6 (m - t) C), then the triangular solves (m - k) k^2
+      // algorithmic FLOPs: the row norms (2 m C), per pivot step a dot and an
+      // update over the remaining rows (4 (m - t) C), then the triangular
+      // solves (m - k) k^2
       double idf = 0.0;
       for (size_t u = 0; u < compress.size(); ++u) {
         const double m = ij[u].m, k = hk[u];
-        idf += 2.0 * m * C + 6.0 * C * (m * k - k * (k - 1) / 2.0) + (m - k) * k * k;
+        idf += 2.0 * m * C + 4.0 * C * (m * k - k * (k - 1) / 2.0) + (m - k) * k * k;
       }
-      span_end(H, s, sp, CAT_ID, idf, 1);
+      span_end(H, s, sp, CAT_ID, idf, 1, id_ctas);
       for (size_t u = 0; u < compress.size(); ++u) {
         HssNode& nd = H->nodes[compress[u]];
         nd.k = hk[u];
@@ -1451,9 +1459,10 @@ int hss_history(sk_hss_handle h, int32_t* ints, double* reals) {
 
 int64_t hss_launch_count(sk_hss_handle h) { return h ? h->launches : 0; }
 
-int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches) {
+int hss_profile(sk_hss_handle h, double* ms, double* flops, int64_t* launches, double* sm_ms) {
   if (!h) return SK_ERR_INVALID_ARG;
   for (int c = 0; c < HSS_CATS; ++c) {
+    if (sm_ms) sm_ms[c] = h->sm_ms[c];
     if (ms) ms[c] = h->ms[c];
     if (flops) flops[c] = h->flops[c];
     if (launches) launches[c] = h->cat_launches[c];

@@ -162,7 +162,7 @@ def lib() -> ctypes.CDLL:
         "hss_node_get": (i32, [vp, i32, i32, vp]),
         "hss_history": (i32, [vp, vp, vp]),
         "hss_launch_count": (i64, [vp]),
-        "hss_profile": (i32, [vp, vp, vp, vp]),
+        "hss_profile": (i32, [vp, vp, vp, vp, vp]),
         "hss_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -736,12 +736,15 @@ class Hss:
     PROFILE_KINDS = ("gather", "local_sketch", "test", "id", "r_tau", "global_sketch")
 
     def profile(self) -> dict:
-        """Per kind of work: device ms, algorithmic FP64 FLOPs, launches."""
+        """Per kind of work: device ms, algorithmic FP64 FLOPs, launches, average SMs held."""
         ms = np.zeros(6)
         fl = np.zeros(6)
         ln = np.zeros(6, dtype=np.int64)
-        _check(lib().hss_profile(self.h, ms.ctypes.data, fl.ctypes.data, ln.ctypes.data), "hss_profile")
-        return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(ln[i]))
+        sm = np.zeros(6)
+        _check(lib().hss_profile(self.h, ms.ctypes.data, fl.ctypes.data, ln.ctypes.data, sm.ctypes.data),
+               "hss_profile")
+        return {k: dict(ms=float(ms[i]), flops=float(fl[i]), launches=int(ln[i]),
+                        avg_sms=float(sm[i] / ms[i]) if ms[i] > 0 else 0.0)
                 for i, k in enumerate(self.PROFILE_KINDS)}
 
     def close(self):

@@ -183,7 +183,7 @@ def test_hss_null_handle_calls(L):
     assert L.hss_node(None, 0, None, None) == jl.SK_ERR_INVALID_ARG
     assert L.hss_node_get(None, 0, jl.SK_HSS_U, ctypes.c_void_p(1 << 20)) == jl.SK_ERR_INVALID_ARG
     assert L.hss_history(None, None, None) == jl.SK_ERR_INVALID_ARG
-    assert L.hss_profile(None, None, None, None) == jl.SK_ERR_INVALID_ARG
+    assert L.hss_profile(None, None, None, None, None) == jl.SK_ERR_INVALID_ARG
     assert L.hss_launch_count(None) == 0
     L.hss_destroy(None)  # no-op
 
