@@ -168,6 +168,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Sum over each half of the warp (lanes 0..15 and 16..31 separately).
+__device__ __forceinline__ double half_sum(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Sum over the CTA; every thread gets the result.  red: >= 33 doubles.
 __device__ double block_sum(double v, double* red) {
@@ -238,23 +244,29 @@ __device__ void project2(Cl& c, const double* __restrict__ Qb, int64_t ld, int c
     double* part = c.hp + c.par * HPS;
     // Q^T w: a warp takes 4 columns at a time, so that each lane has 4
     // (times the unrolled rows) independent loads in flight
-    for (int j0 = c_lo + 4 * wid; j0 < c_hi; j0 += 4 * nw) {
-      const int nj = min(4, c_hi - j0);
+    // each half-warp takes a quad of columns, its 16 lanes over the rows
+    // (rows come in 16s, so few lanes idle when a CTA holds a few dozen rows)
+    const int hw = lane >> 4, hl = lane & 15;
+    for (int jb = c_lo + 8 * wid; jb < c_hi; jb += 8 * nw) {
+      const int j0 = jb + 4 * hw;
+      const int nj = max(0, min(4, c_hi - j0));
       const double* q = Qb + (int64_t)j0 * ld;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      if (nj > 0) {
 #pragma unroll 2
-      for (int i = lane; i < mr; i += 32) {
-        const double wi = w[i];
-        s0 = fma(q[i], wi, s0);
-        if (nj > 1) s1 = fma(q[ld + i], wi, s1);
-        if (nj > 2) s2 = fma(q[2 * ld + i], wi, s2);
-        if (nj > 3) s3 = fma(q[3 * ld + i], wi, s3);
+        for (int i = hl; i < mr; i += 16) {
+          const double wi = w[i];
+          s0 = fma(q[i], wi, s0);
+          if (nj > 1) s1 = fma(q[ld + i], wi, s1);
+          if (nj > 2) s2 = fma(q[2 * ld + i], wi, s2);
+          if (nj > 3) s3 = fma(q[3 * ld + i], wi, s3);
+        }
       }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
-      s2 = warp_sum(s2);
-      s3 = warp_sum(s3);
-      if (lane == 0) {
+      s0 = half_sum(s0);
+      s1 = half_sum(s1);
+      s2 = half_sum(s2);
+      s3 = half_sum(s3);
+      if (hl == 0 && nj > 0) {
         part[j0 - c_lo] = s0;
         if (nj > 1) part[j0 + 1 - c_lo] = s1;
         if (nj > 2) part[j0 + 2 - c_lo] = s2;
@@ -300,15 +312,17 @@ __device__ void project2_group(Cl& c, const double* __restrict__ Qb, int64_t ld,
   const int mr = c.r1 - c.r0;
   for (int pass = 0; pass < 2; ++pass) {
     double* part = c.hp + c.par * HPS;
-    for (int j0 = 4 * wid; j0 < q; j0 += 4 * nw) {
-      const int nj = min(4, q - j0);
+    const int hw = lane >> 4, hl = lane & 15;
+    for (int jb = 8 * wid; jb < q; jb += 8 * nw) {  // a half-warp per quad of columns
+      const int j0 = jb + 4 * hw;
+      const int nj = max(0, min(4, q - j0));
       const double* qc = Qb + (int64_t)j0 * ld;
       double sacc[4][GMAX];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int u = 0; u < GMAX; ++u) sacc[a][u] = 0.0;
-      for (int i = lane; i < mr; i += 32) {
+      for (int i = hl; i < mr && nj > 0; i += 16) {
         double qv[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) qv[a] = a < nj ? qc[a * ld + i] : 0.0;
@@ -325,9 +339,9 @@ __device__ void project2_group(Cl& c, const double* __restrict__ Qb, int64_t ld,
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int u = 0; u < GMAX; ++u)
-          if (a < nj && u < g) {  // uniform over the warp
-            const double v = warp_sum(sacc[a][u]);
-            if (lane == 0) part[u * q + j0 + a] = v;
+          if (u < g) {  // uniform over the warp
+            const double v = half_sum(sacc[a][u]);
+            if (hl == 0 && a < nj) part[u * q + j0 + a] = v;
           }
     }
     cl_finish(c, g * q, h);
