@@ -33,7 +33,9 @@
 // accumulation chain covers more than FOLD * 64 values of K.
 //
 // Warp roles (22 warps, one CTA per SM):
-//   warp 0       TMA producer for the B planes (one elected lane)
+//   warp 0       TMA producer for the B planes (one elected lane); the same
+//                lane asks L2 for the A tile of the unit pf_dist units ahead,
+//                so that the converters' loads find it there
 //   warp 1       TMEM allocation; one lane issues tcgen05.mma and commits
 //   warps 2..17  converters: load FP32 A (coalesced, two K stages ahead in a
 //                ring of three register buffers), split, write bf16 tiles
@@ -44,6 +46,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -205,8 +208,9 @@ struct Converter {
 template <bool TRANS, int PLANES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_sketch_kernel(const float* __restrict__ A, int64_t lda, const __grid_constant__ CUtensorMap tmB0,
-                     const __grid_constant__ CUtensorMap tmB1, const TcWork w, float scale, float* __restrict__ out,
-                     int64_t ldo, int vec_ok, int* err) {
+                     const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmA,
+                     const TcWork w, float scale, float* __restrict__ out, int64_t ldo, int vec_ok, int pf_dist,
+                     int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -250,13 +254,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       tma_prefetch_desc(&tmB0);
       if (PLANES == 2) tma_prefetch_desc(&tmB1);
+      if (pf_dist > 0) tma_prefetch_desc(&tmA);
       const uint32_t b_bytes = (uint32_t)PLANES * (uint32_t)w.nt * 128u;
+      // A tiles into L2 ahead of the converters: units [0, pf_dist) now, unit i + pf_dist at unit i
+      Cursor pc;
+      pc.init(w, u0);
+      int pf = 0;
+      auto prefetch_a = [&]() {
+        if (TRANS) tma_prefetch_l2_2d(&tmA, (int32_t)(pc.mt * TC_BM), pc.ks * TC_BK);
+        else tma_prefetch_l2_2d(&tmA, pc.ks * TC_BK, (int32_t)(pc.mt * TC_BM));
+        pc.next(w);
+        ++pf;
+      };
+      while (pf < min(pf_dist, cnt)) prefetch_a();
       Cursor c;
       c.init(w, u0);
       Ring rg;
       int issued = 0;
       for (int i = 0; i < cnt; ++i, c.next(w), rg.next(w.stages)) {
         if (*abort_flag) break;
+        if (pf_dist > 0 && pf < cnt) prefetch_a();
         if (!mbar_wait(empty(rg.s), rg.ph ^ 1u, err)) {
           *abort_flag = 1;
           break;
@@ -422,6 +439,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 namespace {
 
+// A as FP32 tiles of one unit (128 rows x 64 of K for S, 64 of K x 128 columns
+// for S'), used only for L2 prefetches.  Returns false when A's address or
+// row pitch does not meet the tensor map's 16-byte rules.
+bool encode_a(CUtensorMap* tm, const sk_matrix* A, bool trans) {
+  PFN_encodeTiled enc = get_encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(A->A) & 15) != 0 || (A->ld * 4) % 16 != 0) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)A->cols, (cuuint64_t)A->rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)(A->ld * 4)};
+  const cuuint32_t box[2] = {(cuuint32_t)(trans ? TC_BM : TC_BK), (cuuint32_t)(trans ? TC_BK : TC_BM)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(A->A), gdim, gstride, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Units of A prefetched into L2 ahead of the converters (JLS_TC_PREFETCH
+// overrides; 0 turns the prefetch off).
+int tc_prefetch_units() {
+  static int v = [] {
+    const char* e = std::getenv("JLS_TC_PREFETCH");
+    return e ? std::max(0, std::min(64, std::atoi(e))) : 3;
+  }();
+  return v;
+}
+
 int encode_plane(CUtensorMap* tm, const uint16_t* plane, int64_t n, int rows, int nt) {
   PFN_encodeTiled enc = get_encode_tiled();
   if (!enc) return SK_ERR_DEVICE;
@@ -459,9 +501,11 @@ int launch_tc_planes(int* d_err, const sk_matrix* A, bool trans, int planes, con
   w.tmem_cols = tmem_cols_for(TC_FOLD > 0 ? 2 * w.nt : w.nt);
   if (w.tmem_cols > 512) return SK_ERR_UNSUPPORTED;
 
-  CUtensorMap t0, t1;
+  CUtensorMap t0, t1, ta;
   JLS_CHECK(encode_plane(&t0, p0, k_len, c_hi, w.nt));
   JLS_CHECK(encode_plane(&t1, p1, k_len, c_hi, w.nt));
+  const int pf_dist = encode_a(&ta, A, trans) ? tc_prefetch_units() : 0;
+  if (pf_dist == 0) ta = t0;  // never read
   JLS_CHECK_CUDA(cudaMemset2DAsync(out + c_lo, ldo * sizeof(float), 0, (size_t)ncols * sizeof(float),
                                    (size_t)w.m_rows, s));
   const int64_t tiles = (int64_t)ntiles * w.mtiles;
@@ -473,7 +517,7 @@ int launch_tc_planes(int* d_err, const sk_matrix* A, bool trans, int planes, con
   do {                                                                                                       \
     auto kern = tc_sketch_kernel<TR, PL>;                                                                   \
     JLS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-    kern<<<grid, TC_THREADS, smem, s>>>(a, A->ld, t0, t1, w, scale, out, ldo, vec_ok, d_err);               \
+    kern<<<grid, TC_THREADS, smem, s>>>(a, A->ld, t0, t1, ta, w, scale, out, ldo, vec_ok, pf_dist, d_err);   \
   } while (0)
   if (trans && planes == 2) JLS_TC_LAUNCH(true, 2);
   else if (trans) JLS_TC_LAUNCH(true, 1);
