@@ -999,12 +999,12 @@ int run_gathers(sk_hss* H, std::vector<GatherJob>& jobs, cudaStream_t s) {
 }
 
 // Cluster size for a launch over `nodes` nodes of up to mmax rows: the
-// largest power of two that keeps nodes x ncl within the SMs and 32 rows per
-// CTA, at most max_ncl.
-int pick_ncl(int max_ncl, int nodes, int mmax) {
+// largest power of two that keeps nodes x ncl within the SMs and min_rows rows
+// per CTA, at most max_ncl.
+int pick_ncl(int max_ncl, int nodes, int mmax, int min_rows) {
   const int sms = num_sms();
   int ncl = 1;
-  while (ncl < max_ncl && nodes * ncl * 2 <= sms && mmax >= 32 * ncl * 2) ncl *= 2;
+  while (ncl < max_ncl && nodes * ncl * 2 <= sms && mmax >= min_rows * ncl * 2) ncl *= 2;
   return ncl;
 }
 
@@ -1202,7 +1202,7 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
         mmax = std::max(mmax, t.m);
         qx = std::max(qx, (t.q < 0 ? std::min(t.m, d) : t.q) + dd);
       }
-      const int ncl = pick_ncl(H->max_ncl_test, (int)tj.size(), mmax);
+      const int ncl = pick_ncl(H->max_ncl_test, (int)tj.size(), mmax, 32);
       const int mrx = (mmax + ncl - 1) / ncl;
       TestLayout lay{mrx, qx, 1, std::max(1, std::min(GMAX, 4096 / std::max(1, mrx)))};
       if (test_smem_bytes(lay) > (ncl == 16 ? H->test_smem16 : TEST_SMEM_MAX)) lay.qsm = 0;
@@ -1269,7 +1269,10 @@ int sweep(sk_hss* H, cudaStream_t s, bool* grow) {
       const int sp = span_begin(H, s);
       int mmax = 0;
       for (const IdJob& t : ij) mmax = std::max(mmax, t.m);
-      const int ncl = pick_ncl(H->max_ncl_id, (int)ij.size(), mmax);
+      // a decomposition's arithmetic does not depend on how its rows are split
+      // (each row's dots and updates stay in one warp), so it takes clusters
+      // down to 16 rows per CTA, one row per warp
+      const int ncl = pick_ncl(H->max_ncl_id, (int)ij.size(), mmax, 16);
       IdLayout lay{C, (mmax + ncl - 1) / ncl, std::min(mmax, C), 1};
       if (id_smem_bytes(lay) > (ncl == 16 ? H->id_smem16 : ID_SMEM_MAX)) lay.wsm = 0;
       JLS_CHECK(launch_cl(hss_id_kernel, (unsigned)ij.size(), ncl, id_smem_bytes(lay), s,
