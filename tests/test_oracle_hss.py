@@ -158,3 +158,40 @@ def test_level_scaled_tolerance():
         h0 = [h for h in res["history"] if h[0] == 0 and h[1] == 2 and h[2] == 0][0]
         assert abs(h0[4] / h0[5] - rho) <= 1e-10 * rho
         assert (h0[3] == "passed") == want, (f, h0)
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 1), (7, 8), (64, 64), (65, 64), (1000, 37), (2048, 64), (3001, 100)])
+def test_cluster_tree_partition_and_split_rule(n, leaf):
+    """The tree's leaves are consecutive index ranges covering [0, n) in order,
+    no leaf holds more than `leaf` indices, every split node holds more and
+    gives its left child floor(m / 2) indices, and a node's level is its depth
+    (checked by a walk written independently of the tree's construction)."""
+    root = hss.cluster_tree(n, leaf)
+    leaves, seen = [], 0
+
+    def walk(nd, depth):
+        nonlocal seen
+        assert nd.level == depth and nd.hi > nd.lo
+        m = nd.hi - nd.lo
+        if not nd.children:
+            assert m <= leaf and nd.lo == seen
+            seen = nd.hi
+            leaves.append(m)
+            return
+        assert m > leaf and len(nd.children) == 2
+        a, b = nd.children
+        assert (a.lo, a.hi, b.lo, b.hi) == (nd.lo, nd.lo + m // 2, nd.lo + m // 2, nd.hi)
+        walk(a, depth + 1)
+        walk(b, depth + 1)
+
+    walk(root, 0)
+    assert seen == n and sum(leaves) == n
+    # levels() lists every node once, by depth, left to right
+    lv = hss.levels(root)
+    assert [nd.level for L in lv for nd in L] == sorted(nd.level for L in lv for nd in L)
+    for L in lv:
+        assert [nd.lo for nd in L] == sorted(nd.lo for nd in L)
+    assert sum(len(L) for L in lv) == 2 * len(leaves) - 1
+    # for n = leaf * 2^j the tree is perfect with j + 1 levels
+    if n % leaf == 0 and ((n // leaf) & (n // leaf - 1)) == 0:
+        assert len(lv) == (n // leaf).bit_length() and set(leaves) == {leaf}

@@ -432,3 +432,51 @@ def test_srht_with_replacement_operator():
         ops.Operator("srht", n, d, seed=3)  # without replacement d <= nu
     with pytest.raises(ValueError):
         ops.Operator("gauss", n, 8, seed=3, replace=True)
+
+
+def test_next_pow2_is_the_least_power_of_two_not_below_n():
+    for n in range(1, 5000):
+        p = ops.next_pow2(n)
+        assert p >= n and p & (p - 1) == 0 and (p == 1 or p // 2 < n)
+    assert ops.next_pow2(1 << 40) == 1 << 40 and ops.next_pow2((1 << 40) + 1) == 1 << 41
+
+
+@pytest.mark.parametrize("construction,width,alpha", [("block", 64, 4), ("block", 12, 3), ("graph", 64, 4),
+                                                      ("graph", 5, 5), ("graph", 32, 1)])
+def test_sjlt_block_draws_structure(construction, width, alpha):
+    """Sec. 2.4.3: each row holds alpha +-1 entries; the block construction puts
+    one in each of alpha chunks of width / alpha columns, the graph construction
+    alpha distinct columns (sorted); draws of another block or seed differ."""
+    n = 3000
+    cols, signs = ops.sjlt_block_draws(n, width, alpha, seed=5, block=2, construction=construction)
+    assert cols.shape == (n, alpha) and signs.shape == (n, alpha)
+    assert cols.min() >= 0 and cols.max() < width
+    assert set(np.unique(signs)) <= {-1, 1}
+    if construction == "block":
+        span = width // alpha
+        assert np.array_equal(cols // span, np.broadcast_to(np.arange(alpha), (n, alpha)))
+    else:
+        assert (np.diff(cols, axis=1) > 0).all()
+        if alpha == width:
+            assert (cols == np.arange(width)).all()
+    # both signs and (where there is a choice) every position occur
+    assert (signs == 1).any() and (signs == -1).any()
+    if construction == "graph" and alpha < width:
+        assert np.unique(cols).size == width
+    c2, s2 = ops.sjlt_block_draws(n, width, alpha, seed=5, block=3, construction=construction)
+    c3, s3 = ops.sjlt_block_draws(n, width, alpha, seed=6, block=2, construction=construction)
+    assert not (np.array_equal(c2, cols) and np.array_equal(s2, signs))
+    assert not (np.array_equal(c3, cols) and np.array_equal(s3, signs))
+    c4, s4 = ops.sjlt_block_draws(n, width, alpha, seed=5, block=2, construction=construction)
+    assert np.array_equal(c4, cols) and np.array_equal(s4, signs)
+
+
+def test_sjlt_block_draws_refuses_bad_arguments():
+    with pytest.raises(ValueError):
+        ops.sjlt_block_draws(10, 8, 2, 1, 0, "other")
+    with pytest.raises(ValueError):
+        ops.sjlt_block_draws(10, 8, 0, 1, 0, "graph")
+    with pytest.raises(ValueError):
+        ops.sjlt_block_draws(10, 8, 9, 1, 0, "graph")
+    with pytest.raises(ValueError):
+        ops.sjlt_block_draws(10, 10, 3, 1, 0, "block")
