@@ -71,8 +71,14 @@ extern "C" {
 /* ---- arithmetic of an apply -------------------------------------------- */
 #define SK_PREC_NATIVE 0  /* F64 data: FP64; F32 data: FP32 on CUDA cores          */
 #define SK_PREC_BF16X2 3  /* F32 data: A = A_hi + A_lo (bf16), R likewise (Gaussian)
-                             or exact (+-1, SRHT); tcgen05 tensor cores, FP32
-                             accumulation; SRHT and Gaussian only                  */
+                             or exact (+-1, SRHT; {0, +-1}, SJLT); tcgen05 tensor
+                             cores, FP32 accumulation.  SRHT and Gaussian always
+                             take it; an SJLT product takes it where the route
+                             pick measures it faster (sketch_sjlt_route), else
+                             the SJLT kernels in FP32.  The kernel asks L2 for
+                             A's tiles a few units ahead of use (3; the
+                             environment variable JLS_TC_PREFETCH=0..64 sets
+                             the distance, 0 turns it off)                        */
 #define SK_PREC_FP8    4  /* F32 data: e4m3 hi + lo terms of A per 128 x 128 tile
                              scale and of z per (128 x 1) scale, SRHT signs exact;
                              tcgen05 tensor cores, FP32 accumulation, scales
@@ -159,7 +165,8 @@ int sketch_increment(sk_handle h, int32_t delta_d, void* stream);
  *          handle owns and each block is sketched; S' is computed as the S
  *          product of K(Y, X), which equals K^T.
  *   which  SK_S, SK_ST or SK_BOTH.
- *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 / SK_PREC_FP8 (F32, SRHT/Gaussian).
+ *   prec   SK_PREC_NATIVE, or SK_PREC_BF16X2 (F32; SJLT by measured route) /
+ *          SK_PREC_FP8 (F32, SRHT/Gaussian).
  *   S      device, rows x d_total (ldS >= d_total) of A's dtype; used if which & SK_S.
  *   St     device, cols x d_total (ldSt >= d_total);             used if which & SK_ST.
  *          For SK_C64 data S = A R and S' = A* R are complex (interleaved FP32
